@@ -1,0 +1,193 @@
+/*
+ * dtsph.h - C ABI of the GB300 (sm_103a) library for the inner pseudo-time
+ * iteration of the dual-time EDAC-SPH scheme with particles frozen in pseudo-time
+ * (Ramachandran, Muta & Ramakrishna, arXiv:1904.00861, Algorithm 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: DTSPH_OK (0) on success, a negative DTSPH_E_* code otherwise;
+ *    dtsph_last_error() then holds a one-line message. A failed call leaves the
+ *    context usable unless it returned DTSPH_E_CUDA.
+ *  - Host arrays are owned by the caller and only read (inputs) or written
+ *    (outputs) during the call. Particle arrays are row-major AoS in FP64:
+ *    positions and velocities are n x dim, pressures n. Particle i of every
+ *    output is particle i of the last dtsph_set_particles call (the library
+ *    sorts particles internally and undoes the permutation on output).
+ *  - *_device variants take device pointers (for example torch data_ptr());
+ *    the caller keeps those buffers alive until the stream has consumed them.
+ *  - All GPU work of a context is ordered on the stream passed to dtsph_create
+ *    (NULL = the legacy default stream). A context is not thread-safe.
+ *  - Non-convergence of the pseudo-time loop is not an error: it is reported in
+ *    dtsph_step_stats.reason, following the stop rules of Sec. 3.4.
+ */
+#ifndef DTSPH_H
+#define DTSPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DTSPH_VERSION "0.1.0"
+
+enum {
+    DTSPH_OK = 0,
+    DTSPH_E_ARG = -1,         /* invalid argument (null pointer, size, parameter) */
+    DTSPH_E_STATE = -2,       /* call out of order, e.g. dtsph_step before dtsph_set_particles */
+    DTSPH_E_CUDA = -3,        /* a CUDA runtime call failed */
+    DTSPH_E_OOM = -4,         /* a device allocation failed */
+    DTSPH_E_CAPACITY = -5,    /* a particle had more than max_neighbors neighbours */
+    DTSPH_E_DOMAIN = -6,      /* a particle left the box of a non-periodic axis */
+    DTSPH_E_UNSUPPORTED = -7  /* parameter combination not implemented on the GPU */
+};
+
+typedef enum {
+    DTSPH_FP64 = 0,   /* every floating-point operation in IEEE double */
+    DTSPH_FP32C = 1   /* pair sums in FP32 with Kahan compensation; positions, the
+                         real-time BDF2 source term, the velocity iterate and the
+                         residual reduction in FP64 */
+} dtsph_precision;
+
+/* Parameters of one simulation (Sec. 3.4 and 5 of the paper). Derived values:
+ * c = beta * v_ref, nu_e = h c / 16 (Eq. nu_edac), dtau = dt / beta. */
+typedef struct {
+    int32_t dim;              /* 2 or 3 */
+    int32_t precision;        /* dtsph_precision */
+    int32_t periodic[3];      /* 1 = periodic axis; a periodic axis needs hi - lo >= 9h */
+    int32_t pad0;
+    double lo[3], hi[3];      /* domain box; periodic axes wrap to [lo, hi); on the
+                                 other axes every particle must stay inside */
+    double h;                 /* smoothing length; the quintic kernel has support 3h */
+    double m;                 /* particle mass (uniform) */
+    double rho0;              /* density, held fixed (Sec. 3) */
+    double beta;              /* artificial-compressibility factor, c = beta * v_ref */
+    double v_ref;             /* reference speed of Eq. (conv) */
+    double nu;                /* kinematic viscosity */
+    double dt;                /* real time step */
+    double eta;               /* regulariser of r^2 + eta h^2 (0.01) */
+    double alpha;             /* Monaghan artificial viscosity (0 = off) */
+    double g[3];              /* body force */
+    double eps;               /* tolerance of Eq. (conv) */
+    double stag_tol;          /* stagnation threshold (0.05) */
+    int32_t stag_window;      /* stagnation window in iterations (4; 0 = off) */
+    int32_t max_iter;         /* iteration cap (1000) */
+    int32_t edac;             /* 1: EDAC pressure diffusion on (Eq. dp-dtau-frozen-edac) */
+    int32_t edac_h2_literal;  /* 1: EDAC denominator r^2 + h^2 as printed; 0: r^2 + eta h^2 */
+    int32_t fixed_iters;      /* > 0: run exactly this many iterations per step, no stop rules */
+    int32_t max_neighbors;    /* neighbour capacity per particle (0 = derived from h and m) */
+    int32_t graph;            /* 1: capture each real step in a CUDA graph whose pseudo-time
+                                 loop is a conditional while node; 0: plain launches */
+    int32_t pad1;
+} dtsph_params;
+
+typedef struct {
+    int32_t iters;    /* pseudo-time iterations taken in this real step */
+    int32_t reason;   /* 0 converged, 1 stagnated, 2 iteration cap, 3 non-finite residual,
+                         4 fixed iteration count reached */
+    double rp;        /* mean|dp/dtau| dt / (rho0 c^2) of the last iteration, Eq. (conv) */
+    double rv;        /* mean|dt dV/dtau| / v_ref of the last iteration, Eq. (conv) */
+} dtsph_step_stats;
+
+enum {
+    DTSPH_FIELD_POS = 0,      /* r^n, n x dim */
+    DTSPH_FIELD_VEL = 1,      /* V^n, n x dim */
+    DTSPH_FIELD_P = 2,        /* p^n, n */
+    DTSPH_FIELD_VEL_PREV = 3  /* V^{n-1}, n x dim */
+};
+
+typedef struct dtsph_ctx dtsph_ctx;
+
+/* Creates a context on the current CUDA device. stream: a cudaStream_t, or NULL.
+ * Allocates nothing on the device until dtsph_set_particles. */
+int dtsph_create(const dtsph_params *params, void *stream, dtsph_ctx **out);
+
+/* Frees every device buffer, graph and stream of the context (NULL is a no-op). */
+void dtsph_destroy(dtsph_ctx *ctx);
+
+/* Fluid state at real time t^n (Algorithm 2 starts from it): nf particles with
+ * positions x (nf x dim), velocities V^n (nf x dim), pressures p^n (nf) and the
+ * previous velocities V^{n-1} for the BDF2 term (NULL: V^{n-1} = V^n, as the
+ * paper does without an exact solution, Sec. 3.1). Host pointers. Allocates
+ * the device state (sized for nf plus the current walls); resets the step
+ * counter. Must come after dtsph_set_boundary if there are walls. */
+int dtsph_set_particles(dtsph_ctx *ctx, int64_t nf, const double *x, const double *v,
+                        const double *p, const double *v_prev);
+
+/* As dtsph_set_particles with device pointers; enqueued on the context stream. */
+int dtsph_set_particles_device(dtsph_ctx *ctx, int64_t nf, const double *x, const double *v,
+                               const double *p, const double *v_prev);
+
+/* Fixed solid-wall particles (Sec. 3.2, Adami et al. 2012): nw positions
+ * (nw x dim) and prescribed velocities (nw x dim, NULL = at rest). Their
+ * pressure and ghost velocity are extrapolated from the fluid in every
+ * pseudo-iteration. Host pointers. Call before dtsph_set_particles. */
+int dtsph_set_boundary(dtsph_ctx *ctx, int64_t nw, const double *x, const double *v_wall);
+
+/* Enqueues nsteps real steps of Algorithm 2 (neighbour rebuild, state-n rates
+ * and predictor Eqs. v0/r0, pseudo-time loop Eqs. pkstar_frozen..pkp1_frozen
+ * with Eq. dv_dtau_exact until Eq. conv or a stop rule holds, Eq. r-update).
+ * Asynchronous: returns once the work is enqueued. Per-step statistics go to a
+ * device log read by dtsph_read_stats. */
+int dtsph_step(dtsph_ctx *ctx, int32_t nsteps);
+
+/* Waits for the stream, then reports a device-side error of the steps enqueued
+ * so far (DTSPH_E_CAPACITY, DTSPH_E_DOMAIN) or DTSPH_OK. */
+int dtsph_sync(dtsph_ctx *ctx);
+
+/* Number of real steps taken since dtsph_set_particles (host-side count). */
+int64_t dtsph_step_count(const dtsph_ctx *ctx);
+
+/* Copies the statistics of steps first .. first+count-1 (0-based since
+ * dtsph_set_particles) to out. Waits for the stream. Only the last 65536 steps
+ * are kept. */
+int dtsph_read_stats(dtsph_ctx *ctx, int64_t first, int32_t count, dtsph_step_stats *out);
+
+/* Copies one field of the fluid particles (DTSPH_FIELD_*) into the host array
+ * out, in the caller's particle order. Waits for the stream. */
+int dtsph_read_field(dtsph_ctx *ctx, int32_t field, double *out);
+
+/* As dtsph_read_field into device memory; enqueued on the context stream. */
+int dtsph_read_field_device(dtsph_ctx *ctx, int32_t field, double *out);
+
+/* Test entry: the two rates of Eqs. (dp-dtau-frozen-edac, mom-sph-frozen) at
+ * the current state (positions r^n, V^n, p^n; walls extrapolated first), for
+ * every fluid particle in caller order: ap (nf) and F (nf x dim), host arrays.
+ * Does not change the state. Waits for the stream. */
+int dtsph_eval_rates(dtsph_ctx *ctx, double *ap, double *F);
+
+/* Test entry: builds the neighbour lists N(i) = {j != i : |r_i - r_j| < 3h} at the
+ * current positions (all particles, walls after fluid in the numbering) and
+ * keeps them until the next call. */
+int dtsph_build_neighbors(dtsph_ctx *ctx);
+
+/* Test entry: after dtsph_build_neighbors, writes the neighbours of particle i
+ * (0..nf+nw-1, caller numbering, ascending) to out (capacity cap) and their
+ * number to *count (which may exceed cap; out then holds the first cap). */
+int dtsph_get_neighbors(dtsph_ctx *ctx, int64_t i, int64_t *out, int64_t cap, int64_t *count);
+
+/* Measurement entry: after at least one dtsph_step, re-runs the pseudo-time
+ * iteration kernel of the last step `launches` times (1..256) on its frozen pair
+ * cache, each launch bracketed by CUDA events on the context stream, and
+ * returns the mean launch duration in milliseconds, the algorithmic bytes one
+ * launch must move (particle state read and written once, every cached pair
+ * read once; the layout is described in the design notes) and the number of
+ * cached fluid pairs. The state r^n, V^n, p^n is not changed. Waits for the
+ * stream. */
+int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, double *bytes_per_launch,
+                        int64_t *pairs);
+
+/* Kernel launches this context has made so far (counted on the host; a graph
+ * launch counts the kernels it runs, pseudo-iterations included). */
+int64_t dtsph_kernel_launches(const dtsph_ctx *ctx);
+
+/* Message of the last failed call, or "" (never NULL; valid until the next call). */
+const char *dtsph_last_error(const dtsph_ctx *ctx);
+
+/* DTSPH_VERSION. */
+const char *dtsph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTSPH_H */

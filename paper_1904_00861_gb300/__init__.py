@@ -1,0 +1,313 @@
+"""Python binding of the DTSPH GB300 library (include/dtsph.h).
+
+The functions below carry the C entry points' names and only marshal
+arguments: numpy arrays for host pointers, torch CUDA tensors (or raw integer
+addresses) for device pointers. Every step of the method runs in the CUDA
+library ``_build/libdtsph.so``; there is no other code path. Importing this
+package never builds or loads anything; the first call loads the library and
+raises if it has not been built (``python -m paper_1904_00861_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdtsph.so")
+
+DTSPH_OK = 0
+ERRORS = {
+    -1: "DTSPH_E_ARG", -2: "DTSPH_E_STATE", -3: "DTSPH_E_CUDA", -4: "DTSPH_E_OOM",
+    -5: "DTSPH_E_CAPACITY", -6: "DTSPH_E_DOMAIN", -7: "DTSPH_E_UNSUPPORTED",
+}
+DTSPH_FP64, DTSPH_FP32C = 0, 1
+FIELD_POS, FIELD_VEL, FIELD_P, FIELD_VEL_PREV = 0, 1, 2, 3
+REASONS = {0: "converged", 1: "stagnated", 2: "max_iter", 3: "nonfinite", 4: "fixed"}
+
+
+class DtsphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dtsph_params(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("precision", C.c_int32), ("periodic", C.c_int32 * 3), ("pad0", C.c_int32),
+        ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("h", C.c_double), ("m", C.c_double), ("rho0", C.c_double), ("beta", C.c_double), ("v_ref", C.c_double),
+        ("nu", C.c_double), ("dt", C.c_double), ("eta", C.c_double), ("alpha", C.c_double),
+        ("g", C.c_double * 3), ("eps", C.c_double), ("stag_tol", C.c_double),
+        ("stag_window", C.c_int32), ("max_iter", C.c_int32), ("edac", C.c_int32), ("edac_h2_literal", C.c_int32),
+        ("fixed_iters", C.c_int32), ("max_neighbors", C.c_int32), ("graph", C.c_int32), ("pad1", C.c_int32),
+    ]
+
+
+class dtsph_step_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rp", C.c_double), ("rv", C.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_VP, _DP, _I64P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)
+_SIGS = [
+    ("dtsph_version", C.c_char_p, []),
+    ("dtsph_last_error", C.c_char_p, [_VP]),
+    ("dtsph_create", C.c_int, [C.POINTER(dtsph_params), _VP, C.POINTER(_VP)]),
+    ("dtsph_destroy", None, [_VP]),
+    ("dtsph_set_boundary", C.c_int, [_VP, C.c_int64, _VP, _VP]),
+    ("dtsph_set_particles", C.c_int, [_VP, C.c_int64, _VP, _VP, _VP, _VP]),
+    ("dtsph_set_particles_device", C.c_int, [_VP, C.c_int64, _VP, _VP, _VP, _VP]),
+    ("dtsph_step", C.c_int, [_VP, C.c_int32]),
+    ("dtsph_sync", C.c_int, [_VP]),
+    ("dtsph_step_count", C.c_int64, [_VP]),
+    ("dtsph_read_stats", C.c_int, [_VP, C.c_int64, C.c_int32, C.POINTER(dtsph_step_stats)]),
+    ("dtsph_read_field", C.c_int, [_VP, C.c_int32, _VP]),
+    ("dtsph_read_field_device", C.c_int, [_VP, C.c_int32, _VP]),
+    ("dtsph_eval_rates", C.c_int, [_VP, _VP, _VP]),
+    ("dtsph_build_neighbors", C.c_int, [_VP]),
+    ("dtsph_get_neighbors", C.c_int, [_VP, C.c_int64, _I64P, C.c_int64, _I64P]),
+    ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
+    ("dtsph_kernel_launches", C.c_int64, [_VP]),
+]
+
+
+def lib():
+    """Loads the CUDA library; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"DTSPH CUDA library not built: {LIB_PATH} is missing "
+                              "(run python -m paper_1904_00861_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [s[0] for s in _SIGS]
+
+
+def _check(ctx, rc):
+    if rc != DTSPH_OK:
+        msg = lib().dtsph_last_error(ctx).decode() if ctx else ""
+        raise DtsphError(rc, msg)
+
+
+def _host(a, dim=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _ptr(a):
+    """Address of a numpy array, a torch tensor, or an integer address."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) -> dtsph_params:
+    """Fill dtsph_params from a plain dict (the keys of ``synth`` configs)."""
+    d = dict(periodic=(0, 0, 0), lo=(0, 0, 0), hi=(1, 1, 1), rho0=1.0, beta=10.0, v_ref=1.0, eta=0.01, alpha=0.0,
+             g=(0, 0, 0), eps=1e-3, stag_tol=0.05, stag_window=4, max_iter=1000, edac=1, edac_h2_literal=0,
+             fixed_iters=0, max_neighbors=0)
+    d.update(cfg)
+    d.update(over)
+    p = dtsph_params()
+    p.dim = int(d["dim"])
+    p.precision = int(d.get("precision", precision))
+    p.graph = int(d.get("graph", graph))
+    for a in range(3):
+        p.periodic[a] = int(d["periodic"][a]) if a < len(d["periodic"]) else 0
+        p.lo[a] = float(d["lo"][a]) if a < len(d["lo"]) else 0.0
+        p.hi[a] = float(d["hi"][a]) if a < len(d["hi"]) else 1.0
+        p.g[a] = float(d["g"][a]) if a < len(d["g"]) else 0.0
+    for k in ("h", "m", "rho0", "beta", "v_ref", "nu", "dt", "eta", "alpha", "eps", "stag_tol"):
+        setattr(p, k, float(d[k]))
+    for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "max_neighbors"):
+        setattr(p, k, int(d[k]))
+    return p
+
+
+# ------------------------------------------------------------ entry points
+
+def dtsph_version() -> str:
+    return lib().dtsph_version().decode()
+
+
+def dtsph_create(params: dtsph_params, stream=None) -> int:
+    """Returns the context handle (an integer). stream: cudaStream_t address,
+    a torch.cuda.Stream, or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = C.c_void_p()
+    _check(None, lib().dtsph_create(C.byref(params), stream, C.byref(out)))
+    return out.value
+
+
+def dtsph_destroy(ctx) -> None:
+    lib().dtsph_destroy(ctx)
+
+
+def dtsph_set_boundary(ctx, x, v_wall=None) -> None:
+    x = _host(x)
+    vw = None if v_wall is None else _host(v_wall)
+    _check(ctx, lib().dtsph_set_boundary(ctx, x.shape[0], _ptr(x), _ptr(vw)))
+
+
+def dtsph_set_particles(ctx, x, v, p, v_prev=None) -> None:
+    x, v, p = _host(x), _host(v), _host(p)
+    vp = None if v_prev is None else _host(v_prev)
+    _check(ctx, lib().dtsph_set_particles(ctx, x.shape[0], _ptr(x), _ptr(v), _ptr(p), _ptr(vp)))
+
+
+def dtsph_set_particles_device(ctx, nf, x, v, p, v_prev=None) -> None:
+    _check(ctx, lib().dtsph_set_particles_device(ctx, int(nf), _ptr(x), _ptr(v), _ptr(p), _ptr(v_prev)))
+
+
+def dtsph_step(ctx, nsteps: int = 1) -> None:
+    _check(ctx, lib().dtsph_step(ctx, int(nsteps)))
+
+
+def dtsph_sync(ctx) -> None:
+    _check(ctx, lib().dtsph_sync(ctx))
+
+
+def dtsph_step_count(ctx) -> int:
+    return lib().dtsph_step_count(ctx)
+
+
+def dtsph_read_stats(ctx, first: int, count: int):
+    buf = (dtsph_step_stats * max(count, 1))()
+    _check(ctx, lib().dtsph_read_stats(ctx, int(first), int(count), buf))
+    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv) for b in buf[:count]]
+
+
+def dtsph_read_field(ctx, field: int, n: int, comps: int) -> np.ndarray:
+    out = np.empty((n, comps) if comps > 1 else n, np.float64)
+    _check(ctx, lib().dtsph_read_field(ctx, int(field), _ptr(out)))
+    return out
+
+
+def dtsph_read_field_device(ctx, field: int, out) -> None:
+    _check(ctx, lib().dtsph_read_field_device(ctx, int(field), _ptr(out)))
+
+
+def dtsph_eval_rates(ctx, nf: int, dim: int):
+    ap = np.empty(nf, np.float64)
+    F = np.empty((nf, dim), np.float64)
+    _check(ctx, lib().dtsph_eval_rates(ctx, _ptr(ap), _ptr(F)))
+    return ap, F
+
+
+def dtsph_build_neighbors(ctx) -> None:
+    _check(ctx, lib().dtsph_build_neighbors(ctx))
+
+
+def dtsph_get_neighbors(ctx, i: int, cap: int = 512) -> np.ndarray:
+    out = np.zeros(cap, np.int64)
+    cnt = C.c_int64()
+    _check(ctx, lib().dtsph_get_neighbors(ctx, int(i), out.ctypes.data_as(_I64P), cap, C.byref(cnt)))
+    if cnt.value > cap:
+        return dtsph_get_neighbors(ctx, i, int(cnt.value))
+    return out[: cnt.value].copy()
+
+
+def dtsph_probe_iterate(ctx, launches: int = 20):
+    """Mean duration (ms) of the pseudo-iteration kernel, its algorithmic bytes
+    per launch, and the number of cached fluid pairs."""
+    ms = C.c_float()
+    by = C.c_double()
+    npairs = C.c_int64()
+    _check(ctx, lib().dtsph_probe_iterate(ctx, int(launches), C.byref(ms), C.byref(by), C.byref(npairs)))
+    return float(ms.value), float(by.value), int(npairs.value)
+
+
+def dtsph_kernel_launches(ctx) -> int:
+    return lib().dtsph_kernel_launches(ctx)
+
+
+def dtsph_last_error(ctx) -> str:
+    return lib().dtsph_last_error(ctx).decode()
+
+
+# ------------------------------------------------------------ convenience
+
+class Simulation:
+    """Owns one context. ``Simulation(cfg, precision=DTSPH_FP32C)`` then
+    ``set_state(x, v, p, v_prev, walls=(xw, vw))`` and ``step(n)``."""
+
+    def __init__(self, cfg: dict, precision: int = DTSPH_FP64, stream=None, graph: int = 1, **over):
+        self.cfg = dict(cfg)
+        self.dim = int(cfg["dim"])
+        self.params = make_params(cfg, precision=precision, graph=graph, **over)
+        self.ctx = dtsph_create(self.params, stream)
+        self.nf = 0
+
+    def close(self):
+        if self.ctx:
+            dtsph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, x, v, p, v_prev=None, walls=None, nf=None):
+        nf = len(v) if nf is None else nf
+        x = np.asarray(x, np.float64)
+        if walls is None and x.shape[0] > nf:
+            walls = (x[nf:], None)
+        if walls is not None:
+            dtsph_set_boundary(self.ctx, walls[0], walls[1])
+        dtsph_set_particles(self.ctx, x[:nf], v, p, v_prev)
+        self.nf = nf
+
+    def step(self, nsteps: int = 1):
+        dtsph_step(self.ctx, nsteps)
+
+    def sync(self):
+        dtsph_sync(self.ctx)
+
+    def stats(self, first=0, count=None):
+        n = dtsph_step_count(self.ctx)
+        count = n - first if count is None else count
+        return dtsph_read_stats(self.ctx, first, count)
+
+    def field(self, which: int) -> np.ndarray:
+        comps = 1 if which == FIELD_P else self.dim
+        return dtsph_read_field(self.ctx, which, self.nf, comps)
+
+    @property
+    def x(self):
+        return self.field(FIELD_POS)
+
+    @property
+    def v(self):
+        return self.field(FIELD_VEL)
+
+    @property
+    def p(self):
+        return self.field(FIELD_P)
+
+    @property
+    def v_prev(self):
+        return self.field(FIELD_VEL_PREV)
+
+    def rates(self):
+        return dtsph_eval_rates(self.ctx, self.nf, self.dim)

@@ -1,0 +1,714 @@
+// C ABI of the library (include/dtsph.h): context, device memory, the per-step
+// launch sequence, its CUDA-graph capture, and field read-back.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dtsph.h"
+#include "dtsph_internal.cuh"
+
+using namespace dtsph;
+
+struct dtsph_ctx {
+    dtsph_params prm;
+    Geom G;
+    Phys P;
+    Buffers B;
+    cudaStream_t stream = nullptr;      // caller stream (may be the legacy default stream)
+    cudaStream_t cap = nullptr;         // private stream used for graph capture
+    int device = 0;
+    bool have_particles = false;
+    bool have_nbrs = false;             // dtsph_build_neighbors lists in order B
+    int64_t nw_pending = 0;
+    std::vector<double> xw_host, vw_host;
+    int64_t steps = 0;
+    int64_t launches = 0;
+    int per_step_fixed = 0;             // kernels per step outside the loop
+    int per_iter = 0;                   // kernels per pseudo-iteration
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    std::string err;
+    std::vector<void *> allocs;
+    int nblk = 0;
+    double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
+};
+
+namespace {
+
+const char *kNoCtx = "null context";
+
+int fail(dtsph_ctx *c, int code, const char *fmt, ...)
+{
+    if (!c) return code;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(c, DTSPH_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+template <typename T>
+int dalloc(dtsph_ctx *c, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DTSPH_E_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    return DTSPH_OK;
+}
+
+void free_all(dtsph_ctx *c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    memset(&c->B, 0, sizeof(c->B));
+    c->have_particles = false;
+    c->have_nbrs = false;
+}
+
+double pi() { return 3.14159265358979323846; }
+
+// Quintic spline normalisation: W integrates to 1 over R^dim.
+double quintic_sigma(int dim, double h)
+{
+    return dim == 2 ? 7.0 / (478.0 * pi() * h * h) : 1.0 / (120.0 * pi() * h * h * h);
+}
+
+int setup_geometry(dtsph_ctx *c)
+{
+    const dtsph_params &p = c->prm;
+    Geom &G = c->G;
+    memset(&G, 0, sizeof G);
+    G.dim = p.dim;
+    const double rc = 3.0 * p.h;
+    G.ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        G.periodic[a] = a < p.dim ? p.periodic[a] : 0;
+        G.lo[a] = p.lo[a];
+        G.hi[a] = p.hi[a];
+        if (a >= p.dim) {
+            G.nc[a] = 1;
+            G.s[a] = 1.0;
+            G.inv_s[a] = 1.0;
+            G.s_f[a] = 1.f;
+            G.L[a] = 1.0;
+            G.halfL[a] = 0.5;
+            continue;
+        }
+        double L = p.hi[a] - p.lo[a];
+        if (!(L > 0)) return fail(c, DTSPH_E_ARG, "axis %d: hi must exceed lo", a);
+        // cells strictly wider than 3h so that rounding never separates neighbours
+        long long k = (long long)std::floor(L / (rc * (1.0 + 1e-9)));
+        if (k < 1) k = 1;
+        if (G.periodic[a] && k < 3)
+            return fail(c, DTSPH_E_ARG, "periodic axis %d is shorter than 9h (%g < %g)", a, L, 3 * rc);
+        if (k > (1 << 20)) return fail(c, DTSPH_E_ARG, "axis %d has too many cells", a);
+        G.nc[a] = (int)k;
+        G.s[a] = L / (double)k;
+        G.inv_s[a] = 1.0 / G.s[a];
+        G.s_f[a] = (float)G.s[a];
+        G.L[a] = L;
+        G.halfL[a] = 0.5 * L;
+        G.ncell *= (int)k;
+    }
+    if ((long long)G.nc[0] * G.nc[1] * G.nc[2] > (1LL << 30)) return fail(c, DTSPH_E_ARG, "too many cells");
+    G.rc2 = rc * rc;
+    // FP32 band around (3h)^2: the FP32 separation from cell offsets is accurate
+    // to a few 1e-7 h, so outside +-2e-5 relative the FP32 test decides
+    G.rc2_lo = (float)(G.rc2 * (1.0 - 2e-5));
+    G.rc2_hi = (float)(G.rc2 * (1.0 + 2e-5));
+    return DTSPH_OK;
+}
+
+void setup_phys(dtsph_ctx *c)
+{
+    const dtsph_params &p = c->prm;
+    Phys &P = c->P;
+    memset(&P, 0, sizeof P);
+    P.h = p.h;
+    P.m = p.m;
+    P.rho0 = p.rho0;
+    P.c = p.beta * p.v_ref;
+    P.nu = p.nu;
+    P.nu_e = p.h * P.c / 16.0;
+    P.dt = p.dt;
+    P.dtau = p.dt / p.beta;
+    P.sig_h = quintic_sigma(p.dim, p.h) / p.h;
+    P.eta_h2 = p.eta * p.h * p.h;
+    P.edac_h2 = P.eta_h2;
+    const double rho = p.rho0;
+    P.c_div = p.m * (rho / rho) * P.c * P.c;
+    P.c_edac = 4.0 * p.m / ((rho + rho) * rho) * P.nu_e;
+    P.c_p = p.m / (rho * rho);
+    P.c_visc = 4.0 * p.m * p.nu / (rho + rho);
+    P.c_av = p.alpha * p.h * P.c / rho;
+    for (int a = 0; a < 3; ++a) P.g[a] = a < p.dim ? p.g[a] : 0.0;
+    P.kappa = 2.0 * p.dt / (2.0 * p.dt + 3.0 * P.dtau);
+    P.c3 = 3.0 / (2.0 * p.dt);
+    P.inv_2dt = 1.0 / (2.0 * p.dt);
+    P.edac = p.edac;
+    P.use_av = p.alpha != 0.0;
+}
+
+int validate(dtsph_ctx *c, const dtsph_params *p)
+{
+    if (p->dim != 2 && p->dim != 3) return fail(c, DTSPH_E_ARG, "dim must be 2 or 3");
+    if (p->precision != DTSPH_FP64 && p->precision != DTSPH_FP32C) return fail(c, DTSPH_E_ARG, "bad precision");
+    const double pos[] = {p->h, p->m, p->rho0, p->beta, p->v_ref, p->dt};
+    const char *nm[] = {"h", "m", "rho0", "beta", "v_ref", "dt"};
+    for (int i = 0; i < 6; ++i)
+        if (!(pos[i] > 0) || !std::isfinite(pos[i])) return fail(c, DTSPH_E_ARG, "%s must be positive and finite", nm[i]);
+    if (!(p->nu >= 0) || !(p->eta > 0) || !(p->alpha >= 0) || !(p->eps >= 0) || !(p->stag_tol >= 0))
+        return fail(c, DTSPH_E_ARG, "nu, alpha, eps, stag_tol must be >= 0 and eta > 0");
+    if (p->max_iter < 1 || p->max_iter > (1 << 24)) return fail(c, DTSPH_E_ARG, "max_iter out of range");
+    if (p->stag_window < 0 || p->stag_window > 16) return fail(c, DTSPH_E_ARG, "stag_window must be in [0, 16]");
+    if (p->fixed_iters < 0 || p->fixed_iters > (1 << 24)) return fail(c, DTSPH_E_ARG, "fixed_iters out of range");
+    if (p->edac_h2_literal) return fail(c, DTSPH_E_UNSUPPORTED, "the literal r^2 + h^2 EDAC denominator is oracle-only");
+    if (p->max_neighbors < 0 || p->max_neighbors > 4096) return fail(c, DTSPH_E_ARG, "max_neighbors out of range");
+    return DTSPH_OK;
+}
+
+int neighbour_capacity(const dtsph_params &p)
+{
+    if (p.max_neighbors > 0) return p.max_neighbors;
+    const double vol = p.m / p.rho0;
+    const double rc = 3.0 * p.h;
+    double expect = p.dim == 2 ? pi() * rc * rc / vol : 4.0 / 3.0 * pi() * rc * rc * rc / vol;
+    int k = (int)std::ceil(1.35 * expect) + 8;
+    return std::min(std::max(k, 8), 4096);
+}
+
+int allocate(dtsph_ctx *c, int64_t nf, int64_t nw)
+{
+    free_all(c);
+    Buffers &B = c->B;
+    const int64_t n64 = nf + nw;
+    if (n64 <= 0 || n64 >= (1LL << 31) - 64) return fail(c, DTSPH_E_ARG, "particle count out of range");
+    const int n = (int)n64;
+    const int d = c->prm.dim;
+    B.n = n;
+    B.nf = (int)nf;
+    B.nw = (int)nw;
+    B.dim = d;
+    B.fp32c = c->prm.precision == DTSPH_FP32C;
+    B.K = neighbour_capacity(c->prm);
+    const size_t nd = (size_t)n * d;
+    const size_t nwarps = ((size_t)n + kWarp - 1) / kWarp;
+    const size_t npair = nwarps * B.K * kWarp;
+    int r;
+#define A(p, cnt) if ((r = dalloc(c, &(p), (cnt))) != DTSPH_OK) { free_all(c); return r; }
+    A(B.gid_a, n) A(B.x_a, nd) A(B.xp_a, nd) A(B.vn_a, nd) A(B.vnm1_a, nd) A(B.pn_a, n) A(B.s_a, nd) A(B.cell_a, n)
+    A(B.gid_b, n) A(B.x_b, nd) A(B.vn_b, nd) A(B.vnm1_b, nd) A(B.pn_b, n) A(B.xp_b, nd) A(B.v0_b, nd)
+    A(B.ph0_b, n) A(B.s_b, nd) A(B.cell_b, n)
+    A(B.key, n) A(B.slot, n) A(B.perm, n) A(B.cell_count, c->G.ncell) A(B.cell_start, (size_t)c->G.ncell + 1)
+    A(B.vk[0], nd) A(B.vk[1], nd)
+    A(B.pcount, n) A(B.pj, npair)
+    if (B.fp32c) {
+        A(B.off, n) A(B.nb32[0], n) A(B.nb32[1], n) A(B.pc32, npair)
+    } else {
+        A(B.nb64[0], n) A(B.nb64[1], n) A(B.pc64, npair)
+    }
+    A(B.ap_b, n) A(B.f_b, nd)
+    c->nblk = iterate_blocks(B);
+    A(B.blk, 2 * (size_t)c->nblk) A(B.ls, 1) A(B.stats, kStatRing) A(B.err, 1)
+#undef A
+    CK(cudaMemsetAsync(B.cell_count, 0, sizeof(int) * c->G.ncell, c->stream));
+    CK(cudaMemsetAsync(B.err, 0, sizeof(uint32_t), c->stream));
+    CK(cudaMemsetAsync(B.pcount, 0, sizeof(int) * n, c->stream));
+    LoopState L;
+    memset(&L, 0, sizeof L);
+    L.reason = -1;
+    L.max_iter = c->prm.max_iter;
+    L.fixed_iters = c->prm.fixed_iters;
+    L.stag_window = c->prm.stag_window;
+    L.eps = c->prm.eps;
+    L.stag_tol = c->prm.stag_tol;
+    CK(cudaMemcpyAsync(B.ls, &L, sizeof L, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->P.rp_scale = c->P.dt / (c->P.rho0 * c->P.c * c->P.c) / (double)nf;
+    c->P.rv_scale = c->P.dt / c->prm.v_ref / (double)nf;
+    return DTSPH_OK;
+}
+
+// ---------------------------------------------------------------- step sequence
+
+// Everything of a real step before the pseudo-time loop. Returns kernels launched.
+int enqueue_pre_loop(dtsph_ctx *c, cudaStream_t st)
+{
+    const Buffers &B = c->B;
+    int k = 0;
+    k += launch_binning(B, c->G, B.x_a, B.gid_a, st);          // cells at r^n
+    k += launch_permute_a_to_b(B, c->G, st);
+    k += launch_state_n(B, c->G, c->P, true, st);              // walls, rates, predictor
+    k += launch_binning(B, c->G, B.xp_b, B.gid_b, st);         // cells at r^0
+    k += launch_permute_b_to_a(B, c->G, st);
+    k += launch_pair_cache(B, c->G, c->P, B.xp_a, B.cell_a, B.gid_a, st);
+    k += launch_loop_reset(B, st);
+    return k;
+}
+
+int enqueue_iteration(dtsph_ctx *c, cudaStream_t st, unsigned long long cond, int use_cond)
+{
+    int k = launch_walls_iter(c->B, c->G, c->P, st);
+    k += launch_iterate(c->B, c->G, c->P, cond, use_cond, st);
+    return k;
+}
+
+int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st) { return launch_outer(c->B, c->G, c->P, st); }
+
+// Graph of one real step: pre-loop kernels -> while node (walls, iterate) -> outer.
+int build_graph(dtsph_ctx *c)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    c->graph = g;
+    CK(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->per_step_fixed = enqueue_pre_loop(c, c->cap);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+    CK(cudaGraphAddNode(&wnode, g, dv.data(), nullptr, dv.size(), &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(c->cap, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    c->per_step_fixed += enqueue_post_loop(c, c->cap);
+    cudaGraph_t g2 = nullptr;
+    CK(cudaStreamEndCapture(c->cap, &g2));
+    CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->per_iter = enqueue_iteration(c, c->cap, (unsigned long long)h, 1);
+    cudaGraph_t b2 = nullptr;
+    CK(cudaStreamEndCapture(c->cap, &b2));
+    CK(cudaGraphInstantiate(&c->exec, g, 0));
+    return DTSPH_OK;
+}
+
+int read_loop_state(dtsph_ctx *c, LoopState *L)
+{
+    CK(cudaMemcpyAsync(L, c->B.ls, sizeof *L, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return DTSPH_OK;
+}
+
+// Plain launches: the loop runs in chunks of kernels that return at once when
+// the stop rule already holds; the host checks the device flag between chunks.
+int step_plain(dtsph_ctx *c)
+{
+    c->per_step_fixed = enqueue_pre_loop(c, c->stream);
+    c->launches += c->per_step_fixed;
+    const int cap = c->prm.fixed_iters > 0 ? c->prm.fixed_iters : c->prm.max_iter;
+    int issued = 0;
+    LoopState L;
+    while (true) {
+        const int chunk = 8;
+        for (int i = 0; i < chunk; ++i) {
+            c->per_iter = enqueue_iteration(c, c->stream, 0ull, 0);
+            c->launches += c->per_iter;
+        }
+        issued += chunk;
+        int r = read_loop_state(c, &L);
+        if (r) return r;
+        if (L.done) break;
+        if (issued > cap + 16) return fail(c, DTSPH_E_STATE, "pseudo-time loop did not stop");
+    }
+    c->launches += enqueue_post_loop(c, c->stream);
+    CK(cudaGetLastError());
+    return DTSPH_OK;
+}
+
+int device_error(dtsph_ctx *c)
+{
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, c->B.err, sizeof e, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e & kErrCapacity)
+        return fail(c, DTSPH_E_CAPACITY, "a particle had more than %d neighbours (raise max_neighbors)", c->B.K);
+    if (e & kErrDomain) return fail(c, DTSPH_E_DOMAIN, "a particle left the box of a non-periodic axis");
+    return DTSPH_OK;
+}
+
+int set_particles_impl(dtsph_ctx *c, int64_t nf, const double *x, const double *v, const double *p,
+                       const double *vprev, bool device)
+{
+    if (!x || !v || !p) return fail(c, DTSPH_E_ARG, "x, v and p are required");
+    if (nf <= 0) return fail(c, DTSPH_E_ARG, "nf must be positive");
+    CK(cudaSetDevice(c->device));
+    int r;
+    const int d = c->prm.dim;
+    const bool reuse = c->have_particles && c->B.nf == nf && c->B.nw == c->nw_pending;
+    if (!reuse) {
+        if ((r = allocate(c, nf, c->nw_pending))) return r;
+        // staging buffers for the AoS inputs, kept for later calls of the same size
+        if ((r = dalloc(c, &c->sx, (size_t)nf * d)) || (r = dalloc(c, &c->sv, (size_t)nf * d)) ||
+            (r = dalloc(c, &c->sp, nf)) || (r = dalloc(c, &c->svp, (size_t)nf * d)))
+            return r;
+        if (c->nw_pending > 0 &&
+            ((r = dalloc(c, &c->sxw, c->xw_host.size())) || (r = dalloc(c, &c->svw, c->vw_host.size()))))
+            return r;
+    }
+    const size_t bx = (size_t)nf * d * sizeof(double), bp = (size_t)nf * sizeof(double);
+    double *sx = c->sx, *sv = c->sv, *sp = c->sp, *svp = vprev ? c->svp : nullptr;
+    double *sxw = c->nw_pending > 0 ? c->sxw : nullptr, *svw = c->nw_pending > 0 ? c->svw : nullptr;
+    const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(sx, x, bx, kind, c->stream));
+    CK(cudaMemcpyAsync(sv, v, bx, kind, c->stream));
+    CK(cudaMemcpyAsync(sp, p, bp, kind, c->stream));
+    if (vprev) CK(cudaMemcpyAsync(svp, vprev, bx, kind, c->stream));
+    if (c->nw_pending > 0 && !reuse) {
+        CK(cudaMemcpyAsync(sxw, c->xw_host.data(), c->xw_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(svw, c->vw_host.data(), c->vw_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
+    c->launches += launch_scatter_in(c->B, sx, sv, sp, svp, sxw, svw, c->stream);
+    // a new state restarts the step log and clears device-side error flags
+    CK(cudaMemsetAsync(&c->B.ls->step, 0, sizeof(long long), c->stream));
+    CK(cudaMemsetAsync(c->B.err, 0, sizeof(uint32_t), c->stream));
+    CK(cudaGetLastError());
+    if (!device) CK(cudaStreamSynchronize(c->stream));   // host arrays may be reused once we return
+    c->have_particles = true;
+    c->steps = 0;
+    if (c->prm.graph && !c->exec) {
+        r = build_graph(c);
+        if (r) return r;
+    }
+    return DTSPH_OK;
+}
+
+int read_field_impl(dtsph_ctx *c, int32_t field, double *out, bool device)
+{
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
+    if (!out) return fail(c, DTSPH_E_ARG, "out is null");
+    const Buffers &B = c->B;
+    const double *src;
+    int comps = B.dim;
+    switch (field) {
+    case DTSPH_FIELD_POS: src = B.x_a; break;
+    case DTSPH_FIELD_VEL: src = B.vn_a; break;
+    case DTSPH_FIELD_VEL_PREV: src = B.vnm1_a; break;
+    case DTSPH_FIELD_P: src = B.pn_a; comps = 1; break;
+    default: return fail(c, DTSPH_E_ARG, "unknown field %d", field);
+    }
+    const size_t bytes = (size_t)B.nf * comps * sizeof(double);
+    double *dst = out;
+    double *tmp = nullptr;
+    if (!device) {
+        CK(cudaMallocAsync((void **)&tmp, bytes, c->stream));
+        dst = tmp;
+    }
+    c->launches += launch_unpermute(B, B.gid_a, src, dst, comps, c->stream);
+    CK(cudaGetLastError());
+    if (!device) {
+        CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaFreeAsync(tmp, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return DTSPH_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char *dtsph_version(void) { return DTSPH_VERSION; }
+
+const char *dtsph_last_error(const dtsph_ctx *c) { return c ? c->err.c_str() : kNoCtx; }
+
+int dtsph_create(const dtsph_params *params, void *stream, dtsph_ctx **out)
+{
+    if (!params || !out) return DTSPH_E_ARG;
+    *out = nullptr;
+    dtsph_ctx *c = new (std::nothrow) dtsph_ctx();
+    if (!c) return DTSPH_E_OOM;
+    int r = validate(c, params);
+    if (r) {
+        delete c;
+        return r;
+    }
+    c->prm = *params;
+    if ((r = setup_geometry(c)) != DTSPH_OK) {
+        delete c;
+        return r;
+    }
+    setup_phys(c);
+    memset(&c->B, 0, sizeof c->B);
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return DTSPH_E_CUDA;
+    }
+    *out = c;
+    return DTSPH_OK;
+}
+
+void dtsph_destroy(dtsph_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_all(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+int dtsph_set_boundary(dtsph_ctx *c, int64_t nw, const double *x, const double *v_wall)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (nw < 0 || (nw > 0 && !x)) return fail(c, DTSPH_E_ARG, "bad wall arrays");
+    const int d = c->prm.dim;
+    c->nw_pending = nw;
+    c->xw_host.assign(x, x + (size_t)nw * d);
+    if (v_wall) c->vw_host.assign(v_wall, v_wall + (size_t)nw * d);
+    else c->vw_host.assign((size_t)nw * d, 0.0);
+    free_all(c);   // walls change the particle set: particles must be set again
+    return DTSPH_OK;
+}
+
+int dtsph_set_particles(dtsph_ctx *c, int64_t nf, const double *x, const double *v, const double *p,
+                        const double *v_prev)
+{
+    if (!c) return DTSPH_E_ARG;
+    return set_particles_impl(c, nf, x, v, p, v_prev, false);
+}
+
+int dtsph_set_particles_device(dtsph_ctx *c, int64_t nf, const double *x, const double *v, const double *p,
+                               const double *v_prev)
+{
+    if (!c) return DTSPH_E_ARG;
+    return set_particles_impl(c, nf, x, v, p, v_prev, true);
+}
+
+int dtsph_step(dtsph_ctx *c, int32_t nsteps)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "dtsph_step before dtsph_set_particles");
+    if (nsteps < 0) return fail(c, DTSPH_E_ARG, "nsteps must be >= 0");
+    CK(cudaSetDevice(c->device));
+    c->have_nbrs = false;
+    for (int32_t s = 0; s < nsteps; ++s) {
+        if (c->exec) {
+            CK(cudaGraphLaunch(c->exec, c->stream));
+        } else {
+            int r = step_plain(c);
+            if (r) return r;
+        }
+        ++c->steps;
+    }
+    return DTSPH_OK;
+}
+
+int dtsph_sync(dtsph_ctx *c)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
+    CK(cudaStreamSynchronize(c->stream));
+    return device_error(c);
+}
+
+int64_t dtsph_step_count(const dtsph_ctx *c) { return c ? c->steps : -1; }
+
+int dtsph_read_stats(dtsph_ctx *c, int64_t first, int32_t count, dtsph_step_stats *out)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
+    if (count < 0 || (count > 0 && !out) || first < 0 || first + count > c->steps)
+        return fail(c, DTSPH_E_ARG, "steps [%lld, %lld) not taken (taken: %lld)", (long long)first,
+                    (long long)(first + count), (long long)c->steps);
+    if (c->steps - first > kStatRing) return fail(c, DTSPH_E_ARG, "step %lld no longer in the log", (long long)first);
+    std::vector<StatRec> tmp(kStatRing);
+    CK(cudaMemcpyAsync(tmp.data(), c->B.stats, sizeof(StatRec) * kStatRing, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int32_t i = 0; i < count; ++i) {
+        const StatRec &r = tmp[(first + i) % kStatRing];
+        out[i].iters = r.iters;
+        out[i].reason = r.reason;
+        out[i].rp = r.rp;
+        out[i].rv = r.rv;
+    }
+    return DTSPH_OK;
+}
+
+int dtsph_read_field(dtsph_ctx *c, int32_t field, double *out)
+{
+    if (!c) return DTSPH_E_ARG;
+    CK(cudaSetDevice(c->device));
+    return read_field_impl(c, field, out, false);
+}
+
+int dtsph_read_field_device(dtsph_ctx *c, int32_t field, double *out)
+{
+    if (!c) return DTSPH_E_ARG;
+    CK(cudaSetDevice(c->device));
+    return read_field_impl(c, field, out, true);
+}
+
+int dtsph_eval_rates(dtsph_ctx *c, double *ap, double *F)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
+    if (!ap || !F) return fail(c, DTSPH_E_ARG, "ap and F are required");
+    CK(cudaSetDevice(c->device));
+    const Buffers &B = c->B;
+    c->launches += launch_binning(B, c->G, B.x_a, B.gid_a, c->stream);
+    c->launches += launch_permute_a_to_b(B, c->G, c->stream);
+    c->launches += launch_state_n(B, c->G, c->P, false, c->stream);
+    const size_t bf = (size_t)B.nf * B.dim * sizeof(double), bp = (size_t)B.nf * sizeof(double);
+    double *tmp = nullptr;
+    CK(cudaMallocAsync((void **)&tmp, bf + bp, c->stream));
+    c->launches += launch_unpermute(B, B.gid_b, B.ap_b, tmp, 1, c->stream);
+    c->launches += launch_unpermute(B, B.gid_b, B.f_b, tmp + B.nf, B.dim, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ap, tmp, bp, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(F, tmp + B.nf, bf, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaFreeAsync(tmp, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_nbrs = false;
+    return device_error(c);
+}
+
+int dtsph_build_neighbors(dtsph_ctx *c)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
+    CK(cudaSetDevice(c->device));
+    const Buffers &B = c->B;
+    c->launches += launch_binning(B, c->G, B.x_a, B.gid_a, c->stream);
+    c->launches += launch_permute_a_to_b(B, c->G, c->stream);
+    c->launches += launch_pair_cache(B, c->G, c->P, B.x_b, B.cell_b, B.gid_b, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    int r = device_error(c);
+    c->have_nbrs = r == DTSPH_OK;
+    return r;
+}
+
+int dtsph_get_neighbors(dtsph_ctx *c, int64_t i, int64_t *out, int64_t cap, int64_t *count)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (!c->have_nbrs) return fail(c, DTSPH_E_STATE, "call dtsph_build_neighbors first");
+    const Buffers &B = c->B;
+    if (i < 0 || i >= B.n || !count || (cap > 0 && !out)) return fail(c, DTSPH_E_ARG, "bad index or output");
+    std::vector<uint32_t> gid(B.n);
+    CK(cudaMemcpy(gid.data(), B.gid_b, sizeof(uint32_t) * B.n, cudaMemcpyDeviceToHost));
+    int s = -1;
+    for (int q = 0; q < B.n; ++q)
+        if (gid[q] == (uint32_t)i) { s = q; break; }
+    if (s < 0) return fail(c, DTSPH_E_STATE, "particle %lld not found", (long long)i);
+    int cnt = 0;
+    CK(cudaMemcpy(&cnt, B.pcount + s, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> got;
+    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+    for (int k = 0; k < cnt; ++k) {
+        size_t e = base + (size_t)k * kWarp;
+        uint32_t jb;
+        if (B.fp32c && B.dim == 2) {
+            float4 v;
+            CK(cudaMemcpy(&v, B.pc32 + e, sizeof v, cudaMemcpyDeviceToHost));
+            memcpy(&jb, &v.w, sizeof jb);
+        } else {
+            CK(cudaMemcpy(&jb, B.pj + e, sizeof jb, cudaMemcpyDeviceToHost));
+        }
+        got.push_back((int64_t)gid[jb & ~kWallBit]);
+    }
+    std::sort(got.begin(), got.end());
+    *count = (int64_t)got.size();
+    for (int64_t k = 0; k < cap && k < (int64_t)got.size(); ++k) out[k] = got[k];
+    return DTSPH_OK;
+}
+
+int dtsph_probe_iterate(dtsph_ctx *c, int32_t launches, float *ms_per_launch, double *bytes_per_launch,
+                        int64_t *pairs)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (!c->have_particles || c->steps == 0) return fail(c, DTSPH_E_STATE, "take a step before probing");
+    if (launches < 1 || launches > 256 || !ms_per_launch) return fail(c, DTSPH_E_ARG, "launches must be in [1, 256]");
+    CK(cudaSetDevice(c->device));
+    const Buffers &B = c->B;
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<int> cnt(B.n);
+    std::vector<uint32_t> gid(B.n);
+    CK(cudaMemcpy(cnt.data(), B.pcount, sizeof(int) * B.n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(gid.data(), B.gid_a, sizeof(uint32_t) * B.n, cudaMemcpyDeviceToHost));
+    int64_t np = 0;
+    for (int s = 0; s < B.n; ++s)
+        if (gid[s] < (uint32_t)B.nf) np += cnt[s];
+    // per fluid particle: packed (V, p-hat) read and written, V^k (FP64) read and
+    // written, BDF2 source read, neighbour count read; per pair: the cache entry
+    const int d = B.dim;
+    const double packed = B.fp32c ? 16.0 : 32.0;
+    const double per_particle = 2 * packed + 2 * 8.0 * d + 8.0 * d + 4.0;
+    const double per_pair = B.fp32c ? (d == 2 ? 16.0 : 20.0) : 36.0;
+    std::vector<cudaEvent_t> ev(2 * launches);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    for (int i = 0; i < launches; ++i) {
+        launch_loop_reset(B, c->stream);
+        CK(cudaEventRecord(ev[2 * i], c->stream));
+        launch_iterate(B, c->G, c->P, 0ull, 0, c->stream);
+        CK(cudaEventRecord(ev[2 * i + 1], c->stream));
+    }
+    c->launches += 2 * launches;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    double tot = 0;
+    for (int i = 0; i < launches; ++i) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+        tot += ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    *ms_per_launch = (float)(tot / launches);
+    if (bytes_per_launch) *bytes_per_launch = per_particle * B.nf + per_pair * (double)np;
+    if (pairs) *pairs = np;
+    return DTSPH_OK;
+}
+
+int64_t dtsph_kernel_launches(const dtsph_ctx *c_)
+{
+    dtsph_ctx *c = const_cast<dtsph_ctx *>(c_);
+    if (!c) return -1;
+    if (!c->exec || c->steps == 0) return c->launches;
+    // graph steps: fixed kernels per step plus per-iteration kernels from the log
+    int64_t first = std::max<int64_t>(0, c->steps - kStatRing);
+    std::vector<StatRec> tmp(kStatRing);
+    if (cudaMemcpyAsync(tmp.data(), c->B.stats, sizeof(StatRec) * kStatRing, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return -1;
+    int64_t it = 0;
+    for (int64_t s = first; s < c->steps; ++s) it += tmp[s % kStatRing].iters;
+    return c->launches + c->steps * c->per_step_fixed + it * c->per_iter;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/dtsph.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace dtsph {
+
+constexpr int kBlock = 256;          // threads per block of every particle kernel
+constexpr int kWarp = 32;
+constexpr uint32_t kWallBit = 0x80000000u;   // set in a cached neighbour index when j is a wall
+
+// Error bits raised by kernels into Buffers::err (read by dtsph_sync).
+enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u };
+
+// Cell grid and neighbour-test constants of one binning. Cells have side
+// s[a] >= 3h, so every neighbour lies in the 3^dim surrounding cells.
+struct Geom {
+    int dim;
+    int periodic[3];
+    int nc[3];            // cells per axis
+    int ncell;            // nc[0] * nc[1] * nc[2]
+    double lo[3], hi[3];
+    double L[3], halfL[3];
+    double s[3], inv_s[3];
+    float s_f[3];
+    double rc2;           // (3h)^2, the FP64 neighbour test
+    float rc2_lo, rc2_hi; // FP32 pre-test band: below lo is in, above hi is out
+};
+
+// Physical constants of the pair terms, folded for rho_i = rho_j = rho0 and a
+// uniform mass m (Sec. 3: density held fixed).
+struct Phys {
+    double h, m, rho0, c, nu, nu_e, dt, dtau;
+    double sig_h;        // sigma / h: dW/dr = sig_h * dWdq(q)
+    double eta_h2;       // eta h^2 (viscous and artificial-viscosity denominators)
+    double edac_h2;      // eta h^2, or h^2 for the literal reading
+    double c_div;        // m (rho_i / rho_j) c^2                       divergence term
+    double c_edac;       // 4 m nu_e / ((rho_i + rho_j) rho_j)           EDAC term
+    double c_p;          // m / rho0^2                                  pressure term
+    double c_visc;       // 4 m nu / (rho_i + rho_j)                     viscous term
+    double c_av;         // alpha h c / rho0                            artificial viscosity
+    double g[3];
+    double kappa;        // 2 dt / (2 dt + 3 dtau), Eq. (dv_dtau_exact)
+    double c3;           // 3 / (2 dt)
+    double inv_2dt;      // 1 / (2 dt)
+    double rp_scale;     // dt / (rho0 c^2) / nf
+    double rv_scale;     // dt / v_ref / nf
+    int edac, use_av;
+};
+
+// Convergence control of the pseudo-time loop, one per context, in device memory.
+struct LoopState {
+    int iter;              // iterations completed in this real step
+    int done;              // 1 once a stop rule holds
+    int reason;            // stop reason (dtsph_step_stats.reason), -1 while running
+    unsigned int ticket;   // last-block election counter of the iterate kernel
+    double rp, rv;         // residuals of the last iteration
+    double hist_p[16], hist_v[16];   // ring of the last residuals (stagnation test)
+    int max_iter, fixed_iters, stag_window, pad;
+    double eps, stag_tol;
+    long long step;        // real steps completed (indexes the stats ring)
+};
+
+struct StatRec { int iters, reason; double rp, rv; };
+constexpr int kStatRing = 65536;
+
+// Device buffers of one context. Particle arrays hold all n = nf + nw particles
+// in the order of the latest binning ("A" = the loop order kept between steps,
+// "B" = the order of the binning at r^n inside a step). SoA per component.
+struct Buffers {
+    int n, nf, nw, dim, fp32c, K;   // K = neighbour capacity per particle
+    // order A (persistent)
+    uint32_t *gid_a;       // caller index of each slot (walls: nf + wall index)
+    double *x_a;           // r^n           [dim][n]
+    double *xp_a;          // r^0 (frozen)  [dim][n]
+    double *vn_a;          // V^n (walls: prescribed velocity) [dim][n]
+    double *vnm1_a;        // V^{n-1}       [dim][n]
+    double *pn_a;          // p^n           [n]
+    double *s_a;           // BDF2 source (V^{n-1} - 4 V^n) / (2 dt) [dim][n]
+    int *cell_a;           // cell of each slot
+    // order B (scratch inside a step)
+    uint32_t *gid_b;
+    double *x_b, *vn_b, *vnm1_b, *pn_b, *xp_b, *v0_b, *ph0_b, *s_b;
+    int *cell_b;
+    // binning scratch
+    int *key;              // cell of each particle in the pre-binning order
+    int *slot;             // rank inside its cell (atomic order)
+    int *perm;             // new slot -> old slot
+    int *cell_count;       // [ncell], zero between binnings
+    int *cell_start;       // [ncell + 1]
+    // FP32 offsets of each particle from its cell origin (FP32C geometry)
+    float4 *off;           // [n]
+    // pseudo-time iterates, ping-pong on the iteration parity
+    double *vk[2];         // V^k FP64 [dim][n]
+    double4_32a *nb64[2];      // FP64: (V, p-hat) packed for neighbour gathers
+    float4 *nb32[2];       // FP32C: (V, p-hat) packed for neighbour gathers
+    // pair cache, sliced by warp: entry k of slot i at ((i/32) K + k) 32 + i%32
+    uint32_t *pj;          // neighbour slot (| kWallBit for walls)
+    double4_32a *pc64;         // FP64: (gradW, F_ij)
+    float4 *pc32;          // FP32C: (gradW, F_ij); in 2D .w holds the index bits
+    int *pcount;           // neighbours of each slot
+    // state-n rates (test entry and predictor)
+    double *ap_b;          // [n]
+    double *f_b;           // [dim][n]
+    // residual reduction
+    double *blk;           // [2 * nblocks] block partial sums
+    LoopState *ls;
+    StatRec *stats;        // [kStatRing]
+    uint32_t *err;
+};
+
+// ------------------------------------------------------------ launchers
+// Every launcher enqueues on `st` and returns the number of kernels launched.
+
+int launch_binning(const Buffers &B, const Geom &G, const double *x_keys, const uint32_t *gid_src,
+                   cudaStream_t st);
+int launch_permute_a_to_b(const Buffers &B, const Geom &G, cudaStream_t st);
+int launch_permute_b_to_a(const Buffers &B, const Geom &G, cudaStream_t st);
+int launch_state_n(const Buffers &B, const Geom &G, const Phys &P, bool predictor, cudaStream_t st);
+int launch_pair_cache(const Buffers &B, const Geom &G, const Phys &P, const double *xpos, const int *cell,
+                      const uint32_t *gid, cudaStream_t st);
+int launch_walls_iter(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st);
+int launch_iterate(const Buffers &B, const Geom &G, const Phys &P, unsigned long long cond_handle,
+                   int use_cond, cudaStream_t st);
+int launch_outer(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st);
+int launch_loop_reset(const Buffers &B, cudaStream_t st);
+int launch_unpermute(const Buffers &B, const uint32_t *gid, const double *src, double *out, int comps, cudaStream_t st);
+int launch_scatter_in(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,
+                      const double *xw, const double *vw, cudaStream_t st);
+
+int iterate_blocks(const Buffers &B);
+
+}  // namespace dtsph

@@ -1,0 +1,363 @@
+// The pseudo-time loop of Algorithm 2 (particles frozen in pseudo-time) and the
+// end of the real step.
+//
+// One iteration k, for every fluid particle at once (Jacobi: reads only the
+// iterate k buffers, writes the k+1 buffers):
+//   rates at (V^k, p^{k+1/2}) from the pair cache       Eqs. (dp-dtau-frozen-edac,
+//                                                        mom-sph-frozen)
+//   dV/dtau = {F - (3 V^k - 4 V^n + V^{n-1})/(2 dt)} 2 dt / (2 dt + 3 dtau)
+//                                                        Eq. (dv_dtau_exact)
+//   V^{k+1} = V^k + dtau dV/dtau                         Eq. (vkp1_frozen)
+//   p^{k+1} = p^{k+1/2} + dtau/2 dp/dtau                 Eq. (pkp1_frozen)
+//   p^{k+3/2} = p^{k+1} + dtau/2 dp/dtau                 Eq. (pkstar_frozen), the
+//                                                        next half step with the
+//                                                        rate just computed
+// The pressure is carried as p-hat^k = p^{k+1/2}, so p-hat^{k+1} = p-hat^k +
+// dtau dp/dtau and p^{k+1} = (p-hat^k + p-hat^{k+1}) / 2.
+// Residuals of Eq. (conv): R_p = mean|dp/dtau| dt / (rho0 c^2) and
+// R_v = mean|dt dV/dtau| / v_ref over the fluid particles, reduced per block
+// and finished by the last block to arrive, which also applies the stop rules
+// of Sec. 3.4 and sets the condition of the graph's while node.
+#include "pair_terms.cuh"
+
+namespace dtsph {
+
+namespace {
+
+inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
+
+// Stop rules of Sec. 3.4 on the residual history (ring of the last 16).
+__device__ int stop_rule(const LoopState &L, int k1)
+{
+    double rp = L.hist_p[(k1 - 1) & 15], rv = L.hist_v[(k1 - 1) & 15];
+    if (!isfinite(rp) || !isfinite(rv)) return 3;
+    if (L.fixed_iters > 0) return k1 >= L.fixed_iters ? 4 : -1;
+    if (rp < L.eps && rv < L.eps) return 0;
+    int w = L.stag_window;
+    if (w > 0 && k1 >= w) {
+        bool stag = true;
+        for (int which = 0; which < 2 && stag; ++which) {
+            const double *h = which ? L.hist_v : L.hist_p;
+            double lo = h[(k1 - 1) & 15], hi = lo;
+            for (int t = k1 - w; t < k1; ++t) {
+                double v = h[t & 15];
+                lo = fmin(lo, v);
+                hi = fmax(hi, v);
+            }
+            if (!(hi > 0.0 && (hi - lo) / hi < L.stag_tol)) stag = false;
+        }
+        if (stag) return 1;
+    }
+    if (k1 >= L.max_iter) return 2;
+    return -1;
+}
+
+// Wall values for iteration k from the cached fluid neighbours of each wall slot.
+template <int D, bool F32>
+__global__ void __launch_bounds__(kBlock) k_walls_iter(Buffers B)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n || B.gid_a[s] < (uint32_t)B.nf) return;
+    const int cur = B.ls->iter & 1;
+    if (B.ls->done) return;
+    const int cnt = B.pcount[s];
+    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+    double sw = 0, sp = 0, sv[3] = {0, 0, 0};
+    for (int k = 0; k < cnt; ++k) {
+        size_t e = base + (size_t)k * kWarp;
+        double W, Wg;
+        uint32_t jb;
+        if (F32) {
+            float4 c = B.pc32[e];
+            W = c.x;
+            Wg = c.y;
+            jb = D == 2 ? __float_as_uint(c.w) : B.pj[e];
+        } else {
+            double4_32a c = B.pc64[e];
+            W = c.x;
+            Wg = c.y;
+            jb = B.pj[e];
+        }
+        if (jb & kWallBit) continue;
+        int j = (int)jb;
+        double vx, vy, vz, p;
+        if (F32) {
+            float4 q = B.nb32[cur][j];
+            vx = q.x; vy = q.y; vz = q.z; p = q.w;
+        } else {
+            double4_32a q = B.nb64[cur][j];
+            vx = q.x; vy = q.y; vz = q.z; p = q.w;
+        }
+        sw += W;
+        sp += p * W + Wg;
+        sv[0] += vx * W;
+        sv[1] += vy * W;
+        sv[2] += vz * W;
+    }
+    double gv[3];
+    for (int a = 0; a < 3; ++a) {
+        double vw = a < D ? B.vn_a[(size_t)a * B.n + s] : 0.0;
+        gv[a] = 2.0 * vw - (sw > 0 ? sv[a] / sw : 0.0);
+    }
+    double pw = sw > 0 ? sp / sw : 0.0;
+    if (F32) B.nb32[cur][s] = make_float4((float)gv[0], (float)gv[1], (float)gv[2], (float)pw);
+    else B.nb64[cur][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One pseudo-time iteration over all slots (walls only contribute zeros to the
+// residual). The last block to finish reduces the block partials in a fixed
+// order, so the residual does not depend on block scheduling.
+template <int D, bool F32, bool WALLS>
+__global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned long long cond, int use_cond)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
+    __shared__ double red[2][kBlock / kWarp];
+    __shared__ int last;
+    LoopState *ls = B.ls;
+    const int it = ls->iter;
+    if (!use_cond && ls->done) return;          // whole grid agrees: nothing to do
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int n = B.n;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+
+    T r_ap = T(0), r_av = T(0);
+    if (s < n && (!WALLS || B.gid_a[s] < (uint32_t)B.nf)) {
+        const PairConst<T> k = pair_const<T>(P);
+        T vi[3], pi;
+        if (F32) {
+            float4 q = B.nb32[cur][s];
+            vi[0] = q.x; vi[1] = q.y; vi[2] = q.z; pi = q.w;
+        } else {
+            double4_32a q = B.nb64[cur][s];
+            vi[0] = (T)q.x; vi[1] = (T)q.y; vi[2] = (T)q.z; pi = (T)q.w;
+        }
+        Acc ap, Fa[3];
+        const int cnt = B.pcount[s];
+        const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+        for (int kk = 0; kk < cnt; ++kk) {
+            const size_t e = base + (size_t)kk * kWarp;
+            T g[3], F;
+            uint32_t jb;
+            if (F32) {
+                float4 c = B.pc32[e];
+                g[0] = c.x; g[1] = c.y;
+                if (D == 3) { g[2] = c.z; F = c.w; jb = B.pj[e]; }
+                else { F = c.z; jb = __float_as_uint(c.w); }
+            } else {
+                double4_32a c = B.pc64[e];
+                g[0] = (T)c.x; g[1] = (T)c.y; g[2] = (T)c.z; F = (T)c.w;
+                jb = B.pj[e];
+            }
+            const int j = (int)(jb & ~kWallBit);
+            T vj[3], pj;
+            if (F32) {
+                float4 q = B.nb32[cur][j];
+                vj[0] = q.x; vj[1] = q.y; vj[2] = q.z; pj = q.w;
+            } else {
+                double4_32a q = B.nb64[cur][j];
+                vj[0] = (T)q.x; vj[1] = (T)q.y; vj[2] = (T)q.z; pj = (T)q.w;
+            }
+            if (WALLS && (jb & kWallBit)) {
+                T vd[3] = {T(0), T(0), T(0)};
+                for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_a[(size_t)a * n + j];
+                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vj, pj, ap, Fa);
+            } else {
+                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vj, vj, pj, ap, Fa);
+            }
+        }
+        // BDF2 pseudo-acceleration and the update, FP64
+        double av2 = 0.0;
+        double vnew[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) {
+            const size_t q = (size_t)a * n + s;
+            const double vk = B.vk[cur][q];
+            const double Fv = (double)Fa[a].value() + P.g[a];
+            const double av = P.kappa * (Fv - (P.c3 * vk + B.s_a[q]));
+            vnew[a] = vk + P.dtau * av;
+            B.vk[nxt][q] = vnew[a];
+            av2 += av * av;
+        }
+        const double apv = (double)ap.value();
+        const double pnew = (double)pi + P.dtau * apv;
+        if (F32) B.nb32[nxt][s] = make_float4((float)vnew[0], (float)vnew[1], (float)vnew[2], (float)pnew);
+        else B.nb64[nxt][s] = make_double4_32a(vnew[0], vnew[1], vnew[2], pnew);
+        r_ap = (T)fabs(apv);
+        r_av = (T)sqrt(av2);
+    }
+    // residual partial sums: warp in the working precision, then FP64
+    T w_ap = warp_sum<T>(r_ap), w_av = warp_sum<T>(r_av);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = (double)w_ap;
+        red[1][wid] = (double)w_av;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int w = 0; w < kBlock / kWarp; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        B.blk[2 * blockIdx.x] = a;
+        B.blk[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        unsigned int t = atomicAdd(&ls->ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // last block: fixed-order reduction of the block partials, then the stop rules
+    __threadfence();
+    double a = 0, b = 0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+        a += __ldcg(&B.blk[2 * q]);
+        b += __ldcg(&B.blk[2 * q + 1]);
+    }
+    a = warp_sum<double>(a);
+    b = warp_sum<double>(b);
+    __syncthreads();
+    if (lane == 0) {
+        red[0][wid] = a;
+        red[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0, sb = 0;
+        for (int w = 0; w < kBlock / kWarp; ++w) {
+            sa += red[0][w];
+            sb += red[1][w];
+        }
+        const int k1 = it + 1;
+        ls->rp = sa * P.rp_scale;
+        ls->rv = sb * P.rv_scale;
+        ls->hist_p[it & 15] = ls->rp;
+        ls->hist_v[it & 15] = ls->rv;
+        ls->iter = k1;
+        int r = stop_rule(*ls, k1);
+        ls->reason = r;
+        ls->done = r >= 0;
+        ls->ticket = 0;
+        __threadfence();
+        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, r >= 0 ? 0u : 1u);
+    }
+}
+
+// Eq. (r-update): r^{n+1} = r^n + dt/2 (V^n + V^{n+1}) for fluid slots, then
+// V^{n-1} <- V^n, V^n <- V^K, p^n <- p^K = (p-hat^K + p-hat^{K-1}) / 2; thread 0
+// logs the step.
+template <int D, bool F32>
+__global__ void __launch_bounds__(kBlock) k_outer(Buffers B, Geom G, Phys P)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const LoopState *ls = B.ls;
+    const int K = ls->iter;
+    const int fin = K & 1, prev = fin ^ 1;
+    const int n = B.n;
+    if (s == 0) {
+        LoopState *w = B.ls;
+        long long step = w->step;
+        StatRec r;
+        r.iters = K;
+        r.reason = w->reason;
+        r.rp = w->rp;
+        r.rv = w->rv;
+        B.stats[step % kStatRing] = r;
+        w->step = step + 1;
+    }
+    if (s >= n || B.gid_a[s] >= (uint32_t)B.nf) return;
+    for (int a = 0; a < D; ++a) {
+        const size_t q = (size_t)a * n + s;
+        const double vn = B.vn_a[q];
+        const double vK = B.vk[fin][q];
+        double x = B.x_a[q] + 0.5 * P.dt * (vn + vK);
+        if (G.periodic[a]) {
+            if (x >= G.hi[a]) x -= G.L[a];
+            else if (x < G.lo[a]) x += G.L[a];
+        }
+        B.x_a[q] = x;
+        B.vnm1_a[q] = vn;
+        B.vn_a[q] = vK;
+    }
+    double p1, p0;
+    if (F32) {
+        p1 = B.nb32[fin][s].w;
+        p0 = B.nb32[prev][s].w;
+    } else {
+        p1 = B.nb64[fin][s].w;
+        p0 = B.nb64[prev][s].w;
+    }
+    B.pn_a[s] = 0.5 * (p0 + p1);
+}
+
+__global__ void k_loop_reset(LoopState *ls)
+{
+    ls->iter = 0;
+    ls->done = 0;
+    ls->reason = -1;
+    ls->ticket = 0;
+    ls->rp = 0;
+    ls->rv = 0;
+}
+
+}  // namespace
+
+int iterate_blocks(const Buffers &B) { return blocks(B.n); }
+
+int launch_walls_iter(const Buffers &B, const Geom & /*G*/, const Phys & /*P*/, cudaStream_t st)
+{
+    if (B.nw == 0) return 0;
+    if (B.dim == 2) {
+        if (B.fp32c) k_walls_iter<2, true><<<blocks(B.n), kBlock, 0, st>>>(B);
+        else k_walls_iter<2, false><<<blocks(B.n), kBlock, 0, st>>>(B);
+    } else {
+        if (B.fp32c) k_walls_iter<3, true><<<blocks(B.n), kBlock, 0, st>>>(B);
+        else k_walls_iter<3, false><<<blocks(B.n), kBlock, 0, st>>>(B);
+    }
+    return 1;
+}
+
+int launch_iterate(const Buffers &B, const Geom & /*G*/, const Phys &P, unsigned long long cond, int use_cond,
+                   cudaStream_t st)
+{
+    const int nb = blocks(B.n);
+    const bool w = B.nw > 0;
+#define DTSPH_IT(D_, F_, W_) k_iterate<D_, F_, W_><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond)
+    if (B.dim == 2) {
+        if (B.fp32c) { if (w) DTSPH_IT(2, true, true); else DTSPH_IT(2, true, false); }
+        else { if (w) DTSPH_IT(2, false, true); else DTSPH_IT(2, false, false); }
+    } else {
+        if (B.fp32c) { if (w) DTSPH_IT(3, true, true); else DTSPH_IT(3, true, false); }
+        else { if (w) DTSPH_IT(3, false, true); else DTSPH_IT(3, false, false); }
+    }
+#undef DTSPH_IT
+    return 1;
+}
+
+int launch_outer(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st)
+{
+    if (B.dim == 2) {
+        if (B.fp32c) k_outer<2, true><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
+        else k_outer<2, false><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
+    } else {
+        if (B.fp32c) k_outer<3, true><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
+        else k_outer<3, false><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
+    }
+    return 1;
+}
+
+int launch_loop_reset(const Buffers &B, cudaStream_t st)
+{
+    k_loop_reset<<<1, 1, 0, st>>>(B.ls);
+    return 1;
+}
+
+}  // namespace dtsph

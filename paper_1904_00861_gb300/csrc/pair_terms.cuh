@@ -1,0 +1,132 @@
+// Device functions of the pair summations, shared by the state-n pass (geometry
+// computed on the fly) and the pseudo-time iteration (geometry from the pair
+// cache).
+//
+// For a fluid particle i and a neighbour j, with gradW = dW/dr r_ij / r and
+// F_ij = (r_ij . gradW) / (r^2 + eta h^2), the frozen EDAC rates of the paper
+// (Eqs. dp-dtau-frozen-edac and mom-sph-frozen, rho_i = rho_j = rho0) are
+//   dp_i/dtau += c_div (V_ij . gradW) + c_edac (p_i - p_j) F_ij
+//   F_i       += -c_p (p_i + p_j) gradW - m Pi_ij gradW + c_visc F_ij V_ij
+// where a wall neighbour j contributes its prescribed velocity to V_ij in the
+// divergence term and its ghost velocity in the viscous and artificial-viscosity
+// terms (Adami et al., cited in Sec. 3.2).
+#pragma once
+
+#include "dtsph_internal.cuh"
+
+namespace dtsph {
+
+// Quintic spline, dW/dq up to the factor sigma: -5(3-q)^4 + 30(2-q)^4 - 75(1-q)^4
+// with each term present only inside its support.
+template <typename T>
+__device__ __forceinline__ T quintic_dwdq(T q)
+{
+    T a = T(3) - q;
+    T a2 = a * a;
+    T s = T(-5) * a2 * a2;
+    if (q < T(2)) {
+        T b = T(2) - q;
+        T b2 = b * b;
+        s += T(30) * b2 * b2;
+    }
+    if (q < T(1)) {
+        T c = T(1) - q;
+        T c2 = c * c;
+        s -= T(75) * c2 * c2;
+    }
+    return s;
+}
+
+// W(q) up to sigma: (3-q)^5 - 6(2-q)^5 + 15(1-q)^5 within the supports.
+template <typename T>
+__device__ __forceinline__ T quintic_w(T q)
+{
+    T a = T(3) - q;
+    T a2 = a * a;
+    T s = a2 * a2 * a;
+    if (q < T(2)) {
+        T b = T(2) - q;
+        T b2 = b * b;
+        s -= T(6) * b2 * b2 * b;
+    }
+    if (q < T(1)) {
+        T c = T(1) - q;
+        T c2 = c * c;
+        s += T(15) * c2 * c2 * c;
+    }
+    return s;
+}
+
+// Kahan-compensated accumulator (FP32C path).
+struct Kahan {
+    float s, c;
+    __device__ __forceinline__ Kahan() : s(0.f), c(0.f) {}
+    __device__ __forceinline__ void add(float v)
+    {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s; }
+};
+
+struct Plain64 {
+    double s;
+    __device__ __forceinline__ Plain64() : s(0.0) {}
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <typename T>
+struct PairConst {
+    T c_div, c_edac, c_p, c_visc, c_av_m;   // c_av_m = m * alpha h c / rho0
+    int edac, use_av;
+};
+
+template <typename T>
+__device__ __forceinline__ PairConst<T> pair_const(const Phys &P)
+{
+    PairConst<T> k;
+    k.c_div = (T)P.c_div;
+    k.c_edac = (T)P.c_edac;
+    k.c_p = (T)P.c_p;
+    k.c_visc = (T)P.c_visc;
+    k.c_av_m = (T)(P.m * P.c_av);
+    k.edac = P.edac;
+    k.use_av = P.use_av;
+    return k;
+}
+
+// One pair's contribution. g: gradW_ij (D comps), F: F_ij. vi, pi: own velocity
+// and pressure; vj_div, vj_vis: neighbour velocity seen by the divergence and by
+// the viscous term (equal for fluid neighbours); pj: neighbour pressure.
+template <int D, typename T, typename Acc>
+__device__ __forceinline__ void pair_accumulate(const PairConst<T> &k, const T *g, T F, const T *vi, T pi,
+                                                const T *vj_div, const T *vj_vis, T pj, Acc &ap, Acc *Fi)
+{
+    T vdg = T(0), vvg = T(0);
+    T vv[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        vdg += (vi[a] - vj_div[a]) * g[a];
+        vv[a] = vi[a] - vj_vis[a];
+        vvg += vv[a] * g[a];
+    }
+    T t_ap = k.c_div * vdg;
+    if (k.edac) t_ap += k.c_edac * (pi - pj) * F;
+    ap.add(t_ap);
+    T pres = k.c_p * (pi + pj);
+    if (k.use_av && vvg > T(0)) {
+        // v_ij . r_ij < 0  <=>  v_ij . gradW > 0 (dW/dr < 0); phi_ij = (v_ij . gradW) F / |gradW|^2
+        T g2 = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) g2 += g[a] * g[a];
+        if (g2 > T(0)) pres -= k.c_av_m * vvg * F / g2;   // -m Pi_ij with Pi_ij = -alpha h c phi / rho
+    }
+    T cv = k.c_visc * F;
+#pragma unroll
+    for (int a = 0; a < D; ++a) Fi[a].add(-pres * g[a] + cv * vv[a]);
+}
+
+}  // namespace dtsph

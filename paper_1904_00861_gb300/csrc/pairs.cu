@@ -1,0 +1,335 @@
+// Neighbour traversal kernels: the wall extrapolation and the pair pass at the
+// state n (geometry computed on the fly), and the pair-coefficient cache that the
+// pseudo-time loop reads (geometry frozen for the whole loop, Sec. 2.2; caching
+// kernel gradients across pseudo-iterations is the speed-up the paper points at
+// in Sec. 5 but did not implement).
+//
+// Neighbour test: j != i and |r_ij|^2 < (3h)^2 in IEEE double, squares summed in
+// axis order without FMA, minimum image on periodic axes. The FP32C path first
+// tests an FP32 separation built from per-cell FP32 offsets and falls back to the
+// FP64 test only inside a thin band around 3h, so both paths give the same sets.
+#include "pair_terms.cuh"
+
+namespace dtsph {
+
+namespace {
+
+inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
+
+// Calls body(neighbour cell, dx, dy, dz) for the 3^D cells around `cell`; the
+// shifts are the unwrapped cell offsets (so r_ij = off_i - off_j - shift * s).
+template <int D, class Body>
+__device__ __forceinline__ void visit_cells(const Geom &G, int cell, Body &&body)
+{
+    const int c0 = cell % G.nc[0];
+    const int c1 = (cell / G.nc[0]) % G.nc[1];
+    const int c2 = cell / (G.nc[0] * G.nc[1]);
+    const int zlo = D == 3 ? -1 : 0, zhi = D == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        int z = c2 + dz;
+        if (D == 3 && (z < 0 || z >= G.nc[2])) {
+            if (!G.periodic[2]) continue;
+            z = z < 0 ? z + G.nc[2] : z - G.nc[2];
+        }
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = c1 + dy;
+            if (y < 0 || y >= G.nc[1]) {
+                if (!G.periodic[1]) continue;
+                y = y < 0 ? y + G.nc[1] : y - G.nc[1];
+            }
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = c0 + dx;
+                if (x < 0 || x >= G.nc[0]) {
+                    if (!G.periodic[0]) continue;
+                    x = x < 0 ? x + G.nc[0] : x - G.nc[0];
+                }
+                body((z * G.nc[1] + y) * G.nc[0] + x, dx, dy, dz);
+            }
+        }
+    }
+}
+
+// r_ij in FP64 with the minimum image; returns |r_ij|^2 (no FMA contraction).
+template <int D>
+__device__ __forceinline__ double sep64(const Geom &G, const double *__restrict__ x, int n, int i, int j, double *d)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        double v = __dsub_rn(x[(size_t)a * n + i], x[(size_t)a * n + j]);
+        if (G.periodic[a]) {
+            if (v > G.halfL[a]) v = __dsub_rn(v, G.L[a]);
+            else if (v < -G.halfL[a]) v = __dadd_rn(v, G.L[a]);
+        }
+        d[a] = v;
+    }
+    double r2 = __dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1]));
+    if (D == 3) r2 = __dadd_rn(r2, __dmul_rn(d[2], d[2]));
+    return r2;
+}
+
+// Neighbour test plus the separation in the working precision T.
+// Returns true when j is a neighbour of i; d and r2 hold r_ij and |r_ij|^2.
+template <int D, bool F32, typename T>
+__device__ __forceinline__ bool neighbour(const Geom &G, const double *__restrict__ x, const float4 *__restrict__ off,
+                                          int n, int i, int j, float4 oi, int dx, int dy, int dz, T *d, T &r2)
+{
+    if (F32) {
+        float4 oj = off[j];
+        float f0 = oi.x - oj.x - (float)dx * G.s_f[0];
+        float f1 = oi.y - oj.y - (float)dy * G.s_f[1];
+        float f2 = D == 3 ? oi.z - oj.z - (float)dz * G.s_f[2] : 0.f;
+        float q2 = f0 * f0 + f1 * f1;
+        if (D == 3) q2 += f2 * f2;
+        if (q2 >= G.rc2_hi) return false;
+        if (q2 >= G.rc2_lo) {
+            double e[3];
+            if (!(sep64<D>(G, x, n, i, j, e) < G.rc2)) return false;
+        }
+        d[0] = (T)f0;
+        d[1] = (T)f1;
+        if (D == 3) d[2] = (T)f2;
+        r2 = (T)q2;
+        return true;
+    } else {
+        double e[3];
+        double q2 = sep64<D>(G, x, n, i, j, e);
+        if (!(q2 < G.rc2)) return false;
+#pragma unroll
+        for (int a = 0; a < D; ++a) d[a] = (T)e[a];
+        r2 = (T)q2;
+        return true;
+    }
+}
+
+// gradW_ij and F_ij = (r_ij . gradW_ij) / (r^2 + eta h^2) from r_ij.
+template <int D, typename T>
+__device__ __forceinline__ void grad_coef(const Phys &P, const T *d, T r2, T *g, T &F)
+{
+    if (r2 > T(0)) {
+        T r = sqrt(r2);
+        T dwdr = (T)P.sig_h * quintic_dwdq<T>(r / (T)P.h);
+        T a = dwdr / r;
+#pragma unroll
+        for (int k = 0; k < D; ++k) g[k] = a * d[k];
+        F = dwdr * r / (r2 + (T)P.eta_h2);
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) g[k] = T(0);
+        F = T(0);
+    }
+}
+
+template <typename T> struct Packed;
+template <> struct Packed<double> { using type = double4_32a; };
+template <> struct Packed<float> { using type = float4; };
+
+template <typename T>
+__device__ __forceinline__ const typename Packed<T>::type *nb_ptr(const Buffers &B, int buf);
+template <>
+__device__ __forceinline__ const double4_32a *nb_ptr<double>(const Buffers &B, int buf) { return B.nb64[buf]; }
+template <>
+__device__ __forceinline__ const float4 *nb_ptr<float>(const Buffers &B, int buf) { return B.nb32[buf]; }
+
+// ---------------------------------------------------------------- walls, state n
+
+// Adami et al. wall values at state n in order B: p_w = (sum_f p_f W + rho0 g .
+// sum_f r_wf W) / sum_f W, ghost velocity 2 v_w - sum_f V_f W / sum_f W; written
+// into the packed (V, p) of the wall slot.
+template <int D, bool F32>
+__global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B, Geom G, Phys P)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n || B.gid_b[s] < (uint32_t)B.nf) return;
+    const auto *nb = nb_ptr<T>(B, 1);
+    float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    double sw = 0, sp = 0, sg = 0, sv[3] = {0, 0, 0};
+    double sigma = P.sig_h * P.h;
+    visit_cells<D>(G, B.cell_b[s], [&](int c, int dx, int dy, int dz) {
+        for (int j = B.cell_start[c]; j < B.cell_start[c + 1]; ++j) {
+            if (j == s || B.gid_b[j] >= (uint32_t)B.nf) continue;
+            T d[3], r2;
+            if (!neighbour<D, F32, T>(G, B.x_b, B.off, B.n, s, j, oi, dx, dy, dz, d, r2)) continue;
+            double W = sigma * (double)quintic_w<T>(sqrt(r2) / (T)P.h);
+            auto q = nb[j];
+            double gr = 0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) gr += P.g[a] * (double)d[a];
+            sw += W;
+            sp += (double)q.w * W;
+            sg += P.rho0 * gr * W;
+            sv[0] += (double)q.x * W;
+            sv[1] += (double)q.y * W;
+            if (D == 3) sv[2] += (double)q.z * W;
+        }
+    });
+    double vw[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) vw[a] = B.vn_b[(size_t)a * B.n + s];
+    double pw = sw > 0 ? (sp + sg) / sw : 0.0;
+    double gv[3];
+    for (int a = 0; a < 3; ++a) gv[a] = 2.0 * vw[a] - (sw > 0 ? sv[a] / sw : 0.0);
+    if (F32) B.nb32[1][s] = make_float4((float)gv[0], (float)gv[1], (float)gv[2], (float)pw);
+    else B.nb64[1][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
+}
+
+// ------------------------------------------------------------------ state n pass
+
+// Rates at (r^n, V^n, p^n) in order B. With PRED, also the predictor of Eqs.
+// (v0, r0): V^0 = V^n + dt F^n, r^0 = r^n + dt V^n + dt^2/2 F^n; the first
+// pressure half step p-hat^0 = p^n + dtau/2 dp^n/dtau (Eq. pkstar_frozen with the
+// state-n rate); and the BDF2 source (V^{n-1} - 4 V^n) / (2 dt) of Eq.
+// (dv_dtau_exact), all in FP64.
+template <int D, bool F32, bool PRED>
+__global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n) return;
+    const int n = B.n;
+    if (B.gid_b[s] >= (uint32_t)B.nf) {
+        if (PRED) {
+            for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s] = B.x_b[(size_t)a * n + s];
+        }
+        return;
+    }
+    const auto *nb = nb_ptr<T>(B, 1);
+    const PairConst<T> k = pair_const<T>(P);
+    auto qi = nb[s];
+    T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
+    T pi = (T)qi.w;
+    float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    Acc ap, Fa[3];
+    visit_cells<D>(G, B.cell_b[s], [&](int c, int dx, int dy, int dz) {
+        for (int j = B.cell_start[c]; j < B.cell_start[c + 1]; ++j) {
+            if (j == s) continue;
+            T d[3], r2;
+            if (!neighbour<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2)) continue;
+            T g[3], F;
+            grad_coef<D, T>(P, d, r2, g, F);
+            auto qj = nb[j];
+            T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
+            T vd[3] = {vv[0], vv[1], vv[2]};
+            if (B.gid_b[j] >= (uint32_t)B.nf) {
+                for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
+            }
+            pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
+        }
+    });
+    double apv = (double)ap.value();
+    double Fv[3];
+    for (int a = 0; a < D; ++a) Fv[a] = (double)Fa[a].value() + P.g[a];
+    B.ap_b[s] = apv;
+    for (int a = 0; a < D; ++a) B.f_b[(size_t)a * n + s] = Fv[a];
+    if (PRED) {
+        for (int a = 0; a < D; ++a) {
+            size_t q = (size_t)a * n + s;
+            double V = B.vn_b[q];
+            double xp = B.x_b[q] + P.dt * V + 0.5 * P.dt * P.dt * Fv[a];
+            if (G.periodic[a]) {
+                if (xp >= G.hi[a]) xp -= G.L[a];
+                else if (xp < G.lo[a]) xp += G.L[a];
+            }
+            B.xp_b[q] = xp;
+            B.v0_b[q] = V + P.dt * Fv[a];
+            B.s_b[q] = (B.vnm1_b[q] - 4.0 * V) * P.inv_2dt;
+        }
+        B.ph0_b[s] = B.pn_b[s] + 0.5 * P.dtau * apv;
+    }
+}
+
+// --------------------------------------------------------------- pair cache
+
+// For every slot (order of the latest binning) the list of its neighbours with
+// gradW_ij and F_ij (fluid slot), or W_wf and rho0 (g . r_wf) W_wf (wall slot),
+// sliced by warp so that entry k of the 32 lanes of a warp is contiguous.
+template <int D, bool F32>
+__global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, Geom G, Phys P, const double *__restrict__ xpos,
+                                                       const int *__restrict__ cell, const uint32_t *__restrict__ gid)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n) return;
+    const int n = B.n, K = B.K;
+    const bool wall_s = gid[s] >= (uint32_t)B.nf;
+    const size_t base = (size_t)(s >> 5) * K * kWarp + (s & 31);
+    float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    int cnt = 0;
+    const T sigma = (T)(P.sig_h * P.h);
+    visit_cells<D>(G, cell[s], [&](int c, int dx, int dy, int dz) {
+        for (int j = B.cell_start[c]; j < B.cell_start[c + 1]; ++j) {
+            if (j == s) continue;
+            T d[3], r2;
+            if (!neighbour<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2)) continue;
+            if (cnt < K) {
+                T c4[4] = {T(0), T(0), T(0), T(0)};
+                if (wall_s) {
+                    T W = sigma * quintic_w<T>(sqrt(r2) / (T)P.h);
+                    T gr = T(0);
+                    for (int a = 0; a < D; ++a) gr += (T)P.g[a] * d[a];
+                    c4[0] = W;
+                    c4[1] = (T)P.rho0 * gr * W;
+                } else {
+                    T g[3], F;
+                    grad_coef<D, T>(P, d, r2, g, F);
+                    c4[0] = g[0];
+                    c4[1] = g[1];
+                    if (D == 3) {
+                        c4[2] = g[2];
+                        c4[3] = F;
+                    } else {
+                        c4[2] = F;
+                    }
+                }
+                uint32_t jb = (uint32_t)j | (gid[j] >= (uint32_t)B.nf ? kWallBit : 0u);
+                size_t e = base + (size_t)cnt * kWarp;
+                if (F32) {
+                    float4 v = make_float4((float)c4[0], (float)c4[1], (float)c4[2], (float)c4[3]);
+                    if (D == 2) v.w = __uint_as_float(jb);
+                    else B.pj[e] = jb;
+                    B.pc32[e] = v;
+                } else {
+                    B.pc64[e] = make_double4_32a((double)c4[0], (double)c4[1], (double)c4[2], (double)c4[3]);
+                    B.pj[e] = jb;
+                }
+            }
+            ++cnt;
+        }
+    });
+    if (cnt > K) {
+        atomicOr(B.err, kErrCapacity);
+        cnt = K;
+    }
+    B.pcount[s] = cnt;
+}
+
+}  // namespace
+
+#define DTSPH_DISPATCH(D_, F32_, ...)                                                  \
+    do {                                                                               \
+        if ((D_) == 2 && !(F32_)) { constexpr int D = 2; constexpr bool F32 = false; __VA_ARGS__; } \
+        else if ((D_) == 2) { constexpr int D = 2; constexpr bool F32 = true; __VA_ARGS__; }        \
+        else if (!(F32_)) { constexpr int D = 3; constexpr bool F32 = false; __VA_ARGS__; }         \
+        else { constexpr int D = 3; constexpr bool F32 = true; __VA_ARGS__; }                       \
+    } while (0)
+
+int launch_state_n(const Buffers &B, const Geom &G, const Phys &P, bool predictor, cudaStream_t st)
+{
+    int k = 0;
+    if (B.nw > 0) {
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32><<<blocks(B.n), kBlock, 0, st>>>(B, G, P)));
+        ++k;
+    }
+    if (predictor) DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true><<<blocks(B.n), kBlock, 0, st>>>(B, G, P)));
+    else DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false><<<blocks(B.n), kBlock, 0, st>>>(B, G, P)));
+    return k + 1;
+}
+
+int launch_pair_cache(const Buffers &B, const Geom &G, const Phys &P, const double *xpos, const int *cell,
+                      const uint32_t *gid, cudaStream_t st)
+{
+    DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32><<<blocks(B.n), kBlock, 0, st>>>(B, G, P, xpos, cell, gid)));
+    return 1;
+}
+
+}  // namespace dtsph

@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars: neighbour sets bit-exact; FP64 rates and steps within 1e-10 normwise
+relative (max_i |x_i - y_i| / max_i |y_i|); FP32C velocities within 1e-4 L-inf
+relative (the reduced-precision bar), with the error printed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1904_00861_gb300 as dt
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1904_00861_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def wrap_diff(a, b, box):
+    d = np.asarray(a) - np.asarray(b)
+    if box is not None:
+        d -= box * np.round(d / box)
+    return d
+
+
+def make_sim(d, precision=dt.DTSPH_FP64, graph=1, **over):
+    sim = dt.Simulation(d["cfg"], precision=precision, graph=graph, **over)
+    nf = d["nf"]
+    walls = None if d["vw"] is None else (d["x"][nf:], d["vw"])
+    sim.set_state(d["x"][:nf], d["v"], d["p"], d["v_prev"], walls=walls)
+    return sim
+
+
+def make_oracle(d, **over):
+    return oracle.State(d["cfg"], d["x"], d["v"], d["p"], d["v_prev"], vw=d["vw"], nf=d["nf"], **over)
+
+
+def box_of(d):
+    cfg = d["cfg"]
+    dim = cfg["dim"]
+    if all(cfg["periodic"][:dim]):
+        return np.array(cfg["hi"][:dim]) - np.array(cfg["lo"][:dim])
+    return None
+
+
+# ------------------------------------------------------------- neighbours
+
+CASES = {
+    "tgv2d_jitter": lambda: synth.tgv2d(50, seed=1904),
+    "tgv2d_lattice": lambda: synth.tgv2d(37, jitter=0.0),          # exact 3h ties, ragged n
+    "cavity": lambda: synth.cavity2d(23),
+    "tgv3d": lambda: synth.tgv3d(12, jitter=0.1, seed=5),
+}
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_neighbour_sets_bit_exact(case, prec):
+    d = CASES[case]()
+    sim = make_sim(d, precision=prec)
+    dt.dtsph_build_neighbors(sim.ctx)
+    start, idx = oracle.neighbors(d["cfg"], d["x"])
+    n = len(d["x"])
+    for i in range(n):
+        got = dt.dtsph_get_neighbors(sim.ctx, i)
+        assert np.array_equal(got, idx[start[i]:start[i + 1]]), (case, i)
+    sim.close()
+
+
+# ------------------------------------------------------------------ rates
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_rates_fp64(case):
+    d = CASES[case]()
+    rng = np.random.default_rng(0)
+    v = d["v"] + 0.1 * rng.normal(size=d["v"].shape)
+    p = d["p"] + 0.1 * rng.normal(size=d["p"].shape)
+    d = dict(d, v=v, p=p)
+    sim = make_sim(d)
+    ap, F = sim.rates()
+    ap0, F0, _, _ = oracle.rates(d["cfg"], d["x"], v, p, vw=d["vw"], nf=d["nf"])
+    assert rel(ap, ap0) < 1e-12
+    assert rel(F, F0) < 1e-12
+    sim.close()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_rates_fp32c(case):
+    d = CASES[case]()
+    sim = make_sim(d, precision=dt.DTSPH_FP32C)
+    ap, F = sim.rates()
+    ap0, F0, _, _ = oracle.rates(d["cfg"], d["x"], d["v"], d["p"], vw=d["vw"], nf=d["nf"])
+    e_ap, e_F = rel(ap, ap0), rel(F, F0)
+    print(f"{case}: FP32C rates L-inf rel err ap {e_ap:.2e} F {e_F:.2e}")
+    assert e_ap < 1e-4 and e_F < 1e-4
+    sim.close()
+
+
+# ------------------------------------------------------------------ steps
+
+def run_pair(d, nsteps, precision=dt.DTSPH_FP64, graph=1, **over):
+    sim = make_sim(d, precision=precision, graph=graph, **over)
+    orc = make_oracle(d, **over)
+    out = []
+    for _ in range(nsteps):
+        sim.step(1)
+        rec = orc.step(1)[0]
+        sim.sync()
+        st = sim.stats(dt.dtsph_step_count(sim.ctx) - 1, 1)[0]
+        out.append((st, rec, sim.x, sim.v, sim.p))
+    return sim, orc, out
+
+
+@pytest.mark.parametrize("case,nsteps", [("tgv2d_jitter", 10), ("cavity", 6), ("tgv3d", 3)])
+def test_steps_fp64_match_oracle(case, nsteps):
+    """Every real step: same iteration count and stop reason, and r, V, p within
+    1e-10 normwise relative of the oracle."""
+    d = CASES[case]()
+    box = box_of(d)
+    sim, orc, out = run_pair(d, nsteps)
+    for k, (st, rec, x, v, p) in enumerate(out):
+        assert (st["iters"], st["reason"]) == (rec["iters"], rec["reason"]), (k, st, rec)
+        assert abs(st["rp"] - rec["rp"]) <= 1e-10 * rec["rp"] and abs(st["rv"] - rec["rv"]) <= 1e-10 * rec["rv"]
+    st, rec, x, v, p = out[-1]
+    assert np.max(np.abs(wrap_diff(x, orc.x[:d["nf"]], box))) < 1e-10 * np.max(np.abs(orc.x))
+    assert rel(v, orc.v) < 1e-10
+    assert rel(p, orc.p) < 1e-10
+    assert rel(sim.v_prev, orc.v_prev) < 1e-10
+    sim.close()
+
+
+def test_graph_and_plain_launches_are_bit_identical():
+    d = CASES["tgv2d_jitter"]()
+    a = make_sim(d, graph=1)
+    b = make_sim(d, graph=0)
+    a.step(4)
+    b.step(4)
+    assert np.array_equal(a.v, b.v) and np.array_equal(a.p, b.p) and np.array_equal(a.x, b.x)
+    assert a.stats() == b.stats()
+    a.close()
+    b.close()
+
+
+def test_fixed_iteration_mode_matches_oracle():
+    d = CASES["tgv2d_jitter"]()
+    sim, orc, out = run_pair(d, 3, fixed_iters=5)
+    for st, rec, *_ in out:
+        assert st["iters"] == rec["iters"] == 5 and st["reason"] == rec["reason"] == 4
+    assert rel(out[-1][3], orc.v) < 1e-10
+    sim.close()
+
+
+@pytest.mark.parametrize("case,nsteps", [("tgv2d_jitter", 10), ("cavity", 6), ("tgv3d", 3)])
+def test_steps_fp32c_linf(case, nsteps):
+    """FP32-compensated path: L-inf relative velocity error against the FP64
+    oracle after the run (the bar is 1e-4); iteration counts reported."""
+    d = CASES[case]()
+    sim, orc, out = run_pair(d, nsteps, precision=dt.DTSPH_FP32C)
+    its = [(st["iters"], rec["iters"]) for st, rec, *_ in out]
+    err = rel(out[-1][3], orc.v)
+    perr = rel(out[-1][4], orc.p)
+    print(f"{case}: FP32C L-inf rel velocity err {err:.2e}, pressure {perr:.2e}, iters (gpu, oracle) {its}")
+    assert err < 1e-4
+    sim.close()
+
+
+def test_full_size_taylor_green_200sq():
+    """The 200^2 Taylor-Green workload in the benchmark's launch configuration
+    (graph-captured loop): FP64 against the oracle at 1e-10 and FP32C at 1e-4,
+    over 3 real steps."""
+    d = synth.tgv2d(200)
+    sim, orc, out = run_pair(d, 3)
+    for st, rec, *_ in out:
+        assert st["iters"] == rec["iters"]
+    assert rel(out[-1][3], orc.v) < 1e-10 and rel(out[-1][4], orc.p) < 1e-10
+    sim.close()
+    sim32 = make_sim(d, precision=dt.DTSPH_FP32C)
+    sim32.step(3)
+    err = rel(sim32.v, orc.v)
+    print(f"200^2 FP32C L-inf rel velocity err after 3 steps: {err:.2e}")
+    assert err < 1e-4
+    sim32.close()
+
+
+# -------------------------------------------------------------- invariants
+
+def test_uniform_flow_exact_on_gpu():
+    d = synth.tgv2d(33, jitter=0.1, seed=9)
+    v = np.tile([0.5, -0.25], (d["nf"], 1))
+    d = dict(d, v=v, p=np.zeros(d["nf"]), v_prev=v)
+    for prec in (dt.DTSPH_FP64, dt.DTSPH_FP32C):
+        sim = make_sim(d, precision=prec)
+        sim.step(3)
+        assert np.array_equal(sim.v, v) and np.array_equal(sim.p, np.zeros(d["nf"]))
+        assert all(s["iters"] == 1 and s["reason"] == 0 for s in sim.stats())
+        sim.close()
+
+
+def test_momentum_conserved_fp64():
+    d = synth.tgv2d(40, seed=3)
+    rng = np.random.default_rng(4)
+    v = d["v"] + 0.05 * rng.normal(size=d["v"].shape)
+    d = dict(d, v=v, v_prev=v)
+    sim = make_sim(d)
+    P0 = v.sum(0)
+    sim.step(5)
+    assert np.max(np.abs(sim.v.sum(0) - P0)) < 1e-12 * np.abs(v).sum()
+    sim.close()
+
+
+def test_deterministic_and_resume_bit_identical():
+    d = CASES["tgv2d_jitter"]()
+    a = make_sim(d)
+    a.step(4)
+    b = make_sim(d)
+    b.step(2)
+    b.sync()
+    x, v, p, vp = b.x, b.v, b.p, b.v_prev
+    c = make_sim(dict(d, x=x, v=v, p=p, v_prev=vp))
+    c.step(2)
+    assert np.array_equal(a.v, c.v) and np.array_equal(a.p, c.p) and np.array_equal(a.x, c.x)
+    a2 = make_sim(d)
+    a2.step(4)
+    assert np.array_equal(a.v, a2.v)
+    for s in (a, b, c, a2):
+        s.close()
+
+
+# -------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("n", [9, 11, 33])
+def test_small_and_ragged_sizes(n):
+    """Particle counts that leave partial warps and blocks (9^2 particles is
+    the smallest periodic box with three cells of side >= 3h per axis)."""
+    d = synth.tgv2d(n, seed=n)
+    sim, orc, out = run_pair(d, 2)
+    assert rel(out[-1][3], orc.v) < 1e-10
+    sim.close()
+
+
+def test_capacity_overflow_reported():
+    d = synth.tgv2d(30)
+    sim = make_sim(d, max_neighbors=8)
+    sim.step(1)
+    with pytest.raises(dt.DtsphError) as e:
+        sim.sync()
+    assert e.value.code == -5
+    sim.close()
+
+
+def test_domain_error_reported():
+    d = synth.cavity2d(12)
+    nf = d["nf"]
+    x = d["x"].copy()
+    x[0] = [-1.0, 0.5]            # outside the closed box
+    sim = dt.Simulation(d["cfg"])
+    sim.set_state(x[:nf], d["v"], d["p"], walls=(x[nf:], d["vw"]))
+    sim.step(1)
+    with pytest.raises(dt.DtsphError) as e:
+        sim.sync()
+    assert e.value.code == -6
+    sim.close()
+
+
+def test_call_order_and_argument_errors():
+    d = synth.tgv2d(12)
+    sim = dt.Simulation(d["cfg"])
+    with pytest.raises(dt.DtsphError) as e:
+        sim.step(1)
+    assert e.value.code == -2
+    with pytest.raises(dt.DtsphError):
+        dt.dtsph_read_field(sim.ctx, 7, 1, 1)
+    sim.set_state(d["x"], d["v"], d["p"])
+    with pytest.raises(dt.DtsphError):
+        dt.dtsph_read_stats(sim.ctx, 0, 1)      # no step taken yet
+    sim.close()
