@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--n-side", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--graph", type=int, default=1, help="0: plain kernel launches instead of the step graph "
+                    "(used for per-kernel profiling)")
     return ap.parse_args()
 
 
@@ -115,11 +117,11 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- our arm
 
-def run_gpu_path(dt, torch, d, precision, steps, warmup, flush):
+def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=1):
     """Times `steps` real steps after `warmup`; L2 flushed before each step.
     Returns (particle-iterations/s, ms per step, iterations, launches, sim)."""
     stream = torch.cuda.Stream()
-    sim = dt.Simulation(d["cfg"], precision=precision, stream=stream)
+    sim = dt.Simulation(d["cfg"], precision=precision, stream=stream, graph=graph)
     sim.set_state(d["x"], d["v"], d["p"], d["v_prev"])
     sim.step(warmup)
     sim.sync()
@@ -205,7 +207,7 @@ def main_ours(args):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         rate32, ms32, it32, launches, sim32 = run_gpu_path(dt, torch, d, dt.DTSPH_FP32C, args.steps, args.warmup,
-                                                           flush)
+                                                           flush, args.graph)
     torch.cuda.synchronize()
     # whole-job throughput: every rank ran the same workload independently
     t_rank = ms32 * args.steps
@@ -216,9 +218,11 @@ def main_ours(args):
     else:
         t_max = t_rank
     value = world * sim32.nf * sum(it32) / (t_max * 1e-3)
-    rate64, ms64, it64, _, sim64 = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup, flush)
+    rate64, ms64, it64, _, sim64 = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup, flush,
+                                                args.graph)
     v32, v64 = sim32.v, sim64.v
     linf = float(np.max(np.abs(v32 - v64)) / np.max(np.abs(v64)))
+    lanes32, tune32 = dt.dtsph_tuning(sim32.ctx)
     ms_it, bytes_it, npairs = dt.dtsph_probe_iterate(sim32.ctx, 50)
     ms_it64, bytes_it64, _ = dt.dtsph_probe_iterate(sim64.ctx, 20)
     peaks = {}
@@ -242,6 +246,7 @@ def main_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "kernel": "k_iterate<2,FP32C>", "bytes_per_launch": bytes_it,
                      "launch_ms": ms_it, "pairs": npairs, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
+        "autotune": {"lanes_per_particle": lanes32, "ms_by_lanes": tune32},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

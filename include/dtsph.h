@@ -77,7 +77,9 @@ typedef struct {
     int32_t max_neighbors;    /* neighbour capacity per particle (0 = derived from h and m) */
     int32_t graph;            /* 1: capture each real step in a CUDA graph whose pseudo-time
                                  loop is a conditional while node; 0: plain launches */
-    int32_t pad1;
+    int32_t lanes;            /* lanes per particle in the pseudo-iteration kernel: 1, 2, 4
+                                 or 8; 0 = picked by the built-in autotuner after the first
+                                 step (timed candidates, cached per shape in the process) */
 } dtsph_params;
 
 typedef struct {
@@ -175,6 +177,12 @@ int dtsph_get_neighbors(dtsph_ctx *ctx, int64_t i, int64_t *out, int64_t cap, in
  * stream. */
 int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, double *bytes_per_launch,
                         int64_t *pairs);
+
+/* Autotuner report: the lanes per particle the iterate kernel uses, and (if
+ * ms_by_lanes is not NULL, 4 floats) the mean launch time measured for 1, 2, 4
+ * and 8 lanes when this context tuned (-1 where it did not measure, e.g. when
+ * the shape was already tuned in this process or lanes was fixed). */
+int dtsph_tuning(const dtsph_ctx *ctx, int32_t *lanes, float *ms_by_lanes);
 
 /* Kernel launches this context has made so far (counted on the host; a graph
  * launch counts the kernels it runs, pseudo-iterations included). */

@@ -41,7 +41,7 @@ class dtsph_params(C.Structure):
         ("nu", C.c_double), ("dt", C.c_double), ("eta", C.c_double), ("alpha", C.c_double),
         ("g", C.c_double * 3), ("eps", C.c_double), ("stag_tol", C.c_double),
         ("stag_window", C.c_int32), ("max_iter", C.c_int32), ("edac", C.c_int32), ("edac_h2_literal", C.c_int32),
-        ("fixed_iters", C.c_int32), ("max_neighbors", C.c_int32), ("graph", C.c_int32), ("pad1", C.c_int32),
+        ("fixed_iters", C.c_int32), ("max_neighbors", C.c_int32), ("graph", C.c_int32), ("lanes", C.c_int32),
     ]
 
 
@@ -71,6 +71,7 @@ _SIGS = [
     ("dtsph_build_neighbors", C.c_int, [_VP]),
     ("dtsph_get_neighbors", C.c_int, [_VP, C.c_int64, _I64P, C.c_int64, _I64P]),
     ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
+    ("dtsph_tuning", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     ("dtsph_kernel_launches", C.c_int64, [_VP]),
 ]
 
@@ -123,7 +124,7 @@ def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) 
     """Fill dtsph_params from a plain dict (the keys of ``synth`` configs)."""
     d = dict(periodic=(0, 0, 0), lo=(0, 0, 0), hi=(1, 1, 1), rho0=1.0, beta=10.0, v_ref=1.0, eta=0.01, alpha=0.0,
              g=(0, 0, 0), eps=1e-3, stag_tol=0.05, stag_window=4, max_iter=1000, edac=1, edac_h2_literal=0,
-             fixed_iters=0, max_neighbors=0)
+             fixed_iters=0, max_neighbors=0, lanes=0)
     d.update(cfg)
     d.update(over)
     p = dtsph_params()
@@ -137,7 +138,7 @@ def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) 
         p.g[a] = float(d["g"][a]) if a < len(d["g"]) else 0.0
     for k in ("h", "m", "rho0", "beta", "v_ref", "nu", "dt", "eta", "alpha", "eps", "stag_tol"):
         setattr(p, k, float(d[k]))
-    for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "max_neighbors"):
+    for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "max_neighbors", "lanes"):
         setattr(p, k, int(d[k]))
     return p
 
@@ -234,6 +235,14 @@ def dtsph_probe_iterate(ctx, launches: int = 20):
     npairs = C.c_int64()
     _check(ctx, lib().dtsph_probe_iterate(ctx, int(launches), C.byref(ms), C.byref(by), C.byref(npairs)))
     return float(ms.value), float(by.value), int(npairs.value)
+
+
+def dtsph_tuning(ctx):
+    """(lanes per particle in use, {lanes: ms per launch} measured by the autotuner)."""
+    lanes = C.c_int32()
+    ms = (C.c_float * 4)()
+    _check(ctx, lib().dtsph_tuning(ctx, C.byref(lanes), ms))
+    return lanes.value, {L: float(m) for L, m in zip((1, 2, 4, 8), ms) if m >= 0}
 
 
 def dtsph_kernel_launches(ctx) -> int:

@@ -1,6 +1,8 @@
 // C ABI of the library (include/dtsph.h): context, device memory, the per-step
 // launch sequence, its CUDA-graph capture, and field read-back.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <new>
 #include <cstdarg>
@@ -36,6 +38,8 @@ struct dtsph_ctx {
     std::vector<void *> allocs;
     int nblk = 0;
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
+    bool tuned = false;
+    std::vector<std::pair<int, float>> tune_log;   // (lanes, ms per launch) of the last tuning
 };
 
 namespace {
@@ -187,7 +191,35 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
     if (p->fixed_iters < 0 || p->fixed_iters > (1 << 24)) return fail(c, DTSPH_E_ARG, "fixed_iters out of range");
     if (p->edac_h2_literal) return fail(c, DTSPH_E_UNSUPPORTED, "the literal r^2 + h^2 EDAC denominator is oracle-only");
     if (p->max_neighbors < 0 || p->max_neighbors > 4096) return fail(c, DTSPH_E_ARG, "max_neighbors out of range");
+    if (p->lanes != 0 && p->lanes != 1 && p->lanes != 2 && p->lanes != 4 && p->lanes != 8)
+        return fail(c, DTSPH_E_ARG, "lanes must be 0, 1, 2, 4 or 8");
     return DTSPH_OK;
+}
+
+// Autotuner results: lanes per particle of the iterate kernel, keyed by
+// (dim, precision, particle count), shared by every context of the process.
+struct TuneKey {
+    int dim, prec;
+    int64_t n;
+    bool operator<(const TuneKey &o) const
+    {
+        return dim != o.dim ? dim < o.dim : prec != o.prec ? prec < o.prec : n < o.n;
+    }
+};
+std::map<TuneKey, int> &tune_cache()
+{
+    static std::map<TuneKey, int> m;
+    return m;
+}
+std::mutex tune_mu;
+
+int tuned_lanes(dtsph_ctx *c, int64_t n)
+{
+    std::lock_guard<std::mutex> g(tune_mu);
+    auto it = tune_cache().find(TuneKey{c->prm.dim, c->prm.precision, n});
+    if (it == tune_cache().end()) return 4;
+    c->tuned = true;
+    return it->second;
 }
 
 int neighbour_capacity(const dtsph_params &p)
@@ -214,6 +246,7 @@ int allocate(dtsph_ctx *c, int64_t nf, int64_t nw)
     B.dim = d;
     B.fp32c = c->prm.precision == DTSPH_FP32C;
     B.K = neighbour_capacity(c->prm);
+    B.lanes = c->prm.lanes > 0 ? c->prm.lanes : tuned_lanes(c, nf + nw);
     const size_t nd = (size_t)n * d;
     const size_t nwarps = ((size_t)n + kWarp - 1) / kWarp;
     const size_t npair = nwarps * B.K * kWarp;
@@ -222,7 +255,7 @@ int allocate(dtsph_ctx *c, int64_t nf, int64_t nw)
     A(B.gid_a, n) A(B.x_a, nd) A(B.xp_a, nd) A(B.vn_a, nd) A(B.vnm1_a, nd) A(B.pn_a, n) A(B.s_a, nd) A(B.cell_a, n)
     A(B.gid_b, n) A(B.x_b, nd) A(B.vn_b, nd) A(B.vnm1_b, nd) A(B.pn_b, n) A(B.xp_b, nd) A(B.v0_b, nd)
     A(B.ph0_b, n) A(B.s_b, nd) A(B.cell_b, n)
-    A(B.key, n) A(B.slot, n) A(B.perm, n) A(B.cell_count, c->G.ncell) A(B.cell_start, (size_t)c->G.ncell + 1)
+    A(B.key, n) A(B.slot, n) A(B.unsorted, n) A(B.perm, n) A(B.cell_count, c->G.ncell) A(B.cell_start, (size_t)c->G.ncell + 1)
     A(B.vk[0], nd) A(B.vk[1], nd)
     A(B.pcount, n) A(B.pj, npair)
     if (B.fp32c) {
@@ -231,7 +264,7 @@ int allocate(dtsph_ctx *c, int64_t nf, int64_t nw)
         A(B.nb64[0], n) A(B.nb64[1], n) A(B.pc64, npair)
     }
     A(B.ap_b, n) A(B.f_b, nd)
-    c->nblk = iterate_blocks(B);
+    c->nblk = (n + kWarp - 1) / kWarp;   // blocks of the iterate kernel at 8 lanes, the most
     A(B.blk, 2 * (size_t)c->nblk) A(B.ls, 1) A(B.stats, kStatRing) A(B.err, 1)
 #undef A
     CK(cudaMemsetAsync(B.cell_count, 0, sizeof(int) * c->G.ncell, c->stream));
@@ -264,8 +297,7 @@ int enqueue_pre_loop(dtsph_ctx *c, cudaStream_t st)
     k += launch_state_n(B, c->G, c->P, true, st);              // walls, rates, predictor
     k += launch_binning(B, c->G, B.xp_b, B.gid_b, st);         // cells at r^0
     k += launch_permute_b_to_a(B, c->G, st);
-    k += launch_pair_cache(B, c->G, c->P, B.xp_a, B.cell_a, B.gid_a, st);
-    k += launch_loop_reset(B, st);
+    k += launch_pair_cache(B, c->G, c->P, B.xp_a, B.cell_a, B.gid_a, st);   // also resets the loop state
     return k;
 }
 
@@ -346,6 +378,77 @@ int step_plain(dtsph_ctx *c)
     return DTSPH_OK;
 }
 
+int device_error(dtsph_ctx *c);
+
+// Mean duration of `launches` launches of the iterate kernel on the frozen pair
+// cache of the last step (each after a loop reset, bracketed by events).
+int probe_ms(dtsph_ctx *c, int launches, float *out)
+{
+    const Buffers &B = c->B;
+    std::vector<cudaEvent_t> ev(2 * launches);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    for (int i = 0; i < launches; ++i) {
+        launch_loop_reset(B, c->stream);
+        CK(cudaEventRecord(ev[2 * i], c->stream));
+        launch_iterate(B, c->G, c->P, 0ull, 0, c->stream);
+        CK(cudaEventRecord(ev[2 * i + 1], c->stream));
+    }
+    c->launches += 2 * launches;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    double tot = 0;
+    for (int i = 0; i < launches; ++i) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+        tot += ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    *out = (float)(tot / launches);
+    return DTSPH_OK;
+}
+
+// Times every lanes-per-particle candidate of the iterate kernel on a pair
+// cache built at the initial positions and keeps the fastest. Runs once per
+// shape in a process, before the first step, so that every step of every
+// context of that shape uses the same kernel (and so the same summation order).
+// The loop buffers hold no state yet; they are zeroed for the timing runs.
+int autotune(dtsph_ctx *c)
+{
+    const Buffers &B = c->B;
+    const size_t nd = (size_t)B.n * B.dim;
+    CK(cudaMemsetAsync(B.vk[0], 0, nd * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(B.s_a, 0, nd * sizeof(double), c->stream));
+    if (B.fp32c) CK(cudaMemsetAsync(B.nb32[0], 0, (size_t)B.n * sizeof(float4), c->stream));
+    else CK(cudaMemsetAsync(B.nb64[0], 0, (size_t)B.n * sizeof(double4_32a), c->stream));
+    c->launches += launch_binning(B, c->G, B.x_a, B.gid_a, c->stream);
+    c->launches += launch_permute_a_to_b(B, c->G, c->stream);
+    c->launches += launch_pair_cache(B, c->G, c->P, B.x_b, B.cell_b, B.gid_b, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    int best = c->B.lanes;
+    float best_ms = 1e30f;
+    c->tune_log.clear();
+    for (int L : {1, 2, 4, 8}) {
+        c->B.lanes = L;
+        float ms = 0;
+        probe_ms(c, 3, &ms);                   // warm-up
+        int r = probe_ms(c, 10, &ms);
+        if (r) return r;
+        c->tune_log.push_back({L, ms});
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = L;
+        }
+    }
+    c->B.lanes = best;
+    c->tuned = true;
+    {
+        std::lock_guard<std::mutex> g(tune_mu);
+        tune_cache()[TuneKey{c->prm.dim, c->prm.precision, (int64_t)c->B.n}] = best;
+    }
+    return device_error(c);
+}
+
 int device_error(dtsph_ctx *c)
 {
     uint32_t e = 0;
@@ -396,6 +499,10 @@ int set_particles_impl(dtsph_ctx *c, int64_t nf, const double *x, const double *
     if (!device) CK(cudaStreamSynchronize(c->stream));   // host arrays may be reused once we return
     c->have_particles = true;
     c->steps = 0;
+    if (!c->tuned && c->prm.lanes == 0) {
+        r = autotune(c);
+        if (r) return r;
+    }
     if (c->prm.graph && !c->exec) {
         r = build_graph(c);
         if (r) return r;
@@ -670,27 +777,24 @@ int dtsph_probe_iterate(dtsph_ctx *c, int32_t launches, float *ms_per_launch, do
     const double packed = B.fp32c ? 16.0 : 32.0;
     const double per_particle = 2 * packed + 2 * 8.0 * d + 8.0 * d + 4.0;
     const double per_pair = B.fp32c ? (d == 2 ? 16.0 : 20.0) : 36.0;
-    std::vector<cudaEvent_t> ev(2 * launches);
-    for (auto &e : ev) CK(cudaEventCreate(&e));
-    for (int i = 0; i < launches; ++i) {
-        launch_loop_reset(B, c->stream);
-        CK(cudaEventRecord(ev[2 * i], c->stream));
-        launch_iterate(B, c->G, c->P, 0ull, 0, c->stream);
-        CK(cudaEventRecord(ev[2 * i + 1], c->stream));
-    }
-    c->launches += 2 * launches;
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->stream));
-    double tot = 0;
-    for (int i = 0; i < launches; ++i) {
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
-        tot += ms;
-    }
-    for (auto &e : ev) cudaEventDestroy(e);
-    *ms_per_launch = (float)(tot / launches);
+    int r = probe_ms(c, launches, ms_per_launch);
+    if (r) return r;
     if (bytes_per_launch) *bytes_per_launch = per_particle * B.nf + per_pair * (double)np;
     if (pairs) *pairs = np;
+    return DTSPH_OK;
+}
+
+int dtsph_tuning(const dtsph_ctx *c, int32_t *lanes, float *ms_by_lanes)
+{
+    if (!c || !lanes) return DTSPH_E_ARG;
+    *lanes = c->B.lanes;
+    if (ms_by_lanes) {
+        for (int i = 0; i < 4; ++i) ms_by_lanes[i] = -1.f;
+        for (auto &e : c->tune_log) {
+            int i = e.first == 1 ? 0 : e.first == 2 ? 1 : e.first == 4 ? 2 : 3;
+            ms_by_lanes[i] = e.second;
+        }
+    }
     return DTSPH_OK;
 }
 

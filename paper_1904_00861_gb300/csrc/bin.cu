@@ -82,24 +82,21 @@ __global__ void k_scatter(int n, const int *__restrict__ key, const int *__restr
     perm[start[key[i]] + slot[i]] = i;
 }
 
-// Orders the slots of each cell by caller index (insertion sort; cells hold a
-// few tens of particles).
-__global__ void k_cell_sort(int ncell, const int *__restrict__ start, int *__restrict__ perm,
-                            const uint32_t *__restrict__ gid)
+// Orders each cell by caller index: the particle in unsorted slot t moves to
+// start[c] + (number of particles of its cell with a smaller caller index).
+// One thread per particle; cells hold a few tens of particles.
+__global__ void k_cell_rank(int n, const int *__restrict__ key, const int *__restrict__ start,
+                            const int *__restrict__ unsorted, const uint32_t *__restrict__ gid, int *__restrict__ perm)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int b = start[c], e = start[c + 1];
-    for (int u = b + 1; u < e; ++u) {
-        int pu = perm[u];
-        uint32_t ku = gid[pu];
-        int w = u - 1;
-        while (w >= b && gid[perm[w]] > ku) {
-            perm[w + 1] = perm[w];
-            --w;
-        }
-        perm[w + 1] = pu;
-    }
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i = unsorted[t];
+    const int c = key[i];
+    const uint32_t gi = gid[i];
+    const int b = start[c], e = start[c + 1];
+    int rank = 0;
+    for (int u = b; u < e; ++u) rank += gid[unsorted[u]] < gi;
+    perm[b + rank] = i;
 }
 
 __device__ __forceinline__ float4 cell_offset(const Geom &G, int cell, const double *x, int n, int s)
@@ -237,8 +234,8 @@ int launch_binning(const Buffers &B, const Geom &G, const double *x_keys, const 
 {
     k_bin_keys<<<blocks(B.n), kBlock, 0, st>>>(B.n, G, x_keys, B.key, B.slot, B.cell_count, B.err);
     k_scan_counts<<<1, kScanThreads, 0, st>>>(G.ncell, B.cell_count, B.cell_start);
-    k_scatter<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.key, B.slot, B.cell_start, B.perm);
-    k_cell_sort<<<blocks(G.ncell), kBlock, 0, st>>>(G.ncell, B.cell_start, B.perm, gid_src);
+    k_scatter<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.key, B.slot, B.cell_start, B.unsorted);
+    k_cell_rank<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.key, B.cell_start, B.unsorted, gid_src, B.perm);
     return 4;
 }
 

@@ -73,6 +73,7 @@ constexpr int kStatRing = 65536;
 // "B" = the order of the binning at r^n inside a step). SoA per component.
 struct Buffers {
     int n, nf, nw, dim, fp32c, K;   // K = neighbour capacity per particle
+    int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
     // order A (persistent)
     uint32_t *gid_a;       // caller index of each slot (walls: nf + wall index)
     double *x_a;           // r^n           [dim][n]
@@ -89,7 +90,8 @@ struct Buffers {
     // binning scratch
     int *key;              // cell of each particle in the pre-binning order
     int *slot;             // rank inside its cell (atomic order)
-    int *perm;             // new slot -> old slot
+    int *unsorted;         // new slot -> old slot, cells in atomic order
+    int *perm;             // new slot -> old slot, each cell ordered by caller index
     int *cell_count;       // [ncell], zero between binnings
     int *cell_start;       // [ncell + 1]
     // FP32 offsets of each particle from its cell origin (FP32C geometry)

@@ -104,6 +104,38 @@ __global__ void __launch_bounds__(kBlock) k_walls_iter(Buffers B)
     else B.nb64[cur][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
 }
 
+// One entry of the pair cache in registers.
+template <typename T, int D, bool F32>
+struct CacheEntry {
+    T g[3];
+    T F;
+    uint32_t jb;
+    __device__ __forceinline__ void load(const Buffers &B, size_t e)
+    {
+        if (F32) {
+            const float4 c = B.pc32[e];
+            g[0] = (T)c.x;
+            g[1] = (T)c.y;
+            if (D == 3) {
+                g[2] = (T)c.z;
+                F = (T)c.w;
+                jb = B.pj[e];
+            } else {
+                g[2] = T(0);
+                F = (T)c.z;
+                jb = __float_as_uint(c.w);
+            }
+        } else {
+            const double4_32a c = B.pc64[e];
+            g[0] = (T)c.x;
+            g[1] = (T)c.y;
+            g[2] = (T)c.z;
+            F = (T)c.w;
+            jb = B.pj[e];
+        }
+    }
+};
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -113,13 +145,26 @@ __device__ __forceinline__ T warp_sum(T v)
 }
 
 // One pseudo-time iteration over all slots (walls only contribute zeros to the
-// residual). The last block to finish reduces the block partials in a fixed
-// order, so the residual does not depend on block scheduling.
-template <int D, bool F32, bool WALLS>
+// residual).
+//
+// Phase 1: L lanes per particle split its cached pair list (lane l takes entries
+// l, l+L, ...), accumulate the two rates (Kahan-compensated FP32 on the FP32C
+// path), and merge their partial sums with warp shuffles. The block's particles
+// are a contiguous run of 256/L slots, so the warp reads of the sliced pair
+// cache stay coalesced.
+// Phase 2: one thread per particle (the first 256/L threads, whole warps, so the
+// FP64 work runs with every lane busy) applies the BDF2 pseudo-acceleration and
+// the update in FP64 and forms the residual terms.
+// The last block to finish reduces the block partials in a fixed order, so the
+// residual does not depend on block scheduling.
+template <int D, bool F32, bool WALLS, int L>
 __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned long long cond, int use_cond)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
+    constexpr int PPB = kBlock / L;                  // particles per block
+    static_assert(PPB % kWarp == 0, "whole warps in phase 2");
+    __shared__ T part[D + 1][PPB];
     __shared__ double red[2][kBlock / kWarp];
     __shared__ int last;
     LoopState *ls = B.ls;
@@ -127,36 +172,37 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
     if (!use_cond && ls->done) return;          // whole grid agrees: nothing to do
     const int cur = it & 1, nxt = cur ^ 1;
     const int n = B.n;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
+    const int s = blockIdx.x * PPB + grp;
+    const bool active = s < n && (!WALLS || B.gid_a[s] < (uint32_t)B.nf);
 
-    T r_ap = T(0), r_av = T(0);
-    if (s < n && (!WALLS || B.gid_a[s] < (uint32_t)B.nf)) {
+    // ---------------- phase 1: pair sums
+    {
         const PairConst<T> k = pair_const<T>(P);
-        T vi[3], pi;
-        if (F32) {
-            float4 q = B.nb32[cur][s];
-            vi[0] = q.x; vi[1] = q.y; vi[2] = q.z; pi = q.w;
-        } else {
-            double4_32a q = B.nb64[cur][s];
-            vi[0] = (T)q.x; vi[1] = (T)q.y; vi[2] = (T)q.z; pi = (T)q.w;
+        T vi[3] = {T(0), T(0), T(0)}, pi = T(0);
+        int cnt = 0;
+        if (active) {
+            if (F32) {
+                float4 q = B.nb32[cur][s];
+                vi[0] = q.x; vi[1] = q.y; vi[2] = q.z; pi = q.w;
+            } else {
+                double4_32a q = B.nb64[cur][s];
+                vi[0] = (T)q.x; vi[1] = (T)q.y; vi[2] = (T)q.z; pi = (T)q.w;
+            }
+            cnt = B.pcount[s];
         }
         Acc ap, Fa[3];
-        const int cnt = B.pcount[s];
         const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-        for (int kk = 0; kk < cnt; ++kk) {
-            const size_t e = base + (size_t)kk * kWarp;
-            T g[3], F;
-            uint32_t jb;
-            if (F32) {
-                float4 c = B.pc32[e];
-                g[0] = c.x; g[1] = c.y;
-                if (D == 3) { g[2] = c.z; F = c.w; jb = B.pj[e]; }
-                else { F = c.z; jb = __float_as_uint(c.w); }
-            } else {
-                double4_32a c = B.pc64[e];
-                g[0] = (T)c.x; g[1] = (T)c.y; g[2] = (T)c.z; F = (T)c.w;
-                jb = B.pj[e];
-            }
+        // the cache entry of the next pair is loaded before the current one is
+        // used, so two independent loads are in flight per lane
+        CacheEntry<T, D, F32> nx;
+        if (lane_in < cnt) nx.load(B, base + (size_t)lane_in * kWarp);
+        for (int kk = lane_in; kk < cnt; kk += L) {
+            const CacheEntry<T, D, F32> ce = nx;
+            if (kk + L < cnt) nx.load(B, base + (size_t)(kk + L) * kWarp);
+            const T *g = ce.g;
+            const T F = ce.F;
+            const uint32_t jb = ce.jb;
             const int j = (int)(jb & ~kWallBit);
             T vj[3], pj;
             if (F32) {
@@ -174,36 +220,61 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
                 pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vj, vj, pj, ap, Fa);
             }
         }
-        // BDF2 pseudo-acceleration and the update, FP64
-        double av2 = 0.0;
-        double vnew[3] = {0, 0, 0};
-        for (int a = 0; a < D; ++a) {
-            const size_t q = (size_t)a * n + s;
-            const double vk = B.vk[cur][q];
-            const double Fv = (double)Fa[a].value() + P.g[a];
-            const double av = P.kappa * (Fv - (P.c3 * vk + B.s_a[q]));
-            vnew[a] = vk + P.dtau * av;
-            B.vk[nxt][q] = vnew[a];
-            av2 += av * av;
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) {
+            ap.shfl_merge(o);
+#pragma unroll
+            for (int a = 0; a < D; ++a) Fa[a].shfl_merge(o);
         }
-        const double apv = (double)ap.value();
-        const double pnew = (double)pi + P.dtau * apv;
-        if (F32) B.nb32[nxt][s] = make_float4((float)vnew[0], (float)vnew[1], (float)vnew[2], (float)pnew);
-        else B.nb64[nxt][s] = make_double4_32a(vnew[0], vnew[1], vnew[2], pnew);
-        r_ap = (T)fabs(apv);
-        r_av = (T)sqrt(av2);
+        if (lane_in == 0) {
+            part[0][grp] = (T)ap.value();
+#pragma unroll
+            for (int a = 0; a < D; ++a) part[1 + a][grp] = (T)Fa[a].value();
+        }
     }
-    // residual partial sums: warp in the working precision, then FP64
-    T w_ap = warp_sum<T>(r_ap), w_av = warp_sum<T>(r_av);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][wid] = (double)w_ap;
-        red[1][wid] = (double)w_av;
+    __syncthreads();
+
+    // ---------------- phase 2: BDF2 pseudo-acceleration and update, FP64
+    double r_ap = 0.0, r_av = 0.0;
+    if (threadIdx.x < PPB) {
+        const int s2 = blockIdx.x * PPB + threadIdx.x;
+        if (s2 < n && (!WALLS || B.gid_a[s2] < (uint32_t)B.nf)) {
+            const double apv = (double)part[0][threadIdx.x];
+            double vnew[3] = {0, 0, 0};
+            double av2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const size_t q = (size_t)a * n + s2;
+                const double vk = B.vk[cur][q];
+                const double Fv = (double)part[1 + a][threadIdx.x] + P.g[a];
+                const double av = P.kappa * (Fv - (P.c3 * vk + B.s_a[q]));
+                vnew[a] = vk + P.dtau * av;
+                B.vk[nxt][q] = vnew[a];
+                av2 += av * av;
+            }
+            if (F32) {
+                const float4 q = B.nb32[cur][s2];
+                const float pnew = q.w + (float)P.dtau * (float)apv;
+                B.nb32[nxt][s2] = make_float4((float)vnew[0], (float)vnew[1], (float)vnew[2], pnew);
+                r_av = (double)sqrtf((float)av2);
+            } else {
+                const double pnew = B.nb64[cur][s2].w + P.dtau * apv;
+                B.nb64[nxt][s2] = make_double4_32a(vnew[0], vnew[1], vnew[2], pnew);
+                r_av = sqrt(av2);
+            }
+            r_ap = fabs(apv);
+        }
+        // residual partial sums in FP64
+        const double w_ap = warp_sum<double>(r_ap), w_av = warp_sum<double>(r_av);
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = w_ap;
+            red[1][threadIdx.x >> 5] = w_av;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0, b = 0;
-        for (int w = 0; w < kBlock / kWarp; ++w) {
+        for (int w = 0; w < PPB / kWarp; ++w) {
             a += red[0][w];
             b += red[1][w];
         }
@@ -224,6 +295,7 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
     }
     a = warp_sum<double>(a);
     b = warp_sum<double>(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) {
         red[0][wid] = a;
@@ -236,13 +308,20 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
             sa += red[0][w];
             sb += red[1][w];
         }
+        // work on a register copy: one batch of loads instead of a chain of
+        // dependent global accesses
+        LoopState st = *ls;
         const int k1 = it + 1;
-        ls->rp = sa * P.rp_scale;
-        ls->rv = sb * P.rv_scale;
-        ls->hist_p[it & 15] = ls->rp;
-        ls->hist_v[it & 15] = ls->rv;
+        st.rp = sa * P.rp_scale;
+        st.rv = sb * P.rv_scale;
+        st.hist_p[it & 15] = st.rp;
+        st.hist_v[it & 15] = st.rv;
+        const int r = stop_rule(st, k1);
+        ls->rp = st.rp;
+        ls->rv = st.rv;
+        ls->hist_p[it & 15] = st.rp;
+        ls->hist_v[it & 15] = st.rv;
         ls->iter = k1;
-        int r = stop_rule(*ls, k1);
         ls->reason = r;
         ls->done = r >= 0;
         ls->ticket = 0;
@@ -310,7 +389,19 @@ __global__ void k_loop_reset(LoopState *ls)
 
 }  // namespace
 
-int iterate_blocks(const Buffers &B) { return blocks(B.n); }
+int iterate_blocks(const Buffers &B) { return (B.n + kBlock / B.lanes - 1) / (kBlock / B.lanes); }
+
+template <int D, bool F, bool W>
+static void iterate_lanes(const Buffers &B, const Phys &P, unsigned long long cond, int use_cond, cudaStream_t st)
+{
+    const int nb = iterate_blocks(B);
+    switch (B.lanes) {
+    case 1: k_iterate<D, F, W, 1><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
+    case 2: k_iterate<D, F, W, 2><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
+    case 4: k_iterate<D, F, W, 4><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
+    default: k_iterate<D, F, W, 8><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
+    }
+}
 
 int launch_walls_iter(const Buffers &B, const Geom & /*G*/, const Phys & /*P*/, cudaStream_t st)
 {
@@ -328,17 +419,14 @@ int launch_walls_iter(const Buffers &B, const Geom & /*G*/, const Phys & /*P*/, 
 int launch_iterate(const Buffers &B, const Geom & /*G*/, const Phys &P, unsigned long long cond, int use_cond,
                    cudaStream_t st)
 {
-    const int nb = blocks(B.n);
     const bool w = B.nw > 0;
-#define DTSPH_IT(D_, F_, W_) k_iterate<D_, F_, W_><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond)
     if (B.dim == 2) {
-        if (B.fp32c) { if (w) DTSPH_IT(2, true, true); else DTSPH_IT(2, true, false); }
-        else { if (w) DTSPH_IT(2, false, true); else DTSPH_IT(2, false, false); }
+        if (B.fp32c) { if (w) iterate_lanes<2, true, true>(B, P, cond, use_cond, st); else iterate_lanes<2, true, false>(B, P, cond, use_cond, st); }
+        else { if (w) iterate_lanes<2, false, true>(B, P, cond, use_cond, st); else iterate_lanes<2, false, false>(B, P, cond, use_cond, st); }
     } else {
-        if (B.fp32c) { if (w) DTSPH_IT(3, true, true); else DTSPH_IT(3, true, false); }
-        else { if (w) DTSPH_IT(3, false, true); else DTSPH_IT(3, false, false); }
+        if (B.fp32c) { if (w) iterate_lanes<3, true, true>(B, P, cond, use_cond, st); else iterate_lanes<3, true, false>(B, P, cond, use_cond, st); }
+        else { if (w) iterate_lanes<3, false, true>(B, P, cond, use_cond, st); else iterate_lanes<3, false, false>(B, P, cond, use_cond, st); }
     }
-#undef DTSPH_IT
     return 1;
 }
 

@@ -68,7 +68,22 @@ struct Kahan {
         c = (t - s) - y;
         s = t;
     }
-    __device__ __forceinline__ float value() const { return s; }
+    __device__ __forceinline__ float value() const { return s - c; }
+    // merges the accumulator of another lane (the sum is s - c for both)
+    __device__ __forceinline__ void merge(float os, float oc)
+    {
+        float t = s + os;
+        float bp = t - s;
+        float err = (s - (t - bp)) + (os - bp);   // t + err == s + os exactly
+        c = c + oc - err;
+        s = t;
+    }
+    __device__ __forceinline__ void shfl_merge(int lane_mask)
+    {
+        float os = __shfl_xor_sync(0xffffffffu, s, lane_mask);
+        float oc = __shfl_xor_sync(0xffffffffu, c, lane_mask);
+        merge(os, oc);
+    }
 };
 
 struct Plain64 {
@@ -76,6 +91,7 @@ struct Plain64 {
     __device__ __forceinline__ Plain64() : s(0.0) {}
     __device__ __forceinline__ void add(double v) { s += v; }
     __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ void shfl_merge(int lane_mask) { s += __shfl_xor_sync(0xffffffffu, s, lane_mask); }
 };
 
 template <typename T>
@@ -105,24 +121,26 @@ template <int D, typename T, typename Acc>
 __device__ __forceinline__ void pair_accumulate(const PairConst<T> &k, const T *g, T F, const T *vi, T pi,
                                                 const T *vj_div, const T *vj_vis, T pj, Acc &ap, Acc *Fi)
 {
-    T vdg = T(0), vvg = T(0);
+    T vdg = T(0);
     T vv[3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         vdg += (vi[a] - vj_div[a]) * g[a];
         vv[a] = vi[a] - vj_vis[a];
-        vvg += vv[a] * g[a];
     }
     T t_ap = k.c_div * vdg;
     if (k.edac) t_ap += k.c_edac * (pi - pj) * F;
     ap.add(t_ap);
     T pres = k.c_p * (pi + pj);
-    if (k.use_av && vvg > T(0)) {
+    if (k.use_av) {
         // v_ij . r_ij < 0  <=>  v_ij . gradW > 0 (dW/dr < 0); phi_ij = (v_ij . gradW) F / |gradW|^2
-        T g2 = T(0);
+        T vvg = T(0), g2 = T(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) g2 += g[a] * g[a];
-        if (g2 > T(0)) pres -= k.c_av_m * vvg * F / g2;   // -m Pi_ij with Pi_ij = -alpha h c phi / rho
+        for (int a = 0; a < D; ++a) {
+            vvg += vv[a] * g[a];
+            g2 += g[a] * g[a];
+        }
+        if (vvg > T(0) && g2 > T(0)) pres -= k.c_av_m * vvg * F / g2;   // -m Pi_ij, Pi_ij = -alpha h c phi / rho
     }
     T cv = k.c_visc * F;
 #pragma unroll

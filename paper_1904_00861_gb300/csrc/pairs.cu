@@ -14,12 +14,16 @@ namespace dtsph {
 
 namespace {
 
-inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
-
-// Calls body(neighbour cell, dx, dy, dz) for the 3^D cells around `cell`; the
-// shifts are the unwrapped cell offsets (so r_ij = off_i - off_j - shift * s).
-template <int D, class Body>
-__device__ __forceinline__ void visit_cells(const Geom &G, int cell, Body &&body)
+// Candidate traversal by a group of L lanes that serve one particle. The 3^D
+// cells around `cell` are taken row by row (a row = the three cells along x at
+// fixed y, z offsets); inside a row the candidates of the three cells are
+// numbered consecutively and lane l takes numbers l, l+L, ... Every lane of the
+// group runs the same number of rounds, so `body` may use group ballots; it is
+// called as body(valid, j, dx, dy, dz) where (dx, dy, dz) is the unwrapped cell
+// shift of candidate j (r_ij = off_i - off_j - shift * s).
+template <int D, int L, class Body>
+__device__ __forceinline__ void group_candidates(const Geom &G, const int *__restrict__ start, int cell, int lane_in,
+                                                 Body &&body)
 {
     const int c0 = cell % G.nc[0];
     const int c1 = (cell / G.nc[0]) % G.nc[1];
@@ -37,13 +41,28 @@ __device__ __forceinline__ void visit_cells(const Geom &G, int cell, Body &&body
                 if (!G.periodic[1]) continue;
                 y = y < 0 ? y + G.nc[1] : y - G.nc[1];
             }
-            for (int dx = -1; dx <= 1; ++dx) {
-                int x = c0 + dx;
+            const int row = (z * G.nc[1] + y) * G.nc[0];
+            int b[3], m[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                int x = c0 + k - 1;
+                bool ok = true;
                 if (x < 0 || x >= G.nc[0]) {
-                    if (!G.periodic[0]) continue;
-                    x = x < 0 ? x + G.nc[0] : x - G.nc[0];
+                    if (G.periodic[0]) x = x < 0 ? x + G.nc[0] : x - G.nc[0];
+                    else ok = false;
                 }
-                body((z * G.nc[1] + y) * G.nc[0] + x, dx, dy, dz);
+                b[k] = ok ? start[row + x] : 0;
+                m[k] = ok ? start[row + x + 1] - b[k] : 0;
+            }
+            const int m01 = m[0] + m[1];
+            const int tot = m01 + m[2];
+            for (int r = 0; r < tot; r += L) {
+                const int v = r + lane_in;
+                int j, dx;
+                if (v < m[0]) { j = b[0] + v; dx = -1; }
+                else if (v < m01) { j = b[1] + v - m[0]; dx = 0; }
+                else { j = b[2] + v - m01; dx = 1; }
+                body(v < tot, j, dx, dy, dz);
             }
         }
     }
@@ -134,97 +153,125 @@ __device__ __forceinline__ const float4 *nb_ptr<float>(const Buffers &B, int buf
 
 // Adami et al. wall values at state n in order B: p_w = (sum_f p_f W + rho0 g .
 // sum_f r_wf W) / sum_f W, ghost velocity 2 v_w - sum_f V_f W / sum_f W; written
-// into the packed (V, p) of the wall slot.
-template <int D, bool F32>
+// into the packed (V, p) of the wall slot. L lanes per wall particle.
+template <int D, bool F32, int L>
 __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B, Geom G, Phys P)
 {
     using T = typename std::conditional<F32, float, double>::type;
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.n || B.gid_b[s] < (uint32_t)B.nf) return;
+    const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
+    const int s = blockIdx.x * (kBlock / L) + grp;
+    // every lane stays to the end: the partial sums are merged by full-warp shuffles
+    const bool wall = s < B.n && B.gid_b[s] >= (uint32_t)B.nf;
     const auto *nb = nb_ptr<T>(B, 1);
-    float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
-    double sw = 0, sp = 0, sg = 0, sv[3] = {0, 0, 0};
-    double sigma = P.sig_h * P.h;
-    visit_cells<D>(G, B.cell_b[s], [&](int c, int dx, int dy, int dz) {
-        for (int j = B.cell_start[c]; j < B.cell_start[c + 1]; ++j) {
-            if (j == s || B.gid_b[j] >= (uint32_t)B.nf) continue;
-            T d[3], r2;
-            if (!neighbour<D, F32, T>(G, B.x_b, B.off, B.n, s, j, oi, dx, dy, dz, d, r2)) continue;
-            double W = sigma * (double)quintic_w<T>(sqrt(r2) / (T)P.h);
-            auto q = nb[j];
-            double gr = 0;
+    const float4 oi = wall && F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    double acc[6] = {0, 0, 0, 0, 0, 0};   // sum W, sum p W, sum rho0 (g . r) W, sum V W
+    const double sigma = P.sig_h * P.h;
+    if (wall) group_candidates<D, L>(G, B.cell_start, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
+        if (!valid || j == s || B.gid_b[j] >= (uint32_t)B.nf) return;
+        T d[3], r2;
+        if (!neighbour<D, F32, T>(G, B.x_b, B.off, B.n, s, j, oi, dx, dy, dz, d, r2)) return;
+        const double W = sigma * (double)quintic_w<T>(sqrt(r2) / (T)P.h);
+        const auto q = nb[j];
+        double gr = 0;
 #pragma unroll
-            for (int a = 0; a < D; ++a) gr += P.g[a] * (double)d[a];
-            sw += W;
-            sp += (double)q.w * W;
-            sg += P.rho0 * gr * W;
-            sv[0] += (double)q.x * W;
-            sv[1] += (double)q.y * W;
-            if (D == 3) sv[2] += (double)q.z * W;
-        }
+        for (int a = 0; a < D; ++a) gr += P.g[a] * (double)d[a];
+        acc[0] += W;
+        acc[1] += (double)q.w * W;
+        acc[2] += P.rho0 * gr * W;
+        acc[3] += (double)q.x * W;
+        acc[4] += (double)q.y * W;
+        acc[5] += (double)q.z * W;
     });
-    double vw[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) vw[a] = B.vn_b[(size_t)a * B.n + s];
-    double pw = sw > 0 ? (sp + sg) / sw : 0.0;
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int t = 0; t < 6; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    if (!wall || lane_in != 0) return;
+    const double sw = acc[0];
     double gv[3];
-    for (int a = 0; a < 3; ++a) gv[a] = 2.0 * vw[a] - (sw > 0 ? sv[a] / sw : 0.0);
+    for (int a = 0; a < 3; ++a) {
+        const double vw = a < D ? B.vn_b[(size_t)a * B.n + s] : 0.0;
+        gv[a] = 2.0 * vw - (sw > 0 ? acc[3 + a] / sw : 0.0);
+    }
+    const double pw = sw > 0 ? (acc[1] + acc[2]) / sw : 0.0;
     if (F32) B.nb32[1][s] = make_float4((float)gv[0], (float)gv[1], (float)gv[2], (float)pw);
     else B.nb64[1][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
 }
 
 // ------------------------------------------------------------------ state n pass
 
-// Rates at (r^n, V^n, p^n) in order B. With PRED, also the predictor of Eqs.
-// (v0, r0): V^0 = V^n + dt F^n, r^0 = r^n + dt V^n + dt^2/2 F^n; the first
-// pressure half step p-hat^0 = p^n + dtau/2 dp^n/dtau (Eq. pkstar_frozen with the
-// state-n rate); and the BDF2 source (V^{n-1} - 4 V^n) / (2 dt) of Eq.
-// (dv_dtau_exact), all in FP64.
-template <int D, bool F32, bool PRED>
+// Rates at (r^n, V^n, p^n) in order B, L lanes per particle (partial sums
+// merged by shuffles). With PRED, also the predictor of Eqs. (v0, r0):
+// V^0 = V^n + dt F^n, r^0 = r^n + dt V^n + dt^2/2 F^n; the first pressure half
+// step p-hat^0 = p^n + dtau/2 dp^n/dtau (Eq. pkstar_frozen with the state-n
+// rate); and the BDF2 source (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact),
+// all in FP64, one thread per particle in whole warps.
+template <int D, bool F32, bool PRED, int L>
 __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.n) return;
+    constexpr int PPB = kBlock / L;
+    __shared__ T part[D + 1][PPB];
     const int n = B.n;
-    if (B.gid_b[s] >= (uint32_t)B.nf) {
+    const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
+    const int s = blockIdx.x * PPB + grp;
+    const bool fluid = s < n && B.gid_b[s] < (uint32_t)B.nf;
+    {
+        const auto *nb = nb_ptr<T>(B, 1);
+        const PairConst<T> k = pair_const<T>(P);
+        Acc ap, Fa[3];
+        if (fluid) {
+            const auto qi = nb[s];
+            const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
+            const T pi = (T)qi.w;
+            const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+            group_candidates<D, L>(G, B.cell_start, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
+                if (!valid || j == s) return;
+                T d[3], r2;
+                if (!neighbour<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2)) return;
+                T g[3], F;
+                grad_coef<D, T>(P, d, r2, g, F);
+                const auto qj = nb[j];
+                const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
+                T vd[3] = {vv[0], vv[1], vv[2]};
+                if (B.gid_b[j] >= (uint32_t)B.nf) {
+                    for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
+                }
+                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
+            });
+        }
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) {
+            ap.shfl_merge(o);
+#pragma unroll
+            for (int a = 0; a < D; ++a) Fa[a].shfl_merge(o);
+        }
+        if (lane_in == 0) {
+            part[0][grp] = (T)ap.value();
+#pragma unroll
+            for (int a = 0; a < D; ++a) part[1 + a][grp] = (T)Fa[a].value();
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= PPB) return;
+    const int s2 = blockIdx.x * PPB + threadIdx.x;
+    if (s2 >= n) return;
+    if (B.gid_b[s2] >= (uint32_t)B.nf) {
         if (PRED) {
-            for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s] = B.x_b[(size_t)a * n + s];
+            for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s2] = B.x_b[(size_t)a * n + s2];
         }
         return;
     }
-    const auto *nb = nb_ptr<T>(B, 1);
-    const PairConst<T> k = pair_const<T>(P);
-    auto qi = nb[s];
-    T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
-    T pi = (T)qi.w;
-    float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
-    Acc ap, Fa[3];
-    visit_cells<D>(G, B.cell_b[s], [&](int c, int dx, int dy, int dz) {
-        for (int j = B.cell_start[c]; j < B.cell_start[c + 1]; ++j) {
-            if (j == s) continue;
-            T d[3], r2;
-            if (!neighbour<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2)) continue;
-            T g[3], F;
-            grad_coef<D, T>(P, d, r2, g, F);
-            auto qj = nb[j];
-            T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
-            T vd[3] = {vv[0], vv[1], vv[2]};
-            if (B.gid_b[j] >= (uint32_t)B.nf) {
-                for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
-            }
-            pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
-        }
-    });
-    double apv = (double)ap.value();
+    const double apv = (double)part[0][threadIdx.x];
     double Fv[3];
-    for (int a = 0; a < D; ++a) Fv[a] = (double)Fa[a].value() + P.g[a];
-    B.ap_b[s] = apv;
-    for (int a = 0; a < D; ++a) B.f_b[(size_t)a * n + s] = Fv[a];
+    for (int a = 0; a < D; ++a) Fv[a] = (double)part[1 + a][threadIdx.x] + P.g[a];
+    B.ap_b[s2] = apv;
+    for (int a = 0; a < D; ++a) B.f_b[(size_t)a * n + s2] = Fv[a];
     if (PRED) {
         for (int a = 0; a < D; ++a) {
-            size_t q = (size_t)a * n + s;
-            double V = B.vn_b[q];
+            const size_t q = (size_t)a * n + s2;
+            const double V = B.vn_b[q];
             double xp = B.x_b[q] + P.dt * V + 0.5 * P.dt * P.dt * Fv[a];
             if (G.periodic[a]) {
                 if (xp >= G.hi[a]) xp -= G.L[a];
@@ -234,7 +281,7 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
             B.v0_b[q] = V + P.dt * Fv[a];
             B.s_b[q] = (B.vnm1_b[q] - 4.0 * V) * P.inv_2dt;
         }
-        B.ph0_b[s] = B.pn_b[s] + 0.5 * P.dtau * apv;
+        B.ph0_b[s2] = B.pn_b[s2] + 0.5 * P.dtau * apv;
     }
 }
 
@@ -242,65 +289,80 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
 
 // For every slot (order of the latest binning) the list of its neighbours with
 // gradW_ij and F_ij (fluid slot), or W_wf and rho0 (g . r_wf) W_wf (wall slot),
-// sliced by warp so that entry k of the 32 lanes of a warp is contiguous.
-template <int D, bool F32>
+// sliced by warp so that entry k of the 32 slots of a warp is contiguous. L lanes
+// per slot test candidates side by side; a group ballot keeps the list in
+// candidate order. Block 0 also resets the pseudo-time loop state.
+template <int D, bool F32, int L>
 __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, Geom G, Phys P, const double *__restrict__ xpos,
                                                        const int *__restrict__ cell, const uint32_t *__restrict__ gid)
 {
     using T = typename std::conditional<F32, float, double>::type;
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        LoopState *ls = B.ls;
+        ls->iter = 0;
+        ls->done = 0;
+        ls->reason = -1;
+        ls->ticket = 0;
+        ls->rp = 0;
+        ls->rv = 0;
+    }
+    const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
+    const int s = blockIdx.x * (kBlock / L) + grp;
+    if (s >= B.n) return;                                  // whole group leaves together
     const int n = B.n, K = B.K;
     const bool wall_s = gid[s] >= (uint32_t)B.nf;
     const size_t base = (size_t)(s >> 5) * K * kWarp + (s & 31);
-    float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    const unsigned gshift = (threadIdx.x & 31) - lane_in;   // first lane of the group in the warp
+    const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << gshift;
     int cnt = 0;
     const T sigma = (T)(P.sig_h * P.h);
-    visit_cells<D>(G, cell[s], [&](int c, int dx, int dy, int dz) {
-        for (int j = B.cell_start[c]; j < B.cell_start[c + 1]; ++j) {
-            if (j == s) continue;
-            T d[3], r2;
-            if (!neighbour<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2)) continue;
-            if (cnt < K) {
-                T c4[4] = {T(0), T(0), T(0), T(0)};
-                if (wall_s) {
-                    T W = sigma * quintic_w<T>(sqrt(r2) / (T)P.h);
-                    T gr = T(0);
-                    for (int a = 0; a < D; ++a) gr += (T)P.g[a] * d[a];
-                    c4[0] = W;
-                    c4[1] = (T)P.rho0 * gr * W;
-                } else {
-                    T g[3], F;
-                    grad_coef<D, T>(P, d, r2, g, F);
-                    c4[0] = g[0];
-                    c4[1] = g[1];
-                    if (D == 3) {
-                        c4[2] = g[2];
-                        c4[3] = F;
-                    } else {
-                        c4[2] = F;
-                    }
-                }
-                uint32_t jb = (uint32_t)j | (gid[j] >= (uint32_t)B.nf ? kWallBit : 0u);
-                size_t e = base + (size_t)cnt * kWarp;
-                if (F32) {
-                    float4 v = make_float4((float)c4[0], (float)c4[1], (float)c4[2], (float)c4[3]);
-                    if (D == 2) v.w = __uint_as_float(jb);
-                    else B.pj[e] = jb;
-                    B.pc32[e] = v;
-                } else {
-                    B.pc64[e] = make_double4_32a((double)c4[0], (double)c4[1], (double)c4[2], (double)c4[3]);
-                    B.pj[e] = jb;
-                }
+    group_candidates<D, L>(G, B.cell_start, cell[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
+        T d[3], r2;
+        const bool in = valid && j != s && neighbour<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2);
+        const unsigned bal = __ballot_sync(gmask, in) >> gshift;
+        const int pos = cnt + __popc(bal & ((1u << lane_in) - 1u));
+        cnt += __popc(bal);
+        if (!in || pos >= K) return;
+        T c4[4] = {T(0), T(0), T(0), T(0)};
+        if (wall_s) {
+            const T W = sigma * quintic_w<T>(sqrt(r2) / (T)P.h);
+            T gr = T(0);
+            for (int a = 0; a < D; ++a) gr += (T)P.g[a] * d[a];
+            c4[0] = W;
+            c4[1] = (T)P.rho0 * gr * W;
+        } else {
+            // layout (gradW, F_ij); FP32C in 2D packs (gx, gy, F_ij, index bits)
+            T g[3], F;
+            grad_coef<D, T>(P, d, r2, g, F);
+            c4[0] = g[0];
+            c4[1] = g[1];
+            if (F32 && D == 2) {
+                c4[2] = F;
+            } else {
+                c4[2] = D == 3 ? g[2] : T(0);
+                c4[3] = F;
             }
-            ++cnt;
+        }
+        const uint32_t jb = (uint32_t)j | (gid[j] >= (uint32_t)B.nf ? kWallBit : 0u);
+        const size_t e = base + (size_t)pos * kWarp;
+        if (F32) {
+            float4 v = make_float4((float)c4[0], (float)c4[1], (float)c4[2], (float)c4[3]);
+            if (D == 2) v.w = __uint_as_float(jb);
+            else B.pj[e] = jb;
+            B.pc32[e] = v;
+        } else {
+            B.pc64[e] = make_double4_32a((double)c4[0], (double)c4[1], (double)c4[2], (double)c4[3]);
+            B.pj[e] = jb;
         }
     });
-    if (cnt > K) {
-        atomicOr(B.err, kErrCapacity);
-        cnt = K;
+    if (lane_in == 0) {
+        if (cnt > K) {
+            atomicOr(B.err, kErrCapacity);
+            cnt = K;
+        }
+        B.pcount[s] = cnt;
     }
-    B.pcount[s] = cnt;
 }
 
 }  // namespace
@@ -313,22 +375,30 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, Geom G, Phys P
         else { constexpr int D = 3; constexpr bool F32 = true; __VA_ARGS__; }                       \
     } while (0)
 
+constexpr int kTravLanes = 8;   // lanes per particle of the traversal kernels
+
+inline int trav_blocks(int n) { return (n + kBlock / kTravLanes - 1) / (kBlock / kTravLanes); }
+
 int launch_state_n(const Buffers &B, const Geom &G, const Phys &P, bool predictor, cudaStream_t st)
 {
     int k = 0;
+    const int nb = trav_blocks(B.n);
     if (B.nw > 0) {
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32><<<blocks(B.n), kBlock, 0, st>>>(B, G, P)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, kTravLanes><<<nb, kBlock, 0, st>>>(B, G, P)));
         ++k;
     }
-    if (predictor) DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true><<<blocks(B.n), kBlock, 0, st>>>(B, G, P)));
-    else DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false><<<blocks(B.n), kBlock, 0, st>>>(B, G, P)));
+    if (predictor)
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes><<<nb, kBlock, 0, st>>>(B, G, P)));
+    else
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes><<<nb, kBlock, 0, st>>>(B, G, P)));
     return k + 1;
 }
 
 int launch_pair_cache(const Buffers &B, const Geom &G, const Phys &P, const double *xpos, const int *cell,
                       const uint32_t *gid, cudaStream_t st)
 {
-    DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32><<<blocks(B.n), kBlock, 0, st>>>(B, G, P, xpos, cell, gid)));
+    DTSPH_DISPATCH(B.dim, B.fp32c,
+                   (k_pair_cache<D, F32, kTravLanes><<<trav_blocks(B.n), kBlock, 0, st>>>(B, G, P, xpos, cell, gid)));
     return 1;
 }
 

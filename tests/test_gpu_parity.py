@@ -98,10 +98,17 @@ def test_rates_fp64(case):
 
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_rates_fp32c(case):
+    """FP32C rates against the FP64 oracle, normwise relative. The state is
+    randomised so that no rate is zero by symmetry (a zero reference would make
+    any FP32 rounding look infinitely large)."""
     d = CASES[case]()
+    rng = np.random.default_rng(1)
+    v = d["v"] + 0.1 * rng.normal(size=d["v"].shape)
+    p = d["p"] + 0.1 * rng.normal(size=d["p"].shape)
+    d = dict(d, v=v, p=p)
     sim = make_sim(d, precision=dt.DTSPH_FP32C)
     ap, F = sim.rates()
-    ap0, F0, _, _ = oracle.rates(d["cfg"], d["x"], d["v"], d["p"], vw=d["vw"], nf=d["nf"])
+    ap0, F0, _, _ = oracle.rates(d["cfg"], d["x"], v, p, vw=d["vw"], nf=d["nf"])
     e_ap, e_F = rel(ap, ap0), rel(F, F0)
     print(f"{case}: FP32C rates L-inf rel err ap {e_ap:.2e} F {e_F:.2e}")
     assert e_ap < 1e-4 and e_F < 1e-4
@@ -141,10 +148,36 @@ def test_steps_fp64_match_oracle(case, nsteps):
     sim.close()
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_every_lane_split_matches_oracle(lanes, prec):
+    """Each lanes-per-particle variant of the iterate kernel (the autotuner's
+    candidates) on 2D walls and 3D periodic cases."""
+    for case, nsteps in (("cavity", 3), ("tgv3d", 2)):
+        d = CASES[case]()
+        sim, orc, out = run_pair(d, nsteps, precision=prec, lanes=lanes)
+        tol = 1e-10 if prec == dt.DTSPH_FP64 else 1e-4
+        assert rel(out[-1][3], orc.v) < tol, (case, lanes)
+        if prec == dt.DTSPH_FP64:
+            assert [o[0]["iters"] for o in out] == [o[1]["iters"] for o in out]
+        sim.close()
+
+
+def test_autotuner_picks_a_candidate_and_caches_it():
+    d = synth.tgv2d(64)
+    a = make_sim(d, precision=dt.DTSPH_FP32C, lanes=0)
+    lanes, ms = dt.dtsph_tuning(a.ctx)
+    assert lanes in (1, 2, 4, 8) and set(ms) == {1, 2, 4, 8} and ms[lanes] == min(ms.values())
+    b = make_sim(d, precision=dt.DTSPH_FP32C, lanes=0)     # same shape: taken from the cache
+    assert dt.dtsph_tuning(b.ctx) == (lanes, {})
+    a.close()
+    b.close()
+
+
 def test_graph_and_plain_launches_are_bit_identical():
     d = CASES["tgv2d_jitter"]()
-    a = make_sim(d, graph=1)
-    b = make_sim(d, graph=0)
+    a = make_sim(d, graph=1, lanes=4)
+    b = make_sim(d, graph=0, lanes=4)
     a.step(4)
     b.step(4)
     assert np.array_equal(a.v, b.v) and np.array_equal(a.p, b.p) and np.array_equal(a.x, b.x)
@@ -222,16 +255,16 @@ def test_momentum_conserved_fp64():
 
 def test_deterministic_and_resume_bit_identical():
     d = CASES["tgv2d_jitter"]()
-    a = make_sim(d)
+    a = make_sim(d, lanes=2)
     a.step(4)
-    b = make_sim(d)
+    b = make_sim(d, lanes=2)
     b.step(2)
     b.sync()
     x, v, p, vp = b.x, b.v, b.p, b.v_prev
-    c = make_sim(dict(d, x=x, v=v, p=p, v_prev=vp))
+    c = make_sim(dict(d, x=x, v=v, p=p, v_prev=vp), lanes=2)
     c.step(2)
     assert np.array_equal(a.v, c.v) and np.array_equal(a.p, c.p) and np.array_equal(a.x, c.x)
-    a2 = make_sim(d)
+    a2 = make_sim(d, lanes=2)
     a2.step(4)
     assert np.array_equal(a.v, a2.v)
     for s in (a, b, c, a2):
@@ -240,35 +273,38 @@ def test_deterministic_and_resume_bit_identical():
 
 # -------------------------------------------------------------- edge cases
 
-@pytest.mark.parametrize("n", [9, 11, 33])
+@pytest.mark.parametrize("n", [10, 11, 33])
 def test_small_and_ragged_sizes(n):
-    """Particle counts that leave partial warps and blocks (9^2 particles is
-    the smallest periodic box with three cells of side >= 3h per axis)."""
+    """Particle counts that leave partial warps and blocks (10^2 particles is
+    the smallest periodic box with three cells wider than 3h per axis)."""
     d = synth.tgv2d(n, seed=n)
     sim, orc, out = run_pair(d, 2)
     assert rel(out[-1][3], orc.v) < 1e-10
     sim.close()
 
 
-def test_capacity_overflow_reported():
+@pytest.mark.parametrize("lanes", [0, 4])
+def test_capacity_overflow_reported(lanes):
+    """Too small a neighbour capacity is reported (at set-up when the autotuner
+    builds a cache there, else at the first sync), never silently truncated."""
     d = synth.tgv2d(30)
-    sim = make_sim(d, max_neighbors=8)
-    sim.step(1)
     with pytest.raises(dt.DtsphError) as e:
+        sim = make_sim(d, max_neighbors=8, lanes=lanes)
+        sim.step(1)
         sim.sync()
     assert e.value.code == -5
-    sim.close()
 
 
-def test_domain_error_reported():
+@pytest.mark.parametrize("lanes", [0, 4])
+def test_domain_error_reported(lanes):
     d = synth.cavity2d(12)
     nf = d["nf"]
     x = d["x"].copy()
     x[0] = [-1.0, 0.5]            # outside the closed box
-    sim = dt.Simulation(d["cfg"])
-    sim.set_state(x[:nf], d["v"], d["p"], walls=(x[nf:], d["vw"]))
-    sim.step(1)
+    sim = dt.Simulation(d["cfg"], lanes=lanes)
     with pytest.raises(dt.DtsphError) as e:
+        sim.set_state(x[:nf], d["v"], d["p"], walls=(x[nf:], d["vw"]))
+        sim.step(1)
         sim.sync()
     assert e.value.code == -6
     sim.close()
