@@ -184,6 +184,33 @@ int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, 
  * the shape was already tuned in this process or lanes was fixed). */
 int dtsph_tuning(const dtsph_ctx *ctx, int32_t *lanes, float *ms_by_lanes);
 
+/* Allocation-free rate evaluation, for callers that cannot allocate device
+ * memory when they need the rates: code running while a stream capture it does
+ * not own is open, solvers that reserved their whole device budget up front, and
+ * code called where a synchronous allocation could stall the host thread. The
+ * paper has no counterpart; it computes what dtsph_eval_rates computes (the two
+ * rates of Eqs. dp-dtau-frozen-edac and mom-sph-frozen for every fluid particle,
+ * walls extrapolated first) without a context and without any device allocation.
+ *   params     simulation parameters (as for dtsph_create; graph, lanes ignored)
+ *   nf, x, v, p   fluid positions (nf x dim), velocities (nf x dim), pressures (nf):
+ *              device pointers, row-major AoS, FP64
+ *   nw, xw, vw wall positions and prescribed velocities (device; vw may be NULL)
+ *   ap, F      outputs, device: dp/dtau (nf) and the momentum right-hand side
+ *              (nf x dim), in the caller's particle order
+ *   stream     cudaStream_t or NULL; the call only enqueues work and returns
+ * All work happens in one fixed scratch array of about 4.7 MB that is part of the
+ * library image and that every GPU using the library holds until the process
+ * exits. Limits: nf + nw <= 16384 particles and at most 32768 cells of side 3h,
+ * else DTSPH_E_CAPACITY and nothing is enqueued. The first call on a device looks
+ * up the array's device address (once per device, with that device current): make
+ * that first call before any stream capture. Every call reuses the same array, so
+ * calls whose GPU work can overlap (different streams or threads) race and corrupt
+ * each other; calls ordered on one stream are safe. A particle outside the box of
+ * a non-periodic axis is not reported by this entry (nothing is read back). */
+int dtsph_eval_rates_noalloc(const dtsph_params *params, int64_t nf, const double *x, const double *v,
+                             const double *p, int64_t nw, const double *xw, const double *vw, double *ap,
+                             double *F, void *stream);
+
 /* Kernel launches this context has made so far (counted on the host; a graph
  * launch counts the kernels it runs, pseudo-iterations included). */
 int64_t dtsph_kernel_launches(const dtsph_ctx *ctx);

@@ -73,6 +73,8 @@ _SIGS = [
     ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
     ("dtsph_tuning", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     ("dtsph_kernel_launches", C.c_int64, [_VP]),
+    ("dtsph_eval_rates_noalloc", C.c_int, [C.POINTER(dtsph_params), C.c_int64, _VP, _VP, _VP, C.c_int64, _VP, _VP,
+                                           _VP, _VP, _VP]),
 ]
 
 
@@ -247,6 +249,17 @@ def dtsph_tuning(ctx):
 
 def dtsph_kernel_launches(ctx) -> int:
     return lib().dtsph_kernel_launches(ctx)
+
+
+def dtsph_eval_rates_noalloc(params: dtsph_params, nf, x, v, p, ap, F, nw=0, xw=None, vw=None, stream=None) -> None:
+    """Allocation-free rate evaluation: every array is a device tensor or a
+    device address; only enqueues work on `stream`."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    rc = lib().dtsph_eval_rates_noalloc(C.byref(params), int(nf), _ptr(x), _ptr(v), _ptr(p), int(nw), _ptr(xw),
+                                        _ptr(vw), _ptr(ap), _ptr(F), stream)
+    if rc != DTSPH_OK:
+        raise DtsphError(rc, "dtsph_eval_rates_noalloc")
 
 
 def dtsph_last_error(ctx) -> str:
