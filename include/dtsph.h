@@ -38,7 +38,8 @@ enum {
     DTSPH_E_OOM = -4,         /* a device allocation failed */
     DTSPH_E_CAPACITY = -5,    /* a particle had more than max_neighbors neighbours */
     DTSPH_E_DOMAIN = -6,      /* a particle left the box of a non-periodic axis */
-    DTSPH_E_UNSUPPORTED = -7  /* parameter combination not implemented on the GPU */
+    DTSPH_E_UNSUPPORTED = -7, /* parameter combination not implemented on the GPU */
+    DTSPH_E_TIMEOUT = -8      /* a device-side wait gave up (persistent loop barrier) */
 };
 
 typedef enum {
@@ -75,8 +76,11 @@ typedef struct {
     int32_t edac_h2_literal;  /* 1: EDAC denominator r^2 + h^2 as printed; 0: r^2 + eta h^2 */
     int32_t fixed_iters;      /* > 0: run exactly this many iterations per step, no stop rules */
     int32_t max_neighbors;    /* neighbour capacity per particle (0 = derived from h and m) */
-    int32_t graph;            /* 1: capture each real step in a CUDA graph whose pseudo-time
-                                 loop is a conditional while node; 0: plain launches */
+    int32_t graph;            /* how the pseudo-time loop is driven. 1: each real step is a
+                                 CUDA graph whose loop is a conditional while node (one
+                                 launch per iteration); 2: each real step is a CUDA graph whose
+                                 loop is one persistent cooperative kernel (grid barrier per
+                                 iteration); 0: plain launches, host polls every 8 iterations */
     int32_t lanes;            /* lanes per particle in the pseudo-iteration kernel: 1, 2, 4
                                  or 8; 0 = picked by the built-in autotuner after the first
                                  step (timed candidates, cached per shape in the process) */

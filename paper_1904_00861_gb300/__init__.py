@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdtsph.so")
 DTSPH_OK = 0
 ERRORS = {
     -1: "DTSPH_E_ARG", -2: "DTSPH_E_STATE", -3: "DTSPH_E_CUDA", -4: "DTSPH_E_OOM",
-    -5: "DTSPH_E_CAPACITY", -6: "DTSPH_E_DOMAIN", -7: "DTSPH_E_UNSUPPORTED",
+    -5: "DTSPH_E_CAPACITY", -6: "DTSPH_E_DOMAIN", -7: "DTSPH_E_UNSUPPORTED", -8: "DTSPH_E_TIMEOUT",
 }
 DTSPH_FP64, DTSPH_FP32C = 0, 1
 FIELD_POS, FIELD_VEL, FIELD_P, FIELD_VEL_PREV = 0, 1, 2, 3

@@ -39,6 +39,7 @@ struct dtsph_ctx {
     int nblk = 0;
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
     bool tuned = false;
+    int loop_grid = 0;
     std::vector<std::pair<int, float>> tune_log;   // (lanes, ms per launch) of the last tuning
 };
 
@@ -191,6 +192,7 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
     if (p->fixed_iters < 0 || p->fixed_iters > (1 << 24)) return fail(c, DTSPH_E_ARG, "fixed_iters out of range");
     if (p->edac_h2_literal) return fail(c, DTSPH_E_UNSUPPORTED, "the literal r^2 + h^2 EDAC denominator is oracle-only");
     if (p->max_neighbors < 0 || p->max_neighbors > 4096) return fail(c, DTSPH_E_ARG, "max_neighbors out of range");
+    if (p->graph < 0 || p->graph > 2) return fail(c, DTSPH_E_ARG, "graph must be 0, 1 or 2");
     if (p->lanes != 0 && p->lanes != 1 && p->lanes != 2 && p->lanes != 4 && p->lanes != 8)
         return fail(c, DTSPH_E_ARG, "lanes must be 0, 1, 2, 4 or 8");
     return DTSPH_OK;
@@ -264,8 +266,9 @@ int allocate(dtsph_ctx *c, int64_t nf, int64_t nw)
         A(B.nb64[0], n) A(B.nb64[1], n) A(B.pc64, npair)
     }
     A(B.ap_b, n) A(B.f_b, nd)
-    c->nblk = (n + kWarp - 1) / kWarp;   // blocks of the iterate kernel at 8 lanes, the most
-    A(B.blk, 2 * (size_t)c->nblk) A(B.ls, 1) A(B.stats, kStatRing) A(B.err, 1)
+    c->nblk = (n + kWarp - 1) / kWarp;   // tiles of the iterate kernel at 8 lanes, the most
+    // two residual partials per tile, double-buffered by the persistent loop
+    A(B.blk, 4 * (size_t)c->nblk) A(B.ls, 1) A(B.stats, kStatRing) A(B.err, 1)
 #undef A
     CK(cudaMemsetAsync(B.cell_count, 0, sizeof(int) * c->G.ncell, c->stream));
     CK(cudaMemsetAsync(B.err, 0, sizeof(uint32_t), c->stream));
@@ -310,9 +313,33 @@ int enqueue_iteration(dtsph_ctx *c, cudaStream_t st, unsigned long long cond, in
 
 int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st) { return launch_outer(c->B, c->G, c->P, st); }
 
+// Graph of one real step with the persistent loop: pre-loop kernels -> one
+// cooperative loop kernel -> outer.
+int build_graph_persistent(dtsph_ctx *c)
+{
+    int grid = 0;
+    if (loop_grid(c->B, &grid)) return fail(c, DTSPH_E_CUDA, "occupancy query for the loop kernel failed");
+    c->loop_grid = grid;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    c->graph = g;
+    CK(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->per_step_fixed = enqueue_pre_loop(c, c->cap);
+    cudaError_t e = launch_loop(c->B, c->P, grid, c->cap);
+    c->per_step_fixed += 1 + enqueue_post_loop(c, c->cap);
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g2);
+    if (e != cudaSuccess) return fail(c, DTSPH_E_CUDA, "cooperative loop launch under capture: %s", cudaGetErrorString(e));
+    CK(e2);
+    c->per_iter = 0;
+    CK(cudaGraphInstantiate(&c->exec, g, 0));
+    return DTSPH_OK;
+}
+
 // Graph of one real step: pre-loop kernels -> while node (walls, iterate) -> outer.
 int build_graph(dtsph_ctx *c)
 {
+    if (c->prm.graph == 2) return build_graph_persistent(c);
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     c->graph = g;
@@ -457,6 +484,7 @@ int device_error(dtsph_ctx *c)
     if (e & kErrCapacity)
         return fail(c, DTSPH_E_CAPACITY, "a particle had more than %d neighbours (raise max_neighbors)", c->B.K);
     if (e & kErrDomain) return fail(c, DTSPH_E_DOMAIN, "a particle left the box of a non-periodic axis");
+    if (e & kErrBarrier) return fail(c, DTSPH_E_TIMEOUT, "a grid barrier of the persistent loop timed out");
     return DTSPH_OK;
 }
 

@@ -14,7 +14,7 @@ constexpr int kWarp = 32;
 constexpr uint32_t kWallBit = 0x80000000u;   // set in a cached neighbour index when j is a wall
 
 // Error bits raised by kernels into Buffers::err (read by dtsph_sync).
-enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u };
+enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u };
 
 // Cell grid and neighbour-test constants of one binning. Cells have side
 // s[a] >= 3h, so every neighbour lies in the 3^dim surrounding cells.
@@ -58,6 +58,8 @@ struct LoopState {
     int done;              // 1 once a stop rule holds
     int reason;            // stop reason (dtsph_step_stats.reason), -1 while running
     unsigned int ticket;   // last-block election counter of the iterate kernel
+    unsigned int bar;      // grid-barrier arrival counter of the persistent loop kernel
+    int pad0;
     double rp, rv;         // residuals of the last iteration
     double hist_p[16], hist_v[16];   // ring of the last residuals (stagnation test)
     int max_iter, fixed_iters, stag_window, pad;
@@ -129,6 +131,10 @@ int launch_walls_iter(const Buffers &B, const Geom &G, const Phys &P, cudaStream
 int launch_iterate(const Buffers &B, const Geom &G, const Phys &P, unsigned long long cond_handle,
                    int use_cond, cudaStream_t st);
 int launch_outer(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st);
+// Persistent pseudo-time loop (one cooperative launch per real step): grid size
+// (co-resident blocks, at most one per tile) and the launch itself.
+int loop_grid(const Buffers &B, int *grid);
+cudaError_t launch_loop(const Buffers &B, const Phys &P, int grid, cudaStream_t st);
 int launch_loop_reset(const Buffers &B, cudaStream_t st);
 int launch_unpermute(const Buffers &B, const uint32_t *gid, const double *src, double *out, int comps, cudaStream_t st);
 int launch_scatter_in(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,

@@ -15,9 +15,18 @@
 // The pressure is carried as p-hat^k = p^{k+1/2}, so p-hat^{k+1} = p-hat^k +
 // dtau dp/dtau and p^{k+1} = (p-hat^k + p-hat^{k+1}) / 2.
 // Residuals of Eq. (conv): R_p = mean|dp/dtau| dt / (rho0 c^2) and
-// R_v = mean|dt dV/dtau| / v_ref over the fluid particles, reduced per block
-// and finished by the last block to arrive, which also applies the stop rules
-// of Sec. 3.4 and sets the condition of the graph's while node.
+// R_v = mean|dt dV/dtau| / v_ref over the fluid particles.
+//
+// Two drivers run the same per-tile arithmetic (so they give bit-identical
+// results):
+//  - k_iterate: one launch per iteration; the last block to finish reduces the
+//    per-tile residual partials in a fixed order, applies the stop rules of
+//    Sec. 3.4 and sets the condition of the graph's while node.
+//  - k_loop: one cooperative launch runs every iteration of the real step; the
+//    blocks meet at a grid barrier after each iteration, and every block reduces
+//    the same partials in the same order and takes the same stop decision.
+#include <algorithm>
+
 #include "pair_terms.cuh"
 
 namespace dtsph {
@@ -52,14 +61,11 @@ __device__ int stop_rule(const LoopState &L, int k1)
     return -1;
 }
 
-// Wall values for iteration k from the cached fluid neighbours of each wall slot.
+// Wall values of wall slot s for the iteration whose iterate sits in buffer cur,
+// from the cached fluid neighbours of the slot.
 template <int D, bool F32>
-__global__ void __launch_bounds__(kBlock) k_walls_iter(Buffers B)
+__device__ __forceinline__ void wall_slot(const Buffers &B, int s, int cur)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.n || B.gid_a[s] < (uint32_t)B.nf) return;
-    const int cur = B.ls->iter & 1;
-    if (B.ls->done) return;
     const int cnt = B.pcount[s];
     const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
     double sw = 0, sp = 0, sv[3] = {0, 0, 0};
@@ -104,6 +110,17 @@ __global__ void __launch_bounds__(kBlock) k_walls_iter(Buffers B)
     else B.nb64[cur][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
 }
 
+// Wall values for iteration k (one launch per iteration).
+template <int D, bool F32>
+__global__ void __launch_bounds__(kBlock) k_walls_iter(Buffers B)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n || B.gid_a[s] < (uint32_t)B.nf) return;
+    const int cur = B.ls->iter & 1;
+    if (B.ls->done) return;
+    wall_slot<D, F32>(B, s, cur);
+}
+
 // One entry of the pair cache in registers.
 template <typename T, int D, bool F32>
 struct CacheEntry {
@@ -144,36 +161,37 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// One pseudo-time iteration over all slots (walls only contribute zeros to the
-// residual).
+template <typename T, int D, int L>
+struct TileShared {
+    T part[D + 1][kBlock / L];
+    double red[2][kBlock / kWarp];
+};
+
+// One iteration over tile `tile` (slots tile*PPB .. tile*PPB+PPB-1, PPB = 256/L),
+// by the whole block. Writes iterate k+1 of the tile's fluid particles and
+// returns, on thread 0, the tile's residual sums (sum |dp/dtau|, sum |dV/dtau|).
 //
 // Phase 1: L lanes per particle split its cached pair list (lane l takes entries
 // l, l+L, ...), accumulate the two rates (Kahan-compensated FP32 on the FP32C
-// path), and merge their partial sums with warp shuffles. The block's particles
-// are a contiguous run of 256/L slots, so the warp reads of the sliced pair
-// cache stay coalesced.
-// Phase 2: one thread per particle (the first 256/L threads, whole warps, so the
+// path), and merge their partial sums with warp shuffles. The tile's particles
+// are a contiguous run of slots, so the warp reads of the sliced pair cache
+// stay coalesced.
+// Phase 2: one thread per particle (the first PPB threads, whole warps, so the
 // FP64 work runs with every lane busy) applies the BDF2 pseudo-acceleration and
 // the update in FP64 and forms the residual terms.
-// The last block to finish reduces the block partials in a fixed order, so the
-// residual does not depend on block scheduling.
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned long long cond, int use_cond)
+__device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, int cur, int tile,
+                                               TileShared<typename std::conditional<F32, float, double>::type, D, L> &sh,
+                                               double &blk_ap, double &blk_av)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
-    constexpr int PPB = kBlock / L;                  // particles per block
+    constexpr int PPB = kBlock / L;
     static_assert(PPB % kWarp == 0, "whole warps in phase 2");
-    __shared__ T part[D + 1][PPB];
-    __shared__ double red[2][kBlock / kWarp];
-    __shared__ int last;
-    LoopState *ls = B.ls;
-    const int it = ls->iter;
-    if (!use_cond && ls->done) return;          // whole grid agrees: nothing to do
-    const int cur = it & 1, nxt = cur ^ 1;
+    const int nxt = cur ^ 1;
     const int n = B.n;
     const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
-    const int s = blockIdx.x * PPB + grp;
+    const int s = tile * PPB + grp;
     const bool active = s < n && (!WALLS || B.gid_a[s] < (uint32_t)B.nf);
 
     // ---------------- phase 1: pair sums
@@ -227,9 +245,9 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
             for (int a = 0; a < D; ++a) Fa[a].shfl_merge(o);
         }
         if (lane_in == 0) {
-            part[0][grp] = (T)ap.value();
+            sh.part[0][grp] = (T)ap.value();
 #pragma unroll
-            for (int a = 0; a < D; ++a) part[1 + a][grp] = (T)Fa[a].value();
+            for (int a = 0; a < D; ++a) sh.part[1 + a][grp] = (T)Fa[a].value();
         }
     }
     __syncthreads();
@@ -237,16 +255,16 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
     // ---------------- phase 2: BDF2 pseudo-acceleration and update, FP64
     double r_ap = 0.0, r_av = 0.0;
     if (threadIdx.x < PPB) {
-        const int s2 = blockIdx.x * PPB + threadIdx.x;
+        const int s2 = tile * PPB + threadIdx.x;
         if (s2 < n && (!WALLS || B.gid_a[s2] < (uint32_t)B.nf)) {
-            const double apv = (double)part[0][threadIdx.x];
+            const double apv = (double)sh.part[0][threadIdx.x];
             double vnew[3] = {0, 0, 0};
             double av2 = 0.0;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 const size_t q = (size_t)a * n + s2;
                 const double vk = B.vk[cur][q];
-                const double Fv = (double)part[1 + a][threadIdx.x] + P.g[a];
+                const double Fv = (double)sh.part[1 + a][threadIdx.x] + P.g[a];
                 const double av = P.kappa * (Fv - (P.c3 * vk + B.s_a[q]));
                 vnew[a] = vk + P.dtau * av;
                 B.vk[nxt][q] = vnew[a];
@@ -267,31 +285,32 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
         // residual partial sums in FP64
         const double w_ap = warp_sum<double>(r_ap), w_av = warp_sum<double>(r_av);
         if ((threadIdx.x & 31) == 0) {
-            red[0][threadIdx.x >> 5] = w_ap;
-            red[1][threadIdx.x >> 5] = w_av;
+            sh.red[0][threadIdx.x >> 5] = w_ap;
+            sh.red[1][threadIdx.x >> 5] = w_av;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0, b = 0;
         for (int w = 0; w < PPB / kWarp; ++w) {
-            a += red[0][w];
-            b += red[1][w];
+            a += sh.red[0][w];
+            b += sh.red[1][w];
         }
-        B.blk[2 * blockIdx.x] = a;
-        B.blk[2 * blockIdx.x + 1] = b;
-        __threadfence();
-        unsigned int t = atomicAdd(&ls->ticket, 1u);
-        last = (t == gridDim.x - 1);
+        blk_ap = a;
+        blk_av = b;
     }
-    __syncthreads();
-    if (!last) return;
-    // last block: fixed-order reduction of the block partials, then the stop rules
-    __threadfence();
+    __syncthreads();   // sh is reused by the next tile
+}
+
+// Fixed-order sum of the ntiles per-tile partials at blk (pairs of doubles), by
+// the whole block; every caller gets the same bits. Result on thread 0.
+__device__ __forceinline__ void reduce_tiles(const double *blk, int ntiles, double (&red)[2][kBlock / kWarp],
+                                             double &sa, double &sb)
+{
     double a = 0, b = 0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
-        a += __ldcg(&B.blk[2 * q]);
-        b += __ldcg(&B.blk[2 * q + 1]);
+    for (int q = threadIdx.x; q < ntiles; q += blockDim.x) {
+        a += __ldcg(&blk[2 * q]);
+        b += __ldcg(&blk[2 * q + 1]);
     }
     a = warp_sum<double>(a);
     b = warp_sum<double>(b);
@@ -303,11 +322,41 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sa = 0, sb = 0;
+        sa = 0;
+        sb = 0;
         for (int w = 0; w < kBlock / kWarp; ++w) {
             sa += red[0][w];
             sb += red[1][w];
         }
+    }
+}
+
+// One pseudo-time iteration over all slots; one tile per block.
+template <int D, bool F32, bool WALLS, int L>
+__global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned long long cond, int use_cond)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    __shared__ TileShared<T, D, L> sh;
+    __shared__ int last;
+    LoopState *ls = B.ls;
+    const int it = ls->iter;
+    if (!use_cond && ls->done) return;          // whole grid agrees: nothing to do
+    double a = 0, b = 0;
+    tile_iteration<D, F32, WALLS, L>(B, P, it & 1, blockIdx.x, sh, a, b);
+    if (threadIdx.x == 0) {
+        B.blk[2 * blockIdx.x] = a;
+        B.blk[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        unsigned int t = atomicAdd(&ls->ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // last block: fixed-order reduction of the tile partials, then the stop rules
+    __threadfence();
+    double sa = 0, sb = 0;
+    reduce_tiles(B.blk, gridDim.x, sh.red, sa, sb);
+    if (threadIdx.x == 0) {
         // work on a register copy: one batch of loads instead of a chain of
         // dependent global accesses
         LoopState st = *ls;
@@ -327,6 +376,108 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned 
         ls->ticket = 0;
         __threadfence();
         if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, r >= 0 ? 0u : 1u);
+    }
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier for a cooperative launch (all blocks resident): arrival counter
+// `bar`, reset to 0 before the launch; the epoch-th barrier waits for
+// epoch * gridDim.x arrivals. The wait gives up after one second, raises
+// kErrBarrier and returns false (the caller then stops iterating).
+__device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *err, int &ok_sh)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = epoch * gridDim.x;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        while (*(volatile unsigned int *)bar < target) {
+            __nanosleep(32);
+            if (global_ns() - t0 > 1000000000ull) {
+                atomicOr(err, kErrBarrier);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+// Every pseudo-time iteration of one real step in one cooperative launch. Tiles
+// are dealt to blocks round robin; after each iteration the blocks meet at a
+// grid barrier, each block reduces the per-tile partials (double-buffered on the
+// iteration parity) in the fixed order of k_iterate, and all blocks take the same
+// stop decision. Walls get their own phase and barrier before the fluid phase.
+template <int D, bool F32, bool WALLS, int L>
+__global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B, Phys P)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    constexpr int PPB = kBlock / L;
+    __shared__ TileShared<T, D, L> sh;
+    __shared__ LoopState st;
+    __shared__ int stop, ok_sh;
+    const int ntiles = (B.n + PPB - 1) / PPB;
+    LoopState *ls = B.ls;
+    if (threadIdx.x == 0) {
+        st = *ls;
+        stop = 0;
+    }
+    __syncthreads();
+    unsigned int epoch = 0;
+    int r = -1, it = 0;
+    for (;; ++it) {
+        const int cur = it & 1;
+        if (WALLS) {
+            for (int s = blockIdx.x * kBlock + threadIdx.x; s < B.n; s += gridDim.x * kBlock)
+                if (B.gid_a[s] >= (uint32_t)B.nf) wall_slot<D, F32>(B, s, cur);
+            if (!grid_barrier(&ls->bar, ++epoch, B.err, ok_sh)) break;
+        }
+        double *blk = B.blk + (size_t)(it & 1) * 2 * ntiles;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            double a = 0, b = 0;
+            tile_iteration<D, F32, WALLS, L>(B, P, cur, t, sh, a, b);
+            if (threadIdx.x == 0) {
+                blk[2 * t] = a;
+                blk[2 * t + 1] = b;
+            }
+        }
+        if (!grid_barrier(&ls->bar, ++epoch, B.err, ok_sh)) break;
+        double sa = 0, sb = 0;
+        reduce_tiles(blk, ntiles, sh.red, sa, sb);
+        if (threadIdx.x == 0) {
+            const int k1 = it + 1;
+            st.rp = sa * P.rp_scale;
+            st.rv = sb * P.rv_scale;
+            st.hist_p[it & 15] = st.rp;
+            st.hist_v[it & 15] = st.rv;
+            r = stop_rule(st, k1);
+            stop = r >= 0;
+        }
+        __syncthreads();
+        if (stop) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const bool finished = stop != 0;
+        ls->rp = st.rp;
+        ls->rv = st.rv;
+        for (int q = 0; q < 16; ++q) {
+            ls->hist_p[q] = st.hist_p[q];
+            ls->hist_v[q] = st.hist_v[q];
+        }
+        ls->iter = finished ? it + 1 : it;
+        ls->reason = finished ? r : 3;
+        ls->done = 1;
     }
 }
 
@@ -383,9 +534,13 @@ __global__ void k_loop_reset(LoopState *ls)
     ls->done = 0;
     ls->reason = -1;
     ls->ticket = 0;
+    ls->bar = 0;
     ls->rp = 0;
     ls->rv = 0;
 }
+
+template <int D, bool F, bool W, int L>
+const void *loop_kernel() { return (const void *)k_loop<D, F, W, L>; }
 
 }  // namespace
 
@@ -428,6 +583,58 @@ int launch_iterate(const Buffers &B, const Geom & /*G*/, const Phys &P, unsigned
         else { if (w) iterate_lanes<3, false, true>(B, P, cond, use_cond, st); else iterate_lanes<3, false, false>(B, P, cond, use_cond, st); }
     }
     return 1;
+}
+
+template <int D, bool F, bool W>
+static const void *loop_lanes(int lanes)
+{
+    switch (lanes) {
+    case 1: return loop_kernel<D, F, W, 1>();
+    case 2: return loop_kernel<D, F, W, 2>();
+    case 4: return loop_kernel<D, F, W, 4>();
+    default: return loop_kernel<D, F, W, 8>();
+    }
+}
+
+static const void *loop_function(const Buffers &B)
+{
+    const bool w = B.nw > 0;
+    if (B.dim == 2) {
+        if (B.fp32c) return w ? loop_lanes<2, true, true>(B.lanes) : loop_lanes<2, true, false>(B.lanes);
+        return w ? loop_lanes<2, false, true>(B.lanes) : loop_lanes<2, false, false>(B.lanes);
+    }
+    if (B.fp32c) return w ? loop_lanes<3, true, true>(B.lanes) : loop_lanes<3, true, false>(B.lanes);
+    return w ? loop_lanes<3, false, true>(B.lanes) : loop_lanes<3, false, false>(B.lanes);
+}
+
+int loop_grid(const Buffers &B, int *grid)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop_function(B), kBlock, 0) != cudaSuccess || per_sm < 1)
+        return -1;
+    const int ntiles = iterate_blocks(B);
+    *grid = std::min(ntiles, per_sm * sms);
+    return 0;
+}
+
+cudaError_t launch_loop(const Buffers &B, const Phys &P, int grid, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    Buffers b = B;
+    Phys p = P;
+    void *args[] = {(void *)&b, (void *)&p};
+    return cudaLaunchKernelExC(&cfg, loop_function(B), args);
 }
 
 int launch_outer(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st)

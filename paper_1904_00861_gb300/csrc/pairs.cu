@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, Geom G, Phys P
         ls->done = 0;
         ls->reason = -1;
         ls->ticket = 0;
+        ls->bar = 0;
         ls->rp = 0;
         ls->rv = 0;
     }

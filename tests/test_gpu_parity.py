@@ -186,6 +186,37 @@ def test_graph_and_plain_launches_are_bit_identical():
     b.close()
 
 
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case,nsteps", [("tgv2d_jitter", 4), ("cavity", 3), ("tgv3d", 2)])
+def test_persistent_loop_is_bit_identical(case, nsteps, prec):
+    """graph = 2 (the whole pseudo-time loop in one cooperative kernel with a
+    grid barrier per iteration) gives the same bits as graph = 1 (one launch
+    per iteration in a conditional while node), residuals included."""
+    d = CASES[case]()
+    a = make_sim(d, precision=prec, graph=1, lanes=2)
+    b = make_sim(d, precision=prec, graph=2, lanes=2)
+    a.step(nsteps)
+    b.step(nsteps)
+    b.sync()
+    assert np.array_equal(a.v, b.v) and np.array_equal(a.p, b.p) and np.array_equal(a.x, b.x)
+    assert a.stats() == b.stats()
+    a.close()
+    b.close()
+
+
+def test_persistent_loop_matches_oracle_and_caps():
+    d = CASES["tgv2d_jitter"]()
+    sim, orc, out = run_pair(d, 3, graph=2)
+    for st, rec, *_ in out:
+        assert (st["iters"], st["reason"]) == (rec["iters"], rec["reason"])
+    assert rel(out[-1][3], orc.v) < 1e-10
+    sim.close()
+    sim = make_sim(d, graph=2, eps=1e-14, stag_window=0, max_iter=7)
+    sim.step(2)
+    assert [s["iters"] for s in sim.stats()] == [7, 7] and all(s["reason"] == 2 for s in sim.stats())
+    sim.close()
+
+
 def test_fixed_iteration_mode_matches_oracle():
     d = CASES["tgv2d_jitter"]()
     sim, orc, out = run_pair(d, 3, fixed_iters=5)
