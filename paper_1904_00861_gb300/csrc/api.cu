@@ -172,6 +172,8 @@ void setup_phys(dtsph_ctx *c)
     for (int a = 0; a < 3; ++a) P.g[a] = a < p.dim ? p.g[a] : 0.0;
     P.kappa = 2.0 * p.dt / (2.0 * p.dt + 3.0 * P.dtau);
     P.c3 = 3.0 / (2.0 * p.dt);
+    P.kc3 = P.kappa * P.c3;
+    P.inv_h = 1.0 / p.h;
     P.inv_2dt = 1.0 / (2.0 * p.dt);
     P.edac = p.edac;
     P.use_av = p.alpha != 0.0;

@@ -46,6 +46,8 @@ struct Phys {
     double g[3];
     double kappa;        // 2 dt / (2 dt + 3 dtau), Eq. (dv_dtau_exact)
     double c3;           // 3 / (2 dt)
+    double kc3;          // kappa * 3 / (2 dt)
+    double inv_h;        // 1 / h
     double inv_2dt;      // 1 / (2 dt)
     double rp_scale;     // dt / (rho0 c^2) / nf
     double rv_scale;     // dt / v_ref / nf
@@ -83,7 +85,7 @@ struct Buffers {
     double *vn_a;          // V^n (walls: prescribed velocity) [dim][n]
     double *vnm1_a;        // V^{n-1}       [dim][n]
     double *pn_a;          // p^n           [n]
-    double *s_a;           // BDF2 source (V^{n-1} - 4 V^n) / (2 dt) [dim][n]
+    double *s_a;           // kappa ((V^{n-1} - 4 V^n) / (2 dt) - g): BDF2 source and body force [dim][n]
     int *cell_a;           // cell of each slot
     // order B (scratch inside a step)
     uint32_t *gid_b;

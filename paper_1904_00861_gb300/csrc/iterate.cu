@@ -161,6 +161,22 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Warp sum of (s + e) pairs with two-sum compensation: s accumulates the
+// rounded sum, e the exact rounding errors of every addition.
+__device__ __forceinline__ void warp_sum2(float &s, float &e)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, s, o);
+        const float oe = __shfl_xor_sync(0xffffffffu, e, o);
+        const float t = s + os;
+        const float bp = t - s;
+        const float err = (s - (t - bp)) + (os - bp);
+        s = t;
+        e = e + oe + err;
+    }
+}
+
 template <typename T, int D, int L>
 struct TileShared {
     T part[D + 1][kBlock / L];
@@ -262,13 +278,15 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
             double av2 = 0.0;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
+                // kappa (F + g - (3 V^k - 4 V^n + V^{n-1}) / (2 dt)), with the state-n
+                // part kappa ((V^{n-1} - 4 V^n) / (2 dt) - g) precomputed in s_a
                 const size_t q = (size_t)a * n + s2;
                 const double vk = B.vk[cur][q];
-                const double Fv = (double)sh.part[1 + a][threadIdx.x] + P.g[a];
-                const double av = P.kappa * (Fv - (P.c3 * vk + B.s_a[q]));
-                vnew[a] = vk + P.dtau * av;
+                const double Fv = (double)sh.part[1 + a][threadIdx.x];
+                const double av = fma(P.kappa, Fv, -fma(P.kc3, vk, B.s_a[q]));
+                vnew[a] = fma(P.dtau, av, vk);
                 B.vk[nxt][q] = vnew[a];
-                av2 += av * av;
+                av2 = fma(av, av, av2);
             }
             if (F32) {
                 const float4 q = B.nb32[cur][s2];
@@ -282,8 +300,21 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
             }
             r_ap = fabs(apv);
         }
-        // residual partial sums in FP64
-        const double w_ap = warp_sum<double>(r_ap), w_av = warp_sum<double>(r_av);
+        // residual partial sums: FP64 on the FP64 path; on the FP32C path the
+        // warp level sums the FP32 terms with error-free two-sum compensation
+        // (a double-float sum, accurate to ~1e-12 of the total) and the warp
+        // totals are carried on in FP64
+        double w_ap, w_av;
+        if (F32) {
+            float sa = (float)r_ap, ea = 0.f, sb = (float)r_av, eb = 0.f;
+            warp_sum2(sa, ea);
+            warp_sum2(sb, eb);
+            w_ap = (double)sa + (double)ea;
+            w_av = (double)sb + (double)eb;
+        } else {
+            w_ap = warp_sum<double>(r_ap);
+            w_av = warp_sum<double>(r_av);
+        }
         if ((threadIdx.x & 31) == 0) {
             sh.red[0][threadIdx.x >> 5] = w_ap;
             sh.red[1][threadIdx.x >> 5] = w_av;

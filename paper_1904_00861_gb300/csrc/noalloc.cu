@@ -170,6 +170,7 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     P.dt = p->dt;
     P.dtau = p->dt / p->beta;
     P.sig_h = quintic_sigma_noalloc(p->dim, p->h) / p->h;
+    P.inv_h = 1.0 / p->h;
     P.eta_h2 = p->eta * p->h * p->h;
     P.edac_h2 = P.eta_h2;
     const double rho = p->rho0;

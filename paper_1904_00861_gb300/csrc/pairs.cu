@@ -120,17 +120,31 @@ __device__ __forceinline__ bool neighbour(const Geom &G, const double *__restric
     }
 }
 
-// gradW_ij and F_ij = (r_ij . gradW_ij) / (r^2 + eta h^2) from r_ij.
+// Reciprocal square root and division in the working precision: the fast
+// single-precision forms (a few ulp) on the FP32C path, IEEE double otherwise.
+template <typename T> struct F32Math;
+template <> struct F32Math<float> {
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+};
+template <> struct F32Math<double> {
+    static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+};
+
+// gradW_ij and F_ij = (r_ij . gradW_ij) / (r^2 + eta h^2) from r_ij, with one
+// reciprocal square root: r = r^2 / r, q = r / h, gradW = (dW/dr / r) r_ij.
 template <int D, typename T>
 __device__ __forceinline__ void grad_coef(const Phys &P, const T *d, T r2, T *g, T &F)
 {
     if (r2 > T(0)) {
-        T r = sqrt(r2);
-        T dwdr = (T)P.sig_h * quintic_dwdq<T>(r / (T)P.h);
-        T a = dwdr / r;
+        const T rinv = F32Math<T>::rsqrt(r2);
+        const T r = r2 * rinv;
+        const T dwdr = (T)P.sig_h * quintic_dwdq<T>(r * (T)P.inv_h);
+        const T a = dwdr * rinv;
 #pragma unroll
         for (int k = 0; k < D; ++k) g[k] = a * d[k];
-        F = dwdr * r / (r2 + (T)P.eta_h2);
+        F = F32Math<T>::div(dwdr * r, r2 + (T)P.eta_h2);
     } else {
 #pragma unroll
         for (int k = 0; k < D; ++k) g[k] = T(0);
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B, Geom G, Phy
 // step p-hat^0 = p^n + dtau/2 dp^n/dtau (Eq. pkstar_frozen with the state-n
 // rate); and the BDF2 source (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact),
 // all in FP64, one thread per particle in whole warps.
-template <int D, bool F32, bool PRED, int L>
+template <int D, bool F32, bool PRED, int L, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
 {
     using T = typename std::conditional<F32, float, double>::type;
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
                 const auto qj = nb[j];
                 const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
                 T vd[3] = {vv[0], vv[1], vv[2]};
-                if (B.gid_b[j] >= (uint32_t)B.nf) {
+                if (WALLS && B.gid_b[j] >= (uint32_t)B.nf) {
                     for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
                 }
                 pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
@@ -279,7 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
             }
             B.xp_b[q] = xp;
             B.v0_b[q] = V + P.dt * Fv[a];
-            B.s_b[q] = (B.vnm1_b[q] - 4.0 * V) * P.inv_2dt;
+            B.s_b[q] = P.kappa * ((B.vnm1_b[q] - 4.0 * V) * P.inv_2dt - P.g[a]);
         }
         B.ph0_b[s2] = B.pn_b[s2] + 0.5 * P.dtau * apv;
     }
@@ -388,10 +402,15 @@ int launch_state_n(const Buffers &B, const Geom &G, const Phys &P, bool predicto
         DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, kTravLanes><<<nb, kBlock, 0, st>>>(B, G, P)));
         ++k;
     }
-    if (predictor)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes><<<nb, kBlock, 0, st>>>(B, G, P)));
+    const bool w = B.nw > 0;
+    if (predictor && w)
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, true><<<nb, kBlock, 0, st>>>(B, G, P)));
+    else if (predictor)
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, false><<<nb, kBlock, 0, st>>>(B, G, P)));
+    else if (w)
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, true><<<nb, kBlock, 0, st>>>(B, G, P)));
     else
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes><<<nb, kBlock, 0, st>>>(B, G, P)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, false><<<nb, kBlock, 0, st>>>(B, G, P)));
     return k + 1;
 }
 
