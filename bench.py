@@ -36,8 +36,83 @@ import synth  # noqa: E402
 
 METRIC = "particle-pseudo-iterations/sec (FP32-comp batched vs plain FP64, same GPU) at stated L∞ err"
 UNIT = "particle-iterations/s"
-WORKLOAD = dict(workload="tgv2d-200x200", particles=40000, re=100, dims=2, dt="0.25h", beta=10, eps=1e-3,
-                real_steps_per_bench_step=1)
+
+
+def make_workload(name: str, n_side: int, re: float):
+    """Synthetic input and its config record. tgv2d (default, 200 x 200) is the
+    workload the metric is quoted on; tgv3d (128^3), cavity (200 x 200 + walls)
+    and batch (64 Taylor-Green instances of 32^2..256^2 particles, Re 100..1000)
+    are the other single-GPU configurations."""
+    if name == "tgv2d":
+        n = n_side or 200
+        d = synth.tgv2d(n, re=re or 100.0)
+        cfg = dict(workload=f"tgv2d-{n}x{n}", particles=n * n, re=re or 100.0, dims=2)
+    elif name == "tgv3d":
+        n = n_side or 128
+        d = synth.tgv3d(n, re=re or 1600.0)
+        cfg = dict(workload=f"tgv3d-{n}^3", particles=n ** 3, re=re or 1600.0, dims=3)
+    elif name == "cavity":
+        n = n_side or 200
+        d = synth.cavity2d(n, re=re or 100.0)
+        cfg = dict(workload=f"cavity2d-{n}x{n}", particles=n * n, wall_particles=len(d["x"]) - d["nf"],
+                   re=re or 100.0, dims=2)
+    elif name == "batch":
+        count = n_side or 64
+        d = synth.batch(count)
+        cfg = dict(workload=f"batch-{count}x-tgv2d", instances=count, particles=int(sum(x["nf"] for x in d)),
+                   sides="U{32..256} seed 861", re="10^U[2,3)", dims=2)
+    else:
+        raise ValueError(name)
+    cfg.update(dt="0.25h", beta=10, eps=1e-3, real_steps_per_bench_step=1)
+    return d, cfg
+
+
+class Job:
+    """One context running a workload: a single instance or a batch."""
+
+    def __init__(self, dt, work, precision, stream=None, graph=2):
+        self.dt = dt
+        self.batch = isinstance(work, list)
+        if self.batch:
+            self.sim = dt.Batch([d["cfg"] for d in work], precision=precision, stream=stream, graph=graph)
+            self.sim.set_state(work)
+            self.nfs = [d["nf"] for d in work]
+        else:
+            self.sim = dt.Simulation(work["cfg"], precision=precision, stream=stream, graph=graph)
+            nf = work["nf"]
+            walls = None if work["vw"] is None else (work["x"][nf:], work["vw"])
+            self.sim.set_state(work["x"][:nf], work["v"], work["p"], work["v_prev"], walls=walls)
+            self.nfs = [nf]
+        self.ctx = self.sim.ctx
+
+    def step(self, n=1):
+        self.sim.step(n)
+
+    def sync(self):
+        self.sim.sync()
+
+    def particle_iterations(self, first, count):
+        """Per real step: sum over instances of fluid particles x iterations."""
+        tot = np.zeros(count)
+        for i, nf in enumerate(self.nfs):
+            st = self.sim.stats(i, first, count) if self.batch else self.sim.stats(first, count)
+            tot += nf * np.array([s["iters"] for s in st], dtype=float)
+        return tot
+
+    def iterations(self, first, count):
+        its = []
+        for i in range(len(self.nfs)):
+            st = self.sim.stats(i, first, count) if self.batch else self.sim.stats(first, count)
+            its.append([s["iters"] for s in st])
+        return its
+
+    def velocities(self):
+        if self.batch:
+            return np.concatenate(self.sim.field(self.dt.FIELD_VEL))
+        return self.sim.v
+
+    def close(self):
+        self.sim.close()
 
 
 def parse():
@@ -46,11 +121,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-side", type=int, default=200)
+    ap.add_argument("--workload", default="tgv2d", choices=["tgv2d", "tgv3d", "cavity", "batch"])
+    ap.add_argument("--n-side", type=int, default=0,
+                    help="particles per side, or instances for batch (0: the workload's default)")
+    ap.add_argument("--re", type=float, default=0.0, help="Reynolds number (0: the workload's default)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--graph", type=int, default=1, help="0: plain kernel launches instead of the step graph "
-                    "(used for per-kernel profiling)")
+    ap.add_argument("--graph", type=int, default=2, help="2: step graph with the persistent loop kernel; "
+                    "1: step graph with a while node; 0: plain launches (per-kernel profiling)")
     return ap.parse_args()
 
 
@@ -117,75 +196,91 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- our arm
 
-def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=1):
+def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2):
     """Times `steps` real steps after `warmup`; L2 flushed before each step.
-    Returns (particle-iterations/s, ms per step, iterations, launches, sim)."""
+    Returns (particle-iterations/s, ms per step, iterations, launches, job)."""
     stream = torch.cuda.Stream()
-    sim = dt.Simulation(d["cfg"], precision=precision, stream=stream, graph=graph)
-    sim.set_state(d["x"], d["v"], d["p"], d["v_prev"])
-    sim.step(warmup)
-    sim.sync()
-    l0 = dt.dtsph_kernel_launches(sim.ctx)
+    job = Job(dt, d, precision, stream=stream, graph=graph)
+    job.step(warmup)
+    job.sync()
+    l0 = dt.dtsph_kernel_launches(job.ctx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(stream):
         for k in range(steps):
             flush.zero_()                 # > L2: every step starts from a cold L2
             ev[k][0].record(stream)
-            sim.step(1)
+            job.step(1)
             ev[k][1].record(stream)
     stream.synchronize()
-    sim.sync()
+    job.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
-    st = sim.stats(warmup, steps)
-    iters = [s["iters"] for s in st]
-    launches = dt.dtsph_kernel_launches(sim.ctx) - l0
-    rate = sim.nf * sum(iters) / (sum(ms) * 1e-3)
-    return rate, sum(ms) / steps, iters, launches, sim
+    work = job.particle_iterations(warmup, steps)
+    iters = job.iterations(warmup, steps)
+    launches = dt.dtsph_kernel_launches(job.ctx) - l0
+    rate = float(work.sum()) / (sum(ms) * 1e-3)
+    return rate, sum(ms) / steps, iters, launches, job
 
 
-def run_e2e(dt, torch, d, precision, steps):
+def run_e2e(dt, torch, d, precision, steps, graph=2):
     """End to end through the C ABI with host arrays: per step the state goes
     host -> device, one real step runs, the state comes back device -> host."""
-    sim = dt.Simulation(d["cfg"], precision=precision)
-    x, v, p, vp = (np.ascontiguousarray(a) for a in (d["x"], d["v"], d["p"], d["v_prev"]))
-    sim.set_state(x, v, p, vp)           # allocation and graph build outside the timed region
-    sim.step(1)
-    sim.sync()
-    x, v, p, vp = sim.x, sim.v, sim.p, sim.v_prev
-    nf, dim = sim.nf, sim.dim
-    iters = 0
+    job = Job(dt, d, precision, graph=graph)     # allocation and graph build outside the timed region
+    job.step(1)
+    job.sync()
+    ctx, dim = job.ctx, (d[0] if job.batch else d)["cfg"]["dim"]
+    NF = int(sum(job.nfs))
+    read = lambda f, comps: dt.dtsph_read_field(ctx, f, NF, comps)
+    x, v, p, vp = read(dt.FIELD_POS, dim), read(dt.FIELD_VEL, dim), read(dt.FIELD_P, 1), read(dt.FIELD_VEL_PREV, dim)
+    work = 0.0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        dt.dtsph_set_particles(sim.ctx, x, v, p, vp)
-        dt.dtsph_step(sim.ctx, 1)
-        x, v, p, vp = sim.x, sim.v, sim.p, sim.v_prev
-        iters += sim.stats(0, 1)[0]["iters"]
+        if job.batch:
+            dt.dtsph_batch_set_particles(ctx, job.nfs, x, v, p, vp)
+        else:
+            dt.dtsph_set_particles(ctx, x, v, p, vp)
+        dt.dtsph_step(ctx, 1)
+        x, v, p, vp = read(dt.FIELD_POS, dim), read(dt.FIELD_VEL, dim), read(dt.FIELD_P, 1), read(dt.FIELD_VEL_PREV, dim)
+        work += float(job.particle_iterations(0, 1).sum())
     t = time.perf_counter() - t0
-    h2d = nf * (3 * dim + 1) * 8
-    d2h = nf * (3 * dim + 1) * 8
-    sim.close()
-    return {"value": nf * iters / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    h2d = NF * (3 * dim + 1) * 8
+    d2h = NF * (3 * dim + 1) * 8
+    job.close()
+    return {"value": work / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": 1e3 * t / steps}
 
 
-def cpu_baseline(d, seconds):
+def oracle_states(d, **over):
+    import oracle
+    insts = d if isinstance(d, list) else [d]
+    return [oracle.State(x["cfg"], x["x"], x["v"], x["p"], x["v_prev"], vw=x["vw"], nf=x["nf"], **over) for x in insts]
+
+
+def cpu_baseline(d, seconds, label):
     """The FP64 oracle as it stands on the host cores: real steps of the same
-    workload until `seconds` of wall time have passed (at least one)."""
+    workload (every instance of a batch in turn) until `seconds` of wall time
+    have passed (at least one round). Above 200k particles in one instance a
+    real step is capped at 2 pseudo-iterations."""
     import oracle
     oracle.build()
-    st = oracle.State(d["cfg"], d["x"], d["v"], d["p"], d["v_prev"])
+    big = max(x["nf"] for x in (d if isinstance(d, list) else [d])) > 200000
+    states = oracle_states(d, **(dict(fixed_iters=2) if big else {}))
     t0 = time.perf_counter()
+    work = 0.0
+    rounds = 0
     iters = 0
-    nsteps = 0
     while True:
-        iters += st.step(1)[0]["iters"]
-        nsteps += 1
+        for st in states:
+            it = st.step(1)[0]["iters"]
+            iters += it
+            work += st.nf * it
+        rounds += 1
         if time.perf_counter() - t0 > seconds:
             break
     t = time.perf_counter() - t0
-    return {"value": st.nf * iters / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {nsteps} real steps of the same 200x200 Taylor-Green run ({iters} pseudo-iterations, "
+    what = "real steps capped at 2 pseudo-iterations" if big else "real steps"
+    return {"value": work / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {rounds} {what} of every instance of the same {label} run ({iters} pseudo-iterations, "
                       f"{t:.1f} s wall)"}
 
 
@@ -200,7 +295,7 @@ def main_ours(args):
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1904_00861_gb300 import build as b
     b.build()
-    d = synth.tgv2d(args.n_side)
+    d, wcfg = make_workload(args.workload, args.n_side, args.re)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if world > 1:
         tdist.barrier()
@@ -217,14 +312,20 @@ def main_ours(args):
         t_max = float(tt.item())
     else:
         t_max = t_rank
-    value = world * sim32.nf * sum(it32) / (t_max * 1e-3)
-    rate64, ms64, it64, _, sim64 = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup, flush,
-                                                args.graph)
-    v32, v64 = sim32.v, sim64.v
-    linf = float(np.max(np.abs(v32 - v64)) / np.max(np.abs(v64)))
+    value = world * rate32 * t_rank / t_max
     lanes32, tune32 = dt.dtsph_tuning(sim32.ctx)
     ms_it, bytes_it, npairs = dt.dtsph_probe_iterate(sim32.ctx, 50)
-    ms_it64, bytes_it64, _ = dt.dtsph_probe_iterate(sim64.ctx, 20)
+    fp64 = None
+    linf = None
+    if not args.no_fp64:
+        rate64, ms64, it64, _, sim64 = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup, flush,
+                                                    args.graph)
+        v32, v64 = sim32.velocities(), sim64.velocities()
+        linf = float(np.max(np.abs(v32 - v64)) / np.max(np.abs(v64)))
+        ms_it64, bytes_it64, _ = dt.dtsph_probe_iterate(sim64.ctx, 20)
+        fp64 = {"value": rate64 * world, "ms_per_step": ms64, "iters_per_step_mean": float(np.mean(it64)),
+                "iterate_kernel_ms": ms_it64, "speedup_fp32c_over_fp64": value / (rate64 * world)}
+        sim64.close()
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -232,19 +333,18 @@ def main_ours(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_it / (ms_it * 1e-3) / 1e9
-    e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)))
+    e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+kahan/f64", "data": "synthetic (seeded jittered lattice, exact TGV field)",
-        "config": dict(WORKLOAD, precision="FP32C", parallelism=f"replicas{world}",
+        "vs_baseline": None, "dtype": "f32+kahan/f64", "data": "synthetic (seeded lattice, closed-form initial field)",
+        "config": dict(wcfg, precision="FP32C", parallelism=f"replicas{world}",
                        l2="flushed before every step (256 MB write)"),
         "linf_rel_vel_err_vs_fp64": linf,
         "iters_per_step_mean": float(np.mean(it32)),
-        "fp64": {"value": rate64 * world, "ms_per_step": ms64, "iters_per_step_mean": float(np.mean(it64)),
-                 "iterate_kernel_ms": ms_it64, "speedup_fp32c_over_fp64": value / (rate64 * world)},
+        "fp64": fp64,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "k_iterate<2,FP32C>", "bytes_per_launch": bytes_it,
+                     "traffic": None, "kernel": f"k_iterate<{wcfg['dims']},FP32C>", "bytes_per_launch": bytes_it,
                      "launch_ms": ms_it, "pairs": npairs, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
         "autotune": {"lanes_per_particle": lanes32, "ms_by_lanes": tune32},
         "e2e": e2e,
@@ -252,9 +352,8 @@ def main_ours(args):
         "clocks": clk.summary(),
     }
     sim32.close()
-    sim64.close()
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds, wcfg["workload"])
     if world > 1:
         tdist.barrier()
         tdist.destroy_process_group()
@@ -266,25 +365,32 @@ def main_ours(args):
 
 def main_reference(args):
     """The FP64 oracle timed on the host cores, on this arm's workload and
-    metric; every step is one real step of the 200 x 200 Taylor-Green run."""
+    metric; every step is one real step of the same run."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    d = synth.tgv2d(args.n_side)
-    st = oracle.State(d["cfg"], d["x"], d["v"], d["p"], d["v_prev"])
-    st.step(args.warmup)
+    d, wcfg = make_workload(args.workload, args.n_side, args.re)
+    states = oracle_states(d)
+    for st in states:
+        st.step(args.warmup)
     t0 = time.perf_counter()
-    iters = sum(r["iters"] for r in st.step(args.steps))
+    work = 0.0
+    iters = 0
+    for _ in range(args.steps):
+        for st in states:
+            it = st.step(1)[0]["iters"]
+            iters += it
+            work += st.nf * it
     t = time.perf_counter() - t0
-    value = st.nf * iters / t
+    value = work / t
     cores = oracle.num_threads()
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jittered lattice, exact TGV field)",
-        "config": dict(WORKLOAD, precision="FP64 CPU oracle", parallelism=f"openmp{cores}"),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lattice, closed-form initial field)",
+        "config": dict(wcfg, precision="FP64 CPU oracle", parallelism=f"openmp{cores}"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} real steps after {args.warmup} warm-up steps ({iters} "
                                    f"pseudo-iterations)"},

@@ -136,6 +136,26 @@ int dtsph_set_boundary(dtsph_ctx *ctx, int64_t nw, const double *x, const double
  * device log read by dtsph_read_stats. */
 int dtsph_step(dtsph_ctx *ctx, int32_t nsteps);
 
+/* Batches: one context advancing ninst independent simulations together (each
+ * with its own particles, parameters, walls and pseudo-time loop; they share dim,
+ * precision, graph and lanes). Every step runs all instances in the same
+ * launches; an instance whose loop has stopped skips the remaining iterations.
+ * Results of an instance are bit-identical to running it alone. Fields read back
+ * concatenate the instances' fluid particles in instance order.
+ * dtsph_batch_create: params points to ninst parameter sets (1 <= ninst <= 65535). */
+int dtsph_batch_create(int32_t ninst, const dtsph_params *params, void *stream, dtsph_ctx **out);
+
+/* Walls of instance inst (as dtsph_set_boundary). Call before dtsph_batch_set_particles. */
+int dtsph_batch_set_boundary(dtsph_ctx *ctx, int32_t inst, int64_t nw, const double *x, const double *v_wall);
+
+/* Fluid state of every instance: nf[i] particles for instance i; x, v, p and
+ * v_prev (NULL: = v) hold the instances one after the other (host arrays). */
+int dtsph_batch_set_particles(dtsph_ctx *ctx, const int64_t *nf, const double *x, const double *v,
+                              const double *p, const double *v_prev);
+
+/* dtsph_read_stats for instance inst. */
+int dtsph_batch_read_stats(dtsph_ctx *ctx, int32_t inst, int64_t first, int32_t count, dtsph_step_stats *out);
+
 /* Waits for the stream, then reports a device-side error of the steps enqueued
  * so far (DTSPH_E_CAPACITY, DTSPH_E_DOMAIN) or DTSPH_OK. */
 int dtsph_sync(dtsph_ctx *ctx);

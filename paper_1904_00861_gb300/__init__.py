@@ -72,6 +72,10 @@ _SIGS = [
     ("dtsph_get_neighbors", C.c_int, [_VP, C.c_int64, _I64P, C.c_int64, _I64P]),
     ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
     ("dtsph_tuning", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    ("dtsph_batch_create", C.c_int, [C.c_int32, C.POINTER(dtsph_params), _VP, C.POINTER(_VP)]),
+    ("dtsph_batch_set_boundary", C.c_int, [_VP, C.c_int32, C.c_int64, _VP, _VP]),
+    ("dtsph_batch_set_particles", C.c_int, [_VP, _I64P, _VP, _VP, _VP, _VP]),
+    ("dtsph_batch_read_stats", C.c_int, [_VP, C.c_int32, C.c_int64, C.c_int32, C.POINTER(dtsph_step_stats)]),
     ("dtsph_kernel_launches", C.c_int64, [_VP]),
     ("dtsph_eval_rates_noalloc", C.c_int, [C.POINTER(dtsph_params), C.c_int64, _VP, _VP, _VP, C.c_int64, _VP, _VP,
                                            _VP, _VP, _VP]),
@@ -159,6 +163,35 @@ def dtsph_create(params: dtsph_params, stream=None) -> int:
     out = C.c_void_p()
     _check(None, lib().dtsph_create(C.byref(params), stream, C.byref(out)))
     return out.value
+
+
+def dtsph_batch_create(params_list, stream=None) -> int:
+    """Context of len(params_list) independent instances advanced together."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    arr = (dtsph_params * len(params_list))(*params_list)
+    out = C.c_void_p()
+    _check(None, lib().dtsph_batch_create(len(params_list), arr, stream, C.byref(out)))
+    return out.value
+
+
+def dtsph_batch_set_boundary(ctx, inst, x, v_wall=None) -> None:
+    x = _host(x)
+    vw = None if v_wall is None else _host(v_wall)
+    _check(ctx, lib().dtsph_batch_set_boundary(ctx, int(inst), x.shape[0], _ptr(x), _ptr(vw)))
+
+
+def dtsph_batch_set_particles(ctx, nf, x, v, p, v_prev=None) -> None:
+    nf = np.ascontiguousarray(nf, dtype=np.int64)
+    x, v, p = _host(x), _host(v), _host(p)
+    vp = None if v_prev is None else _host(v_prev)
+    _check(ctx, lib().dtsph_batch_set_particles(ctx, nf.ctypes.data_as(_I64P), _ptr(x), _ptr(v), _ptr(p), _ptr(vp)))
+
+
+def dtsph_batch_read_stats(ctx, inst: int, first: int, count: int):
+    buf = (dtsph_step_stats * max(count, 1))()
+    _check(ctx, lib().dtsph_batch_read_stats(ctx, int(inst), int(first), int(count), buf))
+    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv) for b in buf[:count]]
 
 
 def dtsph_destroy(ctx) -> None:
@@ -268,11 +301,62 @@ def dtsph_last_error(ctx) -> str:
 
 # ------------------------------------------------------------ convenience
 
+class Batch:
+    """Owns one batch context: ``Batch([cfg0, cfg1, ...], precision=...)``, then
+    ``set_state(list_of_instance_dicts)`` (each with x, v, p, v_prev, nf and
+    optional vw walls appended after the fluid in x) and ``step(n)``."""
+
+    def __init__(self, cfgs, precision: int = DTSPH_FP64, stream=None, graph: int = 2, **over):
+        self.cfgs = [dict(c) for c in cfgs]
+        self.dim = int(cfgs[0]["dim"])
+        self.params = [make_params(c, precision=precision, graph=graph, **over) for c in cfgs]
+        self.ctx = dtsph_batch_create(self.params, stream)
+        self.nfs = []
+
+    def close(self):
+        if self.ctx:
+            dtsph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, insts):
+        for i, d in enumerate(insts):
+            nf = d["nf"]
+            if len(d["x"]) > nf:
+                dtsph_batch_set_boundary(self.ctx, i, d["x"][nf:], d.get("vw"))
+        self.nfs = [d["nf"] for d in insts]
+        cat = lambda k: np.concatenate([np.asarray(d[k], np.float64)[: d["nf"]] for d in insts])
+        vp = None if any(d.get("v_prev") is None for d in insts) else cat("v_prev")
+        dtsph_batch_set_particles(self.ctx, self.nfs, cat("x"), cat("v"), cat("p"), vp)
+
+    def step(self, nsteps: int = 1):
+        dtsph_step(self.ctx, nsteps)
+
+    def sync(self):
+        dtsph_sync(self.ctx)
+
+    def stats(self, inst: int, first=0, count=None):
+        n = dtsph_step_count(self.ctx)
+        count = n - first if count is None else count
+        return dtsph_batch_read_stats(self.ctx, inst, first, count)
+
+    def field(self, which: int):
+        """One array per instance."""
+        comps = 1 if which == FIELD_P else self.dim
+        allv = dtsph_read_field(self.ctx, which, sum(self.nfs), comps)
+        return np.split(allv, np.cumsum(self.nfs)[:-1])
+
+
 class Simulation:
     """Owns one context. ``Simulation(cfg, precision=DTSPH_FP32C)`` then
     ``set_state(x, v, p, v_prev, walls=(xw, vw))`` and ``step(n)``."""
 
-    def __init__(self, cfg: dict, precision: int = DTSPH_FP64, stream=None, graph: int = 1, **over):
+    def __init__(self, cfg: dict, precision: int = DTSPH_FP64, stream=None, graph: int = 2, **over):
         self.cfg = dict(cfg)
         self.dim = int(cfg["dim"])
         self.params = make_params(cfg, precision=precision, graph=graph, **over)

@@ -1,13 +1,14 @@
-// C ABI of the library (include/dtsph.h): context, device memory, the per-step
-// launch sequence, its CUDA-graph capture, and field read-back.
+// C ABI of the library (include/dtsph.h): contexts of one or more independent
+// instances, device memory, the per-step launch sequence, its CUDA-graph
+// capture, the autotuner, and field read-back.
 #include <algorithm>
-#include <map>
-#include <mutex>
 #include <cmath>
-#include <new>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -17,17 +18,19 @@
 using namespace dtsph;
 
 struct dtsph_ctx {
-    dtsph_params prm;
-    Geom G;
-    Phys P;
+    int ninst = 1;
+    std::vector<dtsph_params> prm;      // per instance; dim, precision, graph, lanes shared
+    std::vector<Geom> G;
+    std::vector<Phys> P;
+    std::vector<Inst> I;
     Buffers B;
     cudaStream_t stream = nullptr;      // caller stream (may be the legacy default stream)
     cudaStream_t cap = nullptr;         // private stream used for graph capture
     int device = 0;
     bool have_particles = false;
     bool have_nbrs = false;             // dtsph_build_neighbors lists in order B
-    int64_t nw_pending = 0;
-    std::vector<double> xw_host, vw_host;
+    std::vector<std::vector<double>> xw_host, vw_host;   // walls per instance
+    std::vector<int64_t> nf_set;        // fluid particles per instance of the current allocation
     int64_t steps = 0;
     int64_t launches = 0;
     int per_step_fixed = 0;             // kernels per step outside the loop
@@ -36,7 +39,6 @@ struct dtsph_ctx {
     cudaGraph_t graph = nullptr;
     std::string err;
     std::vector<void *> allocs;
-    int nblk = 0;
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
     bool tuned = false;
     int loop_grid = 0;
@@ -101,10 +103,8 @@ double quintic_sigma(int dim, double h)
     return dim == 2 ? 7.0 / (478.0 * pi() * h * h) : 1.0 / (120.0 * pi() * h * h * h);
 }
 
-int setup_geometry(dtsph_ctx *c)
+int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
 {
-    const dtsph_params &p = c->prm;
-    Geom &G = c->G;
     memset(&G, 0, sizeof G);
     G.dim = p.dim;
     const double rc = 3.0 * p.h;
@@ -138,7 +138,7 @@ int setup_geometry(dtsph_ctx *c)
         G.halfL[a] = 0.5 * L;
         G.ncell *= (int)k;
     }
-    if ((long long)G.nc[0] * G.nc[1] * G.nc[2] > (1LL << 30)) return fail(c, DTSPH_E_ARG, "too many cells");
+    if ((long long)G.nc[0] * G.nc[1] * G.nc[2] > (1LL << 28)) return fail(c, DTSPH_E_ARG, "too many cells");
     G.rc2 = rc * rc;
     // FP32 band around (3h)^2: the FP32 separation from cell offsets is accurate
     // to a few 1e-7 h, so outside +-2e-5 relative the FP32 test decides
@@ -147,10 +147,8 @@ int setup_geometry(dtsph_ctx *c)
     return DTSPH_OK;
 }
 
-void setup_phys(dtsph_ctx *c)
+void setup_phys(const dtsph_params &p, Phys &P)
 {
-    const dtsph_params &p = c->prm;
-    Phys &P = c->P;
     memset(&P, 0, sizeof P);
     P.h = p.h;
     P.m = p.m;
@@ -201,13 +199,17 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
 }
 
 // Autotuner results: lanes per particle of the iterate kernel, keyed by
-// (dim, precision, particle count), shared by every context of the process.
+// (dim, precision, slots, instances), shared by every context of the process.
 struct TuneKey {
     int dim, prec;
     int64_t n;
+    int ninst;
     bool operator<(const TuneKey &o) const
     {
-        return dim != o.dim ? dim < o.dim : prec != o.prec ? prec < o.prec : n < o.n;
+        if (dim != o.dim) return dim < o.dim;
+        if (prec != o.prec) return prec < o.prec;
+        if (n != o.n) return n < o.n;
+        return ninst < o.ninst;
     }
 };
 std::map<TuneKey, int> &tune_cache()
@@ -217,10 +219,15 @@ std::map<TuneKey, int> &tune_cache()
 }
 std::mutex tune_mu;
 
+TuneKey tune_key(const dtsph_ctx *c, int64_t n)
+{
+    return TuneKey{c->prm[0].dim, c->prm[0].precision, n, c->ninst};
+}
+
 int tuned_lanes(dtsph_ctx *c, int64_t n)
 {
     std::lock_guard<std::mutex> g(tune_mu);
-    auto it = tune_cache().find(TuneKey{c->prm.dim, c->prm.precision, n});
+    auto it = tune_cache().find(tune_key(c, n));
     if (it == tune_cache().end()) return 4;
     c->tuned = true;
     return it->second;
@@ -236,30 +243,62 @@ int neighbour_capacity(const dtsph_params &p)
     return std::min(std::max(k, 8), 4096);
 }
 
-int allocate(dtsph_ctx *c, int64_t nf, int64_t nw)
+// Device memory for nf[i] fluid particles per instance plus the walls set so far.
+int allocate(dtsph_ctx *c, const int64_t *nf)
 {
     free_all(c);
     Buffers &B = c->B;
-    const int64_t n64 = nf + nw;
-    if (n64 <= 0 || n64 >= (1LL << 31) - 64) return fail(c, DTSPH_E_ARG, "particle count out of range");
-    const int n = (int)n64;
-    const int d = c->prm.dim;
+    const int ni = c->ninst;
+    c->I.assign(ni, Inst{});
+    int64_t slot = 0, fo = 0, wo = 0, co = 0;
+    int K = 0;
+    for (int i = 0; i < ni; ++i) {
+        if (nf[i] <= 0) return fail(c, DTSPH_E_ARG, "instance %d: nf must be positive", i);
+        const int64_t nw = (int64_t)(c->xw_host[i].size() / c->prm[i].dim);
+        Inst &I = c->I[i];
+        slot = (slot + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
+        I.slot_off = (int)slot;
+        I.nf = (int)nf[i];
+        I.nw = (int)nw;
+        I.foff = (int)fo;
+        I.woff = (int)wo;
+        I.cell_off = (int)co;
+        slot += nf[i] + nw;
+        fo += nf[i];
+        wo += nw;
+        co += c->G[i].ncell + 1;   // one empty sentinel cell per instance
+        K = std::max(K, neighbour_capacity(c->prm[i]));
+        if (slot >= (1LL << 31) - 4 * kSlotAlign || co >= (1LL << 31) - 2)
+            return fail(c, DTSPH_E_ARG, "particle or cell count out of range");
+        c->P[i].rp_scale = c->P[i].dt / (c->P[i].rho0 * c->P[i].c * c->P[i].c) / (double)nf[i];
+        c->P[i].rv_scale = c->P[i].dt / c->prm[i].v_ref / (double)nf[i];
+    }
+    const int n = (int)((slot + kSlotAlign - 1) / kSlotAlign * kSlotAlign);
+    const int d = c->prm[0].dim;
     B.n = n;
-    B.nf = (int)nf;
-    B.nw = (int)nw;
+    B.nf = (int)fo;
+    B.nw = (int)wo;
     B.dim = d;
-    B.fp32c = c->prm.precision == DTSPH_FP32C;
-    B.K = neighbour_capacity(c->prm);
-    B.lanes = c->prm.lanes > 0 ? c->prm.lanes : tuned_lanes(c, nf + nw);
+    B.fp32c = c->prm[0].precision == DTSPH_FP32C;
+    B.K = K;
+    B.ninst = ni;
+    B.ncell = (int)co;
+    B.lanes = c->prm[0].lanes > 0 ? c->prm[0].lanes : tuned_lanes(c, n);
     const size_t nd = (size_t)n * d;
     const size_t nwarps = ((size_t)n + kWarp - 1) / kWarp;
     const size_t npair = nwarps * B.K * kWarp;
+    Inst *d_inst;
+    Geom *d_geo;
+    Phys *d_phys;
+    uint16_t *d_inst_of;
     int r;
 #define A(p, cnt) if ((r = dalloc(c, &(p), (cnt))) != DTSPH_OK) { free_all(c); return r; }
+    A(d_inst, ni) A(d_geo, ni) A(d_phys, ni) A(d_inst_of, n)
     A(B.gid_a, n) A(B.x_a, nd) A(B.xp_a, nd) A(B.vn_a, nd) A(B.vnm1_a, nd) A(B.pn_a, n) A(B.s_a, nd) A(B.cell_a, n)
     A(B.gid_b, n) A(B.x_b, nd) A(B.vn_b, nd) A(B.vnm1_b, nd) A(B.pn_b, n) A(B.xp_b, nd) A(B.v0_b, nd)
     A(B.ph0_b, n) A(B.s_b, nd) A(B.cell_b, n)
-    A(B.key, n) A(B.slot, n) A(B.unsorted, n) A(B.perm, n) A(B.cell_count, c->G.ncell) A(B.cell_start, (size_t)c->G.ncell + 1)
+    A(B.key, n) A(B.slot, n) A(B.unsorted, n) A(B.perm, n) A(B.cell_count, (size_t)B.ncell)
+    A(B.cell_start, (size_t)B.ncell + 1)
     A(B.vk[0], nd) A(B.vk[1], nd)
     A(B.pcount, n) A(B.pj, npair)
     if (B.fp32c) {
@@ -268,25 +307,45 @@ int allocate(dtsph_ctx *c, int64_t nf, int64_t nw)
         A(B.nb64[0], n) A(B.nb64[1], n) A(B.pc64, npair)
     }
     A(B.ap_b, n) A(B.f_b, nd)
-    c->nblk = (n + kWarp - 1) / kWarp;   // tiles of the iterate kernel at 8 lanes, the most
-    // two residual partials per tile, double-buffered by the persistent loop
-    A(B.blk, 4 * (size_t)c->nblk) A(B.ls, 1) A(B.stats, kStatRing) A(B.err, 1)
+    // two residual partials per tile (at most one tile per warp of slots),
+    // double-buffered by the persistent loop
+    A(B.blk, 4 * nwarps) A(B.ls, ni) A(B.ctrl, 1) A(B.stats, (size_t)kStatRing * ni) A(B.err, 1)
 #undef A
-    CK(cudaMemsetAsync(B.cell_count, 0, sizeof(int) * c->G.ncell, c->stream));
-    CK(cudaMemsetAsync(B.err, 0, sizeof(uint32_t), c->stream));
-    CK(cudaMemsetAsync(B.pcount, 0, sizeof(int) * n, c->stream));
-    LoopState L;
-    memset(&L, 0, sizeof L);
-    L.reason = -1;
-    L.max_iter = c->prm.max_iter;
-    L.fixed_iters = c->prm.fixed_iters;
-    L.stag_window = c->prm.stag_window;
-    L.eps = c->prm.eps;
-    L.stag_tol = c->prm.stag_tol;
-    CK(cudaMemcpyAsync(B.ls, &L, sizeof L, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    c->P.rp_scale = c->P.dt / (c->P.rho0 * c->P.c * c->P.c) / (double)nf;
-    c->P.rv_scale = c->P.dt / c->prm.v_ref / (double)nf;
+    B.inst = d_inst;
+    B.geo = d_geo;
+    B.phys = d_phys;
+    B.inst_of = d_inst_of;
+    std::vector<uint16_t> inst_of(n);
+    for (int i = 0; i < ni; ++i) {
+        const int lo = c->I[i].slot_off;
+        const int hi = i + 1 < ni ? c->I[i + 1].slot_off : n;
+        for (int s = lo; s < hi; ++s) inst_of[s] = (uint16_t)i;
+    }
+    std::vector<LoopState> ls(ni);
+    for (int i = 0; i < ni; ++i) {
+        LoopState &L = ls[i];
+        memset(&L, 0, sizeof L);
+        L.reason = -1;
+        L.max_iter = c->prm[i].max_iter;
+        L.fixed_iters = c->prm[i].fixed_iters;
+        L.stag_window = c->prm[i].stag_window;
+        L.eps = c->prm[i].eps;
+        L.stag_tol = c->prm[i].stag_tol;
+    }
+    CK(cudaMemcpy(d_inst, c->I.data(), sizeof(Inst) * ni, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_geo, c->G.data(), sizeof(Geom) * ni, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_phys, c->P.data(), sizeof(Phys) * ni, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_inst_of, inst_of.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(B.ls, ls.data(), sizeof(LoopState) * ni, cudaMemcpyHostToDevice));
+    CK(cudaMemset(B.ctrl, 0, sizeof(LoopCtrl)));
+    CK(cudaMemset(B.cell_count, 0, sizeof(int) * B.ncell));
+    CK(cudaMemset(B.err, 0, sizeof(uint32_t)));
+    CK(cudaMemset(B.pcount, 0, sizeof(int) * n));
+    // padding slots of the permutations are never written: -1 marks them
+    CK(cudaMemset(B.unsorted, 0xff, sizeof(int) * n));
+    CK(cudaMemset(B.perm, 0xff, sizeof(int) * n));
+    CK(cudaDeviceSynchronize());
+    c->nf_set.assign(nf, nf + ni);
     return DTSPH_OK;
 }
 
@@ -297,23 +356,23 @@ int enqueue_pre_loop(dtsph_ctx *c, cudaStream_t st)
 {
     const Buffers &B = c->B;
     int k = 0;
-    k += launch_binning(B, c->G, B.x_a, B.gid_a, st);          // cells at r^n
-    k += launch_permute_a_to_b(B, c->G, st);
-    k += launch_state_n(B, c->G, c->P, true, st);              // walls, rates, predictor
-    k += launch_binning(B, c->G, B.xp_b, B.gid_b, st);         // cells at r^0
-    k += launch_permute_b_to_a(B, c->G, st);
-    k += launch_pair_cache(B, c->G, c->P, B.xp_a, B.cell_a, B.gid_a, st);   // also resets the loop state
+    k += launch_binning(B, B.x_a, B.gid_a, st);          // cells at r^n
+    k += launch_permute_a_to_b(B, st);
+    k += launch_state_n(B, true, st);                     // walls, rates, predictor
+    k += launch_binning(B, B.xp_b, B.gid_b, st);         // cells at r^0
+    k += launch_permute_b_to_a(B, st);
+    k += launch_pair_cache(B, B.xp_a, B.cell_a, B.gid_a, st);   // also resets the loop state
     return k;
 }
 
 int enqueue_iteration(dtsph_ctx *c, cudaStream_t st, unsigned long long cond, int use_cond)
 {
-    int k = launch_walls_iter(c->B, c->G, c->P, st);
-    k += launch_iterate(c->B, c->G, c->P, cond, use_cond, st);
+    int k = launch_walls_iter(c->B, st);
+    k += launch_iterate(c->B, cond, use_cond, st);
     return k;
 }
 
-int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st) { return launch_outer(c->B, c->G, c->P, st); }
+int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st) { return launch_outer(c->B, st); }
 
 // Graph of one real step with the persistent loop: pre-loop kernels -> one
 // cooperative loop kernel -> outer.
@@ -327,7 +386,7 @@ int build_graph_persistent(dtsph_ctx *c)
     c->graph = g;
     CK(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     c->per_step_fixed = enqueue_pre_loop(c, c->cap);
-    cudaError_t e = launch_loop(c->B, c->P, grid, c->cap);
+    cudaError_t e = launch_loop(c->B, grid, c->cap);
     c->per_step_fixed += 1 + enqueue_post_loop(c, c->cap);
     cudaGraph_t g2 = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g2);
@@ -341,7 +400,7 @@ int build_graph_persistent(dtsph_ctx *c)
 // Graph of one real step: pre-loop kernels -> while node (walls, iterate) -> outer.
 int build_graph(dtsph_ctx *c)
 {
-    if (c->prm.graph == 2) return build_graph_persistent(c);
+    if (c->prm[0].graph == 2) return build_graph_persistent(c);
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     c->graph = g;
@@ -374,22 +433,16 @@ int build_graph(dtsph_ctx *c)
     return DTSPH_OK;
 }
 
-int read_loop_state(dtsph_ctx *c, LoopState *L)
-{
-    CK(cudaMemcpyAsync(L, c->B.ls, sizeof *L, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return DTSPH_OK;
-}
-
 // Plain launches: the loop runs in chunks of kernels that return at once when
-// the stop rule already holds; the host checks the device flag between chunks.
+// every instance has stopped; the host checks the device counter between chunks.
 int step_plain(dtsph_ctx *c)
 {
     c->per_step_fixed = enqueue_pre_loop(c, c->stream);
     c->launches += c->per_step_fixed;
-    const int cap = c->prm.fixed_iters > 0 ? c->prm.fixed_iters : c->prm.max_iter;
+    int cap = 1;
+    for (const auto &p : c->prm) cap = std::max(cap, p.fixed_iters > 0 ? p.fixed_iters : p.max_iter);
     int issued = 0;
-    LoopState L;
+    LoopCtrl ctrl;
     while (true) {
         const int chunk = 8;
         for (int i = 0; i < chunk; ++i) {
@@ -397,9 +450,9 @@ int step_plain(dtsph_ctx *c)
             c->launches += c->per_iter;
         }
         issued += chunk;
-        int r = read_loop_state(c, &L);
-        if (r) return r;
-        if (L.done) break;
+        CK(cudaMemcpyAsync(&ctrl, c->B.ctrl, sizeof ctrl, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (ctrl.active == 0) break;
         if (issued > cap + 16) return fail(c, DTSPH_E_STATE, "pseudo-time loop did not stop");
     }
     c->launches += enqueue_post_loop(c, c->stream);
@@ -407,7 +460,17 @@ int step_plain(dtsph_ctx *c)
     return DTSPH_OK;
 }
 
-int device_error(dtsph_ctx *c);
+int device_error(dtsph_ctx *c)
+{
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, c->B.err, sizeof e, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e & kErrCapacity)
+        return fail(c, DTSPH_E_CAPACITY, "a particle had more than %d neighbours (raise max_neighbors)", c->B.K);
+    if (e & kErrDomain) return fail(c, DTSPH_E_DOMAIN, "a particle left the box of a non-periodic axis");
+    if (e & kErrBarrier) return fail(c, DTSPH_E_TIMEOUT, "a grid barrier of the persistent loop timed out");
+    return DTSPH_OK;
+}
 
 // Mean duration of `launches` launches of the iterate kernel on the frozen pair
 // cache of the last step (each after a loop reset, bracketed by events).
@@ -419,7 +482,7 @@ int probe_ms(dtsph_ctx *c, int launches, float *out)
     for (int i = 0; i < launches; ++i) {
         launch_loop_reset(B, c->stream);
         CK(cudaEventRecord(ev[2 * i], c->stream));
-        launch_iterate(B, c->G, c->P, 0ull, 0, c->stream);
+        launch_iterate(B, 0ull, 0, c->stream);
         CK(cudaEventRecord(ev[2 * i + 1], c->stream));
     }
     c->launches += 2 * launches;
@@ -449,9 +512,9 @@ int autotune(dtsph_ctx *c)
     CK(cudaMemsetAsync(B.s_a, 0, nd * sizeof(double), c->stream));
     if (B.fp32c) CK(cudaMemsetAsync(B.nb32[0], 0, (size_t)B.n * sizeof(float4), c->stream));
     else CK(cudaMemsetAsync(B.nb64[0], 0, (size_t)B.n * sizeof(double4_32a), c->stream));
-    c->launches += launch_binning(B, c->G, B.x_a, B.gid_a, c->stream);
-    c->launches += launch_permute_a_to_b(B, c->G, c->stream);
-    c->launches += launch_pair_cache(B, c->G, c->P, B.x_b, B.cell_b, B.gid_b, c->stream);
+    c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
+    c->launches += launch_permute_a_to_b(B, c->stream);
+    c->launches += launch_pair_cache(B, B.x_b, B.cell_b, B.gid_b, c->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     int best = c->B.lanes;
@@ -473,67 +536,66 @@ int autotune(dtsph_ctx *c)
     c->tuned = true;
     {
         std::lock_guard<std::mutex> g(tune_mu);
-        tune_cache()[TuneKey{c->prm.dim, c->prm.precision, (int64_t)c->B.n}] = best;
+        tune_cache()[tune_key(c, c->B.n)] = best;
     }
     return device_error(c);
 }
 
-int device_error(dtsph_ctx *c)
-{
-    uint32_t e = 0;
-    CK(cudaMemcpyAsync(&e, c->B.err, sizeof e, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (e & kErrCapacity)
-        return fail(c, DTSPH_E_CAPACITY, "a particle had more than %d neighbours (raise max_neighbors)", c->B.K);
-    if (e & kErrDomain) return fail(c, DTSPH_E_DOMAIN, "a particle left the box of a non-periodic axis");
-    if (e & kErrBarrier) return fail(c, DTSPH_E_TIMEOUT, "a grid barrier of the persistent loop timed out");
-    return DTSPH_OK;
-}
-
-int set_particles_impl(dtsph_ctx *c, int64_t nf, const double *x, const double *v, const double *p,
+int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const double *v, const double *p,
                        const double *vprev, bool device)
 {
-    if (!x || !v || !p) return fail(c, DTSPH_E_ARG, "x, v and p are required");
-    if (nf <= 0) return fail(c, DTSPH_E_ARG, "nf must be positive");
+    if (!x || !v || !p || !nf) return fail(c, DTSPH_E_ARG, "x, v and p are required");
     CK(cudaSetDevice(c->device));
     int r;
-    const int d = c->prm.dim;
-    const bool reuse = c->have_particles && c->B.nf == nf && c->B.nw == c->nw_pending;
+    const int d = c->prm[0].dim;
+    const int ni = c->ninst;
+    int64_t NF = 0, NW = 0;
+    for (int i = 0; i < ni; ++i) {
+        if (nf[i] <= 0) return fail(c, DTSPH_E_ARG, "instance %d: nf must be positive", i);
+        NF += nf[i];
+        NW += (int64_t)(c->xw_host[i].size() / d);
+    }
+    const bool reuse = c->have_particles && c->nf_set.size() == (size_t)ni &&
+                       std::equal(c->nf_set.begin(), c->nf_set.end(), nf) && c->B.nw == NW;
     if (!reuse) {
-        if ((r = allocate(c, nf, c->nw_pending))) return r;
+        if ((r = allocate(c, nf))) return r;
         // staging buffers for the AoS inputs, kept for later calls of the same size
-        if ((r = dalloc(c, &c->sx, (size_t)nf * d)) || (r = dalloc(c, &c->sv, (size_t)nf * d)) ||
-            (r = dalloc(c, &c->sp, nf)) || (r = dalloc(c, &c->svp, (size_t)nf * d)))
+        if ((r = dalloc(c, &c->sx, (size_t)NF * d)) || (r = dalloc(c, &c->sv, (size_t)NF * d)) ||
+            (r = dalloc(c, &c->sp, NF)) || (r = dalloc(c, &c->svp, (size_t)NF * d)) ||
+            (r = dalloc(c, &c->sxw, (size_t)std::max<int64_t>(NW, 1) * d)) ||
+            (r = dalloc(c, &c->svw, (size_t)std::max<int64_t>(NW, 1) * d)))
             return r;
-        if (c->nw_pending > 0 &&
-            ((r = dalloc(c, &c->sxw, c->xw_host.size())) || (r = dalloc(c, &c->svw, c->vw_host.size()))))
-            return r;
+        if (NW > 0) {
+            std::vector<double> xw, vw;
+            for (int i = 0; i < ni; ++i) {
+                xw.insert(xw.end(), c->xw_host[i].begin(), c->xw_host[i].end());
+                vw.insert(vw.end(), c->vw_host[i].begin(), c->vw_host[i].end());
+            }
+            CK(cudaMemcpy(c->sxw, xw.data(), xw.size() * sizeof(double), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->svw, vw.data(), vw.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
     }
-    const size_t bx = (size_t)nf * d * sizeof(double), bp = (size_t)nf * sizeof(double);
-    double *sx = c->sx, *sv = c->sv, *sp = c->sp, *svp = vprev ? c->svp : nullptr;
-    double *sxw = c->nw_pending > 0 ? c->sxw : nullptr, *svw = c->nw_pending > 0 ? c->svw : nullptr;
+    const size_t bx = (size_t)NF * d * sizeof(double), bp = (size_t)NF * sizeof(double);
+    double *svp = vprev ? c->svp : nullptr;
+    double *sxw = NW > 0 ? c->sxw : nullptr, *svw = NW > 0 ? c->svw : nullptr;
     const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(sx, x, bx, kind, c->stream));
-    CK(cudaMemcpyAsync(sv, v, bx, kind, c->stream));
-    CK(cudaMemcpyAsync(sp, p, bp, kind, c->stream));
+    CK(cudaMemcpyAsync(c->sx, x, bx, kind, c->stream));
+    CK(cudaMemcpyAsync(c->sv, v, bx, kind, c->stream));
+    CK(cudaMemcpyAsync(c->sp, p, bp, kind, c->stream));
     if (vprev) CK(cudaMemcpyAsync(svp, vprev, bx, kind, c->stream));
-    if (c->nw_pending > 0 && !reuse) {
-        CK(cudaMemcpyAsync(sxw, c->xw_host.data(), c->xw_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(svw, c->vw_host.data(), c->vw_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    }
-    c->launches += launch_scatter_in(c->B, sx, sv, sp, svp, sxw, svw, c->stream);
+    c->launches += launch_scatter_in(c->B, c->sx, c->sv, c->sp, svp, sxw, svw, c->stream);
     // a new state restarts the step log and clears device-side error flags
-    CK(cudaMemsetAsync(&c->B.ls->step, 0, sizeof(long long), c->stream));
+    for (int i = 0; i < ni; ++i) CK(cudaMemsetAsync(&c->B.ls[i].step, 0, sizeof(long long), c->stream));
     CK(cudaMemsetAsync(c->B.err, 0, sizeof(uint32_t), c->stream));
     CK(cudaGetLastError());
     if (!device) CK(cudaStreamSynchronize(c->stream));   // host arrays may be reused once we return
     c->have_particles = true;
     c->steps = 0;
-    if (!c->tuned && c->prm.lanes == 0) {
+    if (!c->tuned && c->prm[0].lanes == 0) {
         r = autotune(c);
         if (r) return r;
     }
-    if (c->prm.graph && !c->exec) {
+    if (c->prm[0].graph && !c->exec) {
         r = build_graph(c);
         if (r) return r;
     }
@@ -571,6 +633,74 @@ int read_field_impl(dtsph_ctx *c, int32_t field, double *out, bool device)
     return DTSPH_OK;
 }
 
+int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_ctx **out)
+{
+    if (!params || !out || ninst < 1 || ninst > 65535) return DTSPH_E_ARG;
+    *out = nullptr;
+    dtsph_ctx *c = new (std::nothrow) dtsph_ctx();
+    if (!c) return DTSPH_E_OOM;
+    c->ninst = ninst;
+    c->prm.assign(params, params + ninst);
+    c->G.resize(ninst);
+    c->P.resize(ninst);
+    c->xw_host.resize(ninst);
+    c->vw_host.resize(ninst);
+    for (int i = 0; i < ninst; ++i) {
+        int r = validate(c, &params[i]);
+        if (!r && (params[i].dim != params[0].dim || params[i].precision != params[0].precision ||
+                   params[i].graph != params[0].graph || params[i].lanes != params[0].lanes))
+            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph and lanes");
+        if (!r) r = setup_geometry(c, params[i], c->G[i]);
+        if (r) {
+            delete c;
+            return r;
+        }
+        setup_phys(params[i], c->P[i]);
+    }
+    memset(&c->B, 0, sizeof c->B);
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return DTSPH_E_CUDA;
+    }
+    *out = c;
+    return DTSPH_OK;
+}
+
+int set_boundary_impl(dtsph_ctx *c, int32_t inst, int64_t nw, const double *x, const double *v_wall)
+{
+    if (inst < 0 || inst >= c->ninst) return fail(c, DTSPH_E_ARG, "instance %d out of range", inst);
+    if (nw < 0 || (nw > 0 && !x)) return fail(c, DTSPH_E_ARG, "bad wall arrays");
+    const int d = c->prm[inst].dim;
+    c->xw_host[inst].assign(x, x + (size_t)nw * d);
+    if (v_wall) c->vw_host[inst].assign(v_wall, v_wall + (size_t)nw * d);
+    else c->vw_host[inst].assign((size_t)nw * d, 0.0);
+    free_all(c);   // walls change the particle set: particles must be set again
+    return DTSPH_OK;
+}
+
+int read_stats_impl(dtsph_ctx *c, int32_t inst, int64_t first, int32_t count, dtsph_step_stats *out)
+{
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
+    if (inst < 0 || inst >= c->ninst) return fail(c, DTSPH_E_ARG, "instance %d out of range", inst);
+    if (count < 0 || (count > 0 && !out) || first < 0 || first + count > c->steps)
+        return fail(c, DTSPH_E_ARG, "steps [%lld, %lld) not taken (taken: %lld)", (long long)first,
+                    (long long)(first + count), (long long)c->steps);
+    if (c->steps - first > kStatRing) return fail(c, DTSPH_E_ARG, "step %lld no longer in the log", (long long)first);
+    for (int32_t i = 0; i < count; ++i) {
+        StatRec r;
+        const size_t at = (size_t)((first + i) % kStatRing) * c->ninst + inst;
+        CK(cudaMemcpyAsync(&r, c->B.stats + at, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        out[i].iters = r.iters;
+        out[i].reason = r.reason;
+        out[i].rp = r.rp;
+        out[i].rv = r.rv;
+    }
+    return DTSPH_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -583,30 +713,12 @@ const char *dtsph_last_error(const dtsph_ctx *c) { return c ? c->err.c_str() : k
 
 int dtsph_create(const dtsph_params *params, void *stream, dtsph_ctx **out)
 {
-    if (!params || !out) return DTSPH_E_ARG;
-    *out = nullptr;
-    dtsph_ctx *c = new (std::nothrow) dtsph_ctx();
-    if (!c) return DTSPH_E_OOM;
-    int r = validate(c, params);
-    if (r) {
-        delete c;
-        return r;
-    }
-    c->prm = *params;
-    if ((r = setup_geometry(c)) != DTSPH_OK) {
-        delete c;
-        return r;
-    }
-    setup_phys(c);
-    memset(&c->B, 0, sizeof c->B);
-    c->stream = (cudaStream_t)stream;
-    if (cudaGetDevice(&c->device) != cudaSuccess || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        delete c;
-        return DTSPH_E_CUDA;
-    }
-    *out = c;
-    return DTSPH_OK;
+    return create_impl(1, params, stream, out);
+}
+
+int dtsph_batch_create(int32_t ninst, const dtsph_params *params, void *stream, dtsph_ctx **out)
+{
+    return create_impl(ninst, params, stream, out);
 }
 
 void dtsph_destroy(dtsph_ctx *c)
@@ -623,28 +735,36 @@ void dtsph_destroy(dtsph_ctx *c)
 int dtsph_set_boundary(dtsph_ctx *c, int64_t nw, const double *x, const double *v_wall)
 {
     if (!c) return DTSPH_E_ARG;
-    if (nw < 0 || (nw > 0 && !x)) return fail(c, DTSPH_E_ARG, "bad wall arrays");
-    const int d = c->prm.dim;
-    c->nw_pending = nw;
-    c->xw_host.assign(x, x + (size_t)nw * d);
-    if (v_wall) c->vw_host.assign(v_wall, v_wall + (size_t)nw * d);
-    else c->vw_host.assign((size_t)nw * d, 0.0);
-    free_all(c);   // walls change the particle set: particles must be set again
-    return DTSPH_OK;
+    return set_boundary_impl(c, 0, nw, x, v_wall);
+}
+
+int dtsph_batch_set_boundary(dtsph_ctx *c, int32_t inst, int64_t nw, const double *x, const double *v_wall)
+{
+    if (!c) return DTSPH_E_ARG;
+    return set_boundary_impl(c, inst, nw, x, v_wall);
 }
 
 int dtsph_set_particles(dtsph_ctx *c, int64_t nf, const double *x, const double *v, const double *p,
                         const double *v_prev)
 {
     if (!c) return DTSPH_E_ARG;
-    return set_particles_impl(c, nf, x, v, p, v_prev, false);
+    if (c->ninst != 1) return fail(c, DTSPH_E_ARG, "a batch context takes dtsph_batch_set_particles");
+    return set_particles_impl(c, &nf, x, v, p, v_prev, false);
 }
 
 int dtsph_set_particles_device(dtsph_ctx *c, int64_t nf, const double *x, const double *v, const double *p,
                                const double *v_prev)
 {
     if (!c) return DTSPH_E_ARG;
-    return set_particles_impl(c, nf, x, v, p, v_prev, true);
+    if (c->ninst != 1) return fail(c, DTSPH_E_ARG, "a batch context takes dtsph_batch_set_particles");
+    return set_particles_impl(c, &nf, x, v, p, v_prev, true);
+}
+
+int dtsph_batch_set_particles(dtsph_ctx *c, const int64_t *nf, const double *x, const double *v, const double *p,
+                              const double *v_prev)
+{
+    if (!c) return DTSPH_E_ARG;
+    return set_particles_impl(c, nf, x, v, p, v_prev, false);
 }
 
 int dtsph_step(dtsph_ctx *c, int32_t nsteps)
@@ -679,22 +799,13 @@ int64_t dtsph_step_count(const dtsph_ctx *c) { return c ? c->steps : -1; }
 int dtsph_read_stats(dtsph_ctx *c, int64_t first, int32_t count, dtsph_step_stats *out)
 {
     if (!c) return DTSPH_E_ARG;
-    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
-    if (count < 0 || (count > 0 && !out) || first < 0 || first + count > c->steps)
-        return fail(c, DTSPH_E_ARG, "steps [%lld, %lld) not taken (taken: %lld)", (long long)first,
-                    (long long)(first + count), (long long)c->steps);
-    if (c->steps - first > kStatRing) return fail(c, DTSPH_E_ARG, "step %lld no longer in the log", (long long)first);
-    std::vector<StatRec> tmp(kStatRing);
-    CK(cudaMemcpyAsync(tmp.data(), c->B.stats, sizeof(StatRec) * kStatRing, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    for (int32_t i = 0; i < count; ++i) {
-        const StatRec &r = tmp[(first + i) % kStatRing];
-        out[i].iters = r.iters;
-        out[i].reason = r.reason;
-        out[i].rp = r.rp;
-        out[i].rv = r.rv;
-    }
-    return DTSPH_OK;
+    return read_stats_impl(c, 0, first, count, out);
+}
+
+int dtsph_batch_read_stats(dtsph_ctx *c, int32_t inst, int64_t first, int32_t count, dtsph_step_stats *out)
+{
+    if (!c) return DTSPH_E_ARG;
+    return read_stats_impl(c, inst, first, count, out);
 }
 
 int dtsph_read_field(dtsph_ctx *c, int32_t field, double *out)
@@ -718,9 +829,9 @@ int dtsph_eval_rates(dtsph_ctx *c, double *ap, double *F)
     if (!ap || !F) return fail(c, DTSPH_E_ARG, "ap and F are required");
     CK(cudaSetDevice(c->device));
     const Buffers &B = c->B;
-    c->launches += launch_binning(B, c->G, B.x_a, B.gid_a, c->stream);
-    c->launches += launch_permute_a_to_b(B, c->G, c->stream);
-    c->launches += launch_state_n(B, c->G, c->P, false, c->stream);
+    c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
+    c->launches += launch_permute_a_to_b(B, c->stream);
+    c->launches += launch_state_n(B, false, c->stream);
     const size_t bf = (size_t)B.nf * B.dim * sizeof(double), bp = (size_t)B.nf * sizeof(double);
     double *tmp = nullptr;
     CK(cudaMallocAsync((void **)&tmp, bf + bp, c->stream));
@@ -741,9 +852,9 @@ int dtsph_build_neighbors(dtsph_ctx *c)
     if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
     CK(cudaSetDevice(c->device));
     const Buffers &B = c->B;
-    c->launches += launch_binning(B, c->G, B.x_a, B.gid_a, c->stream);
-    c->launches += launch_permute_a_to_b(B, c->G, c->stream);
-    c->launches += launch_pair_cache(B, c->G, c->P, B.x_b, B.cell_b, B.gid_b, c->stream);
+    c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
+    c->launches += launch_permute_a_to_b(B, c->stream);
+    c->launches += launch_pair_cache(B, B.x_b, B.cell_b, B.gid_b, c->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     int r = device_error(c);
@@ -756,7 +867,8 @@ int dtsph_get_neighbors(dtsph_ctx *c, int64_t i, int64_t *out, int64_t cap, int6
     if (!c) return DTSPH_E_ARG;
     if (!c->have_nbrs) return fail(c, DTSPH_E_STATE, "call dtsph_build_neighbors first");
     const Buffers &B = c->B;
-    if (i < 0 || i >= B.n || !count || (cap > 0 && !out)) return fail(c, DTSPH_E_ARG, "bad index or output");
+    if (i < 0 || i >= (int64_t)B.nf + B.nw || !count || (cap > 0 && !out))
+        return fail(c, DTSPH_E_ARG, "bad index or output");
     std::vector<uint32_t> gid(B.n);
     CK(cudaMemcpy(gid.data(), B.gid_b, sizeof(uint32_t) * B.n, cudaMemcpyDeviceToHost));
     int s = -1;
@@ -833,15 +945,22 @@ int64_t dtsph_kernel_launches(const dtsph_ctx *c_)
     dtsph_ctx *c = const_cast<dtsph_ctx *>(c_);
     if (!c) return -1;
     if (!c->exec || c->steps == 0) return c->launches;
-    // graph steps: fixed kernels per step plus per-iteration kernels from the log
-    int64_t first = std::max<int64_t>(0, c->steps - kStatRing);
-    std::vector<StatRec> tmp(kStatRing);
-    if (cudaMemcpyAsync(tmp.data(), c->B.stats, sizeof(StatRec) * kStatRing, cudaMemcpyDeviceToHost, c->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return -1;
+    // graph steps: fixed kernels per step plus, with the while node, the
+    // per-iteration kernels of the longest instance of each step
     int64_t it = 0;
-    for (int64_t s = first; s < c->steps; ++s) it += tmp[s % kStatRing].iters;
+    if (c->per_iter > 0) {
+        const int64_t first = std::max<int64_t>(0, c->steps - kStatRing);
+        std::vector<StatRec> tmp((size_t)kStatRing * c->ninst);
+        if (cudaMemcpyAsync(tmp.data(), c->B.stats, sizeof(StatRec) * tmp.size(), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return -1;
+        for (int64_t s = first; s < c->steps; ++s) {
+            int m = 0;
+            for (int i = 0; i < c->ninst; ++i) m = std::max(m, tmp[(size_t)(s % kStatRing) * c->ninst + i].iters);
+            it += m;
+        }
+    }
     return c->launches + c->steps * c->per_step_fixed + it * c->per_iter;
 }
 

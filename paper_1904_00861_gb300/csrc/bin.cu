@@ -2,9 +2,12 @@
 // the gathers that move the particle state into the new order.
 //
 // The neighbour search of the paper (N(i) = all j with |r_ij| < 3h, Sec. 3) is
-// built on cells of side >= 3h: a counting sort by cell gives every cell a
+// built on cells of side > 3h: a counting sort by cell gives every cell a
 // contiguous slot range, and ordering each cell by caller index makes the
-// result independent of the atomic order of the count pass.
+// result independent of the atomic order of the count pass. All instances of a
+// context are binned together: instance i's cells are numbered from its
+// cell_off, and the scan places its particles at its own (tile-aligned) slot
+// range.
 #include "dtsph_internal.cuh"
 
 namespace dtsph {
@@ -26,35 +29,44 @@ __device__ __forceinline__ int cell_coord(double xa, double lo, double hi, doubl
     return k;
 }
 
-__global__ void k_bin_keys(int n, Geom G, const double *__restrict__ x, int *__restrict__ key,
-                           int *__restrict__ slot, int *__restrict__ count, uint32_t *err)
+// Cell (global index) of every particle of the source order; -1 for padding.
+__global__ void __launch_bounds__(kBlock) k_bin_keys(Buffers B, const double *__restrict__ x,
+                                                     const uint32_t *__restrict__ gid)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    if (gid[i] == kNoParticle) {
+        B.key[i] = -1;
+        return;
+    }
+    const int inst = B.inst_of[i];
+    const Geom &G = B.geo[inst];
     int c = 0, mult = 1;
     for (int a = 0; a < G.dim; ++a) {
-        int k = cell_coord(x[(size_t)a * n + i], G.lo[a], G.hi[a], G.inv_s[a], G.nc[a], G.periodic[a], err);
+        int k = cell_coord(x[(size_t)a * B.n + i], G.lo[a], G.hi[a], G.inv_s[a], G.nc[a], G.periodic[a], B.err);
         c += k * mult;
         mult *= G.nc[a];
     }
-    key[i] = c;
-    slot[i] = atomicAdd(&count[c], 1);
+    c += B.inst[inst].cell_off;
+    B.key[i] = c;
+    B.slot[i] = atomicAdd(&B.cell_count[c], 1);
 }
 
-// Exclusive scan of the per-cell counts by one block; clears the counts for the
-// next binning. Thread t owns a contiguous chunk of cells.
+// Exclusive scan of the per-cell counts by one block, shifted so that each
+// instance's particles start at its slot_off; clears the counts for the next
+// binning. Thread t owns a contiguous chunk of cells.
 constexpr int kScanThreads = 1024;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_counts(int ncell, int *__restrict__ count,
-                                                              int *__restrict__ start)
+__global__ void __launch_bounds__(kScanThreads) k_scan_counts(Buffers B)
 {
     __shared__ int part[kScanThreads];
-    int t = threadIdx.x;
-    int chunk = (ncell + kScanThreads - 1) / kScanThreads;
-    int b = t * chunk;
-    int e = min(b + chunk, ncell);
+    const int ncell = B.ncell;
+    const int t = threadIdx.x;
+    const int chunk = (ncell + kScanThreads - 1) / kScanThreads;
+    const int b = t * chunk;
+    const int e = min(b + chunk, ncell);
     int sum = 0;
-    for (int c = b; c < e; ++c) sum += count[c];
+    for (int c = b; c < e; ++c) sum += B.cell_count[c];
     part[t] = sum;
     __syncthreads();
     // Hillis-Steele inclusive scan of the chunk sums
@@ -64,46 +76,58 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_counts(int ncell, int *__
         part[t] += v;
         __syncthreads();
     }
-    int run = part[t] - sum;
+    int run = part[t] - sum;      // particles before cell b (all instances, no padding)
+    // instance of cell b, then walk: the shift of instance i is slot_off_i minus
+    // the particles of instances 0..i-1
+    int inst = 0;
+    while (inst + 1 < B.ninst && B.inst[inst + 1].cell_off <= b) ++inst;
+    int before = 0;
+    for (int q = 0; q < inst; ++q) before += B.inst[q].nf + B.inst[q].nw;
     for (int c = b; c < e; ++c) {
-        int k = count[c];
-        start[c] = run;
+        while (inst + 1 < B.ninst && B.inst[inst + 1].cell_off <= c) {
+            before += B.inst[inst].nf + B.inst[inst].nw;
+            ++inst;
+        }
+        const int k = B.cell_count[c];
+        B.cell_start[c] = run - before + B.inst[inst].slot_off;
         run += k;
-        count[c] = 0;
+        B.cell_count[c] = 0;
     }
-    if (t == kScanThreads - 1) start[ncell] = part[t];
+    if (t == kScanThreads - 1) B.cell_start[ncell] = B.n;
 }
 
-__global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ slot,
-                          const int *__restrict__ start, int *__restrict__ perm)
+__global__ void __launch_bounds__(kBlock) k_scatter(Buffers B)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    perm[start[key[i]] + slot[i]] = i;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const int c = B.key[i];
+    if (c < 0) return;
+    B.unsorted[B.cell_start[c] + B.slot[i]] = i;
 }
 
 // Orders each cell by caller index: the particle in unsorted slot t moves to
 // start[c] + (number of particles of its cell with a smaller caller index).
-// One thread per particle; cells hold a few tens of particles.
-__global__ void k_cell_rank(int n, const int *__restrict__ key, const int *__restrict__ start,
-                            const int *__restrict__ unsorted, const uint32_t *__restrict__ gid, int *__restrict__ perm)
+// One thread per slot; cells hold a few tens of particles; padding slots (never
+// written by the scatter) stay -1.
+__global__ void __launch_bounds__(kBlock) k_cell_rank(Buffers B, const uint32_t *__restrict__ gid)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int i = unsorted[t];
-    const int c = key[i];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B.n) return;
+    const int i = B.unsorted[t];
+    if (i < 0) return;
+    const int c = B.key[i];
     const uint32_t gi = gid[i];
-    const int b = start[c], e = start[c + 1];
+    const int b = B.cell_start[c], e = B.cell_start[c + 1];
     int rank = 0;
-    for (int u = b; u < e; ++u) rank += gid[unsorted[u]] < gi;
-    perm[b + rank] = i;
+    for (int u = b; u < e; ++u) rank += gid[B.unsorted[u]] < gi;
+    B.perm[b + rank] = i;
 }
 
-__device__ __forceinline__ float4 cell_offset(const Geom &G, int cell, const double *x, int n, int s)
+__device__ __forceinline__ float4 cell_offset(const Geom &G, int local_cell, const double *x, int n, int s)
 {
-    int c0 = cell % G.nc[0];
-    int c1 = (cell / G.nc[0]) % G.nc[1];
-    int c2 = cell / (G.nc[0] * G.nc[1]);
+    const int c0 = local_cell % G.nc[0];
+    const int c1 = (local_cell / G.nc[0]) % G.nc[1];
+    const int c2 = local_cell / (G.nc[0] * G.nc[1]);
     float4 o;
     o.x = (float)(x[s] - (G.lo[0] + c0 * G.s[0]));
     o.y = (float)(x[(size_t)n + s] - (G.lo[1] + c1 * G.s[1]));
@@ -114,158 +138,170 @@ __device__ __forceinline__ float4 cell_offset(const Geom &G, int cell, const dou
 
 // A -> B at the start of a step: state n, and the packed (V^n, p^n) that the
 // state-n pair pass gathers.
-__global__ void k_permute_a_to_b(int n, int nf, int dim, int fp32c, Geom G, const int *__restrict__ perm,
-                                 const int *__restrict__ key, const uint32_t *__restrict__ gid_a,
-                                 const double *__restrict__ x_a, const double *__restrict__ vn_a,
-                                 const double *__restrict__ vnm1_a, const double *__restrict__ pn_a,
-                                 uint32_t *__restrict__ gid_b, double *__restrict__ x_b, double *__restrict__ vn_b,
-                                 double *__restrict__ vnm1_b, double *__restrict__ pn_b, int *__restrict__ cell_b,
-                                 float4 *__restrict__ off, double4_32a *__restrict__ nb64, float4 *__restrict__ nb32)
+__global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int o = perm[s];
-    gid_b[s] = gid_a[o];
-    int cell = key[o];
-    cell_b[s] = cell;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n) return;
+    const int o = B.perm[s];
+    if (o < 0) {
+        B.gid_b[s] = kNoParticle;
+        return;
+    }
+    const int n = B.n, dim = B.dim;
+    B.gid_b[s] = B.gid_a[o];
+    const int cell = B.key[o];
+    B.cell_b[s] = cell;
     double v[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) {
-        size_t so = (size_t)a * n;
-        x_b[so + s] = x_a[so + o];
-        v[a] = vn_a[so + o];
-        vn_b[so + s] = v[a];
-        vnm1_b[so + s] = vnm1_a[so + o];
+        const size_t so = (size_t)a * n;
+        B.x_b[so + s] = B.x_a[so + o];
+        v[a] = B.vn_a[so + o];
+        B.vn_b[so + s] = v[a];
+        B.vnm1_b[so + s] = B.vnm1_a[so + o];
     }
-    double p = pn_a[o];
-    pn_b[s] = p;
-    if (fp32c) {
-        off[s] = cell_offset(G, cell, x_b, n, s);
-        nb32[s] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)p);
+    const double p = B.pn_a[o];
+    B.pn_b[s] = p;
+    if (B.fp32c) {
+        const int inst = B.inst_of[s];
+        B.off[s] = cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.x_b, n, s);
+        B.nb32[1][s] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)p);
     } else {
-        nb64[s] = make_double4_32a(v[0], v[1], v[2], p);
+        B.nb64[1][s] = make_double4_32a(v[0], v[1], v[2], p);
     }
-    (void)nf;
 }
 
 // B -> A after the predictor: the loop order. Carries r^n, r^0, V^n, the BDF2
 // source, and seeds iterate 0 (V^0, p-hat^0).
-__global__ void k_permute_b_to_a(int n, int dim, int fp32c, Geom G, const int *__restrict__ perm,
-                                 const int *__restrict__ key, const uint32_t *__restrict__ gid_b,
-                                 const double *__restrict__ x_b, const double *__restrict__ xp_b,
-                                 const double *__restrict__ vn_b, const double *__restrict__ s_b,
-                                 const double *__restrict__ v0_b, const double *__restrict__ ph0_b,
-                                 uint32_t *__restrict__ gid_a, double *__restrict__ x_a, double *__restrict__ xp_a,
-                                 double *__restrict__ vn_a, double *__restrict__ s_a, int *__restrict__ cell_a,
-                                 float4 *__restrict__ off, double *__restrict__ vk0, double4_32a *__restrict__ nb64,
-                                 float4 *__restrict__ nb32)
+__global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int o = perm[s];
-    gid_a[s] = gid_b[o];
-    int cell = key[o];
-    cell_a[s] = cell;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n) return;
+    const int o = B.perm[s];
+    if (o < 0) {
+        B.gid_a[s] = kNoParticle;
+        return;
+    }
+    const int n = B.n, dim = B.dim;
+    B.gid_a[s] = B.gid_b[o];
+    const int cell = B.key[o];
+    B.cell_a[s] = cell;
     double v[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) {
-        size_t so = (size_t)a * n;
-        x_a[so + s] = x_b[so + o];
-        xp_a[so + s] = xp_b[so + o];
-        vn_a[so + s] = vn_b[so + o];
-        s_a[so + s] = s_b[so + o];
-        v[a] = v0_b[so + o];
-        vk0[so + s] = v[a];
+        const size_t so = (size_t)a * n;
+        B.x_a[so + s] = B.x_b[so + o];
+        B.xp_a[so + s] = B.xp_b[so + o];
+        B.vn_a[so + s] = B.vn_b[so + o];
+        B.s_a[so + s] = B.s_b[so + o];
+        v[a] = B.v0_b[so + o];
+        B.vk[0][so + s] = v[a];
     }
-    double ph = ph0_b[o];
-    if (fp32c) {
-        off[s] = cell_offset(G, cell, xp_a, n, s);
-        nb32[s] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)ph);
+    const double ph = B.ph0_b[o];
+    if (B.fp32c) {
+        const int inst = B.inst_of[s];
+        B.off[s] = cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.xp_a, n, s);
+        B.nb32[0][s] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)ph);
     } else {
-        nb64[s] = make_double4_32a(v[0], v[1], v[2], ph);
+        B.nb64[0][s] = make_double4_32a(v[0], v[1], v[2], ph);
     }
 }
 
-// Caller order -> order A (identity) from AoS inputs.
-__global__ void k_scatter_in(int nf, int nw, int dim, const double *__restrict__ x, const double *__restrict__ v,
-                             const double *__restrict__ p, const double *__restrict__ vprev,
-                             const double *__restrict__ xw, const double *__restrict__ vw, uint32_t *__restrict__ gid,
-                             double *__restrict__ x_a, double *__restrict__ vn_a, double *__restrict__ vnm1_a,
-                             double *__restrict__ pn_a)
+// Caller order -> order A from AoS inputs: slot s of instance i holds its fluid
+// particle s - slot_off (caller index foff + ...), then its walls, then padding.
+__global__ void __launch_bounds__(kBlock) k_scatter_in(Buffers B, const double *__restrict__ x,
+                                                       const double *__restrict__ v, const double *__restrict__ p,
+                                                       const double *__restrict__ vprev,
+                                                       const double *__restrict__ xw, const double *__restrict__ vw)
 {
-    int n = nf + nw;
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    gid[s] = (uint32_t)s;
-    if (s < nf) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n) return;
+    const int n = B.n, dim = B.dim;
+    const Inst I = B.inst[B.inst_of[s]];
+    const int local = s - I.slot_off;
+    if (local < I.nf) {
+        const size_t f = (size_t)I.foff + local;
+        B.gid_a[s] = (uint32_t)f;
         for (int a = 0; a < dim; ++a) {
-            size_t so = (size_t)a * n;
-            x_a[so + s] = x[(size_t)s * dim + a];
-            vn_a[so + s] = v[(size_t)s * dim + a];
-            vnm1_a[so + s] = vprev ? vprev[(size_t)s * dim + a] : v[(size_t)s * dim + a];
+            const size_t so = (size_t)a * n;
+            B.x_a[so + s] = x[f * dim + a];
+            B.vn_a[so + s] = v[f * dim + a];
+            B.vnm1_a[so + s] = vprev ? vprev[f * dim + a] : v[f * dim + a];
         }
-        pn_a[s] = p[s];
+        B.pn_a[s] = p[f];
+    } else if (local < I.nf + I.nw) {
+        const size_t w = (size_t)I.woff + (local - I.nf);
+        B.gid_a[s] = (uint32_t)(B.nf + w);
+        for (int a = 0; a < dim; ++a) {
+            const size_t so = (size_t)a * n;
+            B.x_a[so + s] = xw[w * dim + a];
+            B.vn_a[so + s] = vw ? vw[w * dim + a] : 0.0;
+            B.vnm1_a[so + s] = B.vn_a[so + s];
+        }
+        B.pn_a[s] = 0.0;
     } else {
-        int w = s - nf;
-        for (int a = 0; a < dim; ++a) {
-            size_t so = (size_t)a * n;
-            x_a[so + s] = xw[(size_t)w * dim + a];
-            vn_a[so + s] = vw ? vw[(size_t)w * dim + a] : 0.0;
-            vnm1_a[so + s] = vn_a[so + s];
-        }
-        pn_a[s] = 0.0;
+        B.gid_a[s] = kNoParticle;
     }
 }
 
-// Order A (SoA, comps components) -> caller order (AoS), fluid particles only.
-__global__ void k_unpermute(int n, int nf, int comps, const uint32_t *__restrict__ gid, const double *__restrict__ src,
-                            double *__restrict__ out)
+// Slot order -> caller order (AoS), fluid particles only.
+__global__ void __launch_bounds__(kBlock) k_unpermute(int n, int nf, int comps, const uint32_t *__restrict__ gid,
+                                                      const double *__restrict__ src, double *__restrict__ out)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    uint32_t g = gid[s];
+    const uint32_t g = gid[s];
     if (g >= (uint32_t)nf) return;
     for (int a = 0; a < comps; ++a) out[(size_t)g * comps + a] = src[(size_t)a * n + s];
+}
+
+__global__ void k_fill_instance(Inst *inst, Geom *geo, Phys *phys, int i, Inst I, Geom G, Phys P)
+{
+    inst[i] = I;
+    geo[i] = G;
+    phys[i] = P;
 }
 
 inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
 
 }  // namespace
 
-int launch_binning(const Buffers &B, const Geom &G, const double *x_keys, const uint32_t *gid_src, cudaStream_t st)
+int launch_binning(const Buffers &B, const double *x_keys, const uint32_t *gid_src, cudaStream_t st)
 {
-    k_bin_keys<<<blocks(B.n), kBlock, 0, st>>>(B.n, G, x_keys, B.key, B.slot, B.cell_count, B.err);
-    k_scan_counts<<<1, kScanThreads, 0, st>>>(G.ncell, B.cell_count, B.cell_start);
-    k_scatter<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.key, B.slot, B.cell_start, B.unsorted);
-    k_cell_rank<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.key, B.cell_start, B.unsorted, gid_src, B.perm);
+    k_bin_keys<<<blocks(B.n), kBlock, 0, st>>>(B, x_keys, gid_src);
+    k_scan_counts<<<1, kScanThreads, 0, st>>>(B);
+    k_scatter<<<blocks(B.n), kBlock, 0, st>>>(B);
+    k_cell_rank<<<blocks(B.n), kBlock, 0, st>>>(B, gid_src);
     return 4;
 }
 
-int launch_permute_a_to_b(const Buffers &B, const Geom &G, cudaStream_t st)
+int launch_permute_a_to_b(const Buffers &B, cudaStream_t st)
 {
-    k_permute_a_to_b<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.nf, B.dim, B.fp32c, G, B.perm, B.key, B.gid_a, B.x_a,
-                                                     B.vn_a, B.vnm1_a, B.pn_a, B.gid_b, B.x_b, B.vn_b, B.vnm1_b,
-                                                     B.pn_b, B.cell_b, B.off, B.nb64[1], B.nb32[1]);
+    k_permute_a_to_b<<<blocks(B.n), kBlock, 0, st>>>(B);
     return 1;
 }
 
-int launch_permute_b_to_a(const Buffers &B, const Geom &G, cudaStream_t st)
+int launch_permute_b_to_a(const Buffers &B, cudaStream_t st)
 {
-    k_permute_b_to_a<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.dim, B.fp32c, G, B.perm, B.key, B.gid_b, B.x_b, B.xp_b,
-                                                     B.vn_b, B.s_b, B.v0_b, B.ph0_b, B.gid_a, B.x_a, B.xp_a, B.vn_a,
-                                                     B.s_a, B.cell_a, B.off, B.vk[0], B.nb64[0], B.nb32[0]);
+    k_permute_b_to_a<<<blocks(B.n), kBlock, 0, st>>>(B);
     return 1;
 }
 
 int launch_scatter_in(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,
                       const double *xw, const double *vw, cudaStream_t st)
 {
-    k_scatter_in<<<blocks(B.n), kBlock, 0, st>>>(B.nf, B.nw, B.dim, x, v, p, vprev, xw, vw, B.gid_a, B.x_a, B.vn_a,
-                                                 B.vnm1_a, B.pn_a);
+    k_scatter_in<<<blocks(B.n), kBlock, 0, st>>>(B, x, v, p, vprev, xw, vw);
     return 1;
 }
 
 int launch_unpermute(const Buffers &B, const uint32_t *gid, const double *src, double *out, int comps, cudaStream_t st)
 {
     k_unpermute<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.nf, comps, gid, src, out);
+    return 1;
+}
+
+int launch_fill_instance(Inst *inst, Geom *geo, Phys *phys, int i, const Inst &I, const Geom &G, const Phys &P,
+                         cudaStream_t st)
+{
+    k_fill_instance<<<1, 1, 0, st>>>(inst, geo, phys, i, I, G, P);
     return 1;
 }
 

@@ -16,6 +16,25 @@ constexpr uint32_t kWallBit = 0x80000000u;   // set in a cached neighbour index 
 // Error bits raised by kernels into Buffers::err (read by dtsph_sync).
 enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u };
 
+// A context advances one or more independent simulations ("instances") together.
+// Instance i owns the slot range [slot_off, slot_off + nf + nw) of every particle
+// array, with slot_off a multiple of kSlotAlign; the slots between ranges are
+// padding (caller index kNoParticle). Every block of every particle kernel covers
+// at most kSlotAlign consecutive slots from a multiple of its own width, so a
+// block never straddles two instances.
+constexpr int kSlotAlign = 256;
+constexpr uint32_t kNoParticle = 0xFFFFFFFFu;
+
+struct Inst {
+    int slot_off;          // first slot
+    int nf, nw;            // fluid and wall particles
+    int foff, woff;        // first caller index of its fluid particles / of its walls
+    int cell_off;          // first cell; the instance owns ncell + 1 cells, the last one
+                           // always empty so that its start marks the end of the range
+    int tile_pad;          // unused, keeps the struct 8-byte aligned in tables
+    int pad_;
+};
+
 // Cell grid and neighbour-test constants of one binning. Cells have side
 // s[a] >= 3h, so every neighbour lies in the 3^dim surrounding cells.
 struct Geom {
@@ -54,13 +73,13 @@ struct Phys {
     int edac, use_av;
 };
 
-// Convergence control of the pseudo-time loop, one per context, in device memory.
+// Convergence control of one instance's pseudo-time loop, in device memory.
 struct LoopState {
     int iter;              // iterations completed in this real step
     int done;              // 1 once a stop rule holds
     int reason;            // stop reason (dtsph_step_stats.reason), -1 while running
-    unsigned int ticket;   // last-block election counter of the iterate kernel
-    unsigned int bar;      // grid-barrier arrival counter of the persistent loop kernel
+    unsigned int ticket;   // last-block election counter of the instance's tiles
+    unsigned int bar;      // unused
     int pad0;
     double rp, rv;         // residuals of the last iteration
     double hist_p[16], hist_v[16];   // ring of the last residuals (stagnation test)
@@ -69,17 +88,32 @@ struct LoopState {
     long long step;        // real steps completed (indexes the stats ring)
 };
 
+// Context-wide control words of the pseudo-time loop.
+struct LoopCtrl {
+    unsigned int ticket;   // last-block election over all tiles of the iterate kernel
+    unsigned int bar;      // grid-barrier arrival counter of the persistent loop kernel
+    int active;            // instances still iterating
+    int pad;
+};
+
 struct StatRec { int iters, reason; double rp, rv; };
-constexpr int kStatRing = 65536;
+constexpr int kStatRing = 65536;   // real steps kept per instance
 
 // Device buffers of one context. Particle arrays hold all n = nf + nw particles
 // in the order of the latest binning ("A" = the loop order kept between steps,
 // "B" = the order of the binning at r^n inside a step). SoA per component.
 struct Buffers {
-    int n, nf, nw, dim, fp32c, K;   // K = neighbour capacity per particle
+    int n;                          // slots (all instances, padding included)
+    int nf, nw;                     // fluid and wall particles of all instances
+    int dim, fp32c, K;              // K = neighbour capacity per particle
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
+    int ninst, ncell;               // instances; cells of all instances (sentinels included)
+    const Inst *inst;               // [ninst]
+    const Geom *geo;                // [ninst]
+    const Phys *phys;               // [ninst]
+    const uint16_t *inst_of;        // instance of each slot [n]
     // order A (persistent)
-    uint32_t *gid_a;       // caller index of each slot (walls: nf + wall index)
+    uint32_t *gid_a;       // caller index of each slot (walls: nf + wall index; padding: kNoParticle)
     double *x_a;           // r^n           [dim][n]
     double *xp_a;          // r^0 (frozen)  [dim][n]
     double *vn_a;          // V^n (walls: prescribed velocity) [dim][n]
@@ -97,7 +131,7 @@ struct Buffers {
     int *unsorted;         // new slot -> old slot, cells in atomic order
     int *perm;             // new slot -> old slot, each cell ordered by caller index
     int *cell_count;       // [ncell], zero between binnings
-    int *cell_start;       // [ncell + 1]
+    int *cell_start;       // [ncell + 1], slot of the first particle of each cell
     // FP32 offsets of each particle from its cell origin (FP32C geometry)
     float4 *off;           // [n]
     // pseudo-time iterates, ping-pong on the iteration parity
@@ -113,35 +147,44 @@ struct Buffers {
     double *ap_b;          // [n]
     double *f_b;           // [dim][n]
     // residual reduction
-    double *blk;           // [2 * nblocks] block partial sums
-    LoopState *ls;
-    StatRec *stats;        // [kStatRing]
+    double *blk;           // [2 x tiles], double-buffered: per-tile residual partial sums
+    LoopState *ls;         // [ninst]
+    LoopCtrl *ctrl;
+    StatRec *stats;        // [kStatRing][ninst]
     uint32_t *err;
 };
+
+// Instance owning the block that covers slots [first, first + width): a block
+// never straddles two instances.
+__device__ __forceinline__ int block_instance(const Buffers &B, int first)
+{
+    return first < B.n ? (int)B.inst_of[first] : 0;
+}
 
 // ------------------------------------------------------------ launchers
 // Every launcher enqueues on `st` and returns the number of kernels launched.
 
-int launch_binning(const Buffers &B, const Geom &G, const double *x_keys, const uint32_t *gid_src,
-                   cudaStream_t st);
-int launch_permute_a_to_b(const Buffers &B, const Geom &G, cudaStream_t st);
-int launch_permute_b_to_a(const Buffers &B, const Geom &G, cudaStream_t st);
-int launch_state_n(const Buffers &B, const Geom &G, const Phys &P, bool predictor, cudaStream_t st);
-int launch_pair_cache(const Buffers &B, const Geom &G, const Phys &P, const double *xpos, const int *cell,
-                      const uint32_t *gid, cudaStream_t st);
-int launch_walls_iter(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st);
-int launch_iterate(const Buffers &B, const Geom &G, const Phys &P, unsigned long long cond_handle,
-                   int use_cond, cudaStream_t st);
-int launch_outer(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st);
+int launch_binning(const Buffers &B, const double *x_keys, const uint32_t *gid_src, cudaStream_t st);
+int launch_permute_a_to_b(const Buffers &B, cudaStream_t st);
+int launch_permute_b_to_a(const Buffers &B, cudaStream_t st);
+int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st);
+int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
+int launch_walls_iter(const Buffers &B, cudaStream_t st);
+int launch_iterate(const Buffers &B, unsigned long long cond_handle, int use_cond, cudaStream_t st);
+int launch_outer(const Buffers &B, cudaStream_t st);
 // Persistent pseudo-time loop (one cooperative launch per real step): grid size
 // (co-resident blocks, at most one per tile) and the launch itself.
 int loop_grid(const Buffers &B, int *grid);
-cudaError_t launch_loop(const Buffers &B, const Phys &P, int grid, cudaStream_t st);
+cudaError_t launch_loop(const Buffers &B, int grid, cudaStream_t st);
 int launch_loop_reset(const Buffers &B, cudaStream_t st);
 int launch_unpermute(const Buffers &B, const uint32_t *gid, const double *src, double *out, int comps, cudaStream_t st);
 int launch_scatter_in(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,
                       const double *xw, const double *vw, cudaStream_t st);
+// Writes one instance's tables (inst/geo/phys entry i) from values, for callers
+// whose tables live in device memory they cannot copy into from the host.
+int launch_fill_instance(Inst *inst, Geom *geo, Phys *phys, int i, const Inst &I, const Geom &G, const Phys &P,
+                         cudaStream_t st);
 
-int iterate_blocks(const Buffers &B);
+int iterate_tiles(const Buffers &B);   // tiles of the iterate kernel (one block each)
 
 }  // namespace dtsph

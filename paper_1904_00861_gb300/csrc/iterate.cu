@@ -115,10 +115,12 @@ template <int D, bool F32>
 __global__ void __launch_bounds__(kBlock) k_walls_iter(Buffers B)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.n || B.gid_a[s] < (uint32_t)B.nf) return;
-    const int cur = B.ls->iter & 1;
-    if (B.ls->done) return;
-    wall_slot<D, F32>(B, s, cur);
+    if (s >= B.n) return;
+    const uint32_t g = B.gid_a[s];
+    if (g < (uint32_t)B.nf || g == kNoParticle) return;
+    const LoopState *ls = B.ls + B.inst_of[s];
+    if (ls->done) return;
+    wall_slot<D, F32>(B, s, ls->iter & 1);
 }
 
 // One entry of the pair cache in registers.
@@ -208,7 +210,7 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
     const int n = B.n;
     const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
     const int s = tile * PPB + grp;
-    const bool active = s < n && (!WALLS || B.gid_a[s] < (uint32_t)B.nf);
+    const bool active = s < n && B.gid_a[s] < (uint32_t)B.nf;   // fluid (not wall, not padding)
 
     // ---------------- phase 1: pair sums
     {
@@ -272,7 +274,7 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
     double r_ap = 0.0, r_av = 0.0;
     if (threadIdx.x < PPB) {
         const int s2 = tile * PPB + threadIdx.x;
-        if (s2 < n && (!WALLS || B.gid_a[s2] < (uint32_t)B.nf)) {
+        if (s2 < n && B.gid_a[s2] < (uint32_t)B.nf) {
             const double apv = (double)sh.part[0][threadIdx.x];
             double vnew[3] = {0, 0, 0};
             double av2 = 0.0;
@@ -283,18 +285,18 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
                 const size_t q = (size_t)a * n + s2;
                 const double vk = B.vk[cur][q];
                 const double Fv = (double)sh.part[1 + a][threadIdx.x];
-                const double av = fma(P.kappa, Fv, -fma(P.kc3, vk, B.s_a[q]));
-                vnew[a] = fma(P.dtau, av, vk);
+                const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
+                vnew[a] = __fma_rn(P.dtau, av, vk);
                 B.vk[nxt][q] = vnew[a];
-                av2 = fma(av, av, av2);
+                av2 = __fma_rn(av, av, av2);
             }
             if (F32) {
                 const float4 q = B.nb32[cur][s2];
-                const float pnew = q.w + (float)P.dtau * (float)apv;
+                const float pnew = __fmaf_rn((float)P.dtau, (float)apv, q.w);
                 B.nb32[nxt][s2] = make_float4((float)vnew[0], (float)vnew[1], (float)vnew[2], pnew);
                 r_av = (double)sqrtf((float)av2);
             } else {
-                const double pnew = B.nb64[cur][s2].w + P.dtau * apv;
+                const double pnew = __fma_rn(P.dtau, apv, B.nb64[cur][s2].w);
                 B.nb64[nxt][s2] = make_double4_32a(vnew[0], vnew[1], vnew[2], pnew);
                 r_av = sqrt(av2);
             }
@@ -362,51 +364,94 @@ __device__ __forceinline__ void reduce_tiles(const double *blk, int ntiles, doub
     }
 }
 
-// One pseudo-time iteration over all slots; one tile per block.
+// First tile and end tile of instance i for tiles of ppb slots.
+__device__ __forceinline__ void instance_tiles(const Inst &I, int ppb, int &lo, int &hi)
+{
+    lo = I.slot_off / ppb;
+    hi = (I.slot_off + I.nf + I.nw + ppb - 1) / ppb;
+}
+
+// Updates the loop state of one instance with the residual sums of iteration
+// `it` and applies the stop rules; thread 0 only. Returns the stop reason (-1:
+// continue).
+__device__ __forceinline__ int finish_iteration(LoopState *ls, const Phys &P, int it, double sa, double sb)
+{
+    // work on a register copy: one batch of loads instead of a chain of
+    // dependent global accesses
+    LoopState st = *ls;
+    const int k1 = it + 1;
+    st.rp = sa * P.rp_scale;
+    st.rv = sb * P.rv_scale;
+    st.hist_p[it & 15] = st.rp;
+    st.hist_v[it & 15] = st.rv;
+    const int r = stop_rule(st, k1);
+    ls->rp = st.rp;
+    ls->rv = st.rv;
+    ls->hist_p[it & 15] = st.rp;
+    ls->hist_v[it & 15] = st.rv;
+    ls->iter = k1;
+    ls->reason = r;
+    ls->done = r >= 0;
+    return r;
+}
+
+// One pseudo-time iteration over all slots; one tile per block. The last block
+// of an instance's tiles reduces that instance's partials in a fixed order and
+// applies its stop rules; the last block of all sets the while-node condition
+// (some instance still iterating).
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, Phys P, unsigned long long cond, int use_cond)
+__global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, unsigned long long cond, int use_cond)
 {
     using T = typename std::conditional<F32, float, double>::type;
+    constexpr int PPB = kBlock / L;
     __shared__ TileShared<T, D, L> sh;
-    __shared__ int last;
-    LoopState *ls = B.ls;
+    __shared__ Phys P;
+    __shared__ int last, tlo_sh;
+    if (!use_cond && B.ctrl->active == 0) return;     // whole grid agrees: nothing to do
+    const int inst = block_instance(B, blockIdx.x * PPB);
+    LoopState *ls = B.ls + inst;
+    int tlo, thi;
+    instance_tiles(B.inst[inst], PPB, tlo, thi);
+    const bool mine = (int)blockIdx.x < thi;          // false: a tile made of padding only
     const int it = ls->iter;
-    if (!use_cond && ls->done) return;          // whole grid agrees: nothing to do
-    double a = 0, b = 0;
-    tile_iteration<D, F32, WALLS, L>(B, P, it & 1, blockIdx.x, sh, a, b);
-    if (threadIdx.x == 0) {
-        B.blk[2 * blockIdx.x] = a;
-        B.blk[2 * blockIdx.x + 1] = b;
-        __threadfence();
-        unsigned int t = atomicAdd(&ls->ticket, 1u);
-        last = (t == gridDim.x - 1);
+    const bool work = mine && !ls->done;
+    if (work) {
+        for (int w = threadIdx.x; w < (int)(sizeof(Phys) / 4); w += blockDim.x)
+            reinterpret_cast<int *>(&P)[w] = reinterpret_cast<const int *>(B.phys + inst)[w];
+        __syncthreads();
+        double a = 0, b = 0;
+        tile_iteration<D, F32, WALLS, L>(B, P, it & 1, blockIdx.x, sh, a, b);
+        if (threadIdx.x == 0) {
+            B.blk[2 * blockIdx.x] = a;
+            B.blk[2 * blockIdx.x + 1] = b;
+            __threadfence();
+            const unsigned int t = atomicAdd(&ls->ticket, 1u);
+            last = (t == (unsigned int)(thi - tlo - 1));
+            tlo_sh = tlo;
+        }
+        __syncthreads();
+        if (last) {
+            // last tile of this instance: fixed-order reduction of its partials
+            __threadfence();
+            double sa = 0, sb = 0;
+            reduce_tiles(B.blk + 2 * tlo_sh, thi - tlo_sh, sh.red, sa, sb);
+            if (threadIdx.x == 0) {
+                const int r = finish_iteration(ls, P, it, sa, sb);
+                ls->ticket = 0;
+                if (r >= 0) atomicSub(&B.ctrl->active, 1);
+                __threadfence();
+            }
+        }
     }
-    __syncthreads();
-    if (!last) return;
-    // last block: fixed-order reduction of the tile partials, then the stop rules
-    __threadfence();
-    double sa = 0, sb = 0;
-    reduce_tiles(B.blk, gridDim.x, sh.red, sa, sb);
     if (threadIdx.x == 0) {
-        // work on a register copy: one batch of loads instead of a chain of
-        // dependent global accesses
-        LoopState st = *ls;
-        const int k1 = it + 1;
-        st.rp = sa * P.rp_scale;
-        st.rv = sb * P.rv_scale;
-        st.hist_p[it & 15] = st.rp;
-        st.hist_v[it & 15] = st.rv;
-        const int r = stop_rule(st, k1);
-        ls->rp = st.rp;
-        ls->rv = st.rv;
-        ls->hist_p[it & 15] = st.rp;
-        ls->hist_v[it & 15] = st.rv;
-        ls->iter = k1;
-        ls->reason = r;
-        ls->done = r >= 0;
-        ls->ticket = 0;
         __threadfence();
-        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, r >= 0 ? 0u : 1u);
+        const unsigned int t = atomicAdd(&B.ctrl->ticket, 1u);
+        if (t == gridDim.x - 1) {
+            B.ctrl->ticket = 0;
+            __threadfence();
+            const int active = *(volatile int *)&B.ctrl->active;
+            if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, active > 0 ? 1u : 0u);
+        }
     }
 }
 
@@ -447,22 +492,27 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *er
 
 // Every pseudo-time iteration of one real step in one cooperative launch. Tiles
 // are dealt to blocks round robin; after each iteration the blocks meet at a
-// grid barrier, each block reduces the per-tile partials (double-buffered on the
-// iteration parity) in the fixed order of k_iterate, and all blocks take the same
-// stop decision. Walls get their own phase and barrier before the fluid phase.
+// grid barrier. With one instance every block then reduces the per-tile
+// partials (double-buffered on the iteration parity) in the fixed order of
+// k_iterate and all blocks take the same stop decision. With several, block b
+// finishes instances b, b + grid, ... and a second barrier publishes the
+// decisions; tiles of finished instances are skipped. Walls get their own phase
+// and barrier before the fluid phase.
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B, Phys P)
+__global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     constexpr int PPB = kBlock / L;
     __shared__ TileShared<T, D, L> sh;
     __shared__ LoopState st;
-    __shared__ int stop, ok_sh;
+    __shared__ Phys P;
+    __shared__ int stop, ok_sh, p_inst;
     const int ntiles = (B.n + PPB - 1) / PPB;
-    LoopState *ls = B.ls;
+    const bool single = B.ninst == 1;
     if (threadIdx.x == 0) {
-        st = *ls;
+        if (single) st = *B.ls;
         stop = 0;
+        p_inst = -1;
     }
     __syncthreads();
     unsigned int epoch = 0;
@@ -470,12 +520,25 @@ __global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B, Phys P)
     for (;; ++it) {
         const int cur = it & 1;
         if (WALLS) {
-            for (int s = blockIdx.x * kBlock + threadIdx.x; s < B.n; s += gridDim.x * kBlock)
-                if (B.gid_a[s] >= (uint32_t)B.nf) wall_slot<D, F32>(B, s, cur);
-            if (!grid_barrier(&ls->bar, ++epoch, B.err, ok_sh)) break;
+            for (int s = blockIdx.x * kBlock + threadIdx.x; s < B.n; s += gridDim.x * kBlock) {
+                const uint32_t g = B.gid_a[s];
+                if (g >= (uint32_t)B.nf && g != kNoParticle && !B.ls[B.inst_of[s]].done) wall_slot<D, F32>(B, s, cur);
+            }
+            if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh)) break;
         }
         double *blk = B.blk + (size_t)(it & 1) * 2 * ntiles;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int inst = block_instance(B, t * PPB);
+            int tlo, thi;
+            instance_tiles(B.inst[inst], PPB, tlo, thi);
+            if (t >= thi || (!single && *(volatile int *)&B.ls[inst].done)) continue;
+            if (inst != p_inst) {
+                __syncthreads();
+                for (int w = threadIdx.x; w < (int)(sizeof(Phys) / 4); w += blockDim.x)
+                    reinterpret_cast<int *>(&P)[w] = reinterpret_cast<const int *>(B.phys + inst)[w];
+                __syncthreads();
+                if (threadIdx.x == 0) p_inst = inst;
+            }
             double a = 0, b = 0;
             tile_iteration<D, F32, WALLS, L>(B, P, cur, t, sh, a, b);
             if (threadIdx.x == 0) {
@@ -483,32 +546,62 @@ __global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B, Phys P)
                 blk[2 * t + 1] = b;
             }
         }
-        if (!grid_barrier(&ls->bar, ++epoch, B.err, ok_sh)) break;
-        double sa = 0, sb = 0;
-        reduce_tiles(blk, ntiles, sh.red, sa, sb);
-        if (threadIdx.x == 0) {
-            const int k1 = it + 1;
-            st.rp = sa * P.rp_scale;
-            st.rv = sb * P.rv_scale;
-            st.hist_p[it & 15] = st.rp;
-            st.hist_v[it & 15] = st.rv;
-            r = stop_rule(st, k1);
-            stop = r >= 0;
+        if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh)) break;
+        if (single) {
+            double sa = 0, sb = 0;
+            int tlo, thi;
+            instance_tiles(B.inst[0], PPB, tlo, thi);
+            reduce_tiles(blk + 2 * tlo, thi - tlo, sh.red, sa, sb);
+            if (threadIdx.x == 0) {
+                const int k1 = it + 1;
+                st.rp = sa * B.phys[0].rp_scale;
+                st.rv = sb * B.phys[0].rv_scale;
+                st.hist_p[it & 15] = st.rp;
+                st.hist_v[it & 15] = st.rv;
+                r = stop_rule(st, k1);
+                stop = r >= 0;
+            }
+            __syncthreads();
+            if (stop) break;
+        } else {
+            for (int i = blockIdx.x; i < B.ninst; i += gridDim.x) {
+                if (B.ls[i].done) continue;
+                int tlo, thi;
+                instance_tiles(B.inst[i], PPB, tlo, thi);
+                double sa = 0, sb = 0;
+                reduce_tiles(blk + 2 * tlo, thi - tlo, sh.red, sa, sb);
+                if (threadIdx.x == 0) {
+                    if (finish_iteration(B.ls + i, B.phys[i], it, sa, sb) >= 0) atomicSub(&B.ctrl->active, 1);
+                }
+                __syncthreads();
+            }
+            if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh)) break;
+            if (threadIdx.x == 0) stop = *(volatile int *)&B.ctrl->active == 0;
+            __syncthreads();
+            if (stop) break;
         }
-        __syncthreads();
-        if (stop) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const bool finished = stop != 0;
-        ls->rp = st.rp;
-        ls->rv = st.rv;
-        for (int q = 0; q < 16; ++q) {
-            ls->hist_p[q] = st.hist_p[q];
-            ls->hist_v[q] = st.hist_v[q];
+        if (single) {
+            LoopState *ls = B.ls;
+            const bool finished = stop != 0;
+            ls->rp = st.rp;
+            ls->rv = st.rv;
+            for (int q = 0; q < 16; ++q) {
+                ls->hist_p[q] = st.hist_p[q];
+                ls->hist_v[q] = st.hist_v[q];
+            }
+            ls->iter = finished ? it + 1 : it;
+            ls->reason = finished ? r : 3;
+            ls->done = 1;
+        } else if (!stop) {
+            // a barrier gave up: close every instance still open
+            for (int i = 0; i < B.ninst; ++i)
+                if (!B.ls[i].done) {
+                    B.ls[i].reason = 3;
+                    B.ls[i].done = 1;
+                }
         }
-        ls->iter = finished ? it + 1 : it;
-        ls->reason = finished ? r : 3;
-        ls->done = 1;
     }
 }
 
@@ -516,33 +609,36 @@ __global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B, Phys P)
 // V^{n-1} <- V^n, V^n <- V^K, p^n <- p^K = (p-hat^K + p-hat^{K-1}) / 2; thread 0
 // logs the step.
 template <int D, bool F32>
-__global__ void __launch_bounds__(kBlock) k_outer(Buffers B, Geom G, Phys P)
+__global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const LoopState *ls = B.ls;
+    if (s >= B.n) return;
+    const int inst = B.inst_of[s];
+    LoopState *ls = B.ls + inst;
     const int K = ls->iter;
     const int fin = K & 1, prev = fin ^ 1;
     const int n = B.n;
-    if (s == 0) {
-        LoopState *w = B.ls;
-        long long step = w->step;
+    if (s == B.inst[inst].slot_off) {
+        const long long step = ls->step;
         StatRec r;
         r.iters = K;
-        r.reason = w->reason;
-        r.rp = w->rp;
-        r.rv = w->rv;
-        B.stats[step % kStatRing] = r;
-        w->step = step + 1;
+        r.reason = ls->reason;
+        r.rp = ls->rp;
+        r.rv = ls->rv;
+        B.stats[(step % kStatRing) * B.ninst + inst] = r;
+        ls->step = step + 1;
     }
-    if (s >= n || B.gid_a[s] >= (uint32_t)B.nf) return;
+    if (B.gid_a[s] >= (uint32_t)B.nf) return;           // walls and padding
+    const Geom &G = B.geo[inst];
+    const double dt = B.phys[inst].dt;
     for (int a = 0; a < D; ++a) {
         const size_t q = (size_t)a * n + s;
         const double vn = B.vn_a[q];
         const double vK = B.vk[fin][q];
-        double x = B.x_a[q] + 0.5 * P.dt * (vn + vK);
+        double x = __fma_rn(0.5 * dt, __dadd_rn(vn, vK), B.x_a[q]);
         if (G.periodic[a]) {
-            if (x >= G.hi[a]) x -= G.L[a];
-            else if (x < G.lo[a]) x += G.L[a];
+            if (x >= G.hi[a]) x = __dsub_rn(x, G.L[a]);
+            else if (x < G.lo[a]) x = __dadd_rn(x, G.L[a]);
         }
         B.x_a[q] = x;
         B.vnm1_a[q] = vn;
@@ -556,18 +652,25 @@ __global__ void __launch_bounds__(kBlock) k_outer(Buffers B, Geom G, Phys P)
         p1 = B.nb64[fin][s].w;
         p0 = B.nb64[prev][s].w;
     }
-    B.pn_a[s] = 0.5 * (p0 + p1);
+    B.pn_a[s] = __dmul_rn(0.5, __dadd_rn(p0, p1));
 }
 
-__global__ void k_loop_reset(LoopState *ls)
+__global__ void k_loop_reset(Buffers B)
 {
-    ls->iter = 0;
-    ls->done = 0;
-    ls->reason = -1;
-    ls->ticket = 0;
-    ls->bar = 0;
-    ls->rp = 0;
-    ls->rv = 0;
+    for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
+        LoopState *ls = B.ls + i;
+        ls->iter = 0;
+        ls->done = 0;
+        ls->reason = -1;
+        ls->ticket = 0;
+        ls->rp = 0;
+        ls->rv = 0;
+    }
+    if (threadIdx.x == 0) {
+        B.ctrl->ticket = 0;
+        B.ctrl->bar = 0;
+        B.ctrl->active = B.ninst;
+    }
 }
 
 template <int D, bool F, bool W, int L>
@@ -575,21 +678,21 @@ const void *loop_kernel() { return (const void *)k_loop<D, F, W, L>; }
 
 }  // namespace
 
-int iterate_blocks(const Buffers &B) { return (B.n + kBlock / B.lanes - 1) / (kBlock / B.lanes); }
+int iterate_tiles(const Buffers &B) { return (B.n + kBlock / B.lanes - 1) / (kBlock / B.lanes); }
 
 template <int D, bool F, bool W>
-static void iterate_lanes(const Buffers &B, const Phys &P, unsigned long long cond, int use_cond, cudaStream_t st)
+static void iterate_lanes(const Buffers &B, unsigned long long cond, int use_cond, cudaStream_t st)
 {
-    const int nb = iterate_blocks(B);
+    const int nb = iterate_tiles(B);
     switch (B.lanes) {
-    case 1: k_iterate<D, F, W, 1><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
-    case 2: k_iterate<D, F, W, 2><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
-    case 4: k_iterate<D, F, W, 4><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
-    default: k_iterate<D, F, W, 8><<<nb, kBlock, 0, st>>>(B, P, cond, use_cond); break;
+    case 1: k_iterate<D, F, W, 1><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
+    case 2: k_iterate<D, F, W, 2><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
+    case 4: k_iterate<D, F, W, 4><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
+    default: k_iterate<D, F, W, 8><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
     }
 }
 
-int launch_walls_iter(const Buffers &B, const Geom & /*G*/, const Phys & /*P*/, cudaStream_t st)
+int launch_walls_iter(const Buffers &B, cudaStream_t st)
 {
     if (B.nw == 0) return 0;
     if (B.dim == 2) {
@@ -602,16 +705,15 @@ int launch_walls_iter(const Buffers &B, const Geom & /*G*/, const Phys & /*P*/, 
     return 1;
 }
 
-int launch_iterate(const Buffers &B, const Geom & /*G*/, const Phys &P, unsigned long long cond, int use_cond,
-                   cudaStream_t st)
+int launch_iterate(const Buffers &B, unsigned long long cond, int use_cond, cudaStream_t st)
 {
     const bool w = B.nw > 0;
     if (B.dim == 2) {
-        if (B.fp32c) { if (w) iterate_lanes<2, true, true>(B, P, cond, use_cond, st); else iterate_lanes<2, true, false>(B, P, cond, use_cond, st); }
-        else { if (w) iterate_lanes<2, false, true>(B, P, cond, use_cond, st); else iterate_lanes<2, false, false>(B, P, cond, use_cond, st); }
+        if (B.fp32c) { if (w) iterate_lanes<2, true, true>(B, cond, use_cond, st); else iterate_lanes<2, true, false>(B, cond, use_cond, st); }
+        else { if (w) iterate_lanes<2, false, true>(B, cond, use_cond, st); else iterate_lanes<2, false, false>(B, cond, use_cond, st); }
     } else {
-        if (B.fp32c) { if (w) iterate_lanes<3, true, true>(B, P, cond, use_cond, st); else iterate_lanes<3, true, false>(B, P, cond, use_cond, st); }
-        else { if (w) iterate_lanes<3, false, true>(B, P, cond, use_cond, st); else iterate_lanes<3, false, false>(B, P, cond, use_cond, st); }
+        if (B.fp32c) { if (w) iterate_lanes<3, true, true>(B, cond, use_cond, st); else iterate_lanes<3, true, false>(B, cond, use_cond, st); }
+        else { if (w) iterate_lanes<3, false, true>(B, cond, use_cond, st); else iterate_lanes<3, false, false>(B, cond, use_cond, st); }
     }
     return 1;
 }
@@ -645,12 +747,11 @@ int loop_grid(const Buffers &B, int *grid)
         return -1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop_function(B), kBlock, 0) != cudaSuccess || per_sm < 1)
         return -1;
-    const int ntiles = iterate_blocks(B);
-    *grid = std::min(ntiles, per_sm * sms);
+    *grid = std::min(iterate_tiles(B), per_sm * sms);
     return 0;
 }
 
-cudaError_t launch_loop(const Buffers &B, const Phys &P, int grid, cudaStream_t st)
+cudaError_t launch_loop(const Buffers &B, int grid, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -663,26 +764,25 @@ cudaError_t launch_loop(const Buffers &B, const Phys &P, int grid, cudaStream_t 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     Buffers b = B;
-    Phys p = P;
-    void *args[] = {(void *)&b, (void *)&p};
+    void *args[] = {(void *)&b};
     return cudaLaunchKernelExC(&cfg, loop_function(B), args);
 }
 
-int launch_outer(const Buffers &B, const Geom &G, const Phys &P, cudaStream_t st)
+int launch_outer(const Buffers &B, cudaStream_t st)
 {
     if (B.dim == 2) {
-        if (B.fp32c) k_outer<2, true><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
-        else k_outer<2, false><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
+        if (B.fp32c) k_outer<2, true><<<blocks(B.n), kBlock, 0, st>>>(B);
+        else k_outer<2, false><<<blocks(B.n), kBlock, 0, st>>>(B);
     } else {
-        if (B.fp32c) k_outer<3, true><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
-        else k_outer<3, false><<<blocks(B.n), kBlock, 0, st>>>(B, G, P);
+        if (B.fp32c) k_outer<3, true><<<blocks(B.n), kBlock, 0, st>>>(B);
+        else k_outer<3, false><<<blocks(B.n), kBlock, 0, st>>>(B);
     }
     return 1;
 }
 
 int launch_loop_reset(const Buffers &B, cudaStream_t st)
 {
-    k_loop_reset<<<1, 1, 0, st>>>(B.ls);
+    k_loop_reset<<<1, kBlock, 0, st>>>(B);
     return 1;
 }
 

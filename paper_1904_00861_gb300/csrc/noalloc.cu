@@ -33,7 +33,7 @@ constexpr int kNoallocMaxParticles = 16384;
 constexpr int kNoallocMaxCells = 32768;
 
 // Bytes per particle of the arrays the rate evaluation touches (see carve()).
-constexpr size_t kPerParticle = 4 + 3 * 8 * 3 + 8 + 4 * 4 + 4 + 3 * 8 * 3 + 8 + 4 + 16 + 32 + 8 + 3 * 8;
+constexpr size_t kPerParticle = 4 + 3 * 8 * 3 + 8 + 4 * 4 + 4 + 3 * 8 * 3 + 8 + 4 + 16 + 32 + 8 + 3 * 8 + 2;
 constexpr size_t kScratchBytes =
     ((kPerParticle * kNoallocMaxParticles + 2 * 4 * (size_t)(kNoallocMaxCells + 1) + 64 * 256) + 255) / 256 * 256;
 
@@ -96,6 +96,10 @@ size_t carve(unsigned char *base, int n, int ncell, Buffers &B)
     B.cell_count = (int *)take(4 * (size_t)(ncell + 1));
     B.cell_start = (int *)take(4 * (size_t)(ncell + 1));
     B.err = (uint32_t *)take(256);
+    B.inst_of = (uint16_t *)take(2 * (size_t)n);
+    B.inst = (Inst *)take(sizeof(Inst));
+    B.geo = (Geom *)take(sizeof(Geom));
+    B.phys = (Phys *)take(sizeof(Phys));
     return off;
 }
 
@@ -115,7 +119,8 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
                                         double *F, void *stream)
 {
     if (!p || !x || !v || !pr || !ap || !F || nf <= 0 || nw < 0 || (nw > 0 && !xw)) return DTSPH_E_ARG;
-    if (nf + nw > kNoallocMaxParticles) return DTSPH_E_CAPACITY;   // beyond the fixed scratch
+    const int64_t nslots = (nf + nw + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
+    if (nslots > kNoallocMaxParticles) return DTSPH_E_CAPACITY;   // beyond the fixed scratch
     if ((p->dim != 2 && p->dim != 3) || (p->precision != DTSPH_FP64 && p->precision != DTSPH_FP32C))
         return DTSPH_E_ARG;
     if (!(p->h > 0) || !(p->m > 0) || !(p->rho0 > 0) || !(p->beta > 0) || !(p->v_ref > 0) || !(p->dt > 0) ||
@@ -145,7 +150,7 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
         long long k = (long long)std::floor(L / (rc * (1.0 + 1e-9)));
         if (k < 1) k = 1;
         if (G.periodic[a] && k < 3) return DTSPH_E_ARG;
-        if (k > kNoallocMaxCells || (long long)G.ncell * k > kNoallocMaxCells) return DTSPH_E_CAPACITY;
+        if (k >= kNoallocMaxCells || (long long)G.ncell * k >= kNoallocMaxCells) return DTSPH_E_CAPACITY;
         G.nc[a] = (int)k;
         G.s[a] = L / (double)k;
         G.inv_s[a] = 1.0 / G.s[a];
@@ -188,24 +193,35 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     if (r) return r;
     Buffers B;
     memset(&B, 0, sizeof B);
-    B.n = (int)(nf + nw);
+    B.n = (int)nslots;
     B.nf = (int)nf;
     B.nw = (int)nw;
     B.dim = p->dim;
     B.fp32c = p->precision == DTSPH_FP32C;
-    if (carve(base, B.n, G.ncell, B) > kScratchBytes) return DTSPH_E_CAPACITY;
+    B.ninst = 1;
+    B.ncell = G.ncell + 1;           // the instance's cells and its empty sentinel cell
+    if (carve(base, B.n, B.ncell, B) > kScratchBytes) return DTSPH_E_CAPACITY;
+    Inst I;
+    memset(&I, 0, sizeof I);
+    I.nf = (int)nf;
+    I.nw = (int)nw;
 
     cudaStream_t st = (cudaStream_t)stream;
-    // the counting sort needs zeroed cell counters; the last call may have left any state
-    if (cudaMemsetAsync(B.cell_count, 0, sizeof(int) * (size_t)(G.ncell + 1), st) != cudaSuccess ||
-        cudaMemsetAsync(B.err, 0, sizeof(uint32_t), st) != cudaSuccess) {
+    // the counting sort needs zeroed cell counters and -1 in the permutation
+    // slots it never writes; the last call may have left any state there
+    if (cudaMemsetAsync(B.cell_count, 0, sizeof(int) * (size_t)B.ncell, st) != cudaSuccess ||
+        cudaMemsetAsync(B.err, 0, sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(B.unsorted, 0xff, sizeof(int) * (size_t)B.n, st) != cudaSuccess ||
+        cudaMemsetAsync(B.perm, 0xff, sizeof(int) * (size_t)B.n, st) != cudaSuccess ||
+        cudaMemsetAsync((void *)B.inst_of, 0, sizeof(uint16_t) * (size_t)B.n, st) != cudaSuccess) {
         cudaGetLastError();
         return DTSPH_E_CUDA;
     }
+    launch_fill_instance((Inst *)B.inst, (Geom *)B.geo, (Phys *)B.phys, 0, I, G, P, st);
     launch_scatter_in(B, x, v, pr, nullptr, xw, vw, st);
-    launch_binning(B, G, B.x_a, B.gid_a, st);
-    launch_permute_a_to_b(B, G, st);
-    launch_state_n(B, G, P, false, st);
+    launch_binning(B, B.x_a, B.gid_a, st);
+    launch_permute_a_to_b(B, st);
+    launch_state_n(B, false, st);
     launch_unpermute(B, B.gid_b, B.ap_b, ap, 1, st);
     launch_unpermute(B, B.gid_b, B.f_b, F, B.dim, st);
     if (cudaGetLastError() != cudaSuccess) return DTSPH_E_CUDA;

@@ -16,23 +16,41 @@
 
 namespace dtsph {
 
+// Rounded arithmetic with the rounding of every operation spelled out, so the
+// pair terms give the same bits whichever kernel variant inlines them (the
+// compiler may not fuse or reorder these).
+template <typename T> struct Ar;
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
 // Quintic spline, dW/dq up to the factor sigma: -5(3-q)^4 + 30(2-q)^4 - 75(1-q)^4
 // with each term present only inside its support.
 template <typename T>
 __device__ __forceinline__ T quintic_dwdq(T q)
 {
-    T a = T(3) - q;
-    T a2 = a * a;
-    T s = T(-5) * a2 * a2;
+    using A = Ar<T>;
+    const T a = A::sub(T(3), q);
+    const T a2 = A::mul(a, a);
+    T s = A::mul(A::mul(T(-5), a2), a2);
     if (q < T(2)) {
-        T b = T(2) - q;
-        T b2 = b * b;
-        s += T(30) * b2 * b2;
+        const T b = A::sub(T(2), q);
+        const T b2 = A::mul(b, b);
+        s = A::fma(A::mul(T(30), b2), b2, s);
     }
     if (q < T(1)) {
-        T c = T(1) - q;
-        T c2 = c * c;
-        s -= T(75) * c2 * c2;
+        const T c = A::sub(T(1), q);
+        const T c2 = A::mul(c, c);
+        s = A::fma(A::mul(T(-75), c2), c2, s);
     }
     return s;
 }
@@ -41,18 +59,19 @@ __device__ __forceinline__ T quintic_dwdq(T q)
 template <typename T>
 __device__ __forceinline__ T quintic_w(T q)
 {
-    T a = T(3) - q;
-    T a2 = a * a;
-    T s = a2 * a2 * a;
+    using A = Ar<T>;
+    const T a = A::sub(T(3), q);
+    const T a2 = A::mul(a, a);
+    T s = A::mul(A::mul(a2, a2), a);
     if (q < T(2)) {
-        T b = T(2) - q;
-        T b2 = b * b;
-        s -= T(6) * b2 * b2 * b;
+        const T b = A::sub(T(2), q);
+        const T b2 = A::mul(b, b);
+        s = A::fma(A::mul(T(-6), A::mul(b2, b2)), b, s);
     }
     if (q < T(1)) {
-        T c = T(1) - q;
-        T c2 = c * c;
-        s += T(15) * c2 * c2 * c;
+        const T c = A::sub(T(1), q);
+        const T c2 = A::mul(c, c);
+        s = A::fma(A::mul(T(15), A::mul(c2, c2)), c, s);
     }
     return s;
 }
@@ -121,30 +140,31 @@ template <int D, typename T, typename Acc>
 __device__ __forceinline__ void pair_accumulate(const PairConst<T> &k, const T *g, T F, const T *vi, T pi,
                                                 const T *vj_div, const T *vj_vis, T pj, Acc &ap, Acc *Fi)
 {
+    using A = Ar<T>;
     T vdg = T(0);
     T vv[3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        vdg += (vi[a] - vj_div[a]) * g[a];
-        vv[a] = vi[a] - vj_vis[a];
+        vdg = A::fma(A::sub(vi[a], vj_div[a]), g[a], vdg);
+        vv[a] = A::sub(vi[a], vj_vis[a]);
     }
-    T t_ap = k.c_div * vdg;
-    if (k.edac) t_ap += k.c_edac * (pi - pj) * F;
+    T t_ap = A::mul(k.c_div, vdg);
+    if (k.edac) t_ap = A::fma(A::mul(k.c_edac, A::sub(pi, pj)), F, t_ap);
     ap.add(t_ap);
-    T pres = k.c_p * (pi + pj);
+    T pres = A::mul(k.c_p, A::add(pi, pj));
     if (k.use_av) {
         // v_ij . r_ij < 0  <=>  v_ij . gradW > 0 (dW/dr < 0); phi_ij = (v_ij . gradW) F / |gradW|^2
         T vvg = T(0), g2 = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            vvg += vv[a] * g[a];
-            g2 += g[a] * g[a];
+            vvg = A::fma(vv[a], g[a], vvg);
+            g2 = A::fma(g[a], g[a], g2);
         }
-        if (vvg > T(0) && g2 > T(0)) pres -= k.c_av_m * vvg * F / g2;   // -m Pi_ij, Pi_ij = -alpha h c phi / rho
+        if (vvg > T(0) && g2 > T(0)) pres = A::sub(pres, A::mul(k.c_av_m, A::mul(vvg, F)) / g2);   // -m Pi_ij
     }
-    T cv = k.c_visc * F;
+    const T cv = A::mul(k.c_visc, F);
 #pragma unroll
-    for (int a = 0; a < D; ++a) Fi[a].add(-pres * g[a] + cv * vv[a]);
+    for (int a = 0; a < D; ++a) Fi[a].add(A::fma(cv, vv[a], A::mul(-pres, g[a])));
 }
 
 }  // namespace dtsph

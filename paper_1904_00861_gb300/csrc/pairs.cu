@@ -22,9 +22,11 @@ namespace {
 // called as body(valid, j, dx, dy, dz) where (dx, dy, dz) is the unwrapped cell
 // shift of candidate j (r_ij = off_i - off_j - shift * s).
 template <int D, int L, class Body>
-__device__ __forceinline__ void group_candidates(const Geom &G, const int *__restrict__ start, int cell, int lane_in,
-                                                 Body &&body)
+__device__ __forceinline__ void group_candidates(const Geom &G, const int *__restrict__ start, int cell_off, int cell,
+                                                 int lane_in, Body &&body)
 {
+    start += cell_off;            // the instance's cells, numbered from 0
+    cell -= cell_off;
     const int c0 = cell % G.nc[0];
     const int c1 = (cell / G.nc[0]) % G.nc[1];
     const int c2 = cell / (G.nc[0] * G.nc[1]);
@@ -94,11 +96,12 @@ __device__ __forceinline__ bool neighbour(const Geom &G, const double *__restric
 {
     if (F32) {
         float4 oj = off[j];
-        float f0 = oi.x - oj.x - (float)dx * G.s_f[0];
-        float f1 = oi.y - oj.y - (float)dy * G.s_f[1];
-        float f2 = D == 3 ? oi.z - oj.z - (float)dz * G.s_f[2] : 0.f;
-        float q2 = f0 * f0 + f1 * f1;
-        if (D == 3) q2 += f2 * f2;
+        using A = Ar<float>;
+        const float f0 = A::fma(-(float)dx, G.s_f[0], A::sub(oi.x, oj.x));
+        const float f1 = A::fma(-(float)dy, G.s_f[1], A::sub(oi.y, oj.y));
+        const float f2 = D == 3 ? A::fma(-(float)dz, G.s_f[2], A::sub(oi.z, oj.z)) : 0.f;
+        float q2 = A::fma(f1, f1, A::mul(f0, f0));
+        if (D == 3) q2 = A::fma(f2, f2, q2);
         if (q2 >= G.rc2_hi) return false;
         if (q2 >= G.rc2_lo) {
             double e[3];
@@ -137,14 +140,15 @@ template <> struct F32Math<double> {
 template <int D, typename T>
 __device__ __forceinline__ void grad_coef(const Phys &P, const T *d, T r2, T *g, T &F)
 {
+    using A = Ar<T>;
     if (r2 > T(0)) {
         const T rinv = F32Math<T>::rsqrt(r2);
-        const T r = r2 * rinv;
-        const T dwdr = (T)P.sig_h * quintic_dwdq<T>(r * (T)P.inv_h);
-        const T a = dwdr * rinv;
+        const T r = A::mul(r2, rinv);
+        const T dwdr = A::mul((T)P.sig_h, quintic_dwdq<T>(A::mul(r, (T)P.inv_h)));
+        const T a = A::mul(dwdr, rinv);
 #pragma unroll
-        for (int k = 0; k < D; ++k) g[k] = a * d[k];
-        F = F32Math<T>::div(dwdr * r, r2 + (T)P.eta_h2);
+        for (int k = 0; k < D; ++k) g[k] = A::mul(a, d[k]);
+        F = F32Math<T>::div(A::mul(dwdr, r), A::add(r2, (T)P.eta_h2));
     } else {
 #pragma unroll
         for (int k = 0; k < D; ++k) g[k] = T(0);
@@ -163,28 +167,45 @@ __device__ __forceinline__ const double4_32a *nb_ptr<double>(const Buffers &B, i
 template <>
 __device__ __forceinline__ const float4 *nb_ptr<float>(const Buffers &B, int buf) { return B.nb32[buf]; }
 
+// Copies a table entry into shared memory with the whole block (then syncs).
+template <typename T>
+__device__ __forceinline__ void block_copy(T &dst, const T &src)
+{
+    static_assert(sizeof(T) % 4 == 0, "word copy");
+    for (int w = threadIdx.x; w < (int)(sizeof(T) / 4); w += blockDim.x)
+        reinterpret_cast<int *>(&dst)[w] = reinterpret_cast<const int *>(&src)[w];
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- walls, state n
 
 // Adami et al. wall values at state n in order B: p_w = (sum_f p_f W + rho0 g .
 // sum_f r_wf W) / sum_f W, ghost velocity 2 v_w - sum_f V_f W / sum_f W; written
 // into the packed (V, p) of the wall slot. L lanes per wall particle.
 template <int D, bool F32, int L>
-__global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B, Geom G, Phys P)
+__global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
+    __shared__ Geom G;
+    __shared__ Phys P;
+    const int inst = block_instance(B, blockIdx.x * (kBlock / L));
+    block_copy(G, B.geo[inst]);
+    block_copy(P, B.phys[inst]);
+    const int cell_off = B.inst[inst].cell_off;
     const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
     const int s = blockIdx.x * (kBlock / L) + grp;
     // every lane stays to the end: the partial sums are merged by full-warp shuffles
-    const bool wall = s < B.n && B.gid_b[s] >= (uint32_t)B.nf;
+    const uint32_t gs = s < B.n ? B.gid_b[s] : kNoParticle;
+    const bool wall = gs != kNoParticle && gs >= (uint32_t)B.nf;
     const auto *nb = nb_ptr<T>(B, 1);
     const float4 oi = wall && F32 ? B.off[s] : make_float4(0, 0, 0, 0);
     double acc[6] = {0, 0, 0, 0, 0, 0};   // sum W, sum p W, sum rho0 (g . r) W, sum V W
     const double sigma = P.sig_h * P.h;
-    if (wall) group_candidates<D, L>(G, B.cell_start, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
+    if (wall) group_candidates<D, L>(G, B.cell_start, cell_off, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
         if (!valid || j == s || B.gid_b[j] >= (uint32_t)B.nf) return;
         T d[3], r2;
         if (!neighbour<D, F32, T>(G, B.x_b, B.off, B.n, s, j, oi, dx, dy, dz, d, r2)) return;
-        const double W = sigma * (double)quintic_w<T>(sqrt(r2) / (T)P.h);
+        const double W = sigma * (double)quintic_w<T>(Ar<T>::mul(sqrt(r2), (T)P.inv_h));
         const auto q = nb[j];
         double gr = 0;
 #pragma unroll
@@ -221,12 +242,18 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B, Geom G, Phy
 // rate); and the BDF2 source (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact),
 // all in FP64, one thread per particle in whole warps.
 template <int D, bool F32, bool PRED, int L, bool WALLS>
-__global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
+__global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
     constexpr int PPB = kBlock / L;
     __shared__ T part[D + 1][PPB];
+    __shared__ Geom G;
+    __shared__ Phys P;
+    const int inst = block_instance(B, blockIdx.x * PPB);
+    block_copy(G, B.geo[inst]);
+    block_copy(P, B.phys[inst]);
+    const int cell_off = B.inst[inst].cell_off;
     const int n = B.n;
     const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
     const int s = blockIdx.x * PPB + grp;
@@ -240,7 +267,7 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
             const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
             const T pi = (T)qi.w;
             const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
-            group_candidates<D, L>(G, B.cell_start, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
+            group_candidates<D, L>(G, B.cell_start, cell_off, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
                 if (!valid || j == s) return;
                 T d[3], r2;
                 if (!neighbour<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2)) return;
@@ -270,7 +297,7 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
     __syncthreads();
     if (threadIdx.x >= PPB) return;
     const int s2 = blockIdx.x * PPB + threadIdx.x;
-    if (s2 >= n) return;
+    if (s2 >= n || B.gid_b[s2] == kNoParticle) return;
     if (B.gid_b[s2] >= (uint32_t)B.nf) {
         if (PRED) {
             for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s2] = B.x_b[(size_t)a * n + s2];
@@ -279,23 +306,24 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
     }
     const double apv = (double)part[0][threadIdx.x];
     double Fv[3];
-    for (int a = 0; a < D; ++a) Fv[a] = (double)part[1 + a][threadIdx.x] + P.g[a];
+    for (int a = 0; a < D; ++a) Fv[a] = __dadd_rn((double)part[1 + a][threadIdx.x], P.g[a]);
     B.ap_b[s2] = apv;
     for (int a = 0; a < D; ++a) B.f_b[(size_t)a * n + s2] = Fv[a];
     if (PRED) {
         for (int a = 0; a < D; ++a) {
             const size_t q = (size_t)a * n + s2;
+            // explicit roundings: the same bits in every kernel variant
             const double V = B.vn_b[q];
-            double xp = B.x_b[q] + P.dt * V + 0.5 * P.dt * P.dt * Fv[a];
+            double xp = __fma_rn(0.5 * P.dt * P.dt, Fv[a], __fma_rn(P.dt, V, B.x_b[q]));
             if (G.periodic[a]) {
-                if (xp >= G.hi[a]) xp -= G.L[a];
-                else if (xp < G.lo[a]) xp += G.L[a];
+                if (xp >= G.hi[a]) xp = __dsub_rn(xp, G.L[a]);
+                else if (xp < G.lo[a]) xp = __dadd_rn(xp, G.L[a]);
             }
             B.xp_b[q] = xp;
-            B.v0_b[q] = V + P.dt * Fv[a];
-            B.s_b[q] = P.kappa * ((B.vnm1_b[q] - 4.0 * V) * P.inv_2dt - P.g[a]);
+            B.v0_b[q] = __fma_rn(P.dt, Fv[a], V);
+            B.s_b[q] = __dmul_rn(P.kappa, __fma_rn(__fma_rn(-4.0, V, B.vnm1_b[q]), P.inv_2dt, -P.g[a]));
         }
-        B.ph0_b[s2] = B.pn_b[s2] + 0.5 * P.dtau * apv;
+        B.ph0_b[s2] = __fma_rn(0.5 * P.dtau, apv, B.pn_b[s2]);
     }
 }
 
@@ -307,24 +335,40 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B, Geom G, Phys P)
 // per slot test candidates side by side; a group ballot keeps the list in
 // candidate order. Block 0 also resets the pseudo-time loop state.
 template <int D, bool F32, int L>
-__global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, Geom G, Phys P, const double *__restrict__ xpos,
+__global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *__restrict__ xpos,
                                                        const int *__restrict__ cell, const uint32_t *__restrict__ gid)
 {
     using T = typename std::conditional<F32, float, double>::type;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        LoopState *ls = B.ls;
-        ls->iter = 0;
-        ls->done = 0;
-        ls->reason = -1;
-        ls->ticket = 0;
-        ls->bar = 0;
-        ls->rp = 0;
-        ls->rv = 0;
+    __shared__ Geom G;
+    __shared__ Phys P;
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
+            LoopState *ls = B.ls + i;
+            ls->iter = 0;
+            ls->done = 0;
+            ls->reason = -1;
+            ls->ticket = 0;
+            ls->rp = 0;
+            ls->rv = 0;
+        }
+        if (threadIdx.x == 0) {
+            B.ctrl->ticket = 0;
+            B.ctrl->bar = 0;
+            B.ctrl->active = B.ninst;
+        }
     }
+    const int inst = block_instance(B, blockIdx.x * (kBlock / L));
+    block_copy(G, B.geo[inst]);
+    block_copy(P, B.phys[inst]);
+    const int cell_off = B.inst[inst].cell_off;
     const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
     const int s = blockIdx.x * (kBlock / L) + grp;
     if (s >= B.n) return;                                  // whole group leaves together
     const int n = B.n, K = B.K;
+    if (gid[s] == kNoParticle) {
+        if (lane_in == 0) B.pcount[s] = 0;
+        return;
+    }
     const bool wall_s = gid[s] >= (uint32_t)B.nf;
     const size_t base = (size_t)(s >> 5) * K * kWarp + (s & 31);
     const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
@@ -332,7 +376,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, Geom G, Phys P
     const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << gshift;
     int cnt = 0;
     const T sigma = (T)(P.sig_h * P.h);
-    group_candidates<D, L>(G, B.cell_start, cell[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
+    group_candidates<D, L>(G, B.cell_start, cell_off, cell[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
         T d[3], r2;
         const bool in = valid && j != s && neighbour<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2);
         const unsigned bal = __ballot_sync(gmask, in) >> gshift;
@@ -341,7 +385,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, Geom G, Phys P
         if (!in || pos >= K) return;
         T c4[4] = {T(0), T(0), T(0), T(0)};
         if (wall_s) {
-            const T W = sigma * quintic_w<T>(sqrt(r2) / (T)P.h);
+            const T W = Ar<T>::mul(sigma, quintic_w<T>(Ar<T>::mul(sqrt(r2), (T)P.inv_h)));
             T gr = T(0);
             for (int a = 0; a < D; ++a) gr += (T)P.g[a] * d[a];
             c4[0] = W;
@@ -394,31 +438,30 @@ constexpr int kTravLanes = 8;   // lanes per particle of the traversal kernels
 
 inline int trav_blocks(int n) { return (n + kBlock / kTravLanes - 1) / (kBlock / kTravLanes); }
 
-int launch_state_n(const Buffers &B, const Geom &G, const Phys &P, bool predictor, cudaStream_t st)
+int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st)
 {
     int k = 0;
     const int nb = trav_blocks(B.n);
     if (B.nw > 0) {
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, kTravLanes><<<nb, kBlock, 0, st>>>(B, G, P)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, kTravLanes><<<nb, kBlock, 0, st>>>(B)));
         ++k;
     }
     const bool w = B.nw > 0;
     if (predictor && w)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, true><<<nb, kBlock, 0, st>>>(B, G, P)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, true><<<nb, kBlock, 0, st>>>(B)));
     else if (predictor)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, false><<<nb, kBlock, 0, st>>>(B, G, P)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, false><<<nb, kBlock, 0, st>>>(B)));
     else if (w)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, true><<<nb, kBlock, 0, st>>>(B, G, P)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, true><<<nb, kBlock, 0, st>>>(B)));
     else
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, false><<<nb, kBlock, 0, st>>>(B, G, P)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, false><<<nb, kBlock, 0, st>>>(B)));
     return k + 1;
 }
 
-int launch_pair_cache(const Buffers &B, const Geom &G, const Phys &P, const double *xpos, const int *cell,
-                      const uint32_t *gid, cudaStream_t st)
+int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
 {
     DTSPH_DISPATCH(B.dim, B.fp32c,
-                   (k_pair_cache<D, F32, kTravLanes><<<trav_blocks(B.n), kBlock, 0, st>>>(B, G, P, xpos, cell, gid)));
+                   (k_pair_cache<D, F32, kTravLanes><<<trav_blocks(B.n), kBlock, 0, st>>>(B, xpos, cell, gid)));
     return 1;
 }
 

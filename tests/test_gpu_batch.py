@@ -1,0 +1,101 @@
+"""Batched contexts: several independent instances (uneven sizes, Reynolds
+numbers and wall layouts) advanced together must reproduce, instance by
+instance, the bits of running each one alone, and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1904_00861_gb300 as dt
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1904_00861_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def instances():
+    return [
+        synth.tgv2d(37, re=100.0, seed=11),
+        synth.tgv2d(20, re=630.0, seed=12),
+        synth.cavity2d(18, re=100.0),
+        synth.tgv2d(45, re=250.0, seed=13),
+    ]
+
+
+def solo(d, prec, graph, nsteps, **over):
+    sim = dt.Simulation(d["cfg"], precision=prec, graph=graph, lanes=2, **over)
+    nf = d["nf"]
+    walls = None if d["vw"] is None else (d["x"][nf:], d["vw"])
+    sim.set_state(d["x"][:nf], d["v"], d["p"], d["v_prev"], walls=walls)
+    sim.step(nsteps)
+    out = (sim.x, sim.v, sim.p, sim.stats())
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("graph", [0, 1, 2])
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_batch_equals_solo_runs(prec, graph):
+    insts = instances()
+    nsteps = 3
+    b = dt.Batch([d["cfg"] for d in insts], precision=prec, graph=graph, lanes=2)
+    b.set_state(insts)
+    b.step(nsteps)
+    b.sync()
+    xs, vs, ps = b.field(dt.FIELD_POS), b.field(dt.FIELD_VEL), b.field(dt.FIELD_P)
+    iters = []
+    for i, d in enumerate(insts):
+        x, v, p, st = solo(d, prec, graph, nsteps)
+        assert np.array_equal(xs[i], x) and np.array_equal(vs[i], v) and np.array_equal(ps[i], p), i
+        assert b.stats(i) == st, i
+        iters.append([s["iters"] for s in st])
+    # the instances really ran different numbers of iterations
+    assert len({tuple(t) for t in iters}) > 1
+    b.close()
+
+
+def test_batch_matches_oracle_fp64():
+    insts = instances()
+    b = dt.Batch([d["cfg"] for d in insts], precision=dt.DTSPH_FP64, graph=2)
+    b.set_state(insts)
+    b.step(2)
+    vs = b.field(dt.FIELD_VEL)
+    for i, d in enumerate(insts):
+        orc = oracle.State(d["cfg"], d["x"], d["v"], d["p"], d["v_prev"], vw=d["vw"], nf=d["nf"])
+        recs = orc.step(2)
+        assert [s["iters"] for s in b.stats(i)] == [r["iters"] for r in recs], i
+        assert rel(vs[i], orc.v) < 1e-10, i
+    b.close()
+
+
+def test_batch_with_uneven_tolerances_and_caps():
+    """Per-instance stop rules: one instance capped at 3 iterations, one run at a
+    fixed 5, the others converging freely."""
+    insts = instances()[:3]
+    cfgs = [dict(d["cfg"]) for d in insts]
+    cfgs[0].update(eps=1e-14, stag_window=0, max_iter=3)
+    cfgs[1].update(fixed_iters=5)
+    b = dt.Batch(cfgs, precision=dt.DTSPH_FP32C, graph=2)
+    b.set_state(insts)
+    b.step(2)
+    assert [s["iters"] for s in b.stats(0)] == [3, 3] and all(s["reason"] == 2 for s in b.stats(0))
+    assert [s["iters"] for s in b.stats(1)] == [5, 5] and all(s["reason"] == 4 for s in b.stats(1))
+    assert all(s["reason"] in (0, 1) for s in b.stats(2))
+    b.close()
+
+
+def test_batch_rejects_mixed_dimensions():
+    a = synth.tgv2d(12)
+    c = synth.tgv3d(10)
+    with pytest.raises(dt.DtsphError) as e:
+        dt.Batch([a["cfg"], c["cfg"]])
+    assert e.value.code == -1
