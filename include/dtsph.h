@@ -222,15 +222,18 @@ int dtsph_tuning(const dtsph_ctx *ctx, int32_t *lanes, float *ms_by_lanes);
  *   ap, F      outputs, device: dp/dtau (nf) and the momentum right-hand side
  *              (nf x dim), in the caller's particle order
  *   stream     cudaStream_t or NULL; the call only enqueues work and returns
- * All work happens in one fixed scratch array of about 4.7 MB that is part of the
+ * All work happens in one fixed scratch array of about 20 MB that is part of the
  * library image and that every GPU using the library holds until the process
- * exits. Limits: nf + nw <= 16384 particles and at most 32768 cells of side 3h,
- * else DTSPH_E_CAPACITY and nothing is enqueued. The first call on a device looks
+ * exits. Limits: nf + nw <= 16384 particles, at most 32768 cells of side 3h, and
+ * at most 16384 x 192 neighbour-list entries (nf + nw rounded up to 256, times the
+ * neighbour capacity: max_neighbors, or the one derived from h and m), else
+ * DTSPH_E_CAPACITY and nothing is enqueued. The first call on a device looks
  * up the array's device address (once per device, with that device current): make
  * that first call before any stream capture. Every call reuses the same array, so
  * calls whose GPU work can overlap (different streams or threads) race and corrupt
  * each other; calls ordered on one stream are safe. A particle outside the box of
- * a non-periodic axis is not reported by this entry (nothing is read back). */
+ * a non-periodic axis, or one with more neighbours than the neighbour capacity
+ * (its list is cut there), is not reported by this entry (nothing is read back). */
 int dtsph_eval_rates_noalloc(const dtsph_params *params, int64_t nf, const double *x, const double *v,
                              const double *p, int64_t nw, const double *xw, const double *vw, double *ap,
                              double *F, void *stream);

@@ -263,6 +263,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         I.foff = (int)fo;
         I.woff = (int)wo;
         I.cell_off = (int)co;
+        I.shift = (int)(slot - (fo + wo));
         slot += nf[i] + nw;
         fo += nf[i];
         wo += nw;
@@ -298,9 +299,9 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     A(B.gid_b, n) A(B.x_b, nd) A(B.vn_b, nd) A(B.vnm1_b, nd) A(B.pn_b, n) A(B.xp_b, nd) A(B.v0_b, nd)
     A(B.ph0_b, n) A(B.s_b, nd) A(B.cell_b, n)
     A(B.key, n) A(B.slot, n) A(B.unsorted, n) A(B.perm, n) A(B.cell_count, (size_t)B.ncell)
-    A(B.cell_start, (size_t)B.ncell + 1)
+    A(B.cell_start, (size_t)B.ncell + 1) A(B.scan_tmp, (size_t)B.ncell / 4096 + 2)
     A(B.vk[0], nd) A(B.vk[1], nd)
-    A(B.pcount, n) A(B.pj, npair)
+    A(B.pcount, n) A(B.pj, npair) A(B.pcode, npair)
     if (B.fp32c) {
         A(B.off, n) A(B.nb32[0], n) A(B.nb32[1], n) A(B.pc32, npair)
     } else {
@@ -882,13 +883,7 @@ int dtsph_get_neighbors(dtsph_ctx *c, int64_t i, int64_t *out, int64_t cap, int6
     for (int k = 0; k < cnt; ++k) {
         size_t e = base + (size_t)k * kWarp;
         uint32_t jb;
-        if (B.fp32c && B.dim == 2) {
-            float4 v;
-            CK(cudaMemcpy(&v, B.pc32 + e, sizeof v, cudaMemcpyDeviceToHost));
-            memcpy(&jb, &v.w, sizeof jb);
-        } else {
-            CK(cudaMemcpy(&jb, B.pj + e, sizeof jb, cudaMemcpyDeviceToHost));
-        }
+        CK(cudaMemcpy(&jb, B.pj + e, sizeof jb, cudaMemcpyDeviceToHost));
         got.push_back((int64_t)gid[jb & ~kWallBit]);
     }
     std::sort(got.begin(), got.end());

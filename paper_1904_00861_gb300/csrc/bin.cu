@@ -52,48 +52,116 @@ __global__ void __launch_bounds__(kBlock) k_bin_keys(Buffers B, const double *__
     B.slot[i] = atomicAdd(&B.cell_count[c], 1);
 }
 
-// Exclusive scan of the per-cell counts by one block, shifted so that each
-// instance's particles start at its slot_off; clears the counts for the next
-// binning. Thread t owns a contiguous chunk of cells.
+// Exclusive scan of the per-cell counts, shifted so that each instance's
+// particles start at its slot_off; clears the counts for the next binning.
+// Three passes: per-block totals of kScanCells cells, a scan of those totals by
+// one block, and the final per-cell scan of every block with its offset.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 4;
+constexpr int kScanCells = kScanThreads * kScanPerThread;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_counts(Buffers B)
+// Exclusive prefix sum over the block (kScanThreads threads) of one value each.
+__device__ __forceinline__ int block_exclusive_scan(int v)
 {
-    __shared__ int part[kScanThreads];
-    const int ncell = B.ncell;
-    const int t = threadIdx.x;
-    const int chunk = (ncell + kScanThreads - 1) / kScanThreads;
-    const int b = t * chunk;
-    const int e = min(b + chunk, ncell);
-    int sum = 0;
-    for (int c = b; c < e; ++c) sum += B.cell_count[c];
-    part[t] = sum;
+    __shared__ int warp_tot[kScanThreads / kWarp];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
     __syncthreads();
-    // Hillis-Steele inclusive scan of the chunk sums
-    for (int off = 1; off < kScanThreads; off <<= 1) {
-        int v = t >= off ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int run = part[t] - sum;      // particles before cell b (all instances, no padding)
-    // instance of cell b, then walk: the shift of instance i is slot_off_i minus
-    // the particles of instances 0..i-1
-    int inst = 0;
-    while (inst + 1 < B.ninst && B.inst[inst + 1].cell_off <= b) ++inst;
-    int before = 0;
-    for (int q = 0; q < inst; ++q) before += B.inst[q].nf + B.inst[q].nw;
-    for (int c = b; c < e; ++c) {
-        while (inst + 1 < B.ninst && B.inst[inst + 1].cell_off <= c) {
-            before += B.inst[inst].nf + B.inst[inst].nw;
-            ++inst;
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        int z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
         }
-        const int k = B.cell_count[c];
-        B.cell_start[c] = run - before + B.inst[inst].slot_off;
-        run += k;
-        B.cell_count[c] = 0;
+        warp_tot[lane] = z - w;                 // exclusive prefix of the warp totals
     }
-    if (t == kScanThreads - 1) B.cell_start[ncell] = B.n;
+    __syncthreads();
+    const int before = warp_tot[wid] + x - v;
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partial(Buffers B)
+{
+    const int base = blockIdx.x * kScanCells + threadIdx.x * kScanPerThread;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k)
+        if (base + k < B.ncell) s += B.cell_count[base + k];
+    // block sum
+    __shared__ int red[kScanThreads / kWarp];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kScanThreads / kWarp; ++w) t += red[w];
+        B.scan_tmp[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(Buffers B, int nblocks)
+{
+    // exclusive prefix of the block totals, in chunks of the block width
+    int carry = 0;
+    for (int base = 0; base < nblocks; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < nblocks ? B.scan_tmp[i] : 0;
+        const int ex = block_exclusive_scan(v);
+        if (i < nblocks) B.scan_tmp[i] = carry + ex;
+        // block total: the inclusive value of the last thread
+        __shared__ int last;
+        if (threadIdx.x == kScanThreads - 1) last = ex + v;
+        __syncthreads();
+        carry += last;
+        __syncthreads();
+    }
+}
+
+// Instance owning cell c (instances are few; their cell ranges are ascending).
+__device__ __forceinline__ int cell_instance(const Buffers &B, int c)
+{
+    int lo = 0, hi = B.ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.inst[mid].cell_off <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(Buffers B)
+{
+    const int base = blockIdx.x * kScanCells + threadIdx.x * kScanPerThread;
+    int v[kScanPerThread];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        v[k] = base + k < B.ncell ? B.cell_count[base + k] : 0;
+        s += v[k];
+    }
+    int run = block_exclusive_scan(s) + B.scan_tmp[blockIdx.x];
+    if (base < B.ncell) {
+        int inst = cell_instance(B, base);
+        for (int k = 0; k < kScanPerThread; ++k) {
+            const int c = base + k;
+            if (c >= B.ncell) break;
+            while (inst + 1 < B.ninst && B.inst[inst + 1].cell_off <= c) ++inst;
+            B.cell_start[c] = run + B.inst[inst].shift;
+            run += v[k];
+            B.cell_count[c] = 0;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) B.cell_start[B.ncell] = B.n;
 }
 
 __global__ void __launch_bounds__(kBlock) k_scatter(Buffers B)
@@ -123,7 +191,8 @@ __global__ void __launch_bounds__(kBlock) k_cell_rank(Buffers B, const uint32_t 
     B.perm[b + rank] = i;
 }
 
-__device__ __forceinline__ float4 cell_offset(const Geom &G, int local_cell, const double *x, int n, int s)
+// FP32 offset of slot s from the origin of its cell; .w is 1 for a wall particle.
+__device__ __forceinline__ float4 cell_offset(const Geom &G, int local_cell, const double *x, int n, int s, bool wall)
 {
     const int c0 = local_cell % G.nc[0];
     const int c1 = (local_cell / G.nc[0]) % G.nc[1];
@@ -132,7 +201,7 @@ __device__ __forceinline__ float4 cell_offset(const Geom &G, int local_cell, con
     o.x = (float)(x[s] - (G.lo[0] + c0 * G.s[0]));
     o.y = (float)(x[(size_t)n + s] - (G.lo[1] + c1 * G.s[1]));
     o.z = G.dim == 3 ? (float)(x[2 * (size_t)n + s] - (G.lo[2] + c2 * G.s[2])) : 0.f;
-    o.w = 0.f;
+    o.w = wall ? 1.f : 0.f;
     return o;
 }
 
@@ -148,7 +217,8 @@ __global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
         return;
     }
     const int n = B.n, dim = B.dim;
-    B.gid_b[s] = B.gid_a[o];
+    const uint32_t g = B.gid_a[o];
+    B.gid_b[s] = g;
     const int cell = B.key[o];
     B.cell_b[s] = cell;
     double v[3] = {0, 0, 0};
@@ -163,7 +233,7 @@ __global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
     B.pn_b[s] = p;
     if (B.fp32c) {
         const int inst = B.inst_of[s];
-        B.off[s] = cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.x_b, n, s);
+        B.off[s] = cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.x_b, n, s, g >= (uint32_t)B.nf);
         B.nb32[1][s] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)p);
     } else {
         B.nb64[1][s] = make_double4_32a(v[0], v[1], v[2], p);
@@ -182,7 +252,8 @@ __global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
         return;
     }
     const int n = B.n, dim = B.dim;
-    B.gid_a[s] = B.gid_b[o];
+    const uint32_t g = B.gid_b[o];
+    B.gid_a[s] = g;
     const int cell = B.key[o];
     B.cell_a[s] = cell;
     double v[3] = {0, 0, 0};
@@ -198,7 +269,7 @@ __global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
     const double ph = B.ph0_b[o];
     if (B.fp32c) {
         const int inst = B.inst_of[s];
-        B.off[s] = cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.xp_a, n, s);
+        B.off[s] = cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.xp_a, n, s, g >= (uint32_t)B.nf);
         B.nb32[0][s] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)ph);
     } else {
         B.nb64[0][s] = make_double4_32a(v[0], v[1], v[2], ph);
@@ -267,10 +338,13 @@ inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
 int launch_binning(const Buffers &B, const double *x_keys, const uint32_t *gid_src, cudaStream_t st)
 {
     k_bin_keys<<<blocks(B.n), kBlock, 0, st>>>(B, x_keys, gid_src);
-    k_scan_counts<<<1, kScanThreads, 0, st>>>(B);
+    const int nsb = (B.ncell + kScanCells - 1) / kScanCells;
+    k_scan_partial<<<nsb, kScanThreads, 0, st>>>(B);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(B, nsb);
+    k_scan_final<<<nsb, kScanThreads, 0, st>>>(B);
     k_scatter<<<blocks(B.n), kBlock, 0, st>>>(B);
     k_cell_rank<<<blocks(B.n), kBlock, 0, st>>>(B, gid_src);
-    return 4;
+    return 6;
 }
 
 int launch_permute_a_to_b(const Buffers &B, cudaStream_t st)

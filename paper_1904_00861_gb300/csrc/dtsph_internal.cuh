@@ -31,7 +31,7 @@ struct Inst {
     int foff, woff;        // first caller index of its fluid particles / of its walls
     int cell_off;          // first cell; the instance owns ncell + 1 cells, the last one
                            // always empty so that its start marks the end of the range
-    int tile_pad;          // unused, keeps the struct 8-byte aligned in tables
+    int shift;             // slot_off minus the particles of the instances before it
     int pad_;
 };
 
@@ -132,7 +132,9 @@ struct Buffers {
     int *perm;             // new slot -> old slot, each cell ordered by caller index
     int *cell_count;       // [ncell], zero between binnings
     int *cell_start;       // [ncell + 1], slot of the first particle of each cell
-    // FP32 offsets of each particle from its cell origin (FP32C geometry)
+    int *scan_tmp;         // [ncell / 4096 + 2] block totals of the cell-count scan
+    // FP32 offsets of each particle from its cell origin (FP32C geometry);
+    // .w is 1 for a wall particle
     float4 *off;           // [n]
     // pseudo-time iterates, ping-pong on the iteration parity
     double *vk[2];         // V^k FP64 [dim][n]
@@ -140,6 +142,7 @@ struct Buffers {
     float4 *nb32[2];       // FP32C: (V, p-hat) packed for neighbour gathers
     // pair cache, sliced by warp: entry k of slot i at ((i/32) K + k) 32 + i%32
     uint32_t *pj;          // neighbour slot (| kWallBit for walls)
+    uint8_t *pcode;        // cell shift of the entry: (dx + 1) + 3 (dy + 1) + 9 (dz + 1)
     double4_32a *pc64;         // FP64: (gradW, F_ij)
     float4 *pc32;          // FP32C: (gradW, F_ij); in 2D .w holds the index bits
     int *pcount;           // neighbours of each slot

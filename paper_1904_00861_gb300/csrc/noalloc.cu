@@ -18,6 +18,7 @@
 // are cleared on every call. Two calls whose GPU work overlaps (on different
 // streams, or from different host threads) race on the array and give wrong
 // results; calls ordered on one stream are fine.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -28,14 +29,17 @@
 namespace dtsph {
 namespace {
 
-// Limits of the fixed scratch: particles (fluid + wall) and cells.
+// Limits of the fixed scratch: particles (fluid + wall), cells, and neighbour
+// list entries (padded particles x neighbour capacity).
 constexpr int kNoallocMaxParticles = 16384;
 constexpr int kNoallocMaxCells = 32768;
+constexpr size_t kNoallocMaxEntries = (size_t)kNoallocMaxParticles * 192;
 
 // Bytes per particle of the arrays the rate evaluation touches (see carve()).
 constexpr size_t kPerParticle = 4 + 3 * 8 * 3 + 8 + 4 * 4 + 4 + 3 * 8 * 3 + 8 + 4 + 16 + 32 + 8 + 3 * 8 + 2;
 constexpr size_t kScratchBytes =
-    ((kPerParticle * kNoallocMaxParticles + 2 * 4 * (size_t)(kNoallocMaxCells + 1) + 64 * 256) + 255) / 256 * 256;
+    ((kPerParticle * kNoallocMaxParticles + 5 * kNoallocMaxEntries + 2 * 4 * (size_t)(kNoallocMaxCells + 1) +
+      64 * 256) + 255) / 256 * 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -93,14 +97,30 @@ size_t carve(unsigned char *base, int n, int ncell, Buffers &B)
     else B.nb64[1] = (double4_32a *)nb;
     B.ap_b = (double *)take(8 * (size_t)n);
     B.f_b = (double *)take(8 * nd);
+    B.pcount = (int *)take(4 * (size_t)n);
+    B.pj = (uint32_t *)take(4 * (size_t)n * B.K);
+    B.pcode = (uint8_t *)take((size_t)n * B.K);
     B.cell_count = (int *)take(4 * (size_t)(ncell + 1));
     B.cell_start = (int *)take(4 * (size_t)(ncell + 1));
+    B.scan_tmp = (int *)take(4 * (size_t)(ncell / 4096 + 2));
     B.err = (uint32_t *)take(256);
     B.inst_of = (uint16_t *)take(2 * (size_t)n);
     B.inst = (Inst *)take(sizeof(Inst));
     B.geo = (Geom *)take(sizeof(Geom));
     B.phys = (Phys *)take(sizeof(Phys));
     return off;
+}
+
+// Neighbour list entries per particle: max_neighbors, else 1.35 times the mean
+// count of a uniform fill of the 3h sphere (disc) plus 8.
+int neighbour_capacity_noalloc(const dtsph_params *p)
+{
+    if (p->max_neighbors > 0) return p->max_neighbors;
+    const double pi = 3.14159265358979323846;
+    const double vol = p->m / p->rho0, rc = 3.0 * p->h;
+    const double expect = p->dim == 2 ? pi * rc * rc / vol : 4.0 / 3.0 * pi * rc * rc * rc / vol;
+    const int k = (int)std::ceil(1.35 * expect) + 8;
+    return std::min(std::max(k, 8), 4096);
 }
 
 double quintic_sigma_noalloc(int dim, double h)
@@ -200,6 +220,8 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     B.fp32c = p->precision == DTSPH_FP32C;
     B.ninst = 1;
     B.ncell = G.ncell + 1;           // the instance's cells and its empty sentinel cell
+    B.K = neighbour_capacity_noalloc(p);
+    if ((size_t)B.n * B.K > kNoallocMaxEntries) return DTSPH_E_CAPACITY;
     if (carve(base, B.n, B.ncell, B) > kScratchBytes) return DTSPH_E_CAPACITY;
     Inst I;
     memset(&I, 0, sizeof I);

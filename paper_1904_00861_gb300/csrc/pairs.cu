@@ -1,8 +1,10 @@
-// Neighbour traversal kernels: the wall extrapolation and the pair pass at the
-// state n (geometry computed on the fly), and the pair-coefficient cache that the
-// pseudo-time loop reads (geometry frozen for the whole loop, Sec. 2.2; caching
-// kernel gradients across pseudo-iterations is the speed-up the paper points at
-// in Sec. 5 but did not implement).
+// Neighbour lists and the kernels that walk them: the wall extrapolation and the
+// pair pass at the state n, and the pair-coefficient cache that the pseudo-time
+// loop reads (geometry frozen for the whole loop, Sec. 2.2; caching kernel
+// gradients across pseudo-iterations is the speed-up the paper points at in
+// Sec. 5 but did not implement). The lists are built by a test-only kernel and
+// walked densely by the others, so the pair arithmetic never runs under the
+// distance test, which most candidates fail.
 //
 // Neighbour test: j != i and |r_ij|^2 < (3h)^2 in IEEE double, squares summed in
 // axis order without FMA, minimum image on periodic axes. The FP32C path first
@@ -13,62 +15,6 @@
 namespace dtsph {
 
 namespace {
-
-// Candidate traversal by a group of L lanes that serve one particle. The 3^D
-// cells around `cell` are taken row by row (a row = the three cells along x at
-// fixed y, z offsets); inside a row the candidates of the three cells are
-// numbered consecutively and lane l takes numbers l, l+L, ... Every lane of the
-// group runs the same number of rounds, so `body` may use group ballots; it is
-// called as body(valid, j, dx, dy, dz) where (dx, dy, dz) is the unwrapped cell
-// shift of candidate j (r_ij = off_i - off_j - shift * s).
-template <int D, int L, class Body>
-__device__ __forceinline__ void group_candidates(const Geom &G, const int *__restrict__ start, int cell_off, int cell,
-                                                 int lane_in, Body &&body)
-{
-    start += cell_off;            // the instance's cells, numbered from 0
-    cell -= cell_off;
-    const int c0 = cell % G.nc[0];
-    const int c1 = (cell / G.nc[0]) % G.nc[1];
-    const int c2 = cell / (G.nc[0] * G.nc[1]);
-    const int zlo = D == 3 ? -1 : 0, zhi = D == 3 ? 1 : 0;
-    for (int dz = zlo; dz <= zhi; ++dz) {
-        int z = c2 + dz;
-        if (D == 3 && (z < 0 || z >= G.nc[2])) {
-            if (!G.periodic[2]) continue;
-            z = z < 0 ? z + G.nc[2] : z - G.nc[2];
-        }
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = c1 + dy;
-            if (y < 0 || y >= G.nc[1]) {
-                if (!G.periodic[1]) continue;
-                y = y < 0 ? y + G.nc[1] : y - G.nc[1];
-            }
-            const int row = (z * G.nc[1] + y) * G.nc[0];
-            int b[3], m[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                int x = c0 + k - 1;
-                bool ok = true;
-                if (x < 0 || x >= G.nc[0]) {
-                    if (G.periodic[0]) x = x < 0 ? x + G.nc[0] : x - G.nc[0];
-                    else ok = false;
-                }
-                b[k] = ok ? start[row + x] : 0;
-                m[k] = ok ? start[row + x + 1] - b[k] : 0;
-            }
-            const int m01 = m[0] + m[1];
-            const int tot = m01 + m[2];
-            for (int r = 0; r < tot; r += L) {
-                const int v = r + lane_in;
-                int j, dx;
-                if (v < m[0]) { j = b[0] + v; dx = -1; }
-                else if (v < m01) { j = b[1] + v - m[0]; dx = 0; }
-                else { j = b[2] + v - m01; dx = 1; }
-                body(v < tot, j, dx, dy, dz);
-            }
-        }
-    }
-}
 
 // r_ij in FP64 with the minimum image; returns |r_ij|^2 (no FMA contraction).
 template <int D>
@@ -88,39 +34,218 @@ __device__ __forceinline__ double sep64(const Geom &G, const double *__restrict_
     return r2;
 }
 
-// Neighbour test plus the separation in the working precision T.
-// Returns true when j is a neighbour of i; d and r2 hold r_ij and |r_ij|^2.
+// FP32 separation from cell offsets: the own offset is first moved by the cell
+// shift (dx, dy, dz) s, then the neighbour's offset is subtracted; both the
+// traversal test and the pair terms use this form, so they see the same bits.
+template <int D>
+__device__ __forceinline__ float4 shifted_offset(float4 oi, int dx, int dy, int dz, const float *sf)
+{
+    using A = Ar<float>;
+    float4 p;
+    p.x = A::fma(-(float)dx, sf[0], oi.x);
+    p.y = A::fma(-(float)dy, sf[1], oi.y);
+    p.z = D == 3 ? A::fma(-(float)dz, sf[2], oi.z) : 0.f;
+    p.w = 0.f;
+    return p;
+}
+
+template <int D>
+__device__ __forceinline__ float sep32(float4 ps, float4 oj, float &f0, float &f1, float &f2)
+{
+    using A = Ar<float>;
+    f0 = A::sub(ps.x, oj.x);
+    f1 = A::sub(ps.y, oj.y);
+    f2 = D == 3 ? A::sub(ps.z, oj.z) : 0.f;
+    float q2 = A::fma(f1, f1, A::mul(f0, f0));
+    if (D == 3) q2 = A::fma(f2, f2, q2);
+    return q2;
+}
+
+// Candidate traversal by a warp, L lanes per slot (a group), called by every
+// lane of the warp (active = false for a group without a particle to serve).
+//
+// The 32 / L slots of a warp are consecutive in cell order, so their home
+// cells lie in one or two runs along x of a (y, z) row of cells. The groups of
+// one row share a single candidate stream: for each of the 3^(D-1) neighbour
+// rows, the cells from one left of the run to one right of it, each cell in
+// slot order (the bounds of a row's cells are loaded by the lanes side by side).
+// A round takes L U consecutive candidates of a cell, lane l of every group the
+// candidates l, l + L, ...; a group tests them if the cell lies within one cell
+// of its own along x. Per candidate slice of L, a group ballot ranks the
+// neighbours found, so that each group sees the candidates of its 3^D cells in
+// the order rows (dz, dy), then dx = -1, 0, 1, then slot, and emit(j, code,
+// wall_j, rank) is called for each, with code = (dx + 1) + 3 (dy + 1) + 9 (dz +
+// 1). Returns the group's neighbour count. The FP32C test takes the FP32
+// separation from cell offsets (whose .w flags walls) and decides by the FP64
+// test inside the band around 3h; the FP64 path takes the FP64 test. The loop
+// has no divergent branch: out-of-range candidates are clamped and masked, and
+// the band test runs only when some lane of the warp needs it.
+template <int D, bool F32, int L, class Emit>
+__device__ __forceinline__ int slice_candidates(const Geom &G, const int *__restrict__ start, int cell_off, int cell,
+                                                bool active, int s, const double *__restrict__ x,
+                                                const float4 *__restrict__ off, const uint32_t *__restrict__ gid,
+                                                int n, int nf, Emit &&emit)
+{
+    constexpr unsigned full = 0xffffffffu;
+    constexpr int U = L >= 4 ? 1 : 4 / L;  // candidates per lane and round
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int sub = lane % L;
+    const unsigned first = (unsigned)(lane - sub);
+    const unsigned gbits = L == 32 ? full : ((1u << L) - 1u);
+    const unsigned below = (1u << sub) - 1u;
+    start += cell_off;            // the instance's cells, numbered from 0
+    const int lcell = active ? cell - cell_off : 0;
+    const int cx = lcell % G.nc[0];
+    const int crow = lcell / G.nc[0];
+    const float sf[3] = {G.s_f[0], G.s_f[1], G.s_f[2]};
+    const float rc2_lo = G.rc2_lo, rc2_hi = G.rc2_hi;
+    const double rc2 = G.rc2;
+    const float4 oi = F32 && active ? off[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double xi[3] = {0, 0, 0};
+    if (!F32 && active) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) xi[a] = x[(size_t)a * n + s];
+    }
+    int cnt = 0;
+    unsigned todo = __ballot_sync(full, active);
+    while (todo) {
+        // the groups whose home cell lies in the row of the first lane left
+        const int srow = __shfl_sync(full, crow, __ffs(todo) - 1);
+        const bool mine = ((todo >> lane) & 1u) && crow == srow;
+        todo &= ~__ballot_sync(full, mine);
+        const int xa = __reduce_min_sync(full, mine ? cx : 0x7fffffff);
+        const int xb = __reduce_max_sync(full, mine ? cx : -1);
+        const int ncx = xb - xa + 3;                 // cells of the stream in each row
+        const int sy = srow % G.nc[1], sz = srow / G.nc[1];
+        constexpr int zlo = D == 3 ? -1 : 0, zhi = D == 3 ? 1 : 0;
+        for (int dz = zlo; dz <= zhi; ++dz) {
+            int z = sz + dz;
+            if (D == 3 && (z < 0 || z >= G.nc[2])) {
+                if (!G.periodic[2]) continue;
+                z = z < 0 ? z + G.nc[2] : z - G.nc[2];
+            }
+            for (int dy = -1; dy <= 1; ++dy) {
+                int y = sy + dy;
+                if (y < 0 || y >= G.nc[1]) {
+                    if (!G.periodic[1]) continue;
+                    y = y < 0 ? y + G.nc[1] : y - G.nc[1];
+                }
+                const int row = (z * G.nc[1] + y) * G.nc[0];
+                for (int c0 = 0; c0 < ncx; c0 += kWarp) {
+                    // lane k holds the slot range of stream cell c0 + k (empty if off the grid)
+                    int kb = 0, ke = 0;
+                    if (c0 + lane < ncx) {
+                        int xc = xa - 1 + c0 + lane;
+                        bool ok = true;
+                        if (xc < 0 || xc >= G.nc[0]) {
+                            if (G.periodic[0]) xc = xc < 0 ? xc + G.nc[0] : xc - G.nc[0];
+                            else ok = false;
+                        }
+                        if (ok) {
+                            kb = start[row + xc];
+                            ke = start[row + xc + 1];
+                        }
+                    }
+                    const int mc = min(kWarp, ncx - c0);
+                    for (int t = 0; t < mc; ++t) {
+                        const int jb = __shfl_sync(full, kb, t), je = __shfl_sync(full, ke, t);
+                        if (jb == je) continue;
+                        const int dx = xa - 1 + c0 + t - cx;
+                        const bool part = mine && dx >= -1 && dx <= 1;
+                        if (!__any_sync(full, part)) continue;
+                        const int code = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                        const float4 ps = shifted_offset<D>(oi, dx, dy, dz, sf);
+                        for (int j0 = jb; j0 < je; j0 += L * U) {
+                            bool in[U], band[U], wl[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int j = j0 + u * L + sub;
+                                const bool cand = part && j < je && j != s;
+                                const int jc = j < je ? j : je - 1;   // in range, result unused
+                                if (F32) {
+                                    const float4 oj = off[jc];
+                                    float f0, f1, f2;
+                                    const float q2 = sep32<D>(ps, oj, f0, f1, f2);
+                                    in[u] = cand && q2 < rc2_lo;
+                                    band[u] = cand && q2 >= rc2_lo && q2 < rc2_hi;
+                                    wl[u] = oj.w != 0.f;
+                                } else {
+                                    double d[3];
+#pragma unroll
+                                    for (int a = 0; a < D; ++a) {
+                                        double v = __dsub_rn(xi[a], x[(size_t)a * n + jc]);
+                                        if (G.periodic[a]) {
+                                            if (v > G.halfL[a]) v = __dsub_rn(v, G.L[a]);
+                                            else if (v < -G.halfL[a]) v = __dadd_rn(v, G.L[a]);
+                                        }
+                                        d[a] = v;
+                                    }
+                                    double r2 = __dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1]));
+                                    if (D == 3) r2 = __dadd_rn(r2, __dmul_rn(d[2], d[2]));
+                                    in[u] = cand && r2 < rc2;
+                                    band[u] = false;
+                                    wl[u] = gid[jc] >= (uint32_t)nf;
+                                }
+                            }
+                            if (F32) {
+                                bool any_band = false;
+#pragma unroll
+                                for (int u = 0; u < U; ++u) any_band |= band[u];
+                                // the FP64 decision inside the band (rare)
+                                if (__any_sync(full, any_band)) {
+#pragma unroll
+                                    for (int u = 0; u < U; ++u) {
+                                        if (band[u]) {
+                                            double e[3];
+                                            in[u] = sep64<D>(G, x, n, s, j0 + u * L + sub, e) < rc2;
+                                        }
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const unsigned bal = L == 1 ? (in[u] ? 1u : 0u)
+                                                            : (__ballot_sync(full, in[u]) >> first) & gbits;
+                                if (in[u]) emit(j0 + u * L + sub, code, wl[u], cnt + __popc(bal & below));
+                                cnt += __popc(bal);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return cnt;
+}
+
+// r_ij and |r_ij|^2 in the working precision T of a listed neighbour j (cell
+// shift (dx, dy, dz)), with the arithmetic of the traversal test.
 template <int D, bool F32, typename T>
-__device__ __forceinline__ bool neighbour(const Geom &G, const double *__restrict__ x, const float4 *__restrict__ off,
-                                          int n, int i, int j, float4 oi, int dx, int dy, int dz, T *d, T &r2)
+__device__ __forceinline__ void listed_sep(const Geom &G, const double *__restrict__ x, const float4 *__restrict__ off,
+                                           int n, int i, int j, float4 oi, int dx, int dy, int dz, T *d, T &r2)
 {
     if (F32) {
-        float4 oj = off[j];
-        using A = Ar<float>;
-        const float f0 = A::fma(-(float)dx, G.s_f[0], A::sub(oi.x, oj.x));
-        const float f1 = A::fma(-(float)dy, G.s_f[1], A::sub(oi.y, oj.y));
-        const float f2 = D == 3 ? A::fma(-(float)dz, G.s_f[2], A::sub(oi.z, oj.z)) : 0.f;
-        float q2 = A::fma(f1, f1, A::mul(f0, f0));
-        if (D == 3) q2 = A::fma(f2, f2, q2);
-        if (q2 >= G.rc2_hi) return false;
-        if (q2 >= G.rc2_lo) {
-            double e[3];
-            if (!(sep64<D>(G, x, n, i, j, e) < G.rc2)) return false;
-        }
+        float f0, f1, f2;
+        const float q2 = sep32<D>(shifted_offset<D>(oi, dx, dy, dz, G.s_f), off[j], f0, f1, f2);
         d[0] = (T)f0;
         d[1] = (T)f1;
         if (D == 3) d[2] = (T)f2;
         r2 = (T)q2;
-        return true;
     } else {
         double e[3];
-        double q2 = sep64<D>(G, x, n, i, j, e);
-        if (!(q2 < G.rc2)) return false;
+        const double q2 = sep64<D>(G, x, n, i, j, e);
 #pragma unroll
         for (int a = 0; a < D; ++a) d[a] = (T)e[a];
         r2 = (T)q2;
-        return true;
     }
+}
+
+// Cell shift of a list entry.
+__device__ __forceinline__ void decode_shift(int code, int &dx, int &dy, int &dz)
+{
+    dx = code % 3 - 1;
+    dy = (code / 3) % 3 - 1;
+    dz = code / 9 - 1;
 }
 
 // Reciprocal square root and division in the working precision: the fast
@@ -177,34 +302,77 @@ __device__ __forceinline__ void block_copy(T &dst, const T &src)
     __syncthreads();
 }
 
+// ------------------------------------------------------------- neighbour lists
+
+// Neighbour list of every slot (order of the latest binning) at positions xpos:
+// pj = j (| kWallBit when j is a wall) and pcode = the cell shift, in candidate
+// order, sliced by warp (entry k of slot s at ((s/32) K + k) 32 + s%32), and
+// pcount. One lane per slot (slice_candidates); the pair kernels then walk the
+// lists densely.
+template <int D, bool F32, int L>
+__global__ void __launch_bounds__(kBlock) k_nlist(Buffers B, const double *__restrict__ xpos,
+                                                  const int *__restrict__ cell, const uint32_t *__restrict__ gid)
+{
+    constexpr int SPB = kBlock / L;       // slots per block
+    __shared__ Geom G;
+    const int inst = block_instance(B, blockIdx.x * SPB);
+    block_copy(G, B.geo[inst]);
+    const int cell_off = B.inst[inst].cell_off;
+    const int s = blockIdx.x * SPB + threadIdx.x / L;
+    const int n = B.n, K = B.K;
+    // every lane stays to the end: the traversal runs warp-synchronously
+    const bool act = s < n && gid[s] != kNoParticle;
+    const size_t base = (size_t)(s >> 5) * K * kWarp + (s & 31);
+    int cnt = slice_candidates<D, F32, L>(G, B.cell_start, cell_off, act ? cell[s] : 0, act, s, xpos, B.off, gid, n,
+                                          B.nf, [&](int j, int code, bool wall, int pos) {
+                                              if (pos < K) {
+                                                  const size_t e = base + (size_t)pos * kWarp;
+                                                  B.pj[e] = (uint32_t)j | (wall ? kWallBit : 0u);
+                                                  B.pcode[e] = (uint8_t)code;
+                                              }
+                                          });
+    if (s >= n || threadIdx.x % L != 0) return;
+    if (cnt > K) {
+        atomicOr(B.err, kErrCapacity);
+        cnt = K;
+    }
+    B.pcount[s] = cnt;
+}
+
 // ---------------------------------------------------------------- walls, state n
 
 // Adami et al. wall values at state n in order B: p_w = (sum_f p_f W + rho0 g .
 // sum_f r_wf W) / sum_f W, ghost velocity 2 v_w - sum_f V_f W / sum_f W; written
-// into the packed (V, p) of the wall slot. L lanes per wall particle.
-template <int D, bool F32, int L>
+// into the packed (V, p) of the wall slot. One lane per wall slot, over its
+// neighbour list at r^n.
+template <int D, bool F32>
 __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     __shared__ Geom G;
     __shared__ Phys P;
-    const int inst = block_instance(B, blockIdx.x * (kBlock / L));
+    const int inst = block_instance(B, blockIdx.x * kBlock);
     block_copy(G, B.geo[inst]);
     block_copy(P, B.phys[inst]);
-    const int cell_off = B.inst[inst].cell_off;
-    const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
-    const int s = blockIdx.x * (kBlock / L) + grp;
-    // every lane stays to the end: the partial sums are merged by full-warp shuffles
-    const uint32_t gs = s < B.n ? B.gid_b[s] : kNoParticle;
-    const bool wall = gs != kNoParticle && gs >= (uint32_t)B.nf;
+    const int s = blockIdx.x * kBlock + threadIdx.x;
+    if (s >= B.n) return;
+    const uint32_t gs = B.gid_b[s];
+    if (gs == kNoParticle || gs < (uint32_t)B.nf) return;
     const auto *nb = nb_ptr<T>(B, 1);
-    const float4 oi = wall && F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
     double acc[6] = {0, 0, 0, 0, 0, 0};   // sum W, sum p W, sum rho0 (g . r) W, sum V W
     const double sigma = P.sig_h * P.h;
-    if (wall) group_candidates<D, L>(G, B.cell_start, cell_off, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
-        if (!valid || j == s || B.gid_b[j] >= (uint32_t)B.nf) return;
+    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+    const int cnt = B.pcount[s];
+    for (int k = 0; k < cnt; ++k) {
+        const size_t e = base + (size_t)k * kWarp;
+        const uint32_t jb = B.pj[e];
+        if (jb & kWallBit) continue;                    // fluid neighbours only
+        const int j = (int)jb;
+        int dx, dy, dz;
+        decode_shift(B.pcode[e], dx, dy, dz);
         T d[3], r2;
-        if (!neighbour<D, F32, T>(G, B.x_b, B.off, B.n, s, j, oi, dx, dy, dz, d, r2)) return;
+        listed_sep<D, F32, T>(G, B.x_b, B.off, B.n, s, j, oi, dx, dy, dz, d, r2);
         const double W = sigma * (double)quintic_w<T>(Ar<T>::mul(sqrt(r2), (T)P.inv_h));
         const auto q = nb[j];
         double gr = 0;
@@ -216,12 +384,7 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
         acc[3] += (double)q.x * W;
         acc[4] += (double)q.y * W;
         acc[5] += (double)q.z * W;
-    });
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int t = 0; t < 6; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-    if (!wall || lane_in != 0) return;
+    }
     const double sw = acc[0];
     double gv[3];
     for (int a = 0; a < 3; ++a) {
@@ -235,83 +398,69 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
 
 // ------------------------------------------------------------------ state n pass
 
-// Rates at (r^n, V^n, p^n) in order B, L lanes per particle (partial sums
-// merged by shuffles). With PRED, also the predictor of Eqs. (v0, r0):
-// V^0 = V^n + dt F^n, r^0 = r^n + dt V^n + dt^2/2 F^n; the first pressure half
-// step p-hat^0 = p^n + dtau/2 dp^n/dtau (Eq. pkstar_frozen with the state-n
-// rate); and the BDF2 source (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact),
-// all in FP64, one thread per particle in whole warps.
-template <int D, bool F32, bool PRED, int L, bool WALLS>
+// Rates at (r^n, V^n, p^n) in order B, one lane per slot over its neighbour list
+// at r^n. With PRED, also the predictor of Eqs. (v0, r0): V^0 = V^n + dt F^n,
+// r^0 = r^n + dt V^n + dt^2/2 F^n; the first pressure half step p-hat^0 = p^n +
+// dtau/2 dp^n/dtau (Eq. pkstar_frozen with the state-n rate); and the BDF2
+// source (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact), all in FP64.
+template <int D, bool F32, bool PRED, bool WALLS>
 __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
-    constexpr int PPB = kBlock / L;
-    __shared__ T part[D + 1][PPB];
     __shared__ Geom G;
     __shared__ Phys P;
-    const int inst = block_instance(B, blockIdx.x * PPB);
+    const int inst = block_instance(B, blockIdx.x * kBlock);
     block_copy(G, B.geo[inst]);
     block_copy(P, B.phys[inst]);
-    const int cell_off = B.inst[inst].cell_off;
     const int n = B.n;
-    const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
-    const int s = blockIdx.x * PPB + grp;
-    const bool fluid = s < n && B.gid_b[s] < (uint32_t)B.nf;
-    {
-        const auto *nb = nb_ptr<T>(B, 1);
-        const PairConst<T> k = pair_const<T>(P);
-        Acc ap, Fa[3];
-        if (fluid) {
-            const auto qi = nb[s];
-            const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
-            const T pi = (T)qi.w;
-            const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
-            group_candidates<D, L>(G, B.cell_start, cell_off, B.cell_b[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
-                if (!valid || j == s) return;
-                T d[3], r2;
-                if (!neighbour<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2)) return;
-                T g[3], F;
-                grad_coef<D, T>(P, d, r2, g, F);
-                const auto qj = nb[j];
-                const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
-                T vd[3] = {vv[0], vv[1], vv[2]};
-                if (WALLS && B.gid_b[j] >= (uint32_t)B.nf) {
-                    for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
-                }
-                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
-            });
-        }
-#pragma unroll
-        for (int o = L / 2; o > 0; o >>= 1) {
-            ap.shfl_merge(o);
-#pragma unroll
-            for (int a = 0; a < D; ++a) Fa[a].shfl_merge(o);
-        }
-        if (lane_in == 0) {
-            part[0][grp] = (T)ap.value();
-#pragma unroll
-            for (int a = 0; a < D; ++a) part[1 + a][grp] = (T)Fa[a].value();
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x >= PPB) return;
-    const int s2 = blockIdx.x * PPB + threadIdx.x;
-    if (s2 >= n || B.gid_b[s2] == kNoParticle) return;
-    if (B.gid_b[s2] >= (uint32_t)B.nf) {
+    const int s = blockIdx.x * kBlock + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t gs = B.gid_b[s];
+    if (gs == kNoParticle) return;
+    if (gs >= (uint32_t)B.nf) {
         if (PRED) {
-            for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s2] = B.x_b[(size_t)a * n + s2];
+            for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s] = B.x_b[(size_t)a * n + s];
         }
         return;
     }
-    const double apv = (double)part[0][threadIdx.x];
+    const auto *nb = nb_ptr<T>(B, 1);
+    const PairConst<T> k = pair_const<T>(P);
+    Acc ap, Fa[3];
+    {
+        const auto qi = nb[s];
+        const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
+        const T pi = (T)qi.w;
+        const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+        const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+        const int cnt = B.pcount[s];
+        for (int q = 0; q < cnt; ++q) {
+            const size_t e = base + (size_t)q * kWarp;
+            const uint32_t jb = B.pj[e];
+            const int j = (int)(jb & ~kWallBit);
+            int dx, dy, dz;
+            decode_shift(B.pcode[e], dx, dy, dz);
+            T d[3], r2;
+            listed_sep<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2);
+            T g[3], F;
+            grad_coef<D, T>(P, d, r2, g, F);
+            const auto qj = nb[j];
+            const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
+            T vd[3] = {vv[0], vv[1], vv[2]};
+            if (WALLS && (jb & kWallBit)) {
+                for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
+            }
+            pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
+        }
+    }
+    const double apv = (double)(T)ap.value();
     double Fv[3];
-    for (int a = 0; a < D; ++a) Fv[a] = __dadd_rn((double)part[1 + a][threadIdx.x], P.g[a]);
-    B.ap_b[s2] = apv;
-    for (int a = 0; a < D; ++a) B.f_b[(size_t)a * n + s2] = Fv[a];
+    for (int a = 0; a < D; ++a) Fv[a] = __dadd_rn((double)(T)Fa[a].value(), P.g[a]);
+    B.ap_b[s] = apv;
+    for (int a = 0; a < D; ++a) B.f_b[(size_t)a * n + s] = Fv[a];
     if (PRED) {
         for (int a = 0; a < D; ++a) {
-            const size_t q = (size_t)a * n + s2;
+            const size_t q = (size_t)a * n + s;
             // explicit roundings: the same bits in every kernel variant
             const double V = B.vn_b[q];
             double xp = __fma_rn(0.5 * P.dt * P.dt, Fv[a], __fma_rn(P.dt, V, B.x_b[q]));
@@ -323,20 +472,19 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
             B.v0_b[q] = __fma_rn(P.dt, Fv[a], V);
             B.s_b[q] = __dmul_rn(P.kappa, __fma_rn(__fma_rn(-4.0, V, B.vnm1_b[q]), P.inv_2dt, -P.g[a]));
         }
-        B.ph0_b[s2] = __fma_rn(0.5 * P.dtau, apv, B.pn_b[s2]);
+        B.ph0_b[s] = __fma_rn(0.5 * P.dtau, apv, B.pn_b[s]);
     }
 }
 
 // --------------------------------------------------------------- pair cache
 
-// For every slot (order of the latest binning) the list of its neighbours with
-// gradW_ij and F_ij (fluid slot), or W_wf and rho0 (g . r_wf) W_wf (wall slot),
-// sliced by warp so that entry k of the 32 slots of a warp is contiguous. L lanes
-// per slot test candidates side by side; a group ballot keeps the list in
-// candidate order. Block 0 also resets the pseudo-time loop state.
-template <int D, bool F32, int L>
+// The pair coefficients of every list entry (order of the latest binning):
+// gradW_ij and F_ij for a fluid slot, W_wf and rho0 (g . r_wf) W_wf for a wall
+// slot, at the entry's place in the sliced layout. One lane per slot. Block 0
+// also resets the pseudo-time loop state.
+template <int D, bool F32>
 __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *__restrict__ xpos,
-                                                       const int *__restrict__ cell, const uint32_t *__restrict__ gid)
+                                                       const uint32_t *__restrict__ gid)
 {
     using T = typename std::conditional<F32, float, double>::type;
     __shared__ Geom G;
@@ -357,32 +505,25 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
             B.ctrl->active = B.ninst;
         }
     }
-    const int inst = block_instance(B, blockIdx.x * (kBlock / L));
+    const int inst = block_instance(B, blockIdx.x * kBlock);
     block_copy(G, B.geo[inst]);
     block_copy(P, B.phys[inst]);
-    const int cell_off = B.inst[inst].cell_off;
-    const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
-    const int s = blockIdx.x * (kBlock / L) + grp;
-    if (s >= B.n) return;                                  // whole group leaves together
-    const int n = B.n, K = B.K;
-    if (gid[s] == kNoParticle) {
-        if (lane_in == 0) B.pcount[s] = 0;
-        return;
-    }
+    const int s = blockIdx.x * kBlock + threadIdx.x;
+    const int n = B.n;
+    if (s >= n || gid[s] == kNoParticle) return;
     const bool wall_s = gid[s] >= (uint32_t)B.nf;
-    const size_t base = (size_t)(s >> 5) * K * kWarp + (s & 31);
+    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
     const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
-    const unsigned gshift = (threadIdx.x & 31) - lane_in;   // first lane of the group in the warp
-    const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << gshift;
-    int cnt = 0;
     const T sigma = (T)(P.sig_h * P.h);
-    group_candidates<D, L>(G, B.cell_start, cell_off, cell[s], lane_in, [&](bool valid, int j, int dx, int dy, int dz) {
+    const int cnt = B.pcount[s];
+    for (int q = 0; q < cnt; ++q) {
+        const size_t e = base + (size_t)q * kWarp;
+        const uint32_t jb = B.pj[e];
+        const int j = (int)(jb & ~kWallBit);
+        int dx, dy, dz;
+        decode_shift(B.pcode[e], dx, dy, dz);
         T d[3], r2;
-        const bool in = valid && j != s && neighbour<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2);
-        const unsigned bal = __ballot_sync(gmask, in) >> gshift;
-        const int pos = cnt + __popc(bal & ((1u << lane_in) - 1u));
-        cnt += __popc(bal);
-        if (!in || pos >= K) return;
+        listed_sep<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2);
         T c4[4] = {T(0), T(0), T(0), T(0)};
         if (wall_s) {
             const T W = Ar<T>::mul(sigma, quintic_w<T>(Ar<T>::mul(sqrt(r2), (T)P.inv_h)));
@@ -403,24 +544,13 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
                 c4[3] = F;
             }
         }
-        const uint32_t jb = (uint32_t)j | (gid[j] >= (uint32_t)B.nf ? kWallBit : 0u);
-        const size_t e = base + (size_t)pos * kWarp;
         if (F32) {
             float4 v = make_float4((float)c4[0], (float)c4[1], (float)c4[2], (float)c4[3]);
             if (D == 2) v.w = __uint_as_float(jb);
-            else B.pj[e] = jb;
             B.pc32[e] = v;
         } else {
             B.pc64[e] = make_double4_32a((double)c4[0], (double)c4[1], (double)c4[2], (double)c4[3]);
-            B.pj[e] = jb;
         }
-    });
-    if (lane_in == 0) {
-        if (cnt > K) {
-            atomicOr(B.err, kErrCapacity);
-            cnt = K;
-        }
-        B.pcount[s] = cnt;
     }
 }
 
@@ -434,35 +564,57 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
         else { constexpr int D = 3; constexpr bool F32 = true; __VA_ARGS__; }                       \
     } while (0)
 
-constexpr int kTravLanes = 8;   // lanes per particle of the traversal kernels
+inline int trav_blocks(int n) { return (n + kBlock - 1) / kBlock; }
 
-inline int trav_blocks(int n) { return (n + kBlock / kTravLanes - 1) / (kBlock / kTravLanes); }
+// Lanes per slot of the list build: enough warps to fill the GPU on small
+// problems (each group's candidate chain is latency-bound), one lane per slot
+// on large ones.
+int nlist_lanes(int n)
+{
+    int L = 1;
+    while (L < 8 && (long long)n * L < 400000) L *= 2;
+    return L;
+}
 
+void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
+{
+    const int L = nlist_lanes(B.n);
+    const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
+    if (L == 1) DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist<D, F32, 1><<<nb, kBlock, 0, st>>>(B, xpos, cell, gid)));
+    else if (L == 2) DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist<D, F32, 2><<<nb, kBlock, 0, st>>>(B, xpos, cell, gid)));
+    else if (L == 4) DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist<D, F32, 4><<<nb, kBlock, 0, st>>>(B, xpos, cell, gid)));
+    else DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist<D, F32, 8><<<nb, kBlock, 0, st>>>(B, xpos, cell, gid)));
+}
+
+// Neighbour lists at r^n (order B), then the wall values and the state-n pass.
 int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st)
 {
-    int k = 0;
     const int nb = trav_blocks(B.n);
+    launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st);
+    int k = 1;
     if (B.nw > 0) {
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, kTravLanes><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32><<<nb, kBlock, 0, st>>>(B)));
         ++k;
     }
     const bool w = B.nw > 0;
     if (predictor && w)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, true><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, true><<<nb, kBlock, 0, st>>>(B)));
     else if (predictor)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, kTravLanes, false><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, false><<<nb, kBlock, 0, st>>>(B)));
     else if (w)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, true><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, true><<<nb, kBlock, 0, st>>>(B)));
     else
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, kTravLanes, false><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, false><<<nb, kBlock, 0, st>>>(B)));
     return k + 1;
 }
 
+// Neighbour lists at xpos, then the pair coefficients.
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
 {
-    DTSPH_DISPATCH(B.dim, B.fp32c,
-                   (k_pair_cache<D, F32, kTravLanes><<<trav_blocks(B.n), kBlock, 0, st>>>(B, xpos, cell, gid)));
-    return 1;
+    const int nb = trav_blocks(B.n);
+    launch_nlist(B, xpos, cell, gid, st);
+    DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
+    return 2;
 }
 
 }  // namespace dtsph
