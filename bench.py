@@ -70,15 +70,16 @@ def make_workload(name: str, n_side: int, re: float):
 class Job:
     """One context running a workload: a single instance or a batch."""
 
-    def __init__(self, dt, work, precision, stream=None, graph=2):
+    def __init__(self, dt, work, precision, stream=None, graph=2, lanes=0):
         self.dt = dt
         self.batch = isinstance(work, list)
         if self.batch:
-            self.sim = dt.Batch([d["cfg"] for d in work], precision=precision, stream=stream, graph=graph)
+            self.sim = dt.Batch([d["cfg"] for d in work], precision=precision, stream=stream, graph=graph,
+                                lanes=lanes)
             self.sim.set_state(work)
             self.nfs = [d["nf"] for d in work]
         else:
-            self.sim = dt.Simulation(work["cfg"], precision=precision, stream=stream, graph=graph)
+            self.sim = dt.Simulation(work["cfg"], precision=precision, stream=stream, graph=graph, lanes=lanes)
             nf = work["nf"]
             walls = None if work["vw"] is None else (work["x"][nf:], work["vw"])
             self.sim.set_state(work["x"][:nf], work["v"], work["p"], work["v_prev"], walls=walls)
@@ -130,6 +131,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--graph", type=int, default=2, help="2: step graph with the persistent loop kernel; "
                     "1: step graph with a while node; 0: plain launches (per-kernel profiling)")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="lanes per particle of the iterate kernel (0: autotuned)")
     return ap.parse_args()
 
 
@@ -196,11 +199,11 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- our arm
 
-def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2):
+def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, lanes=0):
     """Times `steps` real steps after `warmup`; L2 flushed before each step.
     Returns (particle-iterations/s, ms per step, iterations, launches, job)."""
     stream = torch.cuda.Stream()
-    job = Job(dt, d, precision, stream=stream, graph=graph)
+    job = Job(dt, d, precision, stream=stream, graph=graph, lanes=lanes)
     job.step(warmup)
     job.sync()
     l0 = dt.dtsph_kernel_launches(job.ctx)
@@ -221,10 +224,10 @@ def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2):
     return rate, sum(ms) / steps, iters, launches, job
 
 
-def run_e2e(dt, torch, d, precision, steps, graph=2):
+def run_e2e(dt, torch, d, precision, steps, graph=2, lanes=0):
     """End to end through the C ABI with host arrays: per step the state goes
     host -> device, one real step runs, the state comes back device -> host."""
-    job = Job(dt, d, precision, graph=graph)     # allocation and graph build outside the timed region
+    job = Job(dt, d, precision, graph=graph, lanes=lanes)   # allocation and graph build outside the timed region
     job.step(1)
     job.sync()
     ctx, dim = job.ctx, (d[0] if job.batch else d)["cfg"]["dim"]
@@ -302,7 +305,7 @@ def main_ours(args):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         rate32, ms32, it32, launches, sim32 = run_gpu_path(dt, torch, d, dt.DTSPH_FP32C, args.steps, args.warmup,
-                                                           flush, args.graph)
+                                                           flush, args.graph, args.lanes)
     torch.cuda.synchronize()
     # whole-job throughput: every rank ran the same workload independently
     t_rank = ms32 * args.steps
@@ -319,7 +322,7 @@ def main_ours(args):
     linf = None
     if not args.no_fp64:
         rate64, ms64, it64, _, sim64 = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup, flush,
-                                                    args.graph)
+                                                    args.graph, args.lanes)
         v32, v64 = sim32.velocities(), sim64.velocities()
         linf = float(np.max(np.abs(v32 - v64)) / np.max(np.abs(v64)))
         ms_it64, bytes_it64, _ = dt.dtsph_probe_iterate(sim64.ctx, 20)
@@ -333,7 +336,7 @@ def main_ours(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_it / (ms_it * 1e-3) / 1e9
-    e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph)
+    e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, args.lanes)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",

@@ -470,6 +470,7 @@ int device_error(dtsph_ctx *c)
         return fail(c, DTSPH_E_CAPACITY, "a particle had more than %d neighbours (raise max_neighbors)", c->B.K);
     if (e & kErrDomain) return fail(c, DTSPH_E_DOMAIN, "a particle left the box of a non-periodic axis");
     if (e & kErrBarrier) return fail(c, DTSPH_E_TIMEOUT, "a grid barrier of the persistent loop timed out");
+    if (e & kErrCopy) return fail(c, DTSPH_E_TIMEOUT, "a bulk copy of pair-cache rows did not complete");
     return DTSPH_OK;
 }
 

@@ -14,7 +14,7 @@ constexpr int kWarp = 32;
 constexpr uint32_t kWallBit = 0x80000000u;   // set in a cached neighbour index when j is a wall
 
 // Error bits raised by kernels into Buffers::err (read by dtsph_sync).
-enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u };
+enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy = 8u };
 
 // A context advances one or more independent simulations ("instances") together.
 // Instance i owns the slot range [slot_off, slot_off + nf + nw) of every particle

@@ -27,6 +27,7 @@
 //    the same partials in the same order and takes the same stop decision.
 #include <algorithm>
 
+#include "bulk.cuh"
 #include "pair_terms.cuh"
 
 namespace dtsph {
@@ -179,11 +180,59 @@ __device__ __forceinline__ void warp_sum2(float &s, float &e)
     }
 }
 
+// Pair-cache rows of one warp in shared memory (one lane per slot). The 32 slots
+// of the warp form one slice of the sliced cache, so their entries k = 0, 1, ...
+// are consecutive rows (32 coefficient records, then, where the index is kept
+// apart, 32 indices). Chunks of kRows rows arrive by bulk copies, kStages chunks
+// in flight, each completing on its stage's mbarrier.
+template <int D, bool F32>
+struct RowFmt {
+    static constexpr int kCoef = F32 ? 16 : 32;                 // bytes of one coefficient record
+    static constexpr bool kSepJ = !(F32 && D == 2);             // index in pj (2D FP32C: in .w)
+    static constexpr int kRows = F32 ? 2 : 1;                   // rows per chunk
+    static constexpr int kStages = 3;
+    static constexpr int kCoefRow = kWarp * kCoef;
+    static constexpr int kJRow = kSepJ ? kWarp * 4 : 0;
+    static constexpr int kStageBytes = kRows * (kCoefRow + kJRow);
+};
+
+template <int D, bool F32>
+struct alignas(128) WarpRing {
+    unsigned char buf[RowFmt<D, F32>::kStages][RowFmt<D, F32>::kStageBytes];
+    uint64_t bar[RowFmt<D, F32>::kStages];
+};
+
+struct NoRing {};
+
 template <typename T, int D, int L>
 struct TileShared {
     T part[D + 1][kBlock / L];
     double red[2][kBlock / kWarp];
+    typename std::conditional<L == 1, WarpRing<D, std::is_same<T, float>::value>[kBlock / kWarp], NoRing>::type ring;
 };
+
+// Bulk-copy state of a warp's ring, kept across tiles: chunks consumed so far
+// (stage = pos % kStages, phase parity = (pos / kStages) & 1), and whether every
+// wait so far completed.
+struct RingPos {
+    uint32_t pos = 0;
+    bool ok = true;
+};
+
+// Initialises the mbarriers of every warp's ring (whole block, then syncs).
+template <typename T, int D, int L>
+__device__ __forceinline__ void ring_init(TileShared<T, D, L> &sh)
+{
+    if constexpr (L == 1) {
+        constexpr bool F32 = std::is_same<T, float>::value;
+        if ((threadIdx.x & 31) == 0) {
+            auto &rg = sh.ring[threadIdx.x >> 5];
+            for (int st = 0; st < RowFmt<D, F32>::kStages; ++st) mbar_init(&rg.bar[st], 1);
+            mbar_fence_init();
+        }
+    }
+    __syncthreads();
+}
 
 // One iteration over tile `tile` (slots tile*PPB .. tile*PPB+PPB-1, PPB = 256/L),
 // by the whole block. Writes iterate k+1 of the tile's fluid particles and
@@ -200,7 +249,7 @@ struct TileShared {
 template <int D, bool F32, bool WALLS, int L>
 __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, int cur, int tile,
                                                TileShared<typename std::conditional<F32, float, double>::type, D, L> &sh,
-                                               double &blk_ap, double &blk_av)
+                                               RingPos &rp, double &blk_ap, double &blk_av)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
@@ -228,32 +277,112 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
             cnt = B.pcount[s];
         }
         Acc ap, Fa[3];
-        const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-        // the cache entry of the next pair is loaded before the current one is
-        // used, so two independent loads are in flight per lane
-        CacheEntry<T, D, F32> nx;
-        if (lane_in < cnt) nx.load(B, base + (size_t)lane_in * kWarp);
-        for (int kk = lane_in; kk < cnt; kk += L) {
-            const CacheEntry<T, D, F32> ce = nx;
-            if (kk + L < cnt) nx.load(B, base + (size_t)(kk + L) * kWarp);
-            const T *g = ce.g;
-            const T F = ce.F;
-            const uint32_t jb = ce.jb;
-            const int j = (int)(jb & ~kWallBit);
-            T vj[3], pj;
-            if (F32) {
-                float4 q = B.nb32[cur][j];
-                vj[0] = q.x; vj[1] = q.y; vj[2] = q.z; pj = q.w;
-            } else {
-                double4_32a q = B.nb64[cur][j];
-                vj[0] = (T)q.x; vj[1] = (T)q.y; vj[2] = (T)q.z; pj = (T)q.w;
-            }
-            if (WALLS && (jb & kWallBit)) {
+        // the pair terms of one cache entry with its gathered neighbour state
+        using Q = typename std::conditional<F32, float4, double4_32a>::type;
+        const Q *nbq = F32 ? (const Q *)(const void *)B.nb32[cur] : (const Q *)(const void *)B.nb64[cur];
+        auto pair = [&](const CacheEntry<T, D, F32> &ce, const Q &q) {
+            const int j = (int)(ce.jb & ~kWallBit);
+            const T vj[3] = {(T)q.x, (T)q.y, (T)q.z};
+            const T pj = (T)q.w;
+            if (WALLS && (ce.jb & kWallBit)) {
                 T vd[3] = {T(0), T(0), T(0)};
                 for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_a[(size_t)a * n + j];
-                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vj, pj, ap, Fa);
+                pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vd, vj, pj, ap, Fa);
             } else {
-                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vj, vj, pj, ap, Fa);
+                pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vj, vj, pj, ap, Fa);
+            }
+        };
+        if constexpr (L == 1) {
+            // the warp's rows stream through its shared-memory ring; the
+            // neighbour states of a chunk's rows are gathered together
+            using RF = RowFmt<D, F32>;
+            constexpr int R = RF::kRows, S = RF::kStages;
+            constexpr unsigned full = 0xffffffffu;
+            const int lane = threadIdx.x & 31;
+            auto &rg = sh.ring[threadIdx.x >> 5];
+            const int cmax = __reduce_max_sync(full, cnt);
+            const int nch = rp.ok ? (cmax + R - 1) / R : 0;
+            const size_t row0 = (size_t)(s >> 5) * B.K;      // first row of the warp's slice
+            const unsigned char *gcoef =
+                (F32 ? (const unsigned char *)B.pc32 : (const unsigned char *)B.pc64) + row0 * RF::kCoefRow;
+            const unsigned char *gj = (const unsigned char *)B.pj + row0 * (kWarp * 4);
+            auto issue = [&](int c) {        // lane 0: chunk c into its stage
+                const int st = (int)((rp.pos + (uint32_t)c) % S);
+                const int r0 = c * R, nr = min(R, cmax - r0);
+                const uint32_t bc = (uint32_t)(nr * RF::kCoefRow), bj = (uint32_t)(nr * RF::kJRow);
+                mbar_arrive_expect_tx(&rg.bar[st], bc + bj);
+                bulk_g2s(rg.buf[st], gcoef + (size_t)r0 * RF::kCoefRow, bc, &rg.bar[st]);
+                if (RF::kSepJ) bulk_g2s(rg.buf[st] + R * RF::kCoefRow, gj + (size_t)r0 * RF::kJRow, bj, &rg.bar[st]);
+            };
+            if (lane == 0)
+                for (int c = 0; c < S && c < nch; ++c) issue(c);
+            int c = 0;
+            for (; c < nch; ++c) {
+                const uint32_t q = rp.pos + (uint32_t)c;
+                const int st = (int)(q % S);
+                if (!mbar_wait(&rg.bar[st], (q / S) & 1u)) break;
+                const int r0 = c * R, nr = min(R, cmax - r0);
+                CacheEntry<T, D, F32> ce[R];
+                Q qv[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r < nr && r0 + r < cnt) {
+                        const unsigned char *rec = rg.buf[st] + r * RF::kCoefRow + lane * RF::kCoef;
+                        if (F32) {
+                            const float4 v = *(const float4 *)rec;
+                            ce[r].g[0] = (T)v.x;
+                            ce[r].g[1] = (T)v.y;
+                            if (D == 3) {
+                                ce[r].g[2] = (T)v.z;
+                                ce[r].F = (T)v.w;
+                            } else {
+                                ce[r].g[2] = T(0);
+                                ce[r].F = (T)v.z;
+                            }
+                            ce[r].jb = D == 2 ? __float_as_uint(v.w)
+                                              : *(const uint32_t *)(rg.buf[st] + R * RF::kCoefRow + r * RF::kJRow +
+                                                                    lane * 4);
+                        } else {
+                            const double4_32a v = *(const double4_32a *)rec;
+                            ce[r].g[0] = (T)v.x;
+                            ce[r].g[1] = (T)v.y;
+                            ce[r].g[2] = (T)v.z;
+                            ce[r].F = (T)v.w;
+                            ce[r].jb = *(const uint32_t *)(rg.buf[st] + R * RF::kCoefRow + r * RF::kJRow + lane * 4);
+                        }
+                        qv[r] = nbq[ce[r].jb & ~kWallBit];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (r < nr && r0 + r < cnt) pair(ce[r], qv[r]);
+                __syncwarp();
+                if (lane == 0 && c + S < nch) {
+                    fence_proxy_async_smem();
+                    issue(c + S);
+                }
+            }
+            if (c < nch) {
+                // a wait gave up: drain what is still in flight (bounded), stop
+                // using the ring and report
+                for (int d = c + 1; d < nch && d < c + S; ++d) {
+                    const uint32_t q = rp.pos + (uint32_t)d;
+                    mbar_wait(&rg.bar[q % S], (q / S) & 1u);
+                }
+                rp.ok = false;
+                if (lane == 0) atomicOr(B.err, kErrCopy);
+            }
+            rp.pos += (uint32_t)nch;
+        } else {
+            const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+            // the cache entry of the next pair is loaded before the current one
+            // is used, so two independent loads are in flight per lane
+            CacheEntry<T, D, F32> nx;
+            if (lane_in < cnt) nx.load(B, base + (size_t)lane_in * kWarp);
+            for (int kk = lane_in; kk < cnt; kk += L) {
+                const CacheEntry<T, D, F32> ce = nx;
+                if (kk + L < cnt) nx.load(B, base + (size_t)(kk + L) * kWarp);
+                pair(ce, nbq[ce.jb & ~kWallBit]);
             }
         }
 #pragma unroll
@@ -408,6 +537,8 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, unsigned long lon
     __shared__ Phys P;
     __shared__ int last, tlo_sh;
     if (!use_cond && B.ctrl->active == 0) return;     // whole grid agrees: nothing to do
+    ring_init(sh);
+    RingPos rp;
     const int inst = block_instance(B, blockIdx.x * PPB);
     LoopState *ls = B.ls + inst;
     int tlo, thi;
@@ -420,7 +551,7 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, unsigned long lon
             reinterpret_cast<int *>(&P)[w] = reinterpret_cast<const int *>(B.phys + inst)[w];
         __syncthreads();
         double a = 0, b = 0;
-        tile_iteration<D, F32, WALLS, L>(B, P, it & 1, blockIdx.x, sh, a, b);
+        tile_iteration<D, F32, WALLS, L>(B, P, it & 1, blockIdx.x, sh, rp, a, b);
         if (threadIdx.x == 0) {
             B.blk[2 * blockIdx.x] = a;
             B.blk[2 * blockIdx.x + 1] = b;
@@ -514,7 +645,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B)
         stop = 0;
         p_inst = -1;
     }
-    __syncthreads();
+    ring_init(sh);
+    RingPos rp;
     unsigned int epoch = 0;
     int r = -1, it = 0;
     for (;; ++it) {
@@ -540,7 +672,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B)
                 if (threadIdx.x == 0) p_inst = inst;
             }
             double a = 0, b = 0;
-            tile_iteration<D, F32, WALLS, L>(B, P, cur, t, sh, a, b);
+            tile_iteration<D, F32, WALLS, L>(B, P, cur, t, sh, rp, a, b);
             if (threadIdx.x == 0) {
                 blk[2 * t] = a;
                 blk[2 * t + 1] = b;

@@ -31,8 +31,8 @@ def instances():
     ]
 
 
-def solo(d, prec, graph, nsteps, **over):
-    sim = dt.Simulation(d["cfg"], precision=prec, graph=graph, lanes=2, **over)
+def solo(d, prec, graph, nsteps, lanes=2, **over):
+    sim = dt.Simulation(d["cfg"], precision=prec, graph=graph, lanes=lanes, **over)
     nf = d["nf"]
     walls = None if d["vw"] is None else (d["x"][nf:], d["vw"])
     sim.set_state(d["x"][:nf], d["v"], d["p"], d["v_prev"], walls=walls)
@@ -42,19 +42,20 @@ def solo(d, prec, graph, nsteps, **over):
     return out
 
 
+@pytest.mark.parametrize("lanes", [1, 2])
 @pytest.mark.parametrize("graph", [0, 1, 2])
 @pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
-def test_batch_equals_solo_runs(prec, graph):
+def test_batch_equals_solo_runs(prec, graph, lanes):
     insts = instances()
     nsteps = 3
-    b = dt.Batch([d["cfg"] for d in insts], precision=prec, graph=graph, lanes=2)
+    b = dt.Batch([d["cfg"] for d in insts], precision=prec, graph=graph, lanes=lanes)
     b.set_state(insts)
     b.step(nsteps)
     b.sync()
     xs, vs, ps = b.field(dt.FIELD_POS), b.field(dt.FIELD_VEL), b.field(dt.FIELD_P)
     iters = []
     for i, d in enumerate(insts):
-        x, v, p, st = solo(d, prec, graph, nsteps)
+        x, v, p, st = solo(d, prec, graph, nsteps, lanes)
         assert np.array_equal(xs[i], x) and np.array_equal(vs[i], v) and np.array_equal(ps[i], p), i
         assert b.stats(i) == st, i
         iters.append([s["iters"] for s in st])

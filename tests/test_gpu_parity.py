@@ -186,15 +186,18 @@ def test_graph_and_plain_launches_are_bit_identical():
     b.close()
 
 
+@pytest.mark.parametrize("lanes", [1, 2])
 @pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
 @pytest.mark.parametrize("case,nsteps", [("tgv2d_jitter", 4), ("cavity", 3), ("tgv3d", 2)])
-def test_persistent_loop_is_bit_identical(case, nsteps, prec):
+def test_persistent_loop_is_bit_identical(case, nsteps, prec, lanes):
     """graph = 2 (the whole pseudo-time loop in one cooperative kernel with a
     grid barrier per iteration) gives the same bits as graph = 1 (one launch
-    per iteration in a conditional while node), residuals included."""
+    per iteration in a conditional while node), residuals included. lanes = 1
+    streams the pair cache through the bulk-copy ring, which the persistent
+    kernel keeps across tiles and iterations."""
     d = CASES[case]()
-    a = make_sim(d, precision=prec, graph=1, lanes=2)
-    b = make_sim(d, precision=prec, graph=2, lanes=2)
+    a = make_sim(d, precision=prec, graph=1, lanes=lanes)
+    b = make_sim(d, precision=prec, graph=2, lanes=lanes)
     a.step(nsteps)
     b.step(nsteps)
     b.sync()
