@@ -70,16 +70,16 @@ def make_workload(name: str, n_side: int, re: float):
 class Job:
     """One context running a workload: a single instance or a batch."""
 
-    def __init__(self, dt, work, precision, stream=None, graph=2, lanes=0):
+    def __init__(self, dt, work, precision, stream=None, graph=2, kern=None):
+        kern = kern or {}
         self.dt = dt
         self.batch = isinstance(work, list)
         if self.batch:
-            self.sim = dt.Batch([d["cfg"] for d in work], precision=precision, stream=stream, graph=graph,
-                                lanes=lanes)
+            self.sim = dt.Batch([d["cfg"] for d in work], precision=precision, stream=stream, graph=graph, **kern)
             self.sim.set_state(work)
             self.nfs = [d["nf"] for d in work]
         else:
-            self.sim = dt.Simulation(work["cfg"], precision=precision, stream=stream, graph=graph, lanes=lanes)
+            self.sim = dt.Simulation(work["cfg"], precision=precision, stream=stream, graph=graph, **kern)
             nf = work["nf"]
             walls = None if work["vw"] is None else (work["x"][nf:], work["vw"])
             self.sim.set_state(work["x"][:nf], work["v"], work["p"], work["v_prev"], walls=walls)
@@ -133,6 +133,7 @@ def parse():
                     "1: step graph with a while node; 0: plain launches (per-kernel profiling)")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="lanes per particle of the iterate kernel (0: autotuned)")
+    ap.add_argument("--stages", type=int, default=0, help="staging depth with --lanes 1 (0: autotuned or 3)")
     return ap.parse_args()
 
 
@@ -199,11 +200,11 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- our arm
 
-def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, lanes=0):
+def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, kern=None):
     """Times `steps` real steps after `warmup`; L2 flushed before each step.
     Returns (particle-iterations/s, ms per step, iterations, launches, job)."""
     stream = torch.cuda.Stream()
-    job = Job(dt, d, precision, stream=stream, graph=graph, lanes=lanes)
+    job = Job(dt, d, precision, stream=stream, graph=graph, kern=kern)
     job.step(warmup)
     job.sync()
     l0 = dt.dtsph_kernel_launches(job.ctx)
@@ -224,10 +225,10 @@ def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, lanes=0
     return rate, sum(ms) / steps, iters, launches, job
 
 
-def run_e2e(dt, torch, d, precision, steps, graph=2, lanes=0):
+def run_e2e(dt, torch, d, precision, steps, graph=2, kern=None):
     """End to end through the C ABI with host arrays: per step the state goes
     host -> device, one real step runs, the state comes back device -> host."""
-    job = Job(dt, d, precision, graph=graph, lanes=lanes)   # allocation and graph build outside the timed region
+    job = Job(dt, d, precision, graph=graph, kern=kern)   # allocation and graph build outside the timed region
     job.step(1)
     job.sync()
     ctx, dim = job.ctx, (d[0] if job.batch else d)["cfg"]["dim"]
@@ -299,13 +300,14 @@ def main_ours(args):
     from paper_1904_00861_gb300 import build as b
     b.build()
     d, wcfg = make_workload(args.workload, args.n_side, args.re)
+    kern = dict(lanes=args.lanes, stages=args.stages)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if world > 1:
         tdist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         rate32, ms32, it32, launches, sim32 = run_gpu_path(dt, torch, d, dt.DTSPH_FP32C, args.steps, args.warmup,
-                                                           flush, args.graph, args.lanes)
+                                                           flush, args.graph, kern)
     torch.cuda.synchronize()
     # whole-job throughput: every rank ran the same workload independently
     t_rank = ms32 * args.steps
@@ -317,12 +319,13 @@ def main_ours(args):
         t_max = t_rank
     value = world * rate32 * t_rank / t_max
     lanes32, tune32 = dt.dtsph_tuning(sim32.ctx)
+    stages32, cand32 = dt.dtsph_tuning_candidates(sim32.ctx)
     ms_it, bytes_it, npairs = dt.dtsph_probe_iterate(sim32.ctx, 50)
     fp64 = None
     linf = None
     if not args.no_fp64:
         rate64, ms64, it64, _, sim64 = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup, flush,
-                                                    args.graph, args.lanes)
+                                                    args.graph, kern)
         v32, v64 = sim32.velocities(), sim64.velocities()
         linf = float(np.max(np.abs(v32 - v64)) / np.max(np.abs(v64)))
         ms_it64, bytes_it64, _ = dt.dtsph_probe_iterate(sim64.ctx, 20)
@@ -336,7 +339,7 @@ def main_ours(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_it / (ms_it * 1e-3) / 1e9
-    e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, args.lanes)
+    e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
@@ -349,7 +352,8 @@ def main_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "kernel": f"k_iterate<{wcfg['dims']},FP32C>", "bytes_per_launch": bytes_it,
                      "launch_ms": ms_it, "pairs": npairs, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
-        "autotune": {"lanes_per_particle": lanes32, "ms_by_lanes": tune32},
+        "autotune": {"lanes_per_particle": lanes32, "stages": stages32, "ms_by_lanes": tune32,
+                     "candidates": [{"lanes": L, "stages": S, "ms": m} for L, S, m in cand32]},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

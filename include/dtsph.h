@@ -84,6 +84,9 @@ typedef struct {
     int32_t lanes;            /* lanes per particle in the pseudo-iteration kernel: 1, 2, 4
                                  or 8; 0 = picked by the built-in autotuner after the first
                                  step (timed candidates, cached per shape in the process) */
+    int32_t stages;           /* staging depth of the one-lane kernel (lanes = 1): pair-cache
+                                 chunks in flight per warp in shared memory, 2..8; 0 = 3, or
+                                 picked by the autotuner together with lanes */
 } dtsph_params;
 
 typedef struct {
@@ -207,6 +210,15 @@ int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, 
  * and 8 lanes when this context tuned (-1 where it did not measure, e.g. when
  * the shape was already tuned in this process or lanes was fixed). */
 int dtsph_tuning(const dtsph_ctx *ctx, int32_t *lanes, float *ms_by_lanes);
+
+/* Every candidate the autotuner timed when this context tuned, in the order
+ * timed: lanes per particle, staging depth (0 for lanes > 1) and mean ms per
+ * launch of the pseudo-iteration kernel. Writes min(cap, count) entries of
+ * the three arrays (each may be NULL when cap is 0); *count = candidates timed
+ * (0 when the shape's choice came from the process cache or lanes was fixed);
+ * *stages = staging depth in use (0 when lanes > 1). */
+int dtsph_tuning_candidates(const dtsph_ctx *ctx, int32_t cap, int32_t *lanes, int32_t *stages, float *ms,
+                            int32_t *count, int32_t *stages_in_use);
 
 /* Allocation-free rate evaluation, for callers that cannot allocate device
  * memory when they need the rates: code running while a stream capture it does

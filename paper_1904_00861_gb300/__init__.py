@@ -42,6 +42,7 @@ class dtsph_params(C.Structure):
         ("g", C.c_double * 3), ("eps", C.c_double), ("stag_tol", C.c_double),
         ("stag_window", C.c_int32), ("max_iter", C.c_int32), ("edac", C.c_int32), ("edac_h2_literal", C.c_int32),
         ("fixed_iters", C.c_int32), ("max_neighbors", C.c_int32), ("graph", C.c_int32), ("lanes", C.c_int32),
+        ("stages", C.c_int32),
     ]
 
 
@@ -72,6 +73,8 @@ _SIGS = [
     ("dtsph_get_neighbors", C.c_int, [_VP, C.c_int64, _I64P, C.c_int64, _I64P]),
     ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
     ("dtsph_tuning", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    ("dtsph_tuning_candidates", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("dtsph_batch_create", C.c_int, [C.c_int32, C.POINTER(dtsph_params), _VP, C.POINTER(_VP)]),
     ("dtsph_batch_set_boundary", C.c_int, [_VP, C.c_int32, C.c_int64, _VP, _VP]),
     ("dtsph_batch_set_particles", C.c_int, [_VP, _I64P, _VP, _VP, _VP, _VP]),
@@ -130,7 +133,7 @@ def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) 
     """Fill dtsph_params from a plain dict (the keys of ``synth`` configs)."""
     d = dict(periodic=(0, 0, 0), lo=(0, 0, 0), hi=(1, 1, 1), rho0=1.0, beta=10.0, v_ref=1.0, eta=0.01, alpha=0.0,
              g=(0, 0, 0), eps=1e-3, stag_tol=0.05, stag_window=4, max_iter=1000, edac=1, edac_h2_literal=0,
-             fixed_iters=0, max_neighbors=0, lanes=0)
+             fixed_iters=0, max_neighbors=0, lanes=0, stages=0)
     d.update(cfg)
     d.update(over)
     p = dtsph_params()
@@ -144,7 +147,8 @@ def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) 
         p.g[a] = float(d["g"][a]) if a < len(d["g"]) else 0.0
     for k in ("h", "m", "rho0", "beta", "v_ref", "nu", "dt", "eta", "alpha", "eps", "stag_tol"):
         setattr(p, k, float(d[k]))
-    for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "max_neighbors", "lanes"):
+    for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "max_neighbors", "lanes",
+              "stages"):
         setattr(p, k, int(d[k]))
     return p
 
@@ -270,6 +274,17 @@ def dtsph_probe_iterate(ctx, launches: int = 20):
     npairs = C.c_int64()
     _check(ctx, lib().dtsph_probe_iterate(ctx, int(launches), C.byref(ms), C.byref(by), C.byref(npairs)))
     return float(ms.value), float(by.value), int(npairs.value)
+
+
+def dtsph_tuning_candidates(ctx):
+    """(staging depth in use, [(lanes, stages, ms per launch), ...] timed by the
+    autotuner, in the order timed)."""
+    cnt, s_use = C.c_int32(), C.c_int32()
+    _check(ctx, lib().dtsph_tuning_candidates(ctx, 0, None, None, None, C.byref(cnt), C.byref(s_use)))
+    n = cnt.value
+    la, st, ms = (C.c_int32 * max(n, 1))(), (C.c_int32 * max(n, 1))(), (C.c_float * max(n, 1))()
+    _check(ctx, lib().dtsph_tuning_candidates(ctx, n, la, st, ms, C.byref(cnt), C.byref(s_use)))
+    return s_use.value, [(int(la[i]), int(st[i]), float(ms[i])) for i in range(n)]
 
 
 def dtsph_tuning(ctx):

@@ -42,7 +42,8 @@ struct dtsph_ctx {
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
     bool tuned = false;
     int loop_grid = 0;
-    std::vector<std::pair<int, float>> tune_log;   // (lanes, ms per launch) of the last tuning
+    struct TuneRec { int lanes, stages; float ms; };
+    std::vector<TuneRec> tune_log;      // candidates timed by the last tuning
 };
 
 namespace {
@@ -158,6 +159,7 @@ void setup_phys(const dtsph_params &p, Phys &P)
     P.nu_e = p.h * P.c / 16.0;
     P.dt = p.dt;
     P.dtau = p.dt / p.beta;
+    P.dtau_f = (float)P.dtau;
     P.sig_h = quintic_sigma(p.dim, p.h) / p.h;
     P.eta_h2 = p.eta * p.h * p.h;
     P.edac_h2 = P.eta_h2;
@@ -195,11 +197,14 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
     if (p->graph < 0 || p->graph > 2) return fail(c, DTSPH_E_ARG, "graph must be 0, 1 or 2");
     if (p->lanes != 0 && p->lanes != 1 && p->lanes != 2 && p->lanes != 4 && p->lanes != 8)
         return fail(c, DTSPH_E_ARG, "lanes must be 0, 1, 2, 4 or 8");
+    if (p->stages != 0 && (p->stages < 2 || p->stages > kMaxStages))
+        return fail(c, DTSPH_E_ARG, "stages must be 0 or in [2, %d]", kMaxStages);
     return DTSPH_OK;
 }
 
-// Autotuner results: lanes per particle of the iterate kernel, keyed by
-// (dim, precision, slots, instances), shared by every context of the process.
+// Autotuner results: lanes per particle of the iterate kernel and, with one
+// lane, its staging depth, keyed by (dim, precision, slots, instances), shared
+// by every context of the process.
 struct TuneKey {
     int dim, prec;
     int64_t n;
@@ -212,11 +217,14 @@ struct TuneKey {
         return ninst < o.ninst;
     }
 };
-std::map<TuneKey, int> &tune_cache()
+struct TuneChoice { int lanes, stages; };
+std::map<TuneKey, TuneChoice> &tune_cache()
 {
-    static std::map<TuneKey, int> m;
+    static std::map<TuneKey, TuneChoice> m;
     return m;
 }
+
+constexpr int kDefaultStages = 3;
 std::mutex tune_mu;
 
 TuneKey tune_key(const dtsph_ctx *c, int64_t n)
@@ -224,13 +232,21 @@ TuneKey tune_key(const dtsph_ctx *c, int64_t n)
     return TuneKey{c->prm[0].dim, c->prm[0].precision, n, c->ninst};
 }
 
-int tuned_lanes(dtsph_ctx *c, int64_t n)
+// Lanes and stages for n slots: the parameters' when fixed, else the process
+// cache's choice for the shape, else 4 lanes until the tuner runs.
+TuneChoice kernel_choice(dtsph_ctx *c, int64_t n)
 {
-    std::lock_guard<std::mutex> g(tune_mu);
-    auto it = tune_cache().find(tune_key(c, n));
-    if (it == tune_cache().end()) return 4;
-    c->tuned = true;
-    return it->second;
+    const dtsph_params &p = c->prm[0];
+    TuneChoice ch{p.lanes > 0 ? p.lanes : 4, p.stages > 0 ? p.stages : kDefaultStages};
+    if (p.lanes == 0) {
+        std::lock_guard<std::mutex> g(tune_mu);
+        auto it = tune_cache().find(tune_key(c, n));
+        if (it != tune_cache().end()) {
+            ch = it->second;
+            c->tuned = true;
+        }
+    }
+    return ch;
 }
 
 int neighbour_capacity(const dtsph_params &p)
@@ -247,6 +263,10 @@ int neighbour_capacity(const dtsph_params &p)
 int allocate(dtsph_ctx *c, const int64_t *nf)
 {
     free_all(c);
+    if (iterate_prepare() != 0) {
+        cudaGetLastError();
+        return fail(c, DTSPH_E_CUDA, "could not raise the shared-memory limit of the iterate kernels");
+    }
     Buffers &B = c->B;
     const int ni = c->ninst;
     c->I.assign(ni, Inst{});
@@ -284,7 +304,11 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     B.K = K;
     B.ninst = ni;
     B.ncell = (int)co;
-    B.lanes = c->prm[0].lanes > 0 ? c->prm[0].lanes : tuned_lanes(c, n);
+    {
+        const TuneChoice ch = kernel_choice(c, n);
+        B.lanes = ch.lanes;
+        B.stages = ch.stages;
+    }
     const size_t nd = (size_t)n * d;
     const size_t nwarps = ((size_t)n + kWarp - 1) / kWarp;
     const size_t npair = nwarps * B.K * kWarp;
@@ -501,11 +525,13 @@ int probe_ms(dtsph_ctx *c, int launches, float *out)
     return DTSPH_OK;
 }
 
-// Times every lanes-per-particle candidate of the iterate kernel on a pair
-// cache built at the initial positions and keeps the fastest. Runs once per
-// shape in a process, before the first step, so that every step of every
-// context of that shape uses the same kernel (and so the same summation order).
-// The loop buffers hold no state yet; they are zeroed for the timing runs.
+// Times the candidates of the iterate kernel (one lane per particle at
+// staging depths 2, 3, 4 and 6 unless stages is fixed, then 2, 4 and 8 lanes)
+// on a pair cache built at the initial positions and keeps the fastest. Runs
+// once per shape in a process, before the first step, so that every step of
+// every context of that shape uses the same kernel (and so the same summation
+// order; the staging depth does not change the arithmetic). The loop buffers
+// hold no state yet; they are zeroed for the timing runs.
 int autotune(dtsph_ctx *c)
 {
     const Buffers &B = c->B;
@@ -519,22 +545,29 @@ int autotune(dtsph_ctx *c)
     c->launches += launch_pair_cache(B, B.x_b, B.cell_b, B.gid_b, c->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
-    int best = c->B.lanes;
+    std::vector<TuneChoice> cand;
+    if (c->prm[0].stages > 0) cand.push_back({1, c->prm[0].stages});
+    else
+        for (int S : {2, 3, 4, 6}) cand.push_back({1, S});
+    for (int L : {2, 4, 8}) cand.push_back({L, kDefaultStages});
+    TuneChoice best{c->B.lanes, c->B.stages};
     float best_ms = 1e30f;
     c->tune_log.clear();
-    for (int L : {1, 2, 4, 8}) {
-        c->B.lanes = L;
+    for (const TuneChoice &ch : cand) {
+        c->B.lanes = ch.lanes;
+        c->B.stages = ch.stages;
         float ms = 0;
         probe_ms(c, 3, &ms);                   // warm-up
         int r = probe_ms(c, 10, &ms);
         if (r) return r;
-        c->tune_log.push_back({L, ms});
+        c->tune_log.push_back({ch.lanes, ch.lanes == 1 ? ch.stages : 0, ms});
         if (ms < best_ms) {
             best_ms = ms;
-            best = L;
+            best = ch;
         }
     }
-    c->B.lanes = best;
+    c->B.lanes = best.lanes;
+    c->B.stages = best.stages;
     c->tuned = true;
     {
         std::lock_guard<std::mutex> g(tune_mu);
@@ -650,8 +683,9 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
     for (int i = 0; i < ninst; ++i) {
         int r = validate(c, &params[i]);
         if (!r && (params[i].dim != params[0].dim || params[i].precision != params[0].precision ||
-                   params[i].graph != params[0].graph || params[i].lanes != params[0].lanes))
-            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph and lanes");
+                   params[i].graph != params[0].graph || params[i].lanes != params[0].lanes ||
+                   params[i].stages != params[0].stages))
+            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph, lanes and stages");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;
@@ -929,10 +963,25 @@ int dtsph_tuning(const dtsph_ctx *c, int32_t *lanes, float *ms_by_lanes)
     if (ms_by_lanes) {
         for (int i = 0; i < 4; ++i) ms_by_lanes[i] = -1.f;
         for (auto &e : c->tune_log) {
-            int i = e.first == 1 ? 0 : e.first == 2 ? 1 : e.first == 4 ? 2 : 3;
-            ms_by_lanes[i] = e.second;
+            int i = e.lanes == 1 ? 0 : e.lanes == 2 ? 1 : e.lanes == 4 ? 2 : 3;
+            if (ms_by_lanes[i] < 0.f || e.ms < ms_by_lanes[i]) ms_by_lanes[i] = e.ms;
         }
     }
+    return DTSPH_OK;
+}
+
+int dtsph_tuning_candidates(const dtsph_ctx *c, int32_t cap, int32_t *lanes, int32_t *stages, float *ms,
+                            int32_t *count, int32_t *stages_in_use)
+{
+    if (!c || !count || cap < 0 || (cap > 0 && (!lanes || !stages || !ms))) return DTSPH_E_ARG;
+    const int n = (int)c->tune_log.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        lanes[i] = c->tune_log[i].lanes;
+        stages[i] = c->tune_log[i].stages;
+        ms[i] = c->tune_log[i].ms;
+    }
+    *count = n;
+    if (stages_in_use) *stages_in_use = c->B.lanes == 1 ? c->B.stages : 0;
     return DTSPH_OK;
 }
 

@@ -23,6 +23,7 @@ enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy
 // at most kSlotAlign consecutive slots from a multiple of its own width, so a
 // block never straddles two instances.
 constexpr int kSlotAlign = 256;
+constexpr int kMaxStages = 8;        // deepest shared-memory ring of the one-lane iterate kernel
 constexpr uint32_t kNoParticle = 0xFFFFFFFFu;
 
 struct Inst {
@@ -70,6 +71,7 @@ struct Phys {
     double inv_2dt;      // 1 / (2 dt)
     double rp_scale;     // dt / (rho0 c^2) / nf
     double rv_scale;     // dt / v_ref / nf
+    float dtau_f;        // dtau rounded to FP32 (the FP32C p-hat update)
     int edac, use_av;
 };
 
@@ -107,6 +109,7 @@ struct Buffers {
     int nf, nw;                     // fluid and wall particles of all instances
     int dim, fp32c, K;              // K = neighbour capacity per particle
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
+    int stages;                     // pair-cache chunks in flight per warp (lanes = 1), 2..kMaxStages
     int ninst, ncell;               // instances; cells of all instances (sentinels included)
     const Inst *inst;               // [ninst]
     const Geom *geo;                // [ninst]
@@ -180,6 +183,9 @@ int launch_outer(const Buffers &B, cudaStream_t st);
 int loop_grid(const Buffers &B, int *grid);
 cudaError_t launch_loop(const Buffers &B, int grid, cudaStream_t st);
 int launch_loop_reset(const Buffers &B, cudaStream_t st);
+// Raises the dynamic shared-memory limit of the kernels that stage pair-cache
+// rows (once per device, before any launch or capture); 0 on success.
+int iterate_prepare();
 int launch_unpermute(const Buffers &B, const uint32_t *gid, const double *src, double *out, int comps, cudaStream_t st);
 int launch_scatter_in(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,
                       const double *xw, const double *vw, cudaStream_t st);

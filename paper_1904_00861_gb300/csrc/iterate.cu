@@ -183,51 +183,71 @@ __device__ __forceinline__ void warp_sum2(float &s, float &e)
 // Pair-cache rows of one warp in shared memory (one lane per slot). The 32 slots
 // of the warp form one slice of the sliced cache, so their entries k = 0, 1, ...
 // are consecutive rows (32 coefficient records, then, where the index is kept
-// apart, 32 indices). Chunks of kRows rows arrive by bulk copies, kStages chunks
-// in flight, each completing on its stage's mbarrier.
+// apart, 32 indices). Chunks of kRows rows arrive by bulk copies into a ring of
+// S stages (S - 1 chunks in flight while one is used), each completing on its
+// stage's mbarrier. The ring of warp w sits at w * stride(S) in dynamic shared
+// memory: S stages, then S barriers.
 template <int D, bool F32>
 struct RowFmt {
     static constexpr int kCoef = F32 ? 16 : 32;                 // bytes of one coefficient record
     static constexpr bool kSepJ = !(F32 && D == 2);             // index in pj (2D FP32C: in .w)
-    static constexpr int kRows = F32 ? 2 : 1;                   // rows per chunk
-    static constexpr int kStages = 3;
+    static constexpr int kRows = F32 ? 4 : 2;                   // rows per chunk
     static constexpr int kCoefRow = kWarp * kCoef;
     static constexpr int kJRow = kSepJ ? kWarp * 4 : 0;
     static constexpr int kStageBytes = kRows * (kCoefRow + kJRow);
+    static __host__ __device__ constexpr size_t stride(int S)
+    {
+        return ((size_t)S * kStageBytes + (size_t)S * 8 + 127) / 128 * 128;
+    }
 };
+
+// Dynamic shared memory of the one-lane kernels for S stages: one ring per warp.
+template <int D, bool F32>
+__host__ __device__ constexpr size_t ring_bytes(int S)
+{
+    return RowFmt<D, F32>::stride(S) * (kBlock / kWarp);
+}
 
 template <int D, bool F32>
-struct alignas(128) WarpRing {
-    unsigned char buf[RowFmt<D, F32>::kStages][RowFmt<D, F32>::kStageBytes];
-    uint64_t bar[RowFmt<D, F32>::kStages];
+struct WarpRing {
+    unsigned char *buf;    // stage st at buf + st * kStageBytes
+    uint64_t *bar;         // S barriers
+    int S;
 };
-
-struct NoRing {};
 
 template <typename T, int D, int L>
 struct TileShared {
     T part[D + 1][kBlock / L];
     double red[2][kBlock / kWarp];
-    typename std::conditional<L == 1, WarpRing<D, std::is_same<T, float>::value>[kBlock / kWarp], NoRing>::type ring;
 };
 
+extern __shared__ __align__(128) unsigned char dyn_smem[];
+
 // Bulk-copy state of a warp's ring, kept across tiles: chunks consumed so far
-// (stage = pos % kStages, phase parity = (pos / kStages) & 1), and whether every
+// (stage = pos % S, phase parity = (pos / S) & 1), and whether every
 // wait so far completed.
 struct RingPos {
     uint32_t pos = 0;
     bool ok = true;
 };
 
+// This warp's ring in dynamic shared memory (one-lane kernels only).
+template <int D, bool F32>
+__device__ __forceinline__ WarpRing<D, F32> warp_ring(int S)
+{
+    using RF = RowFmt<D, F32>;
+    unsigned char *base = dyn_smem + (size_t)(threadIdx.x >> 5) * RF::stride(S);
+    return WarpRing<D, F32>{base, reinterpret_cast<uint64_t *>(base + (size_t)S * RF::kStageBytes), S};
+}
+
 // Initialises the mbarriers of every warp's ring (whole block, then syncs).
-template <typename T, int D, int L>
-__device__ __forceinline__ void ring_init(TileShared<T, D, L> &sh)
+template <int D, bool F32, int L>
+__device__ __forceinline__ void ring_init(int S)
 {
     if constexpr (L == 1) {
-        constexpr bool F32 = std::is_same<T, float>::value;
         if ((threadIdx.x & 31) == 0) {
-            auto &rg = sh.ring[threadIdx.x >> 5];
-            for (int st = 0; st < RowFmt<D, F32>::kStages; ++st) mbar_init(&rg.bar[st], 1);
+            const WarpRing<D, F32> rg = warp_ring<D, F32>(S);
+            for (int st = 0; st < S; ++st) mbar_init(&rg.bar[st], 1);
             mbar_fence_init();
         }
     }
@@ -296,10 +316,11 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
             // the warp's rows stream through its shared-memory ring; the
             // neighbour states of a chunk's rows are gathered together
             using RF = RowFmt<D, F32>;
-            constexpr int R = RF::kRows, S = RF::kStages;
+            constexpr int R = RF::kRows;
+            const int S = B.stages;
             constexpr unsigned full = 0xffffffffu;
             const int lane = threadIdx.x & 31;
-            auto &rg = sh.ring[threadIdx.x >> 5];
+            const WarpRing<D, F32> rg = warp_ring<D, F32>(S);
             const int cmax = __reduce_max_sync(full, cnt);
             const int nch = rp.ok ? (cmax + R - 1) / R : 0;
             const size_t row0 = (size_t)(s >> 5) * B.K;      // first row of the warp's slice
@@ -307,55 +328,57 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
                 (F32 ? (const unsigned char *)B.pc32 : (const unsigned char *)B.pc64) + row0 * RF::kCoefRow;
             const unsigned char *gj = (const unsigned char *)B.pj + row0 * (kWarp * 4);
             auto issue = [&](int c) {        // lane 0: chunk c into its stage
-                const int st = (int)((rp.pos + (uint32_t)c) % S);
+                const int st = (int)((rp.pos + (uint32_t)c) % (uint32_t)S);
                 const int r0 = c * R, nr = min(R, cmax - r0);
                 const uint32_t bc = (uint32_t)(nr * RF::kCoefRow), bj = (uint32_t)(nr * RF::kJRow);
+                unsigned char *stg = rg.buf + (size_t)st * RF::kStageBytes;
                 mbar_arrive_expect_tx(&rg.bar[st], bc + bj);
-                bulk_g2s(rg.buf[st], gcoef + (size_t)r0 * RF::kCoefRow, bc, &rg.bar[st]);
-                if (RF::kSepJ) bulk_g2s(rg.buf[st] + R * RF::kCoefRow, gj + (size_t)r0 * RF::kJRow, bj, &rg.bar[st]);
+                bulk_g2s(stg, gcoef + (size_t)r0 * RF::kCoefRow, bc, &rg.bar[st]);
+                if (RF::kSepJ) bulk_g2s(stg + R * RF::kCoefRow, gj + (size_t)r0 * RF::kJRow, bj, &rg.bar[st]);
             };
             if (lane == 0)
                 for (int c = 0; c < S && c < nch; ++c) issue(c);
             int c = 0;
             for (; c < nch; ++c) {
                 const uint32_t q = rp.pos + (uint32_t)c;
-                const int st = (int)(q % S);
-                if (!mbar_wait(&rg.bar[st], (q / S) & 1u)) break;
+                const int st = (int)(q % (uint32_t)S);
+                if (!mbar_wait(&rg.bar[st], (q / (uint32_t)S) & 1u)) break;
                 const int r0 = c * R, nr = min(R, cmax - r0);
-                CacheEntry<T, D, F32> ce[R];
+                const unsigned char *stg = rg.buf + (size_t)st * RF::kStageBytes;
+                // gather the neighbour states of the chunk's rows first (R loads
+                // in flight per lane), then run the pair terms
+                uint32_t jbv[R];
                 Q qv[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if (r < nr && r0 + r < cnt) {
-                        const unsigned char *rec = rg.buf[st] + r * RF::kCoefRow + lane * RF::kCoef;
-                        if (F32) {
-                            const float4 v = *(const float4 *)rec;
-                            ce[r].g[0] = (T)v.x;
-                            ce[r].g[1] = (T)v.y;
-                            if (D == 3) {
-                                ce[r].g[2] = (T)v.z;
-                                ce[r].F = (T)v.w;
-                            } else {
-                                ce[r].g[2] = T(0);
-                                ce[r].F = (T)v.z;
-                            }
-                            ce[r].jb = D == 2 ? __float_as_uint(v.w)
-                                              : *(const uint32_t *)(rg.buf[st] + R * RF::kCoefRow + r * RF::kJRow +
-                                                                    lane * 4);
-                        } else {
-                            const double4_32a v = *(const double4_32a *)rec;
-                            ce[r].g[0] = (T)v.x;
-                            ce[r].g[1] = (T)v.y;
-                            ce[r].g[2] = (T)v.z;
-                            ce[r].F = (T)v.w;
-                            ce[r].jb = *(const uint32_t *)(rg.buf[st] + R * RF::kCoefRow + r * RF::kJRow + lane * 4);
-                        }
-                        qv[r] = nbq[ce[r].jb & ~kWallBit];
+                        jbv[r] = RF::kSepJ
+                                     ? ((const uint32_t *)(stg + R * RF::kCoefRow + r * RF::kJRow))[lane]
+                                     : __float_as_uint(((const float4 *)(stg + r * RF::kCoefRow))[lane].w);
+                        qv[r] = nbq[jbv[r] & ~kWallBit];
                     }
                 }
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (r < nr && r0 + r < cnt) pair(ce[r], qv[r]);
+                for (int r = 0; r < R; ++r) {
+                    if (r < nr && r0 + r < cnt) {
+                        CacheEntry<T, D, F32> ce;
+                        if (F32) {
+                            const float4 v = ((const float4 *)(stg + r * RF::kCoefRow))[lane];
+                            ce.g[0] = (T)v.x;
+                            ce.g[1] = (T)v.y;
+                            ce.g[2] = D == 3 ? (T)v.z : T(0);
+                            ce.F = D == 3 ? (T)v.w : (T)v.z;
+                        } else {
+                            const double4_32a v = ((const double4_32a *)(stg + r * RF::kCoefRow))[lane];
+                            ce.g[0] = (T)v.x;
+                            ce.g[1] = (T)v.y;
+                            ce.g[2] = (T)v.z;
+                            ce.F = (T)v.w;
+                        }
+                        ce.jb = jbv[r];
+                        pair(ce, qv[r]);
+                    }
+                }
                 __syncwarp();
                 if (lane == 0 && c + S < nch) {
                     fence_proxy_async_smem();
@@ -367,7 +390,7 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
                 // using the ring and report
                 for (int d = c + 1; d < nch && d < c + S; ++d) {
                     const uint32_t q = rp.pos + (uint32_t)d;
-                    mbar_wait(&rg.bar[q % S], (q / S) & 1u);
+                    mbar_wait(&rg.bar[q % (uint32_t)S], (q / (uint32_t)S) & 1u);
                 }
                 rp.ok = false;
                 if (lane == 0) atomicOr(B.err, kErrCopy);
@@ -400,49 +423,66 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
     __syncthreads();
 
     // ---------------- phase 2: BDF2 pseudo-acceleration and update, FP64
-    double r_ap = 0.0, r_av = 0.0;
+    // kappa (F + g - (3 V^k - 4 V^n + V^{n-1}) / (2 dt)), with the state-n part
+    // kappa ((V^{n-1} - 4 V^n) / (2 dt) - g) precomputed in s_a; V^{k+1} in FP64.
+    // On the FP32C path everything past the FP64 velocity update (the FP32
+    // copies, p-hat, the residual terms) stays in FP32, to keep conversions off
+    // the FP64 pipe: the residual terms are summed per warp with error-free
+    // two-sum compensation (a double-float sum, accurate to ~1e-12 of the total)
+    // and the warp totals are carried on in FP64. The FP64 path sums in FP64.
     if (threadIdx.x < PPB) {
         const int s2 = tile * PPB + threadIdx.x;
-        if (s2 < n && B.gid_a[s2] < (uint32_t)B.nf) {
-            const double apv = (double)sh.part[0][threadIdx.x];
-            double vnew[3] = {0, 0, 0};
-            double av2 = 0.0;
+        const bool fl = s2 < n && B.gid_a[s2] < (uint32_t)B.nf;
+        double w_ap, w_av;
+        if (F32) {
+            float r_ap = 0.f, r_av = 0.f;
+            if (fl) {
+                const float apf = (float)sh.part[0][threadIdx.x];
+                float vnf[3] = {0.f, 0.f, 0.f};
+                float av2 = 0.f;
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                // kappa (F + g - (3 V^k - 4 V^n + V^{n-1}) / (2 dt)), with the state-n
-                // part kappa ((V^{n-1} - 4 V^n) / (2 dt) - g) precomputed in s_a
-                const size_t q = (size_t)a * n + s2;
-                const double vk = B.vk[cur][q];
-                const double Fv = (double)sh.part[1 + a][threadIdx.x];
-                const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
-                vnew[a] = __fma_rn(P.dtau, av, vk);
-                B.vk[nxt][q] = vnew[a];
-                av2 = __fma_rn(av, av, av2);
+                for (int a = 0; a < D; ++a) {
+                    const size_t q = (size_t)a * n + s2;
+                    const double vk = B.vk[cur][q];
+                    const double Fv = (double)sh.part[1 + a][threadIdx.x];
+                    const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
+                    const double vnew = __fma_rn(P.dtau, av, vk);
+                    B.vk[nxt][q] = vnew;
+                    vnf[a] = (float)vnew;
+                    const float avf = (float)av;
+                    av2 = __fmaf_rn(avf, avf, av2);
+                }
+                const float pnew = __fmaf_rn(P.dtau_f, apf, B.nb32[cur][s2].w);
+                B.nb32[nxt][s2] = make_float4(vnf[0], vnf[1], vnf[2], pnew);
+                r_av = sqrtf(av2);
+                r_ap = fabsf(apf);
             }
-            if (F32) {
-                const float4 q = B.nb32[cur][s2];
-                const float pnew = __fmaf_rn((float)P.dtau, (float)apv, q.w);
-                B.nb32[nxt][s2] = make_float4((float)vnew[0], (float)vnew[1], (float)vnew[2], pnew);
-                r_av = (double)sqrtf((float)av2);
-            } else {
+            float sa = r_ap, ea = 0.f, sb = r_av, eb = 0.f;
+            warp_sum2(sa, ea);
+            warp_sum2(sb, eb);
+            w_ap = (threadIdx.x & 31) == 0 ? (double)sa + (double)ea : 0.0;
+            w_av = (threadIdx.x & 31) == 0 ? (double)sb + (double)eb : 0.0;
+        } else {
+            double r_ap = 0.0, r_av = 0.0;
+            if (fl) {
+                const double apv = (double)sh.part[0][threadIdx.x];
+                double vnew[3] = {0, 0, 0};
+                double av2 = 0.0;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const size_t q = (size_t)a * n + s2;
+                    const double vk = B.vk[cur][q];
+                    const double Fv = (double)sh.part[1 + a][threadIdx.x];
+                    const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
+                    vnew[a] = __fma_rn(P.dtau, av, vk);
+                    B.vk[nxt][q] = vnew[a];
+                    av2 = __fma_rn(av, av, av2);
+                }
                 const double pnew = __fma_rn(P.dtau, apv, B.nb64[cur][s2].w);
                 B.nb64[nxt][s2] = make_double4_32a(vnew[0], vnew[1], vnew[2], pnew);
                 r_av = sqrt(av2);
+                r_ap = fabs(apv);
             }
-            r_ap = fabs(apv);
-        }
-        // residual partial sums: FP64 on the FP64 path; on the FP32C path the
-        // warp level sums the FP32 terms with error-free two-sum compensation
-        // (a double-float sum, accurate to ~1e-12 of the total) and the warp
-        // totals are carried on in FP64
-        double w_ap, w_av;
-        if (F32) {
-            float sa = (float)r_ap, ea = 0.f, sb = (float)r_av, eb = 0.f;
-            warp_sum2(sa, ea);
-            warp_sum2(sb, eb);
-            w_ap = (double)sa + (double)ea;
-            w_av = (double)sb + (double)eb;
-        } else {
             w_ap = warp_sum<double>(r_ap);
             w_av = warp_sum<double>(r_av);
         }
@@ -529,7 +569,8 @@ __device__ __forceinline__ int finish_iteration(LoopState *ls, const Phys &P, in
 // applies its stop rules; the last block of all sets the while-node condition
 // (some instance still iterating).
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, unsigned long long cond, int use_cond)
+__global__ void __launch_bounds__(kBlock, (F32 && D == 2) ? 4 : 1) k_iterate(Buffers B, unsigned long long cond,
+                                                                          int use_cond)
 {
     using T = typename std::conditional<F32, float, double>::type;
     constexpr int PPB = kBlock / L;
@@ -537,7 +578,7 @@ __global__ void __launch_bounds__(kBlock) k_iterate(Buffers B, unsigned long lon
     __shared__ Phys P;
     __shared__ int last, tlo_sh;
     if (!use_cond && B.ctrl->active == 0) return;     // whole grid agrees: nothing to do
-    ring_init(sh);
+    ring_init<D, F32, L>(B.stages);
     RingPos rp;
     const int inst = block_instance(B, blockIdx.x * PPB);
     LoopState *ls = B.ls + inst;
@@ -630,7 +671,7 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *er
 // decisions; tiles of finished instances are skipped. Walls get their own phase
 // and barrier before the fluid phase.
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B)
+__global__ void __launch_bounds__(kBlock, (F32 && D == 2) ? 4 : 3) k_loop(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     constexpr int PPB = kBlock / L;
@@ -645,7 +686,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_loop(Buffers B)
         stop = 0;
         p_inst = -1;
     }
-    ring_init(sh);
+    ring_init<D, F32, L>(B.stages);
     RingPos rp;
     unsigned int epoch = 0;
     int r = -1, it = 0;
@@ -817,7 +858,7 @@ static void iterate_lanes(const Buffers &B, unsigned long long cond, int use_con
 {
     const int nb = iterate_tiles(B);
     switch (B.lanes) {
-    case 1: k_iterate<D, F, W, 1><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
+    case 1: k_iterate<D, F, W, 1><<<nb, kBlock, ring_bytes<D, F>(B.stages), st>>>(B, cond, use_cond); break;
     case 2: k_iterate<D, F, W, 2><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
     case 4: k_iterate<D, F, W, 4><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
     default: k_iterate<D, F, W, 8><<<nb, kBlock, 0, st>>>(B, cond, use_cond); break;
@@ -861,6 +902,25 @@ static const void *loop_lanes(int lanes)
     }
 }
 
+// Dynamic shared memory of the iterate and loop kernels of this shape.
+static size_t iterate_smem(const Buffers &B)
+{
+    if (B.lanes != 1) return 0;
+    if (B.dim == 2) return B.fp32c ? ring_bytes<2, true>(B.stages) : ring_bytes<2, false>(B.stages);
+    return B.fp32c ? ring_bytes<3, true>(B.stages) : ring_bytes<3, false>(B.stages);
+}
+
+template <int D, bool F, bool W>
+static cudaError_t allow_ring_smem()
+{
+    const int bytes = (int)ring_bytes<D, F>(kMaxStages);
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_iterate<D, F, W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)k_loop<D, F, W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 static const void *loop_function(const Buffers &B)
 {
     const bool w = B.nw > 0;
@@ -877,7 +937,9 @@ int loop_grid(const Buffers &B, int *grid)
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop_function(B), kBlock, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop_function(B), kBlock, iterate_smem(B)) !=
+            cudaSuccess ||
+        per_sm < 1)
         return -1;
     *grid = std::min(iterate_tiles(B), per_sm * sms);
     return 0;
@@ -888,7 +950,7 @@ cudaError_t launch_loop(const Buffers &B, int grid, cudaStream_t st)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBlock);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = iterate_smem(B);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -910,6 +972,19 @@ int launch_outer(const Buffers &B, cudaStream_t st)
         else k_outer<3, false><<<blocks(B.n), kBlock, 0, st>>>(B);
     }
     return 1;
+}
+
+int iterate_prepare()
+{
+    cudaError_t e = allow_ring_smem<2, true, false>();
+    if (e == cudaSuccess) e = allow_ring_smem<2, true, true>();
+    if (e == cudaSuccess) e = allow_ring_smem<2, false, false>();
+    if (e == cudaSuccess) e = allow_ring_smem<2, false, true>();
+    if (e == cudaSuccess) e = allow_ring_smem<3, true, false>();
+    if (e == cudaSuccess) e = allow_ring_smem<3, true, true>();
+    if (e == cudaSuccess) e = allow_ring_smem<3, false, false>();
+    if (e == cudaSuccess) e = allow_ring_smem<3, false, true>();
+    return e == cudaSuccess ? 0 : -1;
 }
 
 int launch_loop_reset(const Buffers &B, cudaStream_t st)

@@ -194,6 +194,7 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     P.nu_e = p->h * P.c / 16.0;
     P.dt = p->dt;
     P.dtau = p->dt / p->beta;
+    P.dtau_f = (float)P.dtau;
     P.sig_h = quintic_sigma_noalloc(p->dim, p->h) / p->h;
     P.inv_h = 1.0 / p->h;
     P.eta_h2 = p->eta * p->h * p->h;

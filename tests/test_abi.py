@@ -55,11 +55,16 @@ def test_version_and_argument_errors_without_gpu(so):
     with pytest.raises(lib_pkg.DtsphError) as e:
         lib_pkg.dtsph_create(p)
     assert e.value.code == -7
+    for bad in (1, 9, -1):        # staging depth outside [2, 8]
+        p = lib_pkg.make_params(dict(dim=2, h=0.1, m=0.01, nu=0.01, dt=0.01, lanes=1, stages=bad))
+        with pytest.raises(lib_pkg.DtsphError) as e:
+            lib_pkg.dtsph_create(p)
+        assert e.value.code == -1
 
 
 def test_struct_layouts_match_header():
     """ctypes mirrors of the C structs have the C sizes (checked by offsets)."""
     P = lib_pkg.dtsph_params
     assert P.lo.offset == 24 and P.h.offset == 72
-    assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 8
+    assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 9 + 4   # int32 fields, tail padding
     assert ctypes.sizeof(lib_pkg.dtsph_step_stats) == 24

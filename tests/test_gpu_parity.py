@@ -163,13 +163,35 @@ def test_every_lane_split_matches_oracle(lanes, prec):
         sim.close()
 
 
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_staging_depth_does_not_change_the_bits(prec):
+    """The one-lane kernel's shared-memory ring depth only changes how many
+    pair-cache chunks are in flight, never the arithmetic."""
+    d = CASES["tgv3d"]()
+    ref = None
+    for stages in (2, 3, 5, 8):
+        sim = make_sim(d, precision=prec, graph=2, lanes=1, stages=stages)
+        sim.step(2)
+        got = (sim.v, sim.p, sim.x, sim.stats())
+        sim.close()
+        if ref is None:
+            ref = got
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(got[:3], ref[:3])) and got[3] == ref[3], stages
+
+
 def test_autotuner_picks_a_candidate_and_caches_it():
     d = synth.tgv2d(64)
     a = make_sim(d, precision=dt.DTSPH_FP32C, lanes=0)
     lanes, ms = dt.dtsph_tuning(a.ctx)
     assert lanes in (1, 2, 4, 8) and set(ms) == {1, 2, 4, 8} and ms[lanes] == min(ms.values())
+    s_use, cand = dt.dtsph_tuning_candidates(a.ctx)
+    assert [(c[0], c[1]) for c in cand] == [(1, 2), (1, 3), (1, 4), (1, 6), (2, 0), (4, 0), (8, 0)]
+    best = min(cand, key=lambda c: c[2])
+    assert (lanes, s_use) == (best[0], best[1])
     b = make_sim(d, precision=dt.DTSPH_FP32C, lanes=0)     # same shape: taken from the cache
     assert dt.dtsph_tuning(b.ctx) == (lanes, {})
+    assert dt.dtsph_tuning_candidates(b.ctx) == (s_use, [])
     a.close()
     b.close()
 
