@@ -205,6 +205,14 @@ int dtsph_get_neighbors(dtsph_ctx *ctx, int64_t i, int64_t *out, int64_t cap, in
 int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, double *bytes_per_launch,
                         int64_t *pairs);
 
+/* Device time (ms) of the pseudo-time loop of real steps first .. first+count-1
+ * (steps are numbered from 0 since dtsph_set_particles; each must be among the
+ * last 256 taken), from CUDA events recorded just before and after the loop of
+ * every step: event nodes of the step graph (graph = 1, 2) or events on the
+ * stream (graph = 0). Waits for those steps to finish. The paper has no
+ * counterpart; it serves measurement (the loop's share of a step). */
+int dtsph_loop_times(dtsph_ctx *ctx, int64_t first, int32_t count, float *ms);
+
 /* Autotuner report: the lanes per particle the iterate kernel uses, and (if
  * ms_by_lanes is not NULL, 4 floats) the mean launch time measured for 1, 2, 4
  * and 8 lanes when this context tuned (-1 where it did not measure, e.g. when

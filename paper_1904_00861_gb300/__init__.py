@@ -73,6 +73,7 @@ _SIGS = [
     ("dtsph_get_neighbors", C.c_int, [_VP, C.c_int64, _I64P, C.c_int64, _I64P]),
     ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
     ("dtsph_tuning", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    ("dtsph_loop_times", C.c_int, [_VP, C.c_int64, C.c_int32, C.POINTER(C.c_float)]),
     ("dtsph_tuning_candidates", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("dtsph_batch_create", C.c_int, [C.c_int32, C.POINTER(dtsph_params), _VP, C.POINTER(_VP)]),
@@ -274,6 +275,13 @@ def dtsph_probe_iterate(ctx, launches: int = 20):
     npairs = C.c_int64()
     _check(ctx, lib().dtsph_probe_iterate(ctx, int(launches), C.byref(ms), C.byref(by), C.byref(npairs)))
     return float(ms.value), float(by.value), int(npairs.value)
+
+
+def dtsph_loop_times(ctx, first: int, count: int):
+    """Device ms of the pseudo-time loop of steps first .. first+count-1."""
+    ms = (C.c_float * max(count, 1))()
+    _check(ctx, lib().dtsph_loop_times(ctx, first, count, ms))
+    return [float(ms[i]) for i in range(count)]
 
 
 def dtsph_tuning_candidates(ctx):

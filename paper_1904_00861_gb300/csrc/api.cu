@@ -42,6 +42,11 @@ struct dtsph_ctx {
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
     bool tuned = false;
     int loop_grid = 0;
+    // events around the pseudo-time loop of each real step (pair step % kLoopEv),
+    // recorded by event nodes of the step graph or on the stream
+    static constexpr int kLoopEv = 256;
+    std::vector<cudaEvent_t> ev_a, ev_b;
+    cudaGraphNode_t node_a = nullptr, node_b = nullptr;
     struct TuneRec { int lanes, stages; float ms; };
     std::vector<TuneRec> tune_log;      // candidates timed by the last tuning
 };
@@ -401,6 +406,27 @@ int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st) { return launch_outer(c->B,
 
 // Graph of one real step with the persistent loop: pre-loop kernels -> one
 // cooperative loop kernel -> outer.
+// The event-record nodes around the loop in a captured step graph.
+int find_event_nodes(dtsph_ctx *c, cudaGraph_t g)
+{
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    c->node_a = c->node_b = nullptr;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        if (ev == c->ev_a[0]) c->node_a = nd;
+        if (ev == c->ev_b[0]) c->node_b = nd;
+    }
+    if (!c->node_a || !c->node_b) return fail(c, DTSPH_E_CUDA, "loop event nodes not found in the step graph");
+    return DTSPH_OK;
+}
+
 int build_graph_persistent(dtsph_ctx *c)
 {
     int grid = 0;
@@ -411,13 +437,19 @@ int build_graph_persistent(dtsph_ctx *c)
     c->graph = g;
     CK(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     c->per_step_fixed = enqueue_pre_loop(c, c->cap);
+    cudaError_t e0 = cudaEventRecordWithFlags(c->ev_a[0], c->cap, cudaEventRecordExternal);
     cudaError_t e = launch_loop(c->B, grid, c->cap);
+    cudaError_t e1 = cudaEventRecordWithFlags(c->ev_b[0], c->cap, cudaEventRecordExternal);
     c->per_step_fixed += 1 + enqueue_post_loop(c, c->cap);
     cudaGraph_t g2 = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g2);
     if (e != cudaSuccess) return fail(c, DTSPH_E_CUDA, "cooperative loop launch under capture: %s", cudaGetErrorString(e));
+    CK(e0);
+    CK(e1);
     CK(e2);
     c->per_iter = 0;
+    int r = find_event_nodes(c, g);
+    if (r) return r;
     CK(cudaGraphInstantiate(&c->exec, g, 0));
     return DTSPH_OK;
 }
@@ -431,6 +463,7 @@ int build_graph(dtsph_ctx *c)
     c->graph = g;
     CK(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     c->per_step_fixed = enqueue_pre_loop(c, c->cap);
+    CK(cudaEventRecordWithFlags(c->ev_a[0], c->cap, cudaEventRecordExternal));
     cudaStreamCaptureStatus cs;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -447,6 +480,7 @@ int build_graph(dtsph_ctx *c)
     CK(cudaGraphAddNode(&wnode, g, dv.data(), nullptr, dv.size(), &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamUpdateCaptureDependencies(c->cap, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaEventRecordWithFlags(c->ev_b[0], c->cap, cudaEventRecordExternal));
     c->per_step_fixed += enqueue_post_loop(c, c->cap);
     cudaGraph_t g2 = nullptr;
     CK(cudaStreamEndCapture(c->cap, &g2));
@@ -454,6 +488,8 @@ int build_graph(dtsph_ctx *c)
     c->per_iter = enqueue_iteration(c, c->cap, (unsigned long long)h, 1);
     cudaGraph_t b2 = nullptr;
     CK(cudaStreamEndCapture(c->cap, &b2));
+    int r = find_event_nodes(c, g);
+    if (r) return r;
     CK(cudaGraphInstantiate(&c->exec, g, 0));
     return DTSPH_OK;
 }
@@ -462,8 +498,10 @@ int build_graph(dtsph_ctx *c)
 // every instance has stopped; the host checks the device counter between chunks.
 int step_plain(dtsph_ctx *c)
 {
+    const int k = (int)(c->steps % dtsph_ctx::kLoopEv);
     c->per_step_fixed = enqueue_pre_loop(c, c->stream);
     c->launches += c->per_step_fixed;
+    CK(cudaEventRecord(c->ev_a[k], c->stream));
     int cap = 1;
     for (const auto &p : c->prm) cap = std::max(cap, p.fixed_iters > 0 ? p.fixed_iters : p.max_iter);
     int issued = 0;
@@ -480,6 +518,7 @@ int step_plain(dtsph_ctx *c)
         if (ctrl.active == 0) break;
         if (issued > cap + 16) return fail(c, DTSPH_E_STATE, "pseudo-time loop did not stop");
     }
+    CK(cudaEventRecord(c->ev_b[k], c->stream));
     c->launches += enqueue_post_loop(c, c->stream);
     CK(cudaGetLastError());
     return DTSPH_OK;
@@ -700,6 +739,15 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
         delete c;
         return DTSPH_E_CUDA;
     }
+    c->ev_a.assign(dtsph_ctx::kLoopEv, nullptr);
+    c->ev_b.assign(dtsph_ctx::kLoopEv, nullptr);
+    for (int k = 0; k < dtsph_ctx::kLoopEv; ++k) {
+        if (cudaEventCreate(&c->ev_a[k]) != cudaSuccess || cudaEventCreate(&c->ev_b[k]) != cudaSuccess) {
+            cudaGetLastError();
+            dtsph_destroy(c);
+            return DTSPH_E_CUDA;
+        }
+    }
     *out = c;
     return DTSPH_OK;
 }
@@ -765,6 +813,10 @@ void dtsph_destroy(dtsph_ctx *c)
     else cudaDeviceSynchronize();
     free_all(c);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (cudaEvent_t e : c->ev_a)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_b)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -812,6 +864,9 @@ int dtsph_step(dtsph_ctx *c, int32_t nsteps)
     c->have_nbrs = false;
     for (int32_t s = 0; s < nsteps; ++s) {
         if (c->exec) {
+            const int k = (int)(c->steps % dtsph_ctx::kLoopEv);
+            CK(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_a, c->ev_a[k]));
+            CK(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_b, c->ev_b[k]));
             CK(cudaGraphLaunch(c->exec, c->stream));
         } else {
             int r = step_plain(c);
@@ -831,6 +886,22 @@ int dtsph_sync(dtsph_ctx *c)
 }
 
 int64_t dtsph_step_count(const dtsph_ctx *c) { return c ? c->steps : -1; }
+
+int dtsph_loop_times(dtsph_ctx *c, int64_t first, int32_t count, float *ms)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (count < 0 || (count > 0 && !ms)) return fail(c, DTSPH_E_ARG, "bad output");
+    if (first < 0 || first + count > c->steps || first < c->steps - dtsph_ctx::kLoopEv)
+        return fail(c, DTSPH_E_ARG, "steps [%lld, %lld) are not among the last %d taken", (long long)first,
+                    (long long)(first + count), dtsph_ctx::kLoopEv);
+    CK(cudaSetDevice(c->device));
+    for (int32_t i = 0; i < count; ++i) {
+        const int k = (int)((first + i) % dtsph_ctx::kLoopEv);
+        CK(cudaEventSynchronize(c->ev_b[k]));
+        CK(cudaEventElapsedTime(&ms[i], c->ev_a[k], c->ev_b[k]));
+    }
+    return DTSPH_OK;
+}
 
 int dtsph_read_stats(dtsph_ctx *c, int64_t first, int32_t count, dtsph_step_stats *out)
 {

@@ -341,30 +341,39 @@ __global__ void __launch_bounds__(kBlock) k_nlist(Buffers B, const double *__res
 
 // ---------------------------------------------------------------- walls, state n
 
+// The list walkers below give each slot a group of L lanes; lane l of a group
+// takes the list entries l, l + L, ... Summing kernels merge the lanes' partial
+// sums by shuffles, so their summation order depends on L alone: they use the
+// fixed kSumLanes, which keeps every context (solo or batched, any size) on
+// the same order. One lane per slot measured fastest on large problems and
+// costs little on small ones. Block b covers slots b * (kBlock / L) ...
+
+constexpr int kSumLanes = 1;
+
 // Adami et al. wall values at state n in order B: p_w = (sum_f p_f W + rho0 g .
 // sum_f r_wf W) / sum_f W, ghost velocity 2 v_w - sum_f V_f W / sum_f W; written
-// into the packed (V, p) of the wall slot. One lane per wall slot, over its
-// neighbour list at r^n.
-template <int D, bool F32>
+// into the packed (V, p) of the wall slot, from its neighbour list at r^n.
+template <int D, bool F32, int L>
 __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
+    constexpr int SPB = kBlock / L;
     __shared__ Geom G;
     __shared__ Phys P;
-    const int inst = block_instance(B, blockIdx.x * kBlock);
+    const int inst = block_instance(B, blockIdx.x * SPB);
     block_copy(G, B.geo[inst]);
     block_copy(P, B.phys[inst]);
-    const int s = blockIdx.x * kBlock + threadIdx.x;
-    if (s >= B.n) return;
-    const uint32_t gs = B.gid_b[s];
-    if (gs == kNoParticle || gs < (uint32_t)B.nf) return;
+    const int s = blockIdx.x * SPB + threadIdx.x / L, lane_in = threadIdx.x % L;
+    // every lane stays to the end: the partial sums are merged by full-warp shuffles
+    const uint32_t gs = s < B.n ? B.gid_b[s] : kNoParticle;
+    const bool wall = gs != kNoParticle && gs >= (uint32_t)B.nf;
     const auto *nb = nb_ptr<T>(B, 1);
-    const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    const float4 oi = wall && F32 ? B.off[s] : make_float4(0, 0, 0, 0);
     double acc[6] = {0, 0, 0, 0, 0, 0};   // sum W, sum p W, sum rho0 (g . r) W, sum V W
     const double sigma = P.sig_h * P.h;
     const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-    const int cnt = B.pcount[s];
-    for (int k = 0; k < cnt; ++k) {
+    const int cnt = wall ? B.pcount[s] : 0;
+    for (int k = lane_in; k < cnt; k += L) {
         const size_t e = base + (size_t)k * kWarp;
         const uint32_t jb = B.pj[e];
         if (jb & kWallBit) continue;                    // fluid neighbours only
@@ -385,6 +394,11 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
         acc[4] += (double)q.y * W;
         acc[5] += (double)q.z * W;
     }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int t = 0; t < 6; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    if (!wall || lane_in != 0) return;
     const double sw = acc[0];
     double gv[3];
     for (int a = 0; a < 3; ++a) {
@@ -398,43 +412,38 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
 
 // ------------------------------------------------------------------ state n pass
 
-// Rates at (r^n, V^n, p^n) in order B, one lane per slot over its neighbour list
-// at r^n. With PRED, also the predictor of Eqs. (v0, r0): V^0 = V^n + dt F^n,
-// r^0 = r^n + dt V^n + dt^2/2 F^n; the first pressure half step p-hat^0 = p^n +
-// dtau/2 dp^n/dtau (Eq. pkstar_frozen with the state-n rate); and the BDF2
-// source (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact), all in FP64.
-template <int D, bool F32, bool PRED, bool WALLS>
+// Rates at (r^n, V^n, p^n) in order B over the neighbour lists at r^n. With
+// PRED, also the predictor of Eqs. (v0, r0): V^0 = V^n + dt F^n, r^0 = r^n +
+// dt V^n + dt^2/2 F^n; the first pressure half step p-hat^0 = p^n + dtau/2
+// dp^n/dtau (Eq. pkstar_frozen with the state-n rate); and the BDF2 source
+// (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact), all in FP64.
+template <int D, bool F32, bool PRED, bool WALLS, int L>
 __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
+    constexpr int SPB = kBlock / L;
     __shared__ Geom G;
     __shared__ Phys P;
-    const int inst = block_instance(B, blockIdx.x * kBlock);
+    const int inst = block_instance(B, blockIdx.x * SPB);
     block_copy(G, B.geo[inst]);
     block_copy(P, B.phys[inst]);
     const int n = B.n;
-    const int s = blockIdx.x * kBlock + threadIdx.x;
-    if (s >= n) return;
-    const uint32_t gs = B.gid_b[s];
-    if (gs == kNoParticle) return;
-    if (gs >= (uint32_t)B.nf) {
-        if (PRED) {
-            for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s] = B.x_b[(size_t)a * n + s];
-        }
-        return;
-    }
+    const int s = blockIdx.x * SPB + threadIdx.x / L, lane_in = threadIdx.x % L;
+    // every lane stays to the end: the partial sums are merged by full-warp shuffles
+    const uint32_t gs = s < n ? B.gid_b[s] : kNoParticle;
+    const bool fluid = gs < (uint32_t)B.nf;
     const auto *nb = nb_ptr<T>(B, 1);
     const PairConst<T> k = pair_const<T>(P);
     Acc ap, Fa[3];
     {
-        const auto qi = nb[s];
+        const typename Packed<T>::type qi = fluid ? nb[s] : typename Packed<T>::type{};
         const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
         const T pi = (T)qi.w;
-        const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+        const float4 oi = F32 && fluid ? B.off[s] : make_float4(0, 0, 0, 0);
         const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-        const int cnt = B.pcount[s];
-        for (int q = 0; q < cnt; ++q) {
+        const int cnt = fluid ? B.pcount[s] : 0;
+        for (int q = lane_in; q < cnt; q += L) {
             const size_t e = base + (size_t)q * kWarp;
             const uint32_t jb = B.pj[e];
             const int j = (int)(jb & ~kWallBit);
@@ -452,6 +461,19 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
             }
             pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
         }
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        ap.shfl_merge(o);
+#pragma unroll
+        for (int a = 0; a < D; ++a) Fa[a].shfl_merge(o);
+    }
+    if (gs == kNoParticle || lane_in != 0) return;
+    if (!fluid) {
+        if (PRED) {
+            for (int a = 0; a < D; ++a) B.xp_b[(size_t)a * n + s] = B.x_b[(size_t)a * n + s];
+        }
+        return;
     }
     const double apv = (double)(T)ap.value();
     double Fv[3];
@@ -480,13 +502,14 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
 
 // The pair coefficients of every list entry (order of the latest binning):
 // gradW_ij and F_ij for a fluid slot, W_wf and rho0 (g . r_wf) W_wf for a wall
-// slot, at the entry's place in the sliced layout. One lane per slot. Block 0
-// also resets the pseudo-time loop state.
-template <int D, bool F32>
+// slot, at the entry's place in the sliced layout. Entries are independent, so
+// L only sets the parallelism. Block 0 also resets the pseudo-time loop state.
+template <int D, bool F32, int L>
 __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *__restrict__ xpos,
                                                        const uint32_t *__restrict__ gid)
 {
     using T = typename std::conditional<F32, float, double>::type;
+    constexpr int SPB = kBlock / L;
     __shared__ Geom G;
     __shared__ Phys P;
     if (blockIdx.x == 0) {
@@ -505,10 +528,10 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
             B.ctrl->active = B.ninst;
         }
     }
-    const int inst = block_instance(B, blockIdx.x * kBlock);
+    const int inst = block_instance(B, blockIdx.x * SPB);
     block_copy(G, B.geo[inst]);
     block_copy(P, B.phys[inst]);
-    const int s = blockIdx.x * kBlock + threadIdx.x;
+    const int s = blockIdx.x * SPB + threadIdx.x / L, lane_in = threadIdx.x % L;
     const int n = B.n;
     if (s >= n || gid[s] == kNoParticle) return;
     const bool wall_s = gid[s] >= (uint32_t)B.nf;
@@ -516,7 +539,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
     const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
     const T sigma = (T)(P.sig_h * P.h);
     const int cnt = B.pcount[s];
-    for (int q = 0; q < cnt; ++q) {
+    for (int q = lane_in; q < cnt; q += L) {
         const size_t e = base + (size_t)q * kWarp;
         const uint32_t jb = B.pj[e];
         const int j = (int)(jb & ~kWallBit);
@@ -564,8 +587,6 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
         else { constexpr int D = 3; constexpr bool F32 = true; __VA_ARGS__; }                       \
     } while (0)
 
-inline int trav_blocks(int n) { return (n + kBlock - 1) / kBlock; }
-
 // Lanes per slot of the list build: enough warps to fill the GPU on small
 // problems (each group's candidate chain is latency-bound), one lane per slot
 // on large ones.
@@ -589,31 +610,36 @@ void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const u
 // Neighbour lists at r^n (order B), then the wall values and the state-n pass.
 int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st)
 {
-    const int nb = trav_blocks(B.n);
+    constexpr int L = kSumLanes;
+    const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
     launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st);
     int k = 1;
     if (B.nw > 0) {
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, L><<<nb, kBlock, 0, st>>>(B)));
         ++k;
     }
     const bool w = B.nw > 0;
     if (predictor && w)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, true><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, true, L><<<nb, kBlock, 0, st>>>(B)));
     else if (predictor)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, false><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, true, false, L><<<nb, kBlock, 0, st>>>(B)));
     else if (w)
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, true><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, true, L><<<nb, kBlock, 0, st>>>(B)));
     else
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, false><<<nb, kBlock, 0, st>>>(B)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_state_n<D, F32, false, false, L><<<nb, kBlock, 0, st>>>(B)));
     return k + 1;
 }
 
 // Neighbour lists at xpos, then the pair coefficients.
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
 {
-    const int nb = trav_blocks(B.n);
     launch_nlist(B, xpos, cell, gid, st);
-    DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
+    const int L = nlist_lanes(B.n);
+    const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
+    if (L == 1) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 1><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
+    else if (L == 2) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 2><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
+    else if (L == 4) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 4><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
+    else DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 8><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     return 2;
 }
 

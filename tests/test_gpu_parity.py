@@ -196,6 +196,21 @@ def test_autotuner_picks_a_candidate_and_caches_it():
     b.close()
 
 
+@pytest.mark.parametrize("graph", [0, 1, 2])
+def test_loop_times_cover_each_step(graph):
+    """Events around the pseudo-time loop of every step (graph event nodes, or
+    events on the stream with plain launches)."""
+    d = CASES["tgv2d_jitter"]()
+    sim = make_sim(d, precision=dt.DTSPH_FP32C, graph=graph)
+    sim.step(3)
+    sim.sync()
+    ms = dt.dtsph_loop_times(sim.ctx, 0, 3)
+    assert len(ms) == 3 and all(0.0 < m < 1e4 for m in ms)
+    with pytest.raises(dt.DtsphError):
+        dt.dtsph_loop_times(sim.ctx, 2, 2)        # step 3 has not been taken
+    sim.close()
+
+
 def test_graph_and_plain_launches_are_bit_identical():
     d = CASES["tgv2d_jitter"]()
     a = make_sim(d, graph=1, lanes=4)
