@@ -214,14 +214,17 @@ int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, 
 int dtsph_loop_times(dtsph_ctx *ctx, int64_t first, int32_t count, float *ms);
 
 /* Autotuner report: the lanes per particle the iterate kernel uses, and (if
- * ms_by_lanes is not NULL, 4 floats) the mean launch time measured for 1, 2, 4
- * and 8 lanes when this context tuned (-1 where it did not measure, e.g. when
- * the shape was already tuned in this process or lanes was fixed). */
+ * ms_by_lanes is not NULL, 4 floats) the best time measured for 1, 2, 4 and 8
+ * lanes when this context tuned (per launch, or per loop iteration with
+ * graph = 2; for one lane the best staging depth; -1 where it did not
+ * measure, e.g. when the shape was already tuned in this process or lanes was
+ * fixed). */
 int dtsph_tuning(const dtsph_ctx *ctx, int32_t *lanes, float *ms_by_lanes);
 
 /* Every candidate the autotuner timed when this context tuned, in the order
  * timed: lanes per particle, staging depth (0 for lanes > 1) and mean ms per
- * launch of the pseudo-iteration kernel. Writes min(cap, count) entries of
+ * launch of the pseudo-iteration kernel (graph = 0, 1) or per iteration of the
+ * persistent loop kernel over four fixed iterations (graph = 2). Writes min(cap, count) entries of
  * the three arrays (each may be NULL when cap is 0); *count = candidates timed
  * (0 when the shape's choice came from the process cache or lanes was fixed);
  * *stages = staging depth in use (0 when lanes > 1). */

@@ -564,9 +564,46 @@ int probe_ms(dtsph_ctx *c, int launches, float *out)
     return DTSPH_OK;
 }
 
+// Mean device time per pseudo-iteration of the persistent loop kernel over
+// `iters` iterations of every instance (fixed_iters forced on the loop state for
+// the probe, then restored), `reps` launches after one untimed launch.
+int probe_loop_ms(dtsph_ctx *c, int iters, int reps, float *out)
+{
+    const Buffers &B = c->B;
+    int grid = 0;
+    if (loop_grid(B, &grid)) return fail(c, DTSPH_E_CUDA, "occupancy query for the loop kernel failed");
+    std::vector<LoopState> saved(c->ninst), probe;
+    CK(cudaMemcpy(saved.data(), B.ls, sizeof(LoopState) * c->ninst, cudaMemcpyDeviceToHost));
+    probe = saved;
+    for (auto &l : probe) l.fixed_iters = iters;
+    CK(cudaMemcpy(B.ls, probe.data(), sizeof(LoopState) * c->ninst, cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float tot = 0;
+    for (int i = 0; i <= reps; ++i) {
+        launch_loop_reset(B, c->stream);
+        CK(cudaEventRecord(e0, c->stream));
+        CK(launch_loop(B, grid, c->stream));
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (i > 0) tot += ms;
+    }
+    c->launches += 2 * (reps + 1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemcpy(B.ls, saved.data(), sizeof(LoopState) * c->ninst, cudaMemcpyHostToDevice));
+    *out = tot / (float)(reps * iters);
+    return DTSPH_OK;
+}
+
 // Times the candidates of the iterate kernel (one lane per particle at
 // staging depths 2, 3, 4 and 6 unless stages is fixed, then 2, 4 and 8 lanes)
-// on a pair cache built at the initial positions and keeps the fastest. Runs
+// on a pair cache built at the initial positions and keeps the fastest: per
+// iteration of the persistent loop kernel when the step runs it (graph = 2),
+// else per launch of the per-iteration kernel. Runs
 // once per shape in a process, before the first step, so that every step of
 // every context of that shape uses the same kernel (and so the same summation
 // order; the staging depth does not change the arithmetic). The loop buffers
@@ -596,8 +633,13 @@ int autotune(dtsph_ctx *c)
         c->B.lanes = ch.lanes;
         c->B.stages = ch.stages;
         float ms = 0;
-        probe_ms(c, 3, &ms);                   // warm-up
-        int r = probe_ms(c, 10, &ms);
+        int r;
+        if (c->prm[0].graph == 2) {
+            r = probe_loop_ms(c, 4, 5, &ms);
+        } else {
+            probe_ms(c, 3, &ms);               // warm-up
+            r = probe_ms(c, 10, &ms);
+        }
         if (r) return r;
         c->tune_log.push_back({ch.lanes, ch.lanes == 1 ? ch.stages : 0, ms});
         if (ms < best_ms) {
