@@ -339,6 +339,161 @@ __global__ void __launch_bounds__(kBlock) k_nlist(Buffers B, const double *__res
     B.pcount[s] = cnt;
 }
 
+// Neighbour lists in 3D on the FP32C path, one warp per home cell. With cells
+// of ~28 particles, a warp of 32 consecutive slots spans more than one cell and
+// its shared candidate stream would hold four cells per row; here the warp
+// serves exactly the particles of one cell (32 at a time), so every staged
+// candidate is one of theirs. The warp stages the candidates of the 27
+// surrounding cells in shared memory, in the order rows (dz, dy), then dx, then
+// slot, each already moved into the home cell's frame (offset + shift s) and
+// tagged with its slot and wall bit; then every lane tests them with broadcast
+// reads. The FP32 test decides outside the band around 3h, the FP64 test inside
+// it, as in slice_candidates, so the lists are the same.
+constexpr int kCellChunk = 256;     // staged candidates per warp
+
+__device__ __forceinline__ int instance_of_cell(const Buffers &B, int c)
+{
+    int lo = 0, hi = B.ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.inst[mid].cell_off <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kBlock) k_nlist_cells3(Buffers B, const double *__restrict__ xpos)
+{
+    __shared__ float4 cand[kBlock / kWarp][kCellChunk + 4];
+    __shared__ uint8_t ccode[kBlock / kWarp][kCellChunk + 4];
+    __shared__ int tpre[kBlock / kWarp][28];      // candidates before neighbour cell k (k = code)
+    __shared__ int tbeg[kBlock / kWarp][27];      // first slot of neighbour cell k
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & (kWarp - 1), w = threadIdx.x >> 5;
+    const int c = blockIdx.x * (kBlock / kWarp) + w;            // global cell of this warp
+    if (c >= B.ncell) return;                                    // whole warp
+    const int inst = instance_of_cell(B, c);
+    const int cell_off = B.inst[inst].cell_off;
+    const Geom &G = B.geo[inst];
+    const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
+    const int lc = c - cell_off;
+    if (lc >= nx * ny * nz) return;                              // the instance's sentinel cell
+    const int *start = B.cell_start + cell_off;
+    const int hb = start[lc], he = start[lc + 1];
+    if (hb == he) return;
+    const int cx = lc % nx, cy = (lc / nx) % ny, cz = lc / (nx * ny);
+    const float sf[3] = {G.s_f[0], G.s_f[1], G.s_f[2]};
+    const float rc2_lo = G.rc2_lo, rc2_hi = G.rc2_hi;
+    const double rc2 = G.rc2;
+    const int n = B.n, K = B.K;
+    float4 *buf = cand[w];
+    uint8_t *cb = ccode[w];
+    // the 27 neighbour cells, loaded side by side: lane k takes the cell with
+    // code k = (dx + 1) + 3 (dy + 1) + 9 (dz + 1) (empty when off a closed edge)
+    int m = 0;
+    if (lane < 27) {
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+        int x = cx + dx, y = cy + dy, z = cz + dz;
+        bool ok = true;
+        if (x < 0 || x >= nx) { if (G.periodic[0]) x = x < 0 ? x + nx : x - nx; else ok = false; }
+        if (y < 0 || y >= ny) { if (G.periodic[1]) y = y < 0 ? y + ny : y - ny; else ok = false; }
+        if (z < 0 || z >= nz) { if (G.periodic[2]) z = z < 0 ? z + nz : z - nz; else ok = false; }
+        if (ok) {
+            const int nc = (z * ny + y) * nx + x;
+            const int jb = start[nc];
+            m = start[nc + 1] - jb;
+            tbeg[w][lane] = jb;
+        } else {
+            tbeg[w][lane] = 0;
+        }
+    }
+    int incl = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane < 27) tpre[w][lane] = incl - m;
+    const int total = __shfl_sync(full, incl, 26);
+    if (lane == 27) tpre[w][27] = total;
+    __syncwarp();
+    for (int h0 = hb; h0 < he; h0 += kWarp) {
+        const int s = h0 + lane;
+        const bool act = s < he;
+        // an idle lane tests from far away: it fails every distance test
+        const float4 oi = act ? B.off[s] : make_float4(3e18f, 3e18f, 3e18f, 0.f);
+        const size_t base = (size_t)(s >> 5) * K * kWarp + (s & 31);
+        uint32_t *pjw = B.pj + base;
+        uint8_t *pcw = B.pcode + base;
+        int cnt = 0;
+        int k = 0;                                   // neighbour cell of this lane's next fill position
+        for (int c0 = 0; c0 < total; c0 += kCellChunk) {
+            const int take = min(total - c0, kCellChunk);
+            // fill: position p of the stream is candidate p - tpre[k] of cell k
+            for (int q = lane; q < take; q += kWarp) {
+                const int p = c0 + q;
+                while (tpre[w][k + 1] <= p) ++k;
+                const int j = tbeg[w][k] + (p - tpre[w][k]);
+                const float4 oj = B.off[j];
+                const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+                float4 e;
+                e.x = __fadd_rn(oj.x, (float)dx * sf[0]);
+                e.y = __fadd_rn(oj.y, (float)dy * sf[1]);
+                e.z = __fadd_rn(oj.z, (float)dz * sf[2]);
+                e.w = __uint_as_float((uint32_t)j | (oj.w != 0.f ? kWallBit : 0u));
+                buf[q] = e;
+                cb[q] = (uint8_t)k;
+            }
+            // pad to a multiple of four with entries that fail every test
+            const int take4 = (take + 3) & ~3;
+            if (take + lane < take4) buf[take + lane] = make_float4(-3e18f, -3e18f, -3e18f, __uint_as_float(kNoParticle));
+            __syncwarp();
+            for (int q = 0; q < take4; q += 4) {
+                bool in[4], band[4];
+                uint32_t jw[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 e = buf[q + u];
+                    const float d0 = __fsub_rn(oi.x, e.x), d1 = __fsub_rn(oi.y, e.y), d2 = __fsub_rn(oi.z, e.z);
+                    const float q2 = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
+                    jw[u] = __float_as_uint(e.w);
+                    const bool other = (jw[u] & ~kWallBit) != (uint32_t)s;
+                    in[u] = q2 < rc2_lo && other;
+                    band[u] = q2 >= rc2_lo && q2 < rc2_hi && other;
+                }
+                // the FP64 decision inside the band (rare)
+                if (__any_sync(full, band[0] || band[1] || band[2] || band[3])) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (band[u]) {
+                            double ee[3];
+                            in[u] = sep64<3>(G, xpos, n, s, (int)(jw[u] & ~kWallBit), ee) < rc2;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (in[u]) {
+                        if (cnt < K) {
+                            pjw[(size_t)cnt * kWarp] = jw[u];
+                            pcw[(size_t)cnt * kWarp] = cb[q + u];
+                        }
+                        ++cnt;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (act) {
+            if (cnt > K) {
+                atomicOr(B.err, kErrCapacity);
+                cnt = K;
+            }
+            B.pcount[s] = cnt;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- walls, state n
 
 // The list walkers below give each slot a group of L lanes; lane l of a group
@@ -599,6 +754,10 @@ int nlist_lanes(int n)
 
 void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
 {
+    if (B.dim == 3 && B.fp32c) {
+        k_nlist_cells3<<<(B.ncell + kBlock / kWarp - 1) / (kBlock / kWarp), kBlock, 0, st>>>(B, xpos);
+        return;
+    }
     const int L = nlist_lanes(B.n);
     const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
     if (L == 1) DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist<D, F32, 1><<<nb, kBlock, 0, st>>>(B, xpos, cell, gid)));
