@@ -67,6 +67,14 @@ def make_workload(name: str, n_side: int, re: float):
     return d, cfg
 
 
+def with_shifting(d, wcfg):
+    """Particle shifting after every real step (Sec. 3.5) in every instance's
+    parameters, for both arms."""
+    for x in (d if isinstance(d, list) else [d]):
+        x["cfg"] = dict(x["cfg"], shifting=1)
+    wcfg["shifting"] = "on (Eqs. shift-deltar, shift-correct, after every real step)"
+
+
 class Job:
     """One context running a workload: a single instance or a batch."""
 
@@ -134,6 +142,7 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="lanes per particle of the iterate kernel (0: autotuned)")
     ap.add_argument("--stages", type=int, default=0, help="staging depth with --lanes 1 (0: autotuned or 3)")
+    ap.add_argument("--shifting", action="store_true", help="particle shifting after every real step (both arms)")
     return ap.parse_args()
 
 
@@ -304,6 +313,8 @@ def main_ours(args):
     from paper_1904_00861_gb300 import build as b
     b.build()
     d, wcfg = make_workload(args.workload, args.n_side, args.re)
+    if args.shifting:
+        with_shifting(d, wcfg)
     kern = dict(lanes=args.lanes, stages=args.stages)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if world > 1:
@@ -399,6 +410,8 @@ def main_reference(args):
     import oracle
     oracle.build()
     d, wcfg = make_workload(args.workload, args.n_side, args.re)
+    if args.shifting:
+        with_shifting(d, wcfg)
     states = oracle_states(d)
     for st in states:
         st.step(args.warmup)

@@ -87,6 +87,12 @@ typedef struct {
     int32_t stages;           /* staging depth of the one-lane kernel (lanes = 1): pair-cache
                                  chunks in flight per warp in shared memory, 2..8; 0 = 3, or
                                  picked by the autotuner together with lanes */
+    int32_t shifting;         /* 1: particle shifting after every real step (Sec. 3.5, Eqs.
+                                 shift-deltar, shift-correct): at the new positions, over fluid
+                                 neighbours, dr_i = -(h^2/2) sum_j V_j (1 + W_ij / W(h)) gradW_ij,
+                                 then p_i += gradp_i . dr_i, V_i += (gradV_i) dr_i with
+                                 grad f_i = sum_j V_j (f_j - f_i) gradW_ij, r_i += dr_i;
+                                 0 = off. Instances of a batch share it. */
 } dtsph_params;
 
 typedef struct {

@@ -204,6 +204,7 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
         return fail(c, DTSPH_E_ARG, "lanes must be 0, 1, 2, 4 or 8");
     if (p->stages != 0 && (p->stages < 2 || p->stages > kMaxStages))
         return fail(c, DTSPH_E_ARG, "stages must be 0 or in [2, %d]", kMaxStages);
+    if (p->shifting != 0 && p->shifting != 1) return fail(c, DTSPH_E_ARG, "shifting must be 0 or 1");
     return DTSPH_OK;
 }
 
@@ -402,10 +403,14 @@ int enqueue_iteration(dtsph_ctx *c, cudaStream_t st, unsigned long long cond, in
     return k;
 }
 
-int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st) { return launch_outer(c->B, st); }
+// After the loop: the position update and buffer rotation, then shifting if on.
+int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st)
+{
+    int k = launch_outer(c->B, st);
+    if (c->prm[0].shifting) k += launch_shift(c->B, st);
+    return k;
+}
 
-// Graph of one real step with the persistent loop: pre-loop kernels -> one
-// cooperative loop kernel -> outer.
 // The event-record nodes around the loop in a captured step graph.
 int find_event_nodes(dtsph_ctx *c, cudaGraph_t g)
 {
@@ -427,6 +432,8 @@ int find_event_nodes(dtsph_ctx *c, cudaGraph_t g)
     return DTSPH_OK;
 }
 
+// Graph of one real step with the persistent loop: pre-loop kernels -> one
+// cooperative loop kernel -> outer.
 int build_graph_persistent(dtsph_ctx *c)
 {
     int grid = 0;
@@ -765,8 +772,8 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
         int r = validate(c, &params[i]);
         if (!r && (params[i].dim != params[0].dim || params[i].precision != params[0].precision ||
                    params[i].graph != params[0].graph || params[i].lanes != params[0].lanes ||
-                   params[i].stages != params[0].stages))
-            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph, lanes and stages");
+                   params[i].stages != params[0].stages || params[i].shifting != params[0].shifting))
+            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph, lanes, stages and shifting");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;

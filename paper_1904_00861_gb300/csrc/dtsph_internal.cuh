@@ -178,6 +178,10 @@ int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, con
 int launch_walls_iter(const Buffers &B, cudaStream_t st);
 int launch_iterate(const Buffers &B, unsigned long long cond_handle, int use_cond, cudaStream_t st);
 int launch_outer(const Buffers &B, cudaStream_t st);
+// Particle shifting of the fluid after the real step: bins at r^{n+1}, gathers
+// the state into order B, builds the lists, and shifts (results written back to
+// order A).
+int launch_shift(const Buffers &B, cudaStream_t st);
 // Persistent pseudo-time loop (one cooperative launch per real step): grid size
 // (co-resident blocks, at most one per tile) and the launch itself.
 int loop_grid(const Buffers &B, int *grid);

@@ -732,6 +732,87 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
     }
 }
 
+// ---------------------------------------------------------------- shifting
+
+// Particle shifting after the real step (Sec. 3.5), in order B at r^{n+1}, one
+// lane per slot, over fluid neighbours only:
+//   dr_i = -(h^2/2) sum_j V_j (1 + W_ij / W(h)) gradW_ij          Eq. (shift-deltar)
+//   f_i <- f_i + (grad f)_i . dr_i, (grad f)_i = sum_j V_j (f_j - f_i) gradW_ij
+//                                                      for f = p, V   Eq. (shift-correct)
+//   r_i <- r_i + dr_i (wrapped on periodic axes)
+// with V_j = m / rho0 and W(h) the kernel at r = h. Every gradient uses the
+// unshifted fields (reads order B); the shifted r, V, p go to the particle's
+// slot in order A (perm), which the next step bins again.
+template <int D, bool F32>
+__global__ void __launch_bounds__(kBlock) k_shift(Buffers B)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
+    __shared__ Geom G;
+    __shared__ Phys P;
+    const int inst = block_instance(B, blockIdx.x * kBlock);
+    block_copy(G, B.geo[inst]);
+    block_copy(P, B.phys[inst]);
+    const int n = B.n;
+    const int s = blockIdx.x * kBlock + threadIdx.x;
+    if (s >= n) return;
+    if (B.gid_b[s] >= (uint32_t)B.nf) return;            // walls and padding stay
+    const auto *nb = nb_ptr<T>(B, 1);                     // (V, p) at r^{n+1}, order B
+    const auto qi = nb[s];
+    const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
+    const T pi = (T)qi.w;
+    const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
+    const T vol = (T)(P.m / P.rho0);
+    const T sigma = (T)(P.sig_h * P.h);
+    const T w_h = sigma * quintic_w<T>(T(1));
+    Acc dr[3], gp[3], gv[3][3];
+    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+    const int cnt = B.pcount[s];
+    for (int k = 0; k < cnt; ++k) {
+        const size_t e = base + (size_t)k * kWarp;
+        const uint32_t jb = B.pj[e];
+        if (jb & kWallBit) continue;                      // fluid neighbours only
+        const int j = (int)jb;
+        int dx, dy, dz;
+        decode_shift(B.pcode[e], dx, dy, dz);
+        T d[3], r2;
+        listed_sep<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2);
+        const T r = sqrt(r2);
+        const T q = r * (T)P.inv_h;
+        const T a = r > T(0) ? (T)P.sig_h * quintic_dwdq<T>(q) / r : T(0);
+        const T fdr = vol * (T(1) + sigma * quintic_w<T>(q) / w_h);
+        const auto qj = nb[j];
+        const T vj[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
+        const T dp = vol * ((T)qj.w - pi);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const T gw = a * d[c];
+            dr[c].add(fdr * gw);
+            gp[c].add(dp * gw);
+#pragma unroll
+            for (int b2 = 0; b2 < D; ++b2) gv[b2][c].add(vol * (vj[b2] - vi[b2]) * gw);
+        }
+    }
+    const double dmul = -0.5 * P.h * P.h;
+    double drv[3] = {0, 0, 0};
+    for (int c = 0; c < D; ++c) drv[c] = dmul * (double)(T)dr[c].value();
+    const int o = B.perm[s];
+    double pnew = B.pn_b[s];
+    for (int c = 0; c < D; ++c) pnew += (double)(T)gp[c].value() * drv[c];
+    B.pn_a[o] = pnew;
+    for (int b2 = 0; b2 < D; ++b2) {
+        double v = B.vn_b[(size_t)b2 * n + s];
+        for (int c = 0; c < D; ++c) v += (double)(T)gv[b2][c].value() * drv[c];
+        B.vn_a[(size_t)b2 * n + o] = v;
+        double x = B.x_b[(size_t)b2 * n + s] + drv[b2];
+        if (G.periodic[b2]) {
+            if (x >= G.hi[b2]) x -= G.L[b2];
+            else if (x < G.lo[b2]) x += G.L[b2];
+        }
+        B.x_a[(size_t)b2 * n + o] = x;
+    }
+}
+
 }  // namespace
 
 #define DTSPH_DISPATCH(D_, F32_, ...)                                                  \
@@ -800,6 +881,15 @@ int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, con
     else if (L == 4) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 4><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     else DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 8><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     return 2;
+}
+
+int launch_shift(const Buffers &B, cudaStream_t st)
+{
+    int k = launch_binning(B, B.x_a, B.gid_a, st);            // cells at r^{n+1}
+    k += launch_permute_a_to_b(B, st);
+    launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st);
+    DTSPH_DISPATCH(B.dim, B.fp32c, (k_shift<D, F32><<<(B.n + kBlock - 1) / kBlock, kBlock, 0, st>>>(B)));
+    return k + 2;
 }
 
 }  // namespace dtsph

@@ -148,6 +148,43 @@ def test_steps_fp64_match_oracle(case, nsteps):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case,nsteps", [("tgv2d_jitter", 4), ("cavity", 3), ("tgv3d", 2)])
+def test_shifting_matches_oracle(case, nsteps, prec):
+    """Particle shifting with the Taylor correction (Sec. 3.5) after every real
+    step against the oracle's shifting: FP64 within 1e-10 with the same
+    iteration counts, FP32C velocities within 1e-4; and the shift really moves
+    the particles (an unshifted oracle run ends elsewhere)."""
+    d = CASES[case]()
+    box = box_of(d)
+    nf = d["nf"]
+    sim, orc, out = run_pair(d, nsteps, precision=prec, shifting=1)
+    st, rec, x, v, p = out[-1]
+    tol = 1e-10 if prec == dt.DTSPH_FP64 else 1e-4
+    if prec == dt.DTSPH_FP64:
+        assert [o[0]["iters"] for o in out] == [o[1]["iters"] for o in out]
+        assert rel(p, orc.p) < tol
+    assert np.max(np.abs(wrap_diff(x, orc.x[:nf], box))) < tol * np.max(np.abs(orc.x))
+    assert rel(v, orc.v) < tol
+    plain = make_oracle(d)
+    plain.step(nsteps)
+    moved = np.max(np.abs(wrap_diff(plain.x[:nf], orc.x[:nf], box)))
+    assert moved > 1e-6 * np.max(np.abs(orc.x)), moved
+    sim.close()
+
+
+def test_shifting_same_bits_in_every_graph_mode():
+    d = CASES["tgv2d_jitter"]()
+    runs = []
+    for graph in (0, 1, 2):
+        sim = make_sim(d, precision=dt.DTSPH_FP32C, graph=graph, lanes=1, shifting=1)
+        sim.step(3)
+        runs.append((sim.x, sim.v, sim.p))
+        sim.close()
+    for r in runs[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(r, runs[0]))
+
+
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 @pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
 def test_every_lane_split_matches_oracle(lanes, prec):
