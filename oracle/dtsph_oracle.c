@@ -29,7 +29,10 @@
  *                        form of Sec. 2.2; convergence test Eq. (conv) with the
  *                        stagnation and iteration-cap rules of Sec. 3.4; position
  *                        update Eq. (r-update); optional shifting Eqs. (shift,
- *                        shift-deltar, shift-correct) of Sec. 3.5.
+ *                        shift-deltar, shift-correct) of Sec. 3.5. Steady mode
+ *                        (Sec. 2.4 "Steady state solutions", Eq. mom-steady):
+ *                        particles fixed, no BDF2 term, no EDAC term, convection
+ *                        term added, the pseudo-time loop as above.
  *
  * Readings taken where the paper is silent or garbled (all listed in the design
  * notes): the EDAC diffusion denominator is r^2 + eta h^2 (edac_h2_literal = 1
@@ -76,7 +79,7 @@ typedef struct {
     int32_t fixed_iters;      /* > 0: exactly this many iterations, no stop rules */
     int32_t use_bruteforce;   /* 1: O(N^2) neighbour search instead of cells */
     int32_t shifting;         /* 1: particle shifting after the real step */
-    int32_t pad_;
+    int32_t steady;           /* 1: steady-state mode (Sec. 2.4, Eq. mom-steady) */
 } orc_params;
 
 typedef struct {
@@ -409,7 +412,7 @@ static void rates(const orc_params *P, int64_t nf, const double *x, const double
             double vij_gw = 0.0;
             for (int a = 0; a < dim; ++a) vij_gw = vij_gw + (vi[a] - vdiv[a]) * gw[a];
             api = api + m * rho / rho * c * c * vij_gw;
-            if (P->edac)
+            if (P->edac && !P->steady)   /* the steady pressure equation has no EDAC term */
                 api = api + 4.0 * m / ((rho + rho) * rho) * nu_e * (p[i] - pj) * rdotgw / (r2 + eh2);
 
             double pi_ij = 0.0;
@@ -425,6 +428,13 @@ static void rates(const orc_params *P, int64_t nf, const double *x, const double
             double visc = m * 4.0 * P->nu * rdotgw / ((rho + rho) * (r2 + P->eta * h * h));
             for (int a = 0; a < dim; ++a)
                 Fi[a] = Fi[a] - m * pres * gw[a] + visc * (vi[a] - vvis[a]);
+            if (P->steady) {
+                /* convection of Eq. (mom-steady): V_i . sum_j (V_i m_i/rho_i + V_j m_j/rho_j)
+                   gradW_ij, the wall's prescribed velocity for a wall neighbour */
+                double vgw = 0.0;
+                for (int a = 0; a < dim; ++a) vgw = vgw + vi[a] * gw[a];
+                for (int a = 0; a < dim; ++a) Fi[a] = Fi[a] - (m / rho * vi[a] + m / rho * vdiv[a]) * vgw;
+            }
         }
         ap[i] = api;
         for (int a = 0; a < dim; ++a) F[i * dim + a] = Fi[a] + P->g[a];
@@ -572,13 +582,18 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
     rates(P, nf, x, v, p, vw, pw, vg, &L, ap_prev, F);
     nlist_free(&L);
 
-    /* predictor, Eqs. (v0, r0); p^0 = p^n */
+    /* predictor, Eqs. (v0, r0); p^0 = p^n. Steady mode: the particles stay and
+       the iteration starts from the state itself (Sec. 2.4) */
     memcpy(x0, x, (size_t)n * dim * sizeof(double));
     for (int64_t i = 0; i < nf; ++i) {
         for (int a = 0; a < dim; ++a) {
             size_t k = (size_t)i * dim + a;
-            vk[k] = v[k] + dt * F[k];
-            x0[k] = x[k] + dt * v[k] + dt * dt / 2.0 * F[k];
+            if (P->steady) {
+                vk[k] = v[k];
+            } else {
+                vk[k] = v[k] + dt * F[k];
+                x0[k] = x[k] + dt * v[k] + dt * dt / 2.0 * F[k];
+            }
         }
         wrap(P, x0 + i * dim);
         pk[i] = p[i];
@@ -599,9 +614,14 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
             double av2 = 0.0;
             for (int a = 0; a < dim; ++a) {
                 size_t q = (size_t)i * dim + a;
-                /* Eq. (dv_dtau_exact), frozen form */
-                double bdf = (3.0 * vk[q] - 4.0 * v[q] + v_prev[q]) / (2.0 * dt);
-                double av = (F[q] - bdf) * kappa;
+                /* Eq. (dv_dtau_exact), frozen form; steady mode: Eq. (mom-steady) as is */
+                double av;
+                if (P->steady) {
+                    av = F[q];
+                } else {
+                    double bdf = (3.0 * vk[q] - 4.0 * v[q] + v_prev[q]) / (2.0 * dt);
+                    av = (F[q] - bdf) * kappa;
+                }
                 vk1[q] = vk[q] + dtau * av;                   /* Eq. (vkp1_frozen) */
                 av2 = av2 + av * av;
             }
@@ -627,18 +647,19 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
     st->rp = hp[k - 1];
     st->rv = hv[k - 1];
 
-    /* Eq. (r-update), then V^{n-1} <- V^n, V^n <- V^{n+1}, p^n <- p^{n+1} */
+    /* Eq. (r-update), then V^{n-1} <- V^n, V^n <- V^{n+1}, p^n <- p^{n+1};
+       steady mode: the particles stay */
     for (int64_t i = 0; i < nf; ++i) {
         for (int a = 0; a < dim; ++a) {
             size_t q = (size_t)i * dim + a;
-            x[q] = x[q] + dt / 2.0 * (v[q] + vk[q]);
+            if (!P->steady) x[q] = x[q] + dt / 2.0 * (v[q] + vk[q]);
             v_prev[q] = v[q];
             v[q] = vk[q];
         }
         wrap(P, x + i * dim);
         p[i] = pk[i];
     }
-    if (P->shifting) {
+    if (P->shifting && !P->steady) {
         if (build_neighbors(P, n, x, &L)) goto out;
         shift(P, nf, x, v, p, &L);
         nlist_free(&L);

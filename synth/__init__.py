@@ -122,6 +122,30 @@ def cavity2d(n: int = 200, re: float = 100.0, U: float = 1.0, layers: int = 3, *
                 v_prev=np.zeros((N, 2)), vw=vw, nf=N)
 
 
+def couette2d(n: int = 30, re: float = 10.0, U: float = 1.0, layers: int = 3, **kw) -> dict:
+    """Plane Couette channel: periodic in x on [0, 1), n*n fluid particles on the
+    regular lattice of [0, 1]^2, `layers` rows of wall particles below y = 0
+    (still) and above y = 1 (moving at (U, 0)); the fluid starts at u = U y,
+    v = 0, p = 0 (the steady solution)."""
+    dx = 1.0 / n
+    cfg = base_params(2, dx, U, U * 1.0 / re, **kw)
+    cfg.update(periodic=(1, 0, 0), lo=(0.0, -layers * dx, 0.0), hi=(1.0, 1.0 + layers * dx, 1.0),
+               workload="couette2d", n_side=n, re=re)
+    i = np.arange(n * n) % n
+    j = np.arange(n * n) // n
+    xf = np.stack([(i + 0.5) * dx, (j + 0.5) * dx], 1)
+    iw = np.arange(n * 2 * layers) % n
+    jw = np.arange(n * 2 * layers) // n
+    jw = np.where(jw < layers, jw - layers, jw - layers + n)
+    xw = np.stack([(iw + 0.5) * dx, (jw + 0.5) * dx], 1)
+    vw = np.zeros_like(xw)
+    vw[xw[:, 1] > 1.0, 0] = U
+    N = n * n
+    v = np.zeros((N, 2))
+    v[:, 0] = U * xf[:, 1]
+    return dict(cfg=cfg, x=np.concatenate([xf, xw]), v=v, p=np.zeros(N), v_prev=v.copy(), vw=vw, nf=N)
+
+
 def tgv3d(n: int = 128, re: float = 1600.0, U: float = 1.0, jitter: float = 0.05, seed: int = 1904, **kw) -> dict:
     """3D Taylor-Green vortex on [0, 2 pi)^3 with n^3 particles: u = U sin x cos y
     cos z, v = -U cos x sin y cos z, w = 0, p = rho0 U^2/16 (cos 2x + cos 2y)(cos 2z

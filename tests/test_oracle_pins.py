@@ -439,3 +439,69 @@ def test_shifting_is_zero_on_a_lattice_and_reduces_disorder():
     before = np.abs(st.x - lat).mean()
     st.step(1)
     assert np.abs(st.x - lat).mean() < 0.9 * before
+
+
+# -------------------------------------------------------------- steady state
+
+def test_steady_convection_operator_against_closed_form():
+    """Eq. (mom-steady), convection term: on u = sin 2 pi x, v = 0 (periodic
+    lattice, p = 0, nu = 0) the momentum rate is -(V . grad)V = -pi sin 4 pi x
+    in x and 0 in y, to the SPH operator error."""
+    d = synth.tgv2d(64, jitter=0.0)
+    x = d["x"]
+    N = len(x)
+    v = np.zeros((N, 2))
+    v[:, 0] = np.sin(2 * math.pi * x[:, 0])
+    cfg = dict(d["cfg"], nu=0.0)
+    _, F, _, _ = oracle.rates(cfg, x, v, np.zeros(N), None, N, steady=1)
+    exact = -math.pi * np.sin(4 * math.pi * x[:, 0])
+    assert np.max(np.abs(F[:, 0] - exact)) < 0.01 * math.pi
+    assert np.max(np.abs(F[:, 1])) < 1e-12
+    _, F0, _, _ = oracle.rates(cfg, x, v, np.zeros(N), None, N, steady=0)
+    assert np.max(np.abs(F0[:, 0])) < 1e-10          # no convection outside the steady mode
+
+
+def test_steady_pressure_equation_has_no_edac_term():
+    """The steady pressure rate is Eq. (dp-dtau-frozen) alone: with V = 0 and a
+    non-uniform p it is zero, where the EDAC term of the unsteady rate is not."""
+    d = synth.tgv2d(32, jitter=0.0)
+    x = d["x"]
+    N = len(x)
+    p = np.sin(2 * math.pi * x[:, 0])
+    ap1, _, _, _ = oracle.rates(d["cfg"], x, np.zeros((N, 2)), p, None, N, steady=1)
+    ap0, _, _, _ = oracle.rates(d["cfg"], x, np.zeros((N, 2)), p, None, N, steady=0)
+    assert np.max(np.abs(ap1)) == 0.0 and np.max(np.abs(ap0)) > 0.1
+
+
+def test_steady_uniform_flow_stays_put():
+    """A uniform flow is a steady solution: the steady iteration leaves V and the
+    particles where they are (every pair term vanishes; the convection sum of
+    gradW over a periodic lattice cancels to rounding)."""
+    d = synth.tgv2d(24, jitter=0.0)
+    N = len(d["x"])
+    v = np.tile([0.7, -0.3], (N, 1))
+    st = oracle.State(d["cfg"], d["x"], v, np.zeros(N), v, steady=1, fixed_iters=20)
+    st.step(1)
+    assert np.max(np.abs(st.v - v)) < 1e-12 and np.max(np.abs(st.p)) < 1e-9
+    assert np.array_equal(st.x, d["x"])
+
+
+def test_steady_couette_from_rest_converges_to_the_linear_profile():
+    """Plane Couette flow between a still wall (y = 0) and one moving at U
+    (y = 1): from rest, the steady iteration (no BDF2 term, particles fixed)
+    reaches u = U y, v = 0, p = 0 to the near-wall SPH error, and its residual
+    vanishes; the unsteady scheme with the same pseudo-iterations in one real
+    step stays close to rest."""
+    d = synth.couette2d(16, re=5.0)
+    nf = d["nf"]
+    y = d["x"][:nf, 1]
+    z = np.zeros_like(d["v"])
+    st = oracle.State(d["cfg"], d["x"], z, d["p"], z, vw=d["vw"], nf=nf, steady=1, fixed_iters=4000)
+    rec = st.step(1)[0]
+    assert np.max(np.abs(st.v[:, 0] - y)) < 1e-3
+    assert np.max(np.abs(st.v[:, 1])) < 1e-12 and np.max(np.abs(st.p)) < 1e-9
+    assert rec["rv"] < 1e-6
+    assert np.array_equal(st.x, d["x"])
+    un = oracle.State(d["cfg"], d["x"], z, d["p"], z, vw=d["vw"], nf=nf, fixed_iters=4000)
+    un.step(1)
+    assert np.max(np.abs(un.v[:, 0] - y)) > 0.3
