@@ -75,6 +75,14 @@ def with_shifting(d, wcfg):
     wcfg["shifting"] = "on (Eqs. shift-deltar, shift-correct, after every real step)"
 
 
+def with_steady(d, wcfg, iters):
+    """Steady-state mode (Sec. 2.4, Eq. mom-steady) with a fixed number of
+    pseudo-iterations per solve, in every instance, for both arms."""
+    for x in (d if isinstance(d, list) else [d]):
+        x["cfg"] = dict(x["cfg"], steady=1, fixed_iters=iters)
+    wcfg["steady"] = f"on: one pseudo-time solve of {iters} iterations per step, particles fixed"
+
+
 class Job:
     """One context running a workload: a single instance or a batch."""
 
@@ -143,6 +151,8 @@ def parse():
                     help="lanes per particle of the iterate kernel (0: autotuned)")
     ap.add_argument("--stages", type=int, default=0, help="staging depth with --lanes 1 (0: autotuned or 3)")
     ap.add_argument("--shifting", action="store_true", help="particle shifting after every real step (both arms)")
+    ap.add_argument("--steady", type=int, default=0,
+                    help="steady-state mode with this many pseudo-iterations per solve (both arms; 0: off)")
     return ap.parse_args()
 
 
@@ -315,6 +325,8 @@ def main_ours(args):
     d, wcfg = make_workload(args.workload, args.n_side, args.re)
     if args.shifting:
         with_shifting(d, wcfg)
+    if args.steady:
+        with_steady(d, wcfg, args.steady)
     kern = dict(lanes=args.lanes, stages=args.stages)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if world > 1:
@@ -412,6 +424,8 @@ def main_reference(args):
     d, wcfg = make_workload(args.workload, args.n_side, args.re)
     if args.shifting:
         with_shifting(d, wcfg)
+    if args.steady:
+        with_steady(d, wcfg, args.steady)
     states = oracle_states(d)
     for st in states:
         st.step(args.warmup)

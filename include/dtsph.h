@@ -93,6 +93,14 @@ typedef struct {
                                  then p_i += gradp_i . dr_i, V_i += (gradV_i) dr_i with
                                  grad f_i = sum_j V_j (f_j - f_i) gradW_ij, r_i += dr_i;
                                  0 = off. Instances of a batch share it. */
+    int32_t steady;           /* 1: steady-state mode (Sec. 2.4 "Steady state solutions", Eq.
+                                 mom-steady): the particles never move; each dtsph_step runs one
+                                 pseudo-time solve from the current state with no real-time
+                                 (BDF2) term, the pressure rate of Eq. (dp-dtau-frozen) without
+                                 the EDAC term, and the convection term V_i . sum_j (V_i m/rho0 +
+                                 V_j m/rho0) gradW_ij in the momentum rate; dt only scales the
+                                 residuals and sets dtau = dt / beta. Shifting must be off.
+                                 Instances of a batch share it. */
 } dtsph_params;
 
 typedef struct {

@@ -182,6 +182,15 @@ void setup_phys(const dtsph_params &p, Phys &P)
     P.inv_2dt = 1.0 / (2.0 * p.dt);
     P.edac = p.edac;
     P.use_av = p.alpha != 0.0;
+    P.vol = p.m / p.rho0;
+    P.steady = p.steady;
+    if (p.steady) {
+        // Eq. (mom-steady): dV/dtau is the momentum rate itself (no BDF2 term);
+        // the pressure rate has no EDAC term
+        P.kappa = 1.0;
+        P.kc3 = 0.0;
+        P.edac = 0;
+    }
 }
 
 int validate(dtsph_ctx *c, const dtsph_params *p)
@@ -205,6 +214,8 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
     if (p->stages != 0 && (p->stages < 2 || p->stages > kMaxStages))
         return fail(c, DTSPH_E_ARG, "stages must be 0 or in [2, %d]", kMaxStages);
     if (p->shifting != 0 && p->shifting != 1) return fail(c, DTSPH_E_ARG, "shifting must be 0 or 1");
+    if (p->steady != 0 && p->steady != 1) return fail(c, DTSPH_E_ARG, "steady must be 0 or 1");
+    if (p->steady && p->shifting) return fail(c, DTSPH_E_ARG, "the steady mode keeps the particles fixed: no shifting");
     return DTSPH_OK;
 }
 
@@ -772,8 +783,9 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
         int r = validate(c, &params[i]);
         if (!r && (params[i].dim != params[0].dim || params[i].precision != params[0].precision ||
                    params[i].graph != params[0].graph || params[i].lanes != params[0].lanes ||
-                   params[i].stages != params[0].stages || params[i].shifting != params[0].shifting))
-            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph, lanes, stages and shifting");
+                   params[i].stages != params[0].stages || params[i].shifting != params[0].shifting ||
+                   params[i].steady != params[0].steady))
+            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph, lanes, stages, shifting and steady");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;

@@ -73,6 +73,10 @@ struct Phys {
     double rv_scale;     // dt / v_ref / nf
     float dtau_f;        // dtau rounded to FP32 (the FP32C p-hat update)
     int edac, use_av;
+    int steady;          // steady-state mode: kappa = 1, no 3/(2dt) term, source -g,
+                         // convection term, particles fixed
+    int pad_s;
+    double vol;          // m / rho0 (convection term)
 };
 
 // Convergence control of one instance's pseudo-time loop, in device memory.

@@ -569,7 +569,7 @@ __device__ __forceinline__ int finish_iteration(LoopState *ls, const Phys &P, in
 // applies its stop rules; the last block of all sets the while-node condition
 // (some instance still iterating).
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock, (F32 && D == 2) ? 4 : 1) k_iterate(Buffers B, unsigned long long cond,
+__global__ void __launch_bounds__(kBlock, F32 ? (D == 2 ? 4 : 3) : 1) k_iterate(Buffers B, unsigned long long cond,
                                                                           int use_cond)
 {
     using T = typename std::conditional<F32, float, double>::type;
@@ -804,16 +804,19 @@ __global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
     if (B.gid_a[s] >= (uint32_t)B.nf) return;           // walls and padding
     const Geom &G = B.geo[inst];
     const double dt = B.phys[inst].dt;
+    const bool move = !B.phys[inst].steady;               // steady mode: the particles stay
     for (int a = 0; a < D; ++a) {
         const size_t q = (size_t)a * n + s;
         const double vn = B.vn_a[q];
         const double vK = B.vk[fin][q];
-        double x = __fma_rn(0.5 * dt, __dadd_rn(vn, vK), B.x_a[q]);
-        if (G.periodic[a]) {
-            if (x >= G.hi[a]) x = __dsub_rn(x, G.L[a]);
-            else if (x < G.lo[a]) x = __dadd_rn(x, G.L[a]);
+        if (move) {
+            double x = __fma_rn(0.5 * dt, __dadd_rn(vn, vK), B.x_a[q]);
+            if (G.periodic[a]) {
+                if (x >= G.hi[a]) x = __dsub_rn(x, G.L[a]);
+                else if (x < G.lo[a]) x = __dadd_rn(x, G.L[a]);
+            }
+            B.x_a[q] = x;
         }
-        B.x_a[q] = x;
         B.vnm1_a[q] = vn;
         B.vn_a[q] = vK;
     }

@@ -116,7 +116,8 @@ struct Plain64 {
 template <typename T>
 struct PairConst {
     T c_div, c_edac, c_p, c_visc, c_av_m;   // c_av_m = m * alpha h c / rho0
-    int edac, use_av;
+    T vol;                                   // m / rho0 (steady convection term)
+    int edac, use_av, steady, rare;         // rare = use_av || steady
 };
 
 template <typename T>
@@ -128,14 +129,18 @@ __device__ __forceinline__ PairConst<T> pair_const(const Phys &P)
     k.c_p = (T)P.c_p;
     k.c_visc = (T)P.c_visc;
     k.c_av_m = (T)(P.m * P.c_av);
+    k.vol = (T)P.vol;
     k.edac = P.edac;
     k.use_av = P.use_av;
+    k.steady = P.steady;
+    k.rare = P.use_av || P.steady;
     return k;
 }
 
 // One pair's contribution. g: gradW_ij (D comps), F: F_ij. vi, pi: own velocity
 // and pressure; vj_div, vj_vis: neighbour velocity seen by the divergence and by
-// the viscous term (equal for fluid neighbours); pj: neighbour pressure.
+// the viscous term (equal for fluid neighbours); pj: neighbour pressure. In the
+// steady-state mode (k.steady) the convection term is added.
 template <int D, typename T, typename Acc>
 __device__ __forceinline__ void pair_accumulate(const PairConst<T> &k, const T *g, T F, const T *vi, T pi,
                                                 const T *vj_div, const T *vj_vis, T pj, Acc &ap, Acc *Fi)
@@ -152,17 +157,33 @@ __device__ __forceinline__ void pair_accumulate(const PairConst<T> &k, const T *
     if (k.edac) t_ap = A::fma(A::mul(k.c_edac, A::sub(pi, pj)), F, t_ap);
     ap.add(t_ap);
     T pres = A::mul(k.c_p, A::add(pi, pj));
-    if (k.use_av) {
-        // v_ij . r_ij < 0  <=>  v_ij . gradW > 0 (dW/dr < 0); phi_ij = (v_ij . gradW) F / |gradW|^2
-        T vvg = T(0), g2 = T(0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            vvg = A::fma(vv[a], g[a], vvg);
-            g2 = A::fma(g[a], g[a], g2);
-        }
-        if (vvg > T(0) && g2 > T(0)) pres = A::sub(pres, A::mul(k.c_av_m, A::mul(vvg, F)) / g2);   // -m Pi_ij
-    }
     const T cv = A::mul(k.c_visc, F);
+    // the terms that most runs do without (artificial viscosity, the steady-mode
+    // convection) sit behind one uniform test
+    if (k.rare) {
+        if (k.use_av) {
+            // v_ij . r_ij < 0  <=>  v_ij . gradW > 0 (dW/dr < 0); phi_ij = (v_ij . gradW) F / |gradW|^2
+            T vvg = T(0), g2 = T(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                vvg = A::fma(vv[a], g[a], vvg);
+                g2 = A::fma(g[a], g[a], g2);
+            }
+            if (vvg > T(0) && g2 > T(0)) pres = A::sub(pres, A::mul(k.c_av_m, A::mul(vvg, F)) / g2);   // -m Pi_ij
+        }
+        if (k.steady) {
+            // convection of Eq. (mom-steady): -(V_i m_i/rho_i + V_j m_j/rho_j) (V_i . gradW_ij),
+            // V_j the divergence-side velocity (prescribed for a wall)
+            T vg = T(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) vg = A::fma(vi[a], g[a], vg);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                Fi[a].add(A::sub(A::fma(cv, vv[a], A::mul(-pres, g[a])),
+                                 A::mul(A::mul(k.vol, A::add(vi[a], vj_div[a])), vg)));
+            return;
+        }
+    }
 #pragma unroll
     for (int a = 0; a < D; ++a) Fi[a].add(A::fma(cv, vv[a], A::mul(-pres, g[a])));
 }

@@ -635,7 +635,17 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
     for (int a = 0; a < D; ++a) Fv[a] = __dadd_rn((double)(T)Fa[a].value(), P.g[a]);
     B.ap_b[s] = apv;
     for (int a = 0; a < D; ++a) B.f_b[(size_t)a * n + s] = Fv[a];
-    if (PRED) {
+    if (PRED && P.steady) {
+        // steady mode: the iteration starts from the state itself, the particles
+        // stay, and the source is -g (the loop forms F + g - 0)
+        for (int a = 0; a < D; ++a) {
+            const size_t q = (size_t)a * n + s;
+            B.xp_b[q] = B.x_b[q];
+            B.v0_b[q] = B.vn_b[q];
+            B.s_b[q] = -P.g[a];
+        }
+        B.ph0_b[s] = __fma_rn(0.5 * P.dtau, apv, B.pn_b[s]);
+    } else if (PRED) {
         for (int a = 0; a < D; ++a) {
             const size_t q = (size_t)a * n + s;
             // explicit roundings: the same bits in every kernel variant

@@ -173,6 +173,69 @@ def test_shifting_matches_oracle(case, nsteps, prec):
     sim.close()
 
 
+STEADY_CASES = {
+    "couette": lambda: synth.couette2d(14, re=5.0),
+    "cavity": lambda: synth.cavity2d(18, re=100.0),
+    # a viscous vortex (cell Reynolds number U h / nu ~ 0.2): the steady iteration's
+    # explicit central convection is unstable at cell Reynolds numbers well above 2
+    "tgv2d_viscous": lambda: synth.tgv2d(30, re=5.0, seed=3),
+}
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case", sorted(STEADY_CASES))
+@pytest.mark.parametrize("fixed", [300, 0])
+def test_steady_mode_matches_oracle(case, prec, fixed):
+    """Steady-state mode (Sec. 2.4, Eq. mom-steady): each step is one
+    pseudo-time solve at fixed positions, no BDF2 and no EDAC term, with the
+    convection term. FP64 within 1e-10 of the oracle's steady mode with the
+    same iteration counts (fixed count, and the stop rules), FP32C velocities
+    within 1e-4; the particles never move."""
+    d = STEADY_CASES[case]()
+    nf = d["nf"]
+    over = dict(steady=1, fixed_iters=fixed) if fixed else dict(steady=1, max_iter=400)
+    sim, orc, out = run_pair(d, 2, precision=prec, **over)
+    st, rec, x, v, p = out[-1]
+    assert np.array_equal(x, d["x"][:nf])
+    tol = 1e-10 if prec == dt.DTSPH_FP64 else 1e-4
+    if prec == dt.DTSPH_FP64:
+        assert [o[0]["iters"] for o in out] == [o[1]["iters"] for o in out]
+        assert rel(p, orc.p) < tol or np.max(np.abs(orc.p)) < 1e-12
+    assert rel(v, orc.v) < tol
+    sim.close()
+
+
+def test_steady_couette_from_rest_on_gpu():
+    """The steady iteration drives plane Couette flow from rest to u = U y."""
+    d = synth.couette2d(16, re=5.0)
+    d["v"][:] = 0.0
+    d["v_prev"][:] = 0.0
+    sim = make_sim(d, precision=dt.DTSPH_FP32C, graph=2, steady=1, fixed_iters=4000)
+    sim.step(1)
+    nf = d["nf"]
+    assert np.max(np.abs(sim.v[:, 0] - d["x"][:nf, 1])) < 2e-3
+    assert np.max(np.abs(sim.v[:, 1])) < 1e-5
+    sim.close()
+
+
+def test_steady_same_bits_in_every_graph_mode():
+    d = STEADY_CASES["cavity"]()
+    runs = []
+    for graph in (0, 1, 2):
+        sim = make_sim(d, precision=dt.DTSPH_FP32C, graph=graph, lanes=1, steady=1, fixed_iters=50)
+        sim.step(2)
+        runs.append((sim.v, sim.p, sim.stats()))
+        sim.close()
+    for r in runs[1:]:
+        assert np.array_equal(r[0], runs[0][0]) and np.array_equal(r[1], runs[0][1]) and r[2] == runs[0][2]
+
+
+def test_steady_with_shifting_is_rejected():
+    d = STEADY_CASES["couette"]()
+    with pytest.raises(dt.DtsphError):
+        make_sim(d, steady=1, shifting=1)
+
+
 def test_shifting_same_bits_in_every_graph_mode():
     d = CASES["tgv2d_jitter"]()
     runs = []
