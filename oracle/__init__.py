@@ -51,6 +51,8 @@ class OrcParams(C.Structure):
         ("use_bruteforce", C.c_int32),
         ("shifting", C.c_int32),
         ("steady", C.c_int32),
+        ("free_surface", C.c_int32),
+        ("pad_", C.c_int32),
     ]
 
 
@@ -107,7 +109,7 @@ def lib():
 _DEFAULTS = dict(
     periodic=(0, 0, 0), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), rho0=1.0, beta=10.0, v_ref=1.0,
     eta=0.01, alpha=0.0, g=(0.0, 0.0, 0.0), eps=1e-3, stag_tol=0.05, stag_window=4, max_iter=1000,
-    edac=1, edac_h2_literal=0, fixed_iters=0, use_bruteforce=0, shifting=0, steady=0,
+    edac=1, edac_h2_literal=0, fixed_iters=0, use_bruteforce=0, shifting=0, steady=0, free_surface=0,
 )
 
 
@@ -127,7 +129,7 @@ def make_params(cfg: dict, **over) -> OrcParams:
     for k in ("h", "m", "rho0", "beta", "v_ref", "nu", "dt", "eta", "alpha", "eps", "stag_tol"):
         setattr(P, k, float(d[k]))
     for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "use_bruteforce", "shifting",
-              "steady"):
+              "steady", "free_surface"):
         setattr(P, k, int(d[k]))
     return P
 

@@ -29,7 +29,9 @@
  *                        form of Sec. 2.2; convergence test Eq. (conv) with the
  *                        stagnation and iteration-cap rules of Sec. 3.4; position
  *                        update Eq. (r-update); optional shifting Eqs. (shift,
- *                        shift-deltar, shift-correct) of Sec. 3.5. Steady mode
+ *                        shift-deltar, shift-correct) of Sec. 3.5 (free-surface
+ *                        particles not shifted in free-surface runs, where the
+ *                        wall pressure is also kept >= 0, Sec. 3.2). Steady mode
  *                        (Sec. 2.4 "Steady state solutions", Eq. mom-steady):
  *                        particles fixed, no BDF2 term, no EDAC term, convection
  *                        term added, the pseudo-time loop as above.
@@ -80,6 +82,9 @@ typedef struct {
     int32_t use_bruteforce;   /* 1: O(N^2) neighbour search instead of cells */
     int32_t shifting;         /* 1: particle shifting after the real step */
     int32_t steady;           /* 1: steady-state mode (Sec. 2.4, Eq. mom-steady) */
+    int32_t free_surface;     /* 1: free-surface run: wall pressure kept >= 0 (Sec. 3.2),
+                                 free-surface particles not shifted (Sec. 3.5) */
+    int32_t pad_;
 } orc_params;
 
 typedef struct {
@@ -354,6 +359,8 @@ static void wall_values(const orc_params *P, int64_t nf, int64_t nw, const doubl
         }
         if (sw > 0.0) {
             pw[w] = (sp + sg) / sw;
+            /* free-surface runs keep the wall pressure positive (Sec. 3.2) */
+            if (P->free_surface && pw[w] < 0.0) pw[w] = 0.0;
             for (int a = 0; a < dim; ++a) vghost[w * dim + a] = 2.0 * vw[w * dim + a] - sv[a] / sw;
         } else {
             pw[w] = 0.0;
@@ -501,14 +508,16 @@ static void shift(const orc_params *P, int64_t nf, double *x, double *v, double 
     if (!dr || !gv || !gp) { free(dr); free(gv); free(gp); return; }
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nf; ++i) {
+        double divr = 0.0;    /* div r_i = -sum_j V_j r_ij . gradW_ij, walls included */
         for (int64_t e = L->start[i]; e < L->start[i + 1]; ++e) {
             int64_t j = L->idx[e];
-            if (j >= nf) continue;
             double d[3];
             separation(P, x + i * dim, x + j * dim, d);
             double r = sqrt(norm2(d, dim));
             double dwdr = orc_dwdr(r, h, dim);
             double W = orc_w(r, h, dim);
+            if (r > 0.0) divr = divr - vol * dwdr * r;     /* r_ij . gradW_ij = dW/dr r */
+            if (j >= nf) continue;
             for (int a = 0; a < dim; ++a) {
                 double gw = r > 0.0 ? dwdr * d[a] / r : 0.0;
                 dr[i * dim + a] = dr[i * dim + a] + vol * (1.0 + W / wdx) * gw;
@@ -517,7 +526,9 @@ static void shift(const orc_params *P, int64_t nf, double *x, double *v, double 
                     gv[(i * dim + b) * dim + a] = gv[(i * dim + b) * dim + a] + vol * (v[j * dim + b] - v[i * dim + b]) * gw;
             }
         }
-        for (int a = 0; a < dim; ++a) dr[i * dim + a] = -0.5 * h * h * dr[i * dim + a];
+        /* Lind et al.'s free-surface test (Sec. 3.5): div r < d - 1/2 -> not shifted */
+        const int surface = P->free_surface && divr < (double)dim - 0.5;
+        for (int a = 0; a < dim; ++a) dr[i * dim + a] = surface ? 0.0 : -0.5 * h * h * dr[i * dim + a];
     }
     for (int64_t i = 0; i < nf; ++i) {
         double dp = 0.0;

@@ -146,6 +146,37 @@ def couette2d(n: int = 30, re: float = 10.0, U: float = 1.0, layers: int = 3, **
     return dict(cfg=cfg, x=np.concatenate([xf, xw]), v=v, p=np.zeros(N), v_prev=v.copy(), vw=vw, nf=N)
 
 
+def dambreak2d(n: int = 20, width: float = 1.0, height: float = 2.0, tank_w: float = 4.0, tank_h: float = 2.5,
+               layers: int = 3, g: float = 9.81, jitter: float = 0.0, seed: int = 1904, **kw) -> dict:
+    """A water column at rest in a tank (a dam-break-like block with a free
+    surface): n x (n height/width) fluid particles on the lattice of
+    [0, width] x [0, height], spacing dx = width / n, optional jitter of each
+    coordinate by jitter*dx*U[-1, 1); `layers` rows of still wall particles
+    under the floor (y < 0) and outside both side walls (x < 0, x > tank_w) up to
+    tank_h; gravity (0, -g); v_ref = sqrt(2 g height); V = 0, p = 0."""
+    dx = width / n
+    U = math.sqrt(2.0 * g * height)
+    cfg = base_params(2, dx, U, 0.0, **kw)
+    cfg.update(periodic=(0, 0, 0), lo=(-layers * dx, -layers * dx, 0.0), hi=(tank_w + layers * dx, tank_h, 1.0),
+               g=(0.0, -g, 0.0), workload="dambreak2d", n_side=n)
+    ny = int(round(height / dx))
+    N = n * ny
+    i = np.arange(N) % n
+    j = np.arange(N) // n
+    r = uniform01(seed, 2 * N)
+    xf = np.stack([(i + 0.5) * dx + jitter * dx * (2.0 * r[:N] - 1.0),
+                   (j + 0.5) * dx + jitter * dx * (2.0 * r[N:] - 1.0)], 1)
+    nxw = int(round(tank_w / dx))
+    nyw = int(round(tank_h / dx))
+    ii = np.arange(-layers, nxw + layers)
+    jj = np.arange(-layers, nyw)
+    II, JJ = np.meshgrid(ii, jj)
+    wall = (II < 0) | (II >= nxw) | (JJ < 0)
+    xw = np.stack([(II[wall] + 0.5) * dx, (JJ[wall] + 0.5) * dx], 1)
+    return dict(cfg=cfg, x=np.concatenate([xf, xw]), v=np.zeros((N, 2)), p=np.zeros(N),
+                v_prev=np.zeros((N, 2)), vw=np.zeros_like(xw), nf=N)
+
+
 def tgv3d(n: int = 128, re: float = 1600.0, U: float = 1.0, jitter: float = 0.05, seed: int = 1904, **kw) -> dict:
     """3D Taylor-Green vortex on [0, 2 pi)^3 with n^3 particles: u = U sin x cos y
     cos z, v = -U cos x sin y cos z, w = 0, p = rho0 U^2/16 (cos 2x + cos 2y)(cos 2z

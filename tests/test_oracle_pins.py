@@ -505,3 +505,44 @@ def test_steady_couette_from_rest_converges_to_the_linear_profile():
     un = oracle.State(d["cfg"], d["x"], z, d["p"], z, vw=d["vw"], nf=nf, fixed_iters=4000)
     un.step(1)
     assert np.max(np.abs(un.v[:, 0] - y)) > 0.3
+
+
+# ------------------------------------------------------------ free surfaces
+
+def test_free_surface_wall_pressure_is_kept_positive():
+    """Free-surface runs keep the Adami wall pressure >= 0 (Sec. 3.2, after
+    Hughes and Graham): on a water column at rest under gravity the side-wall
+    particles above the water line extrapolate negative pressures, which the
+    clamp lifts to exactly zero; every other wall value is unchanged."""
+    d = synth.dambreak2d(12)
+    nf = d["nf"]
+    _, _, pw0, _ = oracle.rates(d["cfg"], d["x"], d["v"], d["p"], d["vw"], nf)
+    _, _, pw1, _ = oracle.rates(d["cfg"], d["x"], d["v"], d["p"], d["vw"], nf, free_surface=1)
+    assert pw0.min() < -0.1
+    assert np.array_equal(pw1, np.maximum(pw0, 0.0))
+
+
+def test_free_surface_particles_are_not_shifted():
+    """Lind et al.'s test (Sec. 3.5): a fluid particle with div r < d - 1/2 is on
+    the free surface and is not shifted. A jittered column at rest without
+    gravity: with the test on, the top row and the column's open side stay
+    exactly where they are, and the interior and the row on the floor (whose
+    support the wall particles fill: div r counts them) are shifted; with it
+    off, every particle moves."""
+    dj = synth.dambreak2d(12, jitter=0.2, seed=4)
+    nf = dj["nf"]
+    dx = dj["cfg"]["dx"]
+    cfg = dict(dj["cfg"], g=(0.0, 0.0, 0.0))
+    x0 = dj["x"][:nf]
+    top = x0[:, 1] > 2.0 - dx
+    side = (x0[:, 0] > 1.0 - dx) & (x0[:, 1] > 3 * dx)
+    inner = (x0[:, 1] < 2.0 - 4 * dx) & (x0[:, 0] < 1.0 - 4 * dx) & (x0[:, 0] > 4 * dx) & (x0[:, 1] > 4 * dx)
+    floor = (x0[:, 1] < dx) & (x0[:, 0] < 1.0 - 4 * dx) & (x0[:, 0] > 4 * dx)
+    moved = {}
+    for fs in (0, 1):
+        st = oracle.State(cfg, dj["x"], dj["v"], dj["p"], dj["v_prev"], vw=dj["vw"], nf=nf, shifting=1,
+                          free_surface=fs)
+        st.step(1)
+        moved[fs] = np.linalg.norm(st.x[:nf] - x0, axis=1)
+    assert np.all(moved[1][top | side] == 0.0)
+    assert np.all(moved[1][inner] > 0.0) and np.all(moved[1][floor] > 0.0) and np.all(moved[0] > 0.0)
