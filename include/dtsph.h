@@ -101,6 +101,11 @@ typedef struct {
                                  V_j m/rho0) gradW_ij in the momentum rate; dt only scales the
                                  residuals and sets dtau = dt / beta. Shifting must be off.
                                  Instances of a batch share it. */
+    int32_t free_surface;     /* 1: free-surface run: the Adami wall pressure is kept >= 0
+                                 (Sec. 3.2), and with shifting a fluid particle with
+                                 div r_i = -sum_j V_j r_ij . gradW_ij < dim - 1/2 (fluid and wall
+                                 neighbours; Lind et al.'s test, Sec. 3.5) is not shifted.
+                                 Instances of a batch share it. */
 } dtsph_params;
 
 typedef struct {

@@ -184,6 +184,7 @@ void setup_phys(const dtsph_params &p, Phys &P)
     P.use_av = p.alpha != 0.0;
     P.vol = p.m / p.rho0;
     P.steady = p.steady;
+    P.free_surface = p.free_surface;
     if (p.steady) {
         // Eq. (mom-steady): dV/dtau is the momentum rate itself (no BDF2 term);
         // the pressure rate has no EDAC term
@@ -216,6 +217,7 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
     if (p->shifting != 0 && p->shifting != 1) return fail(c, DTSPH_E_ARG, "shifting must be 0 or 1");
     if (p->steady != 0 && p->steady != 1) return fail(c, DTSPH_E_ARG, "steady must be 0 or 1");
     if (p->steady && p->shifting) return fail(c, DTSPH_E_ARG, "the steady mode keeps the particles fixed: no shifting");
+    if (p->free_surface != 0 && p->free_surface != 1) return fail(c, DTSPH_E_ARG, "free_surface must be 0 or 1");
     return DTSPH_OK;
 }
 
@@ -784,8 +786,9 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
         if (!r && (params[i].dim != params[0].dim || params[i].precision != params[0].precision ||
                    params[i].graph != params[0].graph || params[i].lanes != params[0].lanes ||
                    params[i].stages != params[0].stages || params[i].shifting != params[0].shifting ||
-                   params[i].steady != params[0].steady))
-            r = fail(c, DTSPH_E_ARG, "instances must share dim, precision, graph, lanes, stages, shifting and steady");
+                   params[i].steady != params[0].steady || params[i].free_surface != params[0].free_surface))
+            r = fail(c, DTSPH_E_ARG,
+                     "instances must share dim, precision, graph, lanes, stages, shifting, steady and free_surface");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;

@@ -75,7 +75,7 @@ struct Phys {
     int edac, use_av;
     int steady;          // steady-state mode: kappa = 1, no 3/(2dt) term, source -g,
                          // convection term, particles fixed
-    int pad_s;
+    int free_surface;    // wall pressure kept >= 0; free-surface particles not shifted
     double vol;          // m / rho0 (convection term)
 };
 

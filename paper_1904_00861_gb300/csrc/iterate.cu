@@ -107,6 +107,7 @@ __device__ __forceinline__ void wall_slot(const Buffers &B, int s, int cur)
         gv[a] = 2.0 * vw - (sw > 0 ? sv[a] / sw : 0.0);
     }
     double pw = sw > 0 ? sp / sw : 0.0;
+    if (pw < 0.0 && B.phys[B.inst_of[s]].free_surface) pw = 0.0;   // free-surface runs (Sec. 3.2)
     if (F32) B.nb32[cur][s] = make_float4((float)gv[0], (float)gv[1], (float)gv[2], (float)pw);
     else B.nb64[cur][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
 }

@@ -560,7 +560,8 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
         const double vw = a < D ? B.vn_b[(size_t)a * B.n + s] : 0.0;
         gv[a] = 2.0 * vw - (sw > 0 ? acc[3 + a] / sw : 0.0);
     }
-    const double pw = sw > 0 ? (acc[1] + acc[2]) / sw : 0.0;
+    double pw = sw > 0 ? (acc[1] + acc[2]) / sw : 0.0;
+    if (pw < 0.0 && P.free_surface) pw = 0.0;     // free-surface runs keep it >= 0 (Sec. 3.2)
     if (F32) B.nb32[1][s] = make_float4((float)gv[0], (float)gv[1], (float)gv[2], (float)pw);
     else B.nb64[1][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
 }
@@ -745,7 +746,8 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
 // ---------------------------------------------------------------- shifting
 
 // Particle shifting after the real step (Sec. 3.5), in order B at r^{n+1}, one
-// lane per slot, over fluid neighbours only:
+// lane per slot, over fluid neighbours only (free-surface runs: particles with
+// div r_i < dim - 1/2, fluid and wall neighbours counted, stay where they are):
 //   dr_i = -(h^2/2) sum_j V_j (1 + W_ij / W(h)) gradW_ij          Eq. (shift-deltar)
 //   f_i <- f_i + (grad f)_i . dr_i, (grad f)_i = sum_j V_j (f_j - f_i) gradW_ij
 //                                                      for f = p, V   Eq. (shift-correct)
@@ -776,13 +778,13 @@ __global__ void __launch_bounds__(kBlock) k_shift(Buffers B)
     const T sigma = (T)(P.sig_h * P.h);
     const T w_h = sigma * quintic_w<T>(T(1));
     Acc dr[3], gp[3], gv[3][3];
+    double divr = 0.0;            // div r_i = -sum_j V_j r_ij . gradW_ij, walls included
     const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
     const int cnt = B.pcount[s];
     for (int k = 0; k < cnt; ++k) {
         const size_t e = base + (size_t)k * kWarp;
         const uint32_t jb = B.pj[e];
-        if (jb & kWallBit) continue;                      // fluid neighbours only
-        const int j = (int)jb;
+        const int j = (int)(jb & ~kWallBit);
         int dx, dy, dz;
         decode_shift(B.pcode[e], dx, dy, dz);
         T d[3], r2;
@@ -790,6 +792,9 @@ __global__ void __launch_bounds__(kBlock) k_shift(Buffers B)
         const T r = sqrt(r2);
         const T q = r * (T)P.inv_h;
         const T a = r > T(0) ? (T)P.sig_h * quintic_dwdq<T>(q) / r : T(0);
+        divr -= (double)(vol * a * r2);                   // r_ij . gradW_ij = (dW/dr / r) r^2
+        if (jb & kWallBit) continue;                      // fluid neighbours only from here
+
         const T fdr = vol * (T(1) + sigma * quintic_w<T>(q) / w_h);
         const auto qj = nb[j];
         const T vj[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
@@ -803,7 +808,9 @@ __global__ void __launch_bounds__(kBlock) k_shift(Buffers B)
             for (int b2 = 0; b2 < D; ++b2) gv[b2][c].add(vol * (vj[b2] - vi[b2]) * gw);
         }
     }
-    const double dmul = -0.5 * P.h * P.h;
+    // a free-surface particle (Lind et al.'s test, Sec. 3.5) is not shifted
+    const bool surface = P.free_surface && divr < (double)D - 0.5;
+    const double dmul = surface ? 0.0 : -0.5 * P.h * P.h;
     double drv[3] = {0, 0, 0};
     for (int c = 0; c < D; ++c) drv[c] = dmul * (double)(T)dr[c].value();
     const int o = B.perm[s];

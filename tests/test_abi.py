@@ -66,5 +66,5 @@ def test_struct_layouts_match_header():
     """ctypes mirrors of the C structs have the C sizes (checked by offsets)."""
     P = lib_pkg.dtsph_params
     assert P.lo.offset == 24 and P.h.offset == 72
-    assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 11 + 4   # int32 fields, tail padding
+    assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 12
     assert ctypes.sizeof(lib_pkg.dtsph_step_stats) == 24

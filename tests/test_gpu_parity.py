@@ -173,6 +173,42 @@ def test_shifting_matches_oracle(case, nsteps, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case", ["tgv2d_jitter", "cavity"])
+def test_artificial_viscosity_matches_oracle(case, prec):
+    """Monaghan's artificial viscosity (Eqs. mom-av, av-phiij) on: FP64 within
+    1e-10 of the oracle with the same iteration counts, FP32C within 1e-4."""
+    d = CASES[case]()
+    sim, orc, out = run_pair(d, 3, precision=prec, alpha=0.1)
+    st, rec, x, v, p = out[-1]
+    if prec == dt.DTSPH_FP64:
+        assert [o[0]["iters"] for o in out] == [o[1]["iters"] for o in out]
+        assert rel(v, orc.v) < 1e-10 and rel(p, orc.p) < 1e-10
+    else:
+        assert rel(v, orc.v) < 1e-4
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("shift", [0, 1])
+def test_dambreak_free_surface_matches_oracle(shift, prec):
+    """A water column in a tank under gravity with a free surface: artificial
+    viscosity, wall pressure kept >= 0, and (shift = 1) shifting that leaves
+    free-surface particles in place. FP64 within 1e-10 of the oracle with the
+    same iteration counts, FP32C within 1e-4."""
+    d = synth.dambreak2d(12, jitter=0.1, seed=2)
+    nf = d["nf"]
+    sim, orc, out = run_pair(d, 3, precision=prec, alpha=0.1, free_surface=1, shifting=shift)
+    st, rec, x, v, p = out[-1]
+    tol = 1e-10 if prec == dt.DTSPH_FP64 else 1e-4
+    if prec == dt.DTSPH_FP64:
+        assert [o[0]["iters"] for o in out] == [o[1]["iters"] for o in out]
+        assert rel(p, orc.p) < tol
+    assert np.max(np.abs(x - orc.x[:nf])) < tol * np.max(np.abs(orc.x))
+    assert rel(v, orc.v) < tol
+    sim.close()
+
+
 STEADY_CASES = {
     "couette": lambda: synth.couette2d(14, re=5.0),
     "cavity": lambda: synth.cavity2d(18, re=100.0),
