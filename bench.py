@@ -42,7 +42,9 @@ def make_workload(name: str, n_side: int, re: float):
     """Synthetic input and its config record. tgv2d (default, 200 x 200) is the
     workload the metric is quoted on; tgv3d (128^3), cavity (200 x 200 + walls)
     and batch (64 Taylor-Green instances of 32^2..256^2 particles, Re 100..1000)
-    are the other single-GPU configurations."""
+    are the other single-GPU configurations; dambreak (a 200 x 400 water column
+    in a tank, free surface, artificial viscosity 0.1, shifting, eps 1e-4, as
+    in the 2D dam break of Sec. 4) measures the free-surface runs."""
     if name == "tgv2d":
         n = n_side or 200
         d = synth.tgv2d(n, re=re or 100.0)
@@ -61,9 +63,18 @@ def make_workload(name: str, n_side: int, re: float):
         d = synth.batch(count)
         cfg = dict(workload=f"batch-{count}x-tgv2d", instances=count, particles=int(sum(x["nf"] for x in d)),
                    sides="U{32..256} seed 861", re="10^U[2,3)", dims=2)
+    elif name == "dambreak":
+        n = n_side or 200
+        d = synth.dambreak2d(n, eps=1e-4)
+        d["cfg"].update(alpha=0.1, free_surface=1, shifting=1)
+        cfg = dict(workload=f"dambreak2d-{n}x{2 * n}", particles=d["nf"], wall_particles=len(d["x"]) - d["nf"],
+                   column="1 m x 2 m at rest, p = 0, gravity 9.81", tank="4 m x 2.5 m, 3 wall layers", dims=2,
+                   alpha=0.1, free_surface="on", shifting="on")
     else:
         raise ValueError(name)
     cfg.update(dt="0.25h", beta=10, eps=1e-3, real_steps_per_bench_step=1)
+    if name == "dambreak":
+        cfg.update(dt="0.25h/sqrt(2 g H)", eps=1e-4)
     return d, cfg
 
 
@@ -138,7 +149,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tgv2d", choices=["tgv2d", "tgv3d", "cavity", "batch"])
+    ap.add_argument("--workload", default="tgv2d", choices=["tgv2d", "tgv3d", "cavity", "batch", "dambreak"])
     ap.add_argument("--n-side", type=int, default=0,
                     help="particles per side, or instances for batch (0: the workload's default)")
     ap.add_argument("--re", type=float, default=0.0, help="Reynolds number (0: the workload's default)")
