@@ -52,7 +52,7 @@ class OrcParams(C.Structure):
         ("shifting", C.c_int32),
         ("steady", C.c_int32),
         ("free_surface", C.c_int32),
-        ("pad_", C.c_int32),
+        ("moving", C.c_int32),
     ]
 
 
@@ -92,10 +92,12 @@ def lib():
         L.orc_neighbors.argtypes = [P, C.c_int64, dp, i64p, i64p, C.c_int64]
         L.orc_rates.restype = C.c_int
         L.orc_rates.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_rates_vt.restype = C.c_int
+        L.orc_rates_vt.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_stop_reason.restype = C.c_int
         L.orc_stop_reason.argtypes = [P, C.c_int32, dp, dp]
         L.orc_step.restype = C.c_int
-        L.orc_step.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.POINTER(OrcStats), dp, dp]
+        L.orc_step.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.POINTER(OrcStats), dp, dp, dp]
         L.orc_run.restype = C.c_int
         L.orc_run.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.c_int32, C.POINTER(OrcStats)]
         L.orc_num_threads.restype = C.c_int
@@ -110,6 +112,7 @@ _DEFAULTS = dict(
     periodic=(0, 0, 0), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), rho0=1.0, beta=10.0, v_ref=1.0,
     eta=0.01, alpha=0.0, g=(0.0, 0.0, 0.0), eps=1e-3, stag_tol=0.05, stag_window=4, max_iter=1000,
     edac=1, edac_h2_literal=0, fixed_iters=0, use_bruteforce=0, shifting=0, steady=0, free_surface=0,
+    moving=0,
 )
 
 
@@ -129,7 +132,7 @@ def make_params(cfg: dict, **over) -> OrcParams:
     for k in ("h", "m", "rho0", "beta", "v_ref", "nu", "dt", "eta", "alpha", "eps", "stag_tol"):
         setattr(P, k, float(d[k]))
     for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "use_bruteforce", "shifting",
-              "steady", "free_surface"):
+              "steady", "free_surface", "moving"):
         setattr(P, k, int(d[k]))
     return P
 
@@ -176,8 +179,9 @@ def neighbors(cfg: dict, x, **over):
     return start, idx[:tot].copy()
 
 
-def rates(cfg: dict, x, v, p, vw=None, nf=None, **over):
-    """dp/dtau and F (the momentum right-hand side) at a given state.
+def rates(cfg: dict, x, v, p, vw=None, nf=None, vt=None, **over):
+    """dp/dtau and F (the momentum right-hand side) at a given state, with the
+    advective terms of a pseudo-velocity vt (fluid only) if given.
 
     x holds fluid then wall positions; v, p are fluid only. Returns (ap, F, pw, vghost)."""
     P = make_params(cfg, **over)
@@ -192,7 +196,9 @@ def rates(cfg: dict, x, v, p, vw=None, nf=None, **over):
     F = np.zeros((max(nf, 1), dim))
     pw = np.zeros(max(nw, 1))
     vg = np.zeros((max(nw, 1), dim))
-    if lib().orc_rates(C.byref(P), nf, nw, _dp(x), _dp(v), _dp(p), _dp(vw), _dp(ap), _dp(F), _dp(pw), _dp(vg)):
+    vt = None if vt is None else _f64(vt)
+    if lib().orc_rates_vt(C.byref(P), nf, nw, _dp(x), _dp(v), _dp(p), _dp(vw), _dp(vt) if vt is not None else None,
+                          _dp(ap), _dp(F), _dp(pw), _dp(vg)):
         raise MemoryError("oracle rates failed")
     return ap[:nf], F[:nf], pw[:nw], vg[:nw]
 
@@ -223,17 +229,20 @@ class State:
         self.stats = []
 
     def step(self, nsteps: int = 1, hist: bool = False, keep_x0: bool = False):
-        """Advance nsteps real steps (Algorithm 2). Returns the per-step stats
-        (with the residual history and the frozen positions r^0 if asked)."""
+        """Advance nsteps real steps (Algorithm 2, or Algorithm 1 with moving =
+        1 or 2). Returns the per-step stats (with the residual history, the
+        positions r^0 after the predictor and the pseudo-time positions r^K at
+        the end of the loop if asked)."""
         out = []
         cap = max(1, self.P.fixed_iters if self.P.fixed_iters > 0 else self.P.max_iter)
         for _ in range(nsteps):
             st = OrcStats()
             hbuf = np.zeros(2 * cap) if hist else None
             x0 = np.zeros_like(self.x) if keep_x0 else None
+            xk = np.zeros_like(self.x) if keep_x0 else None
             rc = lib().orc_step(C.byref(self.P), self.nf, self.nw, _dp(self.x), _dp(self.v), _dp(self.v_prev),
                                 _dp(self.p), _dp(self.vw), C.byref(st), _dp(hbuf) if hist else None,
-                                _dp(x0) if keep_x0 else None)
+                                _dp(x0) if keep_x0 else None, _dp(xk) if keep_x0 else None)
             if rc:
                 raise MemoryError("oracle step failed")
             rec = dict(iters=st.iters, reason=st.reason, rp=st.rp, rv=st.rv)
@@ -242,6 +251,7 @@ class State:
                 rec["hist_v"] = hbuf[cap: cap + st.iters].copy()
             if keep_x0:
                 rec["x0"] = x0
+                rec["xk"] = xk
             out.append(rec)
             self.t += self.P.dt
         self.stats.extend(out)

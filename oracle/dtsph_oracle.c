@@ -35,6 +35,13 @@
  *                        (Sec. 2.4 "Steady state solutions", Eq. mom-steady):
  *                        particles fixed, no BDF2 term, no EDAC term, convection
  *                        term added, the pseudo-time loop as above.
+ *                        Moving mode (Algorithm 1, Sec. 2.1 and 3.1 "Moving
+ *                        particles in pseudo-time"): the pressure rate of
+ *                        Eq. (dp-dtau) and the momentum rate of Eq.
+ *                        (discrete_ME) with the pseudo-velocity V~; positions
+ *                        staged by Eqs. (rkstar, rkp1), V~ by Eq. (vtilde);
+ *                        neighbours either kept from r^0 or rebuilt at every
+ *                        pass (the two advected variants of Sec. 4.1's table).
  *
  * Readings taken where the paper is silent or garbled (all listed in the design
  * notes): the EDAC diffusion denominator is r^2 + eta h^2 (edac_h2_literal = 1
@@ -84,7 +91,9 @@ typedef struct {
     int32_t steady;           /* 1: steady-state mode (Sec. 2.4, Eq. mom-steady) */
     int32_t free_surface;     /* 1: free-surface run: wall pressure kept >= 0 (Sec. 3.2),
                                  free-surface particles not shifted (Sec. 3.5) */
-    int32_t pad_;
+    int32_t moving;           /* 0: particles fixed in pseudo-time (Algorithm 2); 1: moved
+                                 in pseudo-time (Algorithm 1) over the neighbour lists of
+                                 r^0; 2: moved, neighbours rebuilt at every pass */
 } orc_params;
 
 typedef struct {
@@ -377,10 +386,15 @@ static void wall_values(const orc_params *P, int64_t nf, int64_t nw, const doubl
  *  F_i       = -sum_j m_j (p_i/rho_i^2 + p_j/rho_j^2 + Pi_ij) gradW_ij
  *            + sum_j m_j 4 nu (gradW_ij . r_ij) / ((rho_i + rho_j)(r_ij^2 + eta h^2)) V_ij + g
  * Wall neighbours supply p_w, their prescribed velocity in the divergence term,
- * and their ghost velocity in the viscous and artificial-viscosity terms. */
+ * and their ghost velocity in the viscous and artificial-viscosity terms.
+ * With a pseudo-velocity vt (particles moving in pseudo-time), the advective
+ * terms of Eqs. (dp-dtau) and (discrete_ME) are added:
+ *  dp_i/dtau += V~_i . sum_j m_j (p_i/rho_i^2 + p_j/rho_j^2) gradW_ij
+ *  F_i       += sum_j (V_i m_i/rho_i + V_j m_j/rho_j) (V~_i . gradW_ij)
+ * (a wall neighbour supplying its prescribed velocity as V_j). */
 static void rates(const orc_params *P, int64_t nf, const double *x, const double *v,
                   const double *p, const double *vw, const double *pw, const double *vghost,
-                  const nlist *L, double *ap, double *F)
+                  const double *vt, const nlist *L, double *ap, double *F)
 {
     int dim = P->dim;
     double h = P->h, m = P->m, rho = P->rho0;
@@ -390,7 +404,9 @@ static void rates(const orc_params *P, int64_t nf, const double *x, const double
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nf; ++i) {
         double api = 0.0, Fi[3] = {0, 0, 0};
+        double gp[3] = {0, 0, 0};    /* sum_j m_j (p_i/rho_i^2 + p_j/rho_j^2) gradW_ij */
         const double *vi = v + i * dim;
+        const double *vti = vt ? vt + i * dim : NULL;
         for (int64_t e = L->start[i]; e < L->start[i + 1]; ++e) {
             int64_t j = L->idx[e];
             double d[3];
@@ -435,6 +451,14 @@ static void rates(const orc_params *P, int64_t nf, const double *x, const double
             double visc = m * 4.0 * P->nu * rdotgw / ((rho + rho) * (r2 + P->eta * h * h));
             for (int a = 0; a < dim; ++a)
                 Fi[a] = Fi[a] - m * pres * gw[a] + visc * (vi[a] - vvis[a]);
+            if (vti) {
+                double tgw = 0.0;
+                for (int a = 0; a < dim; ++a) tgw = tgw + vti[a] * gw[a];
+                for (int a = 0; a < dim; ++a) {
+                    gp[a] = gp[a] + m * (p[i] / (rho * rho) + pj / (rho * rho)) * gw[a];
+                    Fi[a] = Fi[a] + (m / rho * vi[a] + m / rho * vdiv[a]) * tgw;
+                }
+            }
             if (P->steady) {
                 /* convection of Eq. (mom-steady): V_i . sum_j (V_i m_i/rho_i + V_j m_j/rho_j)
                    gradW_ij, the wall's prescribed velocity for a wall neighbour */
@@ -443,22 +467,32 @@ static void rates(const orc_params *P, int64_t nf, const double *x, const double
                 for (int a = 0; a < dim; ++a) Fi[a] = Fi[a] - (m / rho * vi[a] + m / rho * vdiv[a]) * vgw;
             }
         }
+        if (vti)
+            for (int a = 0; a < dim; ++a) api = api + vti[a] * gp[a];
         ap[i] = api;
         for (int a = 0; a < dim; ++a) F[i * dim + a] = Fi[a] + P->g[a];
     }
 }
 
-/* Exported for the tests: the two rates at a given state. pw and vghost (nw and
- * nw*dim entries) receive the wall values, if there are walls. */
-int orc_rates(const orc_params *P, int64_t nf, int64_t nw, const double *x, const double *v,
-              const double *p, const double *vw, double *ap, double *F, double *pw, double *vghost)
+/* Exported for the tests: the two rates at a given state, with the advective
+ * terms of a pseudo-velocity vt (nf*dim) if vt is not NULL. pw and vghost (nw
+ * and nw*dim entries) receive the wall values, if there are walls. */
+int orc_rates_vt(const orc_params *P, int64_t nf, int64_t nw, const double *x, const double *v,
+                 const double *p, const double *vw, const double *vt, double *ap, double *F, double *pw,
+                 double *vghost)
 {
     nlist L;
     if (build_neighbors(P, nf + nw, x, &L)) return -1;
     if (nw > 0) wall_values(P, nf, nw, x, v, p, vw, &L, pw, vghost);
-    rates(P, nf, x, v, p, vw, pw, vghost, &L, ap, F);
+    rates(P, nf, x, v, p, vw, pw, vghost, vt, &L, ap, F);
     nlist_free(&L);
     return 0;
+}
+
+int orc_rates(const orc_params *P, int64_t nf, int64_t nw, const double *x, const double *v,
+              const double *p, const double *vw, double *ap, double *F, double *pw, double *vghost)
+{
+    return orc_rates_vt(P, nf, nw, x, v, p, vw, NULL, ap, F, pw, vghost);
 }
 
 /* -------------------------------------------------------------- stop rules */
@@ -557,10 +591,12 @@ static void shift(const orc_params *P, int64_t nf, double *x, double *v, double 
  * vw:     nw*dim prescribed wall velocities
  * hist:   optional per-iteration residual log, 2*cap doubles (R_p then R_v),
  *         cap = fixed_iters if set, else max_iter
- * x0_out: optional (nf+nw)*dim copy of the frozen positions r^0
+ * x0_out: optional (nf+nw)*dim copy of the positions r^0 (after the predictor)
+ * xk_out: optional (nf+nw)*dim copy of the pseudo-time positions r^K at the end
+ *         of the loop (r^0 when the particles are fixed in pseudo-time)
  * Returns 0, or -1 on allocation failure. */
 int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, double *v_prev,
-             double *p, const double *vw, orc_stats *st, double *hist, double *x0_out)
+             double *p, const double *vw, orc_stats *st, double *hist, double *x0_out, double *xk_out)
 {
     int dim = P->dim;
     int64_t n = nf + nw;
@@ -583,14 +619,22 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
     double *vg = malloc((size_t)(nw ? nw : 1) * dim * sizeof(double));
     double *hp = malloc((size_t)cap * sizeof(double));
     double *hv = malloc((size_t)cap * sizeof(double));
+    /* moving in pseudo-time: positions r^k and r^{k+1/2} of every particle, V~ */
+    int moving = P->moving && !P->steady;
+    double *xk = malloc((size_t)n * dim * sizeof(double));
+    double *xh = malloc((size_t)n * dim * sizeof(double));
+    double *vt = malloc((nfd ? nfd : 1) * sizeof(double));
     nlist L;
     int rc = -1;
-    if (!x0 || !vk || !vk1 || !pk || !phalf || !ap || !ap_prev || !F || !pw || !vg || !hp || !hv) goto out;
+    if (!x0 || !vk || !vk1 || !pk || !phalf || !ap || !ap_prev || !F || !pw || !vg || !hp || !hv || !xk || !xh ||
+        !vt)
+        goto out;
 
-    /* rates at state n (Algorithm 2, before the predictor) */
+    /* rates at state n (Algorithms 1 and 2, before the predictor); with the
+       particles moving, V~ starts at 0, so these are the frozen rates */
     if (build_neighbors(P, n, x, &L)) goto out;
     if (nw > 0) wall_values(P, nf, nw, x, v, p, vw, &L, pw, vg);
-    rates(P, nf, x, v, p, vw, pw, vg, &L, ap_prev, F);
+    rates(P, nf, x, v, p, vw, pw, vg, NULL, &L, ap_prev, F);
     nlist_free(&L);
 
     /* predictor, Eqs. (v0, r0); p^0 = p^n. Steady mode: the particles stay and
@@ -610,16 +654,35 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
         pk[i] = p[i];
     }
 
-    /* pseudo-time iterations with the particles frozen at r^0 */
+    /* pseudo-time iterations: with the particles frozen at r^0 (Algorithm 2),
+       or moving from r^0 with V~^0 = 0 (Algorithm 1; walls stay) */
+    memcpy(xk, x0, (size_t)n * dim * sizeof(double));
+    memcpy(xh, x0, (size_t)n * dim * sizeof(double));
+    memset(vt, 0, (nfd ? nfd : 1) * sizeof(double));
     if (build_neighbors(P, n, x0, &L)) goto out;
     double kappa = 2.0 * dt / (2.0 * dt + 3.0 * dtau);
     int k = 0, reason = -1;
     while (reason < 0) {
-        /* Eq. (pkstar_frozen), with the rate of the previous pass */
+        if (moving) {
+            /* Eq. (rkstar): r^{k+1/2} = r^k + dtau/2 V~^k, wrapped onto the box */
+            for (int64_t i = 0; i < nf; ++i) {
+                for (int a = 0; a < dim; ++a) {
+                    size_t q = (size_t)i * dim + a;
+                    xh[q] = xk[q] + 0.5 * dtau * vt[q];
+                }
+                wrap(P, xh + i * dim);
+            }
+            if (P->moving == 2) {
+                /* neighbours updated at the moved positions */
+                nlist_free(&L);
+                if (build_neighbors(P, n, xh, &L)) goto out;
+            }
+        }
+        /* Eq. (pkstar_frozen) / (pkstar), with the rate of the previous pass */
         for (int64_t i = 0; i < nf; ++i) phalf[i] = pk[i] + 0.5 * dtau * ap_prev[i];
-        if (nw > 0) wall_values(P, nf, nw, x0, vk, phalf, vw, &L, pw, vg);
+        if (nw > 0) wall_values(P, nf, nw, xh, vk, phalf, vw, &L, pw, vg);
         /* all rates before any update (Jacobi) */
-        rates(P, nf, x0, vk, phalf, vw, pw, vg, &L, ap, F);
+        rates(P, nf, xh, vk, phalf, vw, pw, vg, moving ? vt : NULL, &L, ap, F);
         double sum_ap = 0.0, sum_av = 0.0;
         for (int64_t i = 0; i < nf; ++i) {
             double av2 = 0.0;
@@ -633,8 +696,12 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
                     double bdf = (3.0 * vk[q] - 4.0 * v[q] + v_prev[q]) / (2.0 * dt);
                     av = (F[q] - bdf) * kappa;
                 }
-                vk1[q] = vk[q] + dtau * av;                   /* Eq. (vkp1_frozen) */
+                vk1[q] = vk[q] + dtau * av;                   /* Eq. (vkp1_frozen) / (vkp1) */
                 av2 = av2 + av * av;
+                if (moving) {
+                    vt[q] = dt * av;                          /* Eq. (vtilde) */
+                    xk[q] = xh[q] + 0.5 * dtau * vt[q];       /* Eq. (rkp1) */
+                }
             }
             double pnew = phalf[i] + 0.5 * dtau * ap[i];      /* Eq. (pkp1_frozen) */
             sum_ap = sum_ap + fabs(ap[i]);
@@ -653,6 +720,7 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
     }
     nlist_free(&L);
     if (x0_out) memcpy(x0_out, x0, (size_t)n * dim * sizeof(double));
+    if (xk_out) memcpy(xk_out, xk, (size_t)n * dim * sizeof(double));
     st->iters = k;
     st->reason = reason;
     st->rp = hp[k - 1];
@@ -678,7 +746,7 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
     rc = 0;
 out:
     free(x0); free(vk); free(vk1); free(pk); free(phalf); free(ap); free(ap_prev);
-    free(F); free(pw); free(vg); free(hp); free(hv);
+    free(F); free(pw); free(vg); free(hp); free(hv); free(xk); free(xh); free(vt);
     return rc;
 }
 
@@ -687,7 +755,7 @@ int orc_run(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, d
             double *p, const double *vw, int32_t nsteps, orc_stats *st)
 {
     for (int32_t s = 0; s < nsteps; ++s)
-        if (orc_step(P, nf, nw, x, v, v_prev, p, vw, st + s, NULL, NULL)) return -1;
+        if (orc_step(P, nf, nw, x, v, v_prev, p, vw, st + s, NULL, NULL, NULL)) return -1;
     return 0;
 }
 

@@ -546,3 +546,169 @@ def test_free_surface_particles_are_not_shifted():
         moved[fs] = np.linalg.norm(st.x[:nf] - x0, axis=1)
     assert np.all(moved[1][top | side] == 0.0)
     assert np.all(moved[1][inner] > 0.0) and np.all(moved[1][floor] > 0.0) and np.all(moved[0] > 0.0)
+
+
+# ------------------------------------------- moving particles (Algorithm 1)
+
+def test_moving_pressure_advection_term_against_closed_form():
+    """Eq. (dp-dtau), advective term: with V = 0, p = sin 2 pi x + cos 2 pi y / 2
+    and a uniform pseudo-velocity V~, the rate gains V~ . grad(p) / rho0 (the
+    printed discrete form sum_j m_j (p_i/rho_i^2 + p_j/rho_j^2) gradW_ij, whose
+    1/rho shows with rho0 = 2); a sign slip or p_j - p_i fails. Without V~ (or
+    V~ = 0) the rate is the frozen one, bit for bit."""
+    d = synth.tgv2d(50, jitter=0.0, rho0=2.0)
+    x = d["x"]
+    N = len(x)
+    cfg = d["cfg"]
+    p = np.sin(2 * math.pi * x[:, 0]) + 0.5 * np.cos(2 * math.pi * x[:, 1])
+    vt = np.tile([0.3, -0.7], (N, 1))
+    ap1, F1, _, _ = oracle.rates(cfg, x, np.zeros((N, 2)), p, vt=vt)
+    ap0, F0, _, _ = oracle.rates(cfg, x, np.zeros((N, 2)), p)
+    gx = 2 * math.pi * np.cos(2 * math.pi * x[:, 0])
+    gy = -math.pi * np.sin(2 * math.pi * x[:, 1])
+    exact = (0.3 * gx - 0.7 * gy) / cfg["rho0"]
+    assert np.max(np.abs(ap1 - ap0 - exact)) < 0.02 * np.max(np.abs(exact))
+    assert np.array_equal(F1, F0)                      # V = 0: no momentum advection
+    apz, Fz, _, _ = oracle.rates(cfg, x, np.zeros((N, 2)), p, vt=np.zeros((N, 2)))
+    assert np.array_equal(apz, ap0) and np.array_equal(Fz, F0)
+
+
+def test_moving_momentum_advection_term_against_closed_form():
+    """Eq. (discrete_ME), advective term: on V = (sin 2 pi y, sin 2 pi x / 2)
+    with a uniform V~ = (0.4, 0.9), p = 0, nu = 0, the momentum rate gains
+    (V~ . grad) V. Advecting with V instead of V~ (the slip the paper points out
+    in earlier work), or the wrong sign, fails."""
+    d = synth.tgv2d(64, jitter=0.0)
+    x = d["x"]
+    N = len(x)
+    cfg = dict(d["cfg"], nu=0.0)
+    v = np.stack([np.sin(2 * math.pi * x[:, 1]), 0.5 * np.sin(2 * math.pi * x[:, 0])], 1)
+    vt = np.tile([0.4, 0.9], (N, 1))
+    _, F1, _, _ = oracle.rates(cfg, x, v, np.zeros(N), vt=vt)
+    _, F0, _, _ = oracle.rates(cfg, x, v, np.zeros(N))
+    exact = np.stack([0.9 * 2 * math.pi * np.cos(2 * math.pi * x[:, 1]),
+                      0.4 * 0.5 * 2 * math.pi * np.cos(2 * math.pi * x[:, 0])], 1)
+    assert np.max(np.abs(F1 - F0 - exact)) < 0.01 * np.max(np.abs(exact))
+    wrong = np.stack([v[:, 1] * 2 * math.pi * np.cos(2 * math.pi * x[:, 1]),
+                      v[:, 0] * 0.5 * 2 * math.pi * np.cos(2 * math.pi * x[:, 0])], 1)
+    assert np.max(np.abs(exact - wrong)) > 0.5 * np.max(np.abs(exact))
+
+
+def test_moving_advection_terms_share_the_kernel_gradient_sum():
+    """On a jittered lattice sum_j V_j gradW_ij = G_i is not zero. With p = 1 the
+    pressure term is (2/rho0) V~ . G_i, and with a uniform V = V0 the momentum
+    term is 2 V0 (V~ . G_i), both from the printed (p_i + p_j) and (V_i + V_j)
+    forms: the ratio rho0 V0 ties the two terms' volume factors together."""
+    d = synth.tgv2d(24, jitter=0.3, seed=11, rho0=1.5)
+    x = d["x"]
+    N = len(x)
+    cfg = dict(d["cfg"], nu=0.0)
+    rng = np.random.default_rng(5)
+    vt = rng.uniform(-1, 1, (N, 2))
+    V0 = np.array([0.8, -0.35])
+    ap1, _, _, _ = oracle.rates(cfg, x, np.zeros((N, 2)), np.ones(N), vt=vt)
+    ap0, _, _, _ = oracle.rates(cfg, x, np.zeros((N, 2)), np.ones(N))
+    _, F1, _, _ = oracle.rates(cfg, x, np.tile(V0, (N, 1)), np.zeros(N), vt=vt)
+    _, F0, _, _ = oracle.rates(cfg, x, np.tile(V0, (N, 1)), np.zeros(N))
+    dap = ap1 - ap0
+    dF = F1 - F0
+    assert np.max(np.abs(dap)) > 1e-3                   # the jitter makes G_i visible
+    expect = cfg["rho0"] * dap[:, None] * V0[None, :]
+    assert np.max(np.abs(dF - expect)) < 1e-10 * np.max(np.abs(expect))
+
+
+def _tgv_moving(n=20, jitter=0.2, **over):
+    d = synth.tgv2d(n, jitter=jitter, seed=5)
+    cfg = dict(d["cfg"], **over)
+    return d, cfg
+
+
+@pytest.mark.parametrize("moving", [1, 2])
+def test_moving_one_iteration_equals_frozen(moving):
+    """With V~^0 = 0 the first pass of Algorithm 1 runs at r^{1/2} = r^0 and adds
+    nothing: a step of one pseudo-iteration equals the frozen step bit for bit
+    (a wrong start value of V~ or of the position half step fails)."""
+    d, cfg = _tgv_moving()
+    a = oracle.State(cfg, d["x"], d["v"], d["p"], d["v_prev"], fixed_iters=1)
+    b = oracle.State(cfg, d["x"], d["v"], d["p"], d["v_prev"], fixed_iters=1, moving=moving)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.v, b.v) and np.array_equal(a.p, b.p)
+    c = oracle.State(cfg, d["x"], d["v"], d["p"], d["v_prev"], fixed_iters=3, moving=moving)
+    e = oracle.State(cfg, d["x"], d["v"], d["p"], d["v_prev"], fixed_iters=3)
+    c.step(1)
+    e.step(1)
+    assert not np.array_equal(c.v, e.v)                 # from the second pass on, V~ acts
+
+
+@pytest.mark.parametrize("moving", [1, 2])
+def test_moving_positions_follow_the_pseudo_velocity(moving):
+    """Eqs. (rkstar, rkp1, vtilde) give r^K - r^0 = dtau sum_k V~^k - dtau/2 V~^K
+    with V~^k = dt (dV/dtau)^{k-1/2} = dt (V^k - V^{k-1}) / dtau, so
+    r^K - r^0 = dt (V^K - V^0) - dt/2 (V^K - V^{K-1}), V^0 the predictor of
+    Eq. (v0). Taking dtau for dt in Eq. (vtilde), or dropping a half step, fails.
+    Walls stay where they are."""
+    d = synth.cavity2d(16)
+    nf = d["nf"]
+    cfg = d["cfg"]
+    K = 6
+
+    def run(k):
+        s = oracle.State(cfg, d["x"], d["v"], d["p"], d["v_prev"], d["vw"], nf, fixed_iters=k, moving=moving)
+        rec = s.step(1, keep_x0=True)[0]
+        return s, rec
+
+    sK, rK = run(K)
+    sK1, _ = run(K - 1)
+    _, F, _, _ = oracle.rates(cfg, d["x"], d["v"], d["p"], d["vw"], nf)
+    v0 = d["v"] + cfg["dt"] * F
+    disp = rK["xk"][:nf] - rK["x0"][:nf]
+    expect = cfg["dt"] * (sK.v - v0) - 0.5 * cfg["dt"] * (sK.v - sK1.v)
+    assert np.max(np.abs(expect)) > 1e-9
+    assert np.max(np.abs(disp - expect)) < 1e-9 * np.max(np.abs(expect))
+    assert np.array_equal(rK["xk"][nf:], rK["x0"][nf:])
+    # the pseudo-time displacement is tiny next to h (the reason Sec. 2.2 freezes it)
+    assert np.max(np.abs(disp)) < 1e-2 * cfg["h"]
+
+
+def test_moving_and_frozen_agree_on_taylor_green():
+    """Sec. 4.1 (advection in pseudo-time): moving the particles in pseudo-time,
+    with or without updating the neighbours, leaves the Taylor-Green solution
+    essentially unchanged. 2D, 50^2, Re 100, 10 steps: each variant's L1 error of
+    the velocity magnitude (Eq. tg:l1) is within 2%, within 0.2% of the frozen
+    scheme's, and the velocity fields differ by less than that error."""
+    d = synth.tgv2d(50)
+    out = {}
+    for mv in (0, 1, 2):
+        st = oracle.State(d["cfg"], d["x"], d["v"], d["p"], d["v_prev"], moving=mv)
+        recs = st.step(10)
+        assert all(r["reason"] in (0, 1) for r in recs)
+        u, v, _ = synth.tgv_exact(st.x[:, 0], st.x[:, 1], st.t)
+        ex = np.hypot(u, v)
+        got = np.hypot(st.v[:, 0], st.v[:, 1])
+        out[mv] = (st, np.abs(got - ex).sum() / ex.sum())
+    l1f = out[0][1]
+    for mv in (0, 1, 2):
+        assert out[mv][1] < 0.02
+    for mv in (1, 2):
+        assert abs(out[mv][1] - l1f) < 0.002
+        dv = np.abs(np.hypot(*(out[mv][0].v - out[0][0].v).T)).sum() / np.hypot(*out[0][0].v.T).sum()
+        assert 0 < dv < l1f
+
+
+def test_moving_with_neighbour_update_sees_pairs_that_enter_the_support():
+    """Updating the neighbours while moving (Sec. 4.1's second advected variant):
+    on a perfect lattice the pairs at exactly 3h are out of range at r^0 and the
+    pseudo-time motion brings some of them just inside, so rebuilding the lists at
+    every pass changes the result, by the quintic's (3 - q)^4 at the support edge
+    only; the rebuild agrees bit for bit with a brute-force search."""
+    d = synth.tgv2d(20, jitter=0.0)
+    runs = {}
+    for mv, brute in ((1, 0), (2, 0), (2, 1)):
+        s = oracle.State(d["cfg"], d["x"], d["v"], d["p"], d["v_prev"], moving=mv, fixed_iters=8,
+                         use_bruteforce=brute)
+        s.step(2)
+        runs[mv, brute] = s.v
+    assert not np.array_equal(runs[1, 0], runs[2, 0])
+    assert np.max(np.abs(runs[1, 0] - runs[2, 0])) < 1e-12
+    assert np.array_equal(runs[2, 0], runs[2, 1])
