@@ -94,6 +94,16 @@ def with_steady(d, wcfg, iters):
     wcfg["steady"] = f"on: one pseudo-time solve of {iters} iterations per step, particles fixed"
 
 
+def with_moving(d, wcfg, moving):
+    """Particles moved in pseudo-time (Algorithm 1) in every instance, for both
+    arms: 1 over the lists of r^0, 2 with neighbours updated every pass (the two
+    advected variants that Sec. 4.1 times against the frozen scheme)."""
+    for x in (d if isinstance(d, list) else [d]):
+        x["cfg"] = dict(x["cfg"], moving=moving)
+    wcfg["moving"] = {1: "advected in pseudo-time, lists of r^0 (Algorithm 1)",
+                      2: "advected in pseudo-time, neighbours updated every pass (Algorithm 1)"}[moving]
+
+
 class Job:
     """One context running a workload: a single instance or a batch."""
 
@@ -162,6 +172,9 @@ def parse():
                     help="lanes per particle of the iterate kernel (0: autotuned)")
     ap.add_argument("--stages", type=int, default=0, help="staging depth with --lanes 1 (0: autotuned or 3)")
     ap.add_argument("--shifting", action="store_true", help="particle shifting after every real step (both arms)")
+    ap.add_argument("--moving", type=int, default=0, choices=[0, 1, 2],
+                    help="particles moved in pseudo-time (Algorithm 1; both arms): 1 lists of r^0, "
+                         "2 neighbours updated every pass; 0 frozen")
     ap.add_argument("--steady", type=int, default=0,
                     help="steady-state mode with this many pseudo-iterations per solve (both arms; 0: off)")
     return ap.parse_args()
@@ -338,6 +351,8 @@ def main_ours(args):
         with_shifting(d, wcfg)
     if args.steady:
         with_steady(d, wcfg, args.steady)
+    if args.moving:
+        with_moving(d, wcfg, args.moving)
     kern = dict(lanes=args.lanes, stages=args.stages)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if world > 1:
@@ -388,6 +403,11 @@ def main_ours(args):
     loop_kernel = {2: f"k_loop<{dims},FP32C,lanes={lanes32}> (persistent loop, one launch per step)",
                    1: f"k_iterate<{dims},FP32C,lanes={lanes32}> in the while node (one launch per iteration)",
                    0: f"k_iterate<{dims},FP32C,lanes={lanes32}> (plain launches)"}[args.graph]
+    probe_kernel = f"k_iterate<{dims},FP32C,lanes={lanes32}>"
+    if args.moving:
+        probe_kernel = f"k_move_walls + k_move_iter<{dims},FP32C> (one lane per particle)"
+        loop_kernel = probe_kernel + (" (plain launches)" if args.graph == 0 else
+                                      " in the while node (one launch each per iteration)")
     e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -403,7 +423,7 @@ def main_ours(args):
                      "bytes_per_launch": loop_bytes / len(loop_ms), "launch_ms": sum(loop_ms) / len(loop_ms),
                      "timing": f"CUDA events around the loop of each of the last {len(loop_ms)} timed steps",
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
-        "iterate_probe": {"kernel": f"k_iterate<{dims},FP32C,lanes={lanes32}>", "achieved": achieved_probe,
+        "iterate_probe": {"kernel": probe_kernel, "achieved": achieved_probe,
                           "frac": achieved_probe / hbm, "bytes_per_launch": bytes_it, "launch_ms": ms_it,
                           "pairs": npairs, "timing": "50 launches after the timed region, CUDA events"},
         "autotune": {"lanes_per_particle": lanes32, "stages": stages32, "ms_by_lanes": tune32,
@@ -437,6 +457,8 @@ def main_reference(args):
         with_shifting(d, wcfg)
     if args.steady:
         with_steady(d, wcfg, args.steady)
+    if args.moving:
+        with_moving(d, wcfg, args.moving)
     states = oracle_states(d)
     for st in states:
         st.step(args.warmup)

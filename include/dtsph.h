@@ -39,7 +39,9 @@ enum {
     DTSPH_E_CAPACITY = -5,    /* a particle had more than max_neighbors neighbours */
     DTSPH_E_DOMAIN = -6,      /* a particle left the box of a non-periodic axis */
     DTSPH_E_UNSUPPORTED = -7, /* parameter combination not implemented on the GPU */
-    DTSPH_E_TIMEOUT = -8      /* a device-side wait gave up (persistent loop barrier) */
+    DTSPH_E_TIMEOUT = -8,     /* a device-side wait gave up (persistent loop barrier) */
+    DTSPH_E_SKIN = -9         /* moving = 2: a particle moved farther than skin/2 from r^0 in
+                                 pseudo-time, so the lists may miss a neighbour */
 };
 
 typedef enum {
@@ -106,6 +108,23 @@ typedef struct {
                                  div r_i = -sum_j V_j r_ij . gradW_ij < dim - 1/2 (fluid and wall
                                  neighbours; Lind et al.'s test, Sec. 3.5) is not shifted.
                                  Instances of a batch share it. */
+    int32_t moving;           /* particles in pseudo-time. 0: fixed (Algorithm 2). 1 or 2:
+                                 moved (Algorithm 1): r^{k+1/2} = r^k + dtau/2 V~^k
+                                 (Eq. rkstar), rates at r^{k+1/2} with the advective terms
+                                 V~_i . sum_j m (p_i + p_j)/rho0^2 gradW_ij in dp/dtau (Eq.
+                                 dp-dtau) and sum_j m/rho0 (V_i + V_j) (V~_i . gradW_ij) in the
+                                 momentum rate (Eq. discrete_ME), V~^{k+1} = dt dV/dtau
+                                 (Eq. vtilde), r^{k+1} = r^{k+1/2} + dtau/2 V~^{k+1} (Eq. rkp1),
+                                 V~^0 = 0; walls stay; r^{n+1} still from Eq. (r-update).
+                                 1: over the neighbour lists of r^0; 2: neighbours updated at
+                                 every pass (lists with the cutoff 3h + skin; a particle that
+                                 moves farther than skin/2 from r^0 ends the step with
+                                 DTSPH_E_SKIN). Not with steady. With graph = 2 the loop runs
+                                 as in graph = 1. Instances of a batch share it. */
+    int32_t pad1;
+    double skin;              /* list skin for moving = 2 (a length > 0; the lists then hold
+                                 every pair within 3h + skin, dtsph_get_neighbors included);
+                                 ignored otherwise. Instances of a batch share it. */
 } dtsph_params;
 
 typedef struct {
@@ -215,7 +234,8 @@ int dtsph_get_neighbors(dtsph_ctx *ctx, int64_t i, int64_t *out, int64_t cap, in
 
 /* Measurement entry: after at least one dtsph_step, re-runs the pseudo-time
  * iteration kernel of the last step `launches` times (1..256) on its frozen pair
- * cache, each launch bracketed by CUDA events on the context stream, and
+ * cache (with moving != 0: the moving pass, wall kernel included, on the lists
+ * of the last step), each launch bracketed by CUDA events on the context stream, and
  * returns the mean launch duration in milliseconds, the algorithmic bytes one
  * launch must move (particle state read and written once, every cached pair
  * read once; the layout is described in the design notes) and the number of

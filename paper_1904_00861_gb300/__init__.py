@@ -21,6 +21,7 @@ DTSPH_OK = 0
 ERRORS = {
     -1: "DTSPH_E_ARG", -2: "DTSPH_E_STATE", -3: "DTSPH_E_CUDA", -4: "DTSPH_E_OOM",
     -5: "DTSPH_E_CAPACITY", -6: "DTSPH_E_DOMAIN", -7: "DTSPH_E_UNSUPPORTED", -8: "DTSPH_E_TIMEOUT",
+    -9: "DTSPH_E_SKIN",
 }
 DTSPH_FP64, DTSPH_FP32C = 0, 1
 FIELD_POS, FIELD_VEL, FIELD_P, FIELD_VEL_PREV = 0, 1, 2, 3
@@ -43,6 +44,7 @@ class dtsph_params(C.Structure):
         ("stag_window", C.c_int32), ("max_iter", C.c_int32), ("edac", C.c_int32), ("edac_h2_literal", C.c_int32),
         ("fixed_iters", C.c_int32), ("max_neighbors", C.c_int32), ("graph", C.c_int32), ("lanes", C.c_int32),
         ("stages", C.c_int32), ("shifting", C.c_int32), ("steady", C.c_int32), ("free_surface", C.c_int32),
+        ("moving", C.c_int32), ("pad1", C.c_int32), ("skin", C.c_double),
     ]
 
 
@@ -131,10 +133,12 @@ def _ptr(a):
 
 
 def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) -> dtsph_params:
-    """Fill dtsph_params from a plain dict (the keys of ``synth`` configs)."""
+    """Fill dtsph_params from a plain dict (the keys of ``synth`` configs).
+    With moving = 2 and no skin given, the skin is h / 2."""
     d = dict(periodic=(0, 0, 0), lo=(0, 0, 0), hi=(1, 1, 1), rho0=1.0, beta=10.0, v_ref=1.0, eta=0.01, alpha=0.0,
              g=(0, 0, 0), eps=1e-3, stag_tol=0.05, stag_window=4, max_iter=1000, edac=1, edac_h2_literal=0,
-             fixed_iters=0, max_neighbors=0, lanes=0, stages=0, shifting=0, steady=0, free_surface=0)
+             fixed_iters=0, max_neighbors=0, lanes=0, stages=0, shifting=0, steady=0, free_surface=0, moving=0,
+             skin=0.0)
     d.update(cfg)
     d.update(over)
     p = dtsph_params()
@@ -149,8 +153,11 @@ def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) 
     for k in ("h", "m", "rho0", "beta", "v_ref", "nu", "dt", "eta", "alpha", "eps", "stag_tol"):
         setattr(p, k, float(d[k]))
     for k in ("stag_window", "max_iter", "edac", "edac_h2_literal", "fixed_iters", "max_neighbors", "lanes",
-              "stages", "shifting", "steady", "free_surface"):
+              "stages", "shifting", "steady", "free_surface", "moving"):
         setattr(p, k, int(d[k]))
+    p.skin = float(d["skin"])
+    if p.moving == 2 and p.skin == 0.0:
+        p.skin = 0.5 * p.h
     return p
 
 

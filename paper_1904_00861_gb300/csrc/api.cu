@@ -113,7 +113,9 @@ int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
 {
     memset(&G, 0, sizeof G);
     G.dim = p.dim;
-    const double rc = 3.0 * p.h;
+    // the lists cover 3h, plus the skin when the particles move in pseudo-time
+    // with neighbour updates (pairs beyond 3h add exact zeros)
+    const double rc = 3.0 * p.h + (p.moving == 2 ? p.skin : 0.0);
     G.ncell = 1;
     for (int a = 0; a < 3; ++a) {
         G.periodic[a] = a < p.dim ? p.periodic[a] : 0;
@@ -134,7 +136,8 @@ int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
         long long k = (long long)std::floor(L / (rc * (1.0 + 1e-9)));
         if (k < 1) k = 1;
         if (G.periodic[a] && k < 3)
-            return fail(c, DTSPH_E_ARG, "periodic axis %d is shorter than 9h (%g < %g)", a, L, 3 * rc);
+            return fail(c, DTSPH_E_ARG, "periodic axis %d is shorter than three list cutoffs (%g < %g)", a, L,
+                        3 * rc);
         if (k > (1 << 20)) return fail(c, DTSPH_E_ARG, "axis %d has too many cells", a);
         G.nc[a] = (int)k;
         G.s[a] = L / (double)k;
@@ -146,7 +149,7 @@ int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
     }
     if ((long long)G.nc[0] * G.nc[1] * G.nc[2] > (1LL << 28)) return fail(c, DTSPH_E_ARG, "too many cells");
     G.rc2 = rc * rc;
-    // FP32 band around (3h)^2: the FP32 separation from cell offsets is accurate
+    // FP32 band around the cutoff: the FP32 separation from cell offsets is accurate
     // to a few 1e-7 h, so outside +-2e-5 relative the FP32 test decides
     G.rc2_lo = (float)(G.rc2 * (1.0 - 2e-5));
     G.rc2_hi = (float)(G.rc2 * (1.0 + 2e-5));
@@ -185,6 +188,8 @@ void setup_phys(const dtsph_params &p, Phys &P)
     P.vol = p.m / p.rho0;
     P.steady = p.steady;
     P.free_surface = p.free_surface;
+    P.moving = p.steady ? 0 : p.moving;
+    P.disp2_max = p.moving == 2 ? 0.25 * p.skin * p.skin : 0.0;
     if (p.steady) {
         // Eq. (mom-steady): dV/dtau is the momentum rate itself (no BDF2 term);
         // the pressure rate has no EDAC term
@@ -218,6 +223,10 @@ int validate(dtsph_ctx *c, const dtsph_params *p)
     if (p->steady != 0 && p->steady != 1) return fail(c, DTSPH_E_ARG, "steady must be 0 or 1");
     if (p->steady && p->shifting) return fail(c, DTSPH_E_ARG, "the steady mode keeps the particles fixed: no shifting");
     if (p->free_surface != 0 && p->free_surface != 1) return fail(c, DTSPH_E_ARG, "free_surface must be 0 or 1");
+    if (p->moving < 0 || p->moving > 2) return fail(c, DTSPH_E_ARG, "moving must be 0, 1 or 2");
+    if (p->moving && p->steady) return fail(c, DTSPH_E_ARG, "the steady mode keeps the particles fixed: moving must be 0");
+    if (!(p->skin >= 0) || !std::isfinite(p->skin)) return fail(c, DTSPH_E_ARG, "skin must be >= 0 and finite");
+    if (p->moving == 2 && !(p->skin > 0)) return fail(c, DTSPH_E_ARG, "moving = 2 needs a positive skin");
     return DTSPH_OK;
 }
 
@@ -272,7 +281,7 @@ int neighbour_capacity(const dtsph_params &p)
 {
     if (p.max_neighbors > 0) return p.max_neighbors;
     const double vol = p.m / p.rho0;
-    const double rc = 3.0 * p.h;
+    const double rc = 3.0 * p.h + (p.moving == 2 ? p.skin : 0.0);
     double expect = p.dim == 2 ? pi() * rc * rc / vol : 4.0 / 3.0 * pi() * rc * rc * rc / vol;
     int k = (int)std::ceil(1.35 * expect) + 8;
     return std::min(std::max(k, 8), 4096);
@@ -351,6 +360,12 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         A(B.nb64[0], n) A(B.nb64[1], n) A(B.pc64, npair)
     }
     A(B.ap_b, n) A(B.f_b, nd)
+    if (c->prm[0].moving && !c->prm[0].steady) {
+        A(B.xk[0], nd) A(B.xk[1], nd) A(B.vt, nd)
+        if (B.fp32c) {
+            A(B.offk[0], n) A(B.offk[1], n)
+        }
+    }
     // two residual partials per tile (at most one tile per warp of slots),
     // double-buffered by the persistent loop
     A(B.blk, 4 * nwarps) A(B.ls, ni) A(B.ctrl, 1) A(B.stats, (size_t)kStatRing * ni) A(B.err, 1)
@@ -405,12 +420,14 @@ int enqueue_pre_loop(dtsph_ctx *c, cudaStream_t st)
     k += launch_state_n(B, true, st);                     // walls, rates, predictor
     k += launch_binning(B, B.xp_b, B.gid_b, st);         // cells at r^0
     k += launch_permute_b_to_a(B, st);
-    k += launch_pair_cache(B, B.xp_a, B.cell_a, B.gid_a, st);   // also resets the loop state
+    if (B.xk[0]) k += launch_move_prepare(B, st);              // particles moving in pseudo-time
+    else k += launch_pair_cache(B, B.xp_a, B.cell_a, B.gid_a, st);   // also resets the loop state
     return k;
 }
 
 int enqueue_iteration(dtsph_ctx *c, cudaStream_t st, unsigned long long cond, int use_cond)
 {
+    if (c->B.xk[0]) return launch_move_iteration(c->B, cond, use_cond, st);
     int k = launch_walls_iter(c->B, st);
     k += launch_iterate(c->B, cond, use_cond, st);
     return k;
@@ -477,7 +494,9 @@ int build_graph_persistent(dtsph_ctx *c)
 // Graph of one real step: pre-loop kernels -> while node (walls, iterate) -> outer.
 int build_graph(dtsph_ctx *c)
 {
-    if (c->prm[0].graph == 2) return build_graph_persistent(c);
+    // the persistent loop kernel runs the frozen pass only; moving runs take the
+    // while node
+    if (c->prm[0].graph == 2 && !c->B.xk[0]) return build_graph_persistent(c);
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     c->graph = g;
@@ -554,6 +573,8 @@ int device_error(dtsph_ctx *c)
     if (e & kErrDomain) return fail(c, DTSPH_E_DOMAIN, "a particle left the box of a non-periodic axis");
     if (e & kErrBarrier) return fail(c, DTSPH_E_TIMEOUT, "a grid barrier of the persistent loop timed out");
     if (e & kErrCopy) return fail(c, DTSPH_E_TIMEOUT, "a bulk copy of pair-cache rows did not complete");
+    if (e & kErrSkin)
+        return fail(c, DTSPH_E_SKIN, "a particle moved farther than skin / 2 from r^0 in pseudo-time (raise skin)");
     return DTSPH_OK;
 }
 
@@ -567,10 +588,11 @@ int probe_ms(dtsph_ctx *c, int launches, float *out)
     for (int i = 0; i < launches; ++i) {
         launch_loop_reset(B, c->stream);
         CK(cudaEventRecord(ev[2 * i], c->stream));
-        launch_iterate(B, 0ull, 0, c->stream);
+        // particles moving in pseudo-time: the whole pass (walls, then fluid)
+        c->launches += B.xk[0] ? launch_move_iteration(B, 0ull, 0, c->stream) : launch_iterate(B, 0ull, 0, c->stream);
         CK(cudaEventRecord(ev[2 * i + 1], c->stream));
     }
-    c->launches += 2 * launches;
+    c->launches += launches;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     double tot = 0;
@@ -727,7 +749,7 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
     if (!device) CK(cudaStreamSynchronize(c->stream));   // host arrays may be reused once we return
     c->have_particles = true;
     c->steps = 0;
-    if (!c->tuned && c->prm[0].lanes == 0) {
+    if (!c->tuned && c->prm[0].lanes == 0 && !c->B.xk[0]) {
         r = autotune(c);
         if (r) return r;
     }
@@ -786,9 +808,11 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
         if (!r && (params[i].dim != params[0].dim || params[i].precision != params[0].precision ||
                    params[i].graph != params[0].graph || params[i].lanes != params[0].lanes ||
                    params[i].stages != params[0].stages || params[i].shifting != params[0].shifting ||
-                   params[i].steady != params[0].steady || params[i].free_surface != params[0].free_surface))
+                   params[i].steady != params[0].steady || params[i].free_surface != params[0].free_surface ||
+                   params[i].moving != params[0].moving || params[i].skin != params[0].skin))
             r = fail(c, DTSPH_E_ARG,
-                     "instances must share dim, precision, graph, lanes, stages, shifting, steady and free_surface");
+                     "instances must share dim, precision, graph, lanes, stages, shifting, steady, free_surface, "
+                     "moving and skin");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;
@@ -1075,18 +1099,37 @@ int dtsph_probe_iterate(dtsph_ctx *c, int32_t launches, float *ms_per_launch, do
     std::vector<uint32_t> gid(B.n);
     CK(cudaMemcpy(cnt.data(), B.pcount, sizeof(int) * B.n, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(gid.data(), B.gid_a, sizeof(uint32_t) * B.n, cudaMemcpyDeviceToHost));
-    int64_t np = 0;
-    for (int s = 0; s < B.n; ++s)
+    int64_t np = 0, npw = 0;
+    for (int s = 0; s < B.n; ++s) {
         if (gid[s] < (uint32_t)B.nf) np += cnt[s];
-    // per fluid particle: packed (V, p-hat) read and written, V^k (FP64) read and
-    // written, BDF2 source read, neighbour count read; per pair: the cache entry
+        else if (gid[s] != kNoParticle) npw += cnt[s];
+    }
     const int d = B.dim;
     const double packed = B.fp32c ? 16.0 : 32.0;
-    const double per_particle = 2 * packed + 2 * 8.0 * d + 8.0 * d + 4.0;
-    const double per_pair = B.fp32c ? (d == 2 ? 16.0 : 20.0) : 36.0;
+    double bytes;
+    if (!B.xk[0]) {
+        // per fluid particle: packed (V, p-hat) read and written, V^k (FP64) read
+        // and written, BDF2 source read, neighbour count read; per pair: the cache entry
+        const double per_particle = 2 * packed + 2 * 8.0 * d + 8.0 * d + 4.0;
+        const double per_pair = B.fp32c ? (d == 2 ? 16.0 : 20.0) : 36.0;
+        bytes = per_particle * B.nf + per_pair * (double)np;
+    } else {
+        // moving pass, per fluid particle: packed (V, p-hat), V^k, V~ and r^{k+1/2}
+        // (FP64) read and written, BDF2 source read, slot id and neighbour count
+        // read; FP32C: its FP32 offset read and written and its cell read; with
+        // the skin: r^0 read. Per wall slot: slot id, count, prescribed velocity and
+        // own position read, packed values written. Per list entry (fluid and wall
+        // slots): neighbour index and cell shift.
+        const double pos = B.fp32c ? 16.0 : 8.0 * d;
+        double per_particle = 2 * packed + 3 * 2 * 8.0 * d + 8.0 * d + 8.0;
+        if (B.fp32c) per_particle += 2 * 16.0 + 4.0;
+        if (c->P[0].moving == 2) per_particle += 8.0 * d;
+        const double per_wall = 8.0 + 8.0 * d + pos + packed;
+        bytes = per_particle * B.nf + per_wall * B.nw + 5.0 * (double)(np + npw);
+    }
     int r = probe_ms(c, launches, ms_per_launch);
     if (r) return r;
-    if (bytes_per_launch) *bytes_per_launch = per_particle * B.nf + per_pair * (double)np;
+    if (bytes_per_launch) *bytes_per_launch = bytes;
     if (pairs) *pairs = np;
     return DTSPH_OK;
 }

@@ -14,7 +14,7 @@ constexpr int kWarp = 32;
 constexpr uint32_t kWallBit = 0x80000000u;   // set in a cached neighbour index when j is a wall
 
 // Error bits raised by kernels into Buffers::err (read by dtsph_sync).
-enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy = 8u };
+enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy = 8u, kErrSkin = 16u };
 
 // A context advances one or more independent simulations ("instances") together.
 // Instance i owns the slot range [slot_off, slot_off + nf + nw) of every particle
@@ -47,7 +47,7 @@ struct Geom {
     double L[3], halfL[3];
     double s[3], inv_s[3];
     float s_f[3];
-    double rc2;           // (3h)^2, the FP64 neighbour test
+    double rc2;           // (3h + skin)^2, the FP64 neighbour test (skin: moving = 2 only)
     float rc2_lo, rc2_hi; // FP32 pre-test band: below lo is in, above hi is out
 };
 
@@ -77,6 +77,11 @@ struct Phys {
                          // convection term, particles fixed
     int free_surface;    // wall pressure kept >= 0; free-surface particles not shifted
     double vol;          // m / rho0 (convection term)
+    int moving;          // 0: particles fixed in pseudo-time; 1: moved (Algorithm 1),
+                         // lists of r^0; 2: moved, lists with a skin
+    int pad_m;
+    double disp2_max;    // (skin / 2)^2: the largest squared pseudo-time displacement
+                         // from r^0 that the lists with a skin cover (moving = 2)
 };
 
 // Convergence control of one instance's pseudo-time loop, in device memory.
@@ -153,6 +158,10 @@ struct Buffers {
     double4_32a *pc64;         // FP64: (gradW, F_ij)
     float4 *pc32;          // FP32C: (gradW, F_ij); in 2D .w holds the index bits
     int *pcount;           // neighbours of each slot
+    // particles moving in pseudo-time (Algorithm 1; allocated only then), order A
+    double *xk[2];         // r^{k+1/2} FP64 [dim][n], ping-pong
+    float4 *offk[2];       // FP32C: FP32 offsets of r^{k+1/2} from the slot's cell origin at r^0
+    double *vt;            // V~^k = dt (dV/dtau)^{k-1/2}, Eq. (vtilde) [dim][n] (own slot only)
     // state-n rates (test entry and predictor)
     double *ap_b;          // [n]
     double *f_b;           // [dim][n]
@@ -163,6 +172,15 @@ struct Buffers {
     StatRec *stats;        // [kStatRing][ninst]
     uint32_t *err;
 };
+
+// Runs the statement with D (2 or 3) and F32 (FP32C path) as constants.
+#define DTSPH_DISPATCH(D_, F32_, ...)                                                                \
+    do {                                                                                             \
+        if ((D_) == 2 && !(F32_)) { constexpr int D = 2; constexpr bool F32 = false; __VA_ARGS__; } \
+        else if ((D_) == 2) { constexpr int D = 2; constexpr bool F32 = true; __VA_ARGS__; }        \
+        else if (!(F32_)) { constexpr int D = 3; constexpr bool F32 = false; __VA_ARGS__; }         \
+        else { constexpr int D = 3; constexpr bool F32 = true; __VA_ARGS__; }                       \
+    } while (0)
 
 // Instance owning the block that covers slots [first, first + width): a block
 // never straddles two instances.
@@ -177,11 +195,22 @@ __device__ __forceinline__ int block_instance(const Buffers &B, int first)
 int launch_binning(const Buffers &B, const double *x_keys, const uint32_t *gid_src, cudaStream_t st);
 int launch_permute_a_to_b(const Buffers &B, cudaStream_t st);
 int launch_permute_b_to_a(const Buffers &B, cudaStream_t st);
+// Neighbour lists of every slot at positions xpos (order of the latest binning);
+// one launch.
+void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
 int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st);
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
 int launch_walls_iter(const Buffers &B, cudaStream_t st);
 int launch_iterate(const Buffers &B, unsigned long long cond_handle, int use_cond, cudaStream_t st);
 int launch_outer(const Buffers &B, cudaStream_t st);
+// Particles moving in pseudo-time (Algorithm 1): the lists at r^0 (with the
+// skin for moving = 2), the start iterate r^{1/2} = r^0, V~^0 = 0, and the loop
+// state reset (replaces the pair cache of the frozen loop).
+int launch_move_prepare(const Buffers &B, cudaStream_t st);
+// One moving pseudo-iteration: the wall values at the moved positions, then the
+// pair pass with the advective terms, the update of V, V~, r and p-hat, and the
+// stop rules (sets the while-node condition when use_cond).
+int launch_move_iteration(const Buffers &B, unsigned long long cond_handle, int use_cond, cudaStream_t st);
 // Particle shifting of the fluid after the real step: bins at r^{n+1}, gathers
 // the state into order B, builds the lists, and shifts (results written back to
 // order A).

@@ -28,6 +28,7 @@
 #include <algorithm>
 
 #include "bulk.cuh"
+#include "loop_rules.cuh"
 #include "pair_terms.cuh"
 
 namespace dtsph {
@@ -35,32 +36,6 @@ namespace dtsph {
 namespace {
 
 inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
-
-// Stop rules of Sec. 3.4 on the residual history (ring of the last 16).
-__device__ int stop_rule(const LoopState &L, int k1)
-{
-    double rp = L.hist_p[(k1 - 1) & 15], rv = L.hist_v[(k1 - 1) & 15];
-    if (!isfinite(rp) || !isfinite(rv)) return 3;
-    if (L.fixed_iters > 0) return k1 >= L.fixed_iters ? 4 : -1;
-    if (rp < L.eps && rv < L.eps) return 0;
-    int w = L.stag_window;
-    if (w > 0 && k1 >= w) {
-        bool stag = true;
-        for (int which = 0; which < 2 && stag; ++which) {
-            const double *h = which ? L.hist_v : L.hist_p;
-            double lo = h[(k1 - 1) & 15], hi = lo;
-            for (int t = k1 - w; t < k1; ++t) {
-                double v = h[t & 15];
-                lo = fmin(lo, v);
-                hi = fmax(hi, v);
-            }
-            if (!(hi > 0.0 && (hi - lo) / hi < L.stag_tol)) stag = false;
-        }
-        if (stag) return 1;
-    }
-    if (k1 >= L.max_iter) return 2;
-    return -1;
-}
 
 // Wall values of wall slot s for the iteration whose iterate sits in buffer cur,
 // from the cached fluid neighbours of the slot.
@@ -156,30 +131,6 @@ struct CacheEntry {
         }
     }
 };
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Warp sum of (s + e) pairs with two-sum compensation: s accumulates the
-// rounded sum, e the exact rounding errors of every addition.
-__device__ __forceinline__ void warp_sum2(float &s, float &e)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float os = __shfl_xor_sync(0xffffffffu, s, o);
-        const float oe = __shfl_xor_sync(0xffffffffu, e, o);
-        const float t = s + os;
-        const float bp = t - s;
-        const float err = (s - (t - bp)) + (os - bp);
-        s = t;
-        e = e + oe + err;
-    }
-}
 
 // Pair-cache rows of one warp in shared memory (one lane per slot). The 32 slots
 // of the warp form one slice of the sliced cache, so their entries k = 0, 1, ...
@@ -503,66 +454,6 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
         blk_av = b;
     }
     __syncthreads();   // sh is reused by the next tile
-}
-
-// Fixed-order sum of the ntiles per-tile partials at blk (pairs of doubles), by
-// the whole block; every caller gets the same bits. Result on thread 0.
-__device__ __forceinline__ void reduce_tiles(const double *blk, int ntiles, double (&red)[2][kBlock / kWarp],
-                                             double &sa, double &sb)
-{
-    double a = 0, b = 0;
-    for (int q = threadIdx.x; q < ntiles; q += blockDim.x) {
-        a += __ldcg(&blk[2 * q]);
-        b += __ldcg(&blk[2 * q + 1]);
-    }
-    a = warp_sum<double>(a);
-    b = warp_sum<double>(b);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        red[0][wid] = a;
-        red[1][wid] = b;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        sa = 0;
-        sb = 0;
-        for (int w = 0; w < kBlock / kWarp; ++w) {
-            sa += red[0][w];
-            sb += red[1][w];
-        }
-    }
-}
-
-// First tile and end tile of instance i for tiles of ppb slots.
-__device__ __forceinline__ void instance_tiles(const Inst &I, int ppb, int &lo, int &hi)
-{
-    lo = I.slot_off / ppb;
-    hi = (I.slot_off + I.nf + I.nw + ppb - 1) / ppb;
-}
-
-// Updates the loop state of one instance with the residual sums of iteration
-// `it` and applies the stop rules; thread 0 only. Returns the stop reason (-1:
-// continue).
-__device__ __forceinline__ int finish_iteration(LoopState *ls, const Phys &P, int it, double sa, double sb)
-{
-    // work on a register copy: one batch of loads instead of a chain of
-    // dependent global accesses
-    LoopState st = *ls;
-    const int k1 = it + 1;
-    st.rp = sa * P.rp_scale;
-    st.rv = sb * P.rv_scale;
-    st.hist_p[it & 15] = st.rp;
-    st.hist_v[it & 15] = st.rv;
-    const int r = stop_rule(st, k1);
-    ls->rp = st.rp;
-    ls->rv = st.rv;
-    ls->hist_p[it & 15] = st.rp;
-    ls->hist_v[it & 15] = st.rv;
-    ls->iter = k1;
-    ls->reason = r;
-    ls->done = r >= 0;
-    return r;
 }
 
 // One pseudo-time iteration over all slots; one tile per block. The last block

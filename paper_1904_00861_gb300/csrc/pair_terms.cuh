@@ -34,11 +34,13 @@ template <> struct Ar<double> {
 };
 
 // Quintic spline, dW/dq up to the factor sigma: -5(3-q)^4 + 30(2-q)^4 - 75(1-q)^4
-// with each term present only inside its support.
+// with each term present only inside its support (0 from q = 3 on, so a list
+// built with a wider cutoff adds exact zeros).
 template <typename T>
 __device__ __forceinline__ T quintic_dwdq(T q)
 {
     using A = Ar<T>;
+    if (!(q < T(3))) return T(0);
     const T a = A::sub(T(3), q);
     const T a2 = A::mul(a, a);
     T s = A::mul(A::mul(T(-5), a2), a2);
@@ -55,11 +57,13 @@ __device__ __forceinline__ T quintic_dwdq(T q)
     return s;
 }
 
-// W(q) up to sigma: (3-q)^5 - 6(2-q)^5 + 15(1-q)^5 within the supports.
+// W(q) up to sigma: (3-q)^5 - 6(2-q)^5 + 15(1-q)^5 within the supports (0 from
+// q = 3 on).
 template <typename T>
 __device__ __forceinline__ T quintic_w(T q)
 {
     using A = Ar<T>;
+    if (!(q < T(3))) return T(0);
     const T a = A::sub(T(3), q);
     const T a2 = A::mul(a, a);
     T s = A::mul(A::mul(a2, a2), a);

@@ -60,11 +60,24 @@ def test_version_and_argument_errors_without_gpu(so):
         with pytest.raises(lib_pkg.DtsphError) as e:
             lib_pkg.dtsph_create(p)
         assert e.value.code == -1
+    base = dict(dim=2, h=0.1, m=0.01, nu=0.01, dt=0.01)
+    for over in (dict(moving=3), dict(moving=-1), dict(moving=1, steady=1), dict(moving=1, skin=-0.1)):
+        p = lib_pkg.make_params(dict(base, **over))
+        with pytest.raises(lib_pkg.DtsphError) as e:
+            lib_pkg.dtsph_create(p)
+        assert e.value.code == -1, over
+    p = lib_pkg.make_params(dict(base, moving=2))
+    assert p.skin == 0.05                 # default skin h / 2
+    p.skin = 0.0                          # moving = 2 needs a positive skin
+    with pytest.raises(lib_pkg.DtsphError) as e:
+        lib_pkg.dtsph_create(p)
+    assert e.value.code == -1
 
 
 def test_struct_layouts_match_header():
     """ctypes mirrors of the C structs have the C sizes (checked by offsets)."""
     P = lib_pkg.dtsph_params
     assert P.lo.offset == 24 and P.h.offset == 72
-    assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 12
+    assert P.moving.offset == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 12 and P.skin.offset % 8 == 0
+    assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 14 + 8
     assert ctypes.sizeof(lib_pkg.dtsph_step_stats) == 24

@@ -529,3 +529,93 @@ def test_call_order_and_argument_errors():
     with pytest.raises(dt.DtsphError):
         dt.dtsph_read_stats(sim.ctx, 0, 1)      # no step taken yet
     sim.close()
+
+
+# ------------------------------------------- moving particles (Algorithm 1)
+
+MOVING_CASES = {
+    "tgv2d_jitter": (lambda: synth.tgv2d(50, seed=1904), 4),
+    "cavity": (lambda: synth.cavity2d(23), 3),
+    "tgv3d": (lambda: synth.tgv3d(12, jitter=0.1, seed=5), 2),
+    "dambreak": (lambda: synth.dambreak2d(12, jitter=0.1, seed=2), 3),
+}
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("moving", [1, 2])
+@pytest.mark.parametrize("case", sorted(MOVING_CASES))
+def test_moving_matches_oracle(case, moving, prec):
+    """Particles moving in pseudo-time (Algorithm 1) against the oracle's
+    moving loop, with the lists of r^0 (moving = 1) or neighbours updated at
+    every pass (moving = 2: the GPU's lists with a skin against the oracle's
+    rebuild): FP64 within 1e-10 with the same iteration counts, FP32C within
+    1e-4."""
+    make, nsteps = MOVING_CASES[case]
+    d = make()
+    over = dict(moving=moving)
+    if case == "dambreak":
+        over.update(alpha=0.1, free_surface=1, shifting=1)
+    box = box_of(d)
+    nf = d["nf"]
+    sim, orc, out = run_pair(d, nsteps, precision=prec, **over)
+    st, rec, x, v, p = out[-1]
+    if prec == dt.DTSPH_FP64:
+        assert [(o[0]["iters"], o[0]["reason"]) for o in out] == [(o[1]["iters"], o[1]["reason"]) for o in out]
+        assert rel(v, orc.v) < 1e-10 and rel(p, orc.p) < 1e-10
+        assert np.max(np.abs(wrap_diff(x, orc.x[:nf], box))) < 1e-10 * np.max(np.abs(orc.x))
+    else:
+        e = rel(v, orc.v)
+        print(f"{case} moving={moving}: FP32C L-inf rel err {e:.2e}")
+        assert e < 1e-4
+    sim.close()
+
+
+def test_moving_one_iteration_equals_frozen_on_gpu():
+    """With one pseudo-iteration the moving pass runs at r^0 with V~ = 0 and adds
+    nothing, so the FP64 moving step gives the bits of the frozen step with one
+    lane per particle (the same summation order)."""
+    d = CASES["tgv2d_jitter"]()
+    a = make_sim(d, fixed_iters=1, lanes=1)
+    b = make_sim(d, fixed_iters=1, moving=1)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.v, b.v) and np.array_equal(a.p, b.p)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_moving_same_bits_in_every_graph_mode(prec):
+    """Plain launches, the while-node graph and graph = 2 (which runs the moving
+    loop as graph = 1) give the same bits."""
+    d = CASES["cavity"]()
+    res = []
+    for g in (0, 1, 2):
+        sim = make_sim(d, precision=prec, graph=g, moving=2)
+        sim.step(3)
+        sim.sync()
+        res.append((sim.x, sim.v, sim.p, [s["iters"] for s in sim.stats(0, 3)]))
+        sim.close()
+    for r in res[1:]:
+        assert all(np.array_equal(u, w) for u, w in zip(r[:3], res[0][:3])) and r[3] == res[0][3]
+
+
+def test_moving_skin_exceeded_is_reported():
+    """moving = 2 with a skin far below the pseudo-time displacement ends the
+    step with DTSPH_E_SKIN on the host (no device fault); the probe of a moving
+    context times the moving pass and leaves the state alone."""
+    d = CASES["tgv2d_jitter"]()
+    sim = make_sim(d, moving=2, skin=1e-9 * d["cfg"]["h"])
+    sim.step(1)
+    with pytest.raises(dt.DtsphError) as e:
+        sim.sync()
+    assert e.value.code == -9
+    sim.close()
+    sim = make_sim(d, moving=1)
+    sim.step(1)
+    sim.sync()
+    x, v = sim.x, sim.v
+    ms, by, npairs = dt.dtsph_probe_iterate(sim.ctx, 2)
+    assert ms > 0 and by > 0 and npairs > 0
+    assert np.array_equal(sim.x, x) and np.array_equal(sim.v, v)
+    sim.close()
