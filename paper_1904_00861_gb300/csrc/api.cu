@@ -337,6 +337,19 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         B.lanes = ch.lanes;
         B.stages = ch.stages;
     }
+    if (c->prm[0].moving && !c->prm[0].steady) {
+        // the moving pass: the lanes asked for, else one lane per particle on
+        // the FP32C path (measured fastest: more lanes add blocks beyond the
+        // resident set and redundant per-lane state loads) and up to four on the
+        // FP64 path (FP64-pipe-bound: more threads help while there are few)
+        int L = c->prm[0].lanes;
+        if (L == 0) {
+            L = 1;
+            if (!B.fp32c)
+                while (L < 4 && (long long)n * L < 400000) L *= 2;
+        }
+        B.lanes = L;
+    }
     const size_t nd = (size_t)n * d;
     const size_t nwarps = ((size_t)n + kWarp - 1) / kWarp;
     const size_t npair = nwarps * B.K * kWarp;

@@ -163,12 +163,15 @@ __global__ void __launch_bounds__(kBlock) k_move_walls(Buffers B)
     else B.nb64[cur][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
 }
 
-// One moving iteration over all slots, one lane per slot and one tile of kBlock
-// slots per block; the last block of an instance applies its stop rules, the
-// last block of all sets the while-node condition (as the frozen iterate kernel).
-template <int D, bool F32>
+// One moving iteration over all slots, L lanes per slot (lane l takes the list
+// entries l, l + L, ...; the partial sums merge by warp shuffles and the first
+// lane updates the particle) and one tile of kBlock / L slots per block; the last
+// block of an instance applies its stop rules, the last block of all sets the
+// while-node condition (as the frozen iterate kernel).
+template <int D, bool F32, int L>
 __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long long cond, int use_cond)
 {
+    constexpr int PPB = kBlock / L;
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
     using A = Ar<T>;
@@ -178,10 +181,10 @@ __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long l
     __shared__ int last, tlo_sh;
     if (!use_cond && B.ctrl->active == 0) return;   // whole grid agrees: nothing to do
     const int n = B.n;
-    const int inst = block_instance(B, blockIdx.x * kBlock);
+    const int inst = block_instance(B, blockIdx.x * PPB);
     LoopState *ls = B.ls + inst;
     int tlo, thi;
-    instance_tiles(B.inst[inst], kBlock, tlo, thi);
+    instance_tiles(B.inst[inst], PPB, tlo, thi);
     const bool mine = (int)blockIdx.x < thi;        // false: a tile made of padding only
     const int it = ls->iter;
     const bool work = mine && !ls->done;
@@ -189,11 +192,12 @@ __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long l
         block_copy(G, B.geo[inst]);
         block_copy(P, B.phys[inst]);
         const int cur = it & 1, nxt = cur ^ 1;
-        const int s = blockIdx.x * kBlock + threadIdx.x;
+        const int s = blockIdx.x * PPB + threadIdx.x / L, lane_in = threadIdx.x % L;
         const bool fl = s < n && B.gid_a[s] < (uint32_t)B.nf;
         double r_ap = 0.0, r_av = 0.0;
+        Acc ap, Fa[3], gp[3];
+        const PairConst<T> k = pair_const<T>(P);
         if (fl) {
-            const PairConst<T> k = pair_const<T>(P);
             const auto *nb = nb_ptr<T>(B, cur);
             const auto qi = nb[s];
             const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
@@ -210,37 +214,107 @@ __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long l
             }
             const float4 oi = F32 ? B.offk[cur][s] : make_float4(0.f, 0.f, 0.f, 0.f);
             const T rc2k = (T)(9.0 * P.h * P.h);
-            Acc ap, Fa[3], gp[3];
             const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
             const int cnt = B.pcount[s];
-            for (int q = 0; q < cnt; ++q) {
-                const size_t e = base + (size_t)q * kWarp;
-                const uint32_t jb = B.pj[e];
-                const int j = (int)(jb & ~kWallBit);
-                T d[3];
-                const T r2 = moved_sep<D, F32, T>(G, B, cur, xi, oi, j, B.pcode[e], d);
-                if (!(r2 < rc2k)) continue;          // outside the kernel support: adds nothing
-                T g[3], F;
-                grad_coef<D, T>(P, d, r2, g, F);
-                const auto qj = nb[j];
-                const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
-                T vd[3] = {vv[0], vv[1], vv[2]};
-                if (jb & kWallBit) {
+            // R entries per round: their indices, then their gathers, then the
+            // pair terms, so that R loads are in flight per lane (the entries
+            // stay in the order lane_in, lane_in + L, ...)
+            constexpr int R = F32 ? 4 : 2;
+            using Q = typename Packed<T>::type;
+            for (int q0 = lane_in; q0 < cnt; q0 += L * R) {
+                uint32_t jbv[R];
+                int codev[R];
 #pragma unroll
-                    for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_a[(size_t)a * n + j];
+                for (int r = 0; r < R; ++r) {
+                    const int q = q0 + r * L;
+                    const size_t e = base + (size_t)min(q, cnt - 1) * kWarp;
+                    jbv[r] = B.pj[e];
+                    codev[r] = B.pcode[e];
                 }
-                const T pj = (T)qj.w;
-                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, pj, ap, Fa);
-                // advective terms of Eqs. (dp-dtau) and (discrete_ME)
-                T tg = T(0);
+                Q qv[R];
+                float4 ov[R];
+                T xj[R][3];
 #pragma unroll
-                for (int a = 0; a < D; ++a) tg = A::fma(ti[a], g[a], tg);
-                const T pp = A::mul(k.c_p, A::add(pi, pj));
+                for (int r = 0; r < R; ++r) {
+                    const int j = (int)(jbv[r] & ~kWallBit);
+                    qv[r] = nb[j];
+                    if (F32) {
+                        ov[r] = B.offk[cur][j];
+                    } else {
 #pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    gp[a].add(A::mul(pp, g[a]));
-                    Fa[a].add(A::mul(A::mul(k.vol, A::add(vi[a], vd[a])), tg));
+                        for (int a = 0; a < D; ++a) xj[r][a] = (T)B.xk[cur][(size_t)a * n + j];
+                    }
                 }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (q0 + r * L >= cnt) break;
+                    const uint32_t jb = jbv[r];
+                    const int j = (int)(jb & ~kWallBit);
+                    T d[3], r2;
+                    if (F32) {
+                        int dx, dy, dz;
+                        decode_shift(codev[r], dx, dy, dz);
+                        float f0, f1, f2;
+                        const float q2 = sep32<D>(shifted_offset<D>(oi, dx, dy, dz, G.s_f), ov[r], f0, f1, f2);
+                        d[0] = (T)f0;
+                        d[1] = (T)f1;
+                        if (D == 3) d[2] = (T)f2;
+                        r2 = (T)q2;
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            double v = __dsub_rn((double)xi[a], (double)xj[r][a]);
+                            if (G.periodic[a]) {
+                                if (v > G.halfL[a]) v = __dsub_rn(v, G.L[a]);
+                                else if (v < -G.halfL[a]) v = __dadd_rn(v, G.L[a]);
+                            }
+                            d[a] = (T)v;
+                        }
+                        r2 = A::add(A::mul(d[0], d[0]), A::mul(d[1], d[1]));
+                        if (D == 3) r2 = A::add(r2, A::mul(d[2], d[2]));
+                    }
+                    if (!(r2 < rc2k)) continue;          // outside the kernel support: adds nothing
+                    T g[3], F;
+                    grad_coef<D, T>(P, d, r2, g, F);
+                    const Q qj = qv[r];
+                    const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
+                    T vd[3] = {vv[0], vv[1], vv[2]};
+                    if (jb & kWallBit) {
+#pragma unroll
+                        for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_a[(size_t)a * n + j];
+                    }
+                    const T pj = (T)qj.w;
+                    pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, pj, ap, Fa);
+                    // advective terms of Eqs. (dp-dtau) and (discrete_ME)
+                    T tg = T(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) tg = A::fma(ti[a], g[a], tg);
+                    const T pp = A::mul(k.c_p, A::add(pi, pj));
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        gp[a].add(A::mul(pp, g[a]));
+                        Fa[a].add(A::mul(A::mul(k.vol, A::add(vi[a], vd[a])), tg));
+                    }
+                }
+            }
+        }
+        // every lane takes part in the merges
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) {
+            ap.shfl_merge(o);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                Fa[a].shfl_merge(o);
+                gp[a].shfl_merge(o);
+            }
+        }
+        if (fl && lane_in == 0) {
+            double xh[3] = {0, 0, 0}, vt[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const size_t q = (size_t)a * n + s;
+                xh[a] = B.xk[cur][q];
+                vt[a] = B.vt[q];
             }
             // update in FP64
             double apv = (double)(T)ap.value();
@@ -370,7 +444,12 @@ int launch_move_iteration(const Buffers &B, unsigned long long cond, int use_con
         DTSPH_DISPATCH(B.dim, B.fp32c, (k_move_walls<D, F32><<<blocks(B.n), kBlock, 0, st>>>(B)));
         ++k;
     }
-    DTSPH_DISPATCH(B.dim, B.fp32c, (k_move_iter<D, F32><<<blocks(B.n), kBlock, 0, st>>>(B, cond, use_cond)));
+    // n is a multiple of kSlotAlign, so the tiles of kBlock / L slots cover it exactly
+    const int L = B.lanes, nb = (int)((long long)B.n * L / kBlock);
+    if (L == 1) DTSPH_DISPATCH(B.dim, B.fp32c, (k_move_iter<D, F32, 1><<<nb, kBlock, 0, st>>>(B, cond, use_cond)));
+    else if (L == 2) DTSPH_DISPATCH(B.dim, B.fp32c, (k_move_iter<D, F32, 2><<<nb, kBlock, 0, st>>>(B, cond, use_cond)));
+    else if (L == 4) DTSPH_DISPATCH(B.dim, B.fp32c, (k_move_iter<D, F32, 4><<<nb, kBlock, 0, st>>>(B, cond, use_cond)));
+    else DTSPH_DISPATCH(B.dim, B.fp32c, (k_move_iter<D, F32, 8><<<nb, kBlock, 0, st>>>(B, cond, use_cond)));
     return k + 1;
 }
 
