@@ -350,14 +350,20 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
             rp.pos += (uint32_t)nch;
         } else {
             const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-            // the cache entry of the next pair is loaded before the current one
-            // is used, so two independent loads are in flight per lane
-            CacheEntry<T, D, F32> nx;
-            if (lane_in < cnt) nx.load(B, base + (size_t)lane_in * kWarp);
-            for (int kk = lane_in; kk < cnt; kk += L) {
-                const CacheEntry<T, D, F32> ce = nx;
-                if (kk + L < cnt) nx.load(B, base + (size_t)(kk + L) * kWarp);
-                pair(ce, nbq[ce.jb & ~kWallBit]);
+            // R entries per round: their cache entries, then their neighbour
+            // gathers, then the pair terms, so R loads of each kind are in flight
+            // per lane (the entries keep the order lane_in, lane_in + L, ...)
+            constexpr int R = 4;
+            for (int k0 = lane_in; k0 < cnt; k0 += L * R) {
+                CacheEntry<T, D, F32> ce[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) ce[r].load(B, base + (size_t)min(k0 + r * L, cnt - 1) * kWarp);
+                Q qv[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) qv[r] = nbq[ce[r].jb & ~kWallBit];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (k0 + r * L < cnt) pair(ce[r], qv[r]);
             }
         }
 #pragma unroll
@@ -461,7 +467,8 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
 // applies its stop rules; the last block of all sets the while-node condition
 // (some instance still iterating).
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock, F32 ? (D == 2 ? 4 : 3) : 1) k_iterate(Buffers B, unsigned long long cond,
+__global__ void __launch_bounds__(kBlock, L == 1 ? (F32 ? (D == 2 ? 4 : 3) : 1) : (F32 ? 3 : 1))
+    k_iterate(Buffers B, unsigned long long cond,
                                                                           int use_cond)
 {
     using T = typename std::conditional<F32, float, double>::type;
@@ -563,7 +570,7 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *er
 // decisions; tiles of finished instances are skipped. Walls get their own phase
 // and barrier before the fluid phase.
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock, (F32 && D == 2) ? 4 : 3) k_loop(Buffers B)
+__global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (F32 ? 3 : 2)) k_loop(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     constexpr int PPB = kBlock / L;
