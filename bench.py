@@ -38,6 +38,19 @@ METRIC = "particle-pseudo-iterations/sec (FP32-comp batched vs plain FP64, same 
 UNIT = "particle-iterations/s"
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# loop kernel, from the Nsight Compute captures summarised under profiles/, for
+# the kernel variants those captures profiled: (workload, dim, lanes, stages) ->
+# (bytes, source). A variant not listed reports null.
+NCU_TRAFFIC = {
+    ("tgv2d-200x200", 2, 2, 0): (19.880704e6, "profiles/k_loop_tgv2d_200x200.md"),
+    ("batch-64x-tgv2d", 2, 1, 2): (7.157555e9 + 0.459921e9, "profiles/k_loop_batch64_tgv2d.md"),
+    ("tgv3d-128^3", 3, 1, 2): ((1.181163e9 + 0.020505e9) * (128 / 80) ** 3,
+                               "profiles/k_loop_tgv3d_80.md, an 80^3 capture scaled by the particle count "
+                               "(one iteration per step, streaming traffic)"),
+}
+
+
 def make_workload(name: str, n_side: int, re: float):
     """Synthetic input and its config record. tgv2d (default, 200 x 200) is the
     workload the metric is quoted on; tgv3d (128^3), cavity (200 x 200 + walls)
@@ -408,6 +421,10 @@ def main_ours(args):
         probe_kernel = f"k_move_walls + k_move_iter<{dims},FP32C> (one lane per particle)"
         loop_kernel = probe_kernel + (" (plain launches)" if args.graph == 0 else
                                       " in the while node (one launch each per iteration)")
+    traffic, traffic_src = None, None
+    key = (wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0)
+    if args.graph == 2 and not args.moving and not args.steady and not args.shifting and key in NCU_TRAFFIC:
+        traffic, traffic_src = NCU_TRAFFIC[key]
     e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -419,7 +436,7 @@ def main_ours(args):
         "iters_per_step_mean": float(np.mean(it32)),
         "fp64": fp64,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": loop_kernel,
+                     "traffic": traffic, "traffic_source": traffic_src, "kernel": loop_kernel,
                      "bytes_per_launch": loop_bytes / len(loop_ms), "launch_ms": sum(loop_ms) / len(loop_ms),
                      "timing": f"CUDA events around the loop of each of the last {len(loop_ms)} timed steps",
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
