@@ -256,6 +256,10 @@ __global__ void __launch_bounds__(kBlock) k_nlist_cells3(Buffers B, const double
     const float sf[3] = {G.s_f[0], G.s_f[1], G.s_f[2]};
     const float rc2_lo = G.rc2_lo, rc2_hi = G.rc2_hi;
     const double rc2 = G.rc2;
+    // squared distance from the home cell beyond which no home particle can
+    // reach a candidate: the band's top with a margin far above the rounding of
+    // FP32 offsets (home offsets lie in [0, s] up to that rounding)
+    const float box_cut2 = rc2_hi * 1.001f;
     const int n = B.n, K = B.K;
     float4 *buf = cand[w];
     uint8_t *cb = ccode[w];
@@ -299,21 +303,40 @@ __global__ void __launch_bounds__(kBlock) k_nlist_cells3(Buffers B, const double
         int cnt = 0;
         int k = 0;                                   // neighbour cell of this lane's next fill position
         for (int c0 = 0; c0 < total; c0 += kCellChunk) {
-            const int take = min(total - c0, kCellChunk);
-            // fill: position p of the stream is candidate p - tpre[k] of cell k
-            for (int q = lane; q < take; q += kWarp) {
-                const int p = c0 + q;
-                while (tpre[w][k + 1] <= p) ++k;
-                const int j = tbeg[w][k] + (p - tpre[w][k]);
-                const float4 oj = B.off[j];
-                const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-                float4 e;
-                e.x = __fadd_rn(oj.x, (float)dx * sf[0]);
-                e.y = __fadd_rn(oj.y, (float)dy * sf[1]);
-                e.z = __fadd_rn(oj.z, (float)dz * sf[2]);
-                e.w = __uint_as_float((uint32_t)j | (oj.w != 0.f ? kWallBit : 0u));
-                buf[q] = e;
-                cb[q] = (uint8_t)k;
+            const int span = min(total - c0, kCellChunk);
+            // fill: position p of the stream is candidate p - tpre[k] of cell k.
+            // A candidate farther than the cutoff from every point of the home
+            // cell (the outer parts of the edge and corner cells, about a
+            // quarter of the stream) is dropped here for the whole warp; the
+            // others keep their order (ballot compaction), so the lists are
+            // those of the full stream
+            int take = 0;
+            for (int q0 = 0; q0 < span; q0 += kWarp) {
+                const int q = q0 + lane;
+                bool keep = false;
+                float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < span) {
+                    const int p = c0 + q;
+                    while (tpre[w][k + 1] <= p) ++k;
+                    const int j = tbeg[w][k] + (p - tpre[w][k]);
+                    const float4 oj = B.off[j];
+                    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+                    e.x = __fadd_rn(oj.x, (float)dx * sf[0]);
+                    e.y = __fadd_rn(oj.y, (float)dy * sf[1]);
+                    e.z = __fadd_rn(oj.z, (float)dz * sf[2]);
+                    e.w = __uint_as_float((uint32_t)j | (oj.w != 0.f ? kWallBit : 0u));
+                    const float bx = fmaxf(fmaxf(-e.x, e.x - sf[0]), 0.f);
+                    const float by = fmaxf(fmaxf(-e.y, e.y - sf[1]), 0.f);
+                    const float bz = fmaxf(fmaxf(-e.z, e.z - sf[2]), 0.f);
+                    keep = bx * bx + by * by + bz * bz < box_cut2;
+                }
+                const unsigned bal = __ballot_sync(full, keep);
+                if (keep) {
+                    const int pos = take + __popc(bal & ((1u << lane) - 1u));
+                    buf[pos] = e;
+                    cb[pos] = (uint8_t)k;
+                }
+                take += __popc(bal);
             }
             // pad to a multiple of four with entries that fail every test
             const int take4 = (take + 3) & ~3;
