@@ -154,9 +154,12 @@ void dtsph_destroy(dtsph_ctx *ctx);
 /* Fluid state at real time t^n (Algorithm 2 starts from it): nf particles with
  * positions x (nf x dim), velocities V^n (nf x dim), pressures p^n (nf) and the
  * previous velocities V^{n-1} for the BDF2 term (NULL: V^{n-1} = V^n, as the
- * paper does without an exact solution, Sec. 3.1). Host pointers. Allocates
- * the device state (sized for nf plus the current walls); resets the step
- * counter. Must come after dtsph_set_boundary if there are walls. */
+ * paper does without an exact solution, Sec. 3.1). Host pointers, each holding
+ * its full size: on a device that reads pageable host memory itself
+ * (cudaDevAttrPageableMemoryAccess, as Grace-based systems do over NVLink-C2C) a
+ * kernel reads them in place, otherwise they are copied with cudaMemcpyAsync.
+ * Allocates the device state (sized for nf plus the current walls); resets the
+ * step counter. Must come after dtsph_set_boundary if there are walls. */
 int dtsph_set_particles(dtsph_ctx *ctx, int64_t nf, const double *x, const double *v,
                         const double *p, const double *v_prev);
 
@@ -210,8 +213,17 @@ int64_t dtsph_step_count(const dtsph_ctx *ctx);
 int dtsph_read_stats(dtsph_ctx *ctx, int64_t first, int32_t count, dtsph_step_stats *out);
 
 /* Copies one field of the fluid particles (DTSPH_FIELD_*) into the host array
- * out, in the caller's particle order. Waits for the stream. */
+ * out (nf x comps doubles), in the caller's particle order: on a device that
+ * writes pageable host memory itself a kernel writes out in place, otherwise
+ * cudaMemcpyAsync does. Waits for the stream. */
 int dtsph_read_field(dtsph_ctx *ctx, int32_t field, double *out);
+
+/* The whole fluid state in the caller's particle order into host arrays: r^n and
+ * V^n (nf x dim), p^n (nf), V^{n-1} (nf x dim); a null pointer skips that field.
+ * One call instead of four dtsph_read_field calls: the fields go through one
+ * device scratch buffer and the call waits for the stream once. Host arrays are
+ * written as by dtsph_read_field. */
+int dtsph_read_state(dtsph_ctx *ctx, double *x, double *v, double *p, double *v_prev);
 
 /* As dtsph_read_field into device memory; enqueued on the context stream. */
 int dtsph_read_field_device(dtsph_ctx *ctx, int32_t field, double *out);

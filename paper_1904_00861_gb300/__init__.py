@@ -70,6 +70,7 @@ _SIGS = [
     ("dtsph_read_stats", C.c_int, [_VP, C.c_int64, C.c_int32, C.POINTER(dtsph_step_stats)]),
     ("dtsph_read_field", C.c_int, [_VP, C.c_int32, _VP]),
     ("dtsph_read_field_device", C.c_int, [_VP, C.c_int32, _VP]),
+    ("dtsph_read_state", C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     ("dtsph_eval_rates", C.c_int, [_VP, _VP, _VP]),
     ("dtsph_build_neighbors", C.c_int, [_VP]),
     ("dtsph_get_neighbors", C.c_int, [_VP, C.c_int64, _I64P, C.c_int64, _I64P]),
@@ -244,9 +245,26 @@ def dtsph_read_stats(ctx, first: int, count: int):
     return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv) for b in buf[:count]]
 
 
-def dtsph_read_field(ctx, field: int, n: int, comps: int) -> np.ndarray:
-    out = np.empty((n, comps) if comps > 1 else n, np.float64)
+def dtsph_read_field(ctx, field: int, n: int, comps: int, out=None) -> np.ndarray:
+    """One field of the n fluid particles, into `out` (a C-contiguous float64
+    host array of n * comps values, e.g. pinned) or a new array."""
+    if out is None:
+        out = np.empty((n, comps) if comps > 1 else n, np.float64)
+    elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size != n * comps:
+        raise ValueError("out must be a C-contiguous float64 array of n * comps values")
     _check(ctx, lib().dtsph_read_field(ctx, int(field), _ptr(out)))
+    return out
+
+
+def dtsph_read_state(ctx, n: int, dim: int, out=None):
+    """(r^n, V^n, p^n, V^{n-1}) of the n fluid particles in one call, into the
+    four C-contiguous float64 host arrays of `out` (e.g. pinned) or new ones."""
+    if out is None:
+        out = (np.empty((n, dim)), np.empty((n, dim)), np.empty(n), np.empty((n, dim)))
+    for a, size in zip(out, (n * dim, n * dim, n, n * dim)):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != size:
+            raise ValueError("out must hold C-contiguous float64 arrays of n*dim, n*dim, n, n*dim values")
+    _check(ctx, lib().dtsph_read_state(ctx, *[_ptr(a) for a in out]))
     return out
 
 

@@ -28,6 +28,11 @@ struct dtsph_ctx {
     cudaStream_t cap = nullptr;         // private stream used for graph capture
     int device = 0;
     bool have_particles = false;
+    // the device reads and writes pageable host memory itself (Grace-based
+    // systems over NVLink-C2C: cudaDevAttrPageableMemoryAccess), so the host
+    // arrays of dtsph_set_particles and dtsph_read_field are accessed in place
+    // by kernels instead of through cudaMemcpyAsync's pageable path
+    bool host_direct = false;
     bool have_nbrs = false;             // dtsph_build_neighbors lists in order B
     std::vector<std::vector<double>> xw_host, vw_host;   // walls per instance
     std::vector<int64_t> nf_set;        // fluid particles per instance of the current allocation
@@ -40,6 +45,7 @@ struct dtsph_ctx {
     std::string err;
     std::vector<void *> allocs;
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
+    double *rd = nullptr;                // dtsph_read_state: the fields in caller order (3 nf dim + nf)
     bool tuned = false;
     int loop_grid = 0;
     // events around the pseudo-time loop of each real step (pair step % kLoopEv),
@@ -734,7 +740,8 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
         if ((r = dalloc(c, &c->sx, (size_t)NF * d)) || (r = dalloc(c, &c->sv, (size_t)NF * d)) ||
             (r = dalloc(c, &c->sp, NF)) || (r = dalloc(c, &c->svp, (size_t)NF * d)) ||
             (r = dalloc(c, &c->sxw, (size_t)std::max<int64_t>(NW, 1) * d)) ||
-            (r = dalloc(c, &c->svw, (size_t)std::max<int64_t>(NW, 1) * d)))
+            (r = dalloc(c, &c->svw, (size_t)std::max<int64_t>(NW, 1) * d)) ||
+            (r = dalloc(c, &c->rd, (size_t)NF * (3 * d + 1))))
             return r;
         if (NW > 0) {
             std::vector<double> xw, vw;
@@ -749,12 +756,17 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
     const size_t bx = (size_t)NF * d * sizeof(double), bp = (size_t)NF * sizeof(double);
     double *svp = vprev ? c->svp : nullptr;
     double *sxw = NW > 0 ? c->sxw : nullptr, *svw = NW > 0 ? c->svw : nullptr;
-    const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(c->sx, x, bx, kind, c->stream));
-    CK(cudaMemcpyAsync(c->sv, v, bx, kind, c->stream));
-    CK(cudaMemcpyAsync(c->sp, p, bp, kind, c->stream));
-    if (vprev) CK(cudaMemcpyAsync(svp, vprev, bx, kind, c->stream));
-    c->launches += launch_scatter_in(c->B, c->sx, c->sv, c->sp, svp, sxw, svw, c->stream);
+    if (!device && c->host_direct) {
+        // the scatter kernel reads the caller's arrays where they are
+        c->launches += launch_scatter_in(c->B, x, v, p, vprev, sxw, svw, c->stream);
+    } else {
+        const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(cudaMemcpyAsync(c->sx, x, bx, kind, c->stream));
+        CK(cudaMemcpyAsync(c->sv, v, bx, kind, c->stream));
+        CK(cudaMemcpyAsync(c->sp, p, bp, kind, c->stream));
+        if (vprev) CK(cudaMemcpyAsync(svp, vprev, bx, kind, c->stream));
+        c->launches += launch_scatter_in(c->B, c->sx, c->sv, c->sp, svp, sxw, svw, c->stream);
+    }
     // a new state restarts the step log and clears device-side error flags
     for (int i = 0; i < ni; ++i) CK(cudaMemsetAsync(&c->B.ls[i].step, 0, sizeof(long long), c->stream));
     CK(cudaMemsetAsync(c->B.err, 0, sizeof(uint32_t), c->stream));
@@ -797,10 +809,35 @@ int read_field_impl(dtsph_ctx *c, int32_t field, double *out, bool device)
     c->launches += launch_unpermute(B, B.gid_a, src, dst, comps, c->stream);
     CK(cudaGetLastError());
     if (!device) {
-        CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
+        if (c->host_direct) c->launches += launch_copy(tmp, out, bytes / sizeof(double), c->stream);
+        else CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaFreeAsync(tmp, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    return DTSPH_OK;
+}
+
+// The fluid state in caller order into host arrays (any may be null): every
+// field is unpermuted into the context's scratch, then copied out, with one
+// wait for the stream at the end.
+int read_state_impl(dtsph_ctx *c, double *x, double *v, double *p, double *vprev)
+{
+    if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
+    const Buffers &B = c->B;
+    const size_t nd = (size_t)B.nf * B.dim;
+    struct Field { double *out; const double *src; int comps; size_t off; };
+    const Field f[4] = {{x, B.x_a, B.dim, 0}, {v, B.vn_a, B.dim, nd}, {p, B.pn_a, 1, 2 * nd},
+                        {vprev, B.vnm1_a, B.dim, 2 * nd + (size_t)B.nf}};
+    for (const Field &q : f)
+        if (q.out) c->launches += launch_unpermute(B, B.gid_a, q.src, c->rd + q.off, q.comps, c->stream);
+    for (const Field &q : f) {
+        if (!q.out) continue;
+        const size_t cnt = (size_t)B.nf * q.comps;
+        if (c->host_direct) c->launches += launch_copy(c->rd + q.off, q.out, cnt, c->stream);
+        else CK(cudaMemcpyAsync(q.out, c->rd + q.off, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
     return DTSPH_OK;
 }
 
@@ -835,11 +872,15 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
     }
     memset(&c->B, 0, sizeof c->B);
     c->stream = (cudaStream_t)stream;
-    if (cudaGetDevice(&c->device) != cudaSuccess || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    int pageable = 0;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return DTSPH_E_CUDA;
     }
+    c->host_direct = pageable == 1;
     c->ev_a.assign(dtsph_ctx::kLoopEv, nullptr);
     c->ev_b.assign(dtsph_ctx::kLoopEv, nullptr);
     for (int k = 0; k < dtsph_ctx::kLoopEv; ++k) {
@@ -1021,6 +1062,13 @@ int dtsph_read_field(dtsph_ctx *c, int32_t field, double *out)
     if (!c) return DTSPH_E_ARG;
     CK(cudaSetDevice(c->device));
     return read_field_impl(c, field, out, false);
+}
+
+int dtsph_read_state(dtsph_ctx *c, double *x, double *v, double *p, double *v_prev)
+{
+    if (!c) return DTSPH_E_ARG;
+    CK(cudaSetDevice(c->device));
+    return read_state_impl(c, x, v, p, v_prev);
 }
 
 int dtsph_read_field_device(dtsph_ctx *c, int32_t field, double *out)

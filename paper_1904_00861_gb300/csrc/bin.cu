@@ -366,6 +366,24 @@ int launch_scatter_in(const Buffers &B, const double *x, const double *v, const 
     return 1;
 }
 
+// Contiguous copy of count doubles between any two buffers the device can
+// address (on devices with pageable-memory access: a caller's host array).
+__global__ void __launch_bounds__(kBlock) k_copy(const double *__restrict__ src, double *__restrict__ dst,
+                                                 size_t count)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) dst[i] = src[i];
+}
+
+int launch_copy(const double *src, double *dst, size_t count, cudaStream_t st)
+{
+    if (count == 0) return 0;
+    const size_t want = (count + kBlock - 1) / kBlock;
+    const int nb = (int)(want < 2048 ? want : 2048);
+    k_copy<<<nb, kBlock, 0, st>>>(src, dst, count);
+    return 1;
+}
+
 int launch_unpermute(const Buffers &B, const uint32_t *gid, const double *src, double *out, int comps, cudaStream_t st)
 {
     k_unpermute<<<blocks(B.n), kBlock, 0, st>>>(B.n, B.nf, comps, gid, src, out);

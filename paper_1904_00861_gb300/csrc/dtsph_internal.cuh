@@ -224,6 +224,8 @@ int launch_loop_reset(const Buffers &B, cudaStream_t st);
 // rows (once per device, before any launch or capture); 0 on success.
 int iterate_prepare();
 int launch_unpermute(const Buffers &B, const uint32_t *gid, const double *src, double *out, int comps, cudaStream_t st);
+// Contiguous copy of count doubles by a kernel (0 launches for count = 0).
+int launch_copy(const double *src, double *dst, size_t count, cudaStream_t st);
 int launch_scatter_in(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,
                       const double *xw, const double *vw, cudaStream_t st);
 // Writes one instance's tables (inst/geo/phys entry i) from values, for callers

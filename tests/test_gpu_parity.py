@@ -637,3 +637,45 @@ def test_moving_skin_exceeded_is_reported():
     assert ms > 0 and by > 0 and npairs > 0
     assert np.array_equal(sim.x, x) and np.array_equal(sim.v, v)
     sim.close()
+
+
+def test_host_and_device_transfers_agree():
+    """dtsph_set_particles / dtsph_read_field with host arrays (read and written
+    in place by kernels where the device accesses pageable memory, through
+    cudaMemcpyAsync elsewhere), pageable or pinned, give the same state as the
+    device-pointer entry points."""
+    torch = pytest.importorskip("torch")
+    d = CASES["cavity"]()
+    nf = d["nf"]
+    a = make_sim(d)
+    a.step(2)
+    a.sync()
+    x = dt.dtsph_read_field(a.ctx, dt.FIELD_POS, nf, 2)
+    v = dt.dtsph_read_field(a.ctx, dt.FIELD_VEL, nf, 2)
+    p = dt.dtsph_read_field(a.ctx, dt.FIELD_P, nf, 1)
+    vp = dt.dtsph_read_field(a.ctx, dt.FIELD_VEL_PREV, nf, 2)
+    xd = torch.empty((nf, 2), dtype=torch.float64, device="cuda")
+    dt.dtsph_read_field_device(a.ctx, dt.FIELD_POS, xd)
+    torch.cuda.synchronize()
+    assert np.array_equal(x, xd.cpu().numpy())
+    pin = torch.empty((nf, 2), dtype=torch.float64, pin_memory=True).numpy()
+    dt.dtsph_read_field(a.ctx, dt.FIELD_VEL, nf, 2, out=pin)
+    assert np.array_equal(pin, v)
+    # the whole state in one call, field by field the same
+    xs, vs, ps, vps = dt.dtsph_read_state(a.ctx, nf, 2)
+    assert all(np.array_equal(u, w) for u, w in ((xs, x), (vs, v), (ps, p), (vps, vp)))
+    # the same state sent from host arrays and from device arrays steps to the same bits
+    b = make_sim(d)
+    dt.dtsph_set_particles(b.ctx, x, v, p, vp)
+    c = make_sim(d)
+    t = [torch.from_numpy(np.ascontiguousarray(u)).cuda() for u in (x, v, p, vp)]
+    torch.cuda.synchronize()
+    dt.dtsph_set_particles_device(c.ctx, nf, *t)
+    b.step(1)
+    c.step(1)
+    b.sync()
+    c.sync()
+    for f, comps in ((dt.FIELD_POS, 2), (dt.FIELD_VEL, 2), (dt.FIELD_P, 1)):
+        assert np.array_equal(dt.dtsph_read_field(b.ctx, f, nf, comps), dt.dtsph_read_field(c.ctx, f, nf, comps))
+    for s in (a, b, c):
+        s.close()
