@@ -75,6 +75,11 @@ __device__ __forceinline__ void listed_sep(const Geom &G, const double *__restri
     }
 }
 
+// listed_sep's FP32C separation with the neighbour's offset oj already loaded
+// (the same operations, so the same bits).
+template <int D, typename T>
+__device__ __forceinline__ void offset_sep(const Geom &G, float4 oi, float4 oj, int code, T *d, T &r2);
+
 // Cell shift of a list entry.
 __device__ __forceinline__ void decode_shift(int code, int &dx, int &dy, int &dz)
 {
@@ -135,6 +140,19 @@ __device__ __forceinline__ void block_copy(T &dst, const T &src)
     for (int w = threadIdx.x; w < (int)(sizeof(T) / 4); w += blockDim.x)
         reinterpret_cast<int *>(&dst)[w] = reinterpret_cast<const int *>(&src)[w];
     __syncthreads();
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void offset_sep(const Geom &G, float4 oi, float4 oj, int code, T *d, T &r2)
+{
+    int dx, dy, dz;
+    decode_shift(code, dx, dy, dz);
+    float f0, f1, f2;
+    const float q2 = sep32<D>(shifted_offset<D>(oi, dx, dy, dz, G.s_f), oj, f0, f1, f2);
+    d[0] = (T)f0;
+    d[1] = (T)f1;
+    if (D == 3) d[2] = (T)f2;
+    r2 = (T)q2;
 }
 
 }  // namespace dtsph

@@ -493,23 +493,51 @@ __global__ void __launch_bounds__(kBlock) k_state_n(Buffers B)
         const float4 oi = F32 && fluid ? B.off[s] : make_float4(0, 0, 0, 0);
         const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
         const int cnt = fluid ? B.pcount[s] : 0;
-        for (int q = lane_in; q < cnt; q += L) {
-            const size_t e = base + (size_t)q * kWarp;
-            const uint32_t jb = B.pj[e];
-            const int j = (int)(jb & ~kWallBit);
-            int dx, dy, dz;
-            decode_shift(B.pcode[e], dx, dy, dz);
-            T d[3], r2;
-            listed_sep<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2);
-            T g[3], F;
-            grad_coef<D, T>(P, d, r2, g, F);
-            const auto qj = nb[j];
-            const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
-            T vd[3] = {vv[0], vv[1], vv[2]};
-            if (WALLS && (jb & kWallBit)) {
-                for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
+        // R entries per round: their indices, then their gathers (neighbour
+        // state and, FP32C, offset), then the pair terms, so that R loads are in
+        // flight per lane; the entries keep their order
+        constexpr int R = 4;
+        using Q = typename Packed<T>::type;
+        for (int q0 = lane_in; q0 < cnt; q0 += L * R) {
+            uint32_t jbv[R];
+            int cv[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const size_t e = base + (size_t)min(q0 + r * L, cnt - 1) * kWarp;
+                jbv[r] = B.pj[e];
+                cv[r] = B.pcode[e];
             }
-            pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
+            Q qv[R];
+            float4 ov[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int j = (int)(jbv[r] & ~kWallBit);
+                qv[r] = nb[j];
+                ov[r] = F32 ? B.off[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (q0 + r * L >= cnt) break;
+                const uint32_t jb = jbv[r];
+                const int j = (int)(jb & ~kWallBit);
+                T d[3], r2;
+                if (F32) {
+                    offset_sep<D, T>(G, oi, ov[r], cv[r], d, r2);
+                } else {
+                    int dx, dy, dz;
+                    decode_shift(cv[r], dx, dy, dz);
+                    listed_sep<D, F32, T>(G, B.x_b, B.off, n, s, j, oi, dx, dy, dz, d, r2);
+                }
+                T g[3], F;
+                grad_coef<D, T>(P, d, r2, g, F);
+                const auto qj = qv[r];
+                const T vv[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
+                T vd[3] = {vv[0], vv[1], vv[2]};
+                if (WALLS && (jb & kWallBit)) {
+                    for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_b[(size_t)a * n + j];
+                }
+                pair_accumulate<D, T, Acc>(k, g, F, vi, pi, vd, vv, (T)qj.w, ap, Fa);
+            }
         }
     }
 #pragma unroll
@@ -599,40 +627,63 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
     const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
     const T sigma = (T)(P.sig_h * P.h);
     const int cnt = B.pcount[s];
-    for (int q = lane_in; q < cnt; q += L) {
-        const size_t e = base + (size_t)q * kWarp;
-        const uint32_t jb = B.pj[e];
-        const int j = (int)(jb & ~kWallBit);
-        int dx, dy, dz;
-        decode_shift(B.pcode[e], dx, dy, dz);
-        T d[3], r2;
-        listed_sep<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2);
-        T c4[4] = {T(0), T(0), T(0), T(0)};
-        if (wall_s) {
-            const T W = Ar<T>::mul(sigma, quintic_w<T>(Ar<T>::mul(sqrt(r2), (T)P.inv_h)));
-            T gr = T(0);
-            for (int a = 0; a < D; ++a) gr += (T)P.g[a] * d[a];
-            c4[0] = W;
-            c4[1] = (T)P.rho0 * gr * W;
-        } else {
-            // layout (gradW, F_ij); FP32C in 2D packs (gx, gy, F_ij, index bits)
-            T g[3], F;
-            grad_coef<D, T>(P, d, r2, g, F);
-            c4[0] = g[0];
-            c4[1] = g[1];
-            if (F32 && D == 2) {
-                c4[2] = F;
-            } else {
-                c4[2] = D == 3 ? g[2] : T(0);
-                c4[3] = F;
-            }
+    // R entries per round, their offsets gathered together (as in k_state_n)
+    constexpr int R = 4;
+    for (int q0 = lane_in; q0 < cnt; q0 += L * R) {
+        uint32_t jbv[R];
+        int cv[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const size_t e = base + (size_t)min(q0 + r * L, cnt - 1) * kWarp;
+            jbv[r] = B.pj[e];
+            cv[r] = B.pcode[e];
         }
-        if (F32) {
-            float4 v = make_float4((float)c4[0], (float)c4[1], (float)c4[2], (float)c4[3]);
-            if (D == 2) v.w = __uint_as_float(jb);
-            B.pc32[e] = v;
-        } else {
-            B.pc64[e] = make_double4_32a((double)c4[0], (double)c4[1], (double)c4[2], (double)c4[3]);
+        float4 ov[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            ov[r] = F32 ? B.off[(int)(jbv[r] & ~kWallBit)] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int q = q0 + r * L;
+            if (q >= cnt) break;
+            const size_t e = base + (size_t)q * kWarp;
+            const uint32_t jb = jbv[r];
+            const int j = (int)(jb & ~kWallBit);
+            T d[3], r2;
+            if (F32) {
+                offset_sep<D, T>(G, oi, ov[r], cv[r], d, r2);
+            } else {
+                int dx, dy, dz;
+                decode_shift(cv[r], dx, dy, dz);
+                listed_sep<D, F32, T>(G, xpos, B.off, n, s, j, oi, dx, dy, dz, d, r2);
+            }
+            T c4[4] = {T(0), T(0), T(0), T(0)};
+            if (wall_s) {
+                const T W = Ar<T>::mul(sigma, quintic_w<T>(Ar<T>::mul(sqrt(r2), (T)P.inv_h)));
+                T gr = T(0);
+                for (int a = 0; a < D; ++a) gr += (T)P.g[a] * d[a];
+                c4[0] = W;
+                c4[1] = (T)P.rho0 * gr * W;
+            } else {
+                // layout (gradW, F_ij); FP32C in 2D packs (gx, gy, F_ij, index bits)
+                T g[3], F;
+                grad_coef<D, T>(P, d, r2, g, F);
+                c4[0] = g[0];
+                c4[1] = g[1];
+                if (F32 && D == 2) {
+                    c4[2] = F;
+                } else {
+                    c4[2] = D == 3 ? g[2] : T(0);
+                    c4[3] = F;
+                }
+            }
+            if (F32) {
+                float4 v = make_float4((float)c4[0], (float)c4[1], (float)c4[2], (float)c4[3]);
+                if (D == 2) v.w = __uint_as_float(jb);
+                B.pc32[e] = v;
+            } else {
+                B.pc64[e] = make_double4_32a((double)c4[0], (double)c4[1], (double)c4[2], (double)c4[3]);
+            }
         }
     }
 }
