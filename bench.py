@@ -193,6 +193,21 @@ def parse():
     return ap.parse_args()
 
 
+def whole_job_rate(work_rank: float, t_rank: float, world: int, device=None):
+    """Whole-job throughput of replicas, one per rank: the work of all ranks
+    (summed) over the slowest rank's time (max over ranks). Returns (rate,
+    slowest time). Needs an initialised process group when world > 1."""
+    if world == 1:
+        return work_rank / t_rank, t_rank
+    import torch
+    import torch.distributed as tdist
+    w = torch.tensor([work_rank], dtype=torch.float64, device=device)
+    t = torch.tensor([t_rank], dtype=torch.float64, device=device)
+    tdist.all_reduce(w, op=tdist.ReduceOp.SUM)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(w.item()) / float(t.item()), float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,15 +392,9 @@ def main_ours(args):
         rate32, ms32, it32, launches, sim32, loop32 = run_gpu_path(dt, torch, d, dt.DTSPH_FP32C, args.steps,
                                                                    args.warmup, flush, args.graph, kern)
     torch.cuda.synchronize()
-    # whole-job throughput: every rank ran the same workload independently
-    t_rank = ms32 * args.steps
-    if world > 1:
-        tt = torch.tensor([t_rank], device="cuda", dtype=torch.float64)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_rank
-    value = world * rate32 * t_rank / t_max
+    # whole-job throughput: every rank ran its replica of the workload
+    t_rank = ms32 * args.steps * 1e-3
+    value, _ = whole_job_rate(rate32 * t_rank, t_rank, world, device="cuda")
     lanes32, tune32 = dt.dtsph_tuning(sim32.ctx)
     stages32, cand32 = dt.dtsph_tuning_candidates(sim32.ctx)
     ms_it, bytes_it, npairs = dt.dtsph_probe_iterate(sim32.ctx, 50)
