@@ -100,7 +100,7 @@ def with_shifting(d, wcfg):
 
 
 def with_steady(d, wcfg, iters):
-    """Steady-state mode (Sec. 2.4, Eq. mom-steady) with a fixed number of
+    """Steady-state mode (Sec. 2.3, Eq. mom-steady) with a fixed number of
     pseudo-iterations per solve, in every instance, for both arms."""
     for x in (d if isinstance(d, list) else [d]):
         x["cfg"] = dict(x["cfg"], steady=1, fixed_iters=iters)

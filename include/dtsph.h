@@ -95,7 +95,7 @@ typedef struct {
                                  then p_i += gradp_i . dr_i, V_i += (gradV_i) dr_i with
                                  grad f_i = sum_j V_j (f_j - f_i) gradW_ij, r_i += dr_i;
                                  0 = off. Instances of a batch share it. */
-    int32_t steady;           /* 1: steady-state mode (Sec. 2.4 "Steady state solutions", Eq.
+    int32_t steady;           /* 1: steady-state mode (Sec. 2.3 "Steady state solutions", Eq.
                                  mom-steady): the particles never move; each dtsph_step runs one
                                  pseudo-time solve from the current state with no real-time
                                  (BDF2) term, the pressure rate of Eq. (dp-dtau-frozen) without

@@ -15,7 +15,7 @@
  * What each function follows:
  *   orc_w / orc_dwdr     quintic spline of Morris et al. (cited in Sec. 3.1 for
  *                        the viscous term); the paper names the kernel only
- *                        (Sec. 5.1) and sets h = dx.
+ *                        (Sec. 4.1) and sets h = dx.
  *   orc_neighbors        N(i) of Sec. 3: all j != i with |r_ij| < 3h (the
  *                        quintic support), minimum image on periodic axes.
  *   orc_rates            frozen EDAC pressure rate, Eq. (dp-dtau-frozen-edac),
@@ -32,7 +32,7 @@
  *                        shift-deltar, shift-correct) of Sec. 3.5 (free-surface
  *                        particles not shifted in free-surface runs, where the
  *                        wall pressure is also kept >= 0, Sec. 3.2). Steady mode
- *                        (Sec. 2.4 "Steady state solutions", Eq. mom-steady):
+ *                        (Sec. 2.3 "Steady state solutions", Eq. mom-steady):
  *                        particles fixed, no BDF2 term, no EDAC term, convection
  *                        term added, the pseudo-time loop as above.
  *                        Moving mode (Algorithm 1, Sec. 2.1 and 3.1 "Moving
@@ -88,7 +88,7 @@ typedef struct {
     int32_t fixed_iters;      /* > 0: exactly this many iterations, no stop rules */
     int32_t use_bruteforce;   /* 1: O(N^2) neighbour search instead of cells */
     int32_t shifting;         /* 1: particle shifting after the real step */
-    int32_t steady;           /* 1: steady-state mode (Sec. 2.4, Eq. mom-steady) */
+    int32_t steady;           /* 1: steady-state mode (Sec. 2.3, Eq. mom-steady) */
     int32_t free_surface;     /* 1: free-surface run: wall pressure kept >= 0 (Sec. 3.2),
                                  free-surface particles not shifted (Sec. 3.5) */
     int32_t moving;           /* 0: particles fixed in pseudo-time (Algorithm 2); 1: moved
@@ -638,7 +638,7 @@ int orc_step(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, 
     nlist_free(&L);
 
     /* predictor, Eqs. (v0, r0); p^0 = p^n. Steady mode: the particles stay and
-       the iteration starts from the state itself (Sec. 2.4) */
+       the iteration starts from the state itself (Sec. 2.3) */
     memcpy(x0, x, (size_t)n * dim * sizeof(double));
     for (int64_t i = 0; i < nf; ++i) {
         for (int a = 0; a < dim; ++a) {

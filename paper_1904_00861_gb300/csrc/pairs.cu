@@ -2,7 +2,7 @@
 // pair pass at the state n, and the pair-coefficient cache that the pseudo-time
 // loop reads (geometry frozen for the whole loop, Sec. 2.2; caching kernel
 // gradients across pseudo-iterations is the speed-up the paper points at in
-// Sec. 5 but did not implement). The lists are built by a test-only kernel and
+// Sec. 4.7 but did not implement). The lists are built by a test-only kernel and
 // walked densely by the others, so the pair arithmetic never runs under the
 // distance test, which most candidates fail.
 //

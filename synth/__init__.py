@@ -8,11 +8,11 @@ published definition (Steele, Lea & Flood, "Fast splittable pseudorandom number
 generators", OOPSLA 2014), so the same seed gives the same inputs on every
 machine.
 
-Workloads (shapes and parameters follow the paper's test cases, Sec. 5):
+Workloads (shapes and parameters follow the paper's test cases, Sec. 4):
   tgv2d    2D Taylor-Green vortex, periodic unit square, jittered lattice,
-           exact initial field of Eq. (tgv_sol) (Sec. 5.1).
+           exact initial field of Eq. (tgv_sol) (Sec. 4.1).
   cavity2d 2D lid-driven cavity, regular lattice, three layers of wall
-           particles, lid moving at U (Sec. 5.2).
+           particles, lid moving at U (Sec. 4.2).
   tgv3d    3D periodic Taylor-Green vortex on [0, 2 pi]^3 (textbook initial
            field; not one of the paper's cases).
   batch    many independent tgv2d instances of uneven sizes and Reynolds

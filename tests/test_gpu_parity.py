@@ -222,7 +222,7 @@ STEADY_CASES = {
 @pytest.mark.parametrize("case", sorted(STEADY_CASES))
 @pytest.mark.parametrize("fixed", [300, 0])
 def test_steady_mode_matches_oracle(case, prec, fixed):
-    """Steady-state mode (Sec. 2.4, Eq. mom-steady): each step is one
+    """Steady-state mode (Sec. 2.3, Eq. mom-steady): each step is one
     pseudo-time solve at fixed positions, no BDF2 and no EDAC term, with the
     convection term. FP64 within 1e-10 of the oracle's steady mode with the
     same iteration counts (fixed count, and the stop rules), FP32C velocities
