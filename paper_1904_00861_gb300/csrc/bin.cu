@@ -57,8 +57,10 @@ __global__ void __launch_bounds__(kBlock) k_bin_keys(Buffers B, const double *__
 // Three passes: per-block totals of kScanCells cells, a scan of those totals by
 // one block, and the final per-cell scan of every block with its offset.
 constexpr int kScanThreads = 1024;
-constexpr int kScanPerThread = 4;
+constexpr int kScanPerThread = 4;                              // cells per thread, several blocks
 constexpr int kScanCells = kScanThreads * kScanPerThread;
+constexpr int kScanPerThread1 = 16;                            // cells per thread, one block
+constexpr int kScanCells1 = kScanThreads * kScanPerThread1;
 
 // Exclusive prefix sum over the block (kScanThreads threads) of one value each.
 __device__ __forceinline__ int block_exclusive_scan(int v)
@@ -139,20 +141,23 @@ __device__ __forceinline__ int cell_instance(const Buffers &B, int c)
     return lo;
 }
 
+// PER cells per thread; MULTI: several blocks, each with the carry of the
+// blocks before it (else one block scans every cell, with no carry)
+template <int PER, bool MULTI>
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(Buffers B)
 {
-    const int base = blockIdx.x * kScanCells + threadIdx.x * kScanPerThread;
-    int v[kScanPerThread];
+    const int base = blockIdx.x * kScanThreads * PER + threadIdx.x * PER;
+    int v[PER];
     int s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanPerThread; ++k) {
+    for (int k = 0; k < PER; ++k) {
         v[k] = base + k < B.ncell ? B.cell_count[base + k] : 0;
         s += v[k];
     }
-    int run = block_exclusive_scan(s) + B.scan_tmp[blockIdx.x];
+    int run = block_exclusive_scan(s) + (MULTI ? B.scan_tmp[blockIdx.x] : 0);
     if (base < B.ncell) {
         int inst = cell_instance(B, base);
-        for (int k = 0; k < kScanPerThread; ++k) {
+        for (int k = 0; k < PER; ++k) {
             const int c = base + k;
             if (c >= B.ncell) break;
             while (inst + 1 < B.ninst && B.inst[inst + 1].cell_off <= c) ++inst;
@@ -338,13 +343,21 @@ inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
 int launch_binning(const Buffers &B, const double *x_keys, const uint32_t *gid_src, cudaStream_t st)
 {
     k_bin_keys<<<blocks(B.n), kBlock, 0, st>>>(B, x_keys, gid_src);
-    const int nsb = (B.ncell + kScanCells - 1) / kScanCells;
-    k_scan_partial<<<nsb, kScanThreads, 0, st>>>(B);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(B, nsb);
-    k_scan_final<<<nsb, kScanThreads, 0, st>>>(B);
+    // up to kScanCells1 cells one block scans them all; more take the block
+    // totals, their scan, and the block scans with their carries
+    int k = 3;
+    if (B.ncell <= kScanCells1) {
+        k_scan_final<kScanPerThread1, false><<<1, kScanThreads, 0, st>>>(B);
+    } else {
+        const int nsb = (B.ncell + kScanCells - 1) / kScanCells;
+        k_scan_partial<<<nsb, kScanThreads, 0, st>>>(B);
+        k_scan_top<<<1, kScanThreads, 0, st>>>(B, nsb);
+        k_scan_final<kScanPerThread, true><<<nsb, kScanThreads, 0, st>>>(B);
+        k += 2;
+    }
     k_scatter<<<blocks(B.n), kBlock, 0, st>>>(B);
     k_cell_rank<<<blocks(B.n), kBlock, 0, st>>>(B, gid_src);
-    return 6;
+    return k + 1;
 }
 
 int launch_permute_a_to_b(const Buffers &B, cudaStream_t st)
