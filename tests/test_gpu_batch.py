@@ -100,3 +100,25 @@ def test_batch_rejects_mixed_dimensions():
     with pytest.raises(dt.DtsphError) as e:
         dt.Batch([a["cfg"], c["cfg"]])
     assert e.value.code == -1
+
+
+def test_full_size_batch_sampled_instances():
+    """The 64-instance batch of the benchmark (1,499,340 particles, graph = 2,
+    FP32C, autotuned lanes), one real step; sampled instances (the first, the
+    largest and the smallest) against the oracle run alone: velocities within
+    1e-4."""
+    insts = synth.batch(64)
+    b = dt.Batch([d["cfg"] for d in insts], precision=dt.DTSPH_FP32C, graph=2)
+    b.set_state(insts)
+    b.step(1)
+    b.sync()
+    vs = b.field(dt.FIELD_VEL)
+    sizes = [d["nf"] for d in insts]
+    for i in sorted({0, int(np.argmax(sizes)), int(np.argmin(sizes))}):
+        d = insts[i]
+        orc = oracle.State(d["cfg"], d["x"], d["v"], d["p"], d["v_prev"], vw=d["vw"], nf=d["nf"])
+        orc.step(1)
+        err = rel(vs[i], orc.v)
+        print(f"instance {i} ({sizes[i]} particles): L-inf rel velocity err {err:.2e}")
+        assert err < 1e-4, i
+    b.close()

@@ -418,20 +418,40 @@ def test_steps_fp32c_linf(case, nsteps):
 
 def test_full_size_taylor_green_200sq():
     """The 200^2 Taylor-Green workload in the benchmark's launch configuration
-    (graph-captured loop): FP64 against the oracle at 1e-10 and FP32C at 1e-4,
-    over 3 real steps."""
+    (graph = 2: one persistent loop kernel per step, autotuned lanes): FP64
+    against the oracle at 1e-10 and FP32C at 1e-4, over 3 real steps."""
     d = synth.tgv2d(200)
-    sim, orc, out = run_pair(d, 3)
+    sim, orc, out = run_pair(d, 3, graph=2)
     for st, rec, *_ in out:
         assert st["iters"] == rec["iters"]
     assert rel(out[-1][3], orc.v) < 1e-10 and rel(out[-1][4], orc.p) < 1e-10
     sim.close()
-    sim32 = make_sim(d, precision=dt.DTSPH_FP32C)
+    sim32 = make_sim(d, precision=dt.DTSPH_FP32C, graph=2)
     sim32.step(3)
     err = rel(sim32.v, orc.v)
     print(f"200^2 FP32C L-inf rel velocity err after 3 steps: {err:.2e}")
     assert err < 1e-4
     sim32.close()
+
+
+def test_full_size_taylor_green_3d_128():
+    """The 128^3 3D Taylor-Green workload (2,097,152 particles) in the
+    benchmark's launch configuration, one real step against the oracle's full
+    step: FP64 with the same iteration count within 1e-10, FP32C within 1e-4."""
+    d = synth.tgv3d(128)
+    orc = make_oracle(d)
+    rec = orc.step(1)[0]
+    for prec, tol in ((dt.DTSPH_FP64, 1e-10), (dt.DTSPH_FP32C, 1e-4)):
+        sim = make_sim(d, precision=prec, graph=2)
+        sim.step(1)
+        sim.sync()
+        st = sim.stats(0, 1)[0]
+        if prec == dt.DTSPH_FP64:
+            assert st["iters"] == rec["iters"]
+        err = rel(sim.v, orc.v)
+        print(f"128^3 precision {prec}: L-inf rel velocity err after 1 step {err:.2e}")
+        assert err < tol
+        sim.close()
 
 
 # -------------------------------------------------------------- invariants
