@@ -1,0 +1,48 @@
+"""Host-side checks of bench.py's contract: the metric is the configured one,
+every workload builds its synthetic input and names itself, and each DRAM
+traffic figure the bench reports comes from a committed profile that gives it."""
+import json
+import os
+import re
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_metric_is_the_configured_one():
+    cfg = json.load(open(os.path.join(ROOT, "BASELINE.json")))
+    assert bench.METRIC == cfg["metric"]
+
+
+@pytest.mark.parametrize("name,n", [("tgv2d", 20), ("cavity", 20), ("tgv3d", 12), ("batch", 3), ("dambreak", 12)])
+def test_workloads_build_and_name_themselves(name, n):
+    d, wcfg = bench.make_workload(name, n, 0.0)
+    insts = d if isinstance(d, list) else [d]
+    assert wcfg["workload"] and wcfg["dims"] in (2, 3)
+    for x in insts:
+        nf = x["nf"]
+        assert x["x"].shape[0] >= nf and x["v"].shape == (nf, wcfg["dims"]) and x["p"].shape == (nf,)
+
+
+def test_default_run_is_one_gpu_and_short(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.warmup >= 3 and a.steps <= 200 and a.impl == "ours"
+
+
+def test_traffic_figures_come_from_committed_profiles():
+    for (workload, dim, lanes, stages), (byts, src) in bench.NCU_TRAFFIC.items():
+        path = os.path.join(ROOT, src.split(",")[0])
+        assert os.path.exists(path), path
+        txt = open(path).read()
+        assert "dram__bytes_read" in txt
+        # the profile gives the read figure the bench uses (MB or GB, up to rounding)
+        vals = [float(v) * (1e9 if u == "G" else 1e6)
+                for v, u in re.findall(r"dram__bytes_read\.sum\s*=?\s*([0-9.]+)\s*([MG])[Bb]", txt)]
+        assert vals, path
+        assert any(0.5 * v <= byts for v in vals), path
