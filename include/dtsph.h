@@ -84,8 +84,10 @@ typedef struct {
                                  loop is one persistent cooperative kernel (grid barrier per
                                  iteration); 0: plain launches, host polls every 8 iterations */
     int32_t lanes;            /* lanes per particle in the pseudo-iteration kernel: 1, 2, 4
-                                 or 8; 0 = picked by the built-in autotuner after the first
-                                 step (timed candidates, cached per shape in the process) */
+                                 or 8; 0 = picked by the built-in autotuner when the particles
+                                 are first set (timed candidates, cached per shape in the
+                                 process). With moving != 0, the lanes of the moving pass; 0 =
+                                 one on FP32C, up to four on FP64 (no tuning) */
     int32_t stages;           /* staging depth of the one-lane kernel (lanes = 1): pair-cache
                                  chunks in flight per warp in shared memory, 2..8; 0 = 3, or
                                  picked by the autotuner together with lanes */
