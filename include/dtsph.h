@@ -1,7 +1,8 @@
 /*
  * dtsph.h - C ABI of the GB300 (sm_103a) library for the inner pseudo-time
  * iteration of the dual-time EDAC-SPH scheme with particles frozen in pseudo-time
- * (Ramachandran, Muta & Ramakrishna, arXiv:1904.00861, Algorithm 2).
+ * (Ramachandran, Muta & Ramakrishna, arXiv:1904.00861, Algorithm 2), or moved in
+ * pseudo-time (Algorithm 1, dtsph_params.moving).
  *
  * Conventions shared by every entry point:
  *  - Return value: DTSPH_OK (0) on success, a negative DTSPH_E_* code otherwise;
@@ -51,7 +52,7 @@ typedef enum {
                          residual reduction in FP64 */
 } dtsph_precision;
 
-/* Parameters of one simulation (Sec. 3.4 and 5 of the paper). Derived values:
+/* Parameters of one simulation (Sec. 3.4 and the test cases of Sec. 4). Derived values:
  * c = beta * v_ref, nu_e = h c / 16 (Eq. nu_edac), dtau = dt / beta. */
 typedef struct {
     int32_t dim;              /* 2 or 3 */
