@@ -81,3 +81,25 @@ def test_struct_layouts_match_header():
     assert P.moving.offset == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 12 and P.skin.offset % 8 == 0
     assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 14 + 8
     assert ctypes.sizeof(lib_pkg.dtsph_step_stats) == 24
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built CUDA library the product path raises; there is no CPU
+    fallback."""
+    monkeypatch.setattr(lib_pkg, "LIB_PATH", os.path.join(ROOT, "_build_missing", "libdtsph.so"))
+    monkeypatch.setattr(lib_pkg, "_lib", None)
+    with pytest.raises(ImportError, match="not built"):
+        lib_pkg.lib()
+    cfg = dict(dim=2, h=0.1, m=0.01, nu=0.01, dt=0.01)
+    with pytest.raises(ImportError):
+        lib_pkg.Simulation(cfg)
+
+
+def test_product_package_does_not_load_the_oracle():
+    """The package and its binding import nothing from oracle/ (test
+    infrastructure only)."""
+    import subprocess
+    import sys
+    code = "import sys, paper_1904_00861_gb300; assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
