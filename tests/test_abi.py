@@ -103,3 +103,20 @@ def test_product_package_does_not_load_the_oracle():
     code = "import sys, paper_1904_00861_gb300; assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)"
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle includes only system headers, and no library source includes or
+    imports anything from oracle/."""
+    import glob
+    src = open(os.path.join(ROOT, "oracle", "dtsph_oracle.c")).read()
+    for inc in re.findall(r'#include\s*(\S+)', src):
+        assert inc.startswith("<"), inc
+    lib_files = glob.glob(os.path.join(ROOT, "paper_1904_00861_gb300", "**", "*.*"), recursive=True)
+    lib_files = [f for f in lib_files if f.endswith((".cu", ".cuh", ".h", ".py")) and "_build" not in f]
+    assert lib_files
+    for f in lib_files:
+        for line in open(f).read().splitlines():
+            s = line.strip()
+            if s.startswith(("#include", "import ", "from ")):
+                assert "oracle" not in s, (f, s)
