@@ -712,3 +712,40 @@ def test_moving_with_neighbour_update_sees_pairs_that_enter_the_support():
     assert not np.array_equal(runs[1, 0], runs[2, 0])
     assert np.max(np.abs(runs[1, 0] - runs[2, 0])) < 1e-12
     assert np.array_equal(runs[2, 0], runs[2, 1])
+
+
+# ------------------------------------------------- artificial viscosity (NEXT-4)
+
+def _av_force(cfg, x, v, **over):
+    """The artificial-viscosity part of F: F(alpha) - F(0), p = 0, nu = 0."""
+    p = np.zeros(len(x))
+    _, F1, _, _ = oracle.rates(cfg, x, v, p, nu=0.0, **over)
+    _, F0, _, _ = oracle.rates(cfg, x, v, p, nu=0.0, **dict(over, alpha=0.0))
+    return F1 - F0
+
+
+def test_artificial_viscosity_structure():
+    """Eqs. (mom-av, av-phiij): Pi_ij acts on approaching pairs only (a uniform
+    expansion feels nothing, a uniform compression does), is linear in alpha,
+    Galilean invariant, proportional to the sound speed c (c_ij = c, doubling
+    beta doubles it), and depends on m / rho0 (rho_ij = rho0): doubling both m and
+    rho0 changes nothing. A sign slip in the switch, a v_i + v_j for v_ij, a
+    missing or squared 1/rho fails one of these."""
+    d = synth.tgv2d(20, jitter=0.1, seed=5)
+    x = d["x"]
+    cfg = dict(d["cfg"], periodic=(0, 0, 0), lo=(-1.0, -1.0, 0.0), hi=(2.0, 2.0, 1.0))
+    xc = x - x.mean(0)
+    expand, compress = 0.7 * xc, -0.7 * xc
+    assert np.array_equal(_av_force(cfg, x, expand, alpha=0.1), np.zeros_like(x))
+    Fc = _av_force(cfg, x, compress, alpha=0.1)
+    assert np.max(np.abs(Fc)) > 0.0
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=x.shape)
+    Fa = _av_force(cfg, x, v, alpha=0.1)
+    scale = np.max(np.abs(Fa))
+    assert scale > 0.0
+    assert np.max(np.abs(_av_force(cfg, x, v, alpha=0.2) - 2 * Fa)) < 1e-12 * scale
+    assert np.max(np.abs(_av_force(cfg, x, v + np.array([3.0, -2.0]), alpha=0.1) - Fa)) < 1e-10 * scale
+    assert np.max(np.abs(_av_force(cfg, x, v, alpha=0.1, beta=2 * cfg["beta"]) - 2 * Fa)) < 1e-12 * scale
+    cfg2 = dict(cfg, m=2 * cfg["m"], rho0=2 * cfg["rho0"])
+    assert np.max(np.abs(_av_force(cfg2, x, v, alpha=0.1) - Fa)) < 1e-12 * scale
