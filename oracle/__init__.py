@@ -76,34 +76,61 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
 
 
+def compile_source(src: str, out_path: str) -> str:
+    """Compiles oracle C source text with the flags of build() into out_path."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as f:
+        f.write(src)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", c_path, "-o",
+            out_path, "-lm"]
+    try:
+        subprocess.run(base[:6] + ["-fopenmp"] + base[6:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True)
+    return out_path
+
+
+def source() -> str:
+    """The oracle's C source text."""
+    with open(_SRC) as f:
+        return f.read()
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB_PATH)
-        dp = C.POINTER(C.c_double)
-        i64p = C.POINTER(C.c_int64)
-        P = C.POINTER(OrcParams)
-        L.orc_w.restype = C.c_double
-        L.orc_w.argtypes = [C.c_double, C.c_double, C.c_int]
-        L.orc_dwdr.restype = C.c_double
-        L.orc_dwdr.argtypes = [C.c_double, C.c_double, C.c_int]
-        L.orc_neighbors.restype = C.c_int64
-        L.orc_neighbors.argtypes = [P, C.c_int64, dp, i64p, i64p, C.c_int64]
-        L.orc_rates.restype = C.c_int
-        L.orc_rates.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_rates_vt.restype = C.c_int
-        L.orc_rates_vt.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_stop_reason.restype = C.c_int
-        L.orc_stop_reason.argtypes = [P, C.c_int32, dp, dp]
-        L.orc_step.restype = C.c_int
-        L.orc_step.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.POINTER(OrcStats), dp, dp, dp]
-        L.orc_run.restype = C.c_int
-        L.orc_run.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.c_int32, C.POINTER(OrcStats)]
-        L.orc_num_threads.restype = C.c_int
-        L.orc_set_num_threads.argtypes = [C.c_int]
-        _lib = L
+        _lib = bind(_LIB_PATH)
     return _lib
+
+
+def bind(path: str):
+    """Loads a compiled copy of the oracle and declares its entry points."""
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    i64p = C.POINTER(C.c_int64)
+    P = C.POINTER(OrcParams)
+    L.orc_w.restype = C.c_double
+    L.orc_w.argtypes = [C.c_double, C.c_double, C.c_int]
+    L.orc_dwdr.restype = C.c_double
+    L.orc_dwdr.argtypes = [C.c_double, C.c_double, C.c_int]
+    L.orc_neighbors.restype = C.c_int64
+    L.orc_neighbors.argtypes = [P, C.c_int64, dp, i64p, i64p, C.c_int64]
+    L.orc_rates.restype = C.c_int
+    L.orc_rates.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_rates_vt.restype = C.c_int
+    L.orc_rates_vt.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_stop_reason.restype = C.c_int
+    L.orc_stop_reason.argtypes = [P, C.c_int32, dp, dp]
+    L.orc_step.restype = C.c_int
+    L.orc_step.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.POINTER(OrcStats), dp, dp, dp]
+    L.orc_run.restype = C.c_int
+    L.orc_run.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.c_int32, C.POINTER(OrcStats)]
+    L.orc_shift.restype = C.c_int
+    L.orc_shift.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp]
+    L.orc_num_threads.restype = C.c_int
+    L.orc_set_num_threads.argtypes = [C.c_int]
+    return L
 
 
 # ---------------------------------------------------------------- marshalling
@@ -201,6 +228,22 @@ def rates(cfg: dict, x, v, p, vw=None, nf=None, vt=None, **over):
                           _dp(ap), _dp(F), _dp(pw), _dp(vg)):
         raise MemoryError("oracle rates failed")
     return ap[:nf], F[:nf], pw[:nw], vg[:nw]
+
+
+def shift(cfg: dict, x, v, p, nf=None, **over):
+    """Particle shifting alone (Sec. 3.5, Eqs. shift-deltar and shift-correct)
+    at a given state: neighbour lists at x (fluid then walls), the shift of every
+    fluid particle and the Taylor correction of V and p. Returns the shifted
+    fluid positions and the corrected (V, p); the inputs are not changed."""
+    P = make_params(cfg, **over)
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    p = _f64(p).copy()
+    nf = v.shape[0] if nf is None else nf
+    nw = x.shape[0] - nf
+    if lib().orc_shift(C.byref(P), nf, nw, _dp(x), _dp(v), _dp(p)):
+        raise MemoryError("oracle shift failed")
+    return x[:nf], v, p
 
 
 def stop_reason(cfg: dict, hist_p, hist_v, **over):

@@ -581,6 +581,19 @@ static void shift(const orc_params *P, int64_t nf, double *x, double *v, double 
     free(gp);
 }
 
+/* Exported for the tests: particle shifting alone (Sec. 3.5) on a given state,
+ * with the neighbour lists built at x. x holds nf fluid then nw wall positions;
+ * v (nf*dim) and p (nf) are corrected and the fluid positions shifted in place.
+ * Returns 0, or -1 on allocation failure. */
+int orc_shift(const orc_params *P, int64_t nf, int64_t nw, double *x, double *v, double *p)
+{
+    nlist L;
+    if (build_neighbors(P, nf + nw, x, &L)) return -1;
+    shift(P, nf, x, v, p, &L);
+    nlist_free(&L);
+    return 0;
+}
+
 /* ------------------------------------------------------------- real step */
 
 /* One real step n -> n+1 of Algorithm 2.

@@ -441,6 +441,72 @@ def test_shifting_is_zero_on_a_lattice_and_reduces_disorder():
     assert np.abs(st.x - lat).mean() < 0.9 * before
 
 
+def _open_box(cfg):
+    """The same particles in a box with no periodic axis, large enough that the
+    unit square sits well inside it (interior particles see a full support)."""
+    return dict(cfg, periodic=(0, 0, 0), lo=(-1.0, -1.0, 0.0), hi=(2.0, 2.0, 1.0))
+
+
+def test_shifting_taylor_correction_carries_linear_fields():
+    """Eq. (shift-correct): after a shift dr_i, the corrected values
+    phi_i + (grad phi)_i . dr_i of a linear field phi match phi at the new
+    positions to the accuracy of the SPH gradient on a jittered lattice (a few
+    percent of the uncorrected mismatch |grad phi . dr_i|), for p and for every
+    component of V, each with its own gradient. A dropped correction (ratio 1), a
+    flipped sign (ratio 2), or the gradient of another field (V's for p, one
+    velocity component's for another) fails."""
+    d = synth.tgv2d(40, jitter=0.1, seed=11)
+    cfg = _open_box(d["cfg"])
+    x = d["x"]
+    h = cfg["h"]
+    gp = np.array([1.3, -0.7])
+    A = np.array([[0.5, -1.1], [0.8, 0.3]])
+    b = np.array([0.2, -0.1])
+    p_of = lambda r: 0.4 + r @ gp
+    v_of = lambda r: r @ A.T + b
+    xs, vs, ps = oracle.shift(cfg, x, v_of(x), p_of(x))
+    inner = np.all((x > 4 * h) & (x < 1 - 4 * h), axis=1)
+    dr = np.linalg.norm(xs - x, axis=1)
+    assert np.mean(dr[inner]) > 0.02 * cfg["dx"]           # the shift is not trivially small
+    # corrected mismatch against the uncorrected one, summed over the interior
+    p_corr = np.abs(ps - p_of(xs))[inner].sum()
+    p_unc = np.abs(p_of(x) - p_of(xs))[inner].sum()
+    assert p_corr < 0.1 * p_unc
+    for a in range(2):
+        v_corr = np.abs(vs[:, a] - v_of(xs)[:, a])[inner].sum()
+        v_unc = np.abs(v_of(x)[:, a] - v_of(xs)[:, a])[inner].sum()
+        assert v_corr < 0.1 * v_unc, a
+
+
+def test_shifting_displacement_matches_its_continuum_limit():
+    """Eq. (shift-deltar) with D = h^2/2 against its continuum limit: on a
+    lattice stretched smoothly along x (x = X + a sin 2 pi X, number density
+    n(x) known in closed form), sum_j V_j gradW_ij -> V grad n and sum_j V_j W_ij
+    gradW_ij -> V grad n (integral of W^2) / 2, so dr = -(h^2/2)(1 + int W^2 dA /
+    (2 W(h))) V grad n, with int W^2 dA by quadrature. The kernel is resolved by
+    two particle spacings (h = 2 dx) so that the lattice sums reach the continuum
+    to under 1%. A missing 1/2 (ratio 2), a dropped 1 or a dropped W_ij/W(h) in
+    the factor (ratios 0.40, 0.60) or a flipped sign fails."""
+    n, a = 64, 0.01
+    dx = 1.0 / n
+    X = (np.arange(n) + 0.5) * dx
+    XX, YY = np.meshgrid(X, X)
+    XX, YY = XX.ravel(), YY.ravel()
+    x = np.stack([XX + a * np.sin(2 * np.pi * XX), YY], 1)
+    cfg = dict(synth.tgv2d(n, jitter=0.0)["cfg"], h=2.0 * dx)
+    h, vol = cfg["h"], cfg["m"] / cfg["rho0"]
+    xs, _, _ = oracle.shift(cfg, x, np.zeros_like(x), np.zeros(len(x)))
+    n0 = 1.0 / dx ** 2
+    grad_n = n0 * 4 * np.pi ** 2 * a * np.sin(2 * np.pi * XX) / (1 + 2 * np.pi * a * np.cos(2 * np.pi * XX)) ** 3
+    w2 = integrate.quad(lambda r: 2 * np.pi * r * oracle.w(r, h, 2) ** 2, 0, 3 * h, points=[h, 2 * h], limit=200)[0]
+    expect = -(h * h / 2) * (1 + w2 / (2 * oracle.w(h, h, 2))) * vol * grad_n
+    got = xs[:, 0] - x[:, 0]
+    ratio = np.sum(got * expect) / np.sum(expect * expect)
+    assert abs(ratio - 1.0) < 0.03
+    assert np.max(np.abs(got - expect)) < 0.03 * np.max(np.abs(expect))
+    assert np.max(np.abs(xs[:, 1] - x[:, 1])) < 1e-12 * h     # no shift across the stretching
+
+
 # -------------------------------------------------------------- steady state
 
 def test_steady_convection_operator_against_closed_form():
@@ -749,3 +815,29 @@ def test_artificial_viscosity_structure():
     assert np.max(np.abs(_av_force(cfg, x, v, alpha=0.1, beta=2 * cfg["beta"]) - 2 * Fa)) < 1e-12 * scale
     cfg2 = dict(cfg, m=2 * cfg["m"], rho0=2 * cfg["rho0"])
     assert np.max(np.abs(_av_force(cfg2, x, v, alpha=0.1) - Fa)) < 1e-12 * scale
+
+
+def test_artificial_viscosity_magnitude_against_its_continuum_limit():
+    """Eqs. (mom-av, av-phiij), absolute size: for u = -gamma x - kappa x^2, v = 0
+    every pair approaches, the even part of v_ij . r_ij cancels over the lattice,
+    and -sum_j m Pi_ij gradW_ij tends to alpha h c kappa (3 pi / 4) int_0^{3h} r^4
+    W'(r) / (r^2 + eta h^2) dr in x (0 in y), the integral by quadrature. The
+    kernel is resolved by 1.5 spacings (h = 1.5 dx) so the lattice sum reaches
+    the continuum to about 1%. A missing h_ij (off by 1/h), the denominator r^2 +
+    h^2 (ratio 0.60), a flipped sign or c^2 for c fails."""
+    n = 50
+    d = synth.tgv2d(n, jitter=0.0)
+    x = d["x"]
+    cfg = dict(_open_box(d["cfg"]), h=1.5 * d["cfg"]["dx"])
+    h, eta = cfg["h"], cfg["eta"]
+    c = cfg["beta"] * cfg["v_ref"]
+    gamma, kappa, alpha = 1.0, 0.5, 0.1
+    v = np.stack([-gamma * x[:, 0] - kappa * x[:, 0] ** 2, np.zeros(len(x))], 1)
+    Fa = _av_force(cfg, x, v, alpha=alpha)
+    inner = np.all((x > 4 * h) & (x < 1 - 4 * h), axis=1)
+    moment = integrate.quad(lambda r: r ** 4 * oracle.dwdr(r, h, 2) / (r * r + eta * h * h), 0, 3 * h,
+                            points=[h, 2 * h], limit=200)[0]
+    expect = alpha * h * c * kappa * (3 * np.pi / 4) * moment
+    assert abs(np.mean(Fa[inner, 0]) / expect - 1.0) < 0.03
+    assert np.max(np.abs(Fa[inner, 0] - expect)) < 0.03 * abs(expect)
+    assert np.max(np.abs(Fa[inner, 1])) < 1e-9 * abs(expect)
