@@ -1,20 +1,26 @@
 """Benchmark: particle-pseudo-iterations per second of the frozen EDAC-DTSPH
 hot path on one GB300 (or N independent replicas, one per GPU).
 
-Workload (default): 2D Taylor-Green vortex, periodic unit square, 200 x 200 =
-40,000 particles on a lattice jittered by +-0.1 dx (seed 1904), Re = 100, quintic
-kernel h = dx, beta = 10, dt = 0.25 h, eps = 1e-3. One "step" is one real time
-step: neighbour rebuild, state-n rates and predictor, the pseudo-time loop until
-the convergence test of the paper holds, and the position update. The metric
+Workload (default): the batched ensemble the metric is quoted on, 64
+independent 2D periodic Taylor-Green instances with side counts drawn uniformly
+from 32..256 (seed 861; 1,499,340 particles in all), Re log-uniform in
+[100, 1000], lattices jittered by +-0.1 dx, quintic kernel h = dx, beta = 10,
+dt = 0.25 h, eps = 1e-3, FP32-compensated, all instances in one persistent
+loop launch per real step inside a CUDA graph, lanes and staging depth
+autotuned. One "step" is one real time step of every instance: neighbour
+rebuild, state-n rates and predictor, the pseudo-time loop until the
+convergence test of the paper holds, and the position update. The metric
 counts fluid particles times pseudo-iterations actually taken.
 
 The FP32-compensated path gives `value`; the plain FP64 GPU path is timed in the
-same run on the same steps ("fp64" key), and the L-inf relative velocity error of
-FP32C against it is reported. `e2e` times the same steps through the C ABI with
-host arrays (state copied in, step, state copied out). `cpu_baseline` times the
-FP64 C oracle on the host cores on a bounded sample of the same workload.
+same run on the same steps ("fp64" key). The FP64 oracle runs the same warm-up
+plus timed steps on the host cores; the L-inf relative velocity error of both
+GPU paths against it (`linf_vs_oracle`) and the oracle's own rate
+(`cpu_baseline`) come from that run. `e2e` times the same steps through the C
+ABI with host arrays (state copied in, step, state copied out).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batch|tgv2d|tgv3d|cavity|dambreak]
 """
 from __future__ import annotations
 
@@ -52,10 +58,10 @@ NCU_TRAFFIC = {
 
 
 def make_workload(name: str, n_side: int, re: float):
-    """Synthetic input and its config record. tgv2d (default, 200 x 200) is the
-    workload the metric is quoted on; tgv3d (128^3), cavity (200 x 200 + walls)
-    and batch (64 Taylor-Green instances of 32^2..256^2 particles, Re 100..1000)
-    are the other single-GPU configurations; dambreak (a 200 x 400 water column
+    """Synthetic input and its config record. batch (default: 64 Taylor-Green
+    instances of 32^2..256^2 particles, Re 100..1000) is the workload the metric
+    is quoted on; tgv2d (200 x 200), tgv3d (128^3) and cavity (200 x 200 +
+    walls, Re 100 or 1000) are the other single-GPU configurations; dambreak (a 200 x 400 water column
     in a tank, free surface, artificial viscosity 0.1, shifting, eps 1e-4, as
     in the 2D dam break of Sec. 4) measures the free-surface runs."""
     if name == "tgv2d":
@@ -67,10 +73,13 @@ def make_workload(name: str, n_side: int, re: float):
         d = synth.tgv3d(n, re=re or 1600.0)
         cfg = dict(workload=f"tgv3d-{n}^3", particles=n ** 3, re=re or 1600.0, dims=3)
     elif name == "cavity":
+        # particle shifting on, as in the paper's test cases: without it the
+        # particles the lid drags into the corner pass through the side wall
         n = n_side or 200
         d = synth.cavity2d(n, re=re or 100.0)
+        d["cfg"].update(shifting=1)
         cfg = dict(workload=f"cavity2d-{n}x{n}", particles=n * n, wall_particles=len(d["x"]) - d["nf"],
-                   re=re or 100.0, dims=2)
+                   re=re or 100.0, dims=2, shifting="on (Eqs. shift-deltar, shift-correct, after every real step)")
     elif name == "batch":
         count = n_side or 64
         d = synth.batch(count)
@@ -169,16 +178,20 @@ class Job:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tgv2d", choices=["tgv2d", "tgv3d", "cavity", "batch", "dambreak"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "tgv2d", "tgv3d", "cavity", "dambreak"])
     ap.add_argument("--n-side", type=int, default=0,
                     help="particles per side, or instances for batch (0: the workload's default)")
     ap.add_argument("--re", type=float, default=0.0, help="Reynolds number (0: the workload's default)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle run (no cpu_baseline and no L-inf against the oracle)")
+    ap.add_argument("--trace", type=int, default=0,
+                    help="after the timed run, rerun the same steps untimed and record the kinetic energy every "
+                         "TRACE steps and the iterations of every step (FP32C)")
+    ap.add_argument("--peaks", action="store_true", help="only measure the FP32 and FP64 FMA peaks and print them")
     ap.add_argument("--graph", type=int, default=2, help="2: step graph with the persistent loop kernel; "
                     "1: step graph with a while node; 0: plain launches (per-kernel profiling)")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
@@ -218,23 +231,27 @@ def dist_env():
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    """nvidia-smi clock and throttle-reason samples during the timed region,
+    written to a temporary file that is removed afterwards."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
         self.idx = gpu_index
+        self.period = period_ms
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = None
+        self.rows = []
 
     def __enter__(self):
+        import tempfile
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix="dtsph_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -248,25 +265,30 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.f.close()
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    self.rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        if self.path:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
 
     def summary(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
+        rows = self.rows
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "period_ms": self.period}
 
 
 # ----------------------------------------------------------------- our arm
@@ -331,38 +353,86 @@ def run_e2e(dt, torch, d, precision, steps, graph=2, kern=None):
             "ms_per_step": 1e3 * t / steps, "host_buffers": "pinned, sent and read in place"}
 
 
+def run_trace(dt, d, steps, every, graph=2, kern=None):
+    """The same steps again, untimed (FP32C): iterations and stop reason of
+    every step of every instance, and the kinetic energy (1/2) sum m |V|^2 of all
+    fluid particles every `every` steps (t = step x dt of the first instance)."""
+    job = Job(dt, d, dt.DTSPH_FP32C, graph=graph, kern=kern)
+    insts = d if isinstance(d, list) else [d]
+    m = np.concatenate([np.full(x["nf"], x["cfg"]["m"]) for x in insts])
+    dt0 = insts[0]["cfg"]["dt"]
+    ke = []
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        job.step(k)
+        done += k
+        v = job.velocities()
+        ke.append([done * dt0, float(0.5 * np.sum(m[:, None] * v * v))])
+    job.sync()
+    its = job.iterations(0, steps)
+    job.close()
+    per_step = np.array(its).max(0)
+    return {"steps": steps, "kinetic_energy": ke, "iters_per_step_max_over_instances": per_step.tolist(),
+            "iters_first_10": per_step[:10].tolist(), "iters_last_10": per_step[-10:].tolist(),
+            "iters_mean": float(np.mean(its))}
+
+
 def oracle_states(d, **over):
     import oracle
     insts = d if isinstance(d, list) else [d]
     return [oracle.State(x["cfg"], x["x"], x["v"], x["p"], x["v_prev"], vw=x["vw"], nf=x["nf"], **over) for x in insts]
 
 
-def cpu_baseline(d, seconds, label):
-    """The FP64 oracle as it stands on the host cores: real steps of the same
-    workload (every instance of a batch in turn) until `seconds` of wall time
-    have passed (at least one round). Above 200k particles in one instance a
-    real step is capped at 2 pseudo-iterations."""
+def oracle_run(d, nsteps, label):
+    """The FP64 oracle as it stands on the host cores: `nsteps` real steps of
+    every instance of the workload (instance by instance), timed. Returns the
+    final velocities (instances concatenated), the iterations of every step of
+    every instance, and the cpu_baseline record of the run."""
     import oracle
     oracle.build()
-    big = max(x["nf"] for x in (d if isinstance(d, list) else [d])) > 200000
-    states = oracle_states(d, **(dict(fixed_iters=2) if big else {}))
+    states = oracle_states(d)
     t0 = time.perf_counter()
     work = 0.0
-    rounds = 0
-    iters = 0
-    while True:
-        for st in states:
-            it = st.step(1)[0]["iters"]
-            iters += it
-            work += st.nf * it
-        rounds += 1
-        if time.perf_counter() - t0 > seconds:
-            break
+    iters = []
+    for st in states:
+        recs = st.step(nsteps)
+        iters.append([r["iters"] for r in recs])
+        work += st.nf * sum(r["iters"] for r in recs)
     t = time.perf_counter() - t0
-    what = "real steps capped at 2 pseudo-iterations" if big else "real steps"
-    return {"value": work / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {rounds} {what} of every instance of the same {label} run ({iters} pseudo-iterations, "
-                      f"{t:.1f} s wall)"}
+    v = np.concatenate([st.v for st in states])
+    tot_it = int(sum(map(sum, iters)))
+    rec = {"value": work / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"the first {nsteps} real steps of every instance of the same {label} run ({tot_it} "
+                     f"pseudo-iterations, {t:.1f} s wall): the run the L-inf errors compare against"}
+    return v, iters, rec
+
+
+def linf_rel(v, ref):
+    return float(np.max(np.abs(v - ref)) / np.max(np.abs(ref)))
+
+
+# Algorithmic bytes of one pseudo-iteration in the pair-cache form: per fluid
+# particle its own state (V and p read and written, the BDF2 source read), per
+# cached pair the neighbour index, gradW and F_ij, by path and dimension.
+STATE_BYTES = {(2, True): 52.0, (3, True): 72.0, (2, False): 88.0, (3, False): 120.0}
+PAIR_BYTES = {(2, True): 16.0, (3, True): 20.0, (2, False): 28.0, (3, False): 36.0}
+
+
+def fp64_flops(dim):
+    """FP64 flops (FMA = 2) of the FP64 pseudo-iteration, counted from the pair
+    terms (EDAC on, no artificial viscosity): per cached pair the divergence
+    and EDAC terms of dp/dtau and the pressure and viscous terms of F,
+    8 dim + 9; per fluid particle the BDF2 pseudo-acceleration, the update and
+    the residual terms, 8 dim + 3."""
+    return 8.0 * dim + 3.0, 8.0 * dim + 9.0
+
+
+def measure_peaks(dt):
+    return {"fp32_fma_tflops": dt.dtsph_fma_peak(dt.DTSPH_FP32C) / 1e12,
+            "fp64_fma_tflops": dt.dtsph_fma_peak(dt.DTSPH_FP64) / 1e12,
+            "how": "dtsph_fma_peak: 8 blocks of 256 threads per SM, 8 independent FMA chains per thread, "
+                   "best of 3 launches of ~50 ms, CUDA events"}
 
 
 def main_ours(args):
@@ -372,10 +442,13 @@ def main_ours(args):
     import paper_1904_00861_gb300 as dt
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1904_00861_gb300 import build as b
     b.build()
+    if args.peaks:
+        print(json.dumps(measure_peaks(dt)))
+        return
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     d, wcfg = make_workload(args.workload, args.n_side, args.re)
     if args.shifting:
         with_shifting(d, wcfg)
@@ -398,32 +471,51 @@ def main_ours(args):
     lanes32, tune32 = dt.dtsph_tuning(sim32.ctx)
     stages32, cand32 = dt.dtsph_tuning_candidates(sim32.ctx)
     ms_it, bytes_it, npairs = dt.dtsph_probe_iterate(sim32.ctx, 50)
-    fp64 = None
-    linf = None
-    if not args.no_fp64:
-        rate64, ms64, it64, _, sim64, _ = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup, flush,
-                                                       args.graph, kern)
-        v32, v64 = sim32.velocities(), sim64.velocities()
-        linf = float(np.max(np.abs(v32 - v64)) / np.max(np.abs(v64)))
-        ms_it64, bytes_it64, _ = dt.dtsph_probe_iterate(sim64.ctx, 20)
-        fp64 = {"value": rate64 * world, "ms_per_step": ms64, "iters_per_step_mean": float(np.mean(it64)),
-                "iterate_kernel_ms": ms_it64, "speedup_fp32c_over_fp64": value / (rate64 * world)}
-        sim64.close()
+    v32 = sim32.velocities()
+    dims = wcfg["dims"]
+    nf_tot = float(sum(sim32.nfs))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved_probe = bytes_it / (ms_it * 1e-3) / 1e9
-    # the dominant kernel of the timed steps is the pseudo-time loop: its bytes
-    # per step are the per-iteration bytes of the pair pass (state + cache
-    # entries, per fluid particle) times the particle-iterations of the step
-    nf_tot = float(sum(sim32.nfs))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+    fma = measure_peaks(dt)
+
+    fp64 = None
+    v64 = None
+    if not args.no_fp64:
+        rate64, ms64, it64, _, sim64, loop64 = run_gpu_path(dt, torch, d, dt.DTSPH_FP64, args.steps, args.warmup,
+                                                            flush, args.graph, kern)
+        v64 = sim64.velocities()
+        ms_it64, bytes_it64, npairs64 = dt.dtsph_probe_iterate(sim64.ctx, 20)
+        lanes64, _ = dt.dtsph_tuning(sim64.ctx)
+        # the FP64 loop is bound by the FP64 pipe: algorithmic FP64 flops of the
+        # timed loops over their device time, against the measured FP64 FMA peak
+        f_part, f_pair = fp64_flops(dims)
+        w64, lms64 = loop64
+        flops64 = float(np.sum(w64)) * (f_part + f_pair * npairs64 / nf_tot)
+        ach64 = flops64 / (sum(lms64) * 1e-3) / 1e12
+        fp64 = {"value": rate64 * world, "ms_per_step": ms64, "iters_per_step_mean": float(np.mean(it64)),
+                "iterate_kernel_ms": ms_it64, "speedup_fp32c_over_fp64": value / (rate64 * world),
+                "roofline": {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": fma["fp64_fma_tflops"],
+                             "unit": "TFLOP/s", "frac": ach64 / fma["fp64_fma_tflops"],
+                             "kernel": f"k_loop<{dims},FP64,lanes={lanes64}>",
+                             "flops_per_launch": flops64 / len(lms64), "launch_ms": sum(lms64) / len(lms64),
+                             "flops_counted": f"{f_part:.0f} per particle-iteration + {f_pair:.0f} per pair-iteration "
+                                              f"(FMA = 2), {npairs64 / nf_tot:.2f} pairs per particle",
+                             "peak_source": "dtsph_fma_peak(FP64), measured in this run"}}
+        sim64.close()
+    # the dominant kernel of the timed steps is the pseudo-time loop: its
+    # algorithmic bytes per step are the state and cache-entry bytes of one
+    # pair pass per particle-iteration of the step
     loop_work, loop_ms = loop32
-    loop_bytes = bytes_it * float(np.sum(loop_work)) / nf_tot
+    per_it = STATE_BYTES[(dims, True)] + PAIR_BYTES[(dims, True)] * npairs / nf_tot
+    loop_bytes = per_it * float(np.sum(loop_work))
     achieved = loop_bytes / (sum(loop_ms) * 1e-3) / 1e9
-    dims = wcfg["dims"]
+    probe_bytes = STATE_BYTES[(dims, True)] * nf_tot + PAIR_BYTES[(dims, True)] * npairs
+    achieved_probe = probe_bytes / (ms_it * 1e-3) / 1e9
     loop_kernel = {2: f"k_loop<{dims},FP32C,lanes={lanes32}> (persistent loop, one launch per step)",
                    1: f"k_iterate<{dims},FP32C,lanes={lanes32}> in the while node (one launch per iteration)",
                    0: f"k_iterate<{dims},FP32C,lanes={lanes32}> (plain launches)"}[args.graph]
@@ -437,32 +529,51 @@ def main_ours(args):
     if args.graph == 2 and not args.moving and not args.steady and not args.shifting and key in NCU_TRAFFIC:
         traffic, traffic_src = NCU_TRAFFIC[key]
     e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)
+    trace = run_trace(dt, d, args.warmup + args.steps, args.trace, args.graph, kern) if args.trace else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+kahan/f64", "data": "synthetic (seeded lattice, closed-form initial field)",
         "config": dict(wcfg, precision="FP32C", parallelism=f"replicas{world}",
                        l2="flushed before every step (256 MB write)"),
-        "linf_rel_vel_err_vs_fp64": linf,
+        "linf_vs_oracle": None,
+        "linf_fp32c_vs_fp64_gpu": None if v64 is None else linf_rel(v32, v64),
         "iters_per_step_mean": float(np.mean(it32)),
         "fp64": fp64,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "traffic_source": traffic_src, "kernel": loop_kernel,
                      "bytes_per_launch": loop_bytes / len(loop_ms), "launch_ms": sum(loop_ms) / len(loop_ms),
+                     "bytes_counted": f"{STATE_BYTES[(dims, True)]:.0f} B per particle-iteration + "
+                                      f"{PAIR_BYTES[(dims, True)]:.0f} B per pair-iteration, "
+                                      f"{npairs / nf_tot:.2f} pairs per particle",
                      "timing": f"CUDA events around the loop of each of the last {len(loop_ms)} timed steps",
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
+                     "peak_source": hbm_src},
         "iterate_probe": {"kernel": probe_kernel, "achieved": achieved_probe,
-                          "frac": achieved_probe / hbm, "bytes_per_launch": bytes_it, "launch_ms": ms_it,
-                          "pairs": npairs, "timing": "50 launches after the timed region, CUDA events"},
+                          "frac": achieved_probe / hbm, "bytes_per_launch": probe_bytes, "launch_ms": ms_it,
+                          "pairs": npairs, "timing": "50 launches after the timed region, every instance active, "
+                                                     "CUDA events"},
+        "fma_peaks": fma,
         "autotune": {"lanes_per_particle": lanes32, "stages": stages32, "ms_by_lanes": tune32,
                      "candidates": [{"lanes": L, "stages": S, "ms": m} for L, S, m in cand32]},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if trace is not None:
+        out["trace"] = trace
     sim32.close()
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds, wcfg["workload"])
+        vo, it_o, rec = oracle_run(d, args.warmup + args.steps, wcfg["workload"])
+        out["cpu_baseline"] = rec
+        # the GPU paths' iterations of the timed steps against the oracle's
+        it_o_timed = [its[args.warmup:] for its in it_o]
+        out["linf_vs_oracle"] = {"fp32c": linf_rel(v32, vo), "fp64": None if v64 is None else linf_rel(v64, vo),
+                                 "after_real_steps": args.warmup + args.steps,
+                                 "fp32c_same_iterations_as_oracle": bool(np.array_equal(np.array(it32),
+                                                                                         np.array(it_o_timed))),
+                                 "fp64_same_iterations_as_oracle": None if args.no_fp64 else
+                                 bool(np.array_equal(np.array(it64), np.array(it_o_timed))),
+                                 "measure": "max |V_gpu - V_oracle| / max |V_oracle| over every fluid particle"}
     if world > 1:
         tdist.barrier()
         tdist.destroy_process_group()

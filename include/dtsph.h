@@ -19,6 +19,15 @@
  *    (NULL = the legacy default stream). A context is not thread-safe.
  *  - Non-convergence of the pseudo-time loop is not an error: it is reported in
  *    dtsph_step_stats.reason, following the stop rules of Sec. 3.4.
+ *  - Two environment variables serve tests of the failure paths and are unset
+ *    in normal use; both are read when a context allocates its particle state.
+ *    DTSPH_TEST_ALLOC_LIMIT (bytes): device allocations of the context beyond
+ *    it fail with DTSPH_E_OOM. DTSPH_TEST_BARRIER_WAIT_NS: give-up time of the
+ *    persistent loop's grid barrier (default one second); a step whose barrier
+ *    gave up is reported by dtsph_sync as DTSPH_E_TIMEOUT.
+ *  - DTSPH_TUNE_CACHE (a file name, optional): the autotuner's choices persist
+ *    there across processes, keyed by device, dim, precision, slots, instances
+ *    and loop driver; a shape found in the file is not timed again.
  */
 #ifndef DTSPH_H
 #define DTSPH_H
@@ -59,8 +68,10 @@ typedef struct {
     int32_t precision;        /* dtsph_precision */
     int32_t periodic[3];      /* 1 = periodic axis; a periodic axis needs hi - lo >= 9h */
     int32_t pad0;
-    double lo[3], hi[3];      /* domain box; periodic axes wrap to [lo, hi); on the
-                                 other axes every particle must stay inside */
+    double lo[3], hi[3];      /* domain box; on a periodic axis positions are kept in
+                                 [lo, hi) (input positions outside it are brought in by
+                                 whole box lengths); on the other axes every particle
+                                 must stay inside */
     double h;                 /* smoothing length; the quintic kernel has support 3h */
     double m;                 /* particle mass (uniform) */
     double rho0;              /* density, held fixed (Sec. 3) */
@@ -93,10 +104,11 @@ typedef struct {
                                  chunks in flight per warp in shared memory, 2..8; 0 = 3, or
                                  picked by the autotuner together with lanes */
     int32_t shifting;         /* 1: particle shifting after every real step (Sec. 3.5, Eqs.
-                                 shift-deltar, shift-correct): at the new positions, over fluid
-                                 neighbours, dr_i = -(h^2/2) sum_j V_j (1 + W_ij / W(h)) gradW_ij,
-                                 then p_i += gradp_i . dr_i, V_i += (gradV_i) dr_i with
-                                 grad f_i = sum_j V_j (f_j - f_i) gradW_ij, r_i += dr_i;
+                                 shift-deltar, shift-correct): at the new positions,
+                                 dr_i = -(h^2/2) sum_j V_j (1 + W_ij / W(h)) gradW_ij over every
+                                 neighbour (wall particles included), then p_i += gradp_i . dr_i,
+                                 V_i += (gradV_i) dr_i with grad f_i = sum_j V_j (f_j - f_i)
+                                 gradW_ij over fluid neighbours, r_i += dr_i;
                                  0 = off. Instances of a batch share it. */
     int32_t steady;           /* 1: steady-state mode (Sec. 2.3 "Steady state solutions", Eq.
                                  mom-steady): the particles never move; each dtsph_step runs one
@@ -136,6 +148,9 @@ typedef struct {
                          4 fixed iteration count reached */
     double rp;        /* mean|dp/dtau| dt / (rho0 c^2) of the last iteration, Eq. (conv) */
     double rv;        /* mean|dt dV/dtau| / v_ref of the last iteration, Eq. (conv) */
+    double vmax;      /* max |V^{n+1}| over the fluid particles at the end of the step
+                         (before shifting): the decay diagnostic of the Taylor-Green
+                         runs (Sec. 4.1) */
 } dtsph_step_stats;
 
 enum {
@@ -162,11 +177,15 @@ void dtsph_destroy(dtsph_ctx *ctx);
  * (cudaDevAttrPageableMemoryAccess, as Grace-based systems do over NVLink-C2C) a
  * kernel reads them in place, otherwise they are copied with cudaMemcpyAsync.
  * Allocates the device state (sized for nf plus the current walls); resets the
- * step counter. Must come after dtsph_set_boundary if there are walls. */
+ * step counter. Must come after dtsph_set_boundary if there are walls. A
+ * coordinate on a periodic axis outside [lo, hi) is brought into it by whole box
+ * lengths (walls too); a non-finite position gives DTSPH_E_ARG (a non-finite
+ * velocity or pressure is not an error here: the first step stops with reason 3). */
 int dtsph_set_particles(dtsph_ctx *ctx, int64_t nf, const double *x, const double *v,
                         const double *p, const double *v_prev);
 
-/* As dtsph_set_particles with device pointers; enqueued on the context stream. */
+/* As dtsph_set_particles with device pointers; enqueued on the context stream
+ * (a non-finite position is then reported by dtsph_sync as DTSPH_E_ARG). */
 int dtsph_set_particles_device(dtsph_ctx *ctx, int64_t nf, const double *x, const double *v,
                                const double *p, const double *v_prev);
 
@@ -203,8 +222,9 @@ int dtsph_batch_set_particles(dtsph_ctx *ctx, const int64_t *nf, const double *x
 /* dtsph_read_stats for instance inst. */
 int dtsph_batch_read_stats(dtsph_ctx *ctx, int32_t inst, int64_t first, int32_t count, dtsph_step_stats *out);
 
-/* Waits for the stream, then reports a device-side error of the steps enqueued
- * so far (DTSPH_E_CAPACITY, DTSPH_E_DOMAIN) or DTSPH_OK. */
+/* Waits for the stream, then reports a device-side error of the work enqueued
+ * so far (DTSPH_E_ARG for a non-finite input position, DTSPH_E_CAPACITY,
+ * DTSPH_E_DOMAIN, DTSPH_E_TIMEOUT, DTSPH_E_SKIN) or DTSPH_OK. */
 int dtsph_sync(dtsph_ctx *ctx);
 
 /* Number of real steps taken since dtsph_set_particles (host-side count). */
@@ -267,6 +287,15 @@ int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, 
  * counterpart; it serves measurement (the loop's share of a step). */
 int dtsph_loop_times(dtsph_ctx *ctx, int64_t first, int32_t count, float *ms);
 
+/* Measurement entry: the vector FMA throughput of the current device in FLOP/s
+ * (an FMA counts two), FP64 (precision = DTSPH_FP64) or FP32 (DTSPH_FP32C): every
+ * SM runs eight 256-thread blocks of eight independent multiply-add chains per
+ * thread, timed with CUDA events on a private stream, best of three launches of
+ * about 50 ms each. Allocates and frees a few KB of device memory; waits for its
+ * work. The paper has no counterpart; it is the compute ceiling of the roofline
+ * for kernels bound by FP32 or FP64 arithmetic. */
+int dtsph_fma_peak(int32_t precision, double *flop_per_s);
+
 /* Autotuner report: the lanes per particle the iterate kernel uses, and (if
  * ms_by_lanes is not NULL, 4 floats) the best time measured for 1, 2, 4 and 8
  * lanes when this context tuned (per launch, or per loop iteration with
@@ -291,14 +320,22 @@ int dtsph_tuning_candidates(const dtsph_ctx *ctx, int32_t cap, int32_t *lanes, i
  * code called where a synchronous allocation could stall the host thread. The
  * paper has no counterpart; it computes what dtsph_eval_rates computes (the two
  * rates of Eqs. dp-dtau-frozen-edac and mom-sph-frozen for every fluid particle,
- * walls extrapolated first) without a context and without any device allocation.
- *   params     simulation parameters (as for dtsph_create; graph, lanes ignored)
+ * walls extrapolated first, with the same reading of every parameter: steady,
+ * free_surface, alpha, edac, moving's list cutoff) without a context and without
+ * any device allocation.
+ *   params     simulation parameters, checked as by dtsph_create
  *   nf, x, v, p   fluid positions (nf x dim), velocities (nf x dim), pressures (nf):
  *              device pointers, row-major AoS, FP64
  *   nw, xw, vw wall positions and prescribed velocities (device; vw may be NULL)
  *   ap, F      outputs, device: dp/dtau (nf) and the momentum right-hand side
  *              (nf x dim), in the caller's particle order
- *   stream     cudaStream_t or NULL; the call only enqueues work and returns
+ *   status     optional device int32 (may be NULL): after the call's GPU work it
+ *              holds DTSPH_OK, DTSPH_E_CAPACITY (a particle had more neighbours
+ *              than the neighbour capacity; its list was cut there and its rates
+ *              are wrong) or DTSPH_E_DOMAIN (a particle lay outside the box of a
+ *              non-periodic axis)
+ *   stream     cudaStream_t or NULL; it must belong to the current device. The
+ *              call only enqueues work and returns.
  * All work happens in one fixed scratch array of about 20 MB that is part of the
  * library image and that every GPU using the library holds until the process
  * exits. Limits: nf + nw <= 16384 particles, at most 32768 cells of side 3h, and
@@ -308,12 +345,11 @@ int dtsph_tuning_candidates(const dtsph_ctx *ctx, int32_t cap, int32_t *lanes, i
  * up the array's device address (once per device, with that device current): make
  * that first call before any stream capture. Every call reuses the same array, so
  * calls whose GPU work can overlap (different streams or threads) race and corrupt
- * each other; calls ordered on one stream are safe. A particle outside the box of
- * a non-periodic axis, or one with more neighbours than the neighbour capacity
- * (its list is cut there), is not reported by this entry (nothing is read back). */
+ * each other; calls ordered on one stream are safe. Returns DTSPH_E_ARG for a
+ * stream of another device. */
 int dtsph_eval_rates_noalloc(const dtsph_params *params, int64_t nf, const double *x, const double *v,
                              const double *p, int64_t nw, const double *xw, const double *vw, double *ap,
-                             double *F, void *stream);
+                             double *F, int32_t *status, void *stream);
 
 /* Kernel launches this context has made so far (counted on the host; a graph
  * launch counts the kernels it runs, pseudo-iterations included). */

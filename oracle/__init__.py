@@ -126,6 +126,8 @@ def bind(path: str):
     L.orc_step.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.POINTER(OrcStats), dp, dp, dp]
     L.orc_run.restype = C.c_int
     L.orc_run.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp, dp, dp, C.c_int32, C.POINTER(OrcStats)]
+    L.orc_prepare_positions.restype = C.c_int
+    L.orc_prepare_positions.argtypes = [P, C.c_int64, dp]
     L.orc_shift.restype = C.c_int
     L.orc_shift.argtypes = [P, C.c_int64, C.c_int64, dp, dp, dp]
     L.orc_num_threads.restype = C.c_int
@@ -262,6 +264,8 @@ class State:
         self.P = make_params(cfg, **over)
         dim = self.P.dim
         self.x = _f64(x).copy()
+        if lib().orc_prepare_positions(C.byref(self.P), self.x.shape[0], _dp(self.x)):
+            raise ValueError("a particle position is not finite")
         self.v = _f64(v).copy()
         self.nf = self.v.shape[0] if nf is None else nf
         self.nw = self.x.shape[0] - self.nf

@@ -171,6 +171,27 @@ static void wrap(const orc_params *P, double *r)
     }
 }
 
+/* Input positions: every coordinate must be finite; on a periodic axis a
+ * coordinate outside [lo, hi) is brought into it, x - floor((x - lo) / L) L, then
+ * once more by one L if rounding left it on the edge. The other axes are left as
+ * given. x holds n particles. Returns 0, or -1 if a coordinate is not finite. */
+int orc_prepare_positions(const orc_params *P, int64_t n, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < P->dim; ++a) {
+            double *xa = x + i * P->dim + a;
+            if (!isfinite(*xa)) return -1;
+            if (!P->periodic[a] || (*xa >= P->lo[a] && *xa < P->hi[a])) continue;
+            double L = P->hi[a] - P->lo[a];
+            double q = floor((*xa - P->lo[a]) / L);
+            *xa = *xa - q * L;
+            if (*xa >= P->hi[a]) *xa = *xa - L;
+            else if (*xa < P->lo[a]) *xa = *xa + L;
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------- neighbours */
 
 /* CSR neighbour lists: for particle i, idx[start[i] .. start[i+1]) holds every
@@ -529,7 +550,9 @@ int orc_stop_reason(const orc_params *P, int32_t k_plus_1, const double *hist_p,
 /* --------------------------------------------------------------- shifting */
 
 /* Sec. 3.5: dr_i = -(h^2/2) sum_j (m_j/rho_j)(1 + W_ij / W(dx, h)) gradW_ij with
- * dx = h, then phi_i' = phi_i + (grad phi)_i . dr_i for V and p, using
+ * dx = h over every neighbour j (wall particles included: they continue the
+ * particle distribution, so a particle next to a wall is not pushed into it),
+ * then phi_i' = phi_i + (grad phi)_i . dr_i for V and p, using
  * (grad phi)_i = sum_j (m_j/rho_j)(phi_j - phi_i) gradW_ij (fluid neighbours). */
 static void shift(const orc_params *P, int64_t nf, double *x, double *v, double *p, const nlist *L)
 {
@@ -551,10 +574,16 @@ static void shift(const orc_params *P, int64_t nf, double *x, double *v, double 
             double dwdr = orc_dwdr(r, h, dim);
             double W = orc_w(r, h, dim);
             if (r > 0.0) divr = divr - vol * dwdr * r;     /* r_ij . gradW_ij = dW/dr r */
-            if (j >= nf) continue;
+            /* the displacement counts every neighbour, wall particles included
+               (they continue the particle distribution); the gradients of the
+               Taylor correction use fluid neighbours only */
             for (int a = 0; a < dim; ++a) {
                 double gw = r > 0.0 ? dwdr * d[a] / r : 0.0;
                 dr[i * dim + a] = dr[i * dim + a] + vol * (1.0 + W / wdx) * gw;
+            }
+            if (j >= nf) continue;
+            for (int a = 0; a < dim; ++a) {
+                double gw = r > 0.0 ? dwdr * d[a] / r : 0.0;
                 gp[i * dim + a] = gp[i * dim + a] + vol * (p[j] - p[i]) * gw;
                 for (int b = 0; b < dim; ++b)
                     gv[(i * dim + b) * dim + a] = gv[(i * dim + b) * dim + a] + vol * (v[j * dim + b] - v[i * dim + b]) * gw;

@@ -23,6 +23,8 @@ ERRORS = {
     -5: "DTSPH_E_CAPACITY", -6: "DTSPH_E_DOMAIN", -7: "DTSPH_E_UNSUPPORTED", -8: "DTSPH_E_TIMEOUT",
     -9: "DTSPH_E_SKIN",
 }
+for _code, _name in ERRORS.items():
+    globals()[_name] = _code
 DTSPH_FP64, DTSPH_FP32C = 0, 1
 FIELD_POS, FIELD_VEL, FIELD_P, FIELD_VEL_PREV = 0, 1, 2, 3
 REASONS = {0: "converged", 1: "stagnated", 2: "max_iter", 3: "nonfinite", 4: "fixed"}
@@ -49,7 +51,8 @@ class dtsph_params(C.Structure):
 
 
 class dtsph_step_stats(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rp", C.c_double), ("rv", C.c_double)]
+    _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rp", C.c_double), ("rv", C.c_double),
+                ("vmax", C.c_double)]
 
 
 _lib = None
@@ -84,8 +87,9 @@ _SIGS = [
     ("dtsph_batch_set_particles", C.c_int, [_VP, _I64P, _VP, _VP, _VP, _VP]),
     ("dtsph_batch_read_stats", C.c_int, [_VP, C.c_int32, C.c_int64, C.c_int32, C.POINTER(dtsph_step_stats)]),
     ("dtsph_kernel_launches", C.c_int64, [_VP]),
+    ("dtsph_fma_peak", C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
     ("dtsph_eval_rates_noalloc", C.c_int, [C.POINTER(dtsph_params), C.c_int64, _VP, _VP, _VP, C.c_int64, _VP, _VP,
-                                           _VP, _VP, _VP]),
+                                           _VP, _VP, _VP, _VP]),
 ]
 
 
@@ -204,7 +208,7 @@ def dtsph_batch_set_particles(ctx, nf, x, v, p, v_prev=None) -> None:
 def dtsph_batch_read_stats(ctx, inst: int, first: int, count: int):
     buf = (dtsph_step_stats * max(count, 1))()
     _check(ctx, lib().dtsph_batch_read_stats(ctx, int(inst), int(first), int(count), buf))
-    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv) for b in buf[:count]]
+    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv, vmax=b.vmax) for b in buf[:count]]
 
 
 def dtsph_destroy(ctx) -> None:
@@ -242,7 +246,7 @@ def dtsph_step_count(ctx) -> int:
 def dtsph_read_stats(ctx, first: int, count: int):
     buf = (dtsph_step_stats * max(count, 1))()
     _check(ctx, lib().dtsph_read_stats(ctx, int(first), int(count), buf))
-    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv) for b in buf[:count]]
+    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv, vmax=b.vmax) for b in buf[:count]]
 
 
 def dtsph_read_field(ctx, field: int, n: int, comps: int, out=None) -> np.ndarray:
@@ -332,15 +336,27 @@ def dtsph_kernel_launches(ctx) -> int:
     return lib().dtsph_kernel_launches(ctx)
 
 
-def dtsph_eval_rates_noalloc(params: dtsph_params, nf, x, v, p, ap, F, nw=0, xw=None, vw=None, stream=None) -> None:
+def dtsph_eval_rates_noalloc(params: dtsph_params, nf, x, v, p, ap, F, nw=0, xw=None, vw=None, status=None,
+                             stream=None) -> None:
     """Allocation-free rate evaluation: every array is a device tensor or a
-    device address; only enqueues work on `stream`."""
+    device address (status: an optional device int32 that receives the call's
+    device-side status); only enqueues work on `stream`."""
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     rc = lib().dtsph_eval_rates_noalloc(C.byref(params), int(nf), _ptr(x), _ptr(v), _ptr(p), int(nw), _ptr(xw),
-                                        _ptr(vw), _ptr(ap), _ptr(F), stream)
+                                        _ptr(vw), _ptr(ap), _ptr(F), _ptr(status), stream)
     if rc != DTSPH_OK:
         raise DtsphError(rc, "dtsph_eval_rates_noalloc")
+
+
+def dtsph_fma_peak(precision: int) -> float:
+    """Measured vector FMA throughput of the current device in FLOP/s (FP64 for
+    DTSPH_FP64, FP32 for DTSPH_FP32C)."""
+    out = C.c_double()
+    rc = lib().dtsph_fma_peak(int(precision), C.byref(out))
+    if rc != DTSPH_OK:
+        raise DtsphError(rc, "dtsph_fma_peak")
+    return out.value
 
 
 def dtsph_last_error(ctx) -> str:

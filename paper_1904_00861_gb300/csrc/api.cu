@@ -5,12 +5,15 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/dtsph.h"
 #include "dtsph_internal.cuh"
@@ -44,6 +47,8 @@ struct dtsph_ctx {
     cudaGraph_t graph = nullptr;
     std::string err;
     std::vector<void *> allocs;
+    size_t alloc_bytes = 0;             // device bytes allocated by the context
+    size_t alloc_limit = 0;             // 0, or a cap on alloc_bytes (DTSPH_TEST_ALLOC_LIMIT, tests only)
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
     double *rd = nullptr;                // dtsph_read_state: the fields in caller order (3 nf dim + nf)
     bool tuned = false;
@@ -61,6 +66,13 @@ namespace {
 
 const char *kNoCtx = "null context";
 
+// An NVTX range for the lifetime of the object (host-side spans that profilers
+// such as Nsight Systems show beside the kernels).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 int fail(dtsph_ctx *c, int code, const char *fmt, ...)
 {
     if (!c) return code;
@@ -70,6 +82,28 @@ int fail(dtsph_ctx *c, int code, const char *fmt, ...)
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
     c->err = buf;
+    return code;
+}
+
+// A non-negative integer from the environment, or dflt when unset or malformed.
+unsigned long long env_u64(const char *name, unsigned long long dflt)
+{
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt;
+    char *end = nullptr;
+    const unsigned long long x = strtoull(v, &end, 10);
+    return end && *end == 0 ? x : dflt;
+}
+
+// Formats a message into msg (capacity cap) and returns code.
+int say(char *msg, size_t cap, int code, const char *fmt, ...)
+{
+    if (msg && cap) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(msg, cap, fmt, ap);
+        va_end(ap);
+    }
     return code;
 }
 
@@ -85,12 +119,16 @@ int dalloc(dtsph_ctx *c, T **p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (c->alloc_limit && c->alloc_bytes + count * sizeof(T) > c->alloc_limit)
+        return fail(c, DTSPH_E_OOM, "allocation of %zu bytes would pass the cap of %zu bytes (DTSPH_TEST_ALLOC_LIMIT)",
+                    count * sizeof(T), c->alloc_limit);
     cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, DTSPH_E_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
     }
     c->allocs.push_back(*p);
+    c->alloc_bytes += count * sizeof(T);
     return DTSPH_OK;
 }
 
@@ -102,6 +140,7 @@ void free_all(dtsph_ctx *c)
     c->graph = nullptr;
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    c->alloc_bytes = 0;
     memset(&c->B, 0, sizeof(c->B));
     c->have_particles = false;
     c->have_nbrs = false;
@@ -116,6 +155,16 @@ double quintic_sigma(int dim, double h)
 }
 
 int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
+{
+    char msg[256];
+    const int r = dtsph::make_geometry(p, G, msg, sizeof msg);
+    return r ? fail(c, r, "%s", msg) : DTSPH_OK;
+}
+
+}  // namespace
+
+// Cell grid of one parameter set (cells of side > 3h, + skin for moving = 2).
+int dtsph::make_geometry(const dtsph_params &p, Geom &G, char *msg, size_t cap)
 {
     memset(&G, 0, sizeof G);
     G.dim = p.dim;
@@ -137,14 +186,14 @@ int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
             continue;
         }
         double L = p.hi[a] - p.lo[a];
-        if (!(L > 0)) return fail(c, DTSPH_E_ARG, "axis %d: hi must exceed lo", a);
+        if (!(L > 0)) return say(msg, cap, DTSPH_E_ARG, "axis %d: hi must exceed lo", a);
         // cells strictly wider than 3h so that rounding never separates neighbours
         long long k = (long long)std::floor(L / (rc * (1.0 + 1e-9)));
         if (k < 1) k = 1;
         if (G.periodic[a] && k < 3)
-            return fail(c, DTSPH_E_ARG, "periodic axis %d is shorter than three list cutoffs (%g < %g)", a, L,
-                        3 * rc);
-        if (k > (1 << 20)) return fail(c, DTSPH_E_ARG, "axis %d has too many cells", a);
+            return say(msg, cap, DTSPH_E_ARG, "periodic axis %d is shorter than three list cutoffs (%g < %g)", a,
+                       L, 3 * rc);
+        if (k > (1 << 20)) return say(msg, cap, DTSPH_E_ARG, "axis %d has too many cells", a);
         G.nc[a] = (int)k;
         G.s[a] = L / (double)k;
         G.inv_s[a] = 1.0 / G.s[a];
@@ -153,7 +202,7 @@ int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
         G.halfL[a] = 0.5 * L;
         G.ncell *= (int)k;
     }
-    if ((long long)G.nc[0] * G.nc[1] * G.nc[2] > (1LL << 28)) return fail(c, DTSPH_E_ARG, "too many cells");
+    if ((long long)G.nc[0] * G.nc[1] * G.nc[2] > (1LL << 28)) return say(msg, cap, DTSPH_E_ARG, "too many cells");
     G.rc2 = rc * rc;
     // FP32 band around the cutoff: the FP32 separation from cell offsets is accurate
     // to a few 1e-7 h, so outside +-2e-5 relative the FP32 test decides
@@ -162,7 +211,8 @@ int setup_geometry(dtsph_ctx *c, const dtsph_params &p, Geom &G)
     return DTSPH_OK;
 }
 
-void setup_phys(const dtsph_params &p, Phys &P)
+// Pair-term and update constants of one parameter set (rho_i = rho_j = rho0).
+void dtsph::make_phys(const dtsph_params &p, Phys &P)
 {
     memset(&P, 0, sizeof P);
     P.h = p.h;
@@ -205,50 +255,67 @@ void setup_phys(const dtsph_params &p, Phys &P)
     }
 }
 
-int validate(dtsph_ctx *c, const dtsph_params *p)
+// Range and consistency checks of one parameter set.
+int dtsph::check_params(const dtsph_params *p, char *msg, size_t cap)
 {
-    if (p->dim != 2 && p->dim != 3) return fail(c, DTSPH_E_ARG, "dim must be 2 or 3");
-    if (p->precision != DTSPH_FP64 && p->precision != DTSPH_FP32C) return fail(c, DTSPH_E_ARG, "bad precision");
+    if (p->dim != 2 && p->dim != 3) return say(msg, cap, DTSPH_E_ARG, "dim must be 2 or 3");
+    if (p->precision != DTSPH_FP64 && p->precision != DTSPH_FP32C) return say(msg, cap, DTSPH_E_ARG, "bad precision");
     const double pos[] = {p->h, p->m, p->rho0, p->beta, p->v_ref, p->dt};
     const char *nm[] = {"h", "m", "rho0", "beta", "v_ref", "dt"};
     for (int i = 0; i < 6; ++i)
-        if (!(pos[i] > 0) || !std::isfinite(pos[i])) return fail(c, DTSPH_E_ARG, "%s must be positive and finite", nm[i]);
+        if (!(pos[i] > 0) || !std::isfinite(pos[i])) return say(msg, cap, DTSPH_E_ARG, "%s must be positive and finite", nm[i]);
     if (!(p->nu >= 0) || !(p->eta > 0) || !(p->alpha >= 0) || !(p->eps >= 0) || !(p->stag_tol >= 0))
-        return fail(c, DTSPH_E_ARG, "nu, alpha, eps, stag_tol must be >= 0 and eta > 0");
-    if (p->max_iter < 1 || p->max_iter > (1 << 24)) return fail(c, DTSPH_E_ARG, "max_iter out of range");
-    if (p->stag_window < 0 || p->stag_window > 16) return fail(c, DTSPH_E_ARG, "stag_window must be in [0, 16]");
-    if (p->fixed_iters < 0 || p->fixed_iters > (1 << 24)) return fail(c, DTSPH_E_ARG, "fixed_iters out of range");
-    if (p->edac_h2_literal) return fail(c, DTSPH_E_UNSUPPORTED, "the literal r^2 + h^2 EDAC denominator is oracle-only");
-    if (p->max_neighbors < 0 || p->max_neighbors > 4096) return fail(c, DTSPH_E_ARG, "max_neighbors out of range");
-    if (p->graph < 0 || p->graph > 2) return fail(c, DTSPH_E_ARG, "graph must be 0, 1 or 2");
+        return say(msg, cap, DTSPH_E_ARG, "nu, alpha, eps, stag_tol must be >= 0 and eta > 0");
+    if (p->max_iter < 1 || p->max_iter > (1 << 24)) return say(msg, cap, DTSPH_E_ARG, "max_iter out of range");
+    if (p->stag_window < 0 || p->stag_window > 16) return say(msg, cap, DTSPH_E_ARG, "stag_window must be in [0, 16]");
+    if (p->fixed_iters < 0 || p->fixed_iters > (1 << 24)) return say(msg, cap, DTSPH_E_ARG, "fixed_iters out of range");
+    if (p->edac_h2_literal) return say(msg, cap, DTSPH_E_UNSUPPORTED, "the literal r^2 + h^2 EDAC denominator is oracle-only");
+    if (p->max_neighbors < 0 || p->max_neighbors > 4096) return say(msg, cap, DTSPH_E_ARG, "max_neighbors out of range");
+    if (p->graph < 0 || p->graph > 2) return say(msg, cap, DTSPH_E_ARG, "graph must be 0, 1 or 2");
     if (p->lanes != 0 && p->lanes != 1 && p->lanes != 2 && p->lanes != 4 && p->lanes != 8)
-        return fail(c, DTSPH_E_ARG, "lanes must be 0, 1, 2, 4 or 8");
+        return say(msg, cap, DTSPH_E_ARG, "lanes must be 0, 1, 2, 4 or 8");
     if (p->stages != 0 && (p->stages < 2 || p->stages > kMaxStages))
-        return fail(c, DTSPH_E_ARG, "stages must be 0 or in [2, %d]", kMaxStages);
-    if (p->shifting != 0 && p->shifting != 1) return fail(c, DTSPH_E_ARG, "shifting must be 0 or 1");
-    if (p->steady != 0 && p->steady != 1) return fail(c, DTSPH_E_ARG, "steady must be 0 or 1");
-    if (p->steady && p->shifting) return fail(c, DTSPH_E_ARG, "the steady mode keeps the particles fixed: no shifting");
-    if (p->free_surface != 0 && p->free_surface != 1) return fail(c, DTSPH_E_ARG, "free_surface must be 0 or 1");
-    if (p->moving < 0 || p->moving > 2) return fail(c, DTSPH_E_ARG, "moving must be 0, 1 or 2");
-    if (p->moving && p->steady) return fail(c, DTSPH_E_ARG, "the steady mode keeps the particles fixed: moving must be 0");
-    if (!(p->skin >= 0) || !std::isfinite(p->skin)) return fail(c, DTSPH_E_ARG, "skin must be >= 0 and finite");
-    if (p->moving == 2 && !(p->skin > 0)) return fail(c, DTSPH_E_ARG, "moving = 2 needs a positive skin");
+        return say(msg, cap, DTSPH_E_ARG, "stages must be 0 or in [2, %d]", kMaxStages);
+    if (p->shifting != 0 && p->shifting != 1) return say(msg, cap, DTSPH_E_ARG, "shifting must be 0 or 1");
+    if (p->steady != 0 && p->steady != 1) return say(msg, cap, DTSPH_E_ARG, "steady must be 0 or 1");
+    if (p->steady && p->shifting) return say(msg, cap, DTSPH_E_ARG, "the steady mode keeps the particles fixed: no shifting");
+    if (p->free_surface != 0 && p->free_surface != 1) return say(msg, cap, DTSPH_E_ARG, "free_surface must be 0 or 1");
+    if (p->moving < 0 || p->moving > 2) return say(msg, cap, DTSPH_E_ARG, "moving must be 0, 1 or 2");
+    if (p->moving && p->steady) return say(msg, cap, DTSPH_E_ARG, "the steady mode keeps the particles fixed: moving must be 0");
+    if (!(p->skin >= 0) || !std::isfinite(p->skin)) return say(msg, cap, DTSPH_E_ARG, "skin must be >= 0 and finite");
+    if (p->moving == 2 && !(p->skin > 0)) return say(msg, cap, DTSPH_E_ARG, "moving = 2 needs a positive skin");
     return DTSPH_OK;
 }
 
+namespace {
+
+int validate(dtsph_ctx *c, const dtsph_params *p)
+{
+    char msg[256];
+    const int r = dtsph::check_params(p, msg, sizeof msg);
+    return r ? fail(c, r, "%s", msg) : DTSPH_OK;
+}
+
 // Autotuner results: lanes per particle of the iterate kernel and, with one
-// lane, its staging depth, keyed by (dim, precision, slots, instances), shared
-// by every context of the process.
+// lane, its staging depth, keyed by (device, dim, precision, slots, instances,
+// persistent loop or not), shared by every context of the process. With
+// DTSPH_TUNE_CACHE set to a file name they also persist across processes: the
+// file is read once per process, and every new choice is appended to it as one
+// line "dtsph-tune-v1 <device> <dim> <precision> <slots> <instances> <loop>
+// <lanes> <stages>" (the last line of a key wins).
 struct TuneKey {
+    std::string dev;   // device name and SM count, spaces replaced
     int dim, prec;
     int64_t n;
-    int ninst;
+    int ninst, loop;
     bool operator<(const TuneKey &o) const
     {
+        if (dev != o.dev) return dev < o.dev;
         if (dim != o.dim) return dim < o.dim;
         if (prec != o.prec) return prec < o.prec;
         if (n != o.n) return n < o.n;
-        return ninst < o.ninst;
+        if (ninst != o.ninst) return ninst < o.ninst;
+        return loop < o.loop;
     }
 };
 struct TuneChoice { int lanes, stages; };
@@ -260,10 +327,64 @@ std::map<TuneKey, TuneChoice> &tune_cache()
 
 constexpr int kDefaultStages = 3;
 std::mutex tune_mu;
+bool tune_file_read = false;
+
+const char *tune_file() { return getenv("DTSPH_TUNE_CACHE"); }
+
+// Reads the persisted choices once (tune_mu held).
+void load_tune_file()
+{
+    if (tune_file_read) return;
+    tune_file_read = true;
+    const char *path = tune_file();
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char tag[32], dev[160];
+    TuneKey k;
+    long long n = 0;
+    TuneChoice ch;
+    while (fscanf(f, "%31s %159s %d %d %lld %d %d %d %d", tag, dev, &k.dim, &k.prec, &n, &k.ninst, &k.loop, &ch.lanes,
+                  &ch.stages) == 9) {
+        if (strcmp(tag, "dtsph-tune-v1") != 0) continue;
+        const bool ok = (ch.lanes == 1 || ch.lanes == 2 || ch.lanes == 4 || ch.lanes == 8) && ch.stages >= 2 &&
+                        ch.stages <= kMaxStages;
+        if (!ok) continue;
+        k.dev = dev;
+        k.n = n;
+        tune_cache()[k] = ch;
+    }
+    fclose(f);
+}
+
+// Appends one choice to the persisted file (tune_mu held).
+void save_tune_choice(const TuneKey &k, const TuneChoice &ch)
+{
+    const char *path = tune_file();
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "dtsph-tune-v1 %s %d %d %lld %d %d %d %d\n", k.dev.c_str(), k.dim, k.prec, (long long)k.n, k.ninst,
+            k.loop, ch.lanes, ch.stages);
+    fclose(f);
+}
+
+std::string device_tag(int dev)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string name = prop.name;
+    for (char &ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return name + "/" + std::to_string(prop.multiProcessorCount) + "sm";
+}
 
 TuneKey tune_key(const dtsph_ctx *c, int64_t n)
 {
-    return TuneKey{c->prm[0].dim, c->prm[0].precision, n, c->ninst};
+    return TuneKey{device_tag(c->device), c->prm[0].dim, c->prm[0].precision, n, c->ninst, c->prm[0].graph == 2};
 }
 
 // Lanes and stages for n slots: the parameters' when fixed, else the process
@@ -273,8 +394,10 @@ TuneChoice kernel_choice(dtsph_ctx *c, int64_t n)
     const dtsph_params &p = c->prm[0];
     TuneChoice ch{p.lanes > 0 ? p.lanes : 4, p.stages > 0 ? p.stages : kDefaultStages};
     if (p.lanes == 0) {
+        const TuneKey key = tune_key(c, n);
         std::lock_guard<std::mutex> g(tune_mu);
-        auto it = tune_cache().find(tune_key(c, n));
+        load_tune_file();
+        auto it = tune_cache().find(key);
         if (it != tune_cache().end()) {
             ch = it->second;
             c->tuned = true;
@@ -283,7 +406,12 @@ TuneChoice kernel_choice(dtsph_ctx *c, int64_t n)
     return ch;
 }
 
-int neighbour_capacity(const dtsph_params &p)
+
+}  // namespace
+
+// Neighbour-list entries per particle: max_neighbors, else 1.35 times the mean
+// count of a uniform fill of the list cutoff's disc (sphere) plus 8.
+int dtsph::neighbour_capacity(const dtsph_params &p)
 {
     if (p.max_neighbors > 0) return p.max_neighbors;
     const double vol = p.m / p.rho0;
@@ -293,10 +421,16 @@ int neighbour_capacity(const dtsph_params &p)
     return std::min(std::max(k, 8), 4096);
 }
 
+namespace {
+
 // Device memory for nf[i] fluid particles per instance plus the walls set so far.
 int allocate(dtsph_ctx *c, const int64_t *nf)
 {
     free_all(c);
+    // test hooks: a cap on the context's device memory (to exercise DTSPH_E_OOM)
+    // and a shorter give-up time of the persistent loop's grid barrier (to
+    // exercise DTSPH_E_TIMEOUT); both unset in normal use
+    c->alloc_limit = (size_t)env_u64("DTSPH_TEST_ALLOC_LIMIT", 0);
     if (iterate_prepare() != 0) {
         cudaGetLastError();
         return fail(c, DTSPH_E_CUDA, "could not raise the shared-memory limit of the iterate kernels");
@@ -322,7 +456,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         fo += nf[i];
         wo += nw;
         co += c->G[i].ncell + 1;   // one empty sentinel cell per instance
-        K = std::max(K, neighbour_capacity(c->prm[i]));
+        K = std::max(K, dtsph::neighbour_capacity(c->prm[i]));
         if (slot >= (1LL << 31) - 4 * kSlotAlign || co >= (1LL << 31) - 2)
             return fail(c, DTSPH_E_ARG, "particle or cell count out of range");
         c->P[i].rp_scale = c->P[i].dt / (c->P[i].rho0 * c->P[i].c * c->P[i].c) / (double)nf[i];
@@ -338,6 +472,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     B.K = K;
     B.ninst = ni;
     B.ncell = (int)co;
+    B.barrier_ns = env_u64("DTSPH_TEST_BARRIER_WAIT_NS", kBarrierWaitNs);
     {
         const TuneChoice ch = kernel_choice(c, n);
         B.lanes = ch.lanes;
@@ -557,9 +692,13 @@ int build_graph(dtsph_ctx *c)
 int step_plain(dtsph_ctx *c)
 {
     const int k = (int)(c->steps % dtsph_ctx::kLoopEv);
-    c->per_step_fixed = enqueue_pre_loop(c, c->stream);
+    {
+        Range r("dtsph pre-loop: binning, lists, state-n pass, pair cache");
+        c->per_step_fixed = enqueue_pre_loop(c, c->stream);
+    }
     c->launches += c->per_step_fixed;
     CK(cudaEventRecord(c->ev_a[k], c->stream));
+    Range loop_range("dtsph pseudo-time loop");
     int cap = 1;
     for (const auto &p : c->prm) cap = std::max(cap, p.fixed_iters > 0 ? p.fixed_iters : p.max_iter);
     int issued = 0;
@@ -577,6 +716,7 @@ int step_plain(dtsph_ctx *c)
         if (issued > cap + 16) return fail(c, DTSPH_E_STATE, "pseudo-time loop did not stop");
     }
     CK(cudaEventRecord(c->ev_b[k], c->stream));
+    Range outer_range("dtsph outer step");
     c->launches += enqueue_post_loop(c, c->stream);
     CK(cudaGetLastError());
     return DTSPH_OK;
@@ -587,6 +727,7 @@ int device_error(dtsph_ctx *c)
     uint32_t e = 0;
     CK(cudaMemcpyAsync(&e, c->B.err, sizeof e, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (e & kErrNonFinite) return fail(c, DTSPH_E_ARG, "a particle position is not finite");
     if (e & kErrCapacity)
         return fail(c, DTSPH_E_CAPACITY, "a particle had more than %d neighbours (raise max_neighbors)", c->B.K);
     if (e & kErrDomain) return fail(c, DTSPH_E_DOMAIN, "a particle left the box of a non-periodic axis");
@@ -671,6 +812,7 @@ int probe_loop_ms(dtsph_ctx *c, int iters, int reps, float *out)
 // hold no state yet; they are zeroed for the timing runs.
 int autotune(dtsph_ctx *c)
 {
+    Range range("dtsph autotune");
     const Buffers &B = c->B;
     const size_t nd = (size_t)B.n * B.dim;
     CK(cudaMemsetAsync(B.vk[0], 0, nd * sizeof(double), c->stream));
@@ -712,8 +854,10 @@ int autotune(dtsph_ctx *c)
     c->B.stages = best.stages;
     c->tuned = true;
     {
+        const TuneKey key = tune_key(c, c->B.n);
         std::lock_guard<std::mutex> g(tune_mu);
-        tune_cache()[tune_key(c, c->B.n)] = best;
+        tune_cache()[key] = best;
+        save_tune_choice(key, best);
     }
     return device_error(c);
 }
@@ -721,6 +865,7 @@ int autotune(dtsph_ctx *c)
 int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const double *v, const double *p,
                        const double *vprev, bool device)
 {
+    Range range("dtsph_set_particles");
     if (!x || !v || !p || !nf) return fail(c, DTSPH_E_ARG, "x, v and p are required");
     CK(cudaSetDevice(c->device));
     int r;
@@ -755,6 +900,10 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
     }
     const size_t bx = (size_t)NF * d * sizeof(double), bp = (size_t)NF * sizeof(double);
     double *svp = vprev ? c->svp : nullptr;
+    // a new state restarts the step log and clears device-side error flags
+    // (before the scatter, which flags a non-finite position)
+    for (int i = 0; i < ni; ++i) CK(cudaMemsetAsync(&c->B.ls[i].step, 0, sizeof(long long), c->stream));
+    CK(cudaMemsetAsync(c->B.err, 0, sizeof(uint32_t), c->stream));
     double *sxw = NW > 0 ? c->sxw : nullptr, *svw = NW > 0 ? c->svw : nullptr;
     if (!device && c->host_direct) {
         // the scatter kernel reads the caller's arrays where they are
@@ -767,11 +916,13 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
         if (vprev) CK(cudaMemcpyAsync(svp, vprev, bx, kind, c->stream));
         c->launches += launch_scatter_in(c->B, c->sx, c->sv, c->sp, svp, sxw, svw, c->stream);
     }
-    // a new state restarts the step log and clears device-side error flags
-    for (int i = 0; i < ni; ++i) CK(cudaMemsetAsync(&c->B.ls[i].step, 0, sizeof(long long), c->stream));
-    CK(cudaMemsetAsync(c->B.err, 0, sizeof(uint32_t), c->stream));
     CK(cudaGetLastError());
-    if (!device) CK(cudaStreamSynchronize(c->stream));   // host arrays may be reused once we return
+    if (!device) {
+        CK(cudaStreamSynchronize(c->stream));   // host arrays may be reused once we return
+        uint32_t e = 0;
+        CK(cudaMemcpy(&e, c->B.err, sizeof e, cudaMemcpyDeviceToHost));
+        if (e & kErrNonFinite) return fail(c, DTSPH_E_ARG, "a particle position is not finite");
+    }
     c->have_particles = true;
     c->steps = 0;
     if (!c->tuned && c->prm[0].lanes == 0 && !c->B.xk[0]) {
@@ -868,7 +1019,7 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
             delete c;
             return r;
         }
-        setup_phys(params[i], c->P[i]);
+        dtsph::make_phys(params[i], c->P[i]);
     }
     memset(&c->B, 0, sizeof c->B);
     c->stream = (cudaStream_t)stream;
@@ -923,6 +1074,7 @@ int read_stats_impl(dtsph_ctx *c, int32_t inst, int64_t first, int32_t count, dt
         out[i].reason = r.reason;
         out[i].rp = r.rp;
         out[i].rv = r.rv;
+        out[i].vmax = r.vmax;
     }
     return DTSPH_OK;
 }
@@ -1003,6 +1155,7 @@ int dtsph_step(dtsph_ctx *c, int32_t nsteps)
     if (!c->have_particles) return fail(c, DTSPH_E_STATE, "dtsph_step before dtsph_set_particles");
     if (nsteps < 0) return fail(c, DTSPH_E_ARG, "nsteps must be >= 0");
     CK(cudaSetDevice(c->device));
+    Range range(c->exec ? "dtsph_step (step graphs)" : "dtsph_step");
     c->have_nbrs = false;
     for (int32_t s = 0; s < nsteps; ++s) {
         if (c->exec) {

@@ -283,6 +283,23 @@ __global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
 
 // Caller order -> order A from AoS inputs: slot s of instance i holds its fluid
 // particle s - slot_off (caller index foff + ...), then its walls, then padding.
+// An input coordinate: flags a non-finite value; on a periodic axis brings a
+// value outside [lo, hi) into it, x - floor((x - lo) / L) L, then once more by
+// one L if rounding left it on the edge (every operation rounded as written).
+__device__ __forceinline__ double input_coord(double xa, const Geom &G, int a, uint32_t *err)
+{
+    if (!isfinite(xa)) {
+        atomicOr(err, kErrNonFinite);
+        return G.lo[a];
+    }
+    if (!G.periodic[a] || (xa >= G.lo[a] && xa < G.hi[a])) return xa;
+    const double q = floor(__ddiv_rn(__dsub_rn(xa, G.lo[a]), G.L[a]));
+    double y = __dsub_rn(xa, __dmul_rn(q, G.L[a]));
+    if (y >= G.hi[a]) y = __dsub_rn(y, G.L[a]);
+    else if (y < G.lo[a]) y = __dadd_rn(y, G.L[a]);
+    return y;
+}
+
 __global__ void __launch_bounds__(kBlock) k_scatter_in(Buffers B, const double *__restrict__ x,
                                                        const double *__restrict__ v, const double *__restrict__ p,
                                                        const double *__restrict__ vprev,
@@ -292,13 +309,14 @@ __global__ void __launch_bounds__(kBlock) k_scatter_in(Buffers B, const double *
     if (s >= B.n) return;
     const int n = B.n, dim = B.dim;
     const Inst I = B.inst[B.inst_of[s]];
+    const Geom &G = B.geo[B.inst_of[s]];
     const int local = s - I.slot_off;
     if (local < I.nf) {
         const size_t f = (size_t)I.foff + local;
         B.gid_a[s] = (uint32_t)f;
         for (int a = 0; a < dim; ++a) {
             const size_t so = (size_t)a * n;
-            B.x_a[so + s] = x[f * dim + a];
+            B.x_a[so + s] = input_coord(x[f * dim + a], G, a, B.err);
             B.vn_a[so + s] = v[f * dim + a];
             B.vnm1_a[so + s] = vprev ? vprev[f * dim + a] : v[f * dim + a];
         }
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter_in(Buffers B, const double *
         B.gid_a[s] = (uint32_t)(B.nf + w);
         for (int a = 0; a < dim; ++a) {
             const size_t so = (size_t)a * n;
-            B.x_a[so + s] = xw[w * dim + a];
+            B.x_a[so + s] = input_coord(xw[w * dim + a], G, a, B.err);
             B.vn_a[so + s] = vw ? vw[w * dim + a] : 0.0;
             B.vnm1_a[so + s] = B.vn_a[so + s];
         }

@@ -7,6 +7,8 @@
 
 #include <type_traits>
 
+#include "../../include/dtsph.h"
+
 namespace dtsph {
 
 constexpr int kBlock = 256;          // threads per block of every particle kernel
@@ -14,7 +16,8 @@ constexpr int kWarp = 32;
 constexpr uint32_t kWallBit = 0x80000000u;   // set in a cached neighbour index when j is a wall
 
 // Error bits raised by kernels into Buffers::err (read by dtsph_sync).
-enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy = 8u, kErrSkin = 16u };
+enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy = 8u, kErrSkin = 16u,
+                  kErrNonFinite = 32u };
 
 // A context advances one or more independent simulations ("instances") together.
 // Instance i owns the slot range [slot_off, slot_off + nf + nw) of every particle
@@ -25,6 +28,7 @@ enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy
 constexpr int kSlotAlign = 256;
 constexpr int kMaxStages = 8;        // deepest shared-memory ring of the one-lane iterate kernel
 constexpr uint32_t kNoParticle = 0xFFFFFFFFu;
+constexpr unsigned long long kBarrierWaitNs = 1000000000ull;   // grid-barrier give-up time (1 s)
 
 struct Inst {
     int slot_off;          // first slot
@@ -94,7 +98,8 @@ struct LoopState {
     int pad0;
     double rp, rv;         // residuals of the last iteration
     double hist_p[16], hist_v[16];   // ring of the last residuals (stagnation test)
-    int max_iter, fixed_iters, stag_window, pad;
+    int max_iter, fixed_iters, stag_window;
+    int stat_slot;         // entry of the statistics ring this real step writes
     double eps, stag_tol;
     long long step;        // real steps completed (indexes the stats ring)
 };
@@ -107,7 +112,11 @@ struct LoopCtrl {
     int pad;
 };
 
-struct StatRec { int iters, reason; double rp, rv; };
+struct StatRec {
+    int iters, reason;
+    double rp, rv;
+    double vmax;           // max |V^{n+1}| over the instance's fluid particles (before shifting)
+};
 constexpr int kStatRing = 65536;   // real steps kept per instance
 
 // Device buffers of one context. Particle arrays hold all n = nf + nw particles
@@ -120,6 +129,7 @@ struct Buffers {
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
     int stages;                     // pair-cache chunks in flight per warp (lanes = 1), 2..kMaxStages
     int ninst, ncell;               // instances; cells of all instances (sentinels included)
+    unsigned long long barrier_ns;  // give-up time of the persistent loop's grid barrier
     const Inst *inst;               // [ninst]
     const Geom *geo;                // [ninst]
     const Phys *phys;               // [ninst]
@@ -234,5 +244,14 @@ int launch_fill_instance(Inst *inst, Geom *geo, Phys *phys, int i, const Inst &I
                          cudaStream_t st);
 
 int iterate_tiles(const Buffers &B);   // tiles of the iterate kernel (one block each)
+
+// ------------------------------------------------- one parameter set (api.cu)
+// Shared by the context entry points and the allocation-free rate evaluation,
+// so that both read dtsph_params the same way. The first two return DTSPH_OK or
+// a DTSPH_E_* code with a one-line message in msg (capacity cap).
+int check_params(const dtsph_params *p, char *msg, size_t cap);
+int make_geometry(const dtsph_params &p, Geom &G, char *msg, size_t cap);
+void make_phys(const dtsph_params &p, Phys &P);
+int neighbour_capacity(const dtsph_params &p);
 
 }  // namespace dtsph

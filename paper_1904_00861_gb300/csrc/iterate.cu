@@ -338,9 +338,10 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
                 }
             }
             if (c < nch) {
-                // a wait gave up: drain what is still in flight (bounded), stop
-                // using the ring and report
-                for (int d = c + 1; d < nch && d < c + S; ++d) {
+                // a wait gave up: drain what is still in flight, the chunk
+                // whose wait gave up included (each wait bounded), stop using
+                // the ring and report
+                for (int d = c; d < nch && d < c + S; ++d) {
                     const uint32_t q = rp.pos + (uint32_t)d;
                     mbar_wait(&rg.bar[q % (uint32_t)S], (q / (uint32_t)S) & 1u);
                 }
@@ -535,9 +536,11 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 // Grid barrier for a cooperative launch (all blocks resident): arrival counter
 // `bar`, reset to 0 before the launch; the epoch-th barrier waits for
-// epoch * gridDim.x arrivals. The wait gives up after one second, raises
-// kErrBarrier and returns false (the caller then stops iterating).
-__device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *err, int &ok_sh)
+// epoch * gridDim.x arrivals. The wait gives up after limit_ns (one second
+// unless a test shortens it), raises kErrBarrier and returns false (the caller
+// then stops iterating).
+__device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *err, int &ok_sh,
+                             unsigned long long limit_ns)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -548,7 +551,7 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *er
         const unsigned long long t0 = global_ns();
         while (*(volatile unsigned int *)bar < target) {
             __nanosleep(32);
-            if (global_ns() - t0 > 1000000000ull) {
+            if (global_ns() - t0 > limit_ns) {
                 atomicOr(err, kErrBarrier);
                 ok = 0;
                 break;
@@ -561,9 +564,74 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *er
     return ok_sh != 0;
 }
 
+// Batches of up to this many instances deal their active tiles to the blocks
+// of the persistent loop; larger batches take the tiles in the static order.
+constexpr int kDealMaxInst = 1024;
+
+// Exclusive prefix of the active (not yet converged) tiles of every instance,
+// by the whole block: pre[i] = active tiles of instances 0 .. i-1, pre[ninst] =
+// all of them. Reads the instances' done flags, so call it after the barrier
+// that publishes them.
+__device__ void active_tile_prefix(const Buffers &B, int ppb, int *pre)
+{
+    constexpr int E = (kDealMaxInst + kBlock - 1) / kBlock;
+    __shared__ int wsum[kBlock / kWarp];
+    const int ni = B.ninst;
+    const int base = threadIdx.x * E;
+    int cnt[E];
+    int sum = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = base + e;
+        int c = 0;
+        if (i < ni && !*(volatile int *)&B.ls[i].done) {
+            int lo, hi;
+            instance_tiles(B.inst[i], ppb, lo, hi);
+            c = hi - lo;
+        }
+        cnt[e] = c;
+        sum += c;
+    }
+    // exclusive scan of the per-thread sums: within the warp, then over warps
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < wid; ++w) off += wsum[w];
+    int run = off + incl - sum;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = base + e;
+        if (i <= ni) pre[i] = run;
+        run += cnt[e];
+    }
+    __syncthreads();
+}
+
+// The instance whose active tiles hold position k of the dealt order
+// (pre[0] = 0 <= k < pre[ni]).
+__device__ __forceinline__ int dealt_instance(const int *pre, int ni, int k)
+{
+    int lo = 0, hi = ni;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Every pseudo-time iteration of one real step in one cooperative launch. Tiles
-// are dealt to blocks round robin; after each iteration the blocks meet at a
-// grid barrier. With one instance every block then reduces the per-tile
+// are dealt to blocks round robin: with one instance all tiles, with several
+// (up to kDealMaxInst) the tiles of the instances still iterating, so that
+// every block keeps an even share while converged instances drop out; after
+// each iteration the blocks meet at a grid barrier. With one instance every block then reduces the per-tile
 // partials (double-buffered on the iteration parity) in the fixed order of
 // k_iterate and all blocks take the same stop decision. With several, block b
 // finishes instances b, b + grid, ... and a second barrier publishes the
@@ -578,8 +646,10 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
     __shared__ LoopState st;
     __shared__ Phys P;
     __shared__ int stop, ok_sh, p_inst;
+    __shared__ int act_pre[kDealMaxInst + 1];
     const int ntiles = (B.n + PPB - 1) / PPB;
     const bool single = B.ninst == 1;
+    const bool deal = !single && B.ninst <= kDealMaxInst;
     if (threadIdx.x == 0) {
         if (single) st = *B.ls;
         stop = 0;
@@ -596,14 +666,26 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
                 const uint32_t g = B.gid_a[s];
                 if (g >= (uint32_t)B.nf && g != kNoParticle && !B.ls[B.inst_of[s]].done) wall_slot<D, F32>(B, s, cur);
             }
-            if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh)) break;
+            if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh, B.barrier_ns)) break;
         }
         double *blk = B.blk + (size_t)(it & 1) * 2 * ntiles;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const int inst = block_instance(B, t * PPB);
-            int tlo, thi;
-            instance_tiles(B.inst[inst], PPB, tlo, thi);
-            if (t >= thi || (!single && *(volatile int *)&B.ls[inst].done)) continue;
+        int nwork = ntiles;
+        if (deal) {
+            active_tile_prefix(B, PPB, act_pre);
+            nwork = act_pre[B.ninst];
+        }
+        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+            int inst, t, tlo, thi;
+            if (deal) {
+                inst = dealt_instance(act_pre, B.ninst, k);
+                instance_tiles(B.inst[inst], PPB, tlo, thi);
+                t = tlo + (k - act_pre[inst]);
+            } else {
+                t = k;
+                inst = block_instance(B, t * PPB);
+                instance_tiles(B.inst[inst], PPB, tlo, thi);
+                if (t >= thi || (!single && *(volatile int *)&B.ls[inst].done)) continue;
+            }
             if (inst != p_inst) {
                 __syncthreads();
                 for (int w = threadIdx.x; w < (int)(sizeof(Phys) / 4); w += blockDim.x)
@@ -618,7 +700,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
                 blk[2 * t + 1] = b;
             }
         }
-        if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh)) break;
+        if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh, B.barrier_ns)) break;
         if (single) {
             double sa = 0, sb = 0;
             int tlo, thi;
@@ -647,7 +729,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
                 }
                 __syncthreads();
             }
-            if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh)) break;
+            if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh, B.barrier_ns)) break;
             if (threadIdx.x == 0) stop = *(volatile int *)&B.ctrl->active == 0;
             __syncthreads();
             if (stop) break;
@@ -678,75 +760,75 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
 }
 
 // Eq. (r-update): r^{n+1} = r^n + dt/2 (V^n + V^{n+1}) for fluid slots, then
-// V^{n-1} <- V^n, V^n <- V^K, p^n <- p^K = (p-hat^K + p-hat^{K-1}) / 2; thread 0
-// logs the step.
+// V^{n-1} <- V^n, V^n <- V^K, p^n <- p^K = (p-hat^K + p-hat^{K-1}) / 2; the
+// instance's first slot logs the step, and the step's max|V^{n+1}| is folded in
+// per warp (a block never straddles two instances), then by one atomic max per
+// warp on the bits (non-negative doubles order as integers).
 template <int D, bool F32>
 __global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.n) return;
-    const int inst = B.inst_of[s];
+    const int inst = block_instance(B, blockIdx.x * blockDim.x);
     LoopState *ls = B.ls + inst;
-    const int K = ls->iter;
-    const int fin = K & 1, prev = fin ^ 1;
-    const int n = B.n;
-    if (s == B.inst[inst].slot_off) {
-        const long long step = ls->step;
-        StatRec r;
-        r.iters = K;
-        r.reason = ls->reason;
-        r.rp = ls->rp;
-        r.rv = ls->rv;
-        B.stats[(step % kStatRing) * B.ninst + inst] = r;
-        ls->step = step + 1;
-    }
-    if (B.gid_a[s] >= (uint32_t)B.nf) return;           // walls and padding
-    const Geom &G = B.geo[inst];
-    const double dt = B.phys[inst].dt;
-    const bool move = !B.phys[inst].steady;               // steady mode: the particles stay
-    for (int a = 0; a < D; ++a) {
-        const size_t q = (size_t)a * n + s;
-        const double vn = B.vn_a[q];
-        const double vK = B.vk[fin][q];
-        if (move) {
-            double x = __fma_rn(0.5 * dt, __dadd_rn(vn, vK), B.x_a[q]);
-            if (G.periodic[a]) {
-                if (x >= G.hi[a]) x = __dsub_rn(x, G.L[a]);
-                else if (x < G.lo[a]) x = __dadd_rn(x, G.L[a]);
-            }
-            B.x_a[q] = x;
+    StatRec *rec = B.stats + (size_t)ls->stat_slot * B.ninst + inst;
+    const bool fluid = s < B.n && B.gid_a[s] < (uint32_t)B.nf;   // not a wall, not padding
+    double vmag = 0.0;
+    if (s < B.n) {
+        const int K = ls->iter;
+        const int fin = K & 1, prev = fin ^ 1;
+        const int n = B.n;
+        if (s == B.inst[inst].slot_off) {
+            rec->iters = K;
+            rec->reason = ls->reason;
+            rec->rp = ls->rp;
+            rec->rv = ls->rv;
+            ls->step = ls->step + 1;
         }
-        B.vnm1_a[q] = vn;
-        B.vn_a[q] = vK;
+        if (fluid) {
+            const Geom &G = B.geo[inst];
+            const double dt = B.phys[inst].dt;
+            const bool move = !B.phys[inst].steady;               // steady mode: the particles stay
+            double v2 = 0.0;
+            for (int a = 0; a < D; ++a) {
+                const size_t q = (size_t)a * n + s;
+                const double vn = B.vn_a[q];
+                const double vK = B.vk[fin][q];
+                v2 = __fma_rn(vK, vK, v2);
+                if (move) {
+                    double x = __fma_rn(0.5 * dt, __dadd_rn(vn, vK), B.x_a[q]);
+                    if (G.periodic[a]) {
+                        if (x >= G.hi[a]) x = __dsub_rn(x, G.L[a]);
+                        else if (x < G.lo[a]) x = __dadd_rn(x, G.L[a]);
+                    }
+                    B.x_a[q] = x;
+                }
+                B.vnm1_a[q] = vn;
+                B.vn_a[q] = vK;
+            }
+            double p1, p0;
+            if (F32) {
+                p1 = B.nb32[fin][s].w;
+                p0 = B.nb32[prev][s].w;
+            } else {
+                p1 = B.nb64[fin][s].w;
+                p0 = B.nb64[prev][s].w;
+            }
+            B.pn_a[s] = __dmul_rn(0.5, __dadd_rn(p0, p1));
+            vmag = sqrt(v2);
+        }
     }
-    double p1, p0;
-    if (F32) {
-        p1 = B.nb32[fin][s].w;
-        p0 = B.nb32[prev][s].w;
-    } else {
-        p1 = B.nb64[fin][s].w;
-        p0 = B.nb64[prev][s].w;
+    // a NaN speed has larger bits than any finite one, so it shows as the maximum
+    unsigned long long bits = (unsigned long long)__double_as_longlong(vmag);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = other > bits ? other : bits;
     }
-    B.pn_a[s] = __dmul_rn(0.5, __dadd_rn(p0, p1));
+    if ((threadIdx.x & 31) == 0 && bits != 0ull)
+        atomicMax((unsigned long long *)&rec->vmax, bits);
 }
 
-__global__ void k_loop_reset(Buffers B)
-{
-    for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
-        LoopState *ls = B.ls + i;
-        ls->iter = 0;
-        ls->done = 0;
-        ls->reason = -1;
-        ls->ticket = 0;
-        ls->rp = 0;
-        ls->rv = 0;
-    }
-    if (threadIdx.x == 0) {
-        B.ctrl->ticket = 0;
-        B.ctrl->bar = 0;
-        B.ctrl->active = B.ninst;
-    }
-}
+__global__ void k_loop_reset(Buffers B) { reset_loops(B); }
 
 template <int D, bool F, bool W, int L>
 const void *loop_kernel() { return (const void *)k_loop<D, F, W, L>; }

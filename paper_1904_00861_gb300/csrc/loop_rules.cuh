@@ -85,6 +85,31 @@ __device__ __forceinline__ void reduce_tiles(const double *blk, int ntiles, doub
     }
 }
 
+// Resets the pseudo-time loop state of every instance for the loop of a new
+// real step (one block: its threads loop over the instances), points each
+// instance at the entry of the statistics ring that step will write and clears
+// that entry's max|V|, which the outer step accumulates.
+__device__ __forceinline__ void reset_loops(const Buffers &B)
+{
+    for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
+        LoopState *ls = B.ls + i;
+        ls->iter = 0;
+        ls->done = 0;
+        ls->reason = -1;
+        ls->ticket = 0;
+        ls->rp = 0;
+        ls->rv = 0;
+        const int slot = (int)(ls->step % kStatRing);
+        ls->stat_slot = slot;
+        B.stats[(size_t)slot * B.ninst + i].vmax = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        B.ctrl->ticket = 0;
+        B.ctrl->bar = 0;
+        B.ctrl->active = B.ninst;
+    }
+}
+
 // First tile and end tile of instance i for tiles of ppb slots.
 __device__ __forceinline__ void instance_tiles(const Inst &I, int ppb, int &lo, int &hi)
 {

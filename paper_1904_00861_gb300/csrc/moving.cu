@@ -37,20 +37,7 @@ template <bool F32>
 __global__ void __launch_bounds__(kBlock) k_move_init(Buffers B)
 {
     if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
-            LoopState *ls = B.ls + i;
-            ls->iter = 0;
-            ls->done = 0;
-            ls->reason = -1;
-            ls->ticket = 0;
-            ls->rp = 0;
-            ls->rv = 0;
-        }
-        if (threadIdx.x == 0) {
-            B.ctrl->ticket = 0;
-            B.ctrl->bar = 0;
-            B.ctrl->active = B.ninst;
-        }
+        reset_loops(B);
     }
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= B.n || B.gid_a[s] == kNoParticle) return;

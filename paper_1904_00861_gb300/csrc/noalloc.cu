@@ -23,7 +23,6 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/dtsph.h"
 #include "dtsph_internal.cuh"
 
 namespace dtsph {
@@ -35,11 +34,43 @@ constexpr int kNoallocMaxParticles = 16384;
 constexpr int kNoallocMaxCells = 32768;
 constexpr size_t kNoallocMaxEntries = (size_t)kNoallocMaxParticles * 192;
 
-// Bytes per particle of the arrays the rate evaluation touches (see carve()).
-constexpr size_t kPerParticle = 4 + 3 * 8 * 3 + 8 + 4 * 4 + 4 + 3 * 8 * 3 + 8 + 4 + 16 + 32 + 8 + 3 * 8 + 2;
+constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// The arrays carve() takes, in its order, for n slots, ncell cells and K list
+// entries per slot: each size in bytes before its 256-byte rounding.
+constexpr int kCarveArrays = 30;
+struct Carve {
+    size_t bytes[kCarveArrays];
+    int count;
+};
+constexpr Carve carve_sizes(size_t n, size_t ncell, size_t K)
+{
+    const size_t nd = n * 3;
+    Carve c{{4 * n, 8 * nd, 8 * nd, 8 * nd, 8 * n,               // gid_a, x_a, vn_a, vnm1_a, pn_a
+             4 * n, 4 * n, 4 * n, 4 * n,                          // key, slot, unsorted, perm
+             4 * n, 8 * nd, 8 * nd, 8 * nd, 8 * n, 4 * n,         // gid_b, x_b, vn_b, vnm1_b, pn_b, cell_b
+             16 * n, 32 * n, 8 * n, 8 * nd, 4 * n,                // off, packed (V, p), ap_b, f_b, pcount
+             4 * n * K, n * K,                                    // pj, pcode
+             4 * (ncell + 1), 4 * (ncell + 1), 4 * (ncell / 4096 + 2),   // cell_count, cell_start, scan_tmp
+             256, 2 * n, sizeof(Inst), sizeof(Geom), sizeof(Phys)},     // err, inst_of, tables
+            kCarveArrays};
+    return c;
+}
+constexpr size_t carve_total(size_t n, size_t ncell, size_t K)
+{
+    const Carve c = carve_sizes(n, ncell, K);
+    size_t t = 0;
+    for (int i = 0; i < c.count; ++i) t += round256(c.bytes[i]);
+    return t;
+}
+
+// Scratch bytes: the carve of the largest accepted input (every limit at once),
+// with room for the 256-byte rounding of each array. Any input within the
+// limits needs less: each array grows with n, the cells or n K only.
 constexpr size_t kScratchBytes =
-    ((kPerParticle * kNoallocMaxParticles + 5 * kNoallocMaxEntries + 2 * 4 * (size_t)(kNoallocMaxCells + 1) +
-      64 * 256) + 255) / 256 * 256;
+    carve_total(kNoallocMaxParticles, kNoallocMaxCells + 1, 192) + 256 * kCarveArrays;
+static_assert(carve_total(kNoallocMaxParticles, kNoallocMaxCells + 1, 192) <= kScratchBytes,
+              "the largest accepted input fits the scratch array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -48,10 +79,9 @@ std::mutex g_mu;
 unsigned char *g_scratch_ptr[kMaxDevices];   // device address of the array, per device
 
 // Device address of the scratch array on the current device (fetched once).
-int scratch_address(unsigned char **out)
+int scratch_address(int dev, unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DTSPH_E_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return DTSPH_E_CUDA;
     std::lock_guard<std::mutex> g(g_mu);
     if (!g_scratch_ptr[dev]) {
         void *p = nullptr;
@@ -65,68 +95,58 @@ int scratch_address(unsigned char **out)
     return DTSPH_OK;
 }
 
-// Carves the arrays of a Buffers view out of the scratch array (256-byte aligned);
-// returns the bytes used.
+// Carves the arrays of a Buffers view out of the scratch array (256-byte
+// aligned, the order and sizes of carve_sizes); returns the bytes used.
 size_t carve(unsigned char *base, int n, int ncell, Buffers &B)
 {
+    const Carve sz = carve_sizes((size_t)n, (size_t)ncell, (size_t)B.K);
     size_t off = 0;
-    auto take = [&](size_t bytes) {
+    int at = 0;
+    auto take = [&]() {
         unsigned char *p = base + off;
-        off += (bytes + 255) / 256 * 256;
+        off += round256(sz.bytes[at++]);
         return (void *)p;
     };
-    const size_t nd = (size_t)n * 3;
-    B.gid_a = (uint32_t *)take(4 * (size_t)n);
-    B.x_a = (double *)take(8 * nd);
-    B.vn_a = (double *)take(8 * nd);
-    B.vnm1_a = (double *)take(8 * nd);
-    B.pn_a = (double *)take(8 * (size_t)n);
-    B.key = (int *)take(4 * (size_t)n);
-    B.slot = (int *)take(4 * (size_t)n);
-    B.unsorted = (int *)take(4 * (size_t)n);
-    B.perm = (int *)take(4 * (size_t)n);
-    B.gid_b = (uint32_t *)take(4 * (size_t)n);
-    B.x_b = (double *)take(8 * nd);
-    B.vn_b = (double *)take(8 * nd);
-    B.vnm1_b = (double *)take(8 * nd);
-    B.pn_b = (double *)take(8 * (size_t)n);
-    B.cell_b = (int *)take(4 * (size_t)n);
-    B.off = (float4 *)take(16 * (size_t)n);
-    void *nb = take(32 * (size_t)n);
+    B.gid_a = (uint32_t *)take();
+    B.x_a = (double *)take();
+    B.vn_a = (double *)take();
+    B.vnm1_a = (double *)take();
+    B.pn_a = (double *)take();
+    B.key = (int *)take();
+    B.slot = (int *)take();
+    B.unsorted = (int *)take();
+    B.perm = (int *)take();
+    B.gid_b = (uint32_t *)take();
+    B.x_b = (double *)take();
+    B.vn_b = (double *)take();
+    B.vnm1_b = (double *)take();
+    B.pn_b = (double *)take();
+    B.cell_b = (int *)take();
+    B.off = (float4 *)take();
+    void *nb = take();
     if (B.fp32c) B.nb32[1] = (float4 *)nb;
     else B.nb64[1] = (double4_32a *)nb;
-    B.ap_b = (double *)take(8 * (size_t)n);
-    B.f_b = (double *)take(8 * nd);
-    B.pcount = (int *)take(4 * (size_t)n);
-    B.pj = (uint32_t *)take(4 * (size_t)n * B.K);
-    B.pcode = (uint8_t *)take((size_t)n * B.K);
-    B.cell_count = (int *)take(4 * (size_t)(ncell + 1));
-    B.cell_start = (int *)take(4 * (size_t)(ncell + 1));
-    B.scan_tmp = (int *)take(4 * (size_t)(ncell / 4096 + 2));
-    B.err = (uint32_t *)take(256);
-    B.inst_of = (uint16_t *)take(2 * (size_t)n);
-    B.inst = (Inst *)take(sizeof(Inst));
-    B.geo = (Geom *)take(sizeof(Geom));
-    B.phys = (Phys *)take(sizeof(Phys));
-    return off;
+    B.ap_b = (double *)take();
+    B.f_b = (double *)take();
+    B.pcount = (int *)take();
+    B.pj = (uint32_t *)take();
+    B.pcode = (uint8_t *)take();
+    B.cell_count = (int *)take();
+    B.cell_start = (int *)take();
+    B.scan_tmp = (int *)take();
+    B.err = (uint32_t *)take();
+    B.inst_of = (uint16_t *)take();
+    B.inst = (Inst *)take();
+    B.geo = (Geom *)take();
+    B.phys = (Phys *)take();
+    return at == sz.count ? off : (size_t)-1;
 }
 
-// Neighbour list entries per particle: max_neighbors, else 1.35 times the mean
-// count of a uniform fill of the 3h sphere (disc) plus 8.
-int neighbour_capacity_noalloc(const dtsph_params *p)
+// The device-side error bits of the call as a status code for the caller.
+__global__ void k_noalloc_status(const uint32_t *err, int32_t *status)
 {
-    if (p->max_neighbors > 0) return p->max_neighbors;
-    const double pi = 3.14159265358979323846;
-    const double vol = p->m / p->rho0, rc = 3.0 * p->h;
-    const double expect = p->dim == 2 ? pi * rc * rc / vol : 4.0 / 3.0 * pi * rc * rc * rc / vol;
-    const int k = (int)std::ceil(1.35 * expect) + 8;
-    return std::min(std::max(k, 8), 4096);
-}
-
-double quintic_sigma_noalloc(int dim, double h)
-{
-    const double pi = 3.14159265358979323846;
-    return dim == 2 ? 7.0 / (478.0 * pi * h * h) : 1.0 / (120.0 * pi * h * h * h);
+    const uint32_t e = *err;
+    *status = (e & kErrCapacity) ? DTSPH_E_CAPACITY : (e & kErrDomain) ? DTSPH_E_DOMAIN : DTSPH_OK;
 }
 
 }  // namespace
@@ -136,82 +156,31 @@ using namespace dtsph;
 
 extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const double *x, const double *v,
                                         const double *pr, int64_t nw, const double *xw, const double *vw, double *ap,
-                                        double *F, void *stream)
+                                        double *F, int32_t *status, void *stream)
 {
     if (!p || !x || !v || !pr || !ap || !F || nf <= 0 || nw < 0 || (nw > 0 && !xw)) return DTSPH_E_ARG;
     const int64_t nslots = (nf + nw + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
     if (nslots > kNoallocMaxParticles) return DTSPH_E_CAPACITY;   // beyond the fixed scratch
-    if ((p->dim != 2 && p->dim != 3) || (p->precision != DTSPH_FP64 && p->precision != DTSPH_FP32C))
-        return DTSPH_E_ARG;
-    if (!(p->h > 0) || !(p->m > 0) || !(p->rho0 > 0) || !(p->beta > 0) || !(p->v_ref > 0) || !(p->dt > 0) ||
-        !(p->eta > 0) || !(p->nu >= 0) || !(p->alpha >= 0))
-        return DTSPH_E_ARG;
-    if (p->edac_h2_literal) return DTSPH_E_UNSUPPORTED;
-
-    // cell grid: cells wider than 3h, at least three per periodic axis
-    Geom G;
-    memset(&G, 0, sizeof G);
-    G.dim = p->dim;
-    const double rc = 3.0 * p->h;
-    G.ncell = 1;
-    for (int a = 0; a < 3; ++a) {
-        G.periodic[a] = a < p->dim ? p->periodic[a] : 0;
-        G.lo[a] = p->lo[a];
-        G.hi[a] = p->hi[a];
-        if (a >= p->dim) {
-            G.nc[a] = 1;
-            G.s[a] = G.inv_s[a] = G.L[a] = 1.0;
-            G.s_f[a] = 1.f;
-            G.halfL[a] = 0.5;
-            continue;
-        }
-        const double L = p->hi[a] - p->lo[a];
-        if (!(L > 0)) return DTSPH_E_ARG;
-        long long k = (long long)std::floor(L / (rc * (1.0 + 1e-9)));
-        if (k < 1) k = 1;
-        if (G.periodic[a] && k < 3) return DTSPH_E_ARG;
-        if (k >= kNoallocMaxCells || (long long)G.ncell * k >= kNoallocMaxCells) return DTSPH_E_CAPACITY;
-        G.nc[a] = (int)k;
-        G.s[a] = L / (double)k;
-        G.inv_s[a] = 1.0 / G.s[a];
-        G.s_f[a] = (float)G.s[a];
-        G.L[a] = L;
-        G.halfL[a] = 0.5 * L;
-        G.ncell *= (int)k;
-    }
-    G.rc2 = rc * rc;
-    G.rc2_lo = (float)(G.rc2 * (1.0 - 2e-5));
-    G.rc2_hi = (float)(G.rc2 * (1.0 + 2e-5));
-
-    // pair-term constants, rho_i = rho_j = rho0
-    Phys P;
-    memset(&P, 0, sizeof P);
-    P.h = p->h;
-    P.m = p->m;
-    P.rho0 = p->rho0;
-    P.c = p->beta * p->v_ref;
-    P.nu = p->nu;
-    P.nu_e = p->h * P.c / 16.0;
-    P.dt = p->dt;
-    P.dtau = p->dt / p->beta;
-    P.dtau_f = (float)P.dtau;
-    P.sig_h = quintic_sigma_noalloc(p->dim, p->h) / p->h;
-    P.inv_h = 1.0 / p->h;
-    P.eta_h2 = p->eta * p->h * p->h;
-    P.edac_h2 = P.eta_h2;
-    const double rho = p->rho0;
-    P.c_div = p->m * (rho / rho) * P.c * P.c;
-    P.c_edac = 4.0 * p->m / ((rho + rho) * rho) * P.nu_e;
-    P.c_p = p->m / (rho * rho);
-    P.c_visc = 4.0 * p->m * p->nu / (rho + rho);
-    P.c_av = p->alpha * p->h * P.c / rho;
-    for (int a = 0; a < 3; ++a) P.g[a] = a < p->dim ? p->g[a] : 0.0;
-    P.edac = p->edac;
-    P.use_av = p->alpha != 0.0;
-
-    unsigned char *base = nullptr;
-    int r = scratch_address(&base);
+    // the same reading of the parameters as dtsph_create / dtsph_eval_rates
+    int r = check_params(p, nullptr, 0);
     if (r) return r;
+    Geom G;
+    if ((r = make_geometry(*p, G, nullptr, 0))) return r;
+    if (G.ncell + 1 > kNoallocMaxCells + 1) return DTSPH_E_CAPACITY;
+    Phys P;
+    make_phys(*p, P);
+
+    // the kernels run on the caller's stream, so the scratch address must be the
+    // one of that stream's device, which must be the current one
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sdev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return DTSPH_E_CUDA;
+    }
+    if (sdev != dev) return DTSPH_E_ARG;
+    unsigned char *base = nullptr;
+    if ((r = scratch_address(dev, &base))) return r;
     Buffers B;
     memset(&B, 0, sizeof B);
     B.n = (int)nslots;
@@ -221,7 +190,7 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     B.fp32c = p->precision == DTSPH_FP32C;
     B.ninst = 1;
     B.ncell = G.ncell + 1;           // the instance's cells and its empty sentinel cell
-    B.K = neighbour_capacity_noalloc(p);
+    B.K = neighbour_capacity(*p);
     if ((size_t)B.n * B.K > kNoallocMaxEntries) return DTSPH_E_CAPACITY;
     if (carve(base, B.n, B.ncell, B) > kScratchBytes) return DTSPH_E_CAPACITY;
     Inst I;
@@ -229,7 +198,6 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     I.nf = (int)nf;
     I.nw = (int)nw;
 
-    cudaStream_t st = (cudaStream_t)stream;
     // the counting sort needs zeroed cell counters and -1 in the permutation
     // slots it never writes; the last call may have left any state there
     if (cudaMemsetAsync(B.cell_count, 0, sizeof(int) * (size_t)B.ncell, st) != cudaSuccess ||
@@ -247,6 +215,7 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     launch_state_n(B, false, st);
     launch_unpermute(B, B.gid_b, B.ap_b, ap, 1, st);
     launch_unpermute(B, B.gid_b, B.f_b, F, B.dim, st);
+    if (status) k_noalloc_status<<<1, 1, 0, st>>>(B.err, status);
     if (cudaGetLastError() != cudaSuccess) return DTSPH_E_CUDA;
     return DTSPH_OK;
 }

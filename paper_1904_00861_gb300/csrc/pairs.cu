@@ -11,6 +11,7 @@
 // tests an FP32 separation built from per-cell FP32 offsets and falls back to the
 // FP64 test only inside a thin band around 3h, so both paths give the same sets.
 #include "geometry.cuh"
+#include "loop_rules.cuh"
 
 namespace dtsph {
 
@@ -601,20 +602,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
     __shared__ Geom G;
     __shared__ Phys P;
     if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
-            LoopState *ls = B.ls + i;
-            ls->iter = 0;
-            ls->done = 0;
-            ls->reason = -1;
-            ls->ticket = 0;
-            ls->rp = 0;
-            ls->rv = 0;
-        }
-        if (threadIdx.x == 0) {
-            B.ctrl->ticket = 0;
-            B.ctrl->bar = 0;
-            B.ctrl->active = B.ninst;
-        }
+        reset_loops(B);
     }
     const int inst = block_instance(B, blockIdx.x * SPB);
     block_copy(G, B.geo[inst]);
@@ -691,8 +679,10 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
 // ---------------------------------------------------------------- shifting
 
 // Particle shifting after the real step (Sec. 3.5), in order B at r^{n+1}, one
-// lane per slot, over fluid neighbours only (free-surface runs: particles with
-// div r_i < dim - 1/2, fluid and wall neighbours counted, stay where they are):
+// lane per slot; the displacement over every neighbour (wall particles continue
+// the particle distribution), the gradients of the correction over fluid
+// neighbours (free-surface runs: particles with div r_i < dim - 1/2, fluid and
+// wall neighbours counted, stay where they are):
 //   dr_i = -(h^2/2) sum_j V_j (1 + W_ij / W(h)) gradW_ij          Eq. (shift-deltar)
 //   f_i <- f_i + (grad f)_i . dr_i, (grad f)_i = sum_j V_j (f_j - f_i) gradW_ij
 //                                                      for f = p, V   Eq. (shift-correct)
@@ -738,16 +728,19 @@ __global__ void __launch_bounds__(kBlock) k_shift(Buffers B)
         const T q = r * (T)P.inv_h;
         const T a = r > T(0) ? (T)P.sig_h * quintic_dwdq<T>(q) / r : T(0);
         divr -= (double)(vol * a * r2);                   // r_ij . gradW_ij = (dW/dr / r) r^2
-        if (jb & kWallBit) continue;                      // fluid neighbours only from here
-
+        // the displacement counts every neighbour, wall particles included
+        // (they continue the particle distribution)
         const T fdr = vol * (T(1) + sigma * quintic_w<T>(q) / w_h);
+#pragma unroll
+        for (int c = 0; c < D; ++c) dr[c].add(fdr * (a * d[c]));
+        if (jb & kWallBit) continue;                      // the gradients: fluid neighbours only
+
         const auto qj = nb[j];
         const T vj[3] = {(T)qj.x, (T)qj.y, (T)qj.z};
         const T dp = vol * ((T)qj.w - pi);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const T gw = a * d[c];
-            dr[c].add(fdr * gw);
             gp[c].add(dp * gw);
 #pragma unroll
             for (int b2 = 0; b2 < D; ++b2) gv[b2][c].add(vol * (vj[b2] - vi[b2]) * gw);

@@ -74,13 +74,27 @@ def test_version_and_argument_errors_without_gpu(so):
     assert e.value.code == -1
 
 
-def test_struct_layouts_match_header():
-    """ctypes mirrors of the C structs have the C sizes (checked by offsets)."""
-    P = lib_pkg.dtsph_params
-    assert P.lo.offset == 24 and P.h.offset == 72
-    assert P.moving.offset == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 12 and P.skin.offset % 8 == 0
-    assert ctypes.sizeof(P) == 72 + 8 * 9 + 24 + 8 * 2 + 4 * 14 + 8
-    assert ctypes.sizeof(lib_pkg.dtsph_step_stats) == 24
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the C structs have the header's field offsets and
+    sizes, as a C compiler lays them out (gcc on include/dtsph.h)."""
+    import subprocess
+    structs = {"dtsph_params": lib_pkg.dtsph_params, "dtsph_step_stats": lib_pkg.dtsph_step_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dtsph.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln.strip())}
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
 
 
 def test_missing_library_fails_loudly(monkeypatch):

@@ -35,6 +35,25 @@ def test_default_run_is_one_gpu_and_short(monkeypatch):
     assert a.gpus == 1 and a.warmup >= 3 and a.steps <= 200 and a.impl == "ours"
 
 
+def test_default_workload_is_the_batched_ensemble(monkeypatch):
+    """The metric is quoted on the batched ensemble (64 Taylor-Green instances,
+    FP32-compensated, one persistent launch per step): that is the default."""
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    d, wcfg = bench.make_workload(a.workload, a.n_side, a.re)
+    assert a.workload == "batch" and wcfg["workload"] == "batch-64x-tgv2d" and len(d) == 64
+    assert wcfg["particles"] == 1499340
+
+
+def test_algorithmic_bytes_and_flops_follow_the_pair_cache_form():
+    """Per particle-iteration: own state (52 / 72 B on the compensated path, 88 /
+    120 B in FP64) plus one cache entry per pair (16 / 20 B, 28 / 36 B); FP64
+    flops 8 dim + 3 per particle and 8 dim + 9 per pair."""
+    assert bench.STATE_BYTES[(2, True)] + 27.3 * bench.PAIR_BYTES[(2, True)] == pytest.approx(488.8)
+    assert bench.STATE_BYTES[(3, True)] + 112 * bench.PAIR_BYTES[(3, True)] == pytest.approx(2312)
+    assert bench.fp64_flops(2) == (19.0, 25.0) and bench.fp64_flops(3) == (27.0, 33.0)
+
+
 def test_traffic_figures_come_from_committed_profiles():
     for (workload, dim, lanes, stages), (byts, src) in bench.NCU_TRAFFIC.items():
         path = os.path.join(ROOT, src.split(",")[0])

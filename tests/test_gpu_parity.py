@@ -332,6 +332,31 @@ def test_autotuner_picks_a_candidate_and_caches_it():
     b.close()
 
 
+def test_autotuner_choice_persists_across_processes(tmp_path):
+    """With DTSPH_TUNE_CACHE set, the first process tunes a shape and appends its
+    choice to the file; a fresh process takes the same choice from the file and
+    times nothing."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import json, synth, paper_1904_00861_gb300 as dt\n"
+            "d = synth.tgv2d(72, seed=2)\n"
+            "s = dt.Simulation(d['cfg'], precision=dt.DTSPH_FP32C, lanes=0, graph=2)\n"
+            "s.set_state(d['x'], d['v'], d['p'], d['v_prev'])\n"
+            "print(json.dumps([dt.dtsph_tuning(s.ctx)[0], *dt.dtsph_tuning_candidates(s.ctx)]))\n")
+    env = dict(os.environ, DTSPH_TUNE_CACHE=str(tmp_path / "tune.txt"))
+    run = lambda: json.loads(subprocess.run([sys.executable, "-c", code], cwd=root, env=env, check=True,
+                                            capture_output=True, text=True).stdout.strip().splitlines()[-1])
+    lanes1, stages1, cand1 = run()
+    assert len(cand1) == 7
+    lines = (tmp_path / "tune.txt").read_text().split("\n")
+    assert lines[0].startswith("dtsph-tune-v1 ") and lines[0].split()[-2:] == [str(lanes1), str(stages1 or 3)]
+    lanes2, stages2, cand2 = run()
+    assert (lanes2, stages2, cand2) == (lanes1, stages1, [])
+
+
 @pytest.mark.parametrize("graph", [0, 1, 2])
 def test_loop_times_cover_each_step(graph):
     """Events around the pseudo-time loop of every step (graph event nodes, or
@@ -699,3 +724,22 @@ def test_host_and_device_transfers_agree():
         assert np.array_equal(dt.dtsph_read_field(b.ctx, f, nf, comps), dt.dtsph_read_field(c.ctx, f, nf, comps))
     for s in (a, b, c):
         s.close()
+
+
+@pytest.mark.parametrize("graph", [0, 1, 2])
+def test_step_stats_report_max_velocity(graph):
+    """dtsph_step_stats.vmax is max |V^{n+1}| over the fluid particles: equal to
+    the maximum over the velocities read back after the step, and within 1e-10
+    of the oracle's on the FP64 path (the Taylor-Green decay diagnostic)."""
+    d = CASES["tgv2d_jitter"]()
+    sim = make_sim(d, graph=graph)
+    orc = make_oracle(d)
+    for k in range(3):
+        sim.step(1)
+        orc.step(1)
+        st = sim.stats(k, 1)[0]
+        v = sim.v
+        assert st["vmax"] == np.max(np.sqrt(np.sum(v * v, axis=1)))
+        vo = np.max(np.sqrt(np.sum(orc.v * orc.v, axis=1)))
+        assert abs(st["vmax"] - vo) < 1e-10 * vo
+    sim.close()

@@ -55,6 +55,9 @@ MUTANTS = [
       "test_shifting_displacement_matches_its_continuum_limit"]),
     ("shift_drop_one", "(1.0 + W / wdx)", "(W / wdx)", ["test_shifting_displacement_matches_its_continuum_limit"]),
     ("shift_drop_w", "(1.0 + W / wdx)", "(1.0)", ["test_shifting_displacement_matches_its_continuum_limit"]),
+    ("shift_walls_left_out", "dr[i * dim + a] = dr[i * dim + a] + vol * (1.0 + W / wdx) * gw;",
+     "if (j < nf) dr[i * dim + a] = dr[i * dim + a] + vol * (1.0 + W / wdx) * gw;",
+     ["test_shifting_counts_wall_particles_in_the_displacement"]),
     ("taylor_p_sign", "p[i] = p[i] + dp;", "p[i] = p[i] - dp;", ["test_shifting_taylor_correction_carries_linear_fields"]),
     ("taylor_p_dropped", "p[i] = p[i] + dp;", "p[i] = p[i];", ["test_shifting_taylor_correction_carries_linear_fields"]),
     ("taylor_v_dropped", "v[i * dim + b] = v[i * dim + b] + dvb;", "v[i * dim + b] = v[i * dim + b];",

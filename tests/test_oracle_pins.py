@@ -135,6 +135,28 @@ def test_cell_list_equals_bruteforce(case):
     assert np.array_equal(s1, s2) and np.array_equal(i1, i2)
 
 
+def test_state_brings_periodic_inputs_into_the_box_and_refuses_non_finite():
+    """Positions given outside [lo, hi) on a periodic axis are brought in by
+    whole box lengths (against numpy's floored modulo), walls included; a
+    non-finite position is refused."""
+    d = synth.tgv2d(12, jitter=0.1, seed=6)
+    x = d["x"].copy()
+    x[::2, 0] += 1.0
+    x[::3, 1] -= 2.5
+    x[5, 0] = 1.0                      # exactly on the upper edge
+    st = oracle.State(d["cfg"], x, d["v"], d["p"])
+    assert np.max(np.abs(st.x - np.mod(x, 1.0))) < 1e-15
+    assert np.all(st.x >= 0.0) and np.all(st.x < 1.0)
+    bad = d["x"].copy()
+    bad[3, 1] = np.inf
+    with pytest.raises(ValueError):
+        oracle.State(d["cfg"], bad, d["v"], d["p"])
+    c = synth.cavity2d(10)
+    cx = c["x"].copy()
+    cx[0, 0] = 7.0                     # not periodic: left as given
+    assert oracle.State(c["cfg"], cx, c["v"], c["p"], nf=c["nf"]).x[0, 0] == 7.0
+
+
 # ---------------------------------------------------------------- operators
 
 def _lattice(n=50):
@@ -439,6 +461,20 @@ def test_shifting_is_zero_on_a_lattice_and_reduces_disorder():
     before = np.abs(st.x - lat).mean()
     st.step(1)
     assert np.abs(st.x - lat).mean() < 0.9 * before
+
+
+def test_shifting_counts_wall_particles_in_the_displacement():
+    """Eq. (shift-deltar) sums over the neighbours of i, and wall particles are
+    neighbours: on a cavity whose fluid and three wall layers form one regular
+    lattice, every fluid particle sees a symmetric support, so no particle moves
+    (to rounding). Leaving the walls out of the sum would push every particle
+    within 3h of a wall into it."""
+    d = synth.cavity2d(20)
+    nf = d["nf"]
+    x = d["x"]
+    xs, vs, ps = oracle.shift(d["cfg"], x, d["v"], d["p"], nf=nf)
+    assert np.max(np.abs(xs - x[:nf])) < 1e-15
+    assert np.array_equal(vs, d["v"]) and np.array_equal(ps, d["p"])
 
 
 def _open_box(cfg):
