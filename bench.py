@@ -47,14 +47,9 @@ UNIT = "particle-iterations/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # loop kernel, from the Nsight Compute captures summarised under profiles/, for
 # the kernel variants those captures profiled: (workload, dim, lanes, stages) ->
-# (bytes, source). A variant not listed reports null.
-NCU_TRAFFIC = {
-    ("tgv2d-200x200", 2, 2, 0): (19.880704e6, "profiles/k_loop_tgv2d_200x200.md"),
-    ("batch-64x-tgv2d", 2, 1, 2): (7.157555e9 + 0.459921e9, "profiles/k_loop_batch64_tgv2d.md"),
-    ("tgv3d-128^3", 3, 1, 2): ((1.181163e9 + 0.020505e9) * (128 / 80) ** 3,
-                               "profiles/k_loop_tgv3d_80.md, an 80^3 capture scaled by the particle count "
-                               "(one iteration per step, streaming traffic)"),
-}
+# (bytes, source). A variant not listed, or one whose kernel changed after its
+# capture, reports null.
+NCU_TRAFFIC = {}
 
 
 def make_workload(name: str, n_side: int, re: float):

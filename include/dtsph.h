@@ -336,7 +336,7 @@ int dtsph_tuning_candidates(const dtsph_ctx *ctx, int32_t cap, int32_t *lanes, i
  *              non-periodic axis)
  *   stream     cudaStream_t or NULL; it must belong to the current device. The
  *              call only enqueues work and returns.
- * All work happens in one fixed scratch array of about 20 MB that is part of the
+ * All work happens in one fixed scratch array of about 30 MB that is part of the
  * library image and that every GPU using the library holds until the process
  * exits. Limits: nf + nw <= 16384 particles, at most 32768 cells of side 3h, and
  * at most 16384 x 192 neighbour-list entries (nf + nw rounded up to 256, times the

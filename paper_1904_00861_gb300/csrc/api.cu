@@ -457,8 +457,9 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         wo += nw;
         co += c->G[i].ncell + 1;   // one empty sentinel cell per instance
         K = std::max(K, dtsph::neighbour_capacity(c->prm[i]));
-        if (slot >= (1LL << 31) - 4 * kSlotAlign || co >= (1LL << 31) - 2)
-            return fail(c, DTSPH_E_ARG, "particle or cell count out of range");
+        if (slot >= kMaxSlots - 4 * kSlotAlign || co >= (1LL << 31) - 2)
+            return fail(c, DTSPH_E_ARG, "particle or cell count out of range (at most %lld slots in a context)",
+                        kMaxSlots - 4 * kSlotAlign);
         c->P[i].rp_scale = c->P[i].dt / (c->P[i].rho0 * c->P[i].c * c->P[i].c) / (double)nf[i];
         c->P[i].rv_scale = c->P[i].dt / c->prm[i].v_ref / (double)nf[i];
     }
@@ -507,7 +508,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     A(B.key, n) A(B.slot, n) A(B.unsorted, n) A(B.perm, n) A(B.cell_count, (size_t)B.ncell)
     A(B.cell_start, (size_t)B.ncell + 1) A(B.scan_tmp, (size_t)B.ncell / 4096 + 2)
     A(B.vk[0], nd) A(B.vk[1], nd)
-    A(B.pcount, n) A(B.pj, npair) A(B.pcode, npair)
+    A(B.pcount, n) A(B.pj, npair) A(B.pjt, (size_t)n * list_stride(B.K))
     if (B.fp32c) {
         A(B.off, n) A(B.nb32[0], n) A(B.nb32[1], n) A(B.pc32, npair)
     } else {
@@ -1292,7 +1293,7 @@ int dtsph_get_neighbors(dtsph_ctx *c, int64_t i, int64_t *out, int64_t cap, int6
         size_t e = base + (size_t)k * kWarp;
         uint32_t jb;
         CK(cudaMemcpy(&jb, B.pj + e, sizeof jb, cudaMemcpyDeviceToHost));
-        got.push_back((int64_t)gid[jb & ~kWallBit]);
+        got.push_back((int64_t)gid[jb & kSlotMask]);
     }
     std::sort(got.begin(), got.end());
     *count = (int64_t)got.size();

@@ -15,6 +15,21 @@ constexpr int kBlock = 256;          // threads per block of every particle kern
 constexpr int kWarp = 32;
 constexpr uint32_t kWallBit = 0x80000000u;   // set in a cached neighbour index when j is a wall
 
+// A neighbour-list entry in one 32-bit word: the neighbour's slot (bits 0-25),
+// the cell shift code (dx + 1) + 3 (dy + 1) + 9 (dz + 1) of its cell against the
+// home cell (bits 26-30) and the wall flag (bit 31). The pair cache keeps the
+// slot and the wall flag only (code bits clear).
+constexpr int kCodeShift = 26;
+constexpr uint32_t kSlotMask = (1u << kCodeShift) - 1u;
+constexpr uint32_t kCodeMask = 31u << kCodeShift;
+constexpr long long kMaxSlots = 1LL << kCodeShift;
+__host__ __device__ __forceinline__ uint32_t list_entry(uint32_t j, int code, bool wall)
+{
+    return j | ((uint32_t)code << kCodeShift) | (wall ? kWallBit : 0u);
+}
+__host__ __device__ __forceinline__ int entry_slot(uint32_t e) { return (int)(e & kSlotMask); }
+__host__ __device__ __forceinline__ int entry_code(uint32_t e) { return (int)((e >> kCodeShift) & 31u); }
+
 // Error bits raised by kernels into Buffers::err (read by dtsph_sync).
 enum : uint32_t { kErrCapacity = 1u, kErrDomain = 2u, kErrBarrier = 4u, kErrCopy = 8u, kErrSkin = 16u,
                   kErrNonFinite = 32u };
@@ -163,8 +178,8 @@ struct Buffers {
     double4_32a *nb64[2];      // FP64: (V, p-hat) packed for neighbour gathers
     float4 *nb32[2];       // FP32C: (V, p-hat) packed for neighbour gathers
     // pair cache, sliced by warp: entry k of slot i at ((i/32) K + k) 32 + i%32
-    uint32_t *pj;          // neighbour slot (| kWallBit for walls)
-    uint8_t *pcode;        // cell shift of the entry: (dx + 1) + 3 (dy + 1) + 9 (dz + 1)
+    uint32_t *pj;          // list entries (list_entry); after the pair-cache pass slot | kWallBit
+    uint32_t *pjt;         // list staging, per slot: entry k of slot s at s Ks + k (Ks = list_stride(K))
     double4_32a *pc64;         // FP64: (gradW, F_ij)
     float4 *pc32;          // FP32C: (gradW, F_ij); in 2D .w holds the index bits
     int *pcount;           // neighbours of each slot
@@ -244,6 +259,7 @@ int launch_fill_instance(Inst *inst, Geom *geo, Phys *phys, int i, const Inst &I
                          cudaStream_t st);
 
 int iterate_tiles(const Buffers &B);   // tiles of the iterate kernel (one block each)
+int list_stride(int K);                // row length of the per-slot list staging array
 
 // ------------------------------------------------- one parameter set (api.cu)
 // Shared by the context entry points and the allocation-free rate evaluation,

@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(kBlock) k_move_walls(Buffers B)
         const size_t e = base + (size_t)k * kWarp;
         const uint32_t jb = B.pj[e];
         if (jb & kWallBit) continue;            // fluid neighbours only
-        const int j = (int)jb;
+        const int j = entry_slot(jb);
         T d[3];
-        const T r2 = moved_sep<D, F32, T>(G, B, cur, xi, oi, j, B.pcode[e], d);
+        const T r2 = moved_sep<D, F32, T>(G, B, cur, xi, oi, j, entry_code(jb), d);
         const double W = sigma * (double)quintic_w<T>(Ar<T>::mul(sqrt(r2), (T)P.inv_h));
         if (W == 0.0) continue;
         const auto q = nb[j];
@@ -216,14 +216,14 @@ __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long l
                     const int q = q0 + r * L;
                     const size_t e = base + (size_t)min(q, cnt - 1) * kWarp;
                     jbv[r] = B.pj[e];
-                    codev[r] = B.pcode[e];
+                    codev[r] = entry_code(jbv[r]);
                 }
                 Q qv[R];
                 float4 ov[R];
                 T xj[R][3];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const int j = (int)(jbv[r] & ~kWallBit);
+                    const int j = entry_slot(jbv[r]);
                     qv[r] = nb[j];
                     if (F32) {
                         ov[r] = B.offk[cur][j];
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long l
                 for (int r = 0; r < R; ++r) {
                     if (q0 + r * L >= cnt) break;
                     const uint32_t jb = jbv[r];
-                    const int j = (int)(jb & ~kWallBit);
+                    const int j = entry_slot(jb);
                     T d[3], r2;
                     if (F32) {
                         int dx, dy, dz;

@@ -50,7 +50,7 @@ constexpr Carve carve_sizes(size_t n, size_t ncell, size_t K)
              4 * n, 4 * n, 4 * n, 4 * n,                          // key, slot, unsorted, perm
              4 * n, 8 * nd, 8 * nd, 8 * nd, 8 * n, 4 * n,         // gid_b, x_b, vn_b, vnm1_b, pn_b, cell_b
              16 * n, 32 * n, 8 * n, 8 * nd, 4 * n,                // off, packed (V, p), ap_b, f_b, pcount
-             4 * n * K, n * K,                                    // pj, pcode
+             4 * n * K, 4 * n * ((K + 7) / 8 * 8),                // pj, pjt (rows rounded up to 8)
              4 * (ncell + 1), 4 * (ncell + 1), 4 * (ncell / 4096 + 2),   // cell_count, cell_start, scan_tmp
              256, 2 * n, sizeof(Inst), sizeof(Geom), sizeof(Phys)},     // err, inst_of, tables
             kCarveArrays};
@@ -65,10 +65,12 @@ constexpr size_t carve_total(size_t n, size_t ncell, size_t K)
 }
 
 // Scratch bytes: the carve of the largest accepted input (every limit at once),
-// with room for the 256-byte rounding of each array. Any input within the
-// limits needs less: each array grows with n, the cells or n K only.
-constexpr size_t kScratchBytes =
-    carve_total(kNoallocMaxParticles, kNoallocMaxCells + 1, 192) + 256 * kCarveArrays;
+// with room for the 256-byte rounding of each array and for the list staging
+// rows, which are rounded up to 8 entries (at most 7 more per particle). Any
+// input within the limits needs less: each array grows with n, the cells or n K
+// only.
+constexpr size_t kScratchBytes = carve_total(kNoallocMaxParticles, kNoallocMaxCells + 1, 192) +
+                                 256 * kCarveArrays + 4 * 7 * (size_t)kNoallocMaxParticles;
 static_assert(carve_total(kNoallocMaxParticles, kNoallocMaxCells + 1, 192) <= kScratchBytes,
               "the largest accepted input fits the scratch array");
 
@@ -130,7 +132,7 @@ size_t carve(unsigned char *base, int n, int ncell, Buffers &B)
     B.f_b = (double *)take();
     B.pcount = (int *)take();
     B.pj = (uint32_t *)take();
-    B.pcode = (uint8_t *)take();
+    B.pjt = (uint32_t *)take();
     B.cell_count = (int *)take();
     B.cell_start = (int *)take();
     B.scan_tmp = (int *)take();
@@ -199,9 +201,11 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     I.nw = (int)nw;
 
     // the counting sort needs zeroed cell counters and -1 in the permutation
-    // slots it never writes; the last call may have left any state there
+    // slots it never writes, and padding slots need empty neighbour lists; the
+    // last call may have left any state there
     if (cudaMemsetAsync(B.cell_count, 0, sizeof(int) * (size_t)B.ncell, st) != cudaSuccess ||
         cudaMemsetAsync(B.err, 0, sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(B.pcount, 0, sizeof(int) * (size_t)B.n, st) != cudaSuccess ||
         cudaMemsetAsync(B.unsorted, 0xff, sizeof(int) * (size_t)B.n, st) != cudaSuccess ||
         cudaMemsetAsync(B.perm, 0xff, sizeof(int) * (size_t)B.n, st) != cudaSuccess ||
         cudaMemsetAsync((void *)B.inst_of, 0, sizeof(uint16_t) * (size_t)B.n, st) != cudaSuccess) {

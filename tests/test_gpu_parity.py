@@ -728,8 +728,8 @@ def test_host_and_device_transfers_agree():
 
 @pytest.mark.parametrize("graph", [0, 1, 2])
 def test_step_stats_report_max_velocity(graph):
-    """dtsph_step_stats.vmax is max |V^{n+1}| over the fluid particles: equal to
-    the maximum over the velocities read back after the step, and within 1e-10
+    """dtsph_step_stats.vmax is max |V^{n+1}| over the fluid particles: the
+    maximum over the velocities read back after the step (to an ulp or two), and within 1e-10
     of the oracle's on the FP64 path (the Taylor-Green decay diagnostic)."""
     d = CASES["tgv2d_jitter"]()
     sim = make_sim(d, graph=graph)
@@ -739,7 +739,8 @@ def test_step_stats_report_max_velocity(graph):
         orc.step(1)
         st = sim.stats(k, 1)[0]
         v = sim.v
-        assert st["vmax"] == np.max(np.sqrt(np.sum(v * v, axis=1)))
+        vmax = np.max(np.sqrt(np.sum(v * v, axis=1)))
+        assert abs(st["vmax"] - vmax) <= 4e-16 * vmax       # the GPU sums the squares with FMA
         vo = np.max(np.sqrt(np.sum(orc.v * orc.v, axis=1)))
         assert abs(st["vmax"] - vo) < 1e-10 * vo
     sim.close()
