@@ -349,9 +349,10 @@ def run_e2e(dt, torch, d, precision, steps, graph=2, kern=None):
 
 
 def run_trace(dt, d, steps, every, graph=2, kern=None):
-    """The same steps again, untimed (FP32C): iterations and stop reason of
-    every step of every instance, and the kinetic energy (1/2) sum m |V|^2 of all
-    fluid particles every `every` steps (t = step x dt of the first instance)."""
+    """The same steps again, untimed (FP32C): the kinetic energy (1/2) sum m |V|^2
+    of all fluid particles every `every` steps (t = step x dt of the first
+    instance), the mean pseudo-iterations per step over each such block of
+    steps, and the stop reasons of all steps."""
     job = Job(dt, d, dt.DTSPH_FP32C, graph=graph, kern=kern)
     insts = d if isinstance(d, list) else [d]
     m = np.concatenate([np.full(x["nf"], x["cfg"]["m"]) for x in insts])
@@ -363,14 +364,19 @@ def run_trace(dt, d, steps, every, graph=2, kern=None):
         job.step(k)
         done += k
         v = job.velocities()
-        ke.append([done * dt0, float(0.5 * np.sum(m[:, None] * v * v))])
+        ke.append([round(done * dt0, 6), float(0.5 * np.sum(m[:, None] * v * v))])
     job.sync()
-    its = job.iterations(0, steps)
+    its = np.array(job.iterations(0, steps)).max(0)
+    reasons = []
+    for i in range(len(insts)):
+        st = job.sim.stats(i, 0, steps) if job.batch else job.sim.stats(0, steps)
+        reasons += [s["reason"] for s in st]
     job.close()
-    per_step = np.array(its).max(0)
-    return {"steps": steps, "kinetic_energy": ke, "iters_per_step_max_over_instances": per_step.tolist(),
-            "iters_first_10": per_step[:10].tolist(), "iters_last_10": per_step[-10:].tolist(),
-            "iters_mean": float(np.mean(its))}
+    blocks = [float(np.mean(its[b:b + every])) for b in range(0, steps, every)]
+    names = {0: "converged", 1: "stagnated", 2: "iteration cap", 3: "non-finite", 4: "fixed count"}
+    return {"steps": steps, "every": every, "kinetic_energy": ke, "iters_per_step_mean_by_block": blocks,
+            "iters_total": int(its.sum()),
+            "stop_reasons": {names[r]: int(c) for r, c in zip(*np.unique(reasons, return_counts=True))}}
 
 
 def oracle_states(d, **over):
