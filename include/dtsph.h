@@ -274,8 +274,10 @@ int dtsph_get_neighbors(dtsph_ctx *ctx, int64_t i, int64_t *out, int64_t cap, in
  * returns the mean launch duration in milliseconds, the algorithmic bytes one
  * launch must move (particle state read and written once, every cached pair
  * read once; the layout is described in the design notes) and the number of
- * cached fluid pairs. The state r^n, V^n, p^n is not changed. Waits for the
- * stream. */
+ * cached fluid pairs. With shifting on, the shifting pass has replaced the
+ * step's lists by its own, so the kernel runs on a pair cache built for the
+ * current positions instead (DTSPH_E_STATE with moving != 0). The state r^n,
+ * V^n, p^n is not changed. Waits for the stream. */
 int dtsph_probe_iterate(dtsph_ctx *ctx, int32_t launches, float *ms_per_launch, double *bytes_per_launch,
                         int64_t *pairs);
 

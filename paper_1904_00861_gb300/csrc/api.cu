@@ -524,6 +524,14 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     // two residual partials per tile (at most one tile per warp of slots),
     // double-buffered by the persistent loop
     A(B.blk, 4 * nwarps) A(B.ls, ni) A(B.ctrl, 1) A(B.stats, (size_t)kStatRing * ni) A(B.err, 1)
+    // batches without walls (frozen particles) run the decoupled loop kernel,
+    // unless DTSPH_LOCKSTEP_LOOP=1 asks for the lockstep one (comparisons)
+    int *d_sched = nullptr;
+    B.async_loop = ni > 1 && ni <= kDealMaxInst && wo == 0 && !(c->prm[0].moving && !c->prm[0].steady) &&
+                   env_u64("DTSPH_LOCKSTEP_LOOP", 0) == 0;
+    if (B.async_loop) {
+        A(B.il, ni) A(d_sched, ni)
+    }
 #undef A
     B.inst = d_inst;
     B.geo = d_geo;
@@ -551,6 +559,18 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     CK(cudaMemcpy(d_phys, c->P.data(), sizeof(Phys) * ni, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_inst_of, inst_of.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(B.ls, ls.data(), sizeof(LoopState) * ni, cudaMemcpyHostToDevice));
+    if (B.async_loop) {
+        // search order of the decoupled loop: the instances with the fewest
+        // tiles first (they take the most iterations)
+        std::vector<int> order(ni);
+        for (int i = 0; i < ni; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return c->I[a].nf + c->I[a].nw < c->I[b].nf + c->I[b].nw;
+        });
+        CK(cudaMemcpy(d_sched, order.data(), sizeof(int) * ni, cudaMemcpyHostToDevice));
+        CK(cudaMemset(B.il, 0, sizeof(InstLoop) * ni));
+        B.sched = d_sched;
+    }
     CK(cudaMemset(B.ctrl, 0, sizeof(LoopCtrl)));
     CK(cudaMemset(B.cell_count, 0, sizeof(int) * B.ncell));
     CK(cudaMemset(B.err, 0, sizeof(uint32_t)));
@@ -739,11 +759,10 @@ int device_error(dtsph_ctx *c)
     return DTSPH_OK;
 }
 
-// Mean duration of `launches` launches of the iterate kernel on the frozen pair
-// cache of the last step (each after a loop reset, bracketed by events).
-int probe_ms(dtsph_ctx *c, int launches, float *out)
+// Mean duration of `launches` launches of the iterate kernel on the pair cache
+// that B describes (each after a loop reset, bracketed by events).
+int probe_ms(dtsph_ctx *c, const Buffers &B, int launches, float *out)
 {
-    const Buffers &B = c->B;
     std::vector<cudaEvent_t> ev(2 * launches);
     for (auto &e : ev) CK(cudaEventCreate(&e));
     for (int i = 0; i < launches; ++i) {
@@ -841,8 +860,8 @@ int autotune(dtsph_ctx *c)
         if (c->prm[0].graph == 2) {
             r = probe_loop_ms(c, 4, 5, &ms);
         } else {
-            probe_ms(c, 3, &ms);               // warm-up
-            r = probe_ms(c, 10, &ms);
+            probe_ms(c, c->B, 3, &ms);         // warm-up
+            r = probe_ms(c, c->B, 10, &ms);
         }
         if (r) return r;
         c->tune_log.push_back({ch.lanes, ch.lanes == 1 ? ch.stages : 0, ms});
@@ -1308,8 +1327,24 @@ int dtsph_probe_iterate(dtsph_ctx *c, int32_t launches, float *ms_per_launch, do
     if (!c->have_particles || c->steps == 0) return fail(c, DTSPH_E_STATE, "take a step before probing");
     if (launches < 1 || launches > 256 || !ms_per_launch) return fail(c, DTSPH_E_ARG, "launches must be in [1, 256]");
     CK(cudaSetDevice(c->device));
-    const Buffers &B = c->B;
     CK(cudaStreamSynchronize(c->stream));
+    // The shifting pass after the loop bins the particles again at r^{n+1} and
+    // builds its neighbour lists over the index part of the step's pair cache.
+    // With shifting on, the probe therefore builds a cache of its own for the
+    // current positions, in that binned order (fluid flags and wall velocities
+    // of the same order), from arrays that every step rebuilds before use.
+    Buffers B = c->B;
+    if (c->prm[0].shifting) {
+        if (B.xk[0])
+            return fail(c, DTSPH_E_STATE, "with particles moving in pseudo-time the probe needs a run without shifting");
+        c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
+        c->launches += launch_permute_a_to_b(B, c->stream);
+        c->launches += launch_pair_cache(B, B.x_b, B.cell_b, B.gid_b, c->stream);
+        CK(cudaGetLastError());
+        if (int r = device_error(c)) return r;
+        B.gid_a = B.gid_b;
+        B.vn_a = B.vn_b;
+    }
     std::vector<int> cnt(B.n);
     std::vector<uint32_t> gid(B.n);
     CK(cudaMemcpy(cnt.data(), B.pcount, sizeof(int) * B.n, cudaMemcpyDeviceToHost));
@@ -1342,7 +1377,7 @@ int dtsph_probe_iterate(dtsph_ctx *c, int32_t launches, float *ms_per_launch, do
         const double per_wall = 8.0 + 8.0 * d + pos + packed;
         bytes = per_particle * B.nf + per_wall * B.nw + 5.0 * (double)(np + npw);
     }
-    int r = probe_ms(c, launches, ms_per_launch);
+    int r = probe_ms(c, B, launches, ms_per_launch);
     if (r) return r;
     if (bytes_per_launch) *bytes_per_launch = bytes;
     if (pairs) *pairs = np;

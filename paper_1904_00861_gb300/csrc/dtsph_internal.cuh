@@ -44,6 +44,10 @@ constexpr int kSlotAlign = 256;
 constexpr int kMaxStages = 8;        // deepest shared-memory ring of the one-lane iterate kernel
 constexpr uint32_t kNoParticle = 0xFFFFFFFFu;
 constexpr unsigned long long kBarrierWaitNs = 1000000000ull;   // grid-barrier give-up time (1 s)
+// Batches of up to this many instances deal their active tiles to the blocks
+// of the persistent loop (and may run the decoupled loop); larger batches take
+// the tiles in the static order.
+constexpr int kDealMaxInst = 1024;
 
 struct Inst {
     int slot_off;          // first slot
@@ -127,6 +131,15 @@ struct LoopCtrl {
     int pad;
 };
 
+// Work counters of one instance in the decoupled batch loop (k_loop_async):
+// claim = (iteration << 32) | next tile of that iteration to hand out;
+// done_tiles = tiles of the iteration finished so far.
+struct InstLoop {
+    unsigned long long claim;
+    unsigned int done_tiles;
+    int pad;
+};
+
 struct StatRec {
     int iters, reason;
     double rp, rv;
@@ -194,6 +207,9 @@ struct Buffers {
     double *blk;           // [2 x tiles], double-buffered: per-tile residual partial sums
     LoopState *ls;         // [ninst]
     LoopCtrl *ctrl;
+    InstLoop *il;          // [ninst] work counters of the decoupled batch loop (null without it)
+    const int *sched;      // [ninst] instances by ascending tile count (the decoupled loop's search order)
+    int async_loop;        // 1: batches without walls run the decoupled loop kernel
     StatRec *stats;        // [kStatRing][ninst]
     uint32_t *err;
 };

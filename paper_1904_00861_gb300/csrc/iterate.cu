@@ -564,10 +564,6 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int epoch, uint32_t *er
     return ok_sh != 0;
 }
 
-// Batches of up to this many instances deal their active tiles to the blocks
-// of the persistent loop; larger batches take the tiles in the static order.
-constexpr int kDealMaxInst = 1024;
-
 // Exclusive prefix of the active (not yet converged) tiles of every instance,
 // by the whole block: pre[i] = active tiles of instances 0 .. i-1, pre[ninst] =
 // all of them. Reads the instances' done flags, so call it after the barrier
@@ -759,6 +755,148 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
     }
 }
 
+// The block-wide minimum of v (every thread gets it).
+__device__ __forceinline__ int block_min(int v, int *scratch)
+{
+    v = __reduce_min_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int m = scratch[0];
+    for (int w = 1; w < kBlock / kWarp; ++w) m = min(m, scratch[w]);
+    __syncthreads();
+    return m;
+}
+
+// The pseudo-time loop of a batch without walls with the instances decoupled:
+// each instance advances through its iterations on its own, so the long
+// iteration chains of the instances that converge slowly run beside the heavy
+// iterations of the large instances instead of after them. Instance i's tiles
+// of iteration k are handed out by a counter holding (k << 32) | next tile; the
+// block that finishes the iteration's last tile reduces the instance's per-tile
+// partials in the fixed order of k_iterate, applies the stop rules, and then
+// opens iteration k + 1 or retires the instance. A block looks for an open tile
+// from the smallest instances up (they take the most iterations) and waits,
+// bounded by the barrier give-up time, while every open tile is taken. Every
+// tile and every decision is computed as in k_loop, so the results are the
+// same bits.
+template <int D, bool F32, int L>
+__global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (F32 ? 3 : 2))
+    k_loop_async(Buffers B)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    constexpr int PPB = kBlock / L;
+    __shared__ TileShared<T, D, L> sh;
+    __shared__ Phys P;
+    __shared__ int p_inst, w_inst, w_tile, w_it, last_sh, quit;
+    __shared__ int mins[kBlock / kWarp];
+    const int ntiles = (B.n + PPB - 1) / PPB;
+    const int ni = B.ninst;
+    if (threadIdx.x == 0) p_inst = -1;
+    ring_init<D, F32, L>(B.stages);
+    RingPos rp;
+    unsigned long long wait_from = 0;
+    bool waiting = false;
+    for (;;) {
+        // the first instance in search order with a tile left to hand out
+        int cand = 0x7fffffff;
+        for (int q = threadIdx.x; q < ni; q += kBlock) {
+            const int i = B.sched[q];
+            if (*(volatile int *)&B.ls[i].done) continue;
+            const unsigned long long cl = *(volatile unsigned long long *)&B.il[i].claim;
+            int tlo, thi;
+            instance_tiles(B.inst[i], PPB, tlo, thi);
+            if ((int)(cl & 0xffffffffull) < thi - tlo) {
+                cand = q;
+                break;
+            }
+        }
+        cand = block_min(cand, mins);
+        if (threadIdx.x == 0) {
+            w_inst = -1;
+            quit = 0;
+            if (cand != 0x7fffffff) {
+                const int i = B.sched[cand];
+                int tlo, thi;
+                instance_tiles(B.inst[i], PPB, tlo, thi);
+                const unsigned long long old = atomicAdd(&B.il[i].claim, 1ull);
+                const int t = (int)(old & 0xffffffffull);
+                if (t < thi - tlo) {
+                    w_inst = i;
+                    w_tile = tlo + t;
+                    w_it = (int)(old >> 32);
+                    __threadfence();
+                }
+            } else if (*(volatile int *)&B.ctrl->active == 0) {
+                quit = 1;
+            }
+            // every open tile is taken: wait, bounded, for an iteration to open
+            // (thread 0 alone keeps the clock, so the block decides as one)
+            if (w_inst >= 0) {
+                waiting = false;
+            } else if (!quit) {
+                const unsigned long long now = global_ns();
+                if (!waiting) {
+                    waiting = true;
+                    wait_from = now;
+                } else if (now - wait_from > B.barrier_ns) {
+                    atomicOr(B.err, kErrBarrier);
+                    quit = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (quit) break;
+        const int inst = w_inst;
+        if (inst < 0) {
+            __nanosleep(128);
+            continue;
+        }
+        const int t = w_tile, it = w_it;
+        if (inst != p_inst) {
+            for (int w = threadIdx.x; w < (int)(sizeof(Phys) / 4); w += blockDim.x)
+                reinterpret_cast<int *>(&P)[w] = reinterpret_cast<const int *>(B.phys + inst)[w];
+            __syncthreads();
+            if (threadIdx.x == 0) p_inst = inst;
+        }
+        double a = 0, b = 0;
+        tile_iteration<D, F32, false, L>(B, P, it & 1, t, sh, rp, a, b);
+        int tlo, thi;
+        instance_tiles(B.inst[inst], PPB, tlo, thi);
+        double *blk = B.blk + (size_t)(it & 1) * 2 * ntiles;
+        if (threadIdx.x == 0) {
+            blk[2 * t] = a;
+            blk[2 * t + 1] = b;
+            __threadfence();
+            last_sh = atomicAdd(&B.il[inst].done_tiles, 1u) == (unsigned int)(thi - tlo - 1);
+        }
+        __syncthreads();
+        if (last_sh) {
+            // the iteration's last tile: the instance's decision, then the next
+            // iteration opens (or the instance retires)
+            __threadfence();
+            double sa = 0, sb = 0;
+            reduce_tiles(blk + 2 * tlo, thi - tlo, sh.red, sa, sb);
+            if (threadIdx.x == 0) {
+                const int r = finish_iteration(B.ls + inst, P, it, sa, sb);
+                B.il[inst].done_tiles = 0u;
+                __threadfence();
+                if (r >= 0) atomicSub(&B.ctrl->active, 1);
+                else atomicExch(&B.il[inst].claim, (unsigned long long)(it + 1) << 32);
+            }
+            __syncthreads();
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int *)&B.ctrl->active != 0) {
+        // a wait gave up: close every instance still open (the host sees
+        // kErrBarrier)
+        for (int i = 0; i < ni; ++i)
+            if (!B.ls[i].done) {
+                B.ls[i].reason = 3;
+                B.ls[i].done = 1;
+            }
+    }
+}
+
 // Eq. (r-update): r^{n+1} = r^n + dt/2 (V^n + V^{n+1}) for fluid slots, then
 // V^{n-1} <- V^n, V^n <- V^K, p^n <- p^K = (p-hat^K + p-hat^{K-1}) / 2; the
 // instance's first slot logs the step, and the step's max|V^{n+1}| is folded in
@@ -833,6 +971,9 @@ __global__ void k_loop_reset(Buffers B) { reset_loops(B); }
 template <int D, bool F, bool W, int L>
 const void *loop_kernel() { return (const void *)k_loop<D, F, W, L>; }
 
+template <int D, bool F, int L>
+const void *async_kernel() { return (const void *)k_loop_async<D, F, L>; }
+
 }  // namespace
 
 int iterate_tiles(const Buffers &B) { return (B.n + kBlock / B.lanes - 1) / (kBlock / B.lanes); }
@@ -902,11 +1043,29 @@ static cudaError_t allow_ring_smem()
                                          bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute((const void *)k_loop<D, F, W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && !W)
+        e = cudaFuncSetAttribute((const void *)k_loop_async<D, F, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
     return e;
+}
+
+template <int D, bool F>
+static const void *async_lanes(int lanes)
+{
+    switch (lanes) {
+    case 1: return async_kernel<D, F, 1>();
+    case 2: return async_kernel<D, F, 2>();
+    case 4: return async_kernel<D, F, 4>();
+    default: return async_kernel<D, F, 8>();
+    }
 }
 
 static const void *loop_function(const Buffers &B)
 {
+    if (B.async_loop) {
+        if (B.dim == 2) return B.fp32c ? async_lanes<2, true>(B.lanes) : async_lanes<2, false>(B.lanes);
+        return B.fp32c ? async_lanes<3, true>(B.lanes) : async_lanes<3, false>(B.lanes);
+    }
     const bool w = B.nw > 0;
     if (B.dim == 2) {
         if (B.fp32c) return w ? loop_lanes<2, true, true>(B.lanes) : loop_lanes<2, true, false>(B.lanes);

@@ -102,6 +102,10 @@ __device__ __forceinline__ void reset_loops(const Buffers &B)
         const int slot = (int)(ls->step % kStatRing);
         ls->stat_slot = slot;
         B.stats[(size_t)slot * B.ninst + i].vmax = 0.0;
+        if (B.il) {
+            B.il[i].claim = 0ull;
+            B.il[i].done_tiles = 0u;
+        }
     }
     if (threadIdx.x == 0) {
         B.ctrl->ticket = 0;

@@ -684,6 +684,43 @@ def test_moving_skin_exceeded_is_reported():
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case", ["cavity", "tgv3d"])
+def test_probe_after_shifting_leaves_the_run_unchanged(case, prec):
+    """With shifting on, the shifting pass after the loop replaces the step's
+    neighbour lists by its own; the probe then times the iterate kernel on a
+    cache built for the current positions (walls and 3D included). It runs,
+    leaves r, V, p alone, and the next step is bit-identical to that of an
+    unprobed run. With particles moving in pseudo-time and shifting on, it
+    refuses (DTSPH_E_STATE)."""
+    d = CASES[case]()
+    d["cfg"] = dict(d["cfg"], shifting=1)
+    ref = make_sim(d, precision=prec, graph=2)
+    ref.step(3)
+    ref.sync()
+    want = (ref.x, ref.v, ref.p)
+    ref.close()
+    sim = make_sim(d, precision=prec, graph=2)
+    sim.step(2)
+    sim.sync()
+    x, v, p = sim.x, sim.v, sim.p
+    ms, by, npairs = dt.dtsph_probe_iterate(sim.ctx, 3)
+    assert ms > 0 and by > 0 and npairs > 0
+    assert np.array_equal(sim.x, x) and np.array_equal(sim.v, v) and np.array_equal(sim.p, p)
+    sim.step(1)
+    sim.sync()
+    assert all(np.array_equal(a, b) for a, b in zip((sim.x, sim.v, sim.p), want))
+    sim.close()
+    if case == "cavity":
+        sim = make_sim(d, precision=prec, moving=1)
+        sim.step(1)
+        sim.sync()
+        with pytest.raises(dt.DtsphError) as e:
+            dt.dtsph_probe_iterate(sim.ctx, 2)
+        assert e.value.code == -2
+        sim.close()
+
+
 def test_host_and_device_transfers_agree():
     """dtsph_set_particles / dtsph_read_field with host arrays (read and written
     in place by kernels where the device accesses pageable memory, through
