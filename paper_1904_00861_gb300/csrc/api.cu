@@ -503,6 +503,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
 #define A(p, cnt) if ((r = dalloc(c, &(p), (cnt))) != DTSPH_OK) { free_all(c); return r; }
     A(d_inst, ni) A(d_geo, ni) A(d_phys, ni) A(d_inst_of, n)
     A(B.gid_a, n) A(B.x_a, nd) A(B.xp_a, nd) A(B.vn_a, nd) A(B.vnm1_a, nd) A(B.pn_a, n) A(B.s_a, nd) A(B.cell_a, n)
+    A(B.wslot_a, (size_t)wo)
     A(B.gid_b, n) A(B.x_b, nd) A(B.vn_b, nd) A(B.vnm1_b, nd) A(B.pn_b, n) A(B.xp_b, nd) A(B.v0_b, nd)
     A(B.ph0_b, n) A(B.s_b, nd) A(B.cell_b, n)
     A(B.key, n) A(B.slot, n) A(B.unsorted, n) A(B.perm, n) A(B.cell_count, (size_t)B.ncell)

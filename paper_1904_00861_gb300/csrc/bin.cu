@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
     const int n = B.n, dim = B.dim;
     const uint32_t g = B.gid_b[o];
     B.gid_a[s] = g;
+    if (B.wslot_a && g >= (uint32_t)B.nf) B.wslot_a[g - (uint32_t)B.nf] = s;
     const int cell = B.key[o];
     B.cell_a[s] = cell;
     double v[3] = {0, 0, 0};
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter_in(Buffers B, const double *
     } else if (local < I.nf + I.nw) {
         const size_t w = (size_t)I.woff + (local - I.nf);
         B.gid_a[s] = (uint32_t)(B.nf + w);
+        if (B.wslot_a) B.wslot_a[w] = s;
         for (int a = 0; a < dim; ++a) {
             const size_t so = (size_t)a * n;
             B.x_a[so + s] = input_coord(xw[w * dim + a], G, a, B.err);

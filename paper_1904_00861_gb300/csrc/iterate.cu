@@ -37,67 +37,105 @@ namespace {
 
 inline int blocks(int n) { return (n + kBlock - 1) / kBlock; }
 
-// Wall values of wall slot s for the iteration whose iterate sits in buffer cur,
-// from the cached fluid neighbours of the slot.
+// Lanes per wall slot in the wall phase of an iteration (a warp serves
+// 32 / kWallLanes wall slots).
+constexpr int kWallLanes = 8;
+
+// Wall values of wall slot s for the iteration whose iterate sits in buffer
+// cur, from the cached fluid neighbours of the slot, by the kWallLanes lanes of
+// a group (sub: lane in the group; gmask: the group's lanes in the warp). Lane
+// sub takes entries sub, sub + kWallLanes, ..., R of them in flight (their
+// coefficients, then their neighbour gathers); the lanes' partial sums then
+// merge in a fixed order, so every run gives the same bits. Adami et al.:
+// p_w = sum_f (p_f W + rho0 (g . r_wf) W) / sum_f W (the second term cached as
+// Wg), ghost velocity 2 v_w - sum_f V_f W / sum_f W.
 template <int D, bool F32>
-__device__ __forceinline__ void wall_slot(const Buffers &B, int s, int cur)
+__device__ __forceinline__ void wall_slot(const Buffers &B, int s, int cur, int sub, unsigned gmask)
 {
+    constexpr int R = 2;
     const int cnt = B.pcount[s];
     const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-    double sw = 0, sp = 0, sv[3] = {0, 0, 0};
-    for (int k = 0; k < cnt; ++k) {
-        size_t e = base + (size_t)k * kWarp;
-        double W, Wg;
-        uint32_t jb;
-        if (F32) {
-            float4 c = B.pc32[e];
-            W = c.x;
-            Wg = c.y;
-            jb = D == 2 ? __float_as_uint(c.w) : B.pj[e];
-        } else {
-            double4_32a c = B.pc64[e];
-            W = c.x;
-            Wg = c.y;
-            jb = B.pj[e];
+    double acc[5] = {0, 0, 0, 0, 0};    // sum W, sum (p W + Wg), sum V W
+    for (int k0 = sub; k0 < cnt; k0 += kWallLanes * R) {
+        double W[R], Wg[R];
+        uint32_t jb[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const size_t e = base + (size_t)min(k0 + r * kWallLanes, cnt - 1) * kWarp;
+            if (F32) {
+                const float4 c = B.pc32[e];
+                W[r] = c.x;
+                Wg[r] = c.y;
+                jb[r] = D == 2 ? __float_as_uint(c.w) : B.pj[e];
+            } else {
+                const double4_32a c = B.pc64[e];
+                W[r] = c.x;
+                Wg[r] = c.y;
+                jb[r] = B.pj[e];
+            }
         }
-        if (jb & kWallBit) continue;
-        int j = (int)jb;
-        double vx, vy, vz, p;
-        if (F32) {
-            float4 q = B.nb32[cur][j];
-            vx = q.x; vy = q.y; vz = q.z; p = q.w;
-        } else {
-            double4_32a q = B.nb64[cur][j];
-            vx = q.x; vy = q.y; vz = q.z; p = q.w;
+        double q[R][4];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = (int)(jb[r] & ~kWallBit);     // a wall entry's slot is read and not used
+            if (F32) {
+                const float4 v = B.nb32[cur][j];
+                q[r][0] = v.x; q[r][1] = v.y; q[r][2] = v.z; q[r][3] = v.w;
+            } else {
+                const double4_32a v = B.nb64[cur][j];
+                q[r][0] = v.x; q[r][1] = v.y; q[r][2] = v.z; q[r][3] = v.w;
+            }
         }
-        sw += W;
-        sp += p * W + Wg;
-        sv[0] += vx * W;
-        sv[1] += vy * W;
-        sv[2] += vz * W;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (k0 + r * kWallLanes >= cnt || (jb[r] & kWallBit)) continue;   // fluid neighbours only
+            acc[0] += W[r];
+            acc[1] += q[r][3] * W[r] + Wg[r];
+            acc[2] += q[r][0] * W[r];
+            acc[3] += q[r][1] * W[r];
+            acc[4] += q[r][2] * W[r];
+        }
     }
+#pragma unroll
+    for (int o = kWallLanes / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int t = 0; t < 5; ++t) acc[t] += __shfl_xor_sync(gmask, acc[t], o);
+    if (sub != 0) return;
+    const double sw = acc[0];
     double gv[3];
     for (int a = 0; a < 3; ++a) {
-        double vw = a < D ? B.vn_a[(size_t)a * B.n + s] : 0.0;
-        gv[a] = 2.0 * vw - (sw > 0 ? sv[a] / sw : 0.0);
+        const double vw = a < D ? B.vn_a[(size_t)a * B.n + s] : 0.0;
+        gv[a] = 2.0 * vw - (sw > 0 ? acc[2 + a] / sw : 0.0);
     }
-    double pw = sw > 0 ? sp / sw : 0.0;
+    double pw = sw > 0 ? acc[1] / sw : 0.0;
     if (pw < 0.0 && B.phys[B.inst_of[s]].free_surface) pw = 0.0;   // free-surface runs (Sec. 3.2)
     if (F32) B.nb32[cur][s] = make_float4((float)gv[0], (float)gv[1], (float)gv[2], (float)pw);
     else B.nb64[cur][s] = make_double4_32a(gv[0], gv[1], gv[2], pw);
 }
 
-// Wall values for iteration k (one launch per iteration).
+// The lanes of thread t's wall group: its lane in the group and the group's mask.
+__device__ __forceinline__ void wall_group(int t, int &sub, unsigned &gmask)
+{
+    const int lane = t & 31;
+    sub = lane & (kWallLanes - 1);
+    gmask = ((1u << kWallLanes) - 1u) << (lane & ~(kWallLanes - 1));
+}
+
+// Wall values for iteration k (one launch per iteration), kWallLanes lanes per
+// wall particle of the wall list.
 template <int D, bool F32>
 __global__ void __launch_bounds__(kBlock) k_walls_iter(Buffers B)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.n) return;
-    const uint32_t g = B.gid_a[s];
-    if (g < (uint32_t)B.nf || g == kNoParticle) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = t / kWallLanes;                        // the same for the whole group
+    if (w >= B.nw) return;
+    const int s = B.wslot_a[w];
     const LoopState *ls = B.ls + B.inst_of[s];
     if (ls->done) return;
-    wall_slot<D, F32>(B, s, ls->iter & 1);
+    int sub;
+    unsigned gmask;
+    wall_group(t, sub, gmask);
+    wall_slot<D, F32>(B, s, ls->iter & 1, sub, gmask);
 }
 
 // One entry of the pair cache in registers.
@@ -658,9 +696,14 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
     for (;; ++it) {
         const int cur = it & 1;
         if (WALLS) {
-            for (int s = blockIdx.x * kBlock + threadIdx.x; s < B.n; s += gridDim.x * kBlock) {
-                const uint32_t g = B.gid_a[s];
-                if (g >= (uint32_t)B.nf && g != kNoParticle && !B.ls[B.inst_of[s]].done) wall_slot<D, F32>(B, s, cur);
+            // the wall list, kWallLanes lanes per wall particle
+            int sub;
+            unsigned gmask;
+            wall_group(threadIdx.x, sub, gmask);
+            constexpr int GPB = kBlock / kWallLanes;
+            for (int w = blockIdx.x * GPB + (int)threadIdx.x / kWallLanes; w < B.nw; w += gridDim.x * GPB) {
+                const int s = B.wslot_a[w];
+                if (!B.ls[B.inst_of[s]].done) wall_slot<D, F32>(B, s, cur, sub, gmask);
             }
             if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh, B.barrier_ns)) break;
         }
@@ -886,15 +929,10 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (
             __syncthreads();
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int *)&B.ctrl->active != 0) {
-        // a wait gave up: close every instance still open (the host sees
-        // kErrBarrier)
-        for (int i = 0; i < ni; ++i)
-            if (!B.ls[i].done) {
-                B.ls[i].reason = 3;
-                B.ls[i].done = 1;
-            }
-    }
+    // A block leaves after a wait gave up only when it found nothing to claim:
+    // every claimed tile belongs to a block still working, and the block that
+    // completes an iteration opens the next and looks for work again, so the
+    // blocks that stay finish every instance; the host sees kErrBarrier.
 }
 
 // Eq. (r-update): r^{n+1} = r^n + dt/2 (V^n + V^{n+1}) for fluid slots, then
@@ -993,12 +1031,13 @@ static void iterate_lanes(const Buffers &B, unsigned long long cond, int use_con
 int launch_walls_iter(const Buffers &B, cudaStream_t st)
 {
     if (B.nw == 0) return 0;
+    const int nb = (int)(((long long)B.nw * kWallLanes + kBlock - 1) / kBlock);
     if (B.dim == 2) {
-        if (B.fp32c) k_walls_iter<2, true><<<blocks(B.n), kBlock, 0, st>>>(B);
-        else k_walls_iter<2, false><<<blocks(B.n), kBlock, 0, st>>>(B);
+        if (B.fp32c) k_walls_iter<2, true><<<nb, kBlock, 0, st>>>(B);
+        else k_walls_iter<2, false><<<nb, kBlock, 0, st>>>(B);
     } else {
-        if (B.fp32c) k_walls_iter<3, true><<<blocks(B.n), kBlock, 0, st>>>(B);
-        else k_walls_iter<3, false><<<blocks(B.n), kBlock, 0, st>>>(B);
+        if (B.fp32c) k_walls_iter<3, true><<<nb, kBlock, 0, st>>>(B);
+        else k_walls_iter<3, false><<<nb, kBlock, 0, st>>>(B);
     }
     return 1;
 }

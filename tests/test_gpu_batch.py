@@ -122,3 +122,70 @@ def test_full_size_batch_sampled_instances():
         print(f"instance {i} ({sizes[i]} particles): L-inf rel velocity err {err:.2e}")
         assert err < 1e-4, i
     b.close()
+
+
+def wall_free_instances():
+    """Batches without walls run the decoupled loop kernel (each instance
+    iterating on its own); uneven sizes and Reynolds numbers give uneven
+    iteration counts."""
+    return [
+        synth.tgv2d(37, re=100.0, seed=11),
+        synth.tgv2d(20, re=630.0, seed=12),
+        synth.tgv2d(45, re=250.0, seed=13),
+        synth.tgv2d(24, re=1000.0, seed=14),
+        synth.tgv2d(31, re=150.0, seed=15),
+    ]
+
+
+def batch_run(insts, prec, lanes, nsteps):
+    b = dt.Batch([d["cfg"] for d in insts], precision=prec, graph=2, lanes=lanes)
+    b.set_state(insts)
+    b.step(nsteps)
+    b.sync()
+    out = (b.field(dt.FIELD_POS), b.field(dt.FIELD_VEL), b.field(dt.FIELD_P),
+           [b.stats(i) for i in range(len(insts))])
+    b.close()
+    return out
+
+
+@pytest.mark.parametrize("lanes", [1, 4])
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_decoupled_loop_equals_lockstep_loop_and_solo_runs(monkeypatch, prec, lanes):
+    """The decoupled batch loop gives, instance by instance, the bits and step
+    statistics of the lockstep loop (DTSPH_LOCKSTEP_LOOP=1) and of running each
+    instance alone."""
+    insts = wall_free_instances()
+    nsteps = 4
+    dec = batch_run(insts, prec, lanes, nsteps)
+    monkeypatch.setenv("DTSPH_LOCKSTEP_LOOP", "1")
+    lock = batch_run(insts, prec, lanes, nsteps)
+    monkeypatch.delenv("DTSPH_LOCKSTEP_LOOP")
+    iters = []
+    for i, d in enumerate(insts):
+        for k in range(3):
+            assert np.array_equal(dec[k][i], lock[k][i]), (i, k)
+        assert dec[3][i] == lock[3][i], i
+        x, v, p, st = solo(d, prec, 2, nsteps, lanes)
+        assert np.array_equal(dec[0][i], x) and np.array_equal(dec[1][i], v) and np.array_equal(dec[2][i], p), i
+        assert dec[3][i] == st, i
+        iters.append([s["iters"] for s in st])
+    # the instances really iterate unevenly (the decoupled loop's case)
+    assert len({tuple(t) for t in iters}) > 1
+
+
+def test_decoupled_loop_give_up_is_reported(monkeypatch):
+    """A give-up time of zero: blocks that find no open tile leave at their
+    second look, the others finish every instance, and dtsph_sync says
+    DTSPH_E_TIMEOUT; a new context without the setting runs normally."""
+    insts = wall_free_instances()
+    monkeypatch.setenv("DTSPH_TEST_BARRIER_WAIT_NS", "0")
+    b = dt.Batch([d["cfg"] for d in insts], precision=dt.DTSPH_FP32C, graph=2, lanes=1)
+    b.set_state(insts)
+    b.step(1)
+    with pytest.raises(dt.DtsphError) as e:
+        b.sync()
+    assert e.value.code == dt.DTSPH_E_TIMEOUT
+    b.close()
+    monkeypatch.delenv("DTSPH_TEST_BARRIER_WAIT_NS")
+    out = batch_run(insts, dt.DTSPH_FP32C, 1, 1)
+    assert all(st[0]["reason"] in (0, 1) for st in out[3])
