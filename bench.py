@@ -44,11 +44,13 @@ METRIC = "particle-pseudo-iterations/sec (FP32-comp batched vs plain FP64, same 
 UNIT = "particle-iterations/s"
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# loop kernel, from the Nsight Compute captures summarised under profiles/, for
-# the kernel variants those captures profiled: (workload, dim, lanes, stages) ->
-# (bytes, source). A variant not listed, or one whose kernel changed after its
-# capture, reports null.
+# DRAM traffic of the loop kernel from the Nsight Compute captures summarised
+# under profiles/: (workload, dim, lanes, stages) -> (DRAM bytes of the captured
+# launch, dram__bytes_read.sum + dram__bytes_write.sum; algorithmic bytes of that
+# launch; source). A launch's bytes depend on the iterations of its step, so the
+# line reports the captured bytes per algorithmic byte times the algorithmic
+# bytes of its own launches. A variant not listed, or one whose kernel changed
+# after its capture, reports null.
 NCU_TRAFFIC = {}
 
 
@@ -89,9 +91,10 @@ def make_workload(name: str, n_side: int, re: float):
                    alpha=0.1, free_surface="on", shifting="on")
     else:
         raise ValueError(name)
-    cfg.update(dt="0.25h", beta=10, eps=1e-3, real_steps_per_bench_step=1)
+    first = d[0] if isinstance(d, list) else d
+    cfg.update(dt="0.25h", beta=first["cfg"]["beta"], eps=first["cfg"]["eps"], real_steps_per_bench_step=1)
     if name == "dambreak":
-        cfg.update(dt="0.25h/sqrt(2 g H)", eps=1e-4)
+        cfg.update(dt="0.25h/sqrt(2 g H)")
     return d, cfg
 
 
@@ -458,6 +461,9 @@ def main_ours(args):
     if args.moving:
         with_moving(d, wcfg, args.moving)
     kern = dict(lanes=args.lanes, stages=args.stages)
+    # batches without walls run the decoupled loop kernel (the library's rule)
+    decoupled = (args.graph == 2 and isinstance(d, list) and 1 < len(d) <= 1024 and not args.moving
+                 and all(x["vw"] is None for x in d) and os.environ.get("DTSPH_LOCKSTEP_LOOP", "0") in ("", "0"))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if world > 1:
         tdist.barrier()
@@ -502,7 +508,7 @@ def main_ours(args):
                 "iterate_kernel_ms": ms_it64, "speedup_fp32c_over_fp64": value / (rate64 * world),
                 "roofline": {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": fma["fp64_fma_tflops"],
                              "unit": "TFLOP/s", "frac": ach64 / fma["fp64_fma_tflops"],
-                             "kernel": f"k_loop<{dims},FP64,lanes={lanes64}>",
+                             "kernel": f"{'k_loop_async' if decoupled else 'k_loop'}<{dims},FP64,lanes={lanes64}>",
                              "flops_per_launch": flops64 / len(lms64), "launch_ms": sum(lms64) / len(lms64),
                              "flops_counted": f"{f_part:.0f} per particle-iteration + {f_pair:.0f} per pair-iteration "
                                               f"(FMA = 2), {npairs64 / nf_tot:.2f} pairs per particle",
@@ -520,15 +526,23 @@ def main_ours(args):
     loop_kernel = {2: f"k_loop<{dims},FP32C,lanes={lanes32}> (persistent loop, one launch per step)",
                    1: f"k_iterate<{dims},FP32C,lanes={lanes32}> in the while node (one launch per iteration)",
                    0: f"k_iterate<{dims},FP32C,lanes={lanes32}> (plain launches)"}[args.graph]
+    if decoupled:
+        loop_kernel = (f"k_loop_async<{dims},FP32C,lanes={lanes32}> (decoupled batch loop, persistent, "
+                       f"one launch per step)")
     probe_kernel = f"k_iterate<{dims},FP32C,lanes={lanes32}>"
     if args.moving:
         probe_kernel = f"k_move_walls + k_move_iter<{dims},FP32C> (one lane per particle)"
         loop_kernel = probe_kernel + (" (plain launches)" if args.graph == 0 else
                                       " in the while node (one launch each per iteration)")
-    traffic, traffic_src = None, None
+    bytes_by_launch = [per_it * float(w) for w in loop_work]
+    traffic, traffic_src, traffic_cap = None, None, None
     key = (wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0)
     if args.graph == 2 and not args.moving and not args.steady and not args.shifting and key in NCU_TRAFFIC:
-        traffic, traffic_src = NCU_TRAFFIC[key]
+        t_bytes, t_alg, t_src = NCU_TRAFFIC[key]
+        traffic = t_bytes / t_alg * (loop_bytes / len(loop_ms))
+        traffic_src = (f"{t_src}: the captured launch moved {t_bytes / t_alg:.3f} DRAM bytes per algorithmic "
+                       f"byte; times this line's algorithmic bytes per launch")
+        traffic_cap = {"dram_bytes": t_bytes, "algorithmic_bytes": t_alg, "ratio": t_bytes / t_alg}
     e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)
     trace = run_trace(dt, d, args.warmup + args.steps, args.trace, args.graph, kern) if args.trace else None
     out = {
@@ -542,8 +556,10 @@ def main_ours(args):
         "iters_per_step_mean": float(np.mean(it32)),
         "fp64": fp64,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic, "traffic_source": traffic_src, "kernel": loop_kernel,
+                     "traffic": traffic, "traffic_source": traffic_src, "traffic_captured_launch": traffic_cap,
+                     "kernel": loop_kernel,
                      "bytes_per_launch": loop_bytes / len(loop_ms), "launch_ms": sum(loop_ms) / len(loop_ms),
+                     "bytes_by_launch": bytes_by_launch,
                      "bytes_counted": f"{STATE_BYTES[(dims, True)]:.0f} B per particle-iteration + "
                                       f"{PAIR_BYTES[(dims, True)]:.0f} B per pair-iteration, "
                                       f"{npairs / nf_tot:.2f} pairs per particle",

@@ -500,10 +500,18 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     Phys *d_phys;
     uint16_t *d_inst_of;
     int r;
-#define A(p, cnt) if ((r = dalloc(c, &(p), (cnt))) != DTSPH_OK) { free_all(c); return r; }
+#define A(p, cnt) { if ((r = dalloc(c, &(p), (cnt))) != DTSPH_OK) { free_all(c); return r; } }
     A(d_inst, ni) A(d_geo, ni) A(d_phys, ni) A(d_inst_of, n)
     A(B.gid_a, n) A(B.x_a, nd) A(B.xp_a, nd) A(B.vn_a, nd) A(B.vnm1_a, nd) A(B.pn_a, n) A(B.s_a, nd) A(B.cell_a, n)
     A(B.wslot_a, (size_t)wo)
+    if (wo > 0) {
+        // braces: A is an if statement, so a bare else would bind to it
+        if (B.fp32c) {
+            A(B.wv32, n)
+        } else {
+            A(B.wv64, n)
+        }
+    }
     A(B.gid_b, n) A(B.x_b, nd) A(B.vn_b, nd) A(B.vnm1_b, nd) A(B.pn_b, n) A(B.xp_b, nd) A(B.v0_b, nd)
     A(B.ph0_b, n) A(B.s_b, nd) A(B.cell_b, n)
     A(B.key, n) A(B.slot, n) A(B.unsorted, n) A(B.perm, n) A(B.cell_count, (size_t)B.ncell)
@@ -534,6 +542,10 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         A(B.il, ni) A(d_sched, ni)
     }
 #undef A
+    if (wo > 0 && !(B.fp32c ? (const void *)B.wv32 : (const void *)B.wv64)) {
+        free_all(c);
+        return fail(c, DTSPH_E_STATE, "internal: the wall velocity array was not allocated");
+    }
     B.inst = d_inst;
     B.geo = d_geo;
     B.phys = d_phys;
@@ -573,6 +585,8 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         B.sched = d_sched;
     }
     CK(cudaMemset(B.ctrl, 0, sizeof(LoopCtrl)));
+    if (B.wv32) CK(cudaMemset(B.wv32, 0, sizeof(float4) * n));
+    if (B.wv64) CK(cudaMemset(B.wv64, 0, sizeof(double4_32a) * n));
     CK(cudaMemset(B.cell_count, 0, sizeof(int) * B.ncell));
     CK(cudaMemset(B.err, 0, sizeof(uint32_t)));
     CK(cudaMemset(B.pcount, 0, sizeof(int) * n));

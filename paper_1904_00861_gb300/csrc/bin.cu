@@ -212,6 +212,14 @@ __device__ __forceinline__ float4 cell_offset(const Geom &G, int local_cell, con
 
 // A -> B at the start of a step: state n, and the packed (V^n, p^n) that the
 // state-n pair pass gathers.
+// The packed copy of a wall slot's prescribed velocity that the loop gathers
+// with the neighbour states (contexts with walls only).
+__device__ __forceinline__ void store_wall_velocity(const Buffers &B, int s, const double *u)
+{
+    if (B.wv32) B.wv32[s] = make_float4((float)u[0], (float)u[1], (float)u[2], 0.f);
+    if (B.wv64) B.wv64[s] = make_double4_32a(u[0], u[1], u[2], 0.0);
+}
+
 __global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -259,19 +267,22 @@ __global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
     const int n = B.n, dim = B.dim;
     const uint32_t g = B.gid_b[o];
     B.gid_a[s] = g;
-    if (B.wslot_a && g >= (uint32_t)B.nf) B.wslot_a[g - (uint32_t)B.nf] = s;
+    const bool wall = g >= (uint32_t)B.nf;
+    if (B.wslot_a && wall) B.wslot_a[g - (uint32_t)B.nf] = s;
     const int cell = B.key[o];
     B.cell_a[s] = cell;
-    double v[3] = {0, 0, 0};
+    double v[3] = {0, 0, 0}, u[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) {
         const size_t so = (size_t)a * n;
         B.x_a[so + s] = B.x_b[so + o];
         B.xp_a[so + s] = B.xp_b[so + o];
-        B.vn_a[so + s] = B.vn_b[so + o];
+        u[a] = B.vn_b[so + o];
+        B.vn_a[so + s] = u[a];
         B.s_a[so + s] = B.s_b[so + o];
         v[a] = B.v0_b[so + o];
         B.vk[0][so + s] = v[a];
     }
+    if (wall) store_wall_velocity(B, s, u);
     const double ph = B.ph0_b[o];
     if (B.fp32c) {
         const int inst = B.inst_of[s];
@@ -326,13 +337,16 @@ __global__ void __launch_bounds__(kBlock) k_scatter_in(Buffers B, const double *
         const size_t w = (size_t)I.woff + (local - I.nf);
         B.gid_a[s] = (uint32_t)(B.nf + w);
         if (B.wslot_a) B.wslot_a[w] = s;
+        double u[3] = {0, 0, 0};
         for (int a = 0; a < dim; ++a) {
             const size_t so = (size_t)a * n;
             B.x_a[so + s] = input_coord(xw[w * dim + a], G, a, B.err);
-            B.vn_a[so + s] = vw ? vw[w * dim + a] : 0.0;
-            B.vnm1_a[so + s] = B.vn_a[so + s];
+            u[a] = vw ? vw[w * dim + a] : 0.0;
+            B.vn_a[so + s] = u[a];
+            B.vnm1_a[so + s] = u[a];
         }
         B.pn_a[s] = 0.0;
+        store_wall_velocity(B, s, u);
     } else {
         B.gid_a[s] = kNoParticle;
     }

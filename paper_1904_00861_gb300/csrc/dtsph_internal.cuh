@@ -172,6 +172,8 @@ struct Buffers {
     double *s_a;           // kappa ((V^{n-1} - 4 V^n) / (2 dt) - g): BDF2 source and body force [dim][n]
     int *cell_a;           // cell of each slot
     int *wslot_a;          // [nw] slot of each wall particle (by caller wall index), null where no loop runs
+    float4 *wv32;          // FP32C: [n] V^n of each wall slot packed (prescribed velocity), null without walls
+    double4_32a *wv64;     // FP64: the same in FP64
     // order B (scratch inside a step)
     uint32_t *gid_b;
     double *x_b, *vn_b, *vnm1_b, *pn_b, *xp_b, *v0_b, *ph0_b, *s_b;

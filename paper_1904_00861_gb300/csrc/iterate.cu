@@ -244,6 +244,40 @@ __device__ __forceinline__ void ring_init(int S)
     __syncthreads();
 }
 
+// The prescribed velocity of list entry jb's particle if it is a wall particle
+// (the V_j of the divergence term; the packed copy of V^n of order A, in the
+// working precision), else zeros. Issued with the neighbour-state gathers.
+template <int D, bool F32, typename T>
+__device__ __forceinline__ void wall_velocity(const Buffers &B, uint32_t jb, T *vw)
+{
+    vw[0] = vw[1] = vw[2] = T(0);
+    if (!(jb & kWallBit)) return;
+    const int j = (int)(jb & ~kWallBit);
+    if constexpr (F32) {
+        if (D == 2) {
+            const float2 w = *reinterpret_cast<const float2 *>(&B.wv32[j]);
+            vw[0] = (T)w.x;
+            vw[1] = (T)w.y;
+        } else {
+            const float4 w = B.wv32[j];
+            vw[0] = (T)w.x;
+            vw[1] = (T)w.y;
+            vw[2] = (T)w.z;
+        }
+    } else {
+        if (D == 2) {
+            const double2 w = *reinterpret_cast<const double2 *>(&B.wv64[j]);
+            vw[0] = (T)w.x;
+            vw[1] = (T)w.y;
+        } else {
+            const double4_32a w = B.wv64[j];
+            vw[0] = (T)w.x;
+            vw[1] = (T)w.y;
+            vw[2] = (T)w.z;
+        }
+    }
+}
+
 // One iteration over tile `tile` (slots tile*PPB .. tile*PPB+PPB-1, PPB = 256/L),
 // by the whole block. Writes iterate k+1 of the tile's fluid particles and
 // returns, on thread 0, the tile's residual sums (sum |dp/dtau|, sum |dV/dtau|).
@@ -290,14 +324,13 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
         // the pair terms of one cache entry with its gathered neighbour state
         using Q = typename std::conditional<F32, float4, double4_32a>::type;
         const Q *nbq = F32 ? (const Q *)(const void *)B.nb32[cur] : (const Q *)(const void *)B.nb64[cur];
-        auto pair = [&](const CacheEntry<T, D, F32> &ce, const Q &q) {
-            const int j = (int)(ce.jb & ~kWallBit);
+        // vw: the prescribed velocity of a wall neighbour (the divergence term's
+        // V_j), gathered with the neighbour states
+        auto pair = [&](const CacheEntry<T, D, F32> &ce, const Q &q, const T *vw) {
             const T vj[3] = {(T)q.x, (T)q.y, (T)q.z};
             const T pj = (T)q.w;
             if (WALLS && (ce.jb & kWallBit)) {
-                T vd[3] = {T(0), T(0), T(0)};
-                for (int a = 0; a < D; ++a) vd[a] = (T)B.vn_a[(size_t)a * n + j];
-                pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vd, vj, pj, ap, Fa);
+                pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vw, vj, pj, ap, Fa);
             } else {
                 pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vj, vj, pj, ap, Fa);
             }
@@ -339,6 +372,7 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
                 // in flight per lane), then run the pair terms
                 uint32_t jbv[R];
                 Q qv[R];
+                T wv[R][3];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if (r < nr && r0 + r < cnt) {
@@ -346,6 +380,7 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
                                      ? ((const uint32_t *)(stg + R * RF::kCoefRow + r * RF::kJRow))[lane]
                                      : __float_as_uint(((const float4 *)(stg + r * RF::kCoefRow))[lane].w);
                         qv[r] = nbq[jbv[r] & ~kWallBit];
+                        if constexpr (WALLS) wall_velocity<D, F32, T>(B, jbv[r], wv[r]);
                     }
                 }
 #pragma unroll
@@ -366,7 +401,7 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
                             ce.F = (T)v.w;
                         }
                         ce.jb = jbv[r];
-                        pair(ce, qv[r]);
+                        pair(ce, qv[r], wv[r]);
                     }
                 }
                 __syncwarp();
@@ -398,11 +433,15 @@ __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, 
 #pragma unroll
                 for (int r = 0; r < R; ++r) ce[r].load(B, base + (size_t)min(k0 + r * L, cnt - 1) * kWarp);
                 Q qv[R];
+                T wv[R][3];
 #pragma unroll
-                for (int r = 0; r < R; ++r) qv[r] = nbq[ce[r].jb & ~kWallBit];
+                for (int r = 0; r < R; ++r) {
+                    qv[r] = nbq[ce[r].jb & ~kWallBit];
+                    if constexpr (WALLS) wall_velocity<D, F32, T>(B, ce[r].jb, wv[r]);
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    if (k0 + r * L < cnt) pair(ce[r], qv[r]);
+                    if (k0 + r * L < cnt) pair(ce[r], qv[r], wv[r]);
             }
         }
 #pragma unroll
@@ -672,7 +711,7 @@ __device__ __forceinline__ int dealt_instance(const int *pre, int ni, int k)
 // decisions; tiles of finished instances are skipped. Walls get their own phase
 // and barrier before the fluid phase.
 template <int D, bool F32, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2) ? 4 : 3) : (F32 ? 3 : 2)) k_loop(Buffers B)
+__global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2 && !WALLS) ? 4 : 3) : (F32 ? 3 : 2)) k_loop(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     constexpr int PPB = kBlock / L;
