@@ -278,254 +278,284 @@ __device__ __forceinline__ void wall_velocity(const Buffers &B, uint32_t jb, T *
     }
 }
 
+// The working precision of the pair sums: FP32 on the FP32C path, else FP64.
+template <bool F32>
+using Real = typename std::conditional<F32, float, double>::type;
+
+// Phase 1 of an iteration for slot s: L lanes per particle split its cached pair
+// list (lane l takes entries l, l+L, ...), accumulate the two rates
+// (Kahan-compensated FP32 on the FP32C path) and merge their partial sums with
+// warp shuffles; with one lane the warp's rows stream through the warp's
+// shared-memory ring. The rates, in the working precision, are valid on lane
+// lane_in = 0 of the particle's group.
+template <int D, bool F32, bool WALLS, int L>
+__device__ __forceinline__ void pair_sums(const Buffers &B, const Phys &P, int cur, int s, int lane_in, bool active,
+                                          RingPos &rp, Real<F32> &apT, Real<F32> *FT)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
+    const PairConst<T> k = pair_const<T>(P);
+    T vi[3] = {T(0), T(0), T(0)}, pi = T(0);
+    int cnt = 0;
+    if (active) {
+        if (F32) {
+            float4 q = B.nb32[cur][s];
+            vi[0] = q.x; vi[1] = q.y; vi[2] = q.z; pi = q.w;
+        } else {
+            double4_32a q = B.nb64[cur][s];
+            vi[0] = (T)q.x; vi[1] = (T)q.y; vi[2] = (T)q.z; pi = (T)q.w;
+        }
+        cnt = B.pcount[s];
+    }
+    Acc ap, Fa[3];
+    // the pair terms of one cache entry with its gathered neighbour state
+    using Q = typename std::conditional<F32, float4, double4_32a>::type;
+    const Q *nbq = F32 ? (const Q *)(const void *)B.nb32[cur] : (const Q *)(const void *)B.nb64[cur];
+    // vw: the prescribed velocity of a wall neighbour (the divergence term's
+    // V_j), gathered with the neighbour states
+    auto pair = [&](const CacheEntry<T, D, F32> &ce, const Q &q, const T *vw) {
+        const T vj[3] = {(T)q.x, (T)q.y, (T)q.z};
+        const T pj = (T)q.w;
+        if (WALLS && (ce.jb & kWallBit)) {
+            pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vw, vj, pj, ap, Fa);
+        } else {
+            pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vj, vj, pj, ap, Fa);
+        }
+    };
+    if constexpr (L == 1) {
+        // the warp's rows stream through its shared-memory ring; the
+        // neighbour states of a chunk's rows are gathered together
+        using RF = RowFmt<D, F32>;
+        constexpr int R = RF::kRows;
+        const int S = B.stages;
+        constexpr unsigned full = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        const WarpRing<D, F32> rg = warp_ring<D, F32>(S);
+        const int cmax = __reduce_max_sync(full, cnt);
+        const int nch = rp.ok ? (cmax + R - 1) / R : 0;
+        const size_t row0 = (size_t)(s >> 5) * B.K;      // first row of the warp's slice
+        const unsigned char *gcoef =
+            (F32 ? (const unsigned char *)B.pc32 : (const unsigned char *)B.pc64) + row0 * RF::kCoefRow;
+        const unsigned char *gj = (const unsigned char *)B.pj + row0 * (kWarp * 4);
+        auto issue = [&](int c) {        // lane 0: chunk c into its stage
+            const int st = (int)((rp.pos + (uint32_t)c) % (uint32_t)S);
+            const int r0 = c * R, nr = min(R, cmax - r0);
+            const uint32_t bc = (uint32_t)(nr * RF::kCoefRow), bj = (uint32_t)(nr * RF::kJRow);
+            unsigned char *stg = rg.buf + (size_t)st * RF::kStageBytes;
+            mbar_arrive_expect_tx(&rg.bar[st], bc + bj);
+            bulk_g2s(stg, gcoef + (size_t)r0 * RF::kCoefRow, bc, &rg.bar[st]);
+            if (RF::kSepJ) bulk_g2s(stg + R * RF::kCoefRow, gj + (size_t)r0 * RF::kJRow, bj, &rg.bar[st]);
+        };
+        if (lane == 0)
+            for (int c = 0; c < S && c < nch; ++c) issue(c);
+        int c = 0;
+        for (; c < nch; ++c) {
+            const uint32_t q = rp.pos + (uint32_t)c;
+            const int st = (int)(q % (uint32_t)S);
+            if (!mbar_wait(&rg.bar[st], (q / (uint32_t)S) & 1u)) break;
+            const int r0 = c * R, nr = min(R, cmax - r0);
+            const unsigned char *stg = rg.buf + (size_t)st * RF::kStageBytes;
+            // gather the neighbour states of the chunk's rows first (R loads
+            // in flight per lane), then run the pair terms
+            uint32_t jbv[R];
+            Q qv[R];
+            T wv[R][3];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < nr && r0 + r < cnt) {
+                    jbv[r] = RF::kSepJ
+                                 ? ((const uint32_t *)(stg + R * RF::kCoefRow + r * RF::kJRow))[lane]
+                                 : __float_as_uint(((const float4 *)(stg + r * RF::kCoefRow))[lane].w);
+                    qv[r] = nbq[jbv[r] & ~kWallBit];
+                    if constexpr (WALLS) wall_velocity<D, F32, T>(B, jbv[r], wv[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < nr && r0 + r < cnt) {
+                    CacheEntry<T, D, F32> ce;
+                    if (F32) {
+                        const float4 v = ((const float4 *)(stg + r * RF::kCoefRow))[lane];
+                        ce.g[0] = (T)v.x;
+                        ce.g[1] = (T)v.y;
+                        ce.g[2] = D == 3 ? (T)v.z : T(0);
+                        ce.F = D == 3 ? (T)v.w : (T)v.z;
+                    } else {
+                        const double4_32a v = ((const double4_32a *)(stg + r * RF::kCoefRow))[lane];
+                        ce.g[0] = (T)v.x;
+                        ce.g[1] = (T)v.y;
+                        ce.g[2] = (T)v.z;
+                        ce.F = (T)v.w;
+                    }
+                    ce.jb = jbv[r];
+                    pair(ce, qv[r], wv[r]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && c + S < nch) {
+                fence_proxy_async_smem();
+                issue(c + S);
+            }
+        }
+        if (c < nch) {
+            // a wait gave up: drain what is still in flight, the chunk
+            // whose wait gave up included (each wait bounded), stop using
+            // the ring and report
+            for (int d = c; d < nch && d < c + S; ++d) {
+                const uint32_t q = rp.pos + (uint32_t)d;
+                mbar_wait(&rg.bar[q % (uint32_t)S], (q / (uint32_t)S) & 1u);
+            }
+            rp.ok = false;
+            if (lane == 0) atomicOr(B.err, kErrCopy);
+        }
+        rp.pos += (uint32_t)nch;
+    } else {
+        const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+        // R entries per round: their cache entries, then their neighbour
+        // gathers, then the pair terms, so R loads of each kind are in flight
+        // per lane (the entries keep the order lane_in, lane_in + L, ...)
+        constexpr int R = 4;
+        for (int k0 = lane_in; k0 < cnt; k0 += L * R) {
+            CacheEntry<T, D, F32> ce[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) ce[r].load(B, base + (size_t)min(k0 + r * L, cnt - 1) * kWarp);
+            Q qv[R];
+            T wv[R][3];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                qv[r] = nbq[ce[r].jb & ~kWallBit];
+                if constexpr (WALLS) wall_velocity<D, F32, T>(B, ce[r].jb, wv[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (k0 + r * L < cnt) pair(ce[r], qv[r], wv[r]);
+        }
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        ap.shfl_merge(o);
+#pragma unroll
+        for (int a = 0; a < D; ++a) Fa[a].shfl_merge(o);
+    }
+    apT = (T)ap.value();
+#pragma unroll
+    for (int a = 0; a < D; ++a) FT[a] = (T)Fa[a].value();
+}
+
+// Phase 2 of an iteration: the BDF2 pseudo-acceleration and update, FP64
+// kappa (F + g - (3 V^k - 4 V^n + V^{n-1}) / (2 dt)), with the state-n part
+// kappa ((V^{n-1} - 4 V^n) / (2 dt) - g) precomputed in s_a; V^{k+1} in FP64.
+// On the FP32C path everything past the FP64 velocity update (the FP32
+// copies, p-hat, the residual terms) stays in FP32, to keep conversions off
+// the FP64 pipe: the residual terms are summed per warp with error-free
+// two-sum compensation (a double-float sum, accurate to ~1e-12 of the total)
+// and the warp totals are carried on in FP64. The FP64 path sums in FP64.
+// For slot s2 (fl: a fluid slot) with its rates apT, FT from phase 1, by every
+// lane of the warp; the warp's residual sums come back on lane 0.
+template <int D, bool F32>
+__device__ __forceinline__ void update_and_residuals(const Buffers &B, const Phys &P, int cur, int s2, bool fl,
+                                                     Real<F32> apT, const Real<F32> *FT, double &w_ap, double &w_av)
+{
+    const int nxt = cur ^ 1;
+    const int n = B.n;
+    if (F32) {
+        float r_ap = 0.f, r_av = 0.f;
+        if (fl) {
+            const float apf = (float)apT;
+            float vnf[3] = {0.f, 0.f, 0.f};
+            float av2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const size_t q = (size_t)a * n + s2;
+                const double vk = B.vk[cur][q];
+                const double Fv = (double)FT[a];
+                const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
+                const double vnew = __fma_rn(P.dtau, av, vk);
+                B.vk[nxt][q] = vnew;
+                vnf[a] = (float)vnew;
+                const float avf = (float)av;
+                av2 = __fmaf_rn(avf, avf, av2);
+            }
+            const float pnew = __fmaf_rn(P.dtau_f, apf, B.nb32[cur][s2].w);
+            B.nb32[nxt][s2] = make_float4(vnf[0], vnf[1], vnf[2], pnew);
+            r_av = sqrtf(av2);
+            r_ap = fabsf(apf);
+        }
+        float sa = r_ap, ea = 0.f, sb = r_av, eb = 0.f;
+        warp_sum2(sa, ea);
+        warp_sum2(sb, eb);
+        w_ap = (threadIdx.x & 31) == 0 ? (double)sa + (double)ea : 0.0;
+        w_av = (threadIdx.x & 31) == 0 ? (double)sb + (double)eb : 0.0;
+    } else {
+        double r_ap = 0.0, r_av = 0.0;
+        if (fl) {
+            const double apv = (double)apT;
+            double vnew[3] = {0, 0, 0};
+            double av2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const size_t q = (size_t)a * n + s2;
+                const double vk = B.vk[cur][q];
+                const double Fv = (double)FT[a];
+                const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
+                vnew[a] = __fma_rn(P.dtau, av, vk);
+                B.vk[nxt][q] = vnew[a];
+                av2 = __fma_rn(av, av, av2);
+            }
+            const double pnew = __fma_rn(P.dtau, apv, B.nb64[cur][s2].w);
+            B.nb64[nxt][s2] = make_double4_32a(vnew[0], vnew[1], vnew[2], pnew);
+            r_av = sqrt(av2);
+            r_ap = fabs(apv);
+        }
+        w_ap = warp_sum<double>(r_ap);
+        w_av = warp_sum<double>(r_av);
+    }
+}
+
 // One iteration over tile `tile` (slots tile*PPB .. tile*PPB+PPB-1, PPB = 256/L),
 // by the whole block. Writes iterate k+1 of the tile's fluid particles and
-// returns, on thread 0, the tile's residual sums (sum |dp/dtau|, sum |dV/dtau|).
-//
-// Phase 1: L lanes per particle split its cached pair list (lane l takes entries
-// l, l+L, ...), accumulate the two rates (Kahan-compensated FP32 on the FP32C
-// path), and merge their partial sums with warp shuffles. The tile's particles
-// are a contiguous run of slots, so the warp reads of the sliced pair cache
-// stay coalesced.
-// Phase 2: one thread per particle (the first PPB threads, whole warps, so the
-// FP64 work runs with every lane busy) applies the BDF2 pseudo-acceleration and
-// the update in FP64 and forms the residual terms.
+// returns, on thread 0, the tile's residual sums (sum |dp/dtau|, sum |dV/dtau|):
+// the warps' sums added in warp order. The tile's particles are a contiguous run
+// of slots, so the warp reads of the sliced pair cache stay coalesced. Phase 2
+// runs one thread per particle (the first PPB threads, whole warps, so the FP64
+// work runs with every lane busy); with one lane per particle that thread is the
+// particle's phase-1 lane, so the rates stay in registers.
 template <int D, bool F32, bool WALLS, int L>
 __device__ __forceinline__ void tile_iteration(const Buffers &B, const Phys &P, int cur, int tile,
                                                TileShared<typename std::conditional<F32, float, double>::type, D, L> &sh,
                                                RingPos &rp, double &blk_ap, double &blk_av)
 {
     using T = typename std::conditional<F32, float, double>::type;
-    using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
     constexpr int PPB = kBlock / L;
     static_assert(PPB % kWarp == 0, "whole warps in phase 2");
-    const int nxt = cur ^ 1;
     const int n = B.n;
     const int grp = threadIdx.x / L, lane_in = threadIdx.x % L;
     const int s = tile * PPB + grp;
     const bool active = s < n && B.gid_a[s] < (uint32_t)B.nf;   // fluid (not wall, not padding)
-
-    // ---------------- phase 1: pair sums
-    {
-        const PairConst<T> k = pair_const<T>(P);
-        T vi[3] = {T(0), T(0), T(0)}, pi = T(0);
-        int cnt = 0;
-        if (active) {
-            if (F32) {
-                float4 q = B.nb32[cur][s];
-                vi[0] = q.x; vi[1] = q.y; vi[2] = q.z; pi = q.w;
-            } else {
-                double4_32a q = B.nb64[cur][s];
-                vi[0] = (T)q.x; vi[1] = (T)q.y; vi[2] = (T)q.z; pi = (T)q.w;
-            }
-            cnt = B.pcount[s];
-        }
-        Acc ap, Fa[3];
-        // the pair terms of one cache entry with its gathered neighbour state
-        using Q = typename std::conditional<F32, float4, double4_32a>::type;
-        const Q *nbq = F32 ? (const Q *)(const void *)B.nb32[cur] : (const Q *)(const void *)B.nb64[cur];
-        // vw: the prescribed velocity of a wall neighbour (the divergence term's
-        // V_j), gathered with the neighbour states
-        auto pair = [&](const CacheEntry<T, D, F32> &ce, const Q &q, const T *vw) {
-            const T vj[3] = {(T)q.x, (T)q.y, (T)q.z};
-            const T pj = (T)q.w;
-            if (WALLS && (ce.jb & kWallBit)) {
-                pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vw, vj, pj, ap, Fa);
-            } else {
-                pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vj, vj, pj, ap, Fa);
-            }
-        };
-        if constexpr (L == 1) {
-            // the warp's rows stream through its shared-memory ring; the
-            // neighbour states of a chunk's rows are gathered together
-            using RF = RowFmt<D, F32>;
-            constexpr int R = RF::kRows;
-            const int S = B.stages;
-            constexpr unsigned full = 0xffffffffu;
-            const int lane = threadIdx.x & 31;
-            const WarpRing<D, F32> rg = warp_ring<D, F32>(S);
-            const int cmax = __reduce_max_sync(full, cnt);
-            const int nch = rp.ok ? (cmax + R - 1) / R : 0;
-            const size_t row0 = (size_t)(s >> 5) * B.K;      // first row of the warp's slice
-            const unsigned char *gcoef =
-                (F32 ? (const unsigned char *)B.pc32 : (const unsigned char *)B.pc64) + row0 * RF::kCoefRow;
-            const unsigned char *gj = (const unsigned char *)B.pj + row0 * (kWarp * 4);
-            auto issue = [&](int c) {        // lane 0: chunk c into its stage
-                const int st = (int)((rp.pos + (uint32_t)c) % (uint32_t)S);
-                const int r0 = c * R, nr = min(R, cmax - r0);
-                const uint32_t bc = (uint32_t)(nr * RF::kCoefRow), bj = (uint32_t)(nr * RF::kJRow);
-                unsigned char *stg = rg.buf + (size_t)st * RF::kStageBytes;
-                mbar_arrive_expect_tx(&rg.bar[st], bc + bj);
-                bulk_g2s(stg, gcoef + (size_t)r0 * RF::kCoefRow, bc, &rg.bar[st]);
-                if (RF::kSepJ) bulk_g2s(stg + R * RF::kCoefRow, gj + (size_t)r0 * RF::kJRow, bj, &rg.bar[st]);
-            };
-            if (lane == 0)
-                for (int c = 0; c < S && c < nch; ++c) issue(c);
-            int c = 0;
-            for (; c < nch; ++c) {
-                const uint32_t q = rp.pos + (uint32_t)c;
-                const int st = (int)(q % (uint32_t)S);
-                if (!mbar_wait(&rg.bar[st], (q / (uint32_t)S) & 1u)) break;
-                const int r0 = c * R, nr = min(R, cmax - r0);
-                const unsigned char *stg = rg.buf + (size_t)st * RF::kStageBytes;
-                // gather the neighbour states of the chunk's rows first (R loads
-                // in flight per lane), then run the pair terms
-                uint32_t jbv[R];
-                Q qv[R];
-                T wv[R][3];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r < nr && r0 + r < cnt) {
-                        jbv[r] = RF::kSepJ
-                                     ? ((const uint32_t *)(stg + R * RF::kCoefRow + r * RF::kJRow))[lane]
-                                     : __float_as_uint(((const float4 *)(stg + r * RF::kCoefRow))[lane].w);
-                        qv[r] = nbq[jbv[r] & ~kWallBit];
-                        if constexpr (WALLS) wall_velocity<D, F32, T>(B, jbv[r], wv[r]);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r < nr && r0 + r < cnt) {
-                        CacheEntry<T, D, F32> ce;
-                        if (F32) {
-                            const float4 v = ((const float4 *)(stg + r * RF::kCoefRow))[lane];
-                            ce.g[0] = (T)v.x;
-                            ce.g[1] = (T)v.y;
-                            ce.g[2] = D == 3 ? (T)v.z : T(0);
-                            ce.F = D == 3 ? (T)v.w : (T)v.z;
-                        } else {
-                            const double4_32a v = ((const double4_32a *)(stg + r * RF::kCoefRow))[lane];
-                            ce.g[0] = (T)v.x;
-                            ce.g[1] = (T)v.y;
-                            ce.g[2] = (T)v.z;
-                            ce.F = (T)v.w;
-                        }
-                        ce.jb = jbv[r];
-                        pair(ce, qv[r], wv[r]);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0 && c + S < nch) {
-                    fence_proxy_async_smem();
-                    issue(c + S);
-                }
-            }
-            if (c < nch) {
-                // a wait gave up: drain what is still in flight, the chunk
-                // whose wait gave up included (each wait bounded), stop using
-                // the ring and report
-                for (int d = c; d < nch && d < c + S; ++d) {
-                    const uint32_t q = rp.pos + (uint32_t)d;
-                    mbar_wait(&rg.bar[q % (uint32_t)S], (q / (uint32_t)S) & 1u);
-                }
-                rp.ok = false;
-                if (lane == 0) atomicOr(B.err, kErrCopy);
-            }
-            rp.pos += (uint32_t)nch;
-        } else {
-            const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-            // R entries per round: their cache entries, then their neighbour
-            // gathers, then the pair terms, so R loads of each kind are in flight
-            // per lane (the entries keep the order lane_in, lane_in + L, ...)
-            constexpr int R = 4;
-            for (int k0 = lane_in; k0 < cnt; k0 += L * R) {
-                CacheEntry<T, D, F32> ce[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) ce[r].load(B, base + (size_t)min(k0 + r * L, cnt - 1) * kWarp);
-                Q qv[R];
-                T wv[R][3];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    qv[r] = nbq[ce[r].jb & ~kWallBit];
-                    if constexpr (WALLS) wall_velocity<D, F32, T>(B, ce[r].jb, wv[r]);
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (k0 + r * L < cnt) pair(ce[r], qv[r], wv[r]);
-            }
-        }
-#pragma unroll
-        for (int o = L / 2; o > 0; o >>= 1) {
-            ap.shfl_merge(o);
-#pragma unroll
-            for (int a = 0; a < D; ++a) Fa[a].shfl_merge(o);
-        }
+    T apT = T(0), FT[3] = {T(0), T(0), T(0)};
+    pair_sums<D, F32, WALLS, L>(B, P, cur, s, lane_in, active, rp, apT, FT);
+    double w_ap = 0, w_av = 0;
+    if constexpr (L == 1) {
+        update_and_residuals<D, F32>(B, P, cur, s, active, apT, FT, w_ap, w_av);
+    } else {
         if (lane_in == 0) {
-            sh.part[0][grp] = (T)ap.value();
+            sh.part[0][grp] = apT;
 #pragma unroll
-            for (int a = 0; a < D; ++a) sh.part[1 + a][grp] = (T)Fa[a].value();
+            for (int a = 0; a < D; ++a) sh.part[1 + a][grp] = FT[a];
+        }
+        __syncthreads();
+        if (threadIdx.x < PPB) {
+            const int s2 = tile * PPB + threadIdx.x;
+            const bool fl = s2 < n && B.gid_a[s2] < (uint32_t)B.nf;
+            T fq[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int a = 0; a < D; ++a) fq[a] = sh.part[1 + a][threadIdx.x];
+            update_and_residuals<D, F32>(B, P, cur, s2, fl, sh.part[0][threadIdx.x], fq, w_ap, w_av);
         }
     }
-    __syncthreads();
-
-    // ---------------- phase 2: BDF2 pseudo-acceleration and update, FP64
-    // kappa (F + g - (3 V^k - 4 V^n + V^{n-1}) / (2 dt)), with the state-n part
-    // kappa ((V^{n-1} - 4 V^n) / (2 dt) - g) precomputed in s_a; V^{k+1} in FP64.
-    // On the FP32C path everything past the FP64 velocity update (the FP32
-    // copies, p-hat, the residual terms) stays in FP32, to keep conversions off
-    // the FP64 pipe: the residual terms are summed per warp with error-free
-    // two-sum compensation (a double-float sum, accurate to ~1e-12 of the total)
-    // and the warp totals are carried on in FP64. The FP64 path sums in FP64.
-    if (threadIdx.x < PPB) {
-        const int s2 = tile * PPB + threadIdx.x;
-        const bool fl = s2 < n && B.gid_a[s2] < (uint32_t)B.nf;
-        double w_ap, w_av;
-        if (F32) {
-            float r_ap = 0.f, r_av = 0.f;
-            if (fl) {
-                const float apf = (float)sh.part[0][threadIdx.x];
-                float vnf[3] = {0.f, 0.f, 0.f};
-                float av2 = 0.f;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const size_t q = (size_t)a * n + s2;
-                    const double vk = B.vk[cur][q];
-                    const double Fv = (double)sh.part[1 + a][threadIdx.x];
-                    const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
-                    const double vnew = __fma_rn(P.dtau, av, vk);
-                    B.vk[nxt][q] = vnew;
-                    vnf[a] = (float)vnew;
-                    const float avf = (float)av;
-                    av2 = __fmaf_rn(avf, avf, av2);
-                }
-                const float pnew = __fmaf_rn(P.dtau_f, apf, B.nb32[cur][s2].w);
-                B.nb32[nxt][s2] = make_float4(vnf[0], vnf[1], vnf[2], pnew);
-                r_av = sqrtf(av2);
-                r_ap = fabsf(apf);
-            }
-            float sa = r_ap, ea = 0.f, sb = r_av, eb = 0.f;
-            warp_sum2(sa, ea);
-            warp_sum2(sb, eb);
-            w_ap = (threadIdx.x & 31) == 0 ? (double)sa + (double)ea : 0.0;
-            w_av = (threadIdx.x & 31) == 0 ? (double)sb + (double)eb : 0.0;
-        } else {
-            double r_ap = 0.0, r_av = 0.0;
-            if (fl) {
-                const double apv = (double)sh.part[0][threadIdx.x];
-                double vnew[3] = {0, 0, 0};
-                double av2 = 0.0;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const size_t q = (size_t)a * n + s2;
-                    const double vk = B.vk[cur][q];
-                    const double Fv = (double)sh.part[1 + a][threadIdx.x];
-                    const double av = __fma_rn(P.kappa, Fv, -__fma_rn(P.kc3, vk, B.s_a[q]));
-                    vnew[a] = __fma_rn(P.dtau, av, vk);
-                    B.vk[nxt][q] = vnew[a];
-                    av2 = __fma_rn(av, av, av2);
-                }
-                const double pnew = __fma_rn(P.dtau, apv, B.nb64[cur][s2].w);
-                B.nb64[nxt][s2] = make_double4_32a(vnew[0], vnew[1], vnew[2], pnew);
-                r_av = sqrt(av2);
-                r_ap = fabs(apv);
-            }
-            w_ap = warp_sum<double>(r_ap);
-            w_av = warp_sum<double>(r_av);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            sh.red[0][threadIdx.x >> 5] = w_ap;
-            sh.red[1][threadIdx.x >> 5] = w_av;
-        }
+    if (threadIdx.x < PPB && (threadIdx.x & 31) == 0) {
+        sh.red[0][threadIdx.x >> 5] = w_ap;
+        sh.red[1][threadIdx.x >> 5] = w_av;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1050,6 +1080,7 @@ const void *loop_kernel() { return (const void *)k_loop<D, F, W, L>; }
 
 template <int D, bool F, int L>
 const void *async_kernel() { return (const void *)k_loop_async<D, F, L>; }
+
 
 }  // namespace
 
