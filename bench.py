@@ -110,8 +110,10 @@ def with_steady(d, wcfg, iters):
     """Steady-state mode (Sec. 2.3, Eq. mom-steady) with a fixed number of
     pseudo-iterations per solve, in every instance, for both arms."""
     for x in (d if isinstance(d, list) else [d]):
-        x["cfg"] = dict(x["cfg"], steady=1, fixed_iters=iters)
+        # the particles stay where they are, so there is nothing to shift
+        x["cfg"] = dict(x["cfg"], steady=1, fixed_iters=iters, shifting=0)
     wcfg["steady"] = f"on: one pseudo-time solve of {iters} iterations per step, particles fixed"
+    wcfg.pop("shifting", None)
 
 
 def with_moving(d, wcfg, moving):

@@ -313,11 +313,15 @@ __device__ __forceinline__ void pair_sums(const Buffers &B, const Phys &P, int c
     const Q *nbq = F32 ? (const Q *)(const void *)B.nb32[cur] : (const Q *)(const void *)B.nb64[cur];
     // vw: the prescribed velocity of a wall neighbour (the divergence term's
     // V_j), gathered with the neighbour states
+    // (one call for both kinds of neighbour: a warp whose lanes hold both runs
+    // the pair arithmetic once)
     auto pair = [&](const CacheEntry<T, D, F32> &ce, const Q &q, const T *vw) {
         const T vj[3] = {(T)q.x, (T)q.y, (T)q.z};
         const T pj = (T)q.w;
-        if (WALLS && (ce.jb & kWallBit)) {
-            pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vw, vj, pj, ap, Fa);
+        if constexpr (WALLS) {
+            const bool wall = (ce.jb & kWallBit) != 0;
+            const T vd[3] = {wall ? vw[0] : vj[0], wall ? vw[1] : vj[1], wall ? vw[2] : vj[2]};
+            pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vd, vj, pj, ap, Fa);
         } else {
             pair_accumulate<D, T, Acc>(k, ce.g, ce.F, vi, pi, vj, vj, pj, ap, Fa);
         }
@@ -772,7 +776,8 @@ __global__ void __launch_bounds__(kBlock, L == 1 ? ((F32 && D == 2 && !WALLS) ? 
             constexpr int GPB = kBlock / kWallLanes;
             for (int w = blockIdx.x * GPB + (int)threadIdx.x / kWallLanes; w < B.nw; w += gridDim.x * GPB) {
                 const int s = B.wslot_a[w];
-                if (!B.ls[B.inst_of[s]].done) wall_slot<D, F32>(B, s, cur, sub, gmask);
+                // (one instance: it is iterating, no need to look)
+                if (single || !B.ls[B.inst_of[s]].done) wall_slot<D, F32>(B, s, cur, sub, gmask);
             }
             if (!grid_barrier(&B.ctrl->bar, ++epoch, B.err, ok_sh, B.barrier_ns)) break;
         }
