@@ -1322,13 +1322,11 @@ int dtsph_get_neighbors(dtsph_ctx *c, int64_t i, int64_t *out, int64_t cap, int6
     int cnt = 0;
     CK(cudaMemcpy(&cnt, B.pcount + s, sizeof(int), cudaMemcpyDeviceToHost));
     std::vector<int64_t> got;
-    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
-    for (int k = 0; k < cnt; ++k) {
-        size_t e = base + (size_t)k * kWarp;
-        uint32_t jb;
-        CK(cudaMemcpy(&jb, B.pj + e, sizeof jb, cudaMemcpyDeviceToHost));
-        got.push_back((int64_t)gid[jb & kSlotMask]);
-    }
+    std::vector<uint32_t> lst((size_t)std::max(cnt, 0));
+    if (cnt > 0)
+        CK(cudaMemcpy(lst.data(), B.pjt + (size_t)s * list_stride(B.K), sizeof(uint32_t) * cnt,
+                      cudaMemcpyDeviceToHost));
+    for (int k = 0; k < cnt; ++k) got.push_back((int64_t)gid[lst[k] & kSlotMask]);
     std::sort(got.begin(), got.end());
     *count = (int64_t)got.size();
     for (int64_t k = 0; k < cap && k < (int64_t)got.size(); ++k) out[k] = got[k];

@@ -195,7 +195,7 @@ struct Buffers {
     float4 *nb32[2];       // FP32C: (V, p-hat) packed for neighbour gathers
     // pair cache, sliced by warp: entry k of slot i at ((i/32) K + k) 32 + i%32
     uint32_t *pj;          // list entries (list_entry); after the pair-cache pass slot | kWallBit
-    uint32_t *pjt;         // list staging, per slot: entry k of slot s at s Ks + k (Ks = list_stride(K))
+    uint32_t *pjt;         // neighbour lists, per slot: entry k of slot s at s Ks + k (Ks = list_stride(K))
     double4_32a *pc64;         // FP64: (gradW, F_ij)
     float4 *pc32;          // FP32C: (gradW, F_ij); in 2D .w holds the index bits
     int *pcount;           // neighbours of each slot
@@ -241,7 +241,8 @@ int launch_permute_a_to_b(const Buffers &B, cudaStream_t st);
 int launch_permute_b_to_a(const Buffers &B, cudaStream_t st);
 // Neighbour lists of every slot at positions xpos (order of the latest binning);
 // one launch.
-void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
+void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st,
+                  bool sliced);
 int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st);
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
 int launch_walls_iter(const Buffers &B, cudaStream_t st);
@@ -278,7 +279,16 @@ int launch_fill_instance(Inst *inst, Geom *geo, Phys *phys, int i, const Inst &I
                          cudaStream_t st);
 
 int iterate_tiles(const Buffers &B);   // tiles of the iterate kernel (one block each)
-int list_stride(int K);                // row length of the per-slot list staging array
+// Row length of the per-slot neighbour lists: K rounded up to 8 entries, so a
+// row starts on a 32-byte boundary.
+__host__ __device__ constexpr int list_stride(int K) { return (K + 7) / 8 * 8; }
+
+// The neighbour list of slot s as the builders write it (entries in order,
+// pcount[s] of them).
+__device__ __forceinline__ const uint32_t *slot_list(const Buffers &B, int s)
+{
+    return B.pjt + (size_t)s * list_stride(B.K);
+}
 
 // ------------------------------------------------- one parameter set (api.cu)
 // Shared by the context entry points and the allocation-free rate evaluation,

@@ -46,7 +46,8 @@ template <> struct Staged<false> { using type = double4_32a; };
 
 template <int D, bool F32>
 __global__ void __launch_bounds__(kBlock) k_nlist_cells(Buffers B, const double *__restrict__ xpos,
-                                                        const uint32_t *__restrict__ gid, uint32_t *__restrict__ lists)
+                                                        const uint32_t *__restrict__ gid, uint32_t *__restrict__ lists,
+                                                        int Ks)
 {
     constexpr int NC = D == 3 ? 27 : 9;                 // surrounding cells
     constexpr int CH = F32 ? 256 : 128;                 // staged candidates per round
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) k_nlist_cells(Buffers B, const double 
                         const int base = __shfl_sync(full, cnt, h);
                         if (in) {
                             const int pos = base + __popc(bal & lt);
-                            if (pos < K) lists[(size_t)s * K + pos] = ej;
+                            if (pos < K) lists[(size_t)s * Ks + pos] = ej;
                         }
                         if (lane == h) cnt += __popc(bal);
                     }
@@ -433,20 +434,24 @@ __global__ void __launch_bounds__(kBlock) k_list_slice(Buffers B, const uint32_t
 
 }  // namespace
 
-int list_stride(int K) { return (K + kBufEntries - 1) / kBufEntries * kBufEntries; }
+static_assert(list_stride(1) % kBufEntries == 0, "a list row holds whole buffers of the 3D builder");
 
-void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
+// The lists of every slot at xpos into the per-slot layout (slot_list); with
+// `sliced`, also copied into the sliced layout of pj for the kernels that walk
+// them every pseudo-iteration (the moving pass). The passes that read a list
+// once per step (state n, pair cache, shifting) read the per-slot layout.
+void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st,
+                  bool sliced)
 {
     (void)cell;
     const int nb = (B.ncell + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    int Ks = B.K;
+    const int Ks = list_stride(B.K);
     if (B.dim == 3 && B.fp32c) {
-        Ks = list_stride(B.K);
         k_nlist_cells3_f32<<<nb, kBlock, 0, st>>>(B, xpos, B.pjt, Ks);
     } else {
-        DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist_cells<D, F32><<<nb, kBlock, 0, st>>>(B, xpos, gid, B.pjt)));
+        DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist_cells<D, F32><<<nb, kBlock, 0, st>>>(B, xpos, gid, B.pjt, Ks)));
     }
-    k_list_slice<<<(B.n / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock, kBlock, 0, st>>>(B, B.pjt, Ks);
+    if (sliced) k_list_slice<<<(B.n / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock, kBlock, 0, st>>>(B, B.pjt, Ks);
 }
 
 }  // namespace dtsph

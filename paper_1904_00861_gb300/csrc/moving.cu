@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long l
 
 int launch_move_prepare(const Buffers &B, cudaStream_t st)
 {
-    launch_nlist(B, B.xp_a, B.cell_a, B.gid_a, st);
+    launch_nlist(B, B.xp_a, B.cell_a, B.gid_a, st, true);   // walked every pass: sliced
     if (B.fp32c) k_move_init<true><<<blocks(B.n), kBlock, 0, st>>>(B);
     else k_move_init<false><<<blocks(B.n), kBlock, 0, st>>>(B);
     return 2;

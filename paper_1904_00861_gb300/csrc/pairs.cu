@@ -44,11 +44,10 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
     const float4 oi = wall && F32 ? B.off[s] : make_float4(0, 0, 0, 0);
     double acc[6] = {0, 0, 0, 0, 0, 0};   // sum W, sum p W, sum rho0 (g . r) W, sum V W
     const double sigma = P.sig_h * P.h;
-    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+    const uint32_t *lst = slot_list(B, s);
     const int cnt = wall ? B.pcount[s] : 0;
     for (int k = lane_in; k < cnt; k += L) {
-        const size_t e = base + (size_t)k * kWarp;
-        const uint32_t jb = B.pj[e];
+        const uint32_t jb = lst[k];
         if (jb & kWallBit) continue;                    // fluid neighbours only
         const int j = entry_slot(jb);
         int dx, dy, dz;
@@ -115,7 +114,7 @@ __global__ void __launch_bounds__(kBlock, F32 ? 3 : 1) k_state_n(Buffers B)
         const T vi[3] = {(T)qi.x, (T)qi.y, (T)qi.z};
         const T pi = (T)qi.w;
         const float4 oi = F32 && fluid ? B.off[s] : make_float4(0, 0, 0, 0);
-        const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+        const uint32_t *lst = slot_list(B, s);
         const int cnt = fluid ? B.pcount[s] : 0;
         // R entries per round: their indices, then their gathers (neighbour
         // state and, FP32C, offset), then the pair terms, so that R loads are in
@@ -125,12 +124,21 @@ __global__ void __launch_bounds__(kBlock, F32 ? 3 : 1) k_state_n(Buffers B)
         for (int q0 = lane_in; q0 < cnt; q0 += L * R) {
             uint32_t jbv[R];
             int cv[R];
+            if constexpr (L == 1) {
+                // four consecutive entries in one 16-byte load (rows start on
+                // 32-byte boundaries and q0 is a multiple of four); an entry
+                // past the count repeats entry q0, so its gathers stay in bounds
+                const uint4 v = *reinterpret_cast<const uint4 *>(lst + q0);
+                jbv[0] = v.x;
+                jbv[1] = q0 + 1 < cnt ? v.y : v.x;
+                jbv[2] = q0 + 2 < cnt ? v.z : v.x;
+                jbv[3] = q0 + 3 < cnt ? v.w : v.x;
+            } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const size_t e = base + (size_t)min(q0 + r * L, cnt - 1) * kWarp;
-                jbv[r] = B.pj[e];
-                cv[r] = entry_code(jbv[r]);
+                for (int r = 0; r < R; ++r) jbv[r] = lst[min(q0 + r * L, cnt - 1)];
             }
+#pragma unroll
+            for (int r = 0; r < R; ++r) cv[r] = entry_code(jbv[r]);
             Q qv[R];
             float4 ov[R];
 #pragma unroll
@@ -234,7 +242,8 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
     const int n = B.n;
     if (s >= n || gid[s] == kNoParticle) return;
     const bool wall_s = gid[s] >= (uint32_t)B.nf;
-    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+    const uint32_t *lst = slot_list(B, s);                    // the list, per slot
+    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);   // the cache rows, sliced
     const float4 oi = F32 ? B.off[s] : make_float4(0, 0, 0, 0);
     const T sigma = (T)(P.sig_h * P.h);
     const int cnt = B.pcount[s];
@@ -245,8 +254,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
         int cv[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const size_t e = base + (size_t)min(q0 + r * L, cnt - 1) * kWarp;
-            jbv[r] = B.pj[e];
+            jbv[r] = lst[min(q0 + r * L, cnt - 1)];
             cv[r] = entry_code(jbv[r]);
         }
         float4 ov[R];
@@ -337,11 +345,10 @@ __global__ void __launch_bounds__(kBlock) k_shift(Buffers B)
     const T w_h = sigma * quintic_w<T>(T(1));
     Acc dr[3], gp[3], gv[3][3];
     double divr = 0.0;            // div r_i = -sum_j V_j r_ij . gradW_ij, walls included
-    const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);
+    const uint32_t *lst = slot_list(B, s);
     const int cnt = B.pcount[s];
     for (int k = 0; k < cnt; ++k) {
-        const size_t e = base + (size_t)k * kWarp;
-        const uint32_t jb = B.pj[e];
+        const uint32_t jb = lst[k];
         const int j = entry_slot(jb);
         int dx, dy, dz;
         decode_shift(entry_code(jb), dx, dy, dz);
@@ -408,7 +415,7 @@ int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st)
 {
     constexpr int L = kSumLanes;
     const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
-    launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st);
+    launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st, false);
     int k = 1;
     if (B.nw > 0) {
         DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, L><<<nb, kBlock, 0, st>>>(B)));
@@ -429,7 +436,7 @@ int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st)
 // Neighbour lists at xpos, then the pair coefficients.
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
 {
-    launch_nlist(B, xpos, cell, gid, st);
+    launch_nlist(B, xpos, cell, gid, st, false);
     const int L = nlist_lanes(B.n);
     const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
     if (L == 1) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 1><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
@@ -443,7 +450,7 @@ int launch_shift(const Buffers &B, cudaStream_t st)
 {
     int k = launch_binning(B, B.x_a, B.gid_a, st);            // cells at r^{n+1}
     k += launch_permute_a_to_b(B, st);
-    launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st);
+    launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st, false);
     DTSPH_DISPATCH(B.dim, B.fp32c, (k_shift<D, F32><<<(B.n + kBlock - 1) / kBlock, kBlock, 0, st>>>(B)));
     return k + 2;
 }
