@@ -51,7 +51,9 @@ UNIT = "particle-iterations/s"
 # line reports the captured bytes per algorithmic byte times the algorithmic
 # bytes of its own launches. A variant not listed, or one whose kernel changed
 # after its capture, reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("batch-64x-tgv2d", 2, 1, 2): (6.492738e9 + 0.500071e9, 6.667369e9, "profiles/k_loop_async_batch64_tgv2d.md"),
+}
 
 
 def make_workload(name: str, n_side: int, re: float):
