@@ -253,10 +253,20 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
         uint32_t jbv[R];
         int cv[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            jbv[r] = lst[min(q0 + r * L, cnt - 1)];
-            cv[r] = entry_code(jbv[r]);
+        if constexpr (L == 1) {
+            // four consecutive entries in one 16-byte load (as in k_state_n);
+            // an entry past the count repeats entry q0
+            const uint4 v = *reinterpret_cast<const uint4 *>(lst + q0);
+            jbv[0] = v.x;
+            jbv[1] = q0 + 1 < cnt ? v.y : v.x;
+            jbv[2] = q0 + 2 < cnt ? v.z : v.x;
+            jbv[3] = q0 + 3 < cnt ? v.w : v.x;
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) jbv[r] = lst[min(q0 + r * L, cnt - 1)];
         }
+#pragma unroll
+        for (int r = 0; r < R; ++r) cv[r] = entry_code(jbv[r]);
         float4 ov[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) ov[r] = F32 ? B.off[entry_slot(jbv[r])] : make_float4(0.f, 0.f, 0.f, 0.f);
