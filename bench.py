@@ -199,6 +199,9 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="lanes per particle of the iterate kernel (0: autotuned)")
     ap.add_argument("--stages", type=int, default=0, help="staging depth with --lanes 1 (0: autotuned or 3)")
+    ap.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
+                    help="pair terms of the loop: 1 from the pair-coefficient cache, 2 recomputed every "
+                         "pseudo-iteration from the lists (no cache), 0 chosen by the library")
     ap.add_argument("--shifting", action="store_true", help="particle shifting after every real step (both arms)")
     ap.add_argument("--moving", type=int, default=0, choices=[0, 1, 2],
                     help="particles moved in pseudo-time (Algorithm 1; both arms): 1 lists of r^0, "
@@ -464,7 +467,7 @@ def main_ours(args):
         with_steady(d, wcfg, args.steady)
     if args.moving:
         with_moving(d, wcfg, args.moving)
-    kern = dict(lanes=args.lanes, stages=args.stages)
+    kern = dict(lanes=args.lanes, stages=args.stages, form=args.form)
     # batches without walls run the decoupled loop kernel (the library's rule)
     decoupled = (args.graph == 2 and isinstance(d, list) and 1 < len(d) <= 1024 and not args.moving
                  and all(x["vw"] is None for x in d) and os.environ.get("DTSPH_LOCKSTEP_LOOP", "0") in ("", "0"))

@@ -136,7 +136,17 @@ typedef struct {
                                  moves farther than skin/2 from r^0 ends the step with
                                  DTSPH_E_SKIN). Not with steady. With graph = 2 the loop runs
                                  as in graph = 1. Instances of a batch share it. */
-    int32_t pad1;
+    int32_t form;             /* the pair terms of the pseudo-time loop. 1: from the pair-
+                                 coefficient cache, written once per real step by a pass over
+                                 the lists at r^0 (gradW_ij and F_ij per pair). 2: recomputed
+                                 in every pseudo-iteration from the lists at r^0 with the same
+                                 operations (no cache; the cheaper form when a step takes few
+                                 iterations). Both forms give the same bits. 0 (default):
+                                 chosen per real step from the autotuner's timings of both
+                                 forms and the iteration count of the latest finished step
+                                 (graph = 2; the cache otherwise). Form 2 only without walls,
+                                 particles fixed in pseudo-time (DTSPH_E_UNSUPPORTED
+                                 otherwise). Instances of a batch share it. */
     double skin;              /* list skin for moving = 2 (a length > 0; the lists then hold
                                  every pair within 3h + skin, dtsph_get_neighbors included);
                                  ignored otherwise. Instances of a batch share it. */

@@ -284,6 +284,9 @@ int dtsph::check_params(const dtsph_params *p, char *msg, size_t cap)
     if (p->moving && p->steady) return say(msg, cap, DTSPH_E_ARG, "the steady mode keeps the particles fixed: moving must be 0");
     if (!(p->skin >= 0) || !std::isfinite(p->skin)) return say(msg, cap, DTSPH_E_ARG, "skin must be >= 0 and finite");
     if (p->moving == 2 && !(p->skin > 0)) return say(msg, cap, DTSPH_E_ARG, "moving = 2 needs a positive skin");
+    if (p->form < 0 || p->form > 2) return say(msg, cap, DTSPH_E_ARG, "form must be 0, 1 or 2");
+    if (p->form == 2 && p->moving)
+        return say(msg, cap, DTSPH_E_UNSUPPORTED, "form 2 (no pair cache) needs particles fixed in pseudo-time");
     return DTSPH_OK;
 }
 
@@ -538,6 +541,11 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     int *d_sched = nullptr;
     B.async_loop = ni > 1 && ni <= kDealMaxInst && wo == 0 && !(c->prm[0].moving && !c->prm[0].steady) &&
                    env_u64("DTSPH_LOCKSTEP_LOOP", 0) == 0;
+    if (c->prm[0].form == 2 && wo > 0) {
+        free_all(c);
+        return fail(c, DTSPH_E_UNSUPPORTED, "form 2 (no pair cache) is for contexts without walls");
+    }
+    B.form_a = c->prm[0].form == 2;
     if (B.async_loop) {
         A(B.il, ni) A(d_sched, ni)
     }
@@ -610,8 +618,14 @@ int enqueue_pre_loop(dtsph_ctx *c, cudaStream_t st)
     k += launch_state_n(B, true, st);                     // walls, rates, predictor
     k += launch_binning(B, B.xp_b, B.gid_b, st);         // cells at r^0
     k += launch_permute_b_to_a(B, st);
-    if (B.xk[0]) k += launch_move_prepare(B, st);              // particles moving in pseudo-time
-    else k += launch_pair_cache(B, B.xp_a, B.cell_a, B.gid_a, st);   // also resets the loop state
+    if (B.xk[0]) {
+        k += launch_move_prepare(B, st);                          // particles moving in pseudo-time
+    } else if (B.form_a) {
+        launch_nlist(B, B.xp_a, B.cell_a, B.gid_a, st, false);   // the loop recomputes the pair terms
+        k += 1 + launch_loop_reset(B, st);
+    } else {
+        k += launch_pair_cache(B, B.xp_a, B.cell_a, B.gid_a, st);   // also resets the loop state
+    }
     return k;
 }
 
@@ -1044,11 +1058,12 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
         if (!r && (params[i].dim != params[0].dim || params[i].precision != params[0].precision ||
                    params[i].graph != params[0].graph || params[i].lanes != params[0].lanes ||
                    params[i].stages != params[0].stages || params[i].shifting != params[0].shifting ||
+                   params[i].form != params[0].form ||
                    params[i].steady != params[0].steady || params[i].free_surface != params[0].free_surface ||
                    params[i].moving != params[0].moving || params[i].skin != params[0].skin))
             r = fail(c, DTSPH_E_ARG,
-                     "instances must share dim, precision, graph, lanes, stages, shifting, steady, free_surface, "
-                     "moving and skin");
+                     "instances must share dim, precision, graph, lanes, stages, shifting, form, steady, "
+                     "free_surface, moving and skin");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;

@@ -213,6 +213,7 @@ struct Buffers {
     InstLoop *il;          // [ninst] work counters of the decoupled batch loop (null without it)
     const int *sched;      // [ninst] instances by ascending tile count (the decoupled loop's search order)
     int async_loop;        // 1: batches without walls run the decoupled loop kernel
+    int form_a;            // 1: the loop recomputes the pair geometry from the lists (no pair cache)
     StatRec *stats;        // [kStatRing][ninst]
     uint32_t *err;
 };
@@ -279,6 +280,9 @@ int launch_fill_instance(Inst *inst, Geom *geo, Phys *phys, int i, const Inst &I
                          cudaStream_t st);
 
 int iterate_tiles(const Buffers &B);   // tiles of the iterate kernel (one block each)
+// The loop kernels without the pair cache (iterate_fa.cu; contexts without walls).
+void launch_iterate_fa(const Buffers &B, unsigned long long cond, int use_cond, cudaStream_t st);
+const void *loop_function_fa(const Buffers &B);
 // Row length of the per-slot neighbour lists: K rounded up to 8 entries, so a
 // row starts on a 32-byte boundary.
 __host__ __device__ constexpr int list_stride(int K) { return (K + 7) / 8 * 8; }

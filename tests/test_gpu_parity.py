@@ -781,3 +781,67 @@ def test_step_stats_report_max_velocity(graph):
         vo = np.max(np.sqrt(np.sum(orc.v * orc.v, axis=1)))
         assert abs(st["vmax"] - vo) < 1e-10 * vo
     sim.close()
+
+
+@pytest.mark.parametrize("graph", [0, 1, 2])
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case", ["tgv2d_jitter", "tgv3d"])
+def test_form_without_cache_gives_the_bits_of_the_cache(case, prec, graph):
+    """form = 2 recomputes every pair's geometry in every pseudo-iteration from
+    the lists at r^0, with the operations of the pair-cache pass: the same
+    positions, velocities, pressures and iteration counts, bit for bit, as
+    form = 1 (the cache), for one and four lanes per particle."""
+    d = CASES[case]()
+    nsteps = 4 if case == "tgv2d_jitter" else 2
+    for lanes in (1, 4):
+        out = []
+        for form in (1, 2):
+            sim = make_sim(d, precision=prec, graph=graph, lanes=lanes, form=form)
+            sim.step(nsteps)
+            sim.sync()
+            out.append((sim.x, sim.v, sim.p, [s["iters"] for s in sim.stats()]))
+            sim.close()
+        assert all(np.array_equal(a, b) for a, b in zip(out[0][:3], out[1][:3])), lanes
+        assert out[0][3] == out[1][3], lanes
+
+
+def test_form_without_cache_in_a_batch_and_its_limits():
+    """A batch without walls (the decoupled loop) gives the same bits in both
+    forms; form = 2 is refused with walls (their values come from the cache)
+    and with particles moving in pseudo-time."""
+    work = [synth.tgv2d(37, re=100.0, seed=11), synth.tgv2d(20, re=630.0, seed=12),
+            synth.tgv2d(45, re=250.0, seed=13)]
+    res = []
+    for form in (1, 2):
+        b = dt.Batch([dict(w["cfg"], form=form) for w in work], precision=dt.DTSPH_FP32C, graph=2, lanes=1)
+        b.set_state(work)
+        b.step(3)
+        b.sync()
+        res.append((b.field(dt.FIELD_VEL), [[s["iters"] for s in b.stats(i)] for i in range(len(work))]))
+        b.close()
+    assert all(np.array_equal(a, c) for a, c in zip(res[0][0], res[1][0])) and res[0][1] == res[1][1]
+    cav = CASES["cavity"]()
+    with pytest.raises(dt.DtsphError) as e:
+        make_sim(cav, precision=dt.DTSPH_FP32C, graph=2, form=2)
+    assert e.value.code == dt.DTSPH_E_UNSUPPORTED
+    with pytest.raises(dt.DtsphError) as e:
+        dt.Simulation(CASES["tgv2d_jitter"]()["cfg"], precision=dt.DTSPH_FP32C, moving=1, form=2)
+    assert e.value.code == dt.DTSPH_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_form_without_cache_at_200sq_every_lane_count(prec):
+    """The persistent loop without the cache at 200^2, where there are more
+    tiles than SMs and several blocks share an SM: the bits of the cached form
+    over three steps at 1, 2, 4 and 8 lanes per particle."""
+    d = synth.tgv2d(200)
+    for lanes in (1, 2, 4, 8):
+        out = []
+        for form in (1, 2):
+            sim = make_sim(d, precision=prec, graph=2, lanes=lanes, form=form)
+            sim.step(3)
+            sim.sync()
+            out.append((sim.v, sim.p, [s["iters"] for s in sim.stats()]))
+            sim.close()
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1]), lanes
+        assert out[0][2] == out[1][2], lanes
