@@ -52,7 +52,7 @@ UNIT = "particle-iterations/s"
 # bytes of its own launches. A variant not listed, or one whose kernel changed
 # after its capture, reports null.
 NCU_TRAFFIC = {
-    ("batch-64x-tgv2d", 2, 1, 2): (6.492738e9 + 0.500071e9, 6.667369e9, "profiles/k_loop_async_batch64_tgv2d.md"),
+    ("batch-64x-tgv2d", 2, 1, 2, 1): (6.492738e9 + 0.500071e9, 6.667369e9, "profiles/k_loop_async_batch64_tgv2d.md"),
 }
 
 
@@ -160,6 +160,11 @@ class Job:
             st = self.sim.stats(i, first, count) if self.batch else self.sim.stats(first, count)
             tot += nf * np.array([s["iters"] for s in st], dtype=float)
         return tot
+
+    def forms(self, first, count):
+        """Per real step: the pair-term form its loop ran (1 cache, 2 recomputed)."""
+        st = self.sim.stats(0, first, count) if self.batch else self.sim.stats(first, count)
+        return [s["form"] for s in st]
 
     def iterations(self, first, count):
         its = []
@@ -301,8 +306,8 @@ class ClockSampler:
 def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, kern=None):
     """Times `steps` real steps after `warmup`; L2 flushed before each step.
     Returns (particle-iterations/s, ms per step, iterations, launches, job,
-    (per-step particle-iterations, per-step pseudo-time loop ms) of the last
-    timed steps, at most 256)."""
+    (per-step particle-iterations, per-step pseudo-time loop ms, per-step
+    pair-term form) of the last timed steps, at most 256)."""
     stream = torch.cuda.Stream()
     job = Job(dt, d, precision, stream=stream, graph=graph, kern=kern)
     job.step(warmup)
@@ -324,7 +329,8 @@ def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, kern=No
     rate = float(work.sum()) / (sum(ms) * 1e-3)
     nl = min(steps, 256)
     loop_ms = dt.dtsph_loop_times(job.ctx, dt.dtsph_step_count(job.ctx) - nl, nl)
-    return rate, sum(ms) / steps, iters, launches, job, (work[steps - nl:], loop_ms)
+    forms = job.forms(dt.dtsph_step_count(job.ctx) - nl, nl)
+    return rate, sum(ms) / steps, iters, launches, job, (work[steps - nl:], loop_ms, forms)
 
 
 def run_e2e(dt, torch, d, precision, steps, graph=2, kern=None):
@@ -428,6 +434,18 @@ def linf_rel(v, ref):
 # cached pair the neighbour index, gradW and F_ij, by path and dimension.
 STATE_BYTES = {(2, True): 52.0, (3, True): 72.0, (2, False): 88.0, (3, False): 120.0}
 PAIR_BYTES = {(2, True): 16.0, (3, True): 20.0, (2, False): 28.0, (3, False): 36.0}
+# Without the cache: the same state bytes plus the particle's position at r^0
+# (a 16-byte cell offset on the compensated path, dim doubles in FP64), and per
+# listed pair its 4-byte list entry.
+POS_BYTES = {(2, True): 16.0, (3, True): 16.0, (2, False): 16.0, (3, False): 24.0}
+LIST_BYTES = 4.0
+
+
+def loop_bytes_per_particle_iteration(dims, fp32c, form, pairs_per_particle):
+    """Algorithmic bytes of one particle-iteration of the loop in either form."""
+    if form == 2:
+        return STATE_BYTES[(dims, fp32c)] + POS_BYTES[(dims, fp32c)] + LIST_BYTES * pairs_per_particle
+    return STATE_BYTES[(dims, fp32c)] + PAIR_BYTES[(dims, fp32c)] * pairs_per_particle
 
 
 def fp64_flops(dim):
@@ -508,7 +526,7 @@ def main_ours(args):
         # the FP64 loop is bound by the FP64 pipe: algorithmic FP64 flops of the
         # timed loops over their device time, against the measured FP64 FMA peak
         f_part, f_pair = fp64_flops(dims)
-        w64, lms64 = loop64
+        w64, lms64, _ = loop64
         flops64 = float(np.sum(w64)) * (f_part + f_pair * npairs64 / nf_tot)
         ach64 = flops64 / (sum(lms64) * 1e-3) / 1e12
         fp64 = {"value": rate64 * world, "ms_per_step": ms64, "iters_per_step_mean": float(np.mean(it64)),
@@ -518,15 +536,18 @@ def main_ours(args):
                              "kernel": f"{'k_loop_async' if decoupled else 'k_loop'}<{dims},FP64,lanes={lanes64}>",
                              "flops_per_launch": flops64 / len(lms64), "launch_ms": sum(lms64) / len(lms64),
                              "flops_counted": f"{f_part:.0f} per particle-iteration + {f_pair:.0f} per pair-iteration "
-                                              f"(FMA = 2), {npairs64 / nf_tot:.2f} pairs per particle",
+                                              f"(FMA = 2; the pair terms as the cached form evaluates them, "
+                                              f"whichever form ran), {npairs64 / nf_tot:.2f} pairs per particle",
                              "peak_source": "dtsph_fma_peak(FP64), measured in this run"}}
         sim64.close()
     # the dominant kernel of the timed steps is the pseudo-time loop: its
     # algorithmic bytes per step are the state and cache-entry bytes of one
     # pair pass per particle-iteration of the step
-    loop_work, loop_ms = loop32
-    per_it = STATE_BYTES[(dims, True)] + PAIR_BYTES[(dims, True)] * npairs / nf_tot
-    loop_bytes = per_it * float(np.sum(loop_work))
+    loop_work, loop_ms, loop_forms = loop32
+    ppp = npairs / nf_tot
+    per_it_by_form = {f: loop_bytes_per_particle_iteration(dims, True, f, ppp) for f in (1, 2)}
+    bytes_by_launch = [per_it_by_form[f] * float(w) for w, f in zip(loop_work, loop_forms)]
+    loop_bytes = float(sum(bytes_by_launch))
     achieved = loop_bytes / (sum(loop_ms) * 1e-3) / 1e9
     probe_bytes = STATE_BYTES[(dims, True)] * nf_tot + PAIR_BYTES[(dims, True)] * npairs
     achieved_probe = probe_bytes / (ms_it * 1e-3) / 1e9
@@ -541,9 +562,9 @@ def main_ours(args):
         probe_kernel = f"k_move_walls + k_move_iter<{dims},FP32C> (one lane per particle)"
         loop_kernel = probe_kernel + (" (plain launches)" if args.graph == 0 else
                                       " in the while node (one launch each per iteration)")
-    bytes_by_launch = [per_it * float(w) for w in loop_work]
     traffic, traffic_src, traffic_cap = None, None, None
-    key = (wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0)
+    one_form = loop_forms[0] if len(set(loop_forms)) == 1 else 0
+    key = (wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0, one_form)
     if args.graph == 2 and not args.moving and not args.steady and not args.shifting and key in NCU_TRAFFIC:
         t_bytes, t_alg, t_src = NCU_TRAFFIC[key]
         traffic = t_bytes / t_alg * (loop_bytes / len(loop_ms))
@@ -567,9 +588,13 @@ def main_ours(args):
                      "kernel": loop_kernel,
                      "bytes_per_launch": loop_bytes / len(loop_ms), "launch_ms": sum(loop_ms) / len(loop_ms),
                      "bytes_by_launch": bytes_by_launch,
-                     "bytes_counted": f"{STATE_BYTES[(dims, True)]:.0f} B per particle-iteration + "
-                                      f"{PAIR_BYTES[(dims, True)]:.0f} B per pair-iteration, "
-                                      f"{npairs / nf_tot:.2f} pairs per particle",
+                     "bytes_counted": f"cached form: {STATE_BYTES[(dims, True)]:.0f} B per particle-iteration + "
+                                      f"{PAIR_BYTES[(dims, True)]:.0f} B per pair-iteration; uncached form: "
+                                      f"{STATE_BYTES[(dims, True)] + POS_BYTES[(dims, True)]:.0f} B per "
+                                      f"particle-iteration + {LIST_BYTES:.0f} B per pair-iteration; "
+                                      f"{npairs / nf_tot:.2f} pairs per particle; each launch counted in the form "
+                                      f"it ran",
+                     "forms_by_launch": loop_forms,
                      "timing": f"CUDA events around the loop of each of the last {len(loop_ms)} timed steps",
                      "peak_source": hbm_src},
         "iterate_probe": {"kernel": probe_kernel, "achieved": achieved_probe,
@@ -577,6 +602,9 @@ def main_ours(args):
                           "pairs": npairs, "timing": "50 launches after the timed region, every instance active, "
                                                      "CUDA events"},
         "fma_peaks": fma,
+        "form": dict(dt.dtsph_form_stats(sim32.ctx), requested=args.form,
+                     note="kstar = cache pass / (uncached - cached iteration); a step runs uncached when the "
+                          "latest finished step took at most kstar iterations (form 0)"),
         "autotune": {"lanes_per_particle": lanes32, "stages": stages32, "ms_by_lanes": tune32,
                      "candidates": [{"lanes": L, "stages": S, "ms": m} for L, S, m in cand32]},
         "e2e": e2e,

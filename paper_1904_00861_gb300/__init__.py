@@ -52,7 +52,7 @@ class dtsph_params(C.Structure):
 
 class dtsph_step_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rp", C.c_double), ("rv", C.c_double),
-                ("vmax", C.c_double)]
+                ("vmax", C.c_double), ("form", C.c_int32), ("pad", C.c_int32)]
 
 
 _lib = None
@@ -79,6 +79,8 @@ _SIGS = [
     ("dtsph_get_neighbors", C.c_int, [_VP, C.c_int64, _I64P, C.c_int64, _I64P]),
     ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
     ("dtsph_tuning", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    ("dtsph_form_stats", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64)]),
     ("dtsph_loop_times", C.c_int, [_VP, C.c_int64, C.c_int32, C.POINTER(C.c_float)]),
     ("dtsph_tuning_candidates", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -208,7 +210,7 @@ def dtsph_batch_set_particles(ctx, nf, x, v, p, v_prev=None) -> None:
 def dtsph_batch_read_stats(ctx, inst: int, first: int, count: int):
     buf = (dtsph_step_stats * max(count, 1))()
     _check(ctx, lib().dtsph_batch_read_stats(ctx, int(inst), int(first), int(count), buf))
-    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv, vmax=b.vmax) for b in buf[:count]]
+    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv, vmax=b.vmax, form=b.form) for b in buf[:count]]
 
 
 def dtsph_destroy(ctx) -> None:
@@ -246,7 +248,7 @@ def dtsph_step_count(ctx) -> int:
 def dtsph_read_stats(ctx, first: int, count: int):
     buf = (dtsph_step_stats * max(count, 1))()
     _check(ctx, lib().dtsph_read_stats(ctx, int(first), int(count), buf))
-    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv, vmax=b.vmax) for b in buf[:count]]
+    return [dict(iters=b.iters, reason=b.reason, rp=b.rp, rv=b.rv, vmax=b.vmax, form=b.form) for b in buf[:count]]
 
 
 def dtsph_read_field(ctx, field: int, n: int, comps: int, out=None) -> np.ndarray:
@@ -322,6 +324,16 @@ def dtsph_tuning_candidates(ctx):
     la, st, ms = (C.c_int32 * max(n, 1))(), (C.c_int32 * max(n, 1))(), (C.c_float * max(n, 1))()
     _check(ctx, lib().dtsph_tuning_candidates(ctx, n, la, st, ms, C.byref(cnt), C.byref(s_use)))
     return s_use.value, [(int(la[i]), int(st[i]), float(ms[i])) for i in range(n)]
+
+
+def dtsph_form_stats(ctx):
+    """{"kstar", "ms": [cache pass, cached iteration, uncached iteration],
+    "steps_cache", "steps_nocache"} of the pair-term form (dtsph_params.form)."""
+    k = C.c_double()
+    ms = (C.c_float * 3)()
+    a, b = C.c_int64(), C.c_int64()
+    _check(ctx, lib().dtsph_form_stats(ctx, C.byref(k), ms, C.byref(a), C.byref(b)))
+    return {"kstar": k.value, "ms": [float(m) for m in ms], "steps_cache": a.value, "steps_nocache": b.value}
 
 
 def dtsph_tuning(ctx):
@@ -409,6 +421,9 @@ class Batch:
         count = n - first if count is None else count
         return dtsph_batch_read_stats(self.ctx, inst, first, count)
 
+    def form_stats(self):
+        return dtsph_form_stats(self.ctx)
+
     def field(self, which: int):
         """One array per instance."""
         comps = 1 if which == FIELD_P else self.dim
@@ -458,6 +473,9 @@ class Simulation:
         n = dtsph_step_count(self.ctx)
         count = n - first if count is None else count
         return dtsph_read_stats(self.ctx, first, count)
+
+    def form_stats(self):
+        return dtsph_form_stats(self.ctx)
 
     def field(self, which: int) -> np.ndarray:
         comps = 1 if which == FIELD_P else self.dim

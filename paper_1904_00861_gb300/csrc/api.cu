@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -58,6 +59,17 @@ struct dtsph_ctx {
     static constexpr int kLoopEv = 256;
     std::vector<cudaEvent_t> ev_a, ev_b;
     cudaGraphNode_t node_a = nullptr, node_b = nullptr;
+    // form = 0 with the persistent loop, no walls, frozen particles: the step
+    // graph holds both pair-term forms and chooses one per step on the device
+    // (without the cache when the latest finished step took at most kstar
+    // iterations, the break-even count of the two forms' measured costs); both
+    // give the same bits
+    bool form_graph = false;            // the step graph chooses the form
+    int *form_sel = nullptr;            // device: the current step's form
+    unsigned long long *form_count = nullptr;   // device: steps run in each form
+    double kstar = -1.0;                // < 0: not measured
+    float form_ms[3] = {-1.f, -1.f, -1.f};   // cache pass, cached loop and no-cache loop per iteration
+    int64_t steps_cache = 0, steps_nocache = 0;   // steps of the other paths
     struct TuneRec { int lanes, stages; float ms; };
     std::vector<TuneRec> tune_log;      // candidates timed by the last tuning
 };
@@ -138,6 +150,9 @@ void free_all(dtsph_ctx *c)
     if (c->graph) cudaGraphDestroy(c->graph);
     c->exec = nullptr;
     c->graph = nullptr;
+    c->form_graph = false;
+    c->form_sel = nullptr;
+    c->form_count = nullptr;
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
     c->alloc_bytes = 0;
@@ -334,7 +349,21 @@ bool tune_file_read = false;
 
 const char *tune_file() { return getenv("DTSPH_TUNE_CACHE"); }
 
-// Reads the persisted choices once (tune_mu held).
+// The costs the per-step choice of the pair-term form compares, per shape,
+// lanes and staging depth: the break-even iteration count and the three times
+// it comes from (cache pass; cached and uncached loop per pseudo-iteration, ms).
+struct FormCosts { double kstar; float ms[3]; };
+using FormKey = std::tuple<TuneKey, int, int>;
+std::map<FormKey, FormCosts> &form_cache()
+{
+    static std::map<FormKey, FormCosts> m;
+    return m;
+}
+
+// Reads the persisted choices once (tune_mu held): one record per line,
+// "dtsph-tune-v1 <device> dim precision slots instances loop lanes stages" and
+// "dtsph-form-v1 <device> dim precision slots instances loop lanes stages kstar
+// cache_ms cached_ms uncached_ms"; other lines are skipped.
 void load_tune_file()
 {
     if (tune_file_read) return;
@@ -343,19 +372,32 @@ void load_tune_file()
     if (!path || !*path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char tag[32], dev[160];
-    TuneKey k;
-    long long n = 0;
-    TuneChoice ch;
-    while (fscanf(f, "%31s %159s %d %d %lld %d %d %d %d", tag, dev, &k.dim, &k.prec, &n, &k.ninst, &k.loop, &ch.lanes,
-                  &ch.stages) == 9) {
-        if (strcmp(tag, "dtsph-tune-v1") != 0) continue;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char tag[32], dev[160];
+        TuneKey k;
+        long long n = 0;
+        TuneChoice ch;
+        if (sscanf(line, "%31s %159s %d %d %lld %d %d %d %d", tag, dev, &k.dim, &k.prec, &n, &k.ninst, &k.loop,
+                   &ch.lanes, &ch.stages) != 9)
+            continue;
         const bool ok = (ch.lanes == 1 || ch.lanes == 2 || ch.lanes == 4 || ch.lanes == 8) && ch.stages >= 2 &&
                         ch.stages <= kMaxStages;
         if (!ok) continue;
         k.dev = dev;
         k.n = n;
-        tune_cache()[k] = ch;
+        if (strcmp(tag, "dtsph-tune-v1") == 0) {
+            tune_cache()[k] = ch;
+        } else if (strcmp(tag, "dtsph-form-v1") == 0) {
+            FormCosts fc;
+            char t2[32], d2[160];
+            int i0, i1, i2, i3, i4, i5;
+            long long n2;
+            if (sscanf(line, "%31s %159s %d %d %lld %d %d %d %d %lf %f %f %f", t2, d2, &i0, &i1, &n2, &i2, &i3, &i4,
+                       &i5, &fc.kstar, &fc.ms[0], &fc.ms[1], &fc.ms[2]) == 13 &&
+                std::isfinite(fc.kstar))
+                form_cache()[FormKey{k, ch.lanes, ch.stages}] = fc;
+        }
     }
     fclose(f);
 }
@@ -369,6 +411,18 @@ void save_tune_choice(const TuneKey &k, const TuneChoice &ch)
     if (!f) return;
     fprintf(f, "dtsph-tune-v1 %s %d %d %lld %d %d %d %d\n", k.dev.c_str(), k.dim, k.prec, (long long)k.n, k.ninst,
             k.loop, ch.lanes, ch.stages);
+    fclose(f);
+}
+
+// Appends the form costs of a shape to the persisted file (tune_mu held).
+void save_form_costs(const TuneKey &k, int lanes, int stages, const FormCosts &fc)
+{
+    const char *path = tune_file();
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "dtsph-form-v1 %s %d %d %lld %d %d %d %d %.9g %.9g %.9g %.9g\n", k.dev.c_str(), k.dim, k.prec,
+            (long long)k.n, k.ninst, k.loop, lanes, stages, fc.kstar, fc.ms[0], fc.ms[1], fc.ms[2]);
     fclose(f);
 }
 
@@ -430,6 +484,7 @@ namespace {
 int allocate(dtsph_ctx *c, const int64_t *nf)
 {
     free_all(c);
+    c->kstar = -1.0;                  // the form costs belong to the particle set's shape
     // test hooks: a cap on the context's device memory (to exercise DTSPH_E_OOM)
     // and a shorter give-up time of the persistent loop's grid barrier (to
     // exercise DTSPH_E_TIMEOUT); both unset in normal use
@@ -549,6 +604,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     if (B.async_loop) {
         A(B.il, ni) A(d_sched, ni)
     }
+    A(c->form_sel, 1) A(c->form_count, 2)
 #undef A
     if (wo > 0 && !(B.fp32c ? (const void *)B.wv32 : (const void *)B.wv64)) {
         free_all(c);
@@ -620,6 +676,12 @@ int enqueue_pre_loop(dtsph_ctx *c, cudaStream_t st)
     k += launch_permute_b_to_a(B, st);
     if (B.xk[0]) {
         k += launch_move_prepare(B, st);                          // particles moving in pseudo-time
+    } else if (B.form_sel) {
+        // both forms in the graph: the reset kernel picks the step's form; the
+        // pair-cache pass returns at once when the step recomputes the terms
+        launch_nlist(B, B.xp_a, B.cell_a, B.gid_a, st, false);
+        k += 1 + launch_loop_reset(B, st);
+        k += launch_pair_cache_pass(B, B.xp_a, B.gid_a, st);
     } else if (B.form_a) {
         launch_nlist(B, B.xp_a, B.cell_a, B.gid_a, st, false);   // the loop recomputes the pair terms
         k += 1 + launch_loop_reset(B, st);
@@ -646,40 +708,55 @@ int enqueue_post_loop(dtsph_ctx *c, cudaStream_t st)
 }
 
 // The event-record nodes around the loop in a captured step graph.
-int find_event_nodes(dtsph_ctx *c, cudaGraph_t g)
+int find_event_nodes(dtsph_ctx *c, cudaGraph_t g, cudaGraphNode_t *na, cudaGraphNode_t *nb)
 {
     size_t nn = 0;
     CK(cudaGraphGetNodes(g, nullptr, &nn));
     std::vector<cudaGraphNode_t> nodes(nn);
     CK(cudaGraphGetNodes(g, nodes.data(), &nn));
-    c->node_a = c->node_b = nullptr;
+    *na = *nb = nullptr;
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType t;
         CK(cudaGraphNodeGetType(nd, &t));
         if (t != cudaGraphNodeTypeEventRecord) continue;
         cudaEvent_t ev;
         CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
-        if (ev == c->ev_a[0]) c->node_a = nd;
-        if (ev == c->ev_b[0]) c->node_b = nd;
+        if (ev == c->ev_a[0]) *na = nd;
+        if (ev == c->ev_b[0]) *nb = nd;
     }
-    if (!c->node_a || !c->node_b) return fail(c, DTSPH_E_CUDA, "loop event nodes not found in the step graph");
+    if (!*na || !*nb) return fail(c, DTSPH_E_CUDA, "loop event nodes not found in the step graph");
     return DTSPH_OK;
 }
 
 // Graph of one real step with the persistent loop: pre-loop kernels -> one
-// cooperative loop kernel -> outer.
-int build_graph_persistent(dtsph_ctx *c)
+// cooperative loop kernel -> outer. With the per-step choice of the pair-term
+// form (form_sel) the graph holds the loop kernel of each form; the one of the
+// form the step does not run returns at once.
+int build_graph_persistent(dtsph_ctx *c, cudaGraph_t *g_out, cudaGraphExec_t *x_out, cudaGraphNode_t *na,
+                           cudaGraphNode_t *nb)
 {
-    int grid = 0;
+    int grid = 0, grid_a = 0;
     if (loop_grid(c->B, &grid)) return fail(c, DTSPH_E_CUDA, "occupancy query for the loop kernel failed");
     c->loop_grid = grid;
+    const bool both = c->B.form_sel != nullptr;
+    if (both) {
+        Buffers Ba = c->B;
+        Ba.form_a = 1;
+        if (loop_grid(Ba, &grid_a)) return fail(c, DTSPH_E_CUDA, "occupancy query for the loop kernel failed");
+    }
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
-    c->graph = g;
+    *g_out = g;
     CK(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     c->per_step_fixed = enqueue_pre_loop(c, c->cap);
     cudaError_t e0 = cudaEventRecordWithFlags(c->ev_a[0], c->cap, cudaEventRecordExternal);
     cudaError_t e = launch_loop(c->B, grid, c->cap);
+    if (both && e == cudaSuccess) {
+        Buffers Ba = c->B;
+        Ba.form_a = 1;
+        e = launch_loop(Ba, grid_a, c->cap);
+        c->per_step_fixed += 1;
+    }
     cudaError_t e1 = cudaEventRecordWithFlags(c->ev_b[0], c->cap, cudaEventRecordExternal);
     c->per_step_fixed += 1 + enqueue_post_loop(c, c->cap);
     cudaGraph_t g2 = nullptr;
@@ -689,10 +766,17 @@ int build_graph_persistent(dtsph_ctx *c)
     CK(e1);
     CK(e2);
     c->per_iter = 0;
-    int r = find_event_nodes(c, g);
+    int r = find_event_nodes(c, g, na, nb);
     if (r) return r;
-    CK(cudaGraphInstantiate(&c->exec, g, 0));
+    CK(cudaGraphInstantiate(x_out, g, 0));
     return DTSPH_OK;
+}
+
+// The per-step choice of the pair-term form applies: form = 0, the persistent
+// loop, no walls, particles frozen in pseudo-time.
+bool auto_form(const dtsph_ctx *c)
+{
+    return c->prm[0].form == 0 && c->prm[0].graph == 2 && c->B.nw == 0 && !c->B.xk[0];
 }
 
 // Graph of one real step: pre-loop kernels -> while node (walls, iterate) -> outer.
@@ -700,7 +784,21 @@ int build_graph(dtsph_ctx *c)
 {
     // the persistent loop kernel runs the frozen pass only; moving runs take the
     // while node
-    if (c->prm[0].graph == 2 && !c->B.xk[0]) return build_graph_persistent(c);
+    if (c->prm[0].graph == 2 && !c->B.xk[0]) {
+        // the kernels take Buffers by value: the words of the per-step form
+        // choice are set in the graph's copies only
+        c->form_graph = auto_form(c) && c->kstar >= 0.0;
+        if (c->form_graph) {
+            c->B.form_sel = c->form_sel;
+            c->B.form_count = c->form_count;
+            c->B.kstar = c->kstar;
+        }
+        const int r = build_graph_persistent(c, &c->graph, &c->exec, &c->node_a, &c->node_b);
+        c->B.form_sel = nullptr;
+        c->B.form_count = nullptr;
+        if (r) c->form_graph = false;
+        return r;
+    }
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     c->graph = g;
@@ -731,7 +829,7 @@ int build_graph(dtsph_ctx *c)
     c->per_iter = enqueue_iteration(c, c->cap, (unsigned long long)h, 1);
     cudaGraph_t b2 = nullptr;
     CK(cudaStreamEndCapture(c->cap, &b2));
-    int r = find_event_nodes(c, g);
+    int r = find_event_nodes(c, g, &c->node_a, &c->node_b);
     if (r) return r;
     CK(cudaGraphInstantiate(&c->exec, g, 0));
     return DTSPH_OK;
@@ -911,6 +1009,77 @@ int autotune(dtsph_ctx *c)
     return device_error(c);
 }
 
+// The per-step choice of the pair-term form (form = 0): on lists and a pair
+// cache built at the current positions (binned as a step would; the next step
+// rebuilds every array used here), times the pair-cache pass, which the
+// uncached form leaves out (both build the lists), and one pseudo-iteration of
+// the persistent loop in each form at the context's lanes and staging depth. A
+// step of k iterations costs cache + k * cached against k * uncached, so the
+// uncached form pays up to kstar = cache / (uncached - cached) iterations.
+// Cached per shape in the process and in the persisted file.
+int measure_form_costs(dtsph_ctx *c)
+{
+    Range range("dtsph form costs");
+    Buffers &B = c->B;
+    const TuneKey key = tune_key(c, B.n);
+    {
+        std::lock_guard<std::mutex> g(tune_mu);
+        load_tune_file();
+        auto it = form_cache().find(FormKey{key, B.lanes, B.stages});
+        if (it != form_cache().end()) {
+            c->kstar = it->second.kstar;
+            for (int i = 0; i < 3; ++i) c->form_ms[i] = it->second.ms[i];
+            return DTSPH_OK;
+        }
+    }
+    const size_t nd = (size_t)B.n * B.dim;
+    CK(cudaMemsetAsync(B.vk[0], 0, nd * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(B.s_a, 0, nd * sizeof(double), c->stream));
+    if (B.fp32c) CK(cudaMemsetAsync(B.nb32[0], 0, (size_t)B.n * sizeof(float4), c->stream));
+    else CK(cudaMemsetAsync(B.nb64[0], 0, (size_t)B.n * sizeof(double4_32a), c->stream));
+    c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
+    c->launches += launch_permute_a_to_b(B, c->stream);
+    constexpr int kReps = 5;
+    cudaEvent_t e[2];
+    for (auto &ev : e) CK(cudaEventCreate(&ev));
+    float t_cache = 0;
+    for (int rep = 0; rep <= kReps; ++rep) {          // the first is a warm-up
+        launch_nlist(B, B.x_b, B.cell_b, B.gid_b, c->stream, false);
+        CK(cudaEventRecord(e[0], c->stream));
+        launch_pair_cache_pass(B, B.x_b, B.gid_b, c->stream);   // leaves lists and cache for the loops below
+        CK(cudaEventRecord(e[1], c->stream));
+        c->launches += 2;
+        CK(cudaEventSynchronize(e[1]));
+        float a = 0;
+        CK(cudaEventElapsedTime(&a, e[0], e[1]));
+        if (rep > 0) t_cache += a;
+    }
+    for (auto &ev : e) cudaEventDestroy(ev);
+    const float ms_cache = t_cache / kReps;
+    float ms_b = 0, ms_a = 0;
+    B.form_a = 0;
+    int r = probe_loop_ms(c, 4, 5, &ms_b);
+    if (!r) {
+        B.form_a = 1;
+        r = probe_loop_ms(c, 4, 5, &ms_a);
+        B.form_a = 0;
+    }
+    if (r) return r;
+    FormCosts fc;
+    fc.ms[0] = ms_cache;
+    fc.ms[1] = ms_b;
+    fc.ms[2] = ms_a;
+    fc.kstar = ms_a > ms_b ? (double)ms_cache / (double)(ms_a - ms_b) : 1e9;
+    c->kstar = fc.kstar;
+    for (int i = 0; i < 3; ++i) c->form_ms[i] = fc.ms[i];
+    {
+        std::lock_guard<std::mutex> g(tune_mu);
+        form_cache()[FormKey{key, B.lanes, B.stages}] = fc;
+        save_form_costs(key, B.lanes, B.stages, fc);
+    }
+    return device_error(c);
+}
+
 int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const double *v, const double *p,
                        const double *vprev, bool device)
 {
@@ -974,8 +1143,17 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
     }
     c->have_particles = true;
     c->steps = 0;
+    c->steps_cache = c->steps_nocache = 0;
+    CK(cudaMemsetAsync(c->form_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    CK(cudaMemsetAsync(c->form_sel, 0, sizeof(int), c->stream));
+    // the iteration counts of the latest finished step stay: a new state of the
+    // same shape most often continues the same flow
     if (!c->tuned && c->prm[0].lanes == 0 && !c->B.xk[0]) {
         r = autotune(c);
+        if (r) return r;
+    }
+    if (auto_form(c) && c->kstar < 0) {
+        r = measure_form_costs(c);
         if (r) return r;
     }
     if (c->prm[0].graph && !c->exec) {
@@ -1125,6 +1303,8 @@ int read_stats_impl(dtsph_ctx *c, int32_t inst, int64_t first, int32_t count, dt
         out[i].rp = r.rp;
         out[i].rv = r.rv;
         out[i].vmax = r.vmax;
+        out[i].form = r.form ? 2 : 1;
+        out[i].pad = 0;
     }
     return DTSPH_OK;
 }
@@ -1210,12 +1390,15 @@ int dtsph_step(dtsph_ctx *c, int32_t nsteps)
     for (int32_t s = 0; s < nsteps; ++s) {
         if (c->exec) {
             const int k = (int)(c->steps % dtsph_ctx::kLoopEv);
+            // (the graph of the per-step form choice counts its steps on the device)
+            if (!c->form_graph) ++(c->B.form_a ? c->steps_nocache : c->steps_cache);
             CK(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_a, c->ev_a[k]));
             CK(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_b, c->ev_b[k]));
             CK(cudaGraphLaunch(c->exec, c->stream));
         } else {
             int r = step_plain(c);
             if (r) return r;
+            ++(c->B.form_a ? c->steps_nocache : c->steps_cache);
         }
         ++c->steps;
     }
@@ -1409,6 +1592,29 @@ int dtsph_probe_iterate(dtsph_ctx *c, int32_t launches, float *ms_per_launch, do
     if (r) return r;
     if (bytes_per_launch) *bytes_per_launch = bytes;
     if (pairs) *pairs = np;
+    return DTSPH_OK;
+}
+
+int dtsph_form_stats(const dtsph_ctx *c, double *kstar, float *ms, int64_t *steps_cache, int64_t *steps_nocache)
+{
+    if (!c) return DTSPH_E_ARG;
+    if (kstar) *kstar = c->kstar;
+    if (ms)
+        for (int i = 0; i < 3; ++i) ms[i] = c->form_ms[i];
+    int64_t a = c->steps_cache, b = c->steps_nocache;
+    if (c->form_graph) {
+        // the step graph counts its choices on the device
+        unsigned long long n[2] = {0ull, 0ull};
+        if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess ||
+            cudaMemcpy(n, c->form_count, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return DTSPH_E_CUDA;
+        }
+        a = (int64_t)n[0];
+        b = (int64_t)n[1];
+    }
+    if (steps_cache) *steps_cache = a;
+    if (steps_nocache) *steps_nocache = b;
     return DTSPH_OK;
 }
 

@@ -113,7 +113,7 @@ struct LoopState {
     int done;              // 1 once a stop rule holds
     int reason;            // stop reason (dtsph_step_stats.reason), -1 while running
     unsigned int ticket;   // last-block election counter of the instance's tiles
-    unsigned int bar;      // unused
+    int last_iters;        // iterations of the latest finished real step (0: none since allocation)
     int pad0;
     double rp, rv;         // residuals of the last iteration
     double hist_p[16], hist_v[16];   // ring of the last residuals (stagnation test)
@@ -144,6 +144,7 @@ struct StatRec {
     int iters, reason;
     double rp, rv;
     double vmax;           // max |V^{n+1}| over the instance's fluid particles (before shifting)
+    int form, pad;         // 1: the step's loop ran without the pair cache
 };
 constexpr int kStatRing = 65536;   // real steps kept per instance
 
@@ -214,6 +215,13 @@ struct Buffers {
     const int *sched;      // [ninst] instances by ascending tile count (the decoupled loop's search order)
     int async_loop;        // 1: batches without walls run the decoupled loop kernel
     int form_a;            // 1: the loop recomputes the pair geometry from the lists (no pair cache)
+    // the per-step choice of the pair-term form (form = 0), in the step graph
+    // only (null elsewhere): k_loop_reset writes the step's form to *form_sel
+    // (0 cache, 1 recomputed) and counts it in form_count[form]; the kernels of
+    // the other form return at once
+    int *form_sel;
+    unsigned long long *form_count;
+    double kstar;          // the uncached form runs when the latest step took at most kstar iterations
     StatRec *stats;        // [kStatRing][ninst]
     uint32_t *err;
 };
@@ -245,6 +253,7 @@ int launch_permute_b_to_a(const Buffers &B, cudaStream_t st);
 void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st,
                   bool sliced);
 int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st);
+int launch_pair_cache_pass(const Buffers &B, const double *xpos, const uint32_t *gid, cudaStream_t st);
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
 int launch_walls_iter(const Buffers &B, cudaStream_t st);
 int launch_iterate(const Buffers &B, unsigned long long cond_handle, int use_cond, cudaStream_t st);

@@ -822,6 +822,9 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2 && !WA
     __shared__ Geom G;
     __shared__ int stop, ok_sh, p_inst;
     __shared__ int act_pre[kDealMaxInst + 1];
+    if constexpr (!WALLS) {
+        if (skip_form(B, FA)) return;     // the step runs the other pair-term form
+    }
     const int ntiles = (B.n + PPB - 1) / PPB;
     const bool single = B.ninst == 1;
     const bool deal = !single && B.ninst <= kDealMaxInst;
@@ -981,6 +984,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2) ? 4 :
     __shared__ Geom G;
     __shared__ int p_inst, w_inst, w_tile, w_it, last_sh, quit;
     __shared__ int mins[kBlock / kWarp];
+    if (skip_form(B, FA)) return;     // the step runs the other pair-term form
     const int ntiles = (B.n + PPB - 1) / PPB;
     const int ni = B.ninst;
     if (threadIdx.x == 0) p_inst = -1;
@@ -1113,6 +1117,8 @@ __global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
             rec->reason = ls->reason;
             rec->rp = ls->rp;
             rec->rv = ls->rv;
+            rec->form = B.form_sel ? *B.form_sel : B.form_a;
+            ls->last_iters = K;
             ls->step = ls->step + 1;
         }
         if (fluid) {
@@ -1159,7 +1165,43 @@ __global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
         atomicMax((unsigned long long *)&rec->vmax, bits);
 }
 
-__global__ void k_loop_reset(Buffers B) { reset_loops(B); }
+// The pair-term form of the step (form = 0, in the step graph): without the
+// cache when the latest finished step's iterations, averaged over the
+// instances with their fluid counts as weights, are at most kstar (an
+// instance with no finished step since the allocation counts one iteration).
+// Sums in a fixed order; one block.
+__device__ void select_form(const Buffers &B)
+{
+    __shared__ double kw[kBlock], w[kBlock];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
+        const double nf = (double)B.inst[i].nf;
+        const int k = B.ls[i].last_iters;
+        a = __fma_rn(nf, (double)(k > 0 ? k : 1), a);
+        b = __dadd_rn(b, nf);
+    }
+    kw[threadIdx.x] = a;
+    w[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            kw[threadIdx.x] = __dadd_rn(kw[threadIdx.x], kw[threadIdx.x + h]);
+            w[threadIdx.x] = __dadd_rn(w[threadIdx.x], w[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int f = kw[0] <= B.kstar * w[0] ? 1 : 0;
+        *B.form_sel = f;
+        B.form_count[f] += 1ull;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_loop_reset(Buffers B)
+{
+    if (B.form_sel) select_form(B);
+    reset_loops(B);
+}
 
 template <int D, bool F, bool W, int L, bool FA = false>
 const void *loop_kernel() { return (const void *)k_loop<D, F, W, L, FA>; }

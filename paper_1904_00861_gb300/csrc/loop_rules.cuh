@@ -114,6 +114,14 @@ __device__ __forceinline__ void reset_loops(const Buffers &B)
     }
 }
 
+// In a step graph that holds both pair-term forms (form = 0): true in the
+// kernels of the form the step does not run (fa: the kernel recomputes the
+// pair terms). Block-uniform, so a kernel may return before any barrier.
+__device__ __forceinline__ bool skip_form(const Buffers &B, bool fa)
+{
+    return B.form_sel && *(volatile const int *)B.form_sel != (fa ? 1 : 0);
+}
+
 // First tile and end tile of instance i for tiles of ppb slots.
 __device__ __forceinline__ void instance_tiles(const Inst &I, int ppb, int &lo, int &hi)
 {

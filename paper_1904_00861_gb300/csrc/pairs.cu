@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
     constexpr int SPB = kBlock / L;
     __shared__ Geom G;
     __shared__ Phys P;
+    if (skip_form(B, false)) return;     // the step recomputes the pair terms
     if (blockIdx.x == 0) {
         reset_loops(B);
     }
@@ -447,13 +448,18 @@ int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st)
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st)
 {
     launch_nlist(B, xpos, cell, gid, st, false);
+    return 1 + launch_pair_cache_pass(B, xpos, gid, st);
+}
+
+int launch_pair_cache_pass(const Buffers &B, const double *xpos, const uint32_t *gid, cudaStream_t st)
+{
     const int L = nlist_lanes(B.n);
     const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
     if (L == 1) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 1><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     else if (L == 2) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 2><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     else if (L == 4) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 4><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     else DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 8><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
-    return 2;
+    return 1;
 }
 
 int launch_shift(const Buffers &B, cudaStream_t st)

@@ -54,11 +54,23 @@ def test_algorithmic_bytes_and_flops_follow_the_pair_cache_form():
     assert bench.fp64_flops(2) == (19.0, 25.0) and bench.fp64_flops(3) == (27.0, 33.0)
 
 
+def test_algorithmic_bytes_without_the_cache():
+    """The uncached form reads the particle's position at r^0 (16 B cell offset
+    on the compensated path, dim doubles in FP64) and one 4-byte list entry per
+    pair instead of a cache entry; the cached form's figure is unchanged."""
+    f = bench.loop_bytes_per_particle_iteration
+    assert f(2, True, 2, 27.3) == pytest.approx(52 + 16 + 4 * 27.3)
+    assert f(3, True, 2, 112) == pytest.approx(72 + 16 + 4 * 112)
+    assert f(3, False, 2, 112) == pytest.approx(120 + 24 + 4 * 112)
+    assert f(2, True, 1, 27.3) == pytest.approx(488.8)
+
+
 def test_traffic_figures_come_from_committed_profiles():
     """Every DRAM traffic figure bench.py uses comes from a committed profile
     summary that states the captured launch's DRAM bytes and its algorithmic
     bytes, the two numbers the line's traffic is scaled by."""
-    for (workload, dim, lanes, stages), (byts, alg, src) in bench.NCU_TRAFFIC.items():
+    for (workload, dim, lanes, stages, form), (byts, alg, src) in bench.NCU_TRAFFIC.items():
+        assert form in (1, 2)
         path = os.path.join(ROOT, src)
         assert os.path.exists(path), path
         txt = open(path).read()

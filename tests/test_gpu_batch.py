@@ -31,6 +31,12 @@ def instances():
     ]
 
 
+def numbers(stats):
+    """The step records without the pair-term form each step ran (both forms
+    give the same bits; which one ran depends on measured timings)."""
+    return [{k: v for k, v in s.items() if k != "form"} for s in stats]
+
+
 def solo(d, prec, graph, nsteps, lanes=2, **over):
     sim = dt.Simulation(d["cfg"], precision=prec, graph=graph, lanes=lanes, **over)
     nf = d["nf"]
@@ -57,7 +63,7 @@ def test_batch_equals_solo_runs(prec, graph, lanes):
     for i, d in enumerate(insts):
         x, v, p, st = solo(d, prec, graph, nsteps, lanes)
         assert np.array_equal(xs[i], x) and np.array_equal(vs[i], v) and np.array_equal(ps[i], p), i
-        assert b.stats(i) == st, i
+        assert numbers(b.stats(i)) == numbers(st), i
         iters.append([s["iters"] for s in st])
     # the instances really ran different numbers of iterations
     assert len({tuple(t) for t in iters}) > 1
@@ -164,10 +170,10 @@ def test_decoupled_loop_equals_lockstep_loop_and_solo_runs(monkeypatch, prec, la
     for i, d in enumerate(insts):
         for k in range(3):
             assert np.array_equal(dec[k][i], lock[k][i]), (i, k)
-        assert dec[3][i] == lock[3][i], i
+        assert numbers(dec[3][i]) == numbers(lock[3][i]), i
         x, v, p, st = solo(d, prec, 2, nsteps, lanes)
         assert np.array_equal(dec[0][i], x) and np.array_equal(dec[1][i], v) and np.array_equal(dec[2][i], p), i
-        assert dec[3][i] == st, i
+        assert numbers(dec[3][i]) == numbers(st), i
         iters.append([s["iters"] for s in st])
     # the instances really iterate unevenly (the decoupled loop's case)
     assert len({tuple(t) for t in iters}) > 1

@@ -127,10 +127,12 @@ def test_allocation_cap_gives_oom(monkeypatch):
 def test_grid_barrier_give_up_is_reported(monkeypatch, prec):
     """A give-up time of zero: the first block to reach a grid barrier stops
     waiting at once, so the step's persistent loop ends early; dtsph_sync says
-    DTSPH_E_TIMEOUT, and a new context without the setting runs normally."""
+    DTSPH_E_TIMEOUT, and a new context without the setting runs normally.
+    (form = 1: the automatic form would time the loop at dtsph_set_particles,
+    where the give-up would already be reported.)"""
     d = synth.tgv2d(100, seed=4)
     monkeypatch.setenv("DTSPH_TEST_BARRIER_WAIT_NS", "0")
-    sim = sim_of(d, prec, graph=2, lanes=1)
+    sim = sim_of(d, prec, graph=2, lanes=1, form=1)
     sim.step(1)
     with pytest.raises(dt.DtsphError) as e:
         sim.sync()

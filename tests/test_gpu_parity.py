@@ -308,7 +308,7 @@ def test_staging_depth_does_not_change_the_bits(prec):
     for stages in (2, 3, 5, 8):
         sim = make_sim(d, precision=prec, graph=2, lanes=1, stages=stages)
         sim.step(2)
-        got = (sim.v, sim.p, sim.x, sim.stats())
+        got = (sim.v, sim.p, sim.x, [{k: v for k, v in r.items() if k != "form"} for r in sim.stats()])
         sim.close()
         if ref is None:
             ref = got
@@ -400,7 +400,9 @@ def test_persistent_loop_is_bit_identical(case, nsteps, prec, lanes):
     b.step(nsteps)
     b.sync()
     assert np.array_equal(a.v, b.v) and np.array_equal(a.p, b.p) and np.array_equal(a.x, b.x)
-    assert a.stats() == b.stats()
+    # the persistent loop picks the pair-term form per step (same bits)
+    drop = lambda st: [{k: v for k, v in r.items() if k != "form"} for r in st]
+    assert drop(a.stats()) == drop(b.stats())
     a.close()
     b.close()
 
@@ -845,3 +847,127 @@ def test_form_without_cache_at_200sq_every_lane_count(prec):
             sim.close()
         assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1]), lanes
         assert out[0][2] == out[1][2], lanes
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_automatic_form_gives_the_bits_and_reports_its_choice(prec):
+    """form = 0 on the persistent loop measures the cache pass and one
+    pseudo-iteration in each form at dtsph_set_particles, then picks the form
+    of each step on the device from the previous step's iteration count: the bits of
+    form = 1 whatever it picks, k* = cache / (uncached - cached), and every step
+    counted in one of the two forms."""
+    d = CASES["tgv2d_jitter"]()
+    out = []
+    for form in (1, 0):
+        sim = make_sim(d, precision=prec, graph=2, lanes=1, form=form)
+        sim.step(5)
+        sim.sync()
+        st = sim.stats()
+        out.append((sim.x, sim.v, sim.p, [s["iters"] for s in st], sim.form_stats(), [s["form"] for s in st]))
+        sim.close()
+    assert all(np.array_equal(a, b) for a, b in zip(out[0][:3], out[1][:3]))
+    assert out[0][3] == out[1][3] and out[0][5] == [1] * 5
+    fixed, auto = out[0][4], out[1][4]
+    assert fixed["kstar"] < 0 and fixed["steps_cache"] == 5 and fixed["steps_nocache"] == 0
+    ms = auto["ms"]
+    assert ms[0] >= 0 and ms[1] > 0 and ms[2] > 0
+    want = ms[0] / (ms[2] - ms[1]) if ms[2] > ms[1] else 1e9
+    assert auto["kstar"] == pytest.approx(want, rel=1e-5)
+    assert auto["steps_cache"] + auto["steps_nocache"] == 5
+    assert out[1][5].count(2) == auto["steps_nocache"]
+    # a form = 2 context reports every step uncached
+    sim = make_sim(d, precision=prec, graph=2, lanes=1, form=2)
+    sim.step(2)
+    assert [s["form"] for s in sim.stats()] == [2, 2] and sim.form_stats()["steps_nocache"] == 2
+    sim.close()
+
+
+def form_rule(iters, nfs, kstar):
+    """The form each step of a form = 0 run takes: 2 (no cache) when the
+    previous step's iterations, averaged over the instances with their fluid
+    counts as weights, are at most kstar; an instance with no step yet counts
+    one iteration."""
+    prev = [1] * len(nfs)
+    forms = []
+    for k in range(len(iters[0])):
+        kw = float(sum(nf * p for nf, p in zip(nfs, prev)))
+        forms.append(2 if kw <= kstar * float(sum(nfs)) else 1)
+        prev = [its[k] for its in iters]
+    return forms
+
+
+def test_automatic_form_follows_the_iteration_count(tmp_path):
+    """The per-step choice follows the rule exactly, in a solo context and in a
+    batch, for thresholds below, between and above the iteration counts: the
+    measured costs persist in DTSPH_TUNE_CACHE, a fresh process reads the
+    threshold from there, so the test sets kstar by editing the file. The bits
+    do not depend on the choice."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import json, numpy as np, synth, paper_1904_00861_gb300 as dt\n"
+            "out = {}\n"
+            "d = synth.tgv2d(41, seed=5)\n"
+            "s = dt.Simulation(d['cfg'], precision=dt.DTSPH_FP32C, graph=2, lanes=1, stages=2)\n"
+            "s.set_state(d['x'], d['v'], d['p'], d['v_prev'])\n"
+            "s.step(6)\n"
+            "st = s.stats()\n"
+            "out['solo'] = dict(iters=[[r['iters'] for r in st]], forms=[r['form'] for r in st], nfs=[d['nf']],\n"
+            "                   fs=s.form_stats(), v=float(np.sum(np.abs(s.v))))\n"
+            "w = [synth.tgv2d(29, re=100.0, seed=21), synth.tgv2d(17, re=630.0, seed=22),\n"
+            "     synth.tgv2d(33, re=250.0, seed=23)]\n"
+            "b = dt.Batch([x['cfg'] for x in w], precision=dt.DTSPH_FP32C, graph=2, lanes=1, stages=2)\n"
+            "b.set_state(w)\n"
+            "b.step(6)\n"
+            "out['batch'] = dict(iters=[[r['iters'] for r in b.stats(i)] for i in range(3)],\n"
+            "                    forms=[r['form'] for r in b.stats(0)], nfs=[x['nf'] for x in w], fs=b.form_stats(),\n"
+            "                    v=float(sum(np.sum(np.abs(v)) for v in b.field(dt.FIELD_VEL))))\n"
+            "print(json.dumps(out))\n")
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, DTSPH_TUNE_CACHE=str(path))
+    run = lambda: json.loads(subprocess.run([sys.executable, "-c", code], cwd=root, env=env, check=True,
+                                            capture_output=True, text=True).stdout.strip().splitlines()[-1])
+    first = run()
+    lines = [ln.split() for ln in path.read_text().splitlines() if ln.startswith("dtsph-form-v1 ")]
+    assert len(lines) == 2
+    for name in ("solo", "batch"):
+        r = first[name]
+        assert r["forms"] == form_rule(r["iters"], r["nfs"], r["fs"]["kstar"]), name
+        assert r["fs"]["steps_nocache"] == r["forms"].count(2) and r["fs"]["steps_cache"] == r["forms"].count(1)
+    # thresholds that put every step in one form, and one between the counts
+    allk = sorted({k for name in ("solo", "batch") for its in first[name]["iters"] for k in its})
+    mid = 0.5 * (allk[0] + allk[-1])
+    seen = set()
+    for kstar in (0.5, mid, 1e6):
+        path.write_text("".join(" ".join(ln[:9] + [repr(kstar)] + ln[10:]) + "\n" for ln in lines))
+        got = run()
+        for name in ("solo", "batch"):
+            r = got[name]
+            assert r["fs"]["kstar"] == kstar
+            assert r["iters"] == first[name]["iters"] and r["v"] == first[name]["v"], (name, kstar)
+            assert r["forms"] == form_rule(r["iters"], r["nfs"], kstar), (name, kstar)
+            seen.update(r["forms"])
+        if kstar == 0.5:
+            assert got["solo"]["forms"] == [1] * 6 and got["batch"]["forms"] == [1] * 6
+        if kstar == 1e6:
+            assert got["solo"]["forms"] == [2] * 6 and got["batch"]["forms"] == [2] * 6
+    assert seen == {1, 2}
+
+
+def test_automatic_form_counts_restart_with_the_state():
+    """A second set_particles of the same shape keeps k* (no new measurement)
+    and restarts the per-form step counts."""
+    d = CASES["tgv2d_jitter"]()
+    sim = make_sim(d, precision=dt.DTSPH_FP32C, graph=2, lanes=1, form=0)
+    sim.step(3)
+    fs = sim.form_stats()
+    assert fs["steps_cache"] + fs["steps_nocache"] == 3 and fs["kstar"] > 0
+    sim.set_state(d["x"][:d["nf"]], d["v"], d["p"], d["v_prev"])
+    fs2 = sim.form_stats()
+    assert fs2["steps_cache"] == 0 and fs2["steps_nocache"] == 0 and fs2["kstar"] == fs["kstar"]
+    sim.step(2)
+    fs3 = sim.form_stats()
+    assert fs3["steps_cache"] + fs3["steps_nocache"] == 2
+    sim.close()
