@@ -496,7 +496,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     Buffers &B = c->B;
     const int ni = c->ninst;
     c->I.assign(ni, Inst{});
-    int64_t slot = 0, fo = 0, wo = 0, co = 0;
+    int64_t slot = 0, fo = 0, wo = 0, co = 0, so = 0;
     int K = 0;
     for (int i = 0; i < ni; ++i) {
         if (nf[i] <= 0) return fail(c, DTSPH_E_ARG, "instance %d: nf must be positive", i);
@@ -509,11 +509,13 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         I.foff = (int)fo;
         I.woff = (int)wo;
         I.cell_off = (int)co;
+        I.seg_off = (int)so;
         I.shift = (int)(slot - (fo + wo));
         slot += nf[i] + nw;
         fo += nf[i];
         wo += nw;
         co += c->G[i].ncell + 1;   // one empty sentinel cell per instance
+        so += (int64_t)((c->G[i].nc[0] + kSeg2 - 1) / kSeg2) * c->G[i].nc[1] * c->G[i].nc[2];
         K = std::max(K, dtsph::neighbour_capacity(c->prm[i]));
         if (slot >= kMaxSlots - 4 * kSlotAlign || co >= (1LL << 31) - 2)
             return fail(c, DTSPH_E_ARG, "particle or cell count out of range (at most %lld slots in a context)",
@@ -531,6 +533,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     B.K = K;
     B.ninst = ni;
     B.ncell = (int)co;
+    B.nseg2 = (int)so;
     B.barrier_ns = env_u64("DTSPH_TEST_BARRIER_WAIT_NS", kBarrierWaitNs);
     {
         const TuneChoice ch = kernel_choice(c, n);

@@ -49,6 +49,8 @@ constexpr unsigned long long kBarrierWaitNs = 1000000000ull;   // grid-barrier g
 // the tiles in the static order.
 constexpr int kDealMaxInst = 1024;
 
+constexpr int kSeg2 = 3;   // cells along x in one row segment of the 2D FP32C list builder
+
 struct Inst {
     int slot_off;          // first slot
     int nf, nw;            // fluid and wall particles
@@ -56,7 +58,7 @@ struct Inst {
     int cell_off;          // first cell; the instance owns ncell + 1 cells, the last one
                            // always empty so that its start marks the end of the range
     int shift;             // slot_off minus the particles of the instances before it
-    int pad_;
+    int seg_off;           // first row segment of the 2D FP32C list builder (kSeg2 cells along x)
 };
 
 // Cell grid and neighbour-test constants of one binning. Cells have side
@@ -154,6 +156,7 @@ constexpr int kStatRing = 65536;   // real steps kept per instance
 struct Buffers {
     int n;                          // slots (all instances, padding included)
     int nf, nw;                     // fluid and wall particles of all instances
+    int nseg2;                      // row segments of the 2D FP32C list builder, all instances
     int dim, fp32c, K;              // K = neighbour capacity per particle
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
     int stages;                     // pair-cache chunks in flight per warp (lanes = 1), 2..kMaxStages

@@ -26,6 +26,18 @@ namespace {
 
 constexpr int kWarpsPerBlock = kBlock / kWarp;
 
+// Global row segment g -> its instance (segments of instance i start at inst[i].seg_off).
+__device__ __forceinline__ int segment_instance(const Buffers &B, int g)
+{
+    int lo = 0, hi = B.ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.inst[mid].seg_off <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Global cell c -> its instance (cells of instance i start at inst[i].cell_off).
 __device__ __forceinline__ int cell_instance(const Buffers &B, int c)
 {
@@ -402,6 +414,194 @@ __global__ void __launch_bounds__(kBlock) k_nlist_cells3_f32(Buffers B, const do
     }
 }
 
+// 2D lists on the FP32C path, one warp per row segment of up to kSeg2 cells along
+// x (a 2D cell holds about 9 particles, so three cells fill most of the lanes) with
+// the segment's particles in the lanes, as the 3D builder does for one cell. The
+// warp stages the candidates of the 3 x (segment + 2) surrounding cells in the
+// order rows (dy), then column, then slot, moved into the frame of the segment's
+// first cell; each lane tests them four at a time against its particle, keeps
+// those of the three columns around its own cell, and appends its hits through an
+// eight-entry buffer as whole sectors of its list. For every particle the
+// candidates of its own 3 x 3 cells come in the order rows, dx, slot, so its list
+// holds the entries of k_nlist_cells in the same order; outside the band around
+// the cutoff this FP32 separation decides as the canonical one does, and the FP64
+// test decides inside it.
+constexpr int kRowsMinSegments = 16384;
+
+__global__ void __launch_bounds__(kBlock) k_nlist_rows2_f32(Buffers B, const double *__restrict__ xpos,
+                                                            uint32_t *__restrict__ lists, int Ks)
+{
+    constexpr int NCOL = kSeg2 + 2;                     // candidate columns
+    constexpr int NT = 3 * NCOL;                        // candidate cells
+    constexpr int CH = 256;
+    __shared__ float4 cand[kWarpsPerBlock][CH];
+    __shared__ __align__(16) uint32_t buf[kWarpsPerBlock][kWarp][kBufEntries];
+    __shared__ int tpre[kWarpsPerBlock][NT + 1];
+    __shared__ int tbeg[kWarpsPerBlock][NT];
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & (kWarp - 1), w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int g = blockIdx.x * kWarpsPerBlock + w;     // global row segment of this warp
+    if (g >= B.nseg2) return;
+    const int inst = segment_instance(B, g);
+    const int cell_off = B.inst[inst].cell_off;
+    const Geom &G = B.geo[inst];
+    const int nx = G.nc[0], ny = G.nc[1];
+    const int nsx = (nx + kSeg2 - 1) / kSeg2;           // segments per row
+    const int ls = g - B.inst[inst].seg_off;
+    const int cx = (ls % nsx) * kSeg2, cy = ls / nsx;
+    const int lc = cy * nx + cx;
+    const int ns = min(kSeg2, nx - cx);                 // cells of this segment
+    const int *start = B.cell_start + cell_off;
+    const int hb = start[lc], he = start[lc + ns];
+    if (hb == he) return;
+    // first slots of the segment's second and third cells
+    const int b1 = ns > 1 ? start[lc + 1] : he, b2 = ns > 2 ? start[lc + 2] : he;
+    const float sf[2] = {G.s_f[0], G.s_f[1]};
+    const float rc2_lo = G.rc2_lo, rc2_hi = G.rc2_hi;
+    const double rc2 = G.rc2;
+    const float box_cut2 = rc2_hi * 1.001f;
+    const float seg_w = (float)ns * sf[0];
+    const int n = B.n, K = B.K;
+    // the candidate cells side by side: lane t takes row t / NCOL (dy + 1) and
+    // column t % NCOL (x = cx - 1 + column); empty when off a closed edge or past
+    // the segment's last column
+    int m = 0;
+    if (lane < NT) {
+        const int r = lane / NCOL, k = lane % NCOL;
+        int x = cx - 1 + k, y = cy + r - 1;
+        bool ok = k < ns + 2;
+        if (ok && (x < 0 || x >= nx)) { if (G.periodic[0]) x = x < 0 ? x + nx : x - nx; else ok = false; }
+        if (ok && (y < 0 || y >= ny)) { if (G.periodic[1]) y = y < 0 ? y + ny : y - ny; else ok = false; }
+        if (ok) {
+            const int nc = y * nx + x;
+            const int jb = start[nc];
+            m = start[nc + 1] - jb;
+            tbeg[w][lane] = jb;
+        } else {
+            tbeg[w][lane] = 0;
+        }
+    }
+    int incl = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane < NT) tpre[w][lane] = incl - m;
+    const int total = __shfl_sync(full, incl, NT - 1);
+    if (lane == NT) tpre[w][NT] = total;
+    __syncwarp();
+    uint32_t *my = buf[w][lane];
+    for (int h0 = hb; h0 < he; h0 += kWarp) {
+        const int s = h0 + lane;
+        const bool act = s < he;
+        const int kh = (s >= b1) + (s >= b2);           // the lane's cell in the segment
+        // an idle lane tests from far away: it fails every distance test
+        float4 oi = make_float4(3e18f, 3e18f, 0.f, 0.f);
+        if (act) {
+            oi = B.off[s];
+            oi.x = __fadd_rn(oi.x, (float)kh * sf[0]);
+        }
+        uint32_t *out = lists + (size_t)s * Ks;
+        int cnt = 0;
+        int t = 0;
+        for (int c0 = 0; c0 < total; c0 += CH) {
+            const int span = min(total - c0, CH);
+            int take = 0;
+            for (int q0 = 0; q0 < span; q0 += kWarp) {
+                const int q = q0 + lane;
+                bool keep = false;
+                float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < span) {
+                    const int p = c0 + q;
+                    while (tpre[w][t + 1] <= p) ++t;
+                    const int j = tbeg[w][t] + (p - tpre[w][t]);
+                    const float4 oj = B.off[j];
+                    const int r = t / NCOL, k = t % NCOL;
+                    e.x = __fadd_rn(oj.x, (float)(k - 1) * sf[0]);
+                    e.y = __fadd_rn(oj.y, (float)(r - 1) * sf[1]);
+                    // column + 1, and the row's part of the shift code (dx + 1) + 3 (dy + 1) + 9
+                    e.z = __int_as_float(k | ((3 * r + 9) << 8));
+                    e.w = __uint_as_float((uint32_t)j | (oj.w != 0.f ? kWallBit : 0u));
+                    const float bx = fmaxf(fmaxf(-e.x, e.x - seg_w), 0.f);
+                    const float by = fmaxf(fmaxf(-e.y, e.y - sf[1]), 0.f);
+                    keep = bx * bx + by * by < box_cut2;
+                }
+                const unsigned bal = __ballot_sync(full, keep);
+                if (keep) cand[w][take + __popc(bal & lt)] = e;
+                take += __popc(bal);
+            }
+            // pad to a multiple of four with entries that fail every test
+            const int take4 = (take + 3) & ~3;
+            if (take + lane < take4)
+                cand[w][take + lane] = make_float4(-3e18f, -3e18f, __int_as_float(0x7f), __uint_as_float(kNoParticle));
+            __syncwarp();
+            // the tests set one bit per hit (candidate q0 + b: bit b), without
+            // branches; the hits then join the list in candidate order
+            for (int q0 = 0; q0 < take4; q0 += kWarp) {
+                const int qn = min(kWarp, take4 - q0);
+                uint32_t hit = 0u;
+                for (int q = 0; q < qn; q += 4) {
+                    bool band[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 e = cand[w][q0 + q + u];
+                        const int z = __float_as_int(e.z);
+                        const uint32_t dxp = (uint32_t)((z & 0xff) - kh);   // dx + 1 from the lane's cell
+                        const float d0 = __fsub_rn(oi.x, e.x), d1 = __fsub_rn(oi.y, e.y);
+                        const float q2 = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
+                        const bool other = (__float_as_uint(e.w) & kSlotMask) != (uint32_t)s && dxp <= 2u;
+                        hit |= (uint32_t)(q2 < rc2_lo && other) << (q + u);
+                        band[u] = q2 >= rc2_lo && q2 < rc2_hi && other;
+                    }
+                    // the FP64 decision inside the band (rare)
+                    if (__any_sync(full, band[0] || band[1] || band[2] || band[3])) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (band[u]) {
+                                const uint32_t j = __float_as_uint(cand[w][q0 + q + u].w) & kSlotMask;
+                                double d64[3];
+                                if (sep64<2>(G, xpos, n, s, (int)j, d64) < rc2) hit |= 1u << (q + u);
+                            }
+                        }
+                    }
+                }
+                while (hit) {
+                    const int b = __ffs(hit) - 1;
+                    hit &= hit - 1u;
+                    const float4 e = cand[w][q0 + b];
+                    const int z = __float_as_int(e.z);
+                    const uint32_t dxp = (uint32_t)((z & 0xff) - kh);
+                    my[cnt & (kBufEntries - 1)] = __float_as_uint(e.w) | ((dxp + (uint32_t)(z >> 8)) << kCodeShift);
+                    ++cnt;
+                    // a full buffer goes out as one aligned sector of the list
+                    if ((cnt & (kBufEntries - 1)) == 0 && cnt <= K) {
+                        const uint4 a = *reinterpret_cast<const uint4 *>(my);
+                        const uint4 c4 = *reinterpret_cast<const uint4 *>(my + 4);
+                        uint4 *dst = reinterpret_cast<uint4 *>(out + (cnt - kBufEntries));
+                        dst[0] = a;
+                        dst[1] = c4;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (act) {
+            // the entries since the last full buffer
+            const int tail = cnt & (kBufEntries - 1);
+            for (int k = 0; k < tail; ++k)
+                if (cnt - tail + k < K) out[cnt - tail + k] = my[k];
+            if (cnt > K) {
+                atomicOr(B.err, kErrCapacity);
+                cnt = K;
+            }
+            B.pcount[s] = cnt;
+        }
+        __syncwarp();
+    }
+}
+
 // The per-slot lists (slot s at s Ks + k) into the sliced layout, one warp per 32
 // slots: 32-entry pieces of the 32 lists pass through a shared-memory tile, read
 // as whole list segments and written as whole rows.
@@ -448,6 +648,11 @@ void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const u
     const int Ks = list_stride(B.K);
     if (B.dim == 3 && B.fp32c) {
         k_nlist_cells3_f32<<<nb, kBlock, 0, st>>>(B, xpos, B.pjt, Ks);
+    } else if (B.fp32c && B.nseg2 >= kRowsMinSegments) {
+        // enough row segments to fill the GPU several times over; fewer, and a
+        // warp per cell keeps more warps busy (both give the same lists)
+        const int nb2 = (B.nseg2 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        k_nlist_rows2_f32<<<nb2, kBlock, 0, st>>>(B, xpos, B.pjt, Ks);
     } else {
         DTSPH_DISPATCH(B.dim, B.fp32c, (k_nlist_cells<D, F32><<<nb, kBlock, 0, st>>>(B, xpos, gid, B.pjt, Ks)));
     }

@@ -192,6 +192,7 @@ extern "C" int dtsph_eval_rates_noalloc(const dtsph_params *p, int64_t nf, const
     B.fp32c = p->precision == DTSPH_FP32C;
     B.ninst = 1;
     B.ncell = G.ncell + 1;           // the instance's cells and its empty sentinel cell
+    B.nseg2 = (G.nc[0] + kSeg2 - 1) / kSeg2 * G.nc[1] * G.nc[2];   // the 2D FP32C builder's row segments
     B.K = neighbour_capacity(*p);
     if ((size_t)B.n * B.K > kNoallocMaxEntries) return DTSPH_E_CAPACITY;
     if (carve(base, B.n, B.ncell, B) > kScratchBytes) return DTSPH_E_CAPACITY;
