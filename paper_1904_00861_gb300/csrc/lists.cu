@@ -521,9 +521,10 @@ __global__ void __launch_bounds__(kBlock) k_nlist_rows2_f32(Buffers B, const dou
                     const int r = t / NCOL, k = t % NCOL;
                     e.x = __fadd_rn(oj.x, (float)(k - 1) * sf[0]);
                     e.y = __fadd_rn(oj.y, (float)(r - 1) * sf[1]);
-                    // column + 1, and the row's part of the shift code (dx + 1) + 3 (dy + 1) + 9
-                    e.z = __int_as_float(k | ((3 * r + 9) << 8));
-                    e.w = __uint_as_float((uint32_t)j | (oj.w != 0.f ? kWallBit : 0u));
+                    // the column, and the list entry with the row's part of the shift
+                    // code (dx + 1) + 3 (dy + 1) + 9: a lane adds its dx + 1
+                    e.z = __int_as_float(k);
+                    e.w = __uint_as_float(list_entry((uint32_t)j, 3 * r + 9, oj.w != 0.f));
                     const float bx = fmaxf(fmaxf(-e.x, e.x - seg_w), 0.f);
                     const float by = fmaxf(fmaxf(-e.y, e.y - sf[1]), 0.f);
                     keep = bx * bx + by * by < box_cut2;
@@ -537,43 +538,41 @@ __global__ void __launch_bounds__(kBlock) k_nlist_rows2_f32(Buffers B, const dou
             if (take + lane < take4)
                 cand[w][take + lane] = make_float4(-3e18f, -3e18f, __int_as_float(0x7f), __uint_as_float(kNoParticle));
             __syncwarp();
-            // the tests set one bit per hit (candidate q0 + b: bit b), without
-            // branches; the hits then join the list in candidate order
+            // the tests set one bit (candidate q0 + b: bit b) per candidate of the
+            // lane's three columns closer than the band's top, without branches;
+            // each such candidate is then classified in candidate order: the lane's
+            // own particle is skipped, below the band it is a neighbour, inside the
+            // band (rare) the FP64 test decides
             for (int q0 = 0; q0 < take4; q0 += kWarp) {
                 const int qn = min(kWarp, take4 - q0);
-                uint32_t hit = 0u;
+                uint32_t maybe = 0u;
                 for (int q = 0; q < qn; q += 4) {
-                    bool band[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const float4 e = cand[w][q0 + q + u];
-                        const int z = __float_as_int(e.z);
-                        const uint32_t dxp = (uint32_t)((z & 0xff) - kh);   // dx + 1 from the lane's cell
+                        const uint32_t dxp = (uint32_t)(__float_as_int(e.z) - kh);   // dx + 1 from the lane's cell
                         const float d0 = __fsub_rn(oi.x, e.x), d1 = __fsub_rn(oi.y, e.y);
                         const float q2 = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
-                        const bool other = (__float_as_uint(e.w) & kSlotMask) != (uint32_t)s && dxp <= 2u;
-                        hit |= (uint32_t)(q2 < rc2_lo && other) << (q + u);
-                        band[u] = q2 >= rc2_lo && q2 < rc2_hi && other;
-                    }
-                    // the FP64 decision inside the band (rare)
-                    if (__any_sync(full, band[0] || band[1] || band[2] || band[3])) {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (band[u]) {
-                                const uint32_t j = __float_as_uint(cand[w][q0 + q + u].w) & kSlotMask;
-                                double d64[3];
-                                if (sep64<2>(G, xpos, n, s, (int)j, d64) < rc2) hit |= 1u << (q + u);
-                            }
-                        }
+                        if (q2 < rc2_hi && dxp <= 2u) maybe |= 1u << (q + u);
                     }
                 }
-                while (hit) {
-                    const int b = __ffs(hit) - 1;
-                    hit &= hit - 1u;
+                while (maybe) {
+                    const int b = __ffs(maybe) - 1;
+                    maybe &= maybe - 1u;
                     const float4 e = cand[w][q0 + b];
-                    const int z = __float_as_int(e.z);
-                    const uint32_t dxp = (uint32_t)((z & 0xff) - kh);
-                    my[cnt & (kBufEntries - 1)] = __float_as_uint(e.w) | ((dxp + (uint32_t)(z >> 8)) << kCodeShift);
+                    const uint32_t ej = __float_as_uint(e.w);
+                    const int j = entry_slot(ej);
+                    if (j == s) continue;
+                    const float d0 = __fsub_rn(oi.x, e.x), d1 = __fsub_rn(oi.y, e.y);
+                    const float q2 = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
+                    bool in = q2 < rc2_lo;
+                    if (!in) {
+                        double d64[3];
+                        in = sep64<2>(G, xpos, n, s, j, d64) < rc2;
+                    }
+                    if (!in) continue;
+                    const uint32_t dxp = (uint32_t)(__float_as_int(e.z) - kh);
+                    my[cnt & (kBufEntries - 1)] = ej + (dxp << kCodeShift);
                     ++cnt;
                     // a full buffer goes out as one aligned sector of the list
                     if ((cnt & (kBufEntries - 1)) == 0 && cnt <= K) {

@@ -79,6 +79,24 @@ def test_neighbour_sets_bit_exact(case, prec):
     sim.close()
 
 
+def test_neighbour_sets_of_the_row_segment_builder():
+    """At 700^2 (18,174 row segments of three 3h cells) the FP32C lists come from
+    the builder that takes a row segment per warp: the sets equal the oracle's
+    for sampled particles, those next to the periodic edges included."""
+    d = synth.tgv2d(700, seed=7)
+    sim = make_sim(d, precision=dt.DTSPH_FP32C)
+    dt.dtsph_build_neighbors(sim.ctx)
+    start, idx = oracle.neighbors(d["cfg"], d["x"])
+    x = d["x"]
+    rng = np.random.default_rng(3)
+    edge = np.concatenate([np.argsort(x[:, 0])[:20], np.argsort(x[:, 0])[-20:],
+                           np.argsort(x[:, 1])[:20], np.argsort(x[:, 1])[-20:]])
+    for i in np.concatenate([rng.choice(len(x), 160, replace=False), edge]):
+        got = dt.dtsph_get_neighbors(sim.ctx, int(i))
+        assert np.array_equal(got, idx[start[i]:start[i + 1]]), i
+    sim.close()
+
+
 # ------------------------------------------------------------------ rates
 
 @pytest.mark.parametrize("case", sorted(CASES))
