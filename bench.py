@@ -307,7 +307,8 @@ def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, kern=No
     """Times `steps` real steps after `warmup`; L2 flushed before each step.
     Returns (particle-iterations/s, ms per step, iterations, launches, job,
     (per-step particle-iterations, per-step pseudo-time loop ms, per-step
-    pair-term form) of the last timed steps, at most 256)."""
+    pair-term form, per-instance iterations of those steps) of the last timed
+    steps, at most 256)."""
     stream = torch.cuda.Stream()
     job = Job(dt, d, precision, stream=stream, graph=graph, kern=kern)
     job.step(warmup)
@@ -330,7 +331,8 @@ def run_gpu_path(dt, torch, d, precision, steps, warmup, flush, graph=2, kern=No
     nl = min(steps, 256)
     loop_ms = dt.dtsph_loop_times(job.ctx, dt.dtsph_step_count(job.ctx) - nl, nl)
     forms = job.forms(dt.dtsph_step_count(job.ctx) - nl, nl)
-    return rate, sum(ms) / steps, iters, launches, job, (work[steps - nl:], loop_ms, forms)
+    its_last = job.iterations(dt.dtsph_step_count(job.ctx) - nl, nl)
+    return rate, sum(ms) / steps, iters, launches, job, (work[steps - nl:], loop_ms, forms, its_last)
 
 
 def run_e2e(dt, torch, d, precision, steps, graph=2, kern=None):
@@ -448,6 +450,24 @@ def loop_bytes_per_particle_iteration(dims, fp32c, form, pairs_per_particle):
     return STATE_BYTES[(dims, fp32c)] + PAIR_BYTES[(dims, fp32c)] * pairs_per_particle
 
 
+def loop_launch_bytes(dims, fp32c, form, pairs_per_particle, nfs, iters, kstar):
+    """Algorithmic bytes of one step's loop: every instance's iterations in the
+    form the step ran; a step that switched (form 3) ran its first floor(kstar)
+    iterations without the cache and the rest with it."""
+    a = loop_bytes_per_particle_iteration(dims, fp32c, 2, pairs_per_particle)
+    b = loop_bytes_per_particle_iteration(dims, fp32c, 1, pairs_per_particle)
+    m = int(kstar) if 1.0 <= kstar < 1e6 else 0
+    tot = 0.0
+    for nf, k in zip(nfs, iters):
+        if form == 1:
+            tot += nf * k * b
+        elif form == 2:
+            tot += nf * k * a
+        else:
+            tot += nf * (min(k, m) * a + max(k - m, 0) * b)
+    return tot
+
+
 def fp64_flops(dim):
     """FP64 flops (FMA = 2) of the FP64 pseudo-iteration, counted from the pair
     terms (EDAC on, no artificial viscosity): per cached pair the divergence
@@ -526,7 +546,7 @@ def main_ours(args):
         # the FP64 loop is bound by the FP64 pipe: algorithmic FP64 flops of the
         # timed loops over their device time, against the measured FP64 FMA peak
         f_part, f_pair = fp64_flops(dims)
-        w64, lms64, _ = loop64
+        w64, lms64, _, _ = loop64
         flops64 = float(np.sum(w64)) * (f_part + f_pair * npairs64 / nf_tot)
         ach64 = flops64 / (sum(lms64) * 1e-3) / 1e12
         fp64 = {"value": rate64 * world, "ms_per_step": ms64, "iters_per_step_mean": float(np.mean(it64)),
@@ -543,10 +563,11 @@ def main_ours(args):
     # the dominant kernel of the timed steps is the pseudo-time loop: its
     # algorithmic bytes per step are the state and cache-entry bytes of one
     # pair pass per particle-iteration of the step
-    loop_work, loop_ms, loop_forms = loop32
+    loop_work, loop_ms, loop_forms, loop_its = loop32
     ppp = npairs / nf_tot
-    per_it_by_form = {f: loop_bytes_per_particle_iteration(dims, True, f, ppp) for f in (1, 2)}
-    bytes_by_launch = [per_it_by_form[f] * float(w) for w, f in zip(loop_work, loop_forms)]
+    form_rec = dt.dtsph_form_stats(sim32.ctx)
+    bytes_by_launch = [loop_launch_bytes(dims, True, f, ppp, sim32.nfs, [its[k] for its in loop_its],
+                                         form_rec["kstar"]) for k, f in enumerate(loop_forms)]
     loop_bytes = float(sum(bytes_by_launch))
     achieved = loop_bytes / (sum(loop_ms) * 1e-3) / 1e9
     probe_bytes = STATE_BYTES[(dims, True)] * nf_tot + PAIR_BYTES[(dims, True)] * npairs
@@ -593,7 +614,7 @@ def main_ours(args):
                                       f"{STATE_BYTES[(dims, True)] + POS_BYTES[(dims, True)]:.0f} B per "
                                       f"particle-iteration + {LIST_BYTES:.0f} B per pair-iteration; "
                                       f"{npairs / nf_tot:.2f} pairs per particle; each launch counted in the form "
-                                      f"it ran",
+                                      f"it ran (form 3: the first floor(kstar) iterations uncached, the rest cached)",
                      "forms_by_launch": loop_forms,
                      "timing": f"CUDA events around the loop of each of the last {len(loop_ms)} timed steps",
                      "peak_source": hbm_src},
@@ -602,9 +623,10 @@ def main_ours(args):
                           "pairs": npairs, "timing": "50 launches after the timed region, every instance active, "
                                                      "CUDA events"},
         "fma_peaks": fma,
-        "form": dict(dt.dtsph_form_stats(sim32.ctx), requested=args.form,
-                     note="kstar = cache pass / (uncached - cached iteration); a step runs uncached when the "
-                          "latest finished step took at most kstar iterations (form 0)"),
+        "form": dict(form_rec, requested=args.form,
+                     note="kstar = cache pass / (uncached - cached iteration); with form 0 a step starts "
+                          "uncached when the previous step took at most kstar iterations and switches to the "
+                          "cache after floor(kstar) iterations (form 3)"),
         "autotune": {"lanes_per_particle": lanes32, "stages": stages32, "ms_by_lanes": tune32,
                      "candidates": [{"lanes": L, "stages": S, "ms": m} for L, S, m in cand32]},
         "e2e": e2e,

@@ -143,8 +143,10 @@ typedef struct {
                                  operations (no cache; the cheaper form when a step takes few
                                  iterations). Both forms give the same bits. 0 (default):
                                  chosen per real step on the device from the measured costs
-                                 of both forms and the previous step's iteration count
-                                 (graph = 2; the cache otherwise; dtsph_form_stats). Form 2 only without walls,
+                                 of both forms and the previous step's iteration count, a
+                                 step without the cache switching to it after kstar
+                                 iterations (graph = 2; the cache otherwise;
+                                 dtsph_form_stats). Form 2 only without walls,
                                  particles fixed in pseudo-time (DTSPH_E_UNSUPPORTED
                                  otherwise). Instances of a batch share it. */
     double skin;              /* list skin for moving = 2 (a length > 0; the lists then hold
@@ -161,8 +163,9 @@ typedef struct {
     double vmax;      /* max |V^{n+1}| over the fluid particles at the end of the step
                          (before shifting): the decay diagnostic of the Taylor-Green
                          runs (Sec. 4.1) */
-    int32_t form;     /* the pair terms the step's loop used: 1 the pair cache, 2 recomputed
-                         from the lists (dtsph_params.form) */
+    int32_t form;     /* the pair terms the step's loop used (dtsph_params.form): 1 the pair
+                         cache, 2 recomputed from the lists, 3 recomputed for floor(kstar)
+                         iterations, then the cache built and used for the rest */
     int32_t pad;
 } dtsph_step_stats;
 
@@ -330,21 +333,26 @@ int dtsph_tuning_candidates(const dtsph_ctx *ctx, int32_t cap, int32_t *lanes, i
                             int32_t *count, int32_t *stages_in_use);
 
 /* Report of the pair-term form (dtsph_params.form). With form = 0, the
- * persistent loop, no walls and particles fixed in pseudo-time, the context
- * measured at dtsph_set_particles (or took from the process cache or the
- * DTSPH_TUNE_CACHE file) the costs ms[0] = one pair-cache pass, ms[1] = one
- * pseudo-iteration with the cache, ms[2] = one without it (milliseconds, at the
- * lanes and staging depth in use), and *kstar = ms[0] / (ms[2] - ms[1]) (1e9
- * when the uncached iteration is not slower). The step graph then holds both
- * forms and picks one per step on the device, in stream order: without the
- * cache when the previous step took at most kstar iterations (in a batch: the
- * instances' iteration counts averaged with their fluid counts as weights; an
- * instance with no finished step since the particle set's allocation counts
- * one). *kstar < 0 and ms[i] < 0 when nothing was measured. *steps_cache and
- * *steps_nocache count the steps run in each form since dtsph_set_particles
- * (with form = 0 this waits for the context's stream). Any pointer may be NULL.
- * The form of each step is also in dtsph_step_stats.form. */
-int dtsph_form_stats(const dtsph_ctx *ctx, double *kstar, float *ms, int64_t *steps_cache, int64_t *steps_nocache);
+ * persistent loop (one instance, or a batch's decoupled loop), no walls and
+ * particles fixed in pseudo-time, the context measured at dtsph_set_particles
+ * (or took from the process cache or the DTSPH_TUNE_CACHE file) the costs
+ * ms[0] = one pair-cache pass, ms[1] = one pseudo-iteration with the cache,
+ * ms[2] = one without it (milliseconds, at the lanes and staging depth in use),
+ * and *kstar = ms[0] / (ms[2] - ms[1]) (1e9 when the uncached iteration is not
+ * slower). The step graph then holds both forms and picks one per step on the
+ * device, in stream order: without the cache when the previous step took at
+ * most kstar iterations (in a batch: the instances' iteration counts averaged
+ * with their fluid counts as weights; an instance with no finished step since
+ * the particle set's allocation counts one), else with it. A loop without the
+ * cache pauses after floor(kstar) iterations if no stop rule holds; the step
+ * then builds the cache and goes on with it from that iteration (form 3 in
+ * dtsph_step_stats), so a wrong guess costs about one cache pass. All forms
+ * give the same bits. *kstar < 0 and ms[i] < 0 when nothing was measured.
+ * *steps_cache, *steps_nocache and *steps_switched count the steps run in each
+ * form since dtsph_set_particles (with form = 0 this waits for the context's
+ * stream). Any pointer may be NULL. */
+int dtsph_form_stats(const dtsph_ctx *ctx, double *kstar, float *ms, int64_t *steps_cache, int64_t *steps_nocache,
+                     int64_t *steps_switched);
 
 /* Allocation-free rate evaluation, for callers that cannot allocate device
  * memory when they need the rates: code running while a stream capture it does

@@ -80,7 +80,7 @@ _SIGS = [
     ("dtsph_probe_iterate", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_float), _DP, _I64P]),
     ("dtsph_tuning", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     ("dtsph_form_stats", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int64),
-                                   C.POINTER(C.c_int64)]),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("dtsph_loop_times", C.c_int, [_VP, C.c_int64, C.c_int32, C.POINTER(C.c_float)]),
     ("dtsph_tuning_candidates", C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -328,12 +328,14 @@ def dtsph_tuning_candidates(ctx):
 
 def dtsph_form_stats(ctx):
     """{"kstar", "ms": [cache pass, cached iteration, uncached iteration],
-    "steps_cache", "steps_nocache"} of the pair-term form (dtsph_params.form)."""
+    "steps_cache", "steps_nocache", "steps_switched"} of the pair-term form
+    (dtsph_params.form)."""
     k = C.c_double()
     ms = (C.c_float * 3)()
-    a, b = C.c_int64(), C.c_int64()
-    _check(ctx, lib().dtsph_form_stats(ctx, C.byref(k), ms, C.byref(a), C.byref(b)))
-    return {"kstar": k.value, "ms": [float(m) for m in ms], "steps_cache": a.value, "steps_nocache": b.value}
+    a, b, sw = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(ctx, lib().dtsph_form_stats(ctx, C.byref(k), ms, C.byref(a), C.byref(b), C.byref(sw)))
+    return {"kstar": k.value, "ms": [float(m) for m in ms], "steps_cache": a.value, "steps_nocache": b.value,
+            "steps_switched": sw.value}
 
 
 def dtsph_tuning(ctx):

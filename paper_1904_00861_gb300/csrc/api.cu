@@ -607,7 +607,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     if (B.async_loop) {
         A(B.il, ni) A(d_sched, ni)
     }
-    A(c->form_sel, 1) A(c->form_count, 2)
+    A(c->form_sel, 1) A(c->form_count, 3)
 #undef A
     if (wo > 0 && !(B.fp32c ? (const void *)B.wv32 : (const void *)B.wv64)) {
         free_all(c);
@@ -755,9 +755,19 @@ int build_graph_persistent(dtsph_ctx *c, cudaGraph_t *g_out, cudaGraphExec_t *x_
     cudaError_t e0 = cudaEventRecordWithFlags(c->ev_a[0], c->cap, cudaEventRecordExternal);
     cudaError_t e = launch_loop(c->B, grid, c->cap);
     if (both && e == cudaSuccess) {
+        // without the cache (form_run 1), pausing after floor(kstar) iterations;
+        // then, if it paused, the cache pass and the cached loop from there
+        // (form_run 2)
         Buffers Ba = c->B;
         Ba.form_a = 1;
+        Ba.form_run = 1;
         e = launch_loop(Ba, grid_a, c->cap);
+        Ba.form_a = 0;
+        c->per_step_fixed += 1 + launch_loop_resume(Ba, c->cap);
+        Buffers Bc = c->B;
+        Bc.form_run = 2;
+        c->per_step_fixed += launch_pair_cache_pass(Bc, Bc.xp_a, Bc.gid_a, c->cap);
+        if (e == cudaSuccess) e = launch_loop(Bc, grid, c->cap);
         c->per_step_fixed += 1;
     }
     cudaError_t e1 = cudaEventRecordWithFlags(c->ev_b[0], c->cap, cudaEventRecordExternal);
@@ -776,10 +786,12 @@ int build_graph_persistent(dtsph_ctx *c, cudaGraph_t *g_out, cudaGraphExec_t *x_
 }
 
 // The per-step choice of the pair-term form applies: form = 0, the persistent
-// loop, no walls, particles frozen in pseudo-time.
+// loop (one instance, or the decoupled batch loop), no walls, particles frozen
+// in pseudo-time.
 bool auto_form(const dtsph_ctx *c)
 {
-    return c->prm[0].form == 0 && c->prm[0].graph == 2 && c->B.nw == 0 && !c->B.xk[0];
+    return c->prm[0].form == 0 && c->prm[0].graph == 2 && c->B.nw == 0 && !c->B.xk[0] &&
+           (c->ninst == 1 || c->B.async_loop);
 }
 
 // Graph of one real step: pre-loop kernels -> while node (walls, iterate) -> outer.
@@ -1147,7 +1159,7 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
     c->have_particles = true;
     c->steps = 0;
     c->steps_cache = c->steps_nocache = 0;
-    CK(cudaMemsetAsync(c->form_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    CK(cudaMemsetAsync(c->form_count, 0, 3 * sizeof(unsigned long long), c->stream));
     CK(cudaMemsetAsync(c->form_sel, 0, sizeof(int), c->stream));
     // the iteration counts of the latest finished step stay: a new state of the
     // same shape most often continues the same flow
@@ -1306,7 +1318,7 @@ int read_stats_impl(dtsph_ctx *c, int32_t inst, int64_t first, int32_t count, dt
         out[i].rp = r.rp;
         out[i].rv = r.rv;
         out[i].vmax = r.vmax;
-        out[i].form = r.form ? 2 : 1;
+        out[i].form = r.form;
         out[i].pad = 0;
     }
     return DTSPH_OK;
@@ -1598,16 +1610,17 @@ int dtsph_probe_iterate(dtsph_ctx *c, int32_t launches, float *ms_per_launch, do
     return DTSPH_OK;
 }
 
-int dtsph_form_stats(const dtsph_ctx *c, double *kstar, float *ms, int64_t *steps_cache, int64_t *steps_nocache)
+int dtsph_form_stats(const dtsph_ctx *c, double *kstar, float *ms, int64_t *steps_cache, int64_t *steps_nocache,
+                     int64_t *steps_switched)
 {
     if (!c) return DTSPH_E_ARG;
     if (kstar) *kstar = c->kstar;
     if (ms)
         for (int i = 0; i < 3; ++i) ms[i] = c->form_ms[i];
-    int64_t a = c->steps_cache, b = c->steps_nocache;
+    int64_t a = c->steps_cache, b = c->steps_nocache, sw = 0;
     if (c->form_graph) {
         // the step graph counts its choices on the device
-        unsigned long long n[2] = {0ull, 0ull};
+        unsigned long long n[3] = {0ull, 0ull, 0ull};
         if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess ||
             cudaMemcpy(n, c->form_count, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) {
             cudaGetLastError();
@@ -1615,9 +1628,11 @@ int dtsph_form_stats(const dtsph_ctx *c, double *kstar, float *ms, int64_t *step
         }
         a = (int64_t)n[0];
         b = (int64_t)n[1];
+        sw = (int64_t)n[2];
     }
     if (steps_cache) *steps_cache = a;
     if (steps_nocache) *steps_nocache = b;
+    if (steps_switched) *steps_switched = sw;
     return DTSPH_OK;
 }
 

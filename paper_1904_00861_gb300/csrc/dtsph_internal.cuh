@@ -109,6 +109,10 @@ struct Phys {
                          // from r^0 that the lists with a skin cover (moving = 2)
 };
 
+// Stop reason of a loop without the pair cache that reached pause_at iterations
+// without meeting a stop rule (the step goes on with the cache; never reported).
+constexpr int kPaused = -2;
+
 // Convergence control of one instance's pseudo-time loop, in device memory.
 struct LoopState {
     int iter;              // iterations completed in this real step
@@ -116,7 +120,8 @@ struct LoopState {
     int reason;            // stop reason (dtsph_step_stats.reason), -1 while running
     unsigned int ticket;   // last-block election counter of the instance's tiles
     int last_iters;        // iterations of the latest finished real step (0: none since allocation)
-    int pad0;
+    int pause_at;          // a loop without the pair cache pauses after this many iterations
+                           // (0: never); the step then goes on with the cache
     double rp, rv;         // residuals of the last iteration
     double hist_p[16], hist_v[16];   // ring of the last residuals (stagnation test)
     int max_iter, fixed_iters, stag_window;
@@ -146,7 +151,7 @@ struct StatRec {
     int iters, reason;
     double rp, rv;
     double vmax;           // max |V^{n+1}| over the instance's fluid particles (before shifting)
-    int form, pad;         // 1: the step's loop ran without the pair cache
+    int form, pad;         // dtsph_step_stats.form of the step
 };
 constexpr int kStatRing = 65536;   // real steps kept per instance
 
@@ -220,10 +225,12 @@ struct Buffers {
     int form_a;            // 1: the loop recomputes the pair geometry from the lists (no pair cache)
     // the per-step choice of the pair-term form (form = 0), in the step graph
     // only (null elsewhere): k_loop_reset writes the step's form to *form_sel
-    // (0 cache, 1 recomputed) and counts it in form_count[form]; the kernels of
-    // the other form return at once
+    // (0 cache, 1 recomputed; k_loop_resume turns 1 into 2 when a paused loop
+    // goes on with the cache) and counts it in form_count[form]; a launch of
+    // the graph runs only when *form_sel equals its form_run
     int *form_sel;
-    unsigned long long *form_count;
+    unsigned long long *form_count;   // [3]
+    int form_run;
     double kstar;          // the uncached form runs when the latest step took at most kstar iterations
     StatRec *stats;        // [kStatRing][ninst]
     uint32_t *err;
@@ -256,6 +263,7 @@ int launch_permute_b_to_a(const Buffers &B, cudaStream_t st);
 void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st,
                   bool sliced);
 int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st);
+int launch_loop_resume(const Buffers &B, cudaStream_t st);
 int launch_pair_cache_pass(const Buffers &B, const double *xpos, const uint32_t *gid, cudaStream_t st);
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
 int launch_walls_iter(const Buffers &B, cudaStream_t st);

@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? (F32 ? (D == 2 ? 4 : 3
             if (threadIdx.x == 0) {
                 const int r = finish_iteration(ls, P, it, sa, sb);
                 ls->ticket = 0;
-                if (r >= 0) atomicSub(&B.ctrl->active, 1);
+                if (r != -1) atomicSub(&B.ctrl->active, 1);
                 __threadfence();
             }
         }
@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2 && !WA
     __shared__ int stop, ok_sh, p_inst;
     __shared__ int act_pre[kDealMaxInst + 1];
     if constexpr (!WALLS) {
-        if (skip_form(B, FA)) return;     // the step runs the other pair-term form
+        if (skip_form(B)) return;         // the step runs the other pair-term form
     }
     const int ntiles = (B.n + PPB - 1) / PPB;
     const bool single = B.ninst == 1;
@@ -839,7 +839,9 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2 && !WA
     else __syncthreads();
     RingPos rp;
     unsigned int epoch = 0;
-    int r = -1, it = 0;
+    // (one instance: from the loop state's iteration, 0 at the start of a step,
+    // the pause count when a loop without the cache goes on with it)
+    int r = -1, it = single ? st.iter : 0;
     for (;; ++it) {
         const int cur = it & 1;
         if (WALLS) {
@@ -902,8 +904,8 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2 && !WA
                 st.rv = sb * B.phys[0].rv_scale;
                 st.hist_p[it & 15] = st.rp;
                 st.hist_v[it & 15] = st.rv;
-                r = stop_rule(st, k1);
-                stop = r >= 0;
+                r = stop_or_pause(st, k1);
+                stop = r != -1;
             }
             __syncthreads();
             if (stop) break;
@@ -915,7 +917,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2 && !WA
                 double sa = 0, sb = 0;
                 reduce_tiles(blk + 2 * tlo, thi - tlo, sh.red, sa, sb);
                 if (threadIdx.x == 0) {
-                    if (finish_iteration(B.ls + i, B.phys[i], it, sa, sb) >= 0) atomicSub(&B.ctrl->active, 1);
+                    if (finish_iteration(B.ls + i, B.phys[i], it, sa, sb) != -1) atomicSub(&B.ctrl->active, 1);
                 }
                 __syncthreads();
             }
@@ -984,7 +986,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2) ? 4 :
     __shared__ Geom G;
     __shared__ int p_inst, w_inst, w_tile, w_it, last_sh, quit;
     __shared__ int mins[kBlock / kWarp];
-    if (skip_form(B, FA)) return;     // the step runs the other pair-term form
+    if (skip_form(B)) return;         // the step runs the other pair-term form
     const int ntiles = (B.n + PPB - 1) / PPB;
     const int ni = B.ninst;
     if (threadIdx.x == 0) p_inst = -1;
@@ -1082,7 +1084,7 @@ __global__ void __launch_bounds__(kBlock, L == 1 && !FA ? ((F32 && D == 2) ? 4 :
                 const int r = finish_iteration(B.ls + inst, P, it, sa, sb);
                 B.il[inst].done_tiles = 0u;
                 __threadfence();
-                if (r >= 0) atomicSub(&B.ctrl->active, 1);
+                if (r != -1) atomicSub(&B.ctrl->active, 1);   // stopped, or paused
                 else atomicExch(&B.il[inst].claim, (unsigned long long)(it + 1) << 32);
             }
             __syncthreads();
@@ -1117,7 +1119,7 @@ __global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
             rec->reason = ls->reason;
             rec->rp = ls->rp;
             rec->rv = ls->rv;
-            rec->form = B.form_sel ? *B.form_sel : B.form_a;
+            rec->form = B.form_sel ? *B.form_sel + 1 : (B.form_a ? 2 : 1);
             ls->last_iters = K;
             ls->step = ls->step + 1;
         }
@@ -1190,17 +1192,61 @@ __device__ void select_form(const Buffers &B)
         }
         __syncthreads();
     }
+    __shared__ int f_sh;
     if (threadIdx.x == 0) {
         const int f = kw[0] <= B.kstar * w[0] ? 1 : 0;
         *B.form_sel = f;
         B.form_count[f] += 1ull;
+        f_sh = f;
     }
+    __syncthreads();
+    // without the cache the loop pauses after floor(kstar) iterations, where the
+    // cache would have paid for itself; the step then builds it and goes on, so
+    // a wrong guess costs about one cache pass
+    const int m = f_sh && B.kstar >= 1.0 && B.kstar < 1e6 ? (int)B.kstar : 0;
+    for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) B.ls[i].pause_at = m;
 }
 
 __global__ void __launch_bounds__(kBlock) k_loop_reset(Buffers B)
 {
     if (B.form_sel) select_form(B);
     reset_loops(B);
+}
+
+// After a loop without the pair cache (form_run 1): the instances it paused
+// are reopened at their iteration for the cached loop that follows, and the
+// step's form becomes 2 (recomputed, then cached), which runs the cache pass
+// (without a loop reset) and that loop. One block.
+__global__ void __launch_bounds__(kBlock) k_loop_resume(Buffers B)
+{
+    __shared__ int cnt;
+    if (skip_form(B)) return;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < B.ninst; i += blockDim.x) {
+        LoopState *ls = B.ls + i;
+        if (ls->reason == kPaused) {
+            ls->done = 0;
+            ls->reason = -1;
+            ls->ticket = 0;
+            if (B.il) {
+                B.il[i].claim = (unsigned long long)ls->iter << 32;
+                B.il[i].done_tiles = 0u;
+            }
+            atomicAdd(&cnt, 1);
+        }
+        ls->pause_at = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt > 0) {
+        B.ctrl->ticket = 0;
+        B.ctrl->bar = 0;
+        B.ctrl->active = cnt;
+        __threadfence();
+        *B.form_sel = 2;
+        B.form_count[1] -= 1ull;
+        B.form_count[2] += 1ull;
+    }
 }
 
 template <int D, bool F, bool W, int L, bool FA = false>

@@ -32,6 +32,13 @@ __device__ inline int stop_rule(const LoopState &L, int k1)
     return -1;
 }
 
+// stop_rule, or kPaused when no rule holds and the loop reached its pause count.
+__device__ __forceinline__ int stop_or_pause(const LoopState &L, int k1)
+{
+    const int r = stop_rule(L, k1);
+    return r < 0 && L.pause_at > 0 && k1 >= L.pause_at ? kPaused : r;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -114,12 +121,12 @@ __device__ __forceinline__ void reset_loops(const Buffers &B)
     }
 }
 
-// In a step graph that holds both pair-term forms (form = 0): true in the
-// kernels of the form the step does not run (fa: the kernel recomputes the
-// pair terms). Block-uniform, so a kernel may return before any barrier.
-__device__ __forceinline__ bool skip_form(const Buffers &B, bool fa)
+// In a step graph that holds both pair-term forms (form = 0): true in a launch
+// whose form_run is not the step's current form. Block-uniform, so a kernel
+// may return before any barrier.
+__device__ __forceinline__ bool skip_form(const Buffers &B)
 {
-    return B.form_sel && *(volatile const int *)B.form_sel != (fa ? 1 : 0);
+    return B.form_sel && *(volatile const int *)B.form_sel != B.form_run;
 }
 
 // First tile and end tile of instance i for tiles of ppb slots.
@@ -131,7 +138,7 @@ __device__ __forceinline__ void instance_tiles(const Inst &I, int ppb, int &lo, 
 
 // Updates the loop state of one instance with the residual sums of iteration
 // `it` and applies the stop rules; thread 0 only. Returns the stop reason (-1:
-// continue).
+// continue; kPaused: the loop pauses, the instance leaves this launch).
 __device__ __forceinline__ int finish_iteration(LoopState *ls, const Phys &P, int it, double sa, double sb)
 {
     // work on a register copy: one batch of loads instead of a chain of
@@ -142,14 +149,14 @@ __device__ __forceinline__ int finish_iteration(LoopState *ls, const Phys &P, in
     st.rv = sb * P.rv_scale;
     st.hist_p[it & 15] = st.rp;
     st.hist_v[it & 15] = st.rv;
-    const int r = stop_rule(st, k1);
+    const int r = stop_or_pause(st, k1);
     ls->rp = st.rp;
     ls->rv = st.rv;
     ls->hist_p[it & 15] = st.rp;
     ls->hist_v[it & 15] = st.rv;
     ls->iter = k1;
     ls->reason = r;
-    ls->done = r >= 0;
+    ls->done = r != -1;
     return r;
 }
 

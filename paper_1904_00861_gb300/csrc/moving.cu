@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kBlock) k_move_iter(Buffers B, unsigned long l
             if (threadIdx.x == 0) {
                 const int r = finish_iteration(ls, P, it, sa, sb);
                 ls->ticket = 0;
-                if (r >= 0) atomicSub(&B.ctrl->active, 1);
+                if (r != -1) atomicSub(&B.ctrl->active, 1);
                 __threadfence();
             }
         }

@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
     constexpr int SPB = kBlock / L;
     __shared__ Geom G;
     __shared__ Phys P;
-    if (skip_form(B, false)) return;     // the step recomputes the pair terms
-    if (blockIdx.x == 0) {
+    if (skip_form(B)) return;            // the step runs the other pair-term form
+    if (blockIdx.x == 0 && B.form_run != 2) {    // (2: a paused loop goes on with the cache)
         reset_loops(B);
     }
     const int inst = block_instance(B, blockIdx.x * SPB);

@@ -65,6 +65,18 @@ def test_algorithmic_bytes_without_the_cache():
     assert f(2, True, 1, 27.3) == pytest.approx(488.8)
 
 
+def test_loop_bytes_of_a_switched_step():
+    """A step that started without the cache and switched to it after
+    floor(kstar) iterations counts those iterations in the uncached form and
+    the rest in the cached one, instance by instance."""
+    f = bench.loop_launch_bytes
+    a = bench.loop_bytes_per_particle_iteration(2, True, 2, 27.0)
+    b = bench.loop_bytes_per_particle_iteration(2, True, 1, 27.0)
+    assert f(2, True, 1, 27.0, [100, 50], [4, 9], 3.4) == pytest.approx(100 * 4 * b + 50 * 9 * b)
+    assert f(2, True, 2, 27.0, [100, 50], [2, 3], 3.4) == pytest.approx(100 * 2 * a + 50 * 3 * a)
+    assert f(2, True, 3, 27.0, [100, 50], [2, 9], 3.4) == pytest.approx(100 * 2 * a + 50 * (3 * a + 6 * b))
+
+
 def test_traffic_figures_come_from_committed_profiles():
     """Every DRAM traffic figure bench.py uses comes from a committed profile
     summary that states the captured launch's DRAM bytes and its algorithmic

@@ -891,8 +891,8 @@ def test_automatic_form_gives_the_bits_and_reports_its_choice(prec):
     assert ms[0] >= 0 and ms[1] > 0 and ms[2] > 0
     want = ms[0] / (ms[2] - ms[1]) if ms[2] > ms[1] else 1e9
     assert auto["kstar"] == pytest.approx(want, rel=1e-5)
-    assert auto["steps_cache"] + auto["steps_nocache"] == 5
-    assert out[1][5].count(2) == auto["steps_nocache"]
+    assert auto["steps_cache"] + auto["steps_nocache"] + auto["steps_switched"] == 5
+    assert out[1][5].count(2) == auto["steps_nocache"] and out[1][5].count(3) == auto["steps_switched"]
     # a form = 2 context reports every step uncached
     sim = make_sim(d, precision=prec, graph=2, lanes=1, form=2)
     sim.step(2)
@@ -901,16 +901,24 @@ def test_automatic_form_gives_the_bits_and_reports_its_choice(prec):
 
 
 def form_rule(iters, nfs, kstar):
-    """The form each step of a form = 0 run takes: 2 (no cache) when the
+    """The form each step of a form = 0 run takes: without the cache when the
     previous step's iterations, averaged over the instances with their fluid
-    counts as weights, are at most kstar; an instance with no step yet counts
-    one iteration."""
+    counts as weights, are at most kstar (an instance with no step yet counts
+    one iteration), else with it (1). Without the cache the loop pauses after
+    m = floor(kstar) iterations (1 <= kstar < 1e6), so a step in which some
+    instance takes more than m iterations switches to the cache (3); otherwise
+    it stays without it (2)."""
+    m = int(kstar) if 1.0 <= kstar < 1e6 else 0
     prev = [1] * len(nfs)
     forms = []
     for k in range(len(iters[0])):
         kw = float(sum(nf * p for nf, p in zip(nfs, prev)))
-        forms.append(2 if kw <= kstar * float(sum(nfs)) else 1)
-        prev = [its[k] for its in iters]
+        its = [i[k] for i in iters]
+        if kw > kstar * float(sum(nfs)):
+            forms.append(1)
+        else:
+            forms.append(3 if m > 0 and max(its) > m else 2)
+        prev = its
     return forms
 
 
@@ -918,8 +926,9 @@ def test_automatic_form_follows_the_iteration_count(tmp_path):
     """The per-step choice follows the rule exactly, in a solo context and in a
     batch, for thresholds below, between and above the iteration counts: the
     measured costs persist in DTSPH_TUNE_CACHE, a fresh process reads the
-    threshold from there, so the test sets kstar by editing the file. The bits
-    do not depend on the choice."""
+    threshold from there, so the test sets kstar by editing the file. A loop
+    without the cache that pauses and goes on with it (form 3) takes the same
+    iterations; the bits do not depend on the choice."""
     import json
     import os
     import subprocess
@@ -942,6 +951,13 @@ def test_automatic_form_follows_the_iteration_count(tmp_path):
             "out['batch'] = dict(iters=[[r['iters'] for r in b.stats(i)] for i in range(3)],\n"
             "                    forms=[r['form'] for r in b.stats(0)], nfs=[x['nf'] for x in w], fs=b.form_stats(),\n"
             "                    v=float(sum(np.sum(np.abs(v)) for v in b.field(dt.FIELD_VEL))))\n"
+            "d = synth.tgv3d(16, jitter=0.1, seed=9)\n"
+            "s = dt.Simulation(d['cfg'], precision=dt.DTSPH_FP32C, graph=2, lanes=1, stages=2)\n"
+            "s.set_state(d['x'], d['v'], d['p'], d['v_prev'])\n"
+            "s.step(6)\n"
+            "st = s.stats()\n"
+            "out['solo3'] = dict(iters=[[r['iters'] for r in st]], forms=[r['form'] for r in st], nfs=[d['nf']],\n"
+            "                    fs=s.form_stats(), v=float(np.sum(np.abs(s.v))))\n"
             "print(json.dumps(out))\n")
     path = tmp_path / "tune.txt"
     env = dict(os.environ, DTSPH_TUNE_CACHE=str(path))
@@ -949,29 +965,33 @@ def test_automatic_form_follows_the_iteration_count(tmp_path):
                                             capture_output=True, text=True).stdout.strip().splitlines()[-1])
     first = run()
     lines = [ln.split() for ln in path.read_text().splitlines() if ln.startswith("dtsph-form-v1 ")]
-    assert len(lines) == 2
-    for name in ("solo", "batch"):
+    assert len(lines) == 3
+    names = ("solo", "batch", "solo3")
+    for name in names:
         r = first[name]
         assert r["forms"] == form_rule(r["iters"], r["nfs"], r["fs"]["kstar"]), name
         assert r["fs"]["steps_nocache"] == r["forms"].count(2) and r["fs"]["steps_cache"] == r["forms"].count(1)
-    # thresholds that put every step in one form, and one between the counts
-    allk = sorted({k for name in ("solo", "batch") for its in first[name]["iters"] for k in its})
+        assert r["fs"]["steps_switched"] == r["forms"].count(3)
+    # thresholds that put every step in one form, one that switches after one
+    # iteration, and one between the counts
+    allk = sorted({k for name in names for its in first[name]["iters"] for k in its})
     mid = 0.5 * (allk[0] + allk[-1])
     seen = set()
-    for kstar in (0.5, mid, 1e6):
+    # 1.5: every first step starts without the cache and pauses after one iteration
+    for kstar in (0.5, 1.5, mid, 1e6):
         path.write_text("".join(" ".join(ln[:9] + [repr(kstar)] + ln[10:]) + "\n" for ln in lines))
         got = run()
-        for name in ("solo", "batch"):
+        for name in names:
             r = got[name]
             assert r["fs"]["kstar"] == kstar
             assert r["iters"] == first[name]["iters"] and r["v"] == first[name]["v"], (name, kstar)
             assert r["forms"] == form_rule(r["iters"], r["nfs"], kstar), (name, kstar)
             seen.update(r["forms"])
         if kstar == 0.5:
-            assert got["solo"]["forms"] == [1] * 6 and got["batch"]["forms"] == [1] * 6
+            assert all(got[name]["forms"] == [1] * 6 for name in names)
         if kstar == 1e6:
-            assert got["solo"]["forms"] == [2] * 6 and got["batch"]["forms"] == [2] * 6
-    assert seen == {1, 2}
+            assert all(got[name]["forms"] == [2] * 6 for name in names)
+    assert seen == {1, 2, 3}
 
 
 def test_automatic_form_counts_restart_with_the_state():
@@ -981,11 +1001,12 @@ def test_automatic_form_counts_restart_with_the_state():
     sim = make_sim(d, precision=dt.DTSPH_FP32C, graph=2, lanes=1, form=0)
     sim.step(3)
     fs = sim.form_stats()
-    assert fs["steps_cache"] + fs["steps_nocache"] == 3 and fs["kstar"] > 0
+    assert fs["steps_cache"] + fs["steps_nocache"] + fs["steps_switched"] == 3 and fs["kstar"] > 0
     sim.set_state(d["x"][:d["nf"]], d["v"], d["p"], d["v_prev"])
     fs2 = sim.form_stats()
-    assert fs2["steps_cache"] == 0 and fs2["steps_nocache"] == 0 and fs2["kstar"] == fs["kstar"]
+    assert fs2["steps_cache"] == 0 and fs2["steps_nocache"] == 0 and fs2["steps_switched"] == 0
+    assert fs2["kstar"] == fs["kstar"]
     sim.step(2)
     fs3 = sim.form_stats()
-    assert fs3["steps_cache"] + fs3["steps_nocache"] == 2
+    assert fs3["steps_cache"] + fs3["steps_nocache"] + fs3["steps_switched"] == 2
     sim.close()
