@@ -45,14 +45,16 @@ UNIT = "particle-iterations/s"
 
 
 # DRAM traffic of the loop kernel from the Nsight Compute captures summarised
-# under profiles/: (workload, dim, lanes, stages) -> (DRAM bytes of the captured
-# launch, dram__bytes_read.sum + dram__bytes_write.sum; algorithmic bytes of that
-# launch; source). A launch's bytes depend on the iterations of its step, so the
-# line reports the captured bytes per algorithmic byte times the algorithmic
-# bytes of its own launches. A variant not listed, or one whose kernel changed
-# after its capture, reports null.
+# under profiles/: (workload, dim, lanes, stages, pair-term form) -> (DRAM bytes
+# of the captured launch, dram__bytes_read.sum + dram__bytes_write.sum;
+# algorithmic bytes of that launch; source). A launch's bytes depend on the
+# iterations of its step, so the line reports, launch by launch, the captured
+# bytes per algorithmic byte of the form it ran times its own algorithmic bytes.
+# A variant not listed (a step that switched forms included), or one whose
+# kernel changed after its capture, reports null.
 NCU_TRAFFIC = {
-    ("batch-64x-tgv2d", 2, 1, 2, 1): (6.492738e9 + 0.500071e9, 6.667369e9, "profiles/k_loop_async_batch64_tgv2d.md"),
+    ("batch-64x-tgv2d", 2, 1, 2, 1): (6.541071e9 + 0.502044e9, 6.667369e9, "profiles/k_loop_async_batch64_tgv2d.md"),
+    ("batch-64x-tgv2d", 2, 1, 2, 2): (0.682724e9 + 0.142967e9, 2.441234e9, "profiles/k_loop_async_batch64_tgv2d.md"),
 }
 
 
@@ -584,14 +586,16 @@ def main_ours(args):
         loop_kernel = probe_kernel + (" (plain launches)" if args.graph == 0 else
                                       " in the while node (one launch each per iteration)")
     traffic, traffic_src, traffic_cap = None, None, None
-    one_form = loop_forms[0] if len(set(loop_forms)) == 1 else 0
-    key = (wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0, one_form)
-    if args.graph == 2 and not args.moving and not args.steady and not args.shifting and key in NCU_TRAFFIC:
-        t_bytes, t_alg, t_src = NCU_TRAFFIC[key]
-        traffic = t_bytes / t_alg * (loop_bytes / len(loop_ms))
-        traffic_src = (f"{t_src}: the captured launch moved {t_bytes / t_alg:.3f} DRAM bytes per algorithmic "
-                       f"byte; times this line's algorithmic bytes per launch")
-        traffic_cap = {"dram_bytes": t_bytes, "algorithmic_bytes": t_alg, "ratio": t_bytes / t_alg}
+    keys = [(wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0, f) for f in loop_forms]
+    if (args.graph == 2 and not args.moving and not args.steady and not args.shifting
+            and all(k in NCU_TRAFFIC for k in keys)):
+        ratio = {k[-1]: NCU_TRAFFIC[k][0] / NCU_TRAFFIC[k][1] for k in keys}
+        traffic = sum(ratio[f] * b for f, b in zip(loop_forms, bytes_by_launch)) / len(bytes_by_launch)
+        traffic_src = "; ".join(f"{NCU_TRAFFIC[k][2]} (form {k[-1]}): the captured launch moved {ratio[k[-1]]:.3f} "
+                                f"DRAM bytes per algorithmic byte" for k in sorted(set(keys)))
+        traffic_src += "; each of this line's launches times its own algorithmic bytes, averaged"
+        traffic_cap = {f"form{k[-1]}": {"dram_bytes": NCU_TRAFFIC[k][0], "algorithmic_bytes": NCU_TRAFFIC[k][1],
+                                        "ratio": ratio[k[-1]]} for k in sorted(set(keys))}
     e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)
     trace = run_trace(dt, d, args.warmup + args.steps, args.trace, args.graph, kern) if args.trace else None
     out = {

@@ -89,4 +89,6 @@ def test_traffic_figures_come_from_committed_profiles():
         assert "dram__bytes_read" in txt and "dram__bytes_write" in txt, path
         assert f"{byts / 1e9:.3f} GB" in txt, (path, byts)
         assert f"{alg / 1e9:.3f} GB" in txt, (path, alg)
-        assert 0.5 < byts / alg < 3.0
+        # (the form without the cache re-reads its lists and gathers from L2
+        # across iterations, so its DRAM bytes may fall below the algorithmic ones)
+        assert 0.1 < byts / alg < 3.0
