@@ -452,22 +452,29 @@ def loop_bytes_per_particle_iteration(dims, fp32c, form, pairs_per_particle):
     return STATE_BYTES[(dims, fp32c)] + PAIR_BYTES[(dims, fp32c)] * pairs_per_particle
 
 
-def loop_launch_bytes(dims, fp32c, form, pairs_per_particle, nfs, iters, kstar):
-    """Algorithmic bytes of one step's loop: every instance's iterations in the
-    form the step ran; a step that switched (form 3) ran its first floor(kstar)
-    iterations without the cache and the rest with it."""
+def loop_launch_bytes_split(dims, fp32c, form, pairs_per_particle, nfs, iters, kstar):
+    """Algorithmic bytes of one step's loop, (iterations with the cache,
+    iterations without it): every instance's iterations in the form the step
+    ran; a step that switched (form 3) ran its first floor(kstar) iterations
+    without the cache and the rest with it."""
     a = loop_bytes_per_particle_iteration(dims, fp32c, 2, pairs_per_particle)
     b = loop_bytes_per_particle_iteration(dims, fp32c, 1, pairs_per_particle)
     m = int(kstar) if 1.0 <= kstar < 1e6 else 0
-    tot = 0.0
+    cached = uncached = 0.0
     for nf, k in zip(nfs, iters):
         if form == 1:
-            tot += nf * k * b
+            cached += nf * k * b
         elif form == 2:
-            tot += nf * k * a
+            uncached += nf * k * a
         else:
-            tot += nf * (min(k, m) * a + max(k - m, 0) * b)
-    return tot
+            uncached += nf * min(k, m) * a
+            cached += nf * max(k - m, 0) * b
+    return cached, uncached
+
+
+def loop_launch_bytes(dims, fp32c, form, pairs_per_particle, nfs, iters, kstar):
+    """Algorithmic bytes of one step's loop (both parts)."""
+    return sum(loop_launch_bytes_split(dims, fp32c, form, pairs_per_particle, nfs, iters, kstar))
 
 
 def fp64_flops(dim):
@@ -568,8 +575,9 @@ def main_ours(args):
     loop_work, loop_ms, loop_forms, loop_its = loop32
     ppp = npairs / nf_tot
     form_rec = dt.dtsph_form_stats(sim32.ctx)
-    bytes_by_launch = [loop_launch_bytes(dims, True, f, ppp, sim32.nfs, [its[k] for its in loop_its],
-                                         form_rec["kstar"]) for k, f in enumerate(loop_forms)]
+    split_by_launch = [loop_launch_bytes_split(dims, True, f, ppp, sim32.nfs, [its[k] for its in loop_its],
+                                               form_rec["kstar"]) for k, f in enumerate(loop_forms)]
+    bytes_by_launch = [c + u for c, u in split_by_launch]
     loop_bytes = float(sum(bytes_by_launch))
     achieved = loop_bytes / (sum(loop_ms) * 1e-3) / 1e9
     probe_bytes = STATE_BYTES[(dims, True)] * nf_tot + PAIR_BYTES[(dims, True)] * npairs
@@ -586,14 +594,18 @@ def main_ours(args):
         loop_kernel = probe_kernel + (" (plain launches)" if args.graph == 0 else
                                       " in the while node (one launch each per iteration)")
     traffic, traffic_src, traffic_cap = None, None, None
-    keys = [(wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0, f) for f in loop_forms]
+    # a switched step (form 3) counts its iterations with and without the cache
+    # at the two forms' captured ratios
+    used = sorted({g for f in loop_forms for g in ((1, 2) if f == 3 else (f,))})
+    keys = [(wcfg["workload"], dims, lanes32, stages32 if lanes32 == 1 else 0, f) for f in used]
     if (args.graph == 2 and not args.moving and not args.steady and not args.shifting
             and all(k in NCU_TRAFFIC for k in keys)):
         ratio = {k[-1]: NCU_TRAFFIC[k][0] / NCU_TRAFFIC[k][1] for k in keys}
-        traffic = sum(ratio[f] * b for f, b in zip(loop_forms, bytes_by_launch)) / len(bytes_by_launch)
+        traffic = sum(ratio.get(1, 0.0) * c + ratio.get(2, 0.0) * u for c, u in split_by_launch) / len(split_by_launch)
         traffic_src = "; ".join(f"{NCU_TRAFFIC[k][2]} (form {k[-1]}): the captured launch moved {ratio[k[-1]]:.3f} "
                                 f"DRAM bytes per algorithmic byte" for k in sorted(set(keys)))
-        traffic_src += "; each of this line's launches times its own algorithmic bytes, averaged"
+        traffic_src += ("; each of this line's launches times its own algorithmic bytes in each form "
+                        "(a switched step: its iterations without and with the cache), averaged")
         traffic_cap = {f"form{k[-1]}": {"dram_bytes": NCU_TRAFFIC[k][0], "algorithmic_bytes": NCU_TRAFFIC[k][1],
                                         "ratio": ratio[k[-1]]} for k in sorted(set(keys))}
     e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)

@@ -534,6 +534,10 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     B.ninst = ni;
     B.ncell = (int)co;
     B.nseg2 = (int)so;
+    if (cudaDeviceGetAttribute(&B.nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        B.nsm = 1;
+    }
     B.barrier_ns = env_u64("DTSPH_TEST_BARRIER_WAIT_NS", kBarrierWaitNs);
     {
         const TuneChoice ch = kernel_choice(c, n);

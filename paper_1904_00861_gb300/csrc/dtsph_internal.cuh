@@ -49,6 +49,7 @@ constexpr unsigned long long kBarrierWaitNs = 1000000000ull;   // grid-barrier g
 // the tiles in the static order.
 constexpr int kDealMaxInst = 1024;
 
+constexpr int kPassWaveBlocksPerSm = 8;   // blocks per SM of a grid-stride pass that a graph may skip
 constexpr int kSeg2 = 3;   // cells along x in one row segment of the 2D FP32C list builder
 
 struct Inst {
@@ -162,6 +163,7 @@ struct Buffers {
     int n;                          // slots (all instances, padding included)
     int nf, nw;                     // fluid and wall particles of all instances
     int nseg2;                      // row segments of the 2D FP32C list builder, all instances
+    int nsm;                        // streaming multiprocessors of the device
     int dim, fp32c, K;              // K = neighbour capacity per particle
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
     int stages;                     // pair-cache chunks in flight per warp (lanes = 1), 2..kMaxStages

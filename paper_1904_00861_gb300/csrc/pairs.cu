@@ -220,28 +220,16 @@ __global__ void __launch_bounds__(kBlock, F32 ? 3 : 1) k_state_n(Buffers B)
 
 // --------------------------------------------------------------- pair cache
 
-// The pair coefficients of every list entry (order of the latest binning):
-// gradW_ij and F_ij for a fluid slot, W_wf and rho0 (g . r_wf) W_wf for a wall
-// slot, at the entry's place in the sliced layout. Entries are independent, so
-// L only sets the parallelism. Block 0 also resets the pseudo-time loop state.
+// The cache entries of slot s (its list, in the sliced layout); lane threadIdx.x % L
+// of the slot's group takes entries lane, lane + L, ...
 template <int D, bool F32, int L>
-__global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *__restrict__ xpos,
-                                                       const uint32_t *__restrict__ gid)
+__device__ __forceinline__ void pair_cache_slot(const Buffers &B, const Geom &G, const Phys &P,
+                                                const double *__restrict__ xpos, const uint32_t *__restrict__ gid,
+                                                int s)
 {
     using T = typename std::conditional<F32, float, double>::type;
-    constexpr int SPB = kBlock / L;
-    __shared__ Geom G;
-    __shared__ Phys P;
-    if (skip_form(B)) return;            // the step runs the other pair-term form
-    if (blockIdx.x == 0 && B.form_run != 2) {    // (2: a paused loop goes on with the cache)
-        reset_loops(B);
-    }
-    const int inst = block_instance(B, blockIdx.x * SPB);
-    block_copy(G, B.geo[inst]);
-    block_copy(P, B.phys[inst]);
-    const int s = blockIdx.x * SPB + threadIdx.x / L, lane_in = threadIdx.x % L;
+    const int lane_in = threadIdx.x % L;
     const int n = B.n;
-    if (s >= n || gid[s] == kNoParticle) return;
     const bool wall_s = gid[s] >= (uint32_t)B.nf;
     const uint32_t *lst = slot_list(B, s);                    // the list, per slot
     const size_t base = (size_t)(s >> 5) * B.K * kWarp + (s & 31);   // the cache rows, sliced
@@ -315,6 +303,40 @@ __global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *
             }
             if (!(F32 && D == 2)) B.pj[e] = jb;           // the loop reads the index from pj
         }
+    }
+}
+
+// The pair coefficients of every list entry (order of the latest binning):
+// gradW_ij and F_ij for a fluid slot, W_wf and rho0 (g . r_wf) W_wf for a wall
+// slot, at the entry's place in the sliced layout. Entries are independent, so
+// L only sets the parallelism. Block 0 also resets the pseudo-time loop state.
+template <int D, bool F32, int L>
+__global__ void __launch_bounds__(kBlock) k_pair_cache(Buffers B, const double *__restrict__ xpos,
+                                                       const uint32_t *__restrict__ gid)
+{
+    using T = typename std::conditional<F32, float, double>::type;
+    constexpr int SPB = kBlock / L;
+    __shared__ Geom G;
+    __shared__ Phys P;
+    if (skip_form(B)) return;            // the step runs the other pair-term form
+    if (blockIdx.x == 0 && B.form_run != 2) {    // (2: a paused loop goes on with the cache)
+        reset_loops(B);
+    }
+    // tiles of SPB slots, grid-stride (a launch with one block per tile takes
+    // one each; a launch in a graph that may skip it takes one wave of blocks,
+    // so that skipping costs little)
+    const int ntile = (B.n + SPB - 1) / SPB;
+    int p_inst = -1;
+    for (int bt = blockIdx.x; bt < ntile; bt += gridDim.x) {
+        const int inst = block_instance(B, bt * SPB);
+        if (inst != p_inst) {
+            __syncthreads();                 // the previous tile is done with G and P
+            block_copy(G, B.geo[inst]);
+            block_copy(P, B.phys[inst]);
+            p_inst = inst;
+        }
+        const int s = bt * SPB + threadIdx.x / L;
+        if (s < B.n && gid[s] != kNoParticle) pair_cache_slot<D, F32, L>(B, G, P, xpos, gid, s);
     }
 }
 
@@ -454,7 +476,10 @@ int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, con
 int launch_pair_cache_pass(const Buffers &B, const double *xpos, const uint32_t *gid, cudaStream_t st)
 {
     const int L = nlist_lanes(B.n);
-    const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
+    int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
+    // in a graph that may skip the pass (the per-step form choice), one wave of
+    // blocks striding over the tiles, so that a skipped launch costs little
+    if (B.form_sel) nb = std::min(nb, kPassWaveBlocksPerSm * std::max(B.nsm, 1));
     if (L == 1) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 1><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     else if (L == 2) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 2><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
     else if (L == 4) DTSPH_DISPATCH(B.dim, B.fp32c, (k_pair_cache<D, F32, 4><<<nb, kBlock, 0, st>>>(B, xpos, gid)));
