@@ -1139,7 +1139,7 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
     double *svp = vprev ? c->svp : nullptr;
     // a new state restarts the step log and clears device-side error flags
     // (before the scatter, which flags a non-finite position)
-    for (int i = 0; i < ni; ++i) CK(cudaMemsetAsync(&c->B.ls[i].step, 0, sizeof(long long), c->stream));
+    c->launches += launch_restart_steps(c->B, c->stream);
     CK(cudaMemsetAsync(c->B.err, 0, sizeof(uint32_t), c->stream));
     double *sxw = NW > 0 ? c->sxw : nullptr, *svw = NW > 0 ? c->svw : nullptr;
     if (!device && c->host_direct) {
@@ -1312,11 +1312,20 @@ int read_stats_impl(dtsph_ctx *c, int32_t inst, int64_t first, int32_t count, dt
         return fail(c, DTSPH_E_ARG, "steps [%lld, %lld) not taken (taken: %lld)", (long long)first,
                     (long long)(first + count), (long long)c->steps);
     if (c->steps - first > kStatRing) return fail(c, DTSPH_E_ARG, "step %lld no longer in the log", (long long)first);
+    // the instance's records of the range, strided by the instance count in the
+    // ring, in at most two strided copies (the ring wraps at most once), one wait
+    std::vector<StatRec> recs((size_t)count);
+    for (int32_t i = 0; i < count;) {
+        const int64_t slot = (first + i) % kStatRing;
+        const int32_t run = (int32_t)std::min<int64_t>(count - i, kStatRing - slot);
+        CK(cudaMemcpy2DAsync(recs.data() + i, sizeof(StatRec), c->B.stats + (size_t)slot * c->ninst + inst,
+                             sizeof(StatRec) * (size_t)c->ninst, sizeof(StatRec), (size_t)run, cudaMemcpyDeviceToHost,
+                             c->stream));
+        i += run;
+    }
+    if (count > 0) CK(cudaStreamSynchronize(c->stream));
     for (int32_t i = 0; i < count; ++i) {
-        StatRec r;
-        const size_t at = (size_t)((first + i) % kStatRing) * c->ninst + inst;
-        CK(cudaMemcpyAsync(&r, c->B.stats + at, sizeof r, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
+        const StatRec &r = recs[(size_t)i];
         out[i].iters = r.iters;
         out[i].reason = r.reason;
         out[i].rp = r.rp;

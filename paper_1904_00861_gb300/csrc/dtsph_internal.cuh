@@ -266,6 +266,7 @@ void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const u
                   bool sliced);
 int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st);
 int launch_loop_resume(const Buffers &B, cudaStream_t st);
+int launch_restart_steps(const Buffers &B, cudaStream_t st);
 int launch_pair_cache_pass(const Buffers &B, const double *xpos, const uint32_t *gid, cudaStream_t st);
 int launch_pair_cache(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st);
 int launch_walls_iter(const Buffers &B, cudaStream_t st);

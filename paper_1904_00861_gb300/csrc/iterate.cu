@@ -173,6 +173,12 @@ int launch_loop_reset(const Buffers &B, cudaStream_t st)
     return 1;
 }
 
+int launch_restart_steps(const Buffers &B, cudaStream_t st)
+{
+    k_restart_steps<<<1, kBlock, 0, st>>>(B);
+    return 1;
+}
+
 int launch_loop_resume(const Buffers &B, cudaStream_t st)
 {
     k_loop_resume<<<1, kBlock, 0, st>>>(B);

@@ -1213,6 +1213,12 @@ __global__ void __launch_bounds__(kBlock) k_loop_reset(Buffers B)
     reset_loops(B);
 }
 
+// A new particle state: every instance's step log starts again at step 0.
+__global__ void __launch_bounds__(kBlock) k_restart_steps(Buffers B)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.ninst; i += gridDim.x * blockDim.x) B.ls[i].step = 0;
+}
+
 // After a loop without the pair cache (form_run 1): the instances it paused
 // are reopened at their iteration for the cached loop that follows, and the
 // step's form becomes 2 (recomputed, then cached), which runs the cache pass
