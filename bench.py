@@ -209,6 +209,8 @@ def parse():
     ap.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
                     help="pair terms of the loop: 1 from the pair-coefficient cache, 2 recomputed every "
                          "pseudo-iteration from the lists (no cache), 0 chosen by the library")
+    ap.add_argument("--cell-scale", type=float, default=0.0,
+                    help="binning cell side in list cutoffs (0: the smallest cells the stencil allows)")
     ap.add_argument("--shifting", action="store_true", help="particle shifting after every real step (both arms)")
     ap.add_argument("--moving", type=int, default=0, choices=[0, 1, 2],
                     help="particles moved in pseudo-time (Algorithm 1; both arms): 1 lists of r^0, "
@@ -519,7 +521,7 @@ def main_ours(args):
         with_steady(d, wcfg, args.steady)
     if args.moving:
         with_moving(d, wcfg, args.moving)
-    kern = dict(lanes=args.lanes, stages=args.stages, form=args.form)
+    kern = dict(lanes=args.lanes, stages=args.stages, form=args.form, cell_scale=args.cell_scale)
     # batches without walls run the decoupled loop kernel (the library's rule)
     decoupled = (args.graph == 2 and isinstance(d, list) and 1 < len(d) <= 1024 and not args.moving
                  and all(x["vw"] is None for x in d) and os.environ.get("DTSPH_LOCKSTEP_LOOP", "0") in ("", "0"))
@@ -649,6 +651,7 @@ def main_ours(args):
                           "uncached when the previous step took at most kstar iterations and switches to the "
                           "cache after floor(kstar) iterations (form 3)"),
         "autotune": {"lanes_per_particle": lanes32, "stages": stages32, "ms_by_lanes": tune32,
+                     "cell_scale": args.cell_scale or 1.0,
                      "candidates": [{"lanes": L, "stages": S, "ms": m} for L, S, m in cand32]},
         "e2e": e2e,
         "gpu_launches": int(launches),

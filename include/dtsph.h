@@ -152,6 +152,11 @@ typedef struct {
     double skin;              /* list skin for moving = 2 (a length > 0; the lists then hold
                                  every pair within 3h + skin, dtsph_get_neighbors included);
                                  ignored otherwise. Instances of a batch share it. */
+    double cell_scale;        /* side of the binning cells in list cutoffs (3h, + skin): 0 or
+                                 1 (default) the smallest cells the 3^dim stencil allows,
+                                 up to 4 wider ones (more candidates per list; the lists
+                                 hold the same sets, in another order, so the last bits of
+                                 the sums can differ). Instances of a batch share it. */
 } dtsph_params;
 
 typedef struct {

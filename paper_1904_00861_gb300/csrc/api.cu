@@ -203,7 +203,9 @@ int dtsph::make_geometry(const dtsph_params &p, Geom &G, char *msg, size_t cap)
         double L = p.hi[a] - p.lo[a];
         if (!(L > 0)) return say(msg, cap, DTSPH_E_ARG, "axis %d: hi must exceed lo", a);
         // cells strictly wider than 3h so that rounding never separates neighbours
-        long long k = (long long)std::floor(L / (rc * (1.0 + 1e-9)));
+        // (cell_scale > 1: wider cells by that factor)
+        const double side = rc * std::max(1.0, p.cell_scale);
+        long long k = (long long)std::floor(L / (side * (1.0 + 1e-9)));
         if (k < 1) k = 1;
         if (G.periodic[a] && k < 3)
             return say(msg, cap, DTSPH_E_ARG, "periodic axis %d is shorter than three list cutoffs (%g < %g)", a,
@@ -298,6 +300,8 @@ int dtsph::check_params(const dtsph_params *p, char *msg, size_t cap)
     if (p->moving < 0 || p->moving > 2) return say(msg, cap, DTSPH_E_ARG, "moving must be 0, 1 or 2");
     if (p->moving && p->steady) return say(msg, cap, DTSPH_E_ARG, "the steady mode keeps the particles fixed: moving must be 0");
     if (!(p->skin >= 0) || !std::isfinite(p->skin)) return say(msg, cap, DTSPH_E_ARG, "skin must be >= 0 and finite");
+    if (!(p->cell_scale == 0.0 || (p->cell_scale >= 1.0 && p->cell_scale <= 4.0)))
+        return say(msg, cap, DTSPH_E_ARG, "cell_scale must be 0 or in [1, 4]");
     if (p->moving == 2 && !(p->skin > 0)) return say(msg, cap, DTSPH_E_ARG, "moving = 2 needs a positive skin");
     if (p->form < 0 || p->form > 2) return say(msg, cap, DTSPH_E_ARG, "form must be 0, 1 or 2");
     if (p->form == 2 && p->moving)
@@ -1257,10 +1261,11 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
                    params[i].stages != params[0].stages || params[i].shifting != params[0].shifting ||
                    params[i].form != params[0].form ||
                    params[i].steady != params[0].steady || params[i].free_surface != params[0].free_surface ||
-                   params[i].moving != params[0].moving || params[i].skin != params[0].skin))
+                   params[i].moving != params[0].moving || params[i].skin != params[0].skin ||
+                   params[i].cell_scale != params[0].cell_scale))
             r = fail(c, DTSPH_E_ARG,
                      "instances must share dim, precision, graph, lanes, stages, shifting, form, steady, "
-                     "free_surface, moving and skin");
+                     "free_surface, moving, skin and cell_scale");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;

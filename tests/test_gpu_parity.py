@@ -79,6 +79,29 @@ def test_neighbour_sets_bit_exact(case, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case", ["tgv2d_jitter", "cavity", "tgv3d"])
+def test_wider_cells_give_the_same_sets_and_iterations(case, prec):
+    """cell_scale = 1.3 bins into cells 1.3 cutoffs wide: the same neighbour sets
+    as the oracle's, and over three steps the same iteration counts and, up to
+    the summation order of the lists, the same velocities as the smallest cells."""
+    d = CASES[case]()
+    wide = make_sim(d, precision=prec, graph=2, lanes=1, cell_scale=1.3)
+    dt.dtsph_build_neighbors(wide.ctx)
+    start, idx = oracle.neighbors(d["cfg"], d["x"])
+    for i in range(0, len(d["x"]), 7):
+        assert np.array_equal(dt.dtsph_get_neighbors(wide.ctx, i), idx[start[i]:start[i + 1]]), i
+    base = make_sim(d, precision=prec, graph=2, lanes=1)
+    for s in (base, wide):
+        s.step(3)
+        s.sync()
+    assert [r["iters"] for r in base.stats()] == [r["iters"] for r in wide.stats()]
+    tol = 1e-12 if prec == dt.DTSPH_FP64 else 1e-5
+    assert rel(wide.v, base.v) < tol
+    base.close()
+    wide.close()
+
+
 def test_neighbour_sets_of_the_row_segment_builder():
     """At 700^2 (18,174 row segments of three 3h cells) the FP32C lists come from
     the builder that takes a row segment per warp: the sets equal the oracle's
