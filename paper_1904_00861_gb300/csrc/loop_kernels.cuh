@@ -401,14 +401,18 @@ __device__ __forceinline__ void pair_sums(const Buffers &B, const Phys &P, const
         const unsigned char *gcoef =
             (F32 ? (const unsigned char *)B.pc32 : (const unsigned char *)B.pc64) + row0 * RF::kCoefRow;
         const unsigned char *gj = (const unsigned char *)B.pj + row0 * (kWarp * 4);
+        // the cache rows stream through L2 once per pass (first to leave); the
+        // neighbour states, gathered again every pass, stay
+        const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
         auto issue = [&](int c) {        // lane 0: chunk c into its stage
             const int st = (int)((rp.pos + (uint32_t)c) % (uint32_t)S);
             const int r0 = c * R, nr = min(R, cmax - r0);
             const uint32_t bc = (uint32_t)(nr * RF::kCoefRow), bj = (uint32_t)(nr * RF::kJRow);
             unsigned char *stg = rg.buf + (size_t)st * RF::kStageBytes;
             mbar_arrive_expect_tx(&rg.bar[st], bc + bj);
-            bulk_g2s(stg, gcoef + (size_t)r0 * RF::kCoefRow, bc, &rg.bar[st]);
-            if (RF::kSepJ) bulk_g2s(stg + R * RF::kCoefRow, gj + (size_t)r0 * RF::kJRow, bj, &rg.bar[st]);
+            bulk_g2s_hint(stg, gcoef + (size_t)r0 * RF::kCoefRow, bc, &rg.bar[st], pol_stream);
+            if (RF::kSepJ)
+                bulk_g2s_hint(stg + R * RF::kCoefRow, gj + (size_t)r0 * RF::kJRow, bj, &rg.bar[st], pol_stream);
         };
         if (lane == 0)
             for (int c = 0; c < S && c < nch; ++c) issue(c);
@@ -430,7 +434,10 @@ __device__ __forceinline__ void pair_sums(const Buffers &B, const Phys &P, const
                     jbv[r] = RF::kSepJ
                                  ? ((const uint32_t *)(stg + R * RF::kCoefRow + r * RF::kJRow))[lane]
                                  : __float_as_uint(((const float4 *)(stg + r * RF::kCoefRow))[lane].w);
-                    qv[r] = nbq[jbv[r] & ~kWallBit];
+                    if constexpr (F32)
+                        qv[r] = ld_f4_hint(reinterpret_cast<const float4 *>(nbq) + (jbv[r] & ~kWallBit), pol_keep);
+                    else
+                        qv[r] = nbq[jbv[r] & ~kWallBit];
                     if constexpr (WALLS) wall_velocity<D, F32, T>(B, jbv[r], wv[r]);
                 }
             }
