@@ -57,6 +57,14 @@ NCU_TRAFFIC = {
     ("batch-64x-tgv2d", 2, 1, 2, 2): (0.682724e9 + 0.142967e9, 2.441234e9, "profiles/k_loop_async_batch64_tgv2d.md"),
 }
 
+# FP32 flops of the loop without the pair cache, from the FP32 operation counters
+# of an Nsight Compute capture (fadd + fmul + 2 ffma, thread instructions):
+# dim -> (flops per pair-iteration, workload, source). The form is bound by
+# neither HBM nor the FP32 pipe; this places its launches against the FP32 peak.
+NCU_FLOPS_NO_CACHE = {
+    2: (62.51, "batch-64x-tgv2d", "profiles/k_loop_async_batch64_tgv2d.md"),
+}
+
 
 def make_workload(name: str, n_side: int, re: float):
     """Synthetic input and its config record. batch (default: 64 Taylor-Green
@@ -615,6 +623,19 @@ def main_ours(args):
                         "(a switched step: its iterations without and with the cache), averaged")
         traffic_cap = {f"form{k[-1]}": {"dram_bytes": NCU_TRAFFIC[k][0], "algorithmic_bytes": NCU_TRAFFIC[k][1],
                                         "ratio": ratio[k[-1]]} for k in sorted(set(keys))}
+    # the launches that ran without the cache, against the FP32 pipe
+    no_cache = None
+    nc_idx = [k for k, f in enumerate(loop_forms) if f == 2]
+    if nc_idx and dims in NCU_FLOPS_NO_CACHE and not args.moving:
+        fpp, fwl, fsrc = NCU_FLOPS_NO_CACHE[dims]
+        pit = sum(float(loop_work[k]) for k in nc_idx)
+        secs = sum(loop_ms[k] for k in nc_idx) * 1e-3
+        tf = fpp * ppp * pit / secs / 1e12
+        no_cache = {"bound": "alu", "pipe": "fp32", "achieved": tf, "peak": fma["fp32_fma_tflops"],
+                    "unit": "TFLOP/s", "frac": tf / fma["fp32_fma_tflops"], "launches": len(nc_idx),
+                    "flops_counted": f"{fpp:.1f} FP32 flops per pair-iteration (fadd + fmul + 2 ffma per thread, "
+                                     f"measured on {fwl}: {fsrc}), {ppp:.2f} pairs per particle",
+                    "peak_source": "dtsph_fma_peak(FP32), measured in this run"}
     e2e = run_e2e(dt, torch, d, dt.DTSPH_FP32C, max(3, min(args.steps, 30)), args.graph, kern)
     trace = run_trace(dt, d, args.warmup + args.steps, args.trace, args.graph, kern) if args.trace else None
     out = {
@@ -641,6 +662,7 @@ def main_ours(args):
                      "forms_by_launch": loop_forms,
                      "timing": f"CUDA events around the loop of each of the last {len(loop_ms)} timed steps",
                      "peak_source": hbm_src},
+        "roofline_no_cache": no_cache,
         "iterate_probe": {"kernel": probe_kernel, "achieved": achieved_probe,
                           "frac": achieved_probe / hbm, "bytes_per_launch": probe_bytes, "launch_ms": ms_it,
                           "pairs": npairs, "timing": "50 launches after the timed region, every instance active, "
