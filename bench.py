@@ -63,6 +63,7 @@ NCU_TRAFFIC = {
 # neither HBM nor the FP32 pipe; this places its launches against the FP32 peak.
 NCU_FLOPS_NO_CACHE = {
     2: (62.51, "batch-64x-tgv2d", "profiles/k_loop_async_batch64_tgv2d.md"),
+    3: (75.46, "tgv3d 80^3", "profiles/k_loop_no_cache_tgv3d_80.md"),
 }
 
 

@@ -538,6 +538,16 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     B.ninst = ni;
     B.ncell = (int)co;
     B.nseg2 = (int)so;
+    {
+        // the pair cache's rows (sliced, K per slot) against half of L2
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess) {
+            cudaGetLastError();
+            l2 = 0;
+        }
+        const size_t row = B.fp32c ? (d == 2 ? 16 : 20) : (d == 2 ? 36 : 36);
+        B.l2_stream = (size_t)n * (size_t)K * row > (size_t)l2 / 2 ? 1 : 0;
+    }
     if (cudaDeviceGetAttribute(&B.nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
         cudaGetLastError();
         B.nsm = 1;

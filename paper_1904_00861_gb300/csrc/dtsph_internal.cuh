@@ -164,6 +164,7 @@ struct Buffers {
     int nf, nw;                     // fluid and wall particles of all instances
     int nseg2;                      // row segments of the 2D FP32C list builder, all instances
     int nsm;                        // streaming multiprocessors of the device
+    int l2_stream;                  // 1: the pair cache exceeds half of L2 (its rows stream, evicting first)
     int dim, fp32c, K;              // K = neighbour capacity per particle
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
     int stages;                     // pair-cache chunks in flight per warp (lanes = 1), 2..kMaxStages

@@ -401,9 +401,11 @@ __device__ __forceinline__ void pair_sums(const Buffers &B, const Phys &P, const
         const unsigned char *gcoef =
             (F32 ? (const unsigned char *)B.pc32 : (const unsigned char *)B.pc64) + row0 * RF::kCoefRow;
         const unsigned char *gj = (const unsigned char *)B.pj + row0 * (kWarp * 4);
-        // the cache rows stream through L2 once per pass (first to leave); the
-        // neighbour states, gathered again every pass, stay
-        const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
+        // a cache larger than L2 streams through it once per pass (first to
+        // leave); a smaller one stays like the rest; the neighbour states,
+        // gathered again every pass, stay
+        const uint64_t pol_stream = B.l2_stream ? l2_policy_evict_first() : l2_policy_evict_normal();
+        const uint64_t pol_keep = l2_policy_evict_last();
         auto issue = [&](int c) {        // lane 0: chunk c into its stage
             const int st = (int)((rp.pos + (uint32_t)c) % (uint32_t)S);
             const int r0 = c * R, nr = min(R, cmax - r0);
