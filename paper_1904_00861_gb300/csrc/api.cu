@@ -53,7 +53,6 @@ struct dtsph_ctx {
     double *sx = nullptr, *sv = nullptr, *sp = nullptr, *svp = nullptr, *sxw = nullptr, *svw = nullptr;
     double *rd = nullptr;                // dtsph_read_state: the fields in caller order (3 nf dim + nf)
     bool tuned = false;
-    int loop_grid = 0;
     // events around the pseudo-time loop of each real step (pair step % kLoopEv),
     // recorded by event nodes of the step graph or on the stream
     static constexpr int kLoopEv = 256;
@@ -758,7 +757,6 @@ int build_graph_persistent(dtsph_ctx *c, cudaGraph_t *g_out, cudaGraphExec_t *x_
 {
     int grid = 0, grid_a = 0;
     if (loop_grid(c->B, &grid)) return fail(c, DTSPH_E_CUDA, "occupancy query for the loop kernel failed");
-    c->loop_grid = grid;
     const bool both = c->B.form_sel != nullptr;
     if (both) {
         Buffers Ba = c->B;
