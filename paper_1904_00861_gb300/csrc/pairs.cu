@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kBlock) k_walls_state_n(Buffers B)
 // dp^n/dtau (Eq. pkstar_frozen with the state-n rate); and the BDF2 source
 // (V^{n-1} - 4 V^n) / (2 dt) of Eq. (dv_dtau_exact), all in FP64.
 template <int D, bool F32, bool PRED, bool WALLS, int L>
-__global__ void __launch_bounds__(kBlock, F32 ? 3 : 1) k_state_n(Buffers B)
+__global__ void __launch_bounds__(kBlock, F32 ? (D == 2 ? 4 : 3) : 1) k_state_n(Buffers B)
 {
     using T = typename std::conditional<F32, float, double>::type;
     using Acc = typename std::conditional<F32, Kahan, Plain64>::type;
