@@ -143,15 +143,18 @@ class Job:
     """One context running a workload: a single instance or a batch."""
 
     def __init__(self, dt, work, precision, stream=None, graph=2, kern=None):
-        kern = kern or {}
+        kern = dict(kern or {})
+        # list skin in smoothing lengths -> each instance's own length
+        skin_h = kern.pop("list_skin_h", 0.0)
+        cfg_of = lambda d: dict(d["cfg"], list_skin=skin_h * d["cfg"]["h"]) if skin_h > 0 else d["cfg"]
         self.dt = dt
         self.batch = isinstance(work, list)
         if self.batch:
-            self.sim = dt.Batch([d["cfg"] for d in work], precision=precision, stream=stream, graph=graph, **kern)
+            self.sim = dt.Batch([cfg_of(d) for d in work], precision=precision, stream=stream, graph=graph, **kern)
             self.sim.set_state(work)
             self.nfs = [d["nf"] for d in work]
         else:
-            self.sim = dt.Simulation(work["cfg"], precision=precision, stream=stream, graph=graph, **kern)
+            self.sim = dt.Simulation(cfg_of(work), precision=precision, stream=stream, graph=graph, **kern)
             nf = work["nf"]
             walls = None if work["vw"] is None else (work["x"][nf:], work["vw"])
             self.sim.set_state(work["x"][:nf], work["v"], work["p"], work["v_prev"], walls=walls)
@@ -218,6 +221,11 @@ def parse():
     ap.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
                     help="pair terms of the loop: 1 from the pair-coefficient cache, 2 recomputed every "
                          "pseudo-iteration from the lists (no cache), 0 chosen by the library")
+    ap.add_argument("--list-skin", type=float, default=0.05,
+                    help="> 0: the r^0 lists, built with this skin (in smoothing lengths), also serve the next "
+                         "step's pass at r^n (one list build per step where the motion allows, on the device); "
+                         "0: two builds per step. Applies where the library allows it (graph 2, no walls, no "
+                         "shifting, no steady mode, frozen particles)")
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="binning cell side in list cutoffs (0: the smallest cells the stencil allows)")
     ap.add_argument("--shifting", action="store_true", help="particle shifting after every real step (both arms)")
@@ -530,7 +538,11 @@ def main_ours(args):
         with_steady(d, wcfg, args.steady)
     if args.moving:
         with_moving(d, wcfg, args.moving)
-    kern = dict(lanes=args.lanes, stages=args.stages, form=args.form, cell_scale=args.cell_scale)
+    # list reuse where the library supports it
+    reuse_ok = (args.graph == 2 and not args.moving and not args.steady and not args.shifting and
+                all(x["vw"] is None for x in (d if isinstance(d, list) else [d])))
+    kern = dict(lanes=args.lanes, stages=args.stages, form=args.form, cell_scale=args.cell_scale,
+                list_skin_h=args.list_skin if reuse_ok else 0.0)
     # batches without walls run the decoupled loop kernel (the library's rule)
     decoupled = (args.graph == 2 and isinstance(d, list) and 1 < len(d) <= 1024 and not args.moving
                  and all(x["vw"] is None for x in d) and os.environ.get("DTSPH_LOCKSTEP_LOOP", "0") in ("", "0"))
@@ -675,6 +687,7 @@ def main_ours(args):
                           "cache after floor(kstar) iterations (form 3)"),
         "autotune": {"lanes_per_particle": lanes32, "stages": stages32, "ms_by_lanes": tune32,
                      "cell_scale": args.cell_scale or 1.0,
+                     "list_skin_h": kern["list_skin_h"],
                      "candidates": [{"lanes": L, "stages": S, "ms": m} for L, S, m in cand32]},
         "e2e": e2e,
         "gpu_launches": int(launches),

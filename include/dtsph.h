@@ -157,6 +157,17 @@ typedef struct {
                                  up to 4 wider ones (more candidates per list; the lists
                                  hold the same sets, in another order, so the last bits of
                                  the sums can differ). Instances of a batch share it. */
+    double list_skin;         /* > 0: the lists at r^0 of each step are built to 3h + list_skin
+                                 and also serve the next step's pass at r^n (one list build,
+                                 one binning per step instead of two; pairs beyond 3h add
+                                 exact zeros, the kernel gradient vanishing there). When a
+                                 particle's r^{n+1} lies farther than list_skin / 2 from its
+                                 r^0, the next step bins and lists at r^n as without it (on
+                                 the device, in the step graph). Only with the persistent
+                                 loop (graph = 2), no walls, particles fixed in pseudo-time,
+                                 no shifting and no steady mode (DTSPH_E_UNSUPPORTED
+                                 otherwise). 0 (default): two builds per step. The instances
+                                 of a batch all set it (each its own length) or none does. */
 } dtsph_params;
 
 typedef struct {

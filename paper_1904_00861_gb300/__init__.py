@@ -47,6 +47,7 @@ class dtsph_params(C.Structure):
         ("fixed_iters", C.c_int32), ("max_neighbors", C.c_int32), ("graph", C.c_int32), ("lanes", C.c_int32),
         ("stages", C.c_int32), ("shifting", C.c_int32), ("steady", C.c_int32), ("free_surface", C.c_int32),
         ("moving", C.c_int32), ("form", C.c_int32), ("skin", C.c_double), ("cell_scale", C.c_double),
+        ("list_skin", C.c_double),
     ]
 
 
@@ -145,7 +146,7 @@ def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) 
     d = dict(periodic=(0, 0, 0), lo=(0, 0, 0), hi=(1, 1, 1), rho0=1.0, beta=10.0, v_ref=1.0, eta=0.01, alpha=0.0,
              g=(0, 0, 0), eps=1e-3, stag_tol=0.05, stag_window=4, max_iter=1000, edac=1, edac_h2_literal=0,
              fixed_iters=0, max_neighbors=0, lanes=0, stages=0, shifting=0, steady=0, free_surface=0, moving=0,
-             skin=0.0, form=0, cell_scale=0.0)
+             skin=0.0, form=0, cell_scale=0.0, list_skin=0.0)
     d.update(cfg)
     d.update(over)
     p = dtsph_params()
@@ -164,6 +165,7 @@ def make_params(cfg: dict, precision: int = DTSPH_FP64, graph: int = 1, **over) 
         setattr(p, k, int(d[k]))
     p.skin = float(d["skin"])
     p.cell_scale = float(d["cell_scale"])
+    p.list_skin = float(d["list_skin"])
     if p.moving == 2 and p.skin == 0.0:
         p.skin = 0.5 * p.h
     return p

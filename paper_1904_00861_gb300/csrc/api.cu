@@ -64,6 +64,11 @@ struct dtsph_ctx {
     // iterations, the break-even count of the two forms' measured costs); both
     // give the same bits
     bool form_graph = false;            // the step graph chooses the form
+    // reused lists (list_skin > 0): order A, its cells and the lists hold the
+    // binning and the lists of the latest r^0 (or of r^n before the first step);
+    // a call that bins or builds lists otherwise clears this, and the next step
+    // first bins and lists at r^n
+    bool lists_ready = false;
     int *form_sel = nullptr;            // device: the current step's form
     unsigned long long *form_count = nullptr;   // device: steps run in each form
     double kstar = -1.0;                // < 0: not measured
@@ -150,6 +155,7 @@ void free_all(dtsph_ctx *c)
     c->exec = nullptr;
     c->graph = nullptr;
     c->form_graph = false;
+    c->lists_ready = false;
     c->form_sel = nullptr;
     c->form_count = nullptr;
     for (void *p : c->allocs) cudaFree(p);
@@ -183,8 +189,9 @@ int dtsph::make_geometry(const dtsph_params &p, Geom &G, char *msg, size_t cap)
     memset(&G, 0, sizeof G);
     G.dim = p.dim;
     // the lists cover 3h, plus the skin when the particles move in pseudo-time
-    // with neighbour updates (pairs beyond 3h add exact zeros)
-    const double rc = 3.0 * p.h + (p.moving == 2 ? p.skin : 0.0);
+    // with neighbour updates or when the r^0 lists serve the next step at r^n
+    // (pairs beyond 3h add exact zeros)
+    const double rc = 3.0 * p.h + (p.moving == 2 ? p.skin : 0.0) + p.list_skin;
     G.ncell = 1;
     for (int a = 0; a < 3; ++a) {
         G.periodic[a] = a < p.dim ? p.periodic[a] : 0;
@@ -262,6 +269,7 @@ void dtsph::make_phys(const dtsph_params &p, Phys &P)
     P.free_surface = p.free_surface;
     P.moving = p.steady ? 0 : p.moving;
     P.disp2_max = p.moving == 2 ? 0.25 * p.skin * p.skin : 0.0;
+    P.disp2_reuse = 0.25 * p.list_skin * p.list_skin;
     if (p.steady) {
         // Eq. (mom-steady): dV/dtau is the momentum rate itself (no BDF2 term);
         // the pressure rate has no EDAC term
@@ -305,6 +313,11 @@ int dtsph::check_params(const dtsph_params *p, char *msg, size_t cap)
     if (p->form < 0 || p->form > 2) return say(msg, cap, DTSPH_E_ARG, "form must be 0, 1 or 2");
     if (p->form == 2 && p->moving)
         return say(msg, cap, DTSPH_E_UNSUPPORTED, "form 2 (no pair cache) needs particles fixed in pseudo-time");
+    if (!(p->list_skin >= 0) || !std::isfinite(p->list_skin))
+        return say(msg, cap, DTSPH_E_ARG, "list_skin must be >= 0 and finite");
+    if (p->list_skin > 0 && (p->moving || p->steady || p->shifting || p->graph != 2))
+        return say(msg, cap, DTSPH_E_UNSUPPORTED,
+                   "list_skin needs graph = 2, particles fixed in pseudo-time, no shifting and no steady mode");
     return DTSPH_OK;
 }
 
@@ -475,7 +488,7 @@ int dtsph::neighbour_capacity(const dtsph_params &p)
 {
     if (p.max_neighbors > 0) return p.max_neighbors;
     const double vol = p.m / p.rho0;
-    const double rc = 3.0 * p.h + (p.moving == 2 ? p.skin : 0.0);
+    const double rc = 3.0 * p.h + (p.moving == 2 ? p.skin : 0.0) + p.list_skin;
     double expect = p.dim == 2 ? pi() * rc * rc / vol : 4.0 / 3.0 * pi() * rc * rc * rc / vol;
     int k = (int)std::ceil(1.35 * expect) + 8;
     return std::min(std::max(k, 8), 4096);
@@ -621,6 +634,15 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
         return fail(c, DTSPH_E_UNSUPPORTED, "form 2 (no pair cache) is for contexts without walls");
     }
     B.form_a = c->prm[0].form == 2;
+    if (c->prm[0].list_skin > 0 && wo > 0) {
+        free_all(c);
+        return fail(c, DTSPH_E_UNSUPPORTED, "list_skin is for contexts without walls");
+    }
+    B.reuse_lists = c->prm[0].list_skin > 0;
+    B.relist_run = -1;
+    if (B.reuse_lists) {
+        A(B.relist, 1)
+    }
     if (B.async_loop) {
         A(B.il, ni) A(d_sched, ni)
     }
@@ -689,9 +711,24 @@ int enqueue_pre_loop(dtsph_ctx *c, cudaStream_t st)
 {
     const Buffers &B = c->B;
     int k = 0;
-    k += launch_binning(B, B.x_a, B.gid_a, st);          // cells at r^n
-    k += launch_permute_a_to_b(B, st);
-    k += launch_state_n(B, true, st);                     // walls, rates, predictor
+    if (B.reuse_lists) {
+        // the lists at r^0 of the previous step (to 3h + list_skin) hold every
+        // pair within 3h at r^n unless a particle ended the step farther than
+        // list_skin / 2 from its r^0 (*relist): then this step bins and lists at
+        // r^n as without reuse; either way the state-n pass runs on the lists
+        Buffers Br = B;
+        Br.relist_run = 1;
+        k += launch_binning(Br, Br.x_a, Br.gid_a, st);
+        k += launch_permute_a_to_b(Br, st);
+        launch_nlist(Br, Br.x_b, Br.cell_b, Br.gid_b, st, false);
+        Br.relist_run = 0;
+        k += 1 + launch_same_order_a_to_b(Br, st);
+        k += launch_state_n(B, true, st, false);
+    } else {
+        k += launch_binning(B, B.x_a, B.gid_a, st);      // cells at r^n
+        k += launch_permute_a_to_b(B, st);
+        k += launch_state_n(B, true, st);                 // walls, rates, predictor
+    }
     k += launch_binning(B, B.xp_b, B.gid_b, st);         // cells at r^0
     k += launch_permute_b_to_a(B, st);
     if (B.xk[0]) {
@@ -1173,6 +1210,7 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
         if (e & kErrNonFinite) return fail(c, DTSPH_E_ARG, "a particle position is not finite");
     }
     c->have_particles = true;
+    c->lists_ready = false;
     c->steps = 0;
     c->steps_cache = c->steps_nocache = 0;
     CK(cudaMemsetAsync(c->form_count, 0, 3 * sizeof(unsigned long long), c->stream));
@@ -1270,10 +1308,11 @@ int create_impl(int32_t ninst, const dtsph_params *params, void *stream, dtsph_c
                    params[i].form != params[0].form ||
                    params[i].steady != params[0].steady || params[i].free_surface != params[0].free_surface ||
                    params[i].moving != params[0].moving || params[i].skin != params[0].skin ||
-                   params[i].cell_scale != params[0].cell_scale))
+                   params[i].cell_scale != params[0].cell_scale ||
+                   (params[i].list_skin > 0) != (params[0].list_skin > 0)))
             r = fail(c, DTSPH_E_ARG,
                      "instances must share dim, precision, graph, lanes, stages, shifting, form, steady, "
-                     "free_surface, moving, skin and cell_scale");
+                     "free_surface, moving, skin and cell_scale, and list_skin > 0 or not");
         if (!r) r = setup_geometry(c, params[i], c->G[i]);
         if (r) {
             delete c;
@@ -1426,6 +1465,19 @@ int dtsph_step(dtsph_ctx *c, int32_t nsteps)
     if (!c->have_particles) return fail(c, DTSPH_E_STATE, "dtsph_step before dtsph_set_particles");
     if (nsteps < 0) return fail(c, DTSPH_E_ARG, "nsteps must be >= 0");
     CK(cudaSetDevice(c->device));
+    if (c->B.reuse_lists && !c->lists_ready && nsteps > 0) {
+        // bin at r^n, make that order A, list to 3h + list_skin: what the
+        // steps' state-n pass reads
+        const Buffers &B = c->B;
+        c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
+        c->launches += launch_permute_a_to_b(B, c->stream);
+        c->launches += launch_adopt_b(B, c->stream);
+        launch_nlist(B, B.x_a, B.cell_a, B.gid_a, c->stream, false);
+        c->launches += 1;
+        CK(cudaMemsetAsync(B.relist, 0, sizeof(int), c->stream));
+        CK(cudaGetLastError());
+        c->lists_ready = true;
+    }
     Range range(c->exec ? "dtsph_step (step graphs)" : "dtsph_step");
     c->have_nbrs = false;
     for (int32_t s = 0; s < nsteps; ++s) {
@@ -1512,6 +1564,7 @@ int dtsph_eval_rates(dtsph_ctx *c, double *ap, double *F)
     if (!ap || !F) return fail(c, DTSPH_E_ARG, "ap and F are required");
     CK(cudaSetDevice(c->device));
     const Buffers &B = c->B;
+    c->lists_ready = false;                       // the lists are rebuilt at r^n in order B
     c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
     c->launches += launch_permute_a_to_b(B, c->stream);
     c->launches += launch_state_n(B, false, c->stream);
@@ -1535,6 +1588,7 @@ int dtsph_build_neighbors(dtsph_ctx *c)
     if (!c->have_particles) return fail(c, DTSPH_E_STATE, "no particles set");
     CK(cudaSetDevice(c->device));
     const Buffers &B = c->B;
+    c->lists_ready = false;                       // the lists are rebuilt at r^n in order B
     c->launches += launch_binning(B, B.x_a, B.gid_a, c->stream);
     c->launches += launch_permute_a_to_b(B, c->stream);
     c->launches += launch_pair_cache(B, B.x_b, B.cell_b, B.gid_b, c->stream);

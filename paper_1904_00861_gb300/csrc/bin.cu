@@ -33,6 +33,7 @@ __device__ __forceinline__ int cell_coord(double xa, double lo, double hi, doubl
 __global__ void __launch_bounds__(kBlock) k_bin_keys(Buffers B, const double *__restrict__ x,
                                                      const uint32_t *__restrict__ gid)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     if (gid[i] == kNoParticle) {
@@ -93,6 +94,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v)
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_partial(Buffers B)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     const int base = blockIdx.x * kScanCells + threadIdx.x * kScanPerThread;
     int s = 0;
 #pragma unroll
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partial(Buffers B)
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(Buffers B, int nblocks)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     // exclusive prefix of the block totals, in chunks of the block width
     int carry = 0;
     for (int base = 0; base < nblocks; base += kScanThreads) {
@@ -146,6 +149,7 @@ __device__ __forceinline__ int cell_instance(const Buffers &B, int c)
 template <int PER, bool MULTI>
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(Buffers B)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     const int base = blockIdx.x * kScanThreads * PER + threadIdx.x * PER;
     int v[PER];
     int s = 0;
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(Buffers B)
 
 __global__ void __launch_bounds__(kBlock) k_scatter(Buffers B)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const int c = B.key[i];
@@ -184,6 +189,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(Buffers B)
 // written by the scatter) stay -1.
 __global__ void __launch_bounds__(kBlock) k_cell_rank(Buffers B, const uint32_t *__restrict__ gid)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.n) return;
     const int i = B.unsorted[t];
@@ -210,6 +216,26 @@ __device__ __forceinline__ float4 cell_offset(const Geom &G, int local_cell, con
     return o;
 }
 
+// cell_offset of a particle that may have left its cell since the binning (the
+// lists reused at r^n): on a periodic axis the nearest image of the position
+// to the cell, so that a particle wrapped across the box edge keeps the offset
+// that the lists' cell shifts assume.
+__device__ __forceinline__ float4 cell_offset_near(const Geom &G, int local_cell, const double *x, int n, int s,
+                                                   bool wall)
+{
+    const int c[3] = {local_cell % G.nc[0], (local_cell / G.nc[0]) % G.nc[1], local_cell / (G.nc[0] * G.nc[1])};
+    float f[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < G.dim; ++a) {
+        double d = x[(size_t)a * n + s] - (G.lo[a] + c[a] * G.s[a]);
+        if (G.periodic[a]) {
+            if (d > G.halfL[a]) d -= G.L[a];
+            else if (d < -G.halfL[a]) d += G.L[a];
+        }
+        f[a] = (float)d;
+    }
+    return make_float4(f[0], f[1], f[2], wall ? 1.f : 0.f);
+}
+
 // A -> B at the start of a step: state n, and the packed (V^n, p^n) that the
 // state-n pair pass gathers.
 // The packed copy of a wall slot's prescribed velocity that the loop gathers
@@ -220,11 +246,16 @@ __device__ __forceinline__ void store_wall_velocity(const Buffers &B, int s, con
     if (B.wv64) B.wv64[s] = make_double4_32a(u[0], u[1], u[2], 0.0);
 }
 
+// SAME: order B is order A (the r^0 lists of the previous step serve this
+// step): every slot keeps its place and its cell of that binning, and the FP32
+// offsets are taken at r^n from that cell's origin.
+template <bool SAME>
 __global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= B.n) return;
-    const int o = B.perm[s];
+    const int o = SAME ? (B.gid_a[s] == kNoParticle ? -1 : s) : B.perm[s];
     if (o < 0) {
         B.gid_b[s] = kNoParticle;
         return;
@@ -232,7 +263,7 @@ __global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
     const int n = B.n, dim = B.dim;
     const uint32_t g = B.gid_a[o];
     B.gid_b[s] = g;
-    const int cell = B.key[o];
+    const int cell = SAME ? B.cell_a[s] : B.key[o];
     B.cell_b[s] = cell;
     double v[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) {
@@ -246,7 +277,8 @@ __global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
     B.pn_b[s] = p;
     if (B.fp32c) {
         const int inst = B.inst_of[s];
-        B.off[s] = cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.x_b, n, s, g >= (uint32_t)B.nf);
+        B.off[s] = SAME ? cell_offset_near(B.geo[inst], cell - B.inst[inst].cell_off, B.x_b, n, s, g >= (uint32_t)B.nf)
+                        : cell_offset(B.geo[inst], cell - B.inst[inst].cell_off, B.x_b, n, s, g >= (uint32_t)B.nf);
         B.nb32[1][s] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)p);
     } else {
         B.nb64[1][s] = make_double4_32a(v[0], v[1], v[2], p);
@@ -258,6 +290,7 @@ __global__ void __launch_bounds__(kBlock) k_permute_a_to_b(Buffers B)
 __global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (B.relist && s == 0) *B.relist = 0;   // the step's relisting, if any, is done
     if (s >= B.n) return;
     const int o = B.perm[s];
     if (o < 0) {
@@ -396,7 +429,40 @@ int launch_binning(const Buffers &B, const double *x_keys, const uint32_t *gid_s
 
 int launch_permute_a_to_b(const Buffers &B, cudaStream_t st)
 {
-    k_permute_a_to_b<<<blocks(B.n), kBlock, 0, st>>>(B);
+    k_permute_a_to_b<false><<<blocks(B.n), kBlock, 0, st>>>(B);
+    return 1;
+}
+
+int launch_same_order_a_to_b(const Buffers &B, cudaStream_t st)
+{
+    k_permute_a_to_b<true><<<blocks(B.n), kBlock, 0, st>>>(B);
+    return 1;
+}
+
+// Order B becomes order A as it is (the particles binned at r^n, before the
+// first step that reuses the r^0 lists): slot, cell and the state that order A
+// carries between steps.
+__global__ void __launch_bounds__(kBlock) k_adopt_b(Buffers B)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.n) return;
+    const uint32_t g = B.gid_b[s];
+    B.gid_a[s] = g;
+    if (g == kNoParticle) return;
+    B.cell_a[s] = B.cell_b[s];
+    const int n = B.n;
+    for (int a = 0; a < B.dim; ++a) {
+        const size_t q = (size_t)a * n + s;
+        B.x_a[q] = B.x_b[q];
+        B.vn_a[q] = B.vn_b[q];
+        B.vnm1_a[q] = B.vnm1_b[q];
+    }
+    B.pn_a[s] = B.pn_b[s];
+}
+
+int launch_adopt_b(const Buffers &B, cudaStream_t st)
+{
+    k_adopt_b<<<blocks(B.n), kBlock, 0, st>>>(B);
     return 1;
 }
 

@@ -108,6 +108,8 @@ struct Phys {
     int pad_m;
     double disp2_max;    // (skin / 2)^2: the largest squared pseudo-time displacement
                          // from r^0 that the lists with a skin cover (moving = 2)
+    double disp2_reuse;  // (list_skin / 2)^2: the largest squared distance of r^{n+1}
+                         // from r^0 that lets the r^0 lists serve the next step
 };
 
 // Stop reason of a loop without the pair cache that reached pause_at iterations
@@ -165,6 +167,13 @@ struct Buffers {
     int nseg2;                      // row segments of the 2D FP32C list builder, all instances
     int nsm;                        // streaming multiprocessors of the device
     int l2_stream;                  // 1: the pair cache exceeds half of L2 (its rows stream, evicting first)
+    int reuse_lists;                // 1: the r^0 lists (with list_skin) serve the next step at r^n
+    // with reused lists: *relist is 1 when a particle of the latest step ended
+    // farther than list_skin / 2 from its r^0; the next step then bins and lists
+    // at r^n. A launch with relist_run 0 or 1 runs only when *relist equals it
+    // (-1: always); the pass to order A clears *relist
+    int *relist;
+    int relist_run;
     int dim, fp32c, K;              // K = neighbour capacity per particle
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
     int stages;                     // pair-cache chunks in flight per warp (lanes = 1), 2..kMaxStages
@@ -261,11 +270,25 @@ __device__ __forceinline__ int block_instance(const Buffers &B, int first)
 int launch_binning(const Buffers &B, const double *x_keys, const uint32_t *gid_src, cudaStream_t st);
 int launch_permute_a_to_b(const Buffers &B, cudaStream_t st);
 int launch_permute_b_to_a(const Buffers &B, cudaStream_t st);
+#ifdef __CUDACC__
+// True in a launch of the step graph guarded on relisting (see Buffers::relist)
+// whose condition does not hold. Block-uniform.
+__device__ __forceinline__ bool skip_relist(const Buffers &B)
+{
+    return B.relist && B.relist_run >= 0 && *(volatile const int *)B.relist != B.relist_run;
+}
+#endif
+// Order B = order A with offsets at r^n from the slots' cells (lists reused).
+int launch_same_order_a_to_b(const Buffers &B, cudaStream_t st);
+// Order A = order B (after a binning at r^n that starts reusing lists).
+int launch_adopt_b(const Buffers &B, cudaStream_t st);
 // Neighbour lists of every slot at positions xpos (order of the latest binning);
 // one launch.
 void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st,
                   bool sliced);
-int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st);
+// The state-n pass at r^n in order B: its lists built first, or (build_lists
+// false) the r^0 lists of the previous step, built with list_skin, as they are.
+int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st, bool build_lists = true);
 int launch_loop_resume(const Buffers &B, cudaStream_t st);
 int launch_restart_steps(const Buffers &B, cudaStream_t st);
 int launch_pair_cache_pass(const Buffers &B, const double *xpos, const uint32_t *gid, cudaStream_t st);

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kBlock) k_nlist_cells(Buffers B, const double 
                                                         const uint32_t *__restrict__ gid, uint32_t *__restrict__ lists,
                                                         int Ks)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     constexpr int NC = D == 3 ? 27 : 9;                 // surrounding cells
     constexpr int CH = F32 ? 256 : 128;                 // staged candidates per round
     using S = typename Staged<F32>::type;
@@ -265,6 +266,7 @@ constexpr int kBufEntries = 8;
 __global__ void __launch_bounds__(kBlock) k_nlist_cells3_f32(Buffers B, const double *__restrict__ xpos,
                                                              uint32_t *__restrict__ lists, int Ks)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     constexpr int NC = 27;
     constexpr int CH = 256;
     __shared__ float4 cand[kWarpsPerBlock][CH];
@@ -431,6 +433,7 @@ constexpr int kRowsMinSegments = 16384;
 __global__ void __launch_bounds__(kBlock) k_nlist_rows2_f32(Buffers B, const double *__restrict__ xpos,
                                                             uint32_t *__restrict__ lists, int Ks)
 {
+    if (skip_relist(B)) return;   // (the step graph: relisting or not)
     constexpr int NCOL = kSeg2 + 2;                     // candidate columns
     constexpr int NT = 3 * NCOL;                        // candidate cells
     constexpr int CH = 256;

@@ -1136,7 +1136,7 @@ __global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
             const Geom &G = B.geo[inst];
             const double dt = B.phys[inst].dt;
             const bool move = !B.phys[inst].steady;               // steady mode: the particles stay
-            double v2 = 0.0;
+            double v2 = 0.0, d2 = 0.0;
             for (int a = 0; a < D; ++a) {
                 const size_t q = (size_t)a * n + s;
                 const double vn = B.vn_a[q];
@@ -1149,10 +1149,22 @@ __global__ void __launch_bounds__(kBlock) k_outer(Buffers B)
                         else if (x < G.lo[a]) x = __dadd_rn(x, G.L[a]);
                     }
                     B.x_a[q] = x;
+                    if (B.reuse_lists) {
+                        // distance of r^{n+1} from r^0 (nearest image)
+                        double dx = x - B.xp_a[q];
+                        if (G.periodic[a]) {
+                            if (dx > G.halfL[a]) dx -= G.L[a];
+                            else if (dx < -G.halfL[a]) dx += G.L[a];
+                        }
+                        d2 += dx * dx;
+                    }
                 }
                 B.vnm1_a[q] = vn;
                 B.vn_a[q] = vK;
             }
+            // the lists built at r^0 serve the next step only within list_skin / 2;
+            // beyond, the next step bins and lists at r^n itself
+            if (B.reuse_lists && !(d2 < B.phys[inst].disp2_reuse)) *(volatile int *)B.relist = 1;
             double p1, p0;
             if (F32) {
                 p1 = B.nb32[fin][s].w;

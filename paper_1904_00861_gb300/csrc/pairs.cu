@@ -444,12 +444,15 @@ int nlist_lanes(int n)
 }
 
 // Neighbour lists at r^n (order B), then the wall values and the state-n pass.
-int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st)
+int launch_state_n(const Buffers &B, bool predictor, cudaStream_t st, bool build_lists)
 {
     constexpr int L = kSumLanes;
     const int nb = (int)(((long long)B.n * L + kBlock - 1) / kBlock);
-    launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st, false);
-    int k = 1;
+    int k = 0;
+    if (build_lists) {
+        launch_nlist(B, B.x_b, B.cell_b, B.gid_b, st, false);
+        k = 1;
+    }
     if (B.nw > 0) {
         DTSPH_DISPATCH(B.dim, B.fp32c, (k_walls_state_n<D, F32, L><<<nb, kBlock, 0, st>>>(B)));
         ++k;

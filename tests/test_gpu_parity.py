@@ -1033,3 +1033,95 @@ def test_automatic_form_counts_restart_with_the_state():
     fs3 = sim.form_stats()
     assert fs3["steps_cache"] + fs3["steps_nocache"] + fs3["steps_switched"] == 2
     sim.close()
+
+
+# ------------------------------------------------- lists reused at r^n (list_skin)
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+@pytest.mark.parametrize("case", ["tgv2d_jitter", "tgv3d"])
+def test_reused_lists_match_the_oracle(case, prec):
+    """list_skin = h/20: the lists built at r^0 to 3h + skin also serve the next
+    step's pass at r^n (pairs beyond 3h add exact zeros). Over four steps: the
+    oracle's velocities and pressures (1e-10 FP64, 1e-5 FP32C relative) and the
+    iteration counts of the two-build pipeline, step by step; an eval_rates call
+    between steps (which bins and lists anew) changes nothing."""
+    d = CASES[case]()
+    h = d["cfg"]["h"]
+    reuse = make_sim(d, precision=prec, graph=2, lanes=1, list_skin=0.05 * h)
+    base = make_sim(d, precision=prec, graph=2, lanes=1)
+    orc = make_oracle(d)
+    for k in range(4):
+        reuse.step(1)
+        base.step(1)
+        orc.step(1)
+        if k == 1:
+            reuse.rates()
+    reuse.sync()
+    tol = 1e-10 if prec == dt.DTSPH_FP64 else 1e-5
+    assert rel(reuse.v, orc.v) < tol and rel(reuse.p, orc.p) < 10 * tol
+    assert [r["iters"] for r in reuse.stats()] == [r["iters"] for r in base.stats()]
+    assert rel(reuse.v, base.v) < tol
+    reuse.close()
+    base.close()
+
+
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_reused_lists_with_particles_crossing_the_periodic_edges(prec):
+    """The Taylor-Green field carried by a uniform drift, so that particles
+    cross the periodic edges every step (the vortex alone has no flow through
+    them): with the r^0 lists reused at r^n, a particle wrapped to the far side
+    keeps the FP32 offset its lists' cell shifts assume, and after four steps
+    the velocities and pressures match the oracle's as without reuse."""
+    d = CASES["tgv2d_jitter"]()
+    v = d["v"] + np.array([0.5, -0.25])
+    d = dict(d, v=v, v_prev=v)
+    h = d["cfg"]["h"]
+    reuse = make_sim(d, precision=prec, graph=2, lanes=1, list_skin=0.05 * h)
+    orc = make_oracle(d)
+    reuse.step(4)
+    recs = orc.step(4)
+    reuse.sync()
+    tol = 1e-10 if prec == dt.DTSPH_FP64 else 1e-5
+    assert rel(reuse.v, orc.v) < tol and rel(reuse.p, orc.p) < 10 * tol
+    assert [r["iters"] for r in reuse.stats()] == [r["iters"] for r in recs]
+    reuse.close()
+
+
+def test_reused_lists_in_a_batch_and_their_limits():
+    """A batch with each instance's own list skin (h/20) takes the iterations
+    of the instances' solo runs with two builds per step and their velocities to
+    FP32 rounding; with a skin too small for any step's motion every step bins
+    and lists at r^n again, with the same results; walls, shifting and the other
+    loop drivers are refused."""
+    work = [synth.tgv2d(37, re=100.0, seed=11), synth.tgv2d(20, re=630.0, seed=12),
+            synth.tgv2d(45, re=250.0, seed=13)]
+    b = dt.Batch([dict(w["cfg"], list_skin=0.05 * w["cfg"]["h"]) for w in work], precision=dt.DTSPH_FP32C,
+                 graph=2, lanes=1)
+    b.set_state(work)
+    b.step(3)
+    b.sync()
+    vb = b.field(dt.FIELD_VEL)
+    for i, w in enumerate(work):
+        s = make_sim(w, precision=dt.DTSPH_FP32C, graph=2, lanes=1)
+        s.step(3)
+        assert [r["iters"] for r in b.stats(i)] == [r["iters"] for r in s.stats()], i
+        assert rel(vb[i], s.v) < 1e-5, i
+        s.close()
+    b.close()
+    d = CASES["tgv2d_jitter"]()
+    tiny = make_sim(d, precision=dt.DTSPH_FP32C, graph=2, lanes=1, list_skin=1e-12)
+    base = make_sim(d, precision=dt.DTSPH_FP32C, graph=2, lanes=1)
+    for s in (tiny, base):
+        s.step(4)
+        s.sync()
+    assert [r["iters"] for r in tiny.stats()] == [r["iters"] for r in base.stats()]
+    assert rel(tiny.v, base.v) < 1e-5
+    tiny.close()
+    base.close()
+    with pytest.raises(dt.DtsphError) as e:
+        make_sim(CASES["cavity"](), precision=dt.DTSPH_FP32C, graph=2, list_skin=1e-3)
+    assert e.value.code == dt.DTSPH_E_UNSUPPORTED
+    for over in (dict(shifting=1), dict(graph=1)):
+        with pytest.raises(dt.DtsphError) as e:
+            dt.Simulation(d["cfg"], precision=dt.DTSPH_FP32C, **dict(dict(graph=2, list_skin=1e-3), **over))
+        assert e.value.code == dt.DTSPH_E_UNSUPPORTED
