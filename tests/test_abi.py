@@ -72,6 +72,22 @@ def test_version_and_argument_errors_without_gpu(so):
     with pytest.raises(lib_pkg.DtsphError) as e:
         lib_pkg.dtsph_create(p)
     assert e.value.code == -1
+    # the pair-term form, the cell size and the reused lists: bad values are
+    # argument errors, unsupported combinations DTSPH_E_UNSUPPORTED (-7)
+    for over, code in ((dict(form=3), -1), (dict(form=-1), -1), (dict(form=2, moving=1), -7),
+                       (dict(cell_scale=0.5), -1), (dict(cell_scale=5.0), -1), (dict(list_skin=-0.01), -1),
+                       (dict(list_skin=float("nan")), -1), (dict(list_skin=0.01, graph=1), -7),
+                       (dict(list_skin=0.01, graph=2, shifting=1), -7), (dict(list_skin=0.01, graph=2, moving=1), -7),
+                       (dict(list_skin=0.01, graph=2, steady=1), -7)):
+        p = lib_pkg.make_params(dict(base, **over))
+        with pytest.raises(lib_pkg.DtsphError) as e:
+            lib_pkg.dtsph_create(p)
+        assert e.value.code == code, over
+    # a batch's instances all reuse lists (each its own skin) or none does
+    good = [lib_pkg.make_params(dict(base, graph=2, list_skin=0.01)), lib_pkg.make_params(dict(base, graph=2))]
+    with pytest.raises(lib_pkg.DtsphError) as e:
+        lib_pkg.dtsph_batch_create(good)
+    assert e.value.code == -1
 
 
 def test_struct_layouts_match_header(tmp_path):
