@@ -163,7 +163,9 @@ typedef struct {
                                  exact zeros, the kernel gradient vanishing there). When a
                                  particle's r^{n+1} lies farther than list_skin / 2 from its
                                  r^0, the next step bins and lists at r^n as without it (on
-                                 the device, in the step graph). Only with the persistent
+                                 the device, in the step graph); a new state of the same
+                                 particles set between steps keeps the lists on the same
+                                 terms. Only with the persistent
                                  loop (graph = 2), no walls, particles fixed in pseudo-time,
                                  no shifting and no steady mode (DTSPH_E_UNSUPPORTED
                                  otherwise). 0 (default): two builds per step. The instances

@@ -641,7 +641,7 @@ int allocate(dtsph_ctx *c, const int64_t *nf)
     B.reuse_lists = c->prm[0].list_skin > 0;
     B.relist_run = -1;
     if (B.reuse_lists) {
-        A(B.relist, 1)
+        A(B.relist, 1) A(B.slot_of, (size_t)std::max(B.nf, 1))
     }
     if (B.async_loop) {
         A(B.il, ni) A(d_sched, ni)
@@ -1191,16 +1191,24 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
     c->launches += launch_restart_steps(c->B, c->stream);
     CK(cudaMemsetAsync(c->B.err, 0, sizeof(uint32_t), c->stream));
     double *sxw = NW > 0 ? c->sxw : nullptr, *svw = NW > 0 ? c->svw : nullptr;
+    // with reused lists and the same particles: the new state goes into the
+    // slots of order A as they are and the lists stay; a particle beyond the
+    // skin makes the next step bin and list at r^n (on the device)
+    const bool same = reuse && c->B.reuse_lists && c->lists_ready;
+    auto scatter = [&](const double *xs, const double *vs, const double *ps, const double *vps) {
+        return same ? launch_scatter_same(c->B, xs, vs, ps, vps, c->stream)
+                    : launch_scatter_in(c->B, xs, vs, ps, vps, sxw, svw, c->stream);
+    };
     if (!device && c->host_direct) {
         // the scatter kernel reads the caller's arrays where they are
-        c->launches += launch_scatter_in(c->B, x, v, p, vprev, sxw, svw, c->stream);
+        c->launches += scatter(x, v, p, vprev);
     } else {
         const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         CK(cudaMemcpyAsync(c->sx, x, bx, kind, c->stream));
         CK(cudaMemcpyAsync(c->sv, v, bx, kind, c->stream));
         CK(cudaMemcpyAsync(c->sp, p, bp, kind, c->stream));
         if (vprev) CK(cudaMemcpyAsync(svp, vprev, bx, kind, c->stream));
-        c->launches += launch_scatter_in(c->B, c->sx, c->sv, c->sp, svp, sxw, svw, c->stream);
+        c->launches += scatter(c->sx, c->sv, c->sp, svp);
     }
     CK(cudaGetLastError());
     if (!device) {
@@ -1210,7 +1218,7 @@ int set_particles_impl(dtsph_ctx *c, const int64_t *nf, const double *x, const d
         if (e & kErrNonFinite) return fail(c, DTSPH_E_ARG, "a particle position is not finite");
     }
     c->have_particles = true;
-    c->lists_ready = false;
+    c->lists_ready = same;
     c->steps = 0;
     c->steps_cache = c->steps_nocache = 0;
     CK(cudaMemsetAsync(c->form_count, 0, 3 * sizeof(unsigned long long), c->stream));

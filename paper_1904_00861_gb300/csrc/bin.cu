@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(kBlock) k_permute_b_to_a(Buffers B)
     const uint32_t g = B.gid_b[o];
     B.gid_a[s] = g;
     const bool wall = g >= (uint32_t)B.nf;
+    if (B.slot_of && !wall) B.slot_of[g] = s;
     if (B.wslot_a && wall) B.wslot_a[g - (uint32_t)B.nf] = s;
     const int cell = B.key[o];
     B.cell_a[s] = cell;
@@ -449,6 +450,7 @@ __global__ void __launch_bounds__(kBlock) k_adopt_b(Buffers B)
     const uint32_t g = B.gid_b[s];
     B.gid_a[s] = g;
     if (g == kNoParticle) return;
+    if (B.slot_of && g < (uint32_t)B.nf) B.slot_of[g] = s;
     B.cell_a[s] = B.cell_b[s];
     const int n = B.n;
     for (int a = 0; a < B.dim; ++a) {
@@ -463,6 +465,44 @@ __global__ void __launch_bounds__(kBlock) k_adopt_b(Buffers B)
 int launch_adopt_b(const Buffers &B, cudaStream_t st)
 {
     k_adopt_b<<<blocks(B.n), kBlock, 0, st>>>(B);
+    return 1;
+}
+
+// One thread per fluid particle in caller order (contexts without walls): its
+// new state into its slot of order A; the lists at r^0 stay valid while the
+// position lies within list_skin / 2 of the slot's r^0 (nearest image).
+__global__ void __launch_bounds__(kBlock) k_scatter_same(Buffers B, const double *__restrict__ x,
+                                                         const double *__restrict__ v, const double *__restrict__ p,
+                                                         const double *__restrict__ vprev)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= B.nf) return;
+    const int s = B.slot_of[f];
+    const int inst = B.inst_of[s];
+    const Geom &G = B.geo[inst];
+    const int n = B.n, dim = B.dim;
+    double d2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        const size_t so = (size_t)a * n;
+        const double xa = input_coord(x[(size_t)f * dim + a], G, a, B.err);
+        B.x_a[so + s] = xa;
+        B.vn_a[so + s] = v[(size_t)f * dim + a];
+        B.vnm1_a[so + s] = vprev ? vprev[(size_t)f * dim + a] : v[(size_t)f * dim + a];
+        double d = xa - B.xp_a[so + s];
+        if (G.periodic[a]) {
+            if (d > G.halfL[a]) d -= G.L[a];
+            else if (d < -G.halfL[a]) d += G.L[a];
+        }
+        d2 += d * d;
+    }
+    B.pn_a[s] = p[f];
+    if (!(d2 < B.phys[inst].disp2_reuse)) *(volatile int *)B.relist = 1;
+}
+
+int launch_scatter_same(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,
+                        cudaStream_t st)
+{
+    k_scatter_same<<<blocks(B.nf), kBlock, 0, st>>>(B, x, v, p, vprev);
     return 1;
 }
 

@@ -174,6 +174,7 @@ struct Buffers {
     // (-1: always); the pass to order A clears *relist
     int *relist;
     int relist_run;
+    int *slot_of;                   // with reused lists: [nf] slot of each fluid particle (caller index)
     int dim, fp32c, K;              // K = neighbour capacity per particle
     int lanes;                      // lanes per particle in the iterate kernel (1, 2, 4 or 8)
     int stages;                     // pair-cache chunks in flight per warp (lanes = 1), 2..kMaxStages
@@ -282,6 +283,10 @@ __device__ __forceinline__ bool skip_relist(const Buffers &B)
 int launch_same_order_a_to_b(const Buffers &B, cudaStream_t st);
 // Order A = order B (after a binning at r^n that starts reusing lists).
 int launch_adopt_b(const Buffers &B, cudaStream_t st);
+// A new state (caller order) into the slots of order A as they are, the lists
+// kept; a particle farther than list_skin / 2 from its r^0 sets *relist.
+int launch_scatter_same(const Buffers &B, const double *x, const double *v, const double *p, const double *vprev,
+                        cudaStream_t st);
 // Neighbour lists of every slot at positions xpos (order of the latest binning);
 // one launch.
 void launch_nlist(const Buffers &B, const double *xpos, const int *cell, const uint32_t *gid, cudaStream_t st,

@@ -1087,6 +1087,31 @@ def test_reused_lists_with_particles_crossing_the_periodic_edges(prec):
     reuse.close()
 
 
+@pytest.mark.parametrize("prec", [dt.DTSPH_FP64, dt.DTSPH_FP32C])
+def test_reused_lists_survive_setting_the_state_again(prec):
+    """With reused lists, setting the state read back after a step (same
+    particles) writes it into the slots as they are and keeps the lists: the
+    run then has the bits of one that never left the device, across periodic
+    edges (a drift carries particles through them)."""
+    d = CASES["tgv2d_jitter"]()
+    v = d["v"] + np.array([0.5, -0.25])
+    d = dict(d, v=v, v_prev=v)
+    skin = 0.05 * d["cfg"]["h"]
+    a = make_sim(d, precision=prec, graph=2, lanes=1, list_skin=skin)
+    b = make_sim(d, precision=prec, graph=2, lanes=1, list_skin=skin)
+    a.step(4)
+    b.step(2)
+    x, vb, p, vp = dt.dtsph_read_state(b.ctx, b.nf, 2)
+    b.set_state(x, vb, p, vp)
+    b.step(2)
+    for s in (a, b):
+        s.sync()
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.v, b.v) and np.array_equal(a.p, b.p)
+    assert [r["iters"] for r in a.stats()][2:] == [r["iters"] for r in b.stats()]
+    a.close()
+    b.close()
+
+
 def test_reused_lists_in_a_batch_and_their_limits():
     """A batch with each instance's own list skin (h/20) takes the iterations
     of the instances' solo runs with two builds per step and their velocities to
