@@ -1,5 +1,6 @@
 // Neighbour lists N(i) = {j != i : |r_ij| < 3h} (Sec. 3; 3h + skin for moving
-// particles with neighbour updates) of every slot, from the cell binning.
+// particles with neighbour updates, 3h + list_skin for lists reused at the next
+// r^n) of every slot, from the cell binning.
 //
 // One warp per home cell, the candidates in the lanes. The warp stages the
 // particles of the 3^D surrounding cells in shared memory, in the order rows
@@ -8,10 +9,13 @@
 // lane) and every home particle in turn, each lane tests its candidate against
 // that home particle. A ballot ranks the hits, which join the home particle's
 // list as one contiguous run, so a store of the warp touches one or two sectors
-// instead of one per lane. The lists are written per slot (slot s at s K + k)
-// into a staging array; k_list_slice then copies them into the layout the pair
-// kernels read, sliced by warp (entry k of slot s at ((s/32) K + k) 32 + s%32),
-// with whole-row stores.
+// instead of one per lane. The lists are written per slot (slot s at s Ks + k,
+// Ks = K rounded up to 8); the state-n, pair-cache and uncached-loop passes read
+// them there, and only the pass of particles moving in pseudo-time gets a copy
+// sliced by warp (k_list_slice: entry k of slot s at ((s/32) K + k) 32 + s%32).
+// Large 2D problems on the FP32C path take the row-segment builder
+// (k_nlist_rows2_f32), 3D ones k_nlist_cells3_f32; every builder gives the same
+// lists in the same order.
 //
 // The tests are those of the neighbour definition: FP64 positions, squares
 // summed in axis order without FMA, minimum image on periodic axes; the FP32C
