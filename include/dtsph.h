@@ -233,7 +233,9 @@ int dtsph_set_boundary(dtsph_ctx *ctx, int64_t nw, const double *x, const double
  * and predictor Eqs. v0/r0, pseudo-time loop Eqs. pkstar_frozen..pkp1_frozen
  * with Eq. dv_dtau_exact until Eq. conv or a stop rule holds, Eq. r-update).
  * Asynchronous: returns once the work is enqueued. Per-step statistics go to a
- * device log read by dtsph_read_stats. */
+ * device log read by dtsph_read_stats. With list_skin > 0, the first call after
+ * the particle set's binning or lists were rebuilt otherwise (a new particle set,
+ * dtsph_eval_rates, dtsph_build_neighbors) first bins and lists at r^n. */
 int dtsph_step(dtsph_ctx *ctx, int32_t nsteps);
 
 /* Batches: one context advancing ninst independent simulations together (each
